@@ -1,0 +1,148 @@
+"""FP64 CPU oracle for the regular-force step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference legs may import this package.  The product library never calls it,
+and it shares no code with the CUDA path.  The arithmetic lives in
+``nb_oracle.c`` (plain C, FP64, ascending-j loops); this module only compiles
+it with gcc and marshals numpy arrays through ctypes.
+
+Every function cites the passage of the paper it follows in the C source.
+Parity of every function is pinned by tests/test_oracle_pins.py against closed
+forms and invariants (two-body Kepler orbit, Newton's third law, jerk as the
+time derivative of the acceleration, the Plummer potential energy, energy
+conservation, brute-force neighbour sets, finite differences for the adjoint).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nb_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile nb_oracle.c into liboracle.so with gcc (portable flags, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+               "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.orc_predict.argtypes = [i64, dbl, P, P, P, P, P, P, P]
+        lib.orc_predict.restype = None
+        lib.orc_regular_force.argtypes = [i64, P, P, P, i64, P, P, ctypes.c_int, P, P, P, P, P, i32]
+        lib.orc_regular_force.restype = ctypes.c_int
+        lib.orc_regular_force_vjp.argtypes = [i64, P, P, P, i64, P, P, P, P, P, P, P]
+        lib.orc_regular_force_vjp.restype = ctypes.c_int
+        lib.orc_energy.argtypes = [i64, P, P, P, P, P]
+        lib.orc_energy.restype = None
+        lib.orc_hermite_run.argtypes = [i64, P, P, P, dbl, dbl, dbl, dbl, dbl, i64, P]
+        lib.orc_hermite_run.restype = ctypes.c_int
+        lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def num_threads() -> int:
+    return _load().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().orc_set_num_threads(int(n))
+
+
+def predict(t, x, v, a, jerk, t_last):
+    """Hermite predictor of all particles to time t -> (x_p, v_p), each (n,3)."""
+    lib = _load()
+    x, v, a, jerk = (_c(q, np.float64) for q in (x, v, a, jerk))
+    t_last = _c(t_last, np.float64)
+    n = x.shape[0]
+    xp, vp = np.empty_like(x), np.empty_like(v)
+    lib.orc_predict(n, float(t), _p(x), _p(v), _p(a), _p(jerk), _p(t_last), _p(xp), _p(vp))
+    return xp, vp
+
+
+def regular_force(xp, vp, m, idx, rs2, cap: int = 512, lists: bool = True):
+    """acc, jerk (n_i,3), pot (n_i), nb_count (n_i), nb_lists (list of int32 arrays, first `cap`)."""
+    lib = _load()
+    xp, vp, m = _c(xp, np.float64), _c(vp, np.float64), _c(m, np.float64)
+    idx = _c(idx, np.int32)
+    n, n_i = xp.shape[0], idx.shape[0]
+    rs2 = np.atleast_1d(_c(rs2, np.float64))
+    scalar = 1 if rs2.shape[0] == 1 and n_i != 1 else 0
+    if not scalar and rs2.shape[0] != n_i:
+        raise ValueError("rs2 must be a scalar or have one entry per active particle")
+    acc = np.empty((n_i, 3)); jerk = np.empty((n_i, 3)); pot = np.empty(n_i)
+    cnt = np.empty(n_i, np.int32)
+    lst = np.empty((n_i, max(cap, 1)), np.int32) if lists else None
+    rc = lib.orc_regular_force(n, _p(xp), _p(vp), _p(m), n_i, _p(idx), _p(rs2), scalar,
+                               _p(acc), _p(jerk), _p(pot), _p(cnt), _p(lst), int(cap))
+    if rc != 0:
+        raise IndexError("active index outside [0, n)")
+    out_lists = None
+    if lists:
+        out_lists = [lst[k, :min(int(cnt[k]), cap)].copy() for k in range(n_i)]
+    return acc, jerk, pot, cnt, out_lists
+
+
+def regular_force_vjp(xp, vp, m, idx, g_acc, g_jerk, g_pot):
+    """(g_x, g_v, g_m) of L = Σ g_acc·acc + g_jerk·jerk + g_pot·pot over the active set."""
+    lib = _load()
+    xp, vp, m = _c(xp, np.float64), _c(vp, np.float64), _c(m, np.float64)
+    idx = _c(idx, np.int32)
+    g_acc, g_jerk, g_pot = _c(g_acc, np.float64), _c(g_jerk, np.float64), _c(g_pot, np.float64)
+    n, n_i = xp.shape[0], idx.shape[0]
+    gx = np.empty((n, 3)); gv = np.empty((n, 3)); gm = np.empty(n)
+    rc = lib.orc_regular_force_vjp(n, _p(xp), _p(vp), _p(m), n_i, _p(idx), _p(g_acc), _p(g_jerk),
+                                   _p(g_pot), _p(gx), _p(gv), _p(gm))
+    if rc != 0:
+        raise IndexError("active index outside [0, n)")
+    return gx, gv, gm
+
+
+def energy(m, x, v):
+    """(K, W) with K = ½Σ m v², W = -Σ_{i<j} m_i m_j / r_ij."""
+    lib = _load()
+    m, x, v = _c(m, np.float64), _c(x, np.float64), _c(v, np.float64)
+    K, W = ctypes.c_double(), ctypes.c_double()
+    lib.orc_energy(m.shape[0], _p(m), _p(x), _p(v), ctypes.byref(K), ctypes.byref(W))
+    return K.value, W.value
+
+
+def hermite_run(m, x, v, t_end, eta=0.02, eta_s=0.01, dt_max=0.125, dt_fixed=0.0, max_blocks=0):
+    """Block-step Hermite integration to t_end -> (x, v, stats[blocks, particle steps, pairs])."""
+    lib = _load()
+    m = _c(m, np.float64)
+    x = np.array(x, dtype=np.float64, order="C", copy=True)
+    v = np.array(v, dtype=np.float64, order="C", copy=True)
+    stats = np.zeros(4)
+    rc = lib.orc_hermite_run(m.shape[0], _p(m), _p(x), _p(v), float(t_end), float(eta), float(eta_s),
+                             float(dt_max), float(dt_fixed), int(max_blocks), _p(stats))
+    if rc != 0:
+        raise RuntimeError("hermite_run stopped at max_blocks")
+    return x, v, stats[:3]

@@ -1,0 +1,333 @@
+/*
+ * nb_oracle.c — plain FP64 CPU oracle for the regular-force step of NBODY6++GPU
+ * (Wang et al. 2015, MNRAS 450, 4070).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * loads this file; only the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code, header, table or helper with the
+ * CUDA path.
+ *
+ * What it computes, and where the paper defines it:
+ *  - Position/velocity prediction of all particles to the block time
+ *    (Sec. 3.3.3 "Position and velocity prediction"; the Taylor form itself is
+ *    not printed in the paper — it is the standard Hermite predictor the paper
+ *    cites in Sec. 2, Makino 1991).
+ *  - The regular force: for every active particle i, acceleration, its time
+ *    derivative (jerk) and potential summed over all other particles, plus the
+ *    list of neighbours inside r_s (Sec. 2, Ahmad-Cohen scheme; Sec. 3.2.1,
+ *    "Regular force and potential (GPU)"; Table 2 gives the O(N_i N) cost).
+ *    The sums here run over ALL j != i: the split into inside/outside r_s is a
+ *    subtraction by the consumer (reading recorded in the design doc).
+ *  - Its vector-Jacobian product (adjoint), obtained by differentiating the sums.
+ *  - A fourth-order Hermite integrator with hierarchical power-of-two block
+ *    steps (Sec. 2; the corrector and the Aarseth step criterion are the
+ *    textbook forms of Makino 1991 / Makino & Aarseth 1992, which the paper
+ *    cites but does not print).
+ *  - Kinetic and potential energy (Sec. 3.3.2 needs W for N-body scaling).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no ISA intrinsics).
+ * Loops over j run in ascending index order; OpenMP only splits the outer loop
+ * over independent outputs, so every result is bitwise reproducible.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* Hermite predictor (Taylor series to the jerk term) for all n particles:
+ *   dt  = t - t_last
+ *   x_p = x + v dt + a dt^2/2 + jerk dt^3/6
+ *   v_p = v + a dt + jerk dt^2/2
+ * Arrays are row-major (n,3); t_last is (n). */
+void orc_predict(int64_t n, double t, const double *x, const double *v, const double *a,
+                 const double *jk, const double *t_last, double *xp, double *vp)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const double dt = t - t_last[i];
+        for (int c = 0; c < 3; ++c) {
+            const int64_t q = 3 * i + c;
+            xp[q] = x[q] + v[q] * dt + a[q] * dt * dt / 2.0 + jk[q] * dt * dt * dt / 6.0;
+            vp[q] = v[q] + a[q] * dt + jk[q] * dt * dt / 2.0;
+        }
+    }
+}
+
+/* Regular force, jerk and potential of the active particles idx[0..n_i) from all
+ * n predicted particles, with neighbour lists.
+ *
+ * For active i and every j != i (j ascending):
+ *   r = x_j - x_i,  w = v_j - v_i,  r2 = r.r
+ *   acc_i  += m_j r / |r|^3
+ *   jerk_i += m_j [ w / |r|^3 - 3 (r.w) r / |r|^5 ]
+ *   pot_i  -= m_j / |r|
+ *   j is a neighbour of i iff r2 < rs2_i.
+ * Output row k belongs to idx[k].  nb_list is (n_i, cap): the first cap
+ * neighbours in ascending j; nb_count[k] is the true count (may exceed cap).
+ * rs2 is (n_i) or, with rs2_scalar != 0, a single value.  nb_list may be NULL
+ * (counts only).  Returns 0, or -1 on an index outside [0, n). */
+int orc_regular_force(int64_t n, const double *xp, const double *vp, const double *m,
+                      int64_t n_i, const int32_t *idx, const double *rs2, int rs2_scalar,
+                      double *acc, double *jerk, double *pot,
+                      int32_t *nb_count, int32_t *nb_list, int32_t cap)
+{
+    for (int64_t k = 0; k < n_i; ++k)
+        if (idx[k] < 0 || idx[k] >= n) return -1;
+
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < n_i; ++k) {
+        const int64_t i = idx[k];
+        const double rs2_i = rs2_scalar ? rs2[0] : rs2[k];
+        double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0, ph = 0;
+        int32_t cnt = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double rx = xp[3 * j + 0] - xp[3 * i + 0];
+            const double ry = xp[3 * j + 1] - xp[3 * i + 1];
+            const double rz = xp[3 * j + 2] - xp[3 * i + 2];
+            const double wx = vp[3 * j + 0] - vp[3 * i + 0];
+            const double wy = vp[3 * j + 1] - vp[3 * i + 1];
+            const double wz = vp[3 * j + 2] - vp[3 * i + 2];
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            const double rinv = 1.0 / sqrt(r2);
+            const double rinv2 = rinv * rinv;
+            const double mr3 = m[j] * rinv * rinv2;
+            const double rw = rx * wx + ry * wy + rz * wz;
+            ax += mr3 * rx;
+            ay += mr3 * ry;
+            az += mr3 * rz;
+            jx += mr3 * (wx - 3.0 * rw * rinv2 * rx);
+            jy += mr3 * (wy - 3.0 * rw * rinv2 * ry);
+            jz += mr3 * (wz - 3.0 * rw * rinv2 * rz);
+            ph -= m[j] * rinv;
+            if (r2 < rs2_i) {
+                if (nb_list && cnt < cap) nb_list[k * (int64_t)cap + cnt] = (int32_t)j;
+                ++cnt;
+            }
+        }
+        acc[3 * k + 0] = ax;  acc[3 * k + 1] = ay;  acc[3 * k + 2] = az;
+        jerk[3 * k + 0] = jx; jerk[3 * k + 1] = jy; jerk[3 * k + 2] = jz;
+        pot[k] = ph;
+        if (nb_count) nb_count[k] = cnt;
+    }
+    return 0;
+}
+
+/* Per-pair adjoint terms.  For the loss contribution of pair (i, j),
+ *   L_ij = m_j [ g_a.r/|r|^3 + g_j.w/|r|^3 - 3 (r.w)(g_j.r)/|r|^5 - g_p/|r| ],
+ * with cotangents (g_a, g_j, g_p) of (acc_i, jerk_i, pot_i), this returns
+ *   dr = dL_ij/dr,  dw = dL_ij/dw,  dm = dL_ij/dm_j. */
+static void pair_adjoint(double rx, double ry, double rz, double wx, double wy, double wz, double mj,
+                         const double *ga, const double *gj, double gp,
+                         double *dr, double *dw, double *dm)
+{
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double rinv = 1.0 / sqrt(r2);
+    const double rinv2 = rinv * rinv;
+    const double rinv3 = rinv * rinv2;
+    const double rinv5 = rinv3 * rinv2;
+    const double rinv7 = rinv5 * rinv2;
+    const double q = rx * wx + ry * wy + rz * wz;        /* r.w   */
+    const double ar = ga[0] * rx + ga[1] * ry + ga[2] * rz; /* g_a.r */
+    const double jr = gj[0] * rx + gj[1] * ry + gj[2] * rz; /* g_j.r */
+    const double jw = gj[0] * wx + gj[1] * wy + gj[2] * wz; /* g_j.w */
+    const double r[3] = {rx, ry, rz}, w[3] = {wx, wy, wz};
+    for (int c = 0; c < 3; ++c) {
+        /* d/dr of each term of L_ij */
+        const double d_acc = ga[c] * rinv3 - 3.0 * ar * r[c] * rinv5;
+        const double d_jw = -3.0 * jw * r[c] * rinv5;
+        const double d_qjr = -3.0 * (w[c] * jr + q * gj[c]) * rinv5 + 15.0 * q * jr * r[c] * rinv7;
+        const double d_pot = gp * r[c] * rinv3;
+        dr[c] = mj * (d_acc + d_jw + d_qjr + d_pot);
+        dw[c] = mj * (gj[c] * rinv3 - 3.0 * jr * r[c] * rinv5);
+    }
+    *dm = ar * rinv3 + jw * rinv3 - 3.0 * q * jr * rinv5 - gp * rinv;
+}
+
+/* Vector-Jacobian product of (acc, jerk, pot) over the active set w.r.t. the
+ * predicted positions, velocities and masses of all n particles:
+ *   L = sum_k g_acc[k].acc_k + g_jerk[k].jerk_k + g_pot[k] pot_k.
+ * Since r = x_j - x_i and w = v_j - v_i:
+ *   g_x[j] += dL_ij/dr,  g_x[i] -= dL_ij/dr   (same for v),  g_m[j] += dL_ij/dm_j.
+ * The j-side sum (over active i) and the i-side sum (over all j) are two loops
+ * over disjoint outputs.  g_x, g_v (n,3) and g_m (n) are overwritten. */
+int orc_regular_force_vjp(int64_t n, const double *xp, const double *vp, const double *m,
+                          int64_t n_i, const int32_t *idx,
+                          const double *g_acc, const double *g_jerk, const double *g_pot,
+                          double *g_x, double *g_v, double *g_m)
+{
+    for (int64_t k = 0; k < n_i; ++k)
+        if (idx[k] < 0 || idx[k] >= n) return -1;
+    /* j-side: particle j as the source of every active i's sums */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < n; ++j) {
+        double gx[3] = {0, 0, 0}, gv[3] = {0, 0, 0}, gm = 0;
+        for (int64_t k = 0; k < n_i; ++k) {
+            const int64_t i = idx[k];
+            if (i == j) continue;
+            double dr[3], dw[3], dm;
+            pair_adjoint(xp[3 * j] - xp[3 * i], xp[3 * j + 1] - xp[3 * i + 1], xp[3 * j + 2] - xp[3 * i + 2],
+                         vp[3 * j] - vp[3 * i], vp[3 * j + 1] - vp[3 * i + 1], vp[3 * j + 2] - vp[3 * i + 2],
+                         m[j], g_acc + 3 * k, g_jerk + 3 * k, g_pot[k], dr, dw, &dm);
+            for (int c = 0; c < 3; ++c) { gx[c] += dr[c]; gv[c] += dw[c]; }
+            gm += dm;
+        }
+        for (int c = 0; c < 3; ++c) { g_x[3 * j + c] = gx[c]; g_v[3 * j + c] = gv[c]; }
+        g_m[j] = gm;
+    }
+    /* i-side: the active particle as the receiver */
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < n_i; ++k) {
+        const int64_t i = idx[k];
+        double gx[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dr[3], dw[3], dm;
+            pair_adjoint(xp[3 * j] - xp[3 * i], xp[3 * j + 1] - xp[3 * i + 1], xp[3 * j + 2] - xp[3 * i + 2],
+                         vp[3 * j] - vp[3 * i], vp[3 * j + 1] - vp[3 * i + 1], vp[3 * j + 2] - vp[3 * i + 2],
+                         m[j], g_acc + 3 * k, g_jerk + 3 * k, g_pot[k], dr, dw, &dm);
+            for (int c = 0; c < 3; ++c) { gx[c] += dr[c]; gv[c] += dw[c]; }
+        }
+        for (int c = 0; c < 3; ++c) { g_x[3 * i + c] -= gx[c]; g_v[3 * i + c] -= gv[c]; }
+    }
+    return 0;
+}
+
+/* Kinetic and potential energy: K = 1/2 sum m v^2, W = -sum_{i<j} m_i m_j / r_ij. */
+void orc_energy(int64_t n, const double *m, const double *x, const double *v, double *K, double *W)
+{
+    double k = 0.0, w = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        k += 0.5 * m[i] * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+#pragma omp parallel for reduction(+ : w) schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double wi = 0.0;
+        for (int64_t j = i + 1; j < n; ++j) {
+            const double rx = x[3 * j] - x[3 * i], ry = x[3 * j + 1] - x[3 * i + 1], rz = x[3 * j + 2] - x[3 * i + 2];
+            wi -= m[i] * m[j] / sqrt(rx * rx + ry * ry + rz * rz);
+        }
+        w += wi;
+    }
+    *K = k;
+    *W = w;
+}
+
+static double norm3(const double *a) { return sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+/* Largest power of two (2^-k) not above dt_crit and not above dt_max. */
+static double quantise_step(double dt_crit, double dt_max)
+{
+    double dt = dt_max;
+    while (dt > dt_crit && dt > 1e-30) dt *= 0.5;
+    return dt;
+}
+
+/* Fourth-order Hermite integration with hierarchical block time steps.
+ *
+ * Start: force and jerk of all particles at t = 0; dt_i = the largest power of
+ * two below eta_s |a|/|jerk| (capped at dt_max).  Each block step: t_next =
+ * min_i(t_i + dt_i); the active block is every i with t_i + dt_i == t_next; all
+ * particles are predicted to t_next; the active ones get their new force and
+ * jerk (a1, j1) from the predicted state and are corrected with
+ *   a2 = [-6 (a0 - a1) - dt (4 j0 + 2 j1)] / dt^2,
+ *   a3 = [12 (a0 - a1) + 6 dt (j0 + j1)] / dt^3,
+ *   x1 = x_p + dt^4/24 a2 + dt^5/120 a3,   v1 = v_p + dt^3/6 a2 + dt^4/24 a3.
+ * New step from the Aarseth criterion with the end-of-step derivatives
+ * (a2' = a2 + dt a3):
+ *   dt_crit = sqrt(eta (|a1||a2'| + |j1|^2) / (|j1||a3| + |a2'|^2)),
+ * halved until not above dt_crit, or doubled when dt_crit >= 2 dt, t_next is a
+ * multiple of 2 dt and 2 dt <= dt_max (block rule: steps are powers of 0.5).
+ * With dt_fixed > 0 every particle takes that one step (shared time step).
+ * x, v are advanced in place to t_end (all particles synchronised there).
+ * stats (optional, 4 doubles): block steps, particle steps, pair evaluations, 0.
+ * Returns 0, or -2 if max_blocks was reached. */
+int orc_hermite_run(int64_t n, const double *m, double *x, double *v, double t_end, double eta,
+                    double eta_s, double dt_max, double dt_fixed, int64_t max_blocks, double *stats)
+{
+    double *a = calloc(3 * n, sizeof(double)), *jk = calloc(3 * n, sizeof(double));
+    double *xp = malloc(3 * n * sizeof(double)), *vp = malloc(3 * n * sizeof(double));
+    double *t = calloc(n, sizeof(double)), *dt = malloc(n * sizeof(double));
+    double *a1 = malloc(3 * n * sizeof(double)), *j1 = malloc(3 * n * sizeof(double));
+    double *pot = malloc(n * sizeof(double));
+    int32_t *act = malloc(n * sizeof(int32_t));
+    const double zero = 0.0;
+    int rc = 0;
+    double nblocks = 0, nsteps = 0, npairs = 0;
+
+    for (int64_t i = 0; i < n; ++i) act[i] = (int32_t)i;
+    orc_regular_force(n, x, v, m, n, act, &zero, 1, a, jk, pot, NULL, NULL, 0);
+    npairs += (double)n * (double)(n - 1);
+    for (int64_t i = 0; i < n; ++i) {
+        if (dt_fixed > 0) dt[i] = dt_fixed;
+        else dt[i] = quantise_step(eta_s * norm3(a + 3 * i) / norm3(jk + 3 * i), dt_max);
+    }
+
+    for (;;) {
+        double t_next = INFINITY;
+        for (int64_t i = 0; i < n; ++i)
+            if (t[i] + dt[i] < t_next) t_next = t[i] + dt[i];
+        if (t_next > t_end) break;
+        if (max_blocks > 0 && nblocks >= (double)max_blocks) { rc = -2; break; }
+        int64_t n_act = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (t[i] + dt[i] == t_next) act[n_act++] = (int32_t)i;
+        /* predict everybody to the block time */
+        orc_predict(n, t_next, x, v, a, jk, t, xp, vp);
+        orc_regular_force(n, xp, vp, m, n_act, act, &zero, 1, a1, j1, pot, NULL, NULL, 0);
+        npairs += (double)n_act * (double)(n - 1);
+        for (int64_t k = 0; k < n_act; ++k) {
+            const int64_t i = act[k];
+            const double h = dt[i];
+            double a2[3], a3[3], a2e[3];
+            for (int c = 0; c < 3; ++c) {
+                const double da = a[3 * i + c] - a1[3 * k + c];
+                a2[c] = (-6.0 * da - h * (4.0 * jk[3 * i + c] + 2.0 * j1[3 * k + c])) / (h * h);
+                a3[c] = (12.0 * da + 6.0 * h * (jk[3 * i + c] + j1[3 * k + c])) / (h * h * h);
+                x[3 * i + c] = xp[3 * i + c] + h * h * h * h / 24.0 * a2[c] + h * h * h * h * h / 120.0 * a3[c];
+                v[3 * i + c] = vp[3 * i + c] + h * h * h / 6.0 * a2[c] + h * h * h * h / 24.0 * a3[c];
+                a[3 * i + c] = a1[3 * k + c];
+                jk[3 * i + c] = j1[3 * k + c];
+                a2e[c] = a2[c] + h * a3[c];
+            }
+            t[i] = t_next;
+            if (dt_fixed <= 0) {
+                const double na = norm3(a + 3 * i), nj = norm3(jk + 3 * i);
+                const double n2 = norm3(a2e), n3 = norm3(a3);
+                const double crit = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+                double hn = h;
+                if (crit < hn) {
+                    while (hn > crit && hn > 1e-30) hn *= 0.5;
+                } else if (crit >= 2.0 * h && 2.0 * h <= dt_max && fmod(t_next, 2.0 * h) == 0.0) {
+                    hn = 2.0 * h;
+                }
+                dt[i] = hn;
+            }
+        }
+        nblocks += 1;
+        nsteps += (double)n_act;
+    }
+    if (stats) { stats[0] = nblocks; stats[1] = nsteps; stats[2] = npairs; stats[3] = 0; }
+    free(a); free(jk); free(xp); free(vp); free(t); free(dt); free(a1); free(j1); free(pot); free(act);
+    return rc;
+}

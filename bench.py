@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the regular-force step on one or more GB300s.
+
+One step = one regular-force block cycle on the million-body workload: for each
+active block of 2^10, 2^14, 2^17 and 2^20 particles (the sorted time-step list of a
+King W0 = 6 cluster of 2^20 j-particles incl. 5% binary centre-of-mass particles,
+Kroupa masses), predict all particles to the block time (FP64) and compute the mixed-
+precision force, jerk, potential and CSR neighbour lists (r_s for a median of 80,
+cap 512).  value = pairs (N_i x N summed over the blocks) / device time, in
+Ginteractions/s; 60 flops per pair gives the FP32 roofline fraction.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own seeded cluster (independent problems, weak
+scaling, no collective in the step); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "force+jerk Ginteractions/s & %FP32 peak at N=2^20, mixed vs FP64, at stated error"
+UNIT = "Ginteractions/s"
+FLOPS_PER_PAIR = 60
+BLOCKS = (1 << 10, 1 << 14, 1 << 17, 1 << 20)
+NB_CAP = 512
+NB_PER_ROW = 256  # CSR capacity per active particle (median count is ~80)
+WORKLOAD = ("King W0=6, N=2^20 j-particles (5% binary c.m.), Kroupa IMF, N-body units; "
+            "active blocks 2^10/2^14/2^17/2^20 from the sorted step list; "
+            "predict + mixed regular force + neighbour CSR per block")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def build_workload(seed):
+    import workloads as W
+    cl, rs2 = W.king_1m_binaries(seed=seed)
+    steps = W.block_steps(cl, seed=seed)
+    order = W.sorted_step_list(steps).astype(np.int32)
+    a0, j0, tl = W.hermite_state(cl, seed=seed, t_block=0.125, steps=steps)
+    return cl, rs2, order, a0, j0, tl
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def fp32_peak_tflops(num_sms):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flops (FMA) x maximum SM clock."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+        src = "SMs x 128 FP32 lanes x 2 x sm_max_mhz of MEASURED_PEAKS.json"
+    except (OSError, ValueError):
+        src = "SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal maximum SM clock)"
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12, src
+
+
+def oracle_rate(cl, rs2, rows, threads=None):
+    """Oracle pairs/s on `rows` active particles against all j (host cores)."""
+    import oracle
+    if threads:
+        oracle.set_num_threads(threads)
+    t0 = time.perf_counter()
+    oracle.regular_force(cl.x, cl.v, cl.m, rows, rs2, cap=NB_CAP, lists=False)
+    dt = time.perf_counter() - t0
+    return rows.size * cl.n / dt, dt
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    cl, rs2, order, a0, j0, tl = build_workload(seed=2)
+    xp, vp = oracle.predict(0.125, cl.x, cl.v, a0, j0, tl)
+    cl.x, cl.v = xp, vp
+    rate, _ = oracle_rate(cl, rs2, order[:16])
+    rows = int(max(16, min(1 << 20, 6.0 * rate / cl.n)))  # ~6 s of oracle work per step
+    sample = order[:rows]
+    for _ in range(args.warmup):
+        oracle_rate(cl, rs2, sample)
+    tot, pairs = 0.0, 0
+    for _ in range(args.steps):
+        r, dt = oracle_rate(cl, rs2, sample)
+        tot += dt
+        pairs += rows * cl.n
+    value = pairs / tot / 1e9
+    cores = oracle.num_threads()
+    sample_desc = (f"{rows} active rows (head of the sorted step list) x all {cl.n} j per step, "
+                   "FP64 direct sum with neighbour lists")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": cl.n, "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1504_03687_gb300 import Context
+
+    cl, rs2, order, a0, j0, tl = build_workload(seed=2 + 1000 * rank)
+    n = cl.n
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    state = [T(q) for q in (cl.x, cl.v, a0, j0, cl.m, tl)]
+    idx_dev = [T(order[:b]) for b in BLOCKS]
+    rs2_dev = torch.tensor([rs2], dtype=torch.float64, device=dev)
+    ctx = Context(n, precision="mixed", nb_cap=NB_CAP, device=local)
+    ctx.set_particles(*state)
+    outs = [None] * len(BLOCKS)
+
+    def step():
+        for q, b in enumerate(BLOCKS):
+            ctx.predict(0.125)
+            outs[q] = ctx.regular_force(idx_dev[q], rs2_dev, nb_capacity=b * NB_PER_ROW, out=outs[q])
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    pairs_step = sum(BLOCKS) * n
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    ctx.timings()  # reset counters
+    ctx.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)  # L2 flush between timed steps (outside the events)
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ctx.set_timing(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    phase = ctx.timings()
+    ctx.sync()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * pairs_step * args.steps / (ms_max * 1e-3) / 1e9
+    launches = int(sum(v[1] for v in phase.values()))
+    force_ms = phase["force"][0]
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, peak_src = fp32_peak_tflops(num_sms)
+    achieved = FLOPS_PER_PAIR * pairs_step * args.steps / (force_ms * 1e-3) / 1e12
+
+    # accuracy at the stated error: sampled rows of the full block vs the FP64 oracle,
+    # and the GPU FP64 path on the 2^14 block (the >= 3x comparison)
+    extra = {}
+    if rank == 0:
+        import oracle
+        rng = np.random.default_rng(0)
+        sel = np.sort(rng.choice(BLOCKS[-1], 64, replace=False))
+        full = outs[-1]
+        xp, vp = ctx.get_predicted()
+        xp_np, vp_np = xp.cpu().numpy(), vp.cpu().numpy()
+        rows = order[:BLOCKS[-1]][sel]
+        ref = oracle.regular_force(xp_np, vp_np, cl.m, rows, rs2, cap=NB_CAP, lists=False)
+
+        def errs(acc, jerk, pot):
+            ea = np.linalg.norm(acc - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
+            ej = np.linalg.norm(jerk - ref[1], axis=1) / np.linalg.norm(ref[1], axis=1)
+            ep = np.abs(pot - ref[2]) / np.abs(ref[2])
+            return {q: {"median": float(np.median(e)), "max": float(e.max())}
+                    for q, e in (("acc", ea), ("jerk", ej), ("pot", ep))}
+        extra["error_vs_oracle_mixed"] = errs(full.acc[sel].cpu().numpy(), full.jerk[sel].cpu().numpy(),
+                                              full.pot[sel].cpu().numpy())
+        ctx64 = Context(n, precision="fp64", nb_cap=NB_CAP, device=local)
+        ctx64.set_particles(*state)
+        ctx64.predict(0.125)
+        b64 = BLOCKS[1]
+        out64 = ctx64.regular_force(idx_dev[1], rs2_dev, nb_capacity=b64 * NB_PER_ROW)
+        ctx64.sync()
+        ctx64.timings()
+        ctx64.set_timing(True)
+        reps = 2
+        for _ in range(reps):
+            out64 = ctx64.regular_force(idx_dev[1], rs2_dev, nb_capacity=b64 * NB_PER_ROW, out=out64)
+        ph64 = ctx64.timings()
+        ctx64.sync()
+        fp64_rate = reps * b64 * n / (ph64["force"][0] * 1e-3) / 1e9
+        ctx.set_timing(True)
+        for _ in range(reps):
+            ctx.regular_force(idx_dev[1], rs2_dev, nb_capacity=b64 * NB_PER_ROW, out=outs[1])
+        ph32 = ctx.timings()
+        ctx.set_timing(False)
+        mixed_rate = reps * b64 * n / (ph32["force"][0] * 1e-3) / 1e9
+        sel64 = np.sort(rng.choice(b64, 32, replace=False))
+        ref = oracle.regular_force(xp_np, vp_np, cl.m, order[:b64][sel64], rs2, cap=NB_CAP, lists=False)
+        extra["error_vs_oracle_fp64"] = errs(out64.acc[sel64].cpu().numpy(), out64.jerk[sel64].cpu().numpy(),
+                                             out64.pot[sel64].cpu().numpy())
+        extra["fp64_path"] = {"block": b64, "force_kernel_Ginteractions_s": fp64_rate,
+                              "mixed_force_kernel_Ginteractions_s_same_block": mixed_rate,
+                              "mixed_over_fp64": mixed_rate / fp64_rate}
+        ctx64.close()
+
+    # end to end through the public API with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_state = [pin(q) for q in (cl.x, cl.v, a0, j0, cl.m, tl)]
+        h_idx = [pin(order[:b]) for b in BLOCKS]
+        h_out = []
+        for b in BLOCKS:
+            from paper_1504_03687_gb300.api import ForceResult
+            h_out.append(ForceResult(acc=pin(np.empty((b, 3))), jerk=pin(np.empty((b, 3))), pot=pin(np.empty(b)),
+                                     nb_off=pin(np.empty(b + 1, np.int64)),
+                                     nb_idx=pin(np.empty(b * NB_PER_ROW, np.int32)),
+                                     nb_count=pin(np.empty(b, np.int32))))
+        h2d = sum(q.nbytes for q in h_state) + sum(q.nbytes for q in h_idx) + 8 * len(BLOCKS)
+
+        def e2e_step():
+            d2h = 0
+            ctx.set_particles(*h_state)
+            for q, b in enumerate(BLOCKS):
+                ctx.predict(0.125)
+                r = host_force(ctx, h_idx[q], rs2, h_out[q])
+                d2h += r
+            return d2h
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            d2h = e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        el_t = torch.tensor([el], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(el_t, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * pairs_step * args.steps / float(el_t.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        xp, vp = ctx.get_predicted()
+        cl.x, cl.v = xp.cpu().numpy(), vp.cpu().numpy()
+        rate, _ = oracle_rate(cl, rs2, order[:32])
+        rows = int(max(32, min(BLOCKS[-1], 12.0 * rate / n)))  # ~12 s of oracle work
+        rate, dt = oracle_rate(cl, rs2, order[:rows])
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{rows} active rows (head of the sorted step list) x all {n} j, FP64 direct sum "
+                         f"with neighbour lists, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded King W0=6 cluster per rank)",
+            "config": {"workload": WORKLOAD, "n": n, "blocks": list(BLOCKS), "pairs_per_step": pairs_step,
+                       "nb_cap": NB_CAP, "rs2": rs2, "precision": "mixed (ds-f32 differences, f32 pairwise, "
+                       "f64 predictor and per-tile sums)", "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"{world} independent clusters, one per GPU"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "force (mixed tiled / j-streamed)", "peak_source": peak_src,
+                         "flops_per_pair": FLOPS_PER_PAIR, "force_kernel_ms_per_step": force_ms / args.steps},
+            "fp32_peak_frac_whole_step": value * 1e9 * FLOPS_PER_PAIR / (peak * 1e12) / world,
+            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phase.items()},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def host_force(ctx, idx, rs2, out):
+    """nb_regular_force with host buffers; returns the bytes copied device->host."""
+    import ctypes
+    lib = ctx.lib
+    n_i = idx.shape[0]
+    rs2a = np.array([rs2], dtype=np.float64)
+    s = lib.nb_regular_force(ctx.h, n_i, idx.ctypes.data, rs2a.ctypes.data, 1, out.acc.ctypes.data,
+                             out.jerk.ctypes.data, out.pot.ctypes.data, out.nb_off.ctypes.data,
+                             out.nb_idx.ctypes.data, out.nb_idx.shape[0], out.nb_count.ctypes.data, 0)
+    if s not in (0, 5):
+        raise RuntimeError(f"nb_regular_force failed: {s} {lib.nb_last_error(ctx.h).decode()}")
+    used = int(min(out.nb_off[-1], out.nb_idx.shape[0]))
+    return n_i * (24 + 24 + 8 + 4) + (n_i + 1) * 8 + used * 4
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * nbgpu.h — C ABI of the GB300 (sm_103a) regular-force library.
+ *
+ * The library computes the regular-force step of the NBODY6++GPU method
+ * (Wang et al. 2015, MNRAS 450, 4070): every particle of an active block gets
+ * its acceleration, the time derivative of the acceleration (jerk) and its
+ * potential from all N predicted particles, plus the list of its neighbours
+ * inside the radius r_s (Sec. 2, Ahmad-Cohen neighbour scheme; Sec. 3.2.1,
+ * regular force, potential and neighbour list on the GPU; Table 2, O(N_i N)
+ * work per regular step).  All particles are first predicted to the block time
+ * (Sec. 3.3.3; the fourth-order Hermite predictor of Sec. 2).
+ *
+ * Conventions shared by every entry point
+ *  - Units are whatever the caller uses with G = 1 (the paper uses N-body units).
+ *  - Vectors are row-major (n, 3) arrays of double; scalars per particle are (n).
+ *  - The caller owns every buffer it passes; the library owns only the
+ *    context's internal device state and scratch.
+ *  - `on_device` = 1: every array argument of that call is a device pointer and
+ *    the call is asynchronous on the context stream (results are valid after
+ *    nb_sync or any later stream-ordered operation).  `on_device` = 0: every
+ *    array argument is a host pointer; the call copies in, computes, copies out
+ *    and returns after the results are in host memory.
+ *  - Errors never abort the process.  Every function returns an nb_status;
+ *    nb_last_error() gives a one-line description of the last failure.  After a
+ *    CUDA error the context is unusable (NB_ERR_STATE) and should be freed.
+ *  - A context is not thread-safe: use one per host thread / stream.
+ *  - Sums over j run over all j != i.  The sum over particles outside r_s only
+ *    (the Ahmad-Cohen regular force proper) is this result minus the sum over the
+ *    neighbour list, which the caller forms.  No softening is applied; two
+ *    distinct particles at the same position give inf/NaN.
+ */
+#ifndef NBGPU_H
+#define NBGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx; /* opaque */
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_ARG = 1,          /* invalid argument (null pointer, size, index out of range) */
+    NB_ERR_STATE = 2,        /* call order violated, or context broken by an earlier CUDA error */
+    NB_ERR_OOM = 3,          /* device allocation failed */
+    NB_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    NB_ERR_NB_OVERFLOW = 5,  /* warning: results valid, some neighbour lists were cut at nb_cap
+                                or the CSR output capacity was too small */
+    NB_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired */
+    NB_ERR_DEVICE = 7        /* a device-side consistency check failed */
+} nb_status;
+
+typedef enum {
+    NB_FP64 = 0,  /* every step in FP64 */
+    NB_MIXED = 1  /* FP64 predictor; pairwise arithmetic in FP32 on double-single
+                     coordinate differences; per-tile sums promoted to FP64 */
+} nb_precision;
+
+typedef struct {
+    int64_t n_max;      /* largest particle count the context will hold (>= 1) */
+    int32_t precision;  /* nb_precision */
+    int32_t nb_cap;     /* neighbours stored per active particle (>= 1); the true count is
+                           always reported */
+    int32_t device;     /* CUDA device ordinal */
+    int32_t flags;      /* reserved, must be 0 */
+    void *stream;       /* cudaStream_t to run on; NULL = a stream the context creates */
+} nb_config;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t nb_version(void);
+
+/* Create a context on cfg->device.  *out receives the handle (NULL on failure). */
+nb_status nb_init(nb_ctx **out, const nb_config *cfg);
+
+/* Destroy a context and free its device memory.  Safe on NULL. */
+nb_status nb_free(nb_ctx *ctx);
+
+/* Run subsequent calls on `stream` (a cudaStream_t; NULL = CUDA's default stream). */
+nb_status nb_set_stream(nb_ctx *ctx, void *stream);
+
+/* Load the Hermite state of n particles (1 <= n <= n_max): positions x, velocities
+ * v, acceleration a and jerk at each particle's last step time t_last, and masses m
+ * — the inputs of the predictor.  Arrays are copied; the caller keeps ownership. */
+nb_status nb_set_particles(nb_ctx *ctx, int64_t n, const double *x, const double *v,
+                           const double *a, const double *jerk, const double *m,
+                           const double *t_last, int32_t on_device);
+
+/* Predict all n particles to time t (Sec. 3.3.3):
+ *   dt = t - t_last;  x_p = x + v dt + a dt^2/2 + jerk dt^3/6;  v_p = v + a dt + jerk dt^2/2,
+ * in FP64, and build the j-records the force kernels read. */
+nb_status nb_predict(nb_ctx *ctx, double t);
+
+/* Load an already predicted state (x_p, v_p, m) of n particles directly, in place
+ * of nb_set_particles + nb_predict (used by the autograd binding and the chained
+ * integrator, whose predictor runs outside the library). */
+nb_status nb_set_predicted(nb_ctx *ctx, int64_t n, const double *xp, const double *vp,
+                           const double *m, int32_t on_device);
+
+/* Copy the predicted positions and velocities (n,3) out of the context. */
+nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp, int32_t on_device);
+
+/* Regular force step for the active block idx[0..n_i) (Sec. 2, Sec. 3.2.1):
+ *   acc_k  = sum_{j != i} m_j r / |r|^3
+ *   jerk_k = sum_{j != i} m_j [ w / |r|^3 - 3 (r.w) r / |r|^5 ]
+ *   pot_k  = - sum_{j != i} m_j / |r|
+ * with i = idx[k], r = x_p,j - x_p,i, w = v_p,j - v_p,i, over all n predicted particles.
+ * Neighbours: j != i with |r|^2 < rs2 (rs2[k], or rs2[0] for all when rs2_scalar != 0).
+ *
+ * idx:           (n_i) int32, unique, each in [0, n); output row k is for idx[k].
+ * acc, jerk:     (n_i, 3) double, overwritten.   pot: (n_i) double, overwritten.
+ * nb_off:        (n_i + 1) int64 CSR offsets, overwritten (may be NULL with nb_idx NULL).
+ * nb_idx:        (nb_idx_capacity) int32: the neighbours of row k, ascending j, are
+ *                nb_idx[nb_off[k] .. nb_off[k+1]); each list holds at most nb_cap entries
+ *                (the smallest j's).  If the lists need more than nb_idx_capacity entries
+ *                in total, the CSR is cut there and NB_ERR_NB_OVERFLOW is reported.
+ * nb_count_true: (n_i) int32, the untruncated neighbour count of each row (may be NULL).
+ * n_i = 0 is allowed (only nb_off[0] = 0 is written).
+ * Status: NB_ERR_NB_OVERFLOW (a warning, results valid) is returned by this call when
+ * on_device = 0, and by the next nb_sync when on_device = 1. */
+nb_status nb_regular_force(nb_ctx *ctx, int64_t n_i, const int32_t *idx, const double *rs2,
+                           int32_t rs2_scalar, double *acc, double *jerk, double *pot,
+                           int64_t *nb_off, int32_t *nb_idx, int64_t nb_idx_capacity,
+                           int32_t *nb_count_true, int32_t on_device);
+
+/* Vector-Jacobian product of nb_regular_force's (acc, jerk, pot) w.r.t. the predicted
+ * positions, velocities and masses of all n particles (no counterpart in the paper;
+ * obtained by differentiating the sums above).  For
+ *   L = sum_k g_acc[k].acc_k + g_jerk[k].jerk_k + g_pot[k] pot_k
+ * it writes g_x = dL/dx_p, g_v = dL/dv_p (n,3) and g_m = dL/dm (n), overwriting them.
+ * Uses the state of the last nb_predict / nb_set_predicted. */
+nb_status nb_regular_force_backward(nb_ctx *ctx, int64_t n_i, const int32_t *idx,
+                                    const double *g_acc, const double *g_jerk,
+                                    const double *g_pot, double *g_x, double *g_v, double *g_m,
+                                    int32_t on_device);
+
+/* Per-phase device timing: with timing enabled, every phase of every later call is
+ * bracketed by CUDA events on the context stream.  nb_get_timings synchronises the
+ * stream and returns, per phase, the summed device time in ms and the number of kernels
+ * launched since the previous nb_get_timings (launch counts are kept even with timing
+ * off), then resets both.  Phases: 0 predict, 1 force, 2 partial reduction,
+ * 3 neighbour CSR, 4 backward.  ms and launches have 5 entries each. */
+nb_status nb_set_timing(nb_ctx *ctx, int32_t enable);
+nb_status nb_get_timings(nb_ctx *ctx, double *ms, int64_t *launches);
+
+/* Wait for all work queued on the context stream and return the first deferred
+ * status (NB_OK, NB_ERR_NB_OVERFLOW, NB_ERR_TIMEOUT, NB_ERR_DEVICE or a CUDA error)
+ * raised since the previous nb_sync; the deferred status is then cleared. */
+nb_status nb_sync(nb_ctx *ctx);
+
+/* One-line description of the last error on this context (never NULL). */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Describe the launch plan nb_regular_force would use (host-only, no GPU work):
+ * out[0] = kernel id (0 = FP64 tiled, 1 = mixed tiled, 2 = mixed j-streamed),
+ * out[1] = i-particles per CTA, out[2] = j-splits, out[3] = CTAs, out[4] = j-tile. */
+nb_status nb_plan(const nb_ctx *ctx, int64_t n, int64_t n_i, int64_t *out);
+
+/* The same plan for a given device shape, without a context or a GPU (host-only):
+ * num_sms SMs and ctas_per_sm[0..4] resident CTAs of the four mixed tiled variants and
+ * the FP64 tiled kernel (NULL = 1 each). */
+nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
+                      int64_t n_i, int64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBGPU_H */

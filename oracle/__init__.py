@@ -54,6 +54,10 @@ def _load():
         lib.orc_energy.restype = None
         lib.orc_hermite_run.argtypes = [i64, P, P, P, dbl, dbl, dbl, dbl, dbl, i64, P]
         lib.orc_hermite_run.restype = ctypes.c_int
+        lib.orc_hermite_record.argtypes = [i64, P, P, P, dbl, dbl, dbl, dbl, i64, P, P, P, i64, i64, P]
+        lib.orc_hermite_record.restype = ctypes.c_int
+        lib.orc_hermite_replay.argtypes = [i64, P, P, P, i64, P, P, P]
+        lib.orc_hermite_replay.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -146,3 +150,40 @@ def hermite_run(m, x, v, t_end, eta=0.02, eta_s=0.01, dt_max=0.125, dt_fixed=0.0
     if rc != 0:
         raise RuntimeError("hermite_run stopped at max_blocks")
     return x, v, stats[:3]
+
+
+def hermite_record(m, x, v, t_end, eta=0.02, eta_s=0.01, dt_max=0.125, max_blocks=0, cap_blocks=1 << 16):
+    """Block-step run that records its schedule -> (x, v, [(t_next, active int32 array), ...])."""
+    lib = _load()
+    m = _c(m, np.float64)
+    x = np.array(x, dtype=np.float64, order="C", copy=True)
+    v = np.array(v, dtype=np.float64, order="C", copy=True)
+    n = m.shape[0]
+    t_next = np.empty(cap_blocks)
+    off = np.empty(cap_blocks + 1, np.int64)
+    cap_act = cap_blocks * n if cap_blocks * n < (1 << 26) else (1 << 26)
+    act = np.empty(cap_act, np.int32)
+    nb = ctypes.c_int64()
+    rc = lib.orc_hermite_record(n, _p(m), _p(x), _p(v), float(t_end), float(eta), float(eta_s), float(dt_max),
+                                int(max_blocks), _p(t_next), _p(off), _p(act), cap_blocks, cap_act, ctypes.byref(nb))
+    if rc not in (0, -2):
+        raise RuntimeError(f"hermite_record failed ({rc})")
+    sched = [(float(t_next[b]), act[off[b]:off[b + 1]].copy()) for b in range(nb.value)]
+    return x, v, sched
+
+
+def hermite_replay(m, x, v, schedule):
+    """Replay a frozen schedule [(t_next, active), ...] from (x, v) at t = 0 -> (x, v)."""
+    lib = _load()
+    m = _c(m, np.float64)
+    x = np.array(x, dtype=np.float64, order="C", copy=True)
+    v = np.array(v, dtype=np.float64, order="C", copy=True)
+    t_next = np.array([s[0] for s in schedule], dtype=np.float64)
+    off = np.zeros(len(schedule) + 1, np.int64)
+    off[1:] = np.cumsum([len(s[1]) for s in schedule])
+    act = np.ascontiguousarray(np.concatenate([np.asarray(s[1], np.int32) for s in schedule]) if schedule
+                               else np.zeros(0, np.int32))
+    rc = lib.orc_hermite_replay(m.shape[0], _p(m), _p(x), _p(v), len(schedule), _p(t_next), _p(off), _p(act))
+    if rc != 0:
+        raise RuntimeError(f"hermite_replay failed ({rc})")
+    return x, v

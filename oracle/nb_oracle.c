@@ -262,8 +262,51 @@ static double quantise_step(double dt_crit, double dt_max)
  * x, v are advanced in place to t_end (all particles synchronised there).
  * stats (optional, 4 doubles): block steps, particle steps, pair evaluations, 0.
  * Returns 0, or -2 if max_blocks was reached. */
+/* Optional schedule record / replay of hermite_core:
+ *  record: t_next[b] and the active set act_idx[act_off[b] .. act_off[b+1]) of every block
+ *          step b are stored (capacities cap_blocks, cap_act; -3 is returned when full);
+ *  replay: the block times and active sets are taken from the arrays instead of the step
+ *          criterion (a frozen schedule; the corrector still uses h = t_next - t_i). */
+typedef struct {
+    double *t_next;
+    int64_t *act_off;
+    int32_t *act_idx;
+    int64_t cap_blocks, cap_act, n_blocks;
+} orc_schedule;
+
+static int hermite_core(int64_t n, const double *m, double *x, double *v, double t_end, double eta,
+                        double eta_s, double dt_max, double dt_fixed, int64_t max_blocks, double *stats,
+                        orc_schedule *record, const orc_schedule *replay);
+
 int orc_hermite_run(int64_t n, const double *m, double *x, double *v, double t_end, double eta,
                     double eta_s, double dt_max, double dt_fixed, int64_t max_blocks, double *stats)
+{
+    return hermite_core(n, m, x, v, t_end, eta, eta_s, dt_max, dt_fixed, max_blocks, stats, NULL, NULL);
+}
+
+/* As orc_hermite_run, recording the schedule (see orc_schedule); *n_blocks receives its length. */
+int orc_hermite_record(int64_t n, const double *m, double *x, double *v, double t_end, double eta,
+                       double eta_s, double dt_max, int64_t max_blocks, double *t_next, int64_t *act_off,
+                       int32_t *act_idx, int64_t cap_blocks, int64_t cap_act, int64_t *n_blocks)
+{
+    orc_schedule s = {t_next, act_off, act_idx, cap_blocks, cap_act, 0};
+    const int rc = hermite_core(n, m, x, v, t_end, eta, eta_s, dt_max, 0.0, max_blocks, NULL, &s, NULL);
+    *n_blocks = s.n_blocks;
+    return rc;
+}
+
+/* Replay n_blocks recorded block steps from the state (x, v) at t = 0. */
+int orc_hermite_replay(int64_t n, const double *m, double *x, double *v, int64_t n_blocks, const double *t_next,
+                       const int64_t *act_off, const int32_t *act_idx)
+{
+    orc_schedule s = {(double *)t_next, (int64_t *)act_off, (int32_t *)act_idx, n_blocks, act_off[n_blocks],
+                      n_blocks};
+    return hermite_core(n, m, x, v, INFINITY, 0.0, 0.0, 1.0, 0.0, 0, NULL, NULL, &s);
+}
+
+static int hermite_core(int64_t n, const double *m, double *x, double *v, double t_end, double eta,
+                        double eta_s, double dt_max, double dt_fixed, int64_t max_blocks, double *stats,
+                        orc_schedule *record, const orc_schedule *replay)
 {
     double *a = calloc(3 * n, sizeof(double)), *jk = calloc(3 * n, sizeof(double));
     double *xp = malloc(3 * n * sizeof(double)), *vp = malloc(3 * n * sizeof(double));
@@ -285,20 +328,37 @@ int orc_hermite_run(int64_t n, const double *m, double *x, double *v, double t_e
 
     for (;;) {
         double t_next = INFINITY;
-        for (int64_t i = 0; i < n; ++i)
-            if (t[i] + dt[i] < t_next) t_next = t[i] + dt[i];
-        if (t_next > t_end) break;
-        if (max_blocks > 0 && nblocks >= (double)max_blocks) { rc = -2; break; }
         int64_t n_act = 0;
-        for (int64_t i = 0; i < n; ++i)
-            if (t[i] + dt[i] == t_next) act[n_act++] = (int32_t)i;
+        if (replay) {
+            const int64_t b = (int64_t)nblocks;
+            if (b >= replay->n_blocks) break;
+            t_next = replay->t_next[b];
+            for (int64_t q = replay->act_off[b]; q < replay->act_off[b + 1]; ++q) act[n_act++] = replay->act_idx[q];
+        } else {
+            for (int64_t i = 0; i < n; ++i)
+                if (t[i] + dt[i] < t_next) t_next = t[i] + dt[i];
+            if (t_next > t_end) break;
+            if (max_blocks > 0 && nblocks >= (double)max_blocks) { rc = -2; break; }
+            for (int64_t i = 0; i < n; ++i)
+                if (t[i] + dt[i] == t_next) act[n_act++] = (int32_t)i;
+        }
+        if (record) {
+            const int64_t b = record->n_blocks;
+            const int64_t o = b == 0 ? 0 : record->act_off[b];
+            if (b >= record->cap_blocks || o + n_act > record->cap_act) { rc = -3; break; }
+            if (b == 0) record->act_off[0] = 0;
+            record->t_next[b] = t_next;
+            for (int64_t k = 0; k < n_act; ++k) record->act_idx[o + k] = act[k];
+            record->act_off[b + 1] = o + n_act;
+            record->n_blocks = b + 1;
+        }
         /* predict everybody to the block time */
         orc_predict(n, t_next, x, v, a, jk, t, xp, vp);
         orc_regular_force(n, xp, vp, m, n_act, act, &zero, 1, a1, j1, pot, NULL, NULL, 0);
         npairs += (double)n_act * (double)(n - 1);
         for (int64_t k = 0; k < n_act; ++k) {
             const int64_t i = act[k];
-            const double h = dt[i];
+            const double h = t_next - t[i]; /* = dt[i] exactly (dyadic times) unless replaying */
             double a2[3], a3[3], a2e[3];
             for (int c = 0; c < 3; ++c) {
                 const double da = a[3 * i + c] - a1[3 * k + c];
@@ -311,7 +371,7 @@ int orc_hermite_run(int64_t n, const double *m, double *x, double *v, double t_e
                 a2e[c] = a2[c] + h * a3[c];
             }
             t[i] = t_next;
-            if (dt_fixed <= 0) {
+            if (dt_fixed <= 0 && !replay) {
                 const double na = norm3(a + 3 * i), nj = norm3(jk + 3 * i);
                 const double n2 = norm3(a2e), n3 = norm3(a3);
                 const double crit = sqrt(eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));

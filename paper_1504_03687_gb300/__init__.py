@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) regular-force library for NBODY6++GPU-style direct N-body integration.
+
+The regular-force step of Wang et al. (2015): FP64 prediction of all particles,
+then for every particle of an active block the acceleration, jerk and potential
+from all N particles and the neighbour list inside r_s, computed by hand-written
+CUDA kernels behind a C ABI (include/nbgpu.h).  This package is the thin Python
+binding (argument marshalling only).
+"""
+from .api import Context, ForceResult, NBError, NBOverflow, load_library, plan_for  # noqa: F401
+
+__all__ = ["Context", "ForceResult", "NBError", "NBOverflow", "load_library", "plan_for"]

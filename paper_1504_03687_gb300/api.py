@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in include/nbgpu.h.
+
+Argument marshalling only: every step of the regular-force path runs in the CUDA
+kernels of libnbgpu.so.  PyTorch supplies device memory and the stream.  There is
+no CPU fallback: if the library is missing or CUDA is unavailable, calls raise.
+
+Names follow the C ABI (nb_init -> Context, nb_set_particles -> set_particles,
+nb_predict -> predict, nb_regular_force -> regular_force, nb_regular_force_backward
+-> regular_force_backward).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+NB_OK, NB_ERR_ARG, NB_ERR_STATE, NB_ERR_OOM, NB_ERR_CUDA, NB_ERR_NB_OVERFLOW, NB_ERR_TIMEOUT, NB_ERR_DEVICE = range(8)
+STATUS_NAMES = {0: "NB_OK", 1: "NB_ERR_ARG", 2: "NB_ERR_STATE", 3: "NB_ERR_OOM", 4: "NB_ERR_CUDA",
+                5: "NB_ERR_NB_OVERFLOW", 6: "NB_ERR_TIMEOUT", 7: "NB_ERR_DEVICE"}
+NB_FP64, NB_MIXED = 0, 1
+PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED}
+
+# every symbol include/nbgpu.h declares
+EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particles", "nb_predict",
+           "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
+           "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_timing", "nb_get_timings")
+
+
+class NBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class NBOverflow(UserWarning):
+    """Neighbour lists were cut at nb_cap or at the CSR capacity (results otherwise valid)."""
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int64), ("precision", ctypes.c_int32), ("nb_cap", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(build_if_needed: bool = True):
+    """Load libnbgpu.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "nb_version": (i32, []),
+        "nb_init": (st, [ctypes.POINTER(P), ctypes.POINTER(_Config)]),
+        "nb_free": (st, [P]),
+        "nb_set_stream": (st, [P, P]),
+        "nb_set_particles": (st, [P, i64, P, P, P, P, P, P, i32]),
+        "nb_predict": (st, [P, dbl]),
+        "nb_set_predicted": (st, [P, i64, P, P, P, i32]),
+        "nb_get_predicted": (st, [P, P, P, i32]),
+        "nb_regular_force": (st, [P, i64, P, P, i32, P, P, P, P, P, i64, P, i32]),
+        "nb_regular_force_backward": (st, [P, i64, P, P, P, P, P, P, P, i32]),
+        "nb_sync": (st, [P]),
+        "nb_last_error": (ctypes.c_char_p, [P]),
+        "nb_plan": (st, [P, i64, i64, P]),
+        "nb_plan_for": (st, [i32, i32, P, i64, i64, P]),
+        "nb_set_timing": (st, [P, i32]),
+        "nb_get_timings": (st, [P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def plan_for(precision: str, num_sms: int, ctas_per_sm, n: int, n_i: int) -> dict:
+    """Host-only launch plan (no GPU needed)."""
+    lib = load_library()
+    out = (ctypes.c_int64 * 5)()
+    occ = (ctypes.c_int32 * 5)(*ctas_per_sm) if ctas_per_sm is not None else None
+    s = lib.nb_plan_for(PRECISIONS[precision], num_sms, ctypes.cast(occ, ctypes.c_void_p) if occ else None,
+                        n, n_i, ctypes.cast(out, ctypes.c_void_p))
+    if s != NB_OK:
+        raise NBError(s, "nb_plan_for rejected its arguments")
+    return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4])
+
+
+def _ptr(t):
+    """(pointer, on_device) of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None, None
+    if isinstance(t, np.ndarray):
+        if not t.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return t.ctypes.data, 0
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr(), 1 if t.is_cuda else 0
+
+
+@dataclass
+class ForceResult:
+    acc: object
+    jerk: object
+    pot: object
+    nb_off: object = None
+    nb_idx: object = None
+    nb_count: object = None
+
+    def neighbour_lists(self):
+        """Per-row neighbour index arrays (host numpy; synchronises)."""
+        off = self.nb_off.cpu().numpy() if hasattr(self.nb_off, "cpu") else self.nb_off
+        idx = self.nb_idx.cpu().numpy() if hasattr(self.nb_idx, "cpu") else self.nb_idx
+        return [idx[off[k]:off[k + 1]] for k in range(len(off) - 1)]
+
+
+class Context:
+    """One nb_ctx: device state of up to n_max particles at a fixed precision."""
+
+    def __init__(self, n_max: int, precision: str = "mixed", nb_cap: int = 512, device: int = 0,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the regular-force library has no CPU path")
+        self.precision = precision
+        self.nb_cap = nb_cap
+        self.device = device
+        self._stream = stream  # None: follow torch's current stream
+        cfg = _Config(n_max=n_max, precision=PRECISIONS[precision], nb_cap=nb_cap, device=device, flags=0,
+                      stream=None)
+        h = ctypes.c_void_p()
+        s = self.lib.nb_init(ctypes.byref(h), ctypes.byref(cfg))
+        if s != NB_OK:
+            raise NBError(s, f"nb_init(n_max={n_max}, precision={precision}, nb_cap={nb_cap}) failed")
+        self.h = h
+        self.n = 0
+
+    # -- plumbing ------------------------------------------------------------------------
+    def _check(self, s, what, allow_overflow=True):
+        if s == NB_OK:
+            return s
+        msg = self.lib.nb_last_error(self.h).decode()
+        if s == NB_ERR_NB_OVERFLOW and allow_overflow:
+            import warnings
+            warnings.warn(f"{what}: {msg}", NBOverflow, stacklevel=3)
+            return s
+        raise NBError(s, f"{what}: {msg}")
+
+    def _bind_stream(self):
+        torch = self._torch
+        st = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
+        self.lib.nb_set_stream(self.h, ctypes.c_void_p(st.cuda_stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nb_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI mirrors --------------------------------------------------------------------
+    def set_particles(self, x, v, a, jerk, m, t_last):
+        ptrs = [_ptr(q) for q in (x, v, a, jerk, m, t_last)]
+        dev = {p[1] for p in ptrs}
+        if len(dev) != 1:
+            raise ValueError("all arrays must live on the same side (host or device)")
+        self._bind_stream()
+        n = int(m.shape[0])
+        s = self.lib.nb_set_particles(self.h, n, *[p[0] for p in ptrs], dev.pop())
+        self._check(s, "nb_set_particles")
+        self.n = n
+
+    def predict(self, t: float):
+        self._bind_stream()
+        self._check(self.lib.nb_predict(self.h, float(t)), "nb_predict")
+
+    def set_predicted(self, xp, vp, m):
+        ptrs = [_ptr(q) for q in (xp, vp, m)]
+        dev = {p[1] for p in ptrs}
+        if len(dev) != 1:
+            raise ValueError("all arrays must live on the same side (host or device)")
+        self._bind_stream()
+        n = int(m.shape[0])
+        self._check(self.lib.nb_set_predicted(self.h, n, *[p[0] for p in ptrs], dev.pop()), "nb_set_predicted")
+        self.n = n
+
+    def get_predicted(self):
+        torch = self._torch
+        xp = torch.empty((self.n, 3), dtype=torch.float64, device=f"cuda:{self.device}")
+        vp = torch.empty_like(xp)
+        self._bind_stream()
+        self._check(self.lib.nb_get_predicted(self.h, xp.data_ptr(), vp.data_ptr(), 1), "nb_get_predicted")
+        return xp, vp
+
+    def regular_force(self, idx, rs2, neighbours: bool = True, nb_capacity: int | None = None,
+                      out: ForceResult | None = None) -> ForceResult:
+        """Regular force, jerk, potential (+ CSR neighbour lists) of the active block idx.
+
+        idx: int32 tensor (device) or numpy array (host); rs2: scalar float or per-row
+        array.  Device inputs give device outputs (asynchronous; nb_sync() reports the
+        deferred status); host inputs give host outputs (synchronous).
+        """
+        torch = self._torch
+        on_dev = isinstance(idx, torch.Tensor) and idx.is_cuda
+        n_i = int(idx.shape[0])
+        scalar = np.isscalar(rs2) or (hasattr(rs2, "ndim") and rs2.ndim == 0)
+        if on_dev:
+            dev = idx.device
+            if isinstance(rs2, torch.Tensor) and rs2.is_cuda and rs2.dtype == torch.float64:
+                # a device tensor: one entry = the same r_s^2 for every row
+                rs2_t = rs2.reshape(-1).contiguous()
+                scalar = rs2_t.numel() == 1
+            elif scalar:
+                rs2_t = torch.full((1,), float(rs2), dtype=torch.float64, device=dev)
+            else:
+                rs2_t = torch.as_tensor(rs2, dtype=torch.float64, device=dev).contiguous()
+            if out is None:
+                cap = (nb_capacity if nb_capacity is not None else n_i * self.nb_cap) if neighbours else 0
+                out = ForceResult(
+                    acc=torch.empty((n_i, 3), dtype=torch.float64, device=dev),
+                    jerk=torch.empty((n_i, 3), dtype=torch.float64, device=dev),
+                    pot=torch.empty((n_i,), dtype=torch.float64, device=dev),
+                    nb_off=torch.empty((n_i + 1,), dtype=torch.int64, device=dev) if neighbours else None,
+                    nb_idx=torch.empty((max(cap, 1),), dtype=torch.int32, device=dev) if neighbours else None,
+                    nb_count=torch.empty((n_i,), dtype=torch.int32, device=dev) if neighbours else None)
+            self._bind_stream()
+            cap_elems = int(out.nb_idx.numel()) if out.nb_idx is not None else 0
+            s = self.lib.nb_regular_force(
+                self.h, n_i, idx.data_ptr(), rs2_t.data_ptr(), 1 if scalar else 0, out.acc.data_ptr(),
+                out.jerk.data_ptr(), out.pot.data_ptr(), _ptr(out.nb_off)[0], _ptr(out.nb_idx)[0], cap_elems,
+                _ptr(out.nb_count)[0], 1)
+            self._check(s, "nb_regular_force")
+            out._rs2_keepalive = rs2_t
+            return out
+        idx_np = np.ascontiguousarray(np.asarray(idx), dtype=np.int32)
+        rs2_np = np.ascontiguousarray(np.atleast_1d(np.asarray(rs2, dtype=np.float64)))
+        cap = (nb_capacity if nb_capacity is not None else n_i * self.nb_cap) if neighbours else 0
+        res = ForceResult(acc=np.empty((n_i, 3)), jerk=np.empty((n_i, 3)), pot=np.empty(n_i),
+                          nb_off=np.empty(n_i + 1, np.int64) if neighbours else None,
+                          nb_idx=np.empty(max(cap, 1), np.int32) if neighbours else None,
+                          nb_count=np.empty(n_i, np.int32) if neighbours else None)
+        self._bind_stream()
+        s = self.lib.nb_regular_force(
+            self.h, n_i, idx_np.ctypes.data, rs2_np.ctypes.data, 1 if scalar else 0, res.acc.ctypes.data,
+            res.jerk.ctypes.data, res.pot.ctypes.data, _ptr(res.nb_off)[0], _ptr(res.nb_idx)[0],
+            cap if neighbours else 0, _ptr(res.nb_count)[0], 0)
+        res.status = self._check(s, "nb_regular_force")
+        return res
+
+    def regular_force_backward(self, idx, g_acc, g_jerk, g_pot):
+        """(g_x, g_v, g_m) for all n particles (device tensors in, device tensors out)."""
+        torch = self._torch
+        dev = idx.device
+        gx = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        gv = torch.empty_like(gx)
+        gm = torch.empty((self.n,), dtype=torch.float64, device=dev)
+        self._bind_stream()
+        s = self.lib.nb_regular_force_backward(self.h, int(idx.shape[0]), idx.data_ptr(), g_acc.data_ptr(),
+                                               g_jerk.data_ptr(), g_pot.data_ptr(), gx.data_ptr(), gv.data_ptr(),
+                                               gm.data_ptr(), 1)
+        self._check(s, "nb_regular_force_backward")
+        return gx, gv, gm
+
+    def set_timing(self, enable: bool = True):
+        self._check(self.lib.nb_set_timing(self.h, 1 if enable else 0), "nb_set_timing")
+
+    PHASES = ("predict", "force", "reduce", "neighbours", "backward")
+
+    def timings(self) -> dict:
+        """{phase: (device ms, kernel launches)} since the last call; synchronises."""
+        ms = (ctypes.c_double * 5)()
+        ln = (ctypes.c_int64 * 5)()
+        self._check(self.lib.nb_get_timings(self.h, ctypes.cast(ms, ctypes.c_void_p),
+                                            ctypes.cast(ln, ctypes.c_void_p)), "nb_get_timings")
+        return {p: (ms[q], ln[q]) for q, p in enumerate(self.PHASES)}
+
+    def sync(self, allow_overflow: bool = True) -> int:
+        return self._check(self.lib.nb_sync(self.h), "nb_sync", allow_overflow)
+
+    def plan(self, n: int, n_i: int) -> dict:
+        out = (ctypes.c_int64 * 5)()
+        self._check(self.lib.nb_plan(self.h, n, n_i, ctypes.cast(out, ctypes.c_void_p)), "nb_plan")
+        return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4])

@@ -1,0 +1,187 @@
+// force_fp64.cu — K2: regular force, jerk, potential and neighbour capture with every
+// operation in FP64 (paper Sec. 3.2.1).  The reference-precision GPU path: same work
+// decomposition as the mixed kernels (tiled for large active blocks, j-streamed for tiny
+// ones), FP64 partial sums [split][7][n_i] added in a fixed order by k_reduce.
+//
+// The neighbour test uses r^2 = (rx*rx + ry*ry) + rz*rz with IEEE round-to-nearest and no
+// contraction, the same arithmetic as a plain C evaluation of the definition.
+#include "nb_common.cuh"
+#include "nb_kernels.cuh"
+
+namespace nbgpu {
+
+__device__ __forceinline__ void record_neighbour64(const ForceArgs &A, int64_t k, int64_t j)
+{
+    const int pos = atomicAdd(A.nb_cnt + k, 1);
+    if (pos < A.cap) A.nb_tmp[k * (int64_t)A.cap + pos] = (int32_t)j;
+}
+
+// acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] -= m/|r|
+__device__ __forceinline__ double pair_f64(const dvec4 &p0, const dvec4 &p1, const double (&xi)[3],
+                                           const double (&vi)[3], bool self, double *acc)
+{
+    const double rx = __dsub_rn(p0.x, xi[0]), ry = __dsub_rn(p0.y, xi[1]), rz = __dsub_rn(p0.z, xi[2]);
+    const double r2 = r2_f64(rx, ry, rz);
+    const double rinv = self ? 0.0 : rsqrt(r2);
+    const double wx = p1.x - vi[0], wy = p1.y - vi[1], wz = p1.z - vi[2];
+    const double rw = rx * wx + ry * wy + rz * wz;
+    const double rinv2 = rinv * rinv;
+    const double mr = p0.w * rinv;
+    const double mr3 = mr * rinv2;
+    const double beta = -3.0 * rw * rinv2;
+    acc[0] += mr3 * rx;
+    acc[1] += mr3 * ry;
+    acc[2] += mr3 * rz;
+    acc[3] += mr3 * (wx + beta * rx);
+    acc[4] += mr3 * (wy + beta * ry);
+    acc[5] += mr3 * (wz + beta * rz);
+    acc[6] -= mr;
+    return r2;
+}
+
+template <int BLOCK, int TJ>
+__global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
+{
+    __shared__ __align__(16) dvec4 sj[2][2 * TJ];
+    const int tid = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * BLOCK + tid;
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles * s) / A.S, t1 = (A.n_tiles * (s + 1)) / A.S;
+    const dvec4 *rec = static_cast<const dvec4 *>(A.rec);
+
+    int64_t g = -1;
+    if (k < A.n_i) {
+        g = A.idx[k];
+        if (g < 0 || g >= A.n) {
+            if (s == 0) atomicOr(A.status, ST_BAD_INDEX);
+            g = -1;
+        }
+    }
+    double xi[3] = {0, 0, 0}, vi[3] = {0, 0, 0}, rs2 = -1.0;
+    if (g >= 0) {
+        const dvec4 p0 = rec[2 * g], p1 = rec[2 * g + 1];
+        xi[0] = p0.x; xi[1] = p0.y; xi[2] = p0.z;
+        vi[0] = p1.x; vi[1] = p1.y; vi[2] = p1.z;
+        if (A.want_nb) rs2 = A.rs2[A.rs2_scalar ? 0 : k];
+    }
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+
+    auto load_tile = [&](int buf, int64_t t) {
+        const dvec4 *src = rec + t * (2 * TJ);
+        // each dvec4 is two 16-byte halves
+        for (int e = tid; e < 4 * TJ; e += BLOCK)
+            cp_async16(reinterpret_cast<char *>(&sj[buf][0]) + 16 * e,
+                       reinterpret_cast<const char *>(src) + 16 * e);
+        cp_async_commit();
+    };
+    if (t0 < t1) load_tile(0, t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        const int buf = (int)((t - t0) & 1);
+        if (t + 1 < t1) {
+            load_tile(buf ^ 1, t + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int64_t jb = t * TJ;
+#pragma unroll 2
+        for (int jj = 0; jj < TJ; ++jj) {
+            const int64_t j = jb + jj;
+            const double r2 = pair_f64(sj[buf][2 * jj], sj[buf][2 * jj + 1], xi, vi, j == g, acc);
+            if (r2 < rs2 && j != g && j < A.n) record_neighbour64(A, k, j);
+        }
+        __syncthreads();
+    }
+    if (k < A.n_i) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) A.part[((int64_t)s * 7 + c) * A.n_i + k] = acc[c];
+    }
+}
+
+template <int IB, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_force_fp64_jstream(ForceArgs A)
+{
+    __shared__ double red[BLOCK / 32][IB][7];
+    const int tid = threadIdx.x;
+    const int s = blockIdx.y;
+    const int64_t k0 = (int64_t)blockIdx.x * IB;
+    const int64_t j0 = (A.n * s) / A.S, j1 = (A.n * (s + 1)) / A.S;
+    const dvec4 *rec = static_cast<const dvec4 *>(A.rec);
+
+    double xi[IB][3], vi[IB][3], rs2[IB];
+    int64_t gi[IB];
+#pragma unroll
+    for (int q = 0; q < IB; ++q) {
+        const int64_t k = k0 + q;
+        int64_t g = -1;
+        if (k < A.n_i) {
+            g = A.idx[k];
+            if (g < 0 || g >= A.n) {
+                if (s == 0 && tid == 0) atomicOr(A.status, ST_BAD_INDEX);
+                g = -1;
+            }
+        }
+        gi[q] = g;
+        rs2[q] = -1.0;
+        if (g >= 0) {
+            const dvec4 p0 = rec[2 * g], p1 = rec[2 * g + 1];
+            xi[q][0] = p0.x; xi[q][1] = p0.y; xi[q][2] = p0.z;
+            vi[q][0] = p1.x; vi[q][1] = p1.y; vi[q][2] = p1.z;
+            if (A.want_nb) rs2[q] = A.rs2[A.rs2_scalar ? 0 : k];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) xi[q][c] = vi[q][c] = 0.0;
+        }
+    }
+    double acc[IB][7];
+#pragma unroll
+    for (int q = 0; q < IB; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[q][c] = 0.0;
+    for (int64_t j = j0 + tid; j < j1; j += BLOCK) {
+        const dvec4 p0 = rec[2 * j], p1 = rec[2 * j + 1];
+#pragma unroll
+        for (int q = 0; q < IB; ++q) {
+            const double r2 = pair_f64(p0, p1, xi[q], vi[q], j == gi[q], acc[q]);
+            if (r2 < rs2[q] && j != gi[q]) record_neighbour64(A, k0 + q, j);
+        }
+    }
+    const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < IB; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const double v = warp_sum(acc[q][c]);
+            if (lane == 0) red[w][q][c] = v;
+        }
+    __syncthreads();
+    for (int e = tid; e < IB * 7; e += BLOCK) {
+        const int q = e / 7, c = e % 7;
+        const int64_t k = k0 + q;
+        if (k < A.n_i) {
+            double sum = 0.0;
+#pragma unroll
+            for (int ww = 0; ww < BLOCK / 32; ++ww) sum += red[ww][q][c];
+            A.part[((int64_t)s * 7 + c) * A.n_i + k] = sum;
+        }
+    }
+}
+
+void *fp64_tiled_fn() { return (void *)k_force_fp64_tiled<128, 64>; }
+void *fp64_jstream_fn(int v) { return v == 0 ? (void *)k_force_fp64_jstream<1, 256> : (void *)k_force_fp64_jstream<4, 256>; }
+int fp64_jstream_ib(int v) { return v == 0 ? 1 : 4; }
+
+void launch_force_fp64(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a)
+{
+    dim3 grid((unsigned)ctas_x, (unsigned)S);
+    if (kernel == 0) {
+        k_force_fp64_tiled<128, 64><<<grid, 128, 0, st>>>(a);
+    } else if (variant == 0) {
+        k_force_fp64_jstream<1, 256><<<grid, 256, 0, st>>>(a);
+    } else {
+        k_force_fp64_jstream<4, 256><<<grid, 256, 0, st>>>(a);
+    }
+}
+
+}  // namespace nbgpu

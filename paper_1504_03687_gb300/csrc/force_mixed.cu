@@ -1,0 +1,304 @@
+// force_mixed.cu — K3: regular force, jerk, potential and neighbour capture in mixed
+// precision (paper Sec. 3.2.1: the regular force and neighbour list on the GPU).
+//
+// Precision scheme: positions arrive as FP64 split into hi/lo floats; the coordinate
+// difference is formed in double-single ((hi - hi) + (lo - lo)), every other pairwise
+// operation runs in FP32 on the CUDA cores (one MUFU rsqrt per pair), per-i sums are
+// accumulated in FP32 over one j-tile and promoted to FP64 at the end of every tile.
+// Not a dense contraction, so no tensor cores.
+//
+// Two kernels:
+//  * tiled     : CTA = NI*BLOCK active particles (NI per thread, register-blocked) x one
+//                j-range; j-tiles of TJ records are staged in shared memory with cp.async
+//                (double-buffered) and broadcast to all threads.  FP32-issue bound.
+//  * j-streamed: for tiny active blocks.  CTA = IB active particles x one j-chunk; each
+//                thread streams its own j-records from HBM (coalesced) and the block
+//                reduces the IB x 7 partial sums with warp shuffles.  HBM/latency bound.
+// Both write FP64 partial sums [split][7][n_i] that k_reduce adds in a fixed order, so
+// results are bitwise reproducible for a given launch plan.
+#include "nb_common.cuh"
+#include "nb_kernels.cuh"
+
+namespace nbgpu {
+
+__device__ __forceinline__ void record_neighbour(const ForceArgs &A, int64_t k, int64_t j)
+{
+    const int pos = atomicAdd(A.nb_cnt + k, 1);
+    if (pos < A.cap) A.nb_tmp[k * (int64_t)A.cap + pos] = (int32_t)j;
+}
+
+// One pair (i <- j) in mixed precision; returns r^2 for the neighbour test.
+// acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] += m/|r|
+template <bool MASK>
+__device__ __forceinline__ float pair_mixed(float jxh, float jyh, float jzh, float jm, float jxl,
+                                            float jyl, float jzl, float jvx, float jvy, float jvz,
+                                            float ixh, float iyh, float izh, float ixl, float iyl,
+                                            float izl, float ivx, float ivy, float ivz, bool self,
+                                            float *acc)
+{
+    const float dx = ds_diff(jxh, jxl, ixh, ixl);
+    const float dy = ds_diff(jyh, jyl, iyh, iyl);
+    const float dz = ds_diff(jzh, jzl, izh, izl);
+    const float r2 = r2_f32(dx, dy, dz);
+    float rinv = rsqrtf(r2);
+    if (MASK) rinv = self ? 0.f : rinv;
+    const float wx = jvx - ivx, wy = jvy - ivy, wz = jvz - ivz;
+    const float rw = dx * wx + dy * wy + dz * wz;
+    const float rinv2 = rinv * rinv;
+    const float mr = jm * rinv;
+    const float mr3 = mr * rinv2;
+    const float beta = rw * (rinv2 * -3.f);
+    acc[0] += mr3 * dx;
+    acc[1] += mr3 * dy;
+    acc[2] += mr3 * dz;
+    acc[3] += mr3 * (wx + beta * dx);
+    acc[4] += mr3 * (wy + beta * dy);
+    acc[5] += mr3 * (wz + beta * dz);
+    acc[6] += mr;
+    return r2;
+}
+
+template <int NI, bool MASK, int TJ>
+__device__ __forceinline__ void tile_mixed(const float4 *__restrict__ sj, int64_t jb, const ForceArgs &A,
+                                           const float (&ih)[NI][3], const float (&il)[NI][3],
+                                           const float (&iv)[NI][3], const float (&rs2f)[NI],
+                                           const int64_t (&gi)[NI], const int64_t (&kk)[NI],
+                                           float (&acc)[NI][7])
+{
+#pragma unroll 4
+    for (int jj = 0; jj < TJ; ++jj) {
+        const float4 p0 = sj[3 * jj], p1 = sj[3 * jj + 1], p2 = sj[3 * jj + 2];
+        const int64_t j = jb + jj;
+        float r2[NI];
+        bool hit = false;
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+            r2[q] = pair_mixed<MASK>(p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p2.x, p2.y, p2.z,
+                                     ih[q][0], ih[q][1], ih[q][2], il[q][0], il[q][1], il[q][2],
+                                     iv[q][0], iv[q][1], iv[q][2], MASK && (j == gi[q]), acc[q]);
+            hit |= r2[q] < rs2f[q];
+        }
+        if (hit) {
+#pragma unroll
+            for (int q = 0; q < NI; ++q)
+                if (r2[q] < rs2f[q] && j != gi[q] && j < A.n) record_neighbour(A, kk[q], j);
+        }
+    }
+}
+
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled(ForceArgs A)
+{
+    __shared__ __align__(16) float4 sj[2][3 * TJ];
+    const int tid = threadIdx.x;
+    const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles * s) / A.S, t1 = (A.n_tiles * (s + 1)) / A.S;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+
+    float ih[NI][3], il[NI][3], iv[NI][3], rs2f[NI];
+    int64_t gi[NI], kk[NI];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t k = kbase + q * BLOCK + tid;
+        kk[q] = k;
+        int64_t g = -1;
+        if (k < A.n_i) {
+            g = A.idx[k];
+            if (g < 0 || g >= A.n) {
+                if (s == 0) atomicOr(A.status, ST_BAD_INDEX);
+                g = -1;
+            }
+        }
+        gi[q] = g;
+        if (g >= 0) {
+            const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
+            ih[q][0] = p0.x; ih[q][1] = p0.y; ih[q][2] = p0.z;
+            il[q][0] = p1.x; il[q][1] = p1.y; il[q][2] = p1.z;
+            iv[q][0] = p2.x; iv[q][1] = p2.y; iv[q][2] = p2.z;
+            rs2f[q] = A.want_nb ? __double2float_rn(A.rs2[A.rs2_scalar ? 0 : k]) : -1.f;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ih[q][c] = il[q][c] = iv[q][c] = 0.f;
+            rs2f[q] = -1.f;
+        }
+    }
+    double dacc[NI][7];
+#pragma unroll
+    for (int q = 0; q < NI; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) dacc[q][c] = 0.0;
+
+    auto load_tile = [&](int buf, int64_t t) {
+        const float4 *src = rec + t * (3 * TJ);
+#pragma unroll
+        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16(&sj[buf][e], src + e);
+        cp_async_commit();
+    };
+
+    if (t0 < t1) load_tile(0, t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        const int buf = (int)((t - t0) & 1);
+        if (t + 1 < t1) {
+            load_tile(buf ^ 1, t + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int64_t jb = t * TJ;
+        bool mine = false;
+#pragma unroll
+        for (int q = 0; q < NI; ++q) mine |= (gi[q] >= jb && gi[q] < jb + TJ);
+        float acc[NI][7];
+#pragma unroll
+        for (int q = 0; q < NI; ++q)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) acc[q][c] = 0.f;
+        if (__any_sync(0xffffffffu, mine))
+            tile_mixed<NI, true, TJ>(sj[buf], jb, A, ih, il, iv, rs2f, gi, kk, acc);
+        else
+            tile_mixed<NI, false, TJ>(sj[buf], jb, A, ih, il, iv, rs2f, gi, kk, acc);
+#pragma unroll
+        for (int q = 0; q < NI; ++q)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) dacc[q][c] += (double)acc[q][c];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t k = kk[q];
+        if (k < A.n_i) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+                A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -dacc[q][c] : dacc[q][c];
+        }
+    }
+}
+
+// j-streamed kernel for small active blocks: blockIdx.x = batch of IB active particles,
+// blockIdx.y = j-chunk.  Chunks are contiguous ranges of whole particles [j0, j1).
+template <int IB, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_force_mixed_jstream(ForceArgs A)
+{
+    __shared__ double red[BLOCK / 32][IB][7];
+    const int tid = threadIdx.x;
+    const int s = blockIdx.y;
+    const int64_t k0 = (int64_t)blockIdx.x * IB;
+    const int64_t j0 = (A.n * s) / A.S, j1 = (A.n * (s + 1)) / A.S;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+
+    float ih[IB][3], il[IB][3], iv[IB][3], rs2f[IB];
+    int64_t gi[IB];
+#pragma unroll
+    for (int q = 0; q < IB; ++q) {
+        const int64_t k = k0 + q;
+        int64_t g = -1;
+        if (k < A.n_i) {
+            g = A.idx[k];
+            if (g < 0 || g >= A.n) {
+                if (s == 0 && tid == 0) atomicOr(A.status, ST_BAD_INDEX);
+                g = -1;
+            }
+        }
+        gi[q] = g;
+        if (g >= 0) {
+            const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
+            ih[q][0] = p0.x; ih[q][1] = p0.y; ih[q][2] = p0.z;
+            il[q][0] = p1.x; il[q][1] = p1.y; il[q][2] = p1.z;
+            iv[q][0] = p2.x; iv[q][1] = p2.y; iv[q][2] = p2.z;
+            rs2f[q] = A.want_nb ? __double2float_rn(A.rs2[A.rs2_scalar ? 0 : k]) : -1.f;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ih[q][c] = il[q][c] = iv[q][c] = 0.f;
+            rs2f[q] = -1.f;
+        }
+    }
+    float acc[IB][7];
+#pragma unroll
+    for (int q = 0; q < IB; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[q][c] = 0.f;
+
+    for (int64_t j = j0 + tid; j < j1; j += BLOCK) {
+        const float4 p0 = __ldg(rec + 3 * j), p1 = __ldg(rec + 3 * j + 1), p2 = __ldg(rec + 3 * j + 2);
+#pragma unroll
+        for (int q = 0; q < IB; ++q) {
+            const float r2 = pair_mixed<true>(p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p2.x, p2.y,
+                                              p2.z, ih[q][0], ih[q][1], ih[q][2], il[q][0], il[q][1],
+                                              il[q][2], iv[q][0], iv[q][1], iv[q][2], j == gi[q], acc[q]);
+            if (r2 < rs2f[q] && j != gi[q]) record_neighbour(A, k0 + q, j);
+        }
+    }
+    // block reduction: warp shuffles, then one FP64 slot per warp, summed in warp order
+    const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < IB; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const float v = warp_sum(acc[q][c]);
+            if (lane == 0) red[w][q][c] = (double)v;
+        }
+    __syncthreads();
+    for (int e = tid; e < IB * 7; e += BLOCK) {
+        const int q = e / 7, c = e % 7;
+        const int64_t k = k0 + q;
+        if (k < A.n_i) {
+            double sum = 0.0;
+#pragma unroll
+            for (int ww = 0; ww < BLOCK / 32; ++ww) sum += red[ww][q][c];
+            A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -sum : sum;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Variants.  Tiled: (NI, BLOCK, TJ); the plan's `variant` indexes this table.
+struct TiledVariant {
+    int ni, block, tj;
+};
+static const TiledVariant kTiled[] = {{4, 128, 256}, {2, 128, 256}, {1, 128, 256}, {4, 256, 256}};
+
+void *mixed_tiled_fn(int v)
+{
+    switch (v) {
+    case 0: return (void *)k_force_mixed_tiled<4, 128, 256, 3>;
+    case 1: return (void *)k_force_mixed_tiled<2, 128, 256, 4>;
+    case 2: return (void *)k_force_mixed_tiled<1, 128, 256, 4>;
+    default: return (void *)k_force_mixed_tiled<4, 256, 256, 1>;
+    }
+}
+int mixed_tiled_i_per_cta(int v) { return kTiled[v].ni * kTiled[v].block; }
+int mixed_tiled_block(int v) { return kTiled[v].block; }
+int mixed_tiled_tj(int v) { return kTiled[v].tj; }
+
+void *mixed_jstream_fn(int v)
+{
+    switch (v) {
+    case 0: return (void *)k_force_mixed_jstream<1, 256>;
+    case 1: return (void *)k_force_mixed_jstream<4, 256>;
+    default: return (void *)k_force_mixed_jstream<8, 256>;
+    }
+}
+int mixed_jstream_ib(int v) { return v == 0 ? 1 : (v == 1 ? 4 : 8); }
+
+void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a)
+{
+    dim3 grid((unsigned)ctas_x, (unsigned)S);
+    if (kernel == 1) {
+        switch (variant) {
+        case 0: k_force_mixed_tiled<4, 128, 256, 3><<<grid, 128, 0, st>>>(a); break;
+        case 1: k_force_mixed_tiled<2, 128, 256, 4><<<grid, 128, 0, st>>>(a); break;
+        case 2: k_force_mixed_tiled<1, 128, 256, 4><<<grid, 128, 0, st>>>(a); break;
+        default: k_force_mixed_tiled<4, 256, 256, 1><<<grid, 256, 0, st>>>(a); break;
+        }
+    } else {
+        switch (variant) {
+        case 0: k_force_mixed_jstream<1, 256><<<grid, 256, 0, st>>>(a); break;
+        case 1: k_force_mixed_jstream<4, 256><<<grid, 256, 0, st>>>(a); break;
+        default: k_force_mixed_jstream<8, 256><<<grid, 256, 0, st>>>(a); break;
+        }
+    }
+}
+
+}  // namespace nbgpu

@@ -1,0 +1,707 @@
+// nb_api.cu — the C ABI declared in include/nbgpu.h: context, validation, device buffers,
+// launch planning and the call sequence of one regular-force step:
+//   nb_predict  : K1 predictor -> j-records
+//   nb_regular_force : zero counters -> K2/K3 force (+ neighbour capture) -> K4 reduce
+//                      -> K5 neighbour CSR
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nbgpu.h"
+#include "nb_common.cuh"
+#include "nb_kernels.cuh"
+
+using namespace nbgpu;
+
+namespace nbgpu {
+void *mixed_tiled_fn(int v);
+int mixed_tiled_i_per_cta(int v);
+int mixed_tiled_block(int v);
+int mixed_tiled_tj(int v);
+int mixed_jstream_ib(int v);
+void *fp64_tiled_fn();
+int fp64_jstream_ib(int v);
+void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
+void launch_force_fp64(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
+size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms, int64_t *rows_pad_out, int *SA,
+                             int *SB);
+int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx, int64_t n_i,
+                   const double *g_acc, const double *g_jerk, const double *g_pot, double *g_x, double *g_v,
+                   double *g_m, void *scratch, unsigned *status, int num_sms);
+}  // namespace nbgpu
+
+static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
+static constexpr int kMaxCap = 8192;   // largest nb_cap (sort buffers live in shared memory)
+
+struct nb_ctx {
+    int device = 0, precision = 0, cap = 0, num_sms = 0;
+    int occ[8] = {0};
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    int64_t n_max = 0, n = 0, n_pad = 0;
+    bool have_state = false, have_pred = false, broken = false;
+    double *x = nullptr, *v = nullptr, *a = nullptr, *jk = nullptr, *m = nullptr, *tl = nullptr;
+    double *xp = nullptr, *vp = nullptr;
+    void *rec = nullptr;  // dvec4[2*n_pad] or float4[3*n_pad]
+    unsigned *status = nullptr;
+    // grow-only scratch
+    double *part = nullptr; size_t part_cap = 0;
+    int32_t *nb_tmp = nullptr; size_t nb_tmp_cap = 0;
+    int32_t *nb_cnt = nullptr; size_t nb_cnt_cap = 0;
+    int32_t *over = nullptr; size_t over_cap = 0;
+    int64_t *scan = nullptr; size_t scan_cap = 0;
+    char *stage = nullptr; size_t stage_cap = 0;
+    char *adj = nullptr; size_t adj_cap = 0;
+    char err[512] = {0};
+    // per-phase device timing (CUDA events on the context stream) and launch counters
+    bool timing = false;
+    struct Span {
+        cudaEvent_t a, b;
+        int phase;
+    };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> evpool;
+    int64_t launches[8] = {0};
+};
+
+enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_COUNT = 5 };
+
+static cudaEvent_t ev_take(nb_ctx *c)
+{
+    if (!c->evpool.empty()) {
+        cudaEvent_t e = c->evpool.back();
+        c->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+static cudaEvent_t span_begin(nb_ctx *c)
+{
+    if (!c->timing) return nullptr;
+    cudaEvent_t a = ev_take(c);
+    if (a) cudaEventRecord(a, c->stream);
+    return a;
+}
+
+static void span_end(nb_ctx *c, int phase, cudaEvent_t a, int kernels)
+{
+    c->launches[phase] += kernels;
+    if (!c->timing || !a) return;
+    cudaEvent_t b = ev_take(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->spans.push_back({a, b, phase});
+}
+
+// ------------------------------------------------------------------------------ helpers
+static nb_status fail(nb_ctx *c, nb_status s, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+static nb_status cuda_fail(nb_ctx *c, cudaError_t e, const char *what)
+{
+    if (c) {
+        snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+        // errors that poison the context are sticky
+        if (e != cudaErrorMemoryAllocation && e != cudaErrorInvalidValue) c->broken = true;
+    }
+    return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t _e = (call);                        \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
+    } while (0)
+
+#define CK_LAUNCH(what) CK(cudaGetLastError(), what)
+
+static nb_status grow(nb_ctx *c, void **p, size_t *cap, size_t need_bytes, const char *what)
+{
+    if (need_bytes <= *cap && *p) return NB_OK;
+    if (*p) {
+        // the old buffer may still be read by queued work
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    size_t bytes = need_bytes < 256 ? 256 : need_bytes;
+    bytes = bytes + bytes / 4;  // headroom to avoid regrowth on small changes
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(c, e, what);
+    }
+    *cap = bytes;
+    return NB_OK;
+}
+
+static nb_status check_usable(nb_ctx *c)
+{
+    if (!c) return NB_ERR_ARG;
+    if (c->broken) return fail(c, NB_ERR_STATE, "context unusable after an earlier CUDA error: %s", c->err);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return NB_OK;
+}
+
+static nb_status status_from_flags(nb_ctx *c, unsigned f)
+{
+    if (f & ST_BAD_INDEX) return fail(c, NB_ERR_ARG, "an active index was outside [0, n)");
+    if (f & ST_DUP_INDEX) return fail(c, NB_ERR_ARG, "an active index appears more than once");
+    if (f & ST_TIMEOUT) return fail(c, NB_ERR_TIMEOUT, "a bounded device-side wait expired");
+    if (f & ST_DEVICE) return fail(c, NB_ERR_DEVICE, "a device-side consistency check failed");
+    if (f & ST_CSR_FULL) return fail(c, NB_ERR_NB_OVERFLOW, "neighbour CSR capacity too small; lists cut");
+    if (f & ST_NB_TRUNCATED) return fail(c, NB_ERR_NB_OVERFLOW, "some neighbour lists were cut at nb_cap");
+    return NB_OK;
+}
+
+static nb_status sync_and_collect(nb_ctx *c)
+{
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    unsigned f = 0;
+    CK(cudaMemcpy(&f, c->status + SS_FLAGS, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+    CK(cudaMemset(c->status + SS_FLAGS, 0, sizeof(unsigned)), "clear status");
+    return status_from_flags(c, f);
+}
+
+// ------------------------------------------------------------------------------ planner
+namespace nbgpu {
+
+static double wave_eff(int64_t ctas, int64_t P)
+{
+    if (P <= 0) return 1.0;
+    const int64_t waves = (ctas + P - 1) / P;
+    return (double)ctas / (double)(waves * P);
+}
+
+// Picks the kernel, its variant and the j-split S.  Tiny active blocks take the j-streamed
+// kernel (every CTA streams a contiguous j-chunk for a few i); larger ones the tiled kernel,
+// with S chosen so that the CTA count fills whole waves of the GPU (each split must keep at
+// least two j-tiles).  Relative per-pair speed of the tiled variants weights the choice.
+Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i)
+{
+    Plan p{};
+    if (num_sms <= 0) num_sms = 152;
+    const int64_t n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
+    if (precision == NB_MIXED) {
+        if (n_i <= 32) {
+            p.kernel = 2;
+            p.variant = n_i <= 2 ? 0 : (n_i <= 16 ? 1 : 2);
+            p.i_per_cta = mixed_jstream_ib(p.variant);
+            const int64_t batches = (n_i + p.i_per_cta - 1) / p.i_per_cta;
+            int64_t S = (4 * (int64_t)num_sms + batches - 1) / batches;
+            const int64_t smax = n / 2048 > 1 ? n / 2048 : 1;  // >= 2048 j per CTA
+            if (S > smax) S = smax;
+            if (S < 1) S = 1;
+            p.S = (int)S;
+            p.ctas = batches * S;
+            p.tj = 0;
+            return p;
+        }
+        static const double speed[4] = {1.0, 0.90, 0.78, 0.98};
+        double best = -1.0;
+        for (int v = 0; v < 4; ++v) {
+            const int ipc = mixed_tiled_i_per_cta(v), tj = mixed_tiled_tj(v);
+            const int64_t tiles = n_pad / tj;
+            const int64_t itiles = (n_i + ipc - 1) / ipc;
+            const int64_t P = (int64_t)num_sms * (occ && occ[v] > 0 ? occ[v] : 1);
+            const double util = (double)n_i / (double)(itiles * ipc);
+            int64_t smax = tiles / 2 > 1 ? tiles / 2 : 1;
+            if (smax > 2048) smax = 2048;
+            for (int64_t S = 1; S <= smax; ++S) {
+                const int64_t ctas = itiles * S;
+                // a split costs one partial-sum write per i; penalise many splits slightly
+                const double score = speed[v] * util * wave_eff(ctas, P) * (1.0 - 0.0005 * (double)S);
+                if (score > best + 1e-12) {
+                    best = score;
+                    p.kernel = 1;
+                    p.variant = v;
+                    p.i_per_cta = ipc;
+                    p.S = (int)S;
+                    p.ctas = ctas;
+                    p.tj = tj;
+                }
+                if (ctas >= 64 * P) break;
+            }
+        }
+        return p;
+    }
+    // FP64
+    if (n_i <= 64) {
+        p.kernel = 3;
+        p.variant = n_i <= 4 ? 0 : 1;
+        p.i_per_cta = fp64_jstream_ib(p.variant);
+        const int64_t batches = (n_i + p.i_per_cta - 1) / p.i_per_cta;
+        int64_t S = (4 * (int64_t)num_sms + batches - 1) / batches;
+        const int64_t smax = n / 1024 > 1 ? n / 1024 : 1;
+        if (S > smax) S = smax;
+        if (S < 1) S = 1;
+        p.S = (int)S;
+        p.ctas = batches * S;
+        p.tj = 0;
+        return p;
+    }
+    const int ipc = 128, tj = 64;
+    const int64_t tiles = n_pad / tj;
+    const int64_t itiles = (n_i + ipc - 1) / ipc;
+    const int64_t P = (int64_t)num_sms * (occ && occ[4] > 0 ? occ[4] : 1);
+    int64_t smax = tiles / 2 > 1 ? tiles / 2 : 1;
+    if (smax > 2048) smax = 2048;
+    double best = -1.0;
+    for (int64_t S = 1; S <= smax; ++S) {
+        const int64_t ctas = itiles * S;
+        const double score = wave_eff(ctas, P) * (1.0 - 0.0005 * (double)S);
+        if (score > best + 1e-12) {
+            best = score;
+            p.kernel = 0;
+            p.variant = 0;
+            p.i_per_cta = ipc;
+            p.S = (int)S;
+            p.ctas = ctas;
+            p.tj = tj;
+        }
+        if (ctas >= 64 * P) break;
+    }
+    return p;
+}
+
+void query_occupancy(int *occ)
+{
+    for (int v = 0; v < 4; ++v) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mixed_tiled_fn(v), mixed_tiled_block(v), 0) !=
+            cudaSuccess)
+            b = 1;
+        occ[v] = b > 0 ? b : 1;
+    }
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fp64_tiled_fn(), 128, 0) != cudaSuccess) b = 1;
+    occ[4] = b > 0 ? b : 1;
+}
+
+void launch_force(cudaStream_t st, const Plan &p, ForceArgs a)
+{
+    const int64_t ctas_x = p.ctas / p.S;
+    a.S = p.S;
+    a.n_tiles = p.tj > 0 ? ((a.n + kTilePad - 1) / kTilePad) * kTilePad / p.tj : 0;
+    if (p.kernel == 1 || p.kernel == 2)
+        launch_force_mixed(st, p.kernel, p.variant, ctas_x, p.S, a);
+    else
+        launch_force_fp64(st, p.kernel, p.variant, ctas_x, p.S, a);
+}
+
+}  // namespace nbgpu
+
+// ------------------------------------------------------------------------------ ABI
+extern "C" {
+
+int32_t nb_version(void) { return 100; }
+
+nb_status nb_init(nb_ctx **out, const nb_config *cfg)
+{
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return NB_ERR_ARG;
+    if (cfg->n_max < 1 || cfg->nb_cap < 1 || cfg->nb_cap > kMaxCap || cfg->flags != 0 ||
+        (cfg->precision != NB_FP64 && cfg->precision != NB_MIXED) || cfg->n_max > (int64_t)INT32_MAX - kTilePad)
+        return NB_ERR_ARG;
+    nb_ctx *c = new (std::nothrow) nb_ctx();
+    if (!c) return NB_ERR_OOM;
+    c->device = cfg->device;
+    c->precision = cfg->precision;
+    c->cap = cfg->nb_cap;
+    c->n_max = cfg->n_max;
+    auto bail = [&](nb_status s) {
+        nb_free(c);
+        return s;
+    };
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return bail(NB_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return bail(NB_ERR_CUDA);
+    if (cfg->stream) {
+        c->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(NB_ERR_CUDA);
+        c->stream = c->own_stream;
+    }
+    query_occupancy(c->occ);
+    const int64_t nm = c->n_max, npad = ((nm + kTilePad - 1) / kTilePad) * kTilePad;
+    const size_t v3 = (size_t)nm * 3 * sizeof(double), s1 = (size_t)nm * sizeof(double);
+    const size_t rec_bytes = c->precision == NB_FP64 ? (size_t)npad * 2 * sizeof(dvec4) : (size_t)npad * 3 * sizeof(float4);
+    if (cudaMalloc(&c->x, v3) != cudaSuccess || cudaMalloc(&c->v, v3) != cudaSuccess ||
+        cudaMalloc(&c->a, v3) != cudaSuccess || cudaMalloc(&c->jk, v3) != cudaSuccess ||
+        cudaMalloc(&c->m, s1) != cudaSuccess || cudaMalloc(&c->tl, s1) != cudaSuccess ||
+        cudaMalloc(&c->xp, v3) != cudaSuccess || cudaMalloc(&c->vp, v3) != cudaSuccess ||
+        cudaMalloc(&c->rec, rec_bytes) != cudaSuccess ||
+        cudaMalloc(&c->status, SS_WORDS * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(NB_ERR_OOM);
+    }
+    if (cudaMemset(c->status, 0, SS_WORDS * sizeof(unsigned)) != cudaSuccess) return bail(NB_ERR_CUDA);
+    *out = c;
+    return NB_OK;
+}
+
+nb_status nb_free(nb_ctx *c)
+{
+    if (!c) return NB_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
+                    c->part, c->nb_tmp, c->nb_cnt, c->over, c->scan, c->stage, c->adj};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    for (auto &sp : c->spans) {
+        cudaEventDestroy(sp.a);
+        cudaEventDestroy(sp.b);
+    }
+    for (auto e : c->evpool) cudaEventDestroy(e);
+    delete c;
+    return NB_OK;
+}
+
+nb_status nb_set_stream(nb_ctx *c, void *stream)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    // NULL is CUDA's default (legacy) stream, which is what a framework reports when it
+    // runs on the default stream; work then orders with the framework's own kernels.
+    c->stream = (cudaStream_t)stream;
+    return NB_OK;
+}
+
+static nb_status copy_in(nb_ctx *c, void *dst, const void *src, size_t bytes, int on_device)
+{
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream),
+       "cudaMemcpyAsync (in)");
+    return NB_OK;
+}
+
+nb_status nb_set_particles(nb_ctx *c, int64_t n, const double *x, const double *v, const double *a,
+                           const double *jerk, const double *m, const double *t_last, int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (n < 1 || n > c->n_max) return fail(c, NB_ERR_ARG, "n=%lld outside [1, n_max=%lld]", (long long)n, (long long)c->n_max);
+    if (!x || !v || !a || !jerk || !m || !t_last) return fail(c, NB_ERR_ARG, "null array");
+    const size_t b3 = (size_t)n * 3 * sizeof(double), b1 = (size_t)n * sizeof(double);
+    if ((s = copy_in(c, c->x, x, b3, on_device)) || (s = copy_in(c, c->v, v, b3, on_device)) ||
+        (s = copy_in(c, c->a, a, b3, on_device)) || (s = copy_in(c, c->jk, jerk, b3, on_device)) ||
+        (s = copy_in(c, c->m, m, b1, on_device)) || (s = copy_in(c, c->tl, t_last, b1, on_device)))
+        return s;
+    c->n = n;
+    c->n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
+    c->have_state = true;
+    c->have_pred = false;
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
+nb_status nb_predict(nb_ctx *c, double t)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!c->have_state) return fail(c, NB_ERR_STATE, "nb_predict before nb_set_particles");
+    cudaEvent_t t0 = span_begin(c);
+    launch_predict(c->stream, c->n, c->n_pad, t, c->x, c->v, c->a, c->jk, c->tl, c->m, c->xp, c->vp,
+                   c->precision == NB_FP64 ? c->rec : nullptr, c->precision == NB_MIXED ? c->rec : nullptr);
+    CK_LAUNCH("k_predict launch");
+    span_end(c, PH_PREDICT, t0, 1);
+    c->have_pred = true;
+    return NB_OK;
+}
+
+nb_status nb_set_predicted(nb_ctx *c, int64_t n, const double *xp, const double *vp, const double *m,
+                           int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (n < 1 || n > c->n_max) return fail(c, NB_ERR_ARG, "n=%lld outside [1, n_max=%lld]", (long long)n, (long long)c->n_max);
+    if (!xp || !vp || !m) return fail(c, NB_ERR_ARG, "null array");
+    const size_t b3 = (size_t)n * 3 * sizeof(double), b1 = (size_t)n * sizeof(double);
+    if ((s = copy_in(c, c->xp, xp, b3, on_device)) || (s = copy_in(c, c->vp, vp, b3, on_device)) ||
+        (s = copy_in(c, c->m, m, b1, on_device)))
+        return s;
+    c->n = n;
+    c->n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
+    launch_pack_predicted(c->stream, n, c->n_pad, c->xp, c->vp, c->m, c->precision == NB_FP64 ? c->rec : nullptr,
+                          c->precision == NB_MIXED ? c->rec : nullptr);
+    CK_LAUNCH("k_pack launch");
+    c->have_state = false;
+    c->have_pred = true;
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
+nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!c->have_pred) return fail(c, NB_ERR_STATE, "no predicted state");
+    if (!xp || !vp) return fail(c, NB_ERR_ARG, "null array");
+    const size_t b3 = (size_t)c->n * 3 * sizeof(double);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(xp, c->xp, b3, kind, c->stream), "cudaMemcpyAsync");
+    CK(cudaMemcpyAsync(vp, c->vp, b3, kind, c->stream), "cudaMemcpyAsync");
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
+nb_status nb_plan(const nb_ctx *c, int64_t n, int64_t n_i, int64_t *out)
+{
+    if (!c || !out || n < 1 || n_i < 0) return NB_ERR_ARG;
+    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i);
+    out[0] = p.kernel;
+    out[1] = p.i_per_cta;
+    out[2] = p.S;
+    out[3] = p.ctas;
+    out[4] = p.tj;
+    return NB_OK;
+}
+
+nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n, int64_t n_i,
+                      int64_t *out)
+{
+    if (!out || n < 1 || n_i < 0 || (precision != NB_FP64 && precision != NB_MIXED)) return NB_ERR_ARG;
+    int occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    if (ctas_per_sm)
+        for (int q = 0; q < 5; ++q) occ[q] = ctas_per_sm[q];
+    Plan p = plan_force(precision, num_sms, occ, n, n_i);
+    out[0] = p.kernel;
+    out[1] = p.i_per_cta;
+    out[2] = p.S;
+    out[3] = p.ctas;
+    out[4] = p.tj;
+    return NB_OK;
+}
+
+nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const double *rs2, int32_t rs2_scalar,
+                           double *acc, double *jerk, double *pot, int64_t *nb_off, int32_t *nb_idx,
+                           int64_t nb_idx_capacity, int32_t *nb_count_true, int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!c->have_pred) return fail(c, NB_ERR_STATE, "nb_regular_force before nb_predict / nb_set_predicted");
+    if (n_i < 0 || n_i > (int64_t)INT32_MAX) return fail(c, NB_ERR_ARG, "n_i=%lld out of range", (long long)n_i);
+    if (nb_idx && (!nb_off || nb_idx_capacity < 0)) return fail(c, NB_ERR_ARG, "nb_idx needs nb_off and a capacity >= 0");
+    if (n_i > 0 && (!idx || !rs2 || !acc || !jerk || !pot)) return fail(c, NB_ERR_ARG, "null array");
+    const bool want_nb = nb_off || nb_count_true;
+    if (n_i == 0) {
+        if (nb_off) {
+            if (on_device) CK(cudaMemsetAsync(nb_off, 0, sizeof(int64_t), c->stream), "cudaMemsetAsync");
+            else nb_off[0] = 0;
+        }
+        return NB_OK;
+    }
+    const int64_t n = c->n;
+    // host mode: validate on the host and stage everything on the device
+    const int32_t *d_idx = idx;
+    const double *d_rs2 = rs2;
+    double *d_acc = acc, *d_jerk = jerk, *d_pot = pot;
+    int64_t *d_off = nb_off;
+    int32_t *d_nbidx = nb_idx, *d_cnt_true = nb_count_true;
+    const size_t n_rs2 = rs2_scalar ? 1 : (size_t)n_i;
+    if (!on_device) {
+        for (int64_t k = 0; k < n_i; ++k)
+            if (idx[k] < 0 || idx[k] >= n) return fail(c, NB_ERR_ARG, "idx[%lld]=%d outside [0, %lld)", (long long)k, idx[k], (long long)n);
+        const size_t cap_nb = nb_idx ? (size_t)nb_idx_capacity : 0;
+        const size_t bytes = 256 * 8 + (size_t)n_i * 4 + n_rs2 * 8 + (size_t)n_i * 7 * 8 + ((size_t)n_i + 1) * 8 +
+                             cap_nb * 4 + (size_t)n_i * 4;
+        if ((s = grow(c, (void **)&c->stage, &c->stage_cap, bytes, "staging buffer")) != NB_OK) return s;
+        char *p = c->stage;
+        auto take = [&](size_t b) {
+            char *q = p;
+            p += (b + 255) & ~(size_t)255;
+            return q;
+        };
+        d_idx = (int32_t *)take((size_t)n_i * 4);
+        d_rs2 = (double *)take(n_rs2 * 8);
+        d_acc = (double *)take((size_t)n_i * 24);
+        d_jerk = (double *)take((size_t)n_i * 24);
+        d_pot = (double *)take((size_t)n_i * 8);
+        d_off = nb_off ? (int64_t *)take(((size_t)n_i + 1) * 8) : nullptr;
+        d_nbidx = nb_idx ? (int32_t *)take(cap_nb * 4 + 4) : nullptr;
+        d_cnt_true = nb_count_true ? (int32_t *)take((size_t)n_i * 4) : nullptr;
+        CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
+        CK(cudaMemcpyAsync((void *)d_rs2, rs2, n_rs2 * 8, cudaMemcpyHostToDevice, c->stream), "copy rs2");
+    }
+    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i);
+    const size_t part_bytes = (size_t)p.S * 7 * (size_t)n_i * sizeof(double);
+    if ((s = grow(c, (void **)&c->part, &c->part_cap, part_bytes, "partial sums")) != NB_OK) return s;
+    if ((s = grow(c, (void **)&c->nb_cnt, &c->nb_cnt_cap, (size_t)n_i * 4, "neighbour counters")) != NB_OK) return s;
+    const size_t scan_elems = neighbour_scan_tmp_elems(n_i) + (d_off ? 0 : (size_t)n_i + 1);
+    if (want_nb) {
+        if ((s = grow(c, (void **)&c->nb_tmp, &c->nb_tmp_cap, (size_t)n_i * c->cap * 4, "neighbour slots")) != NB_OK) return s;
+        if ((s = grow(c, (void **)&c->over, &c->over_cap, (size_t)n_i * 4, "overflow list")) != NB_OK) return s;
+        if ((s = grow(c, (void **)&c->scan, &c->scan_cap, scan_elems * 8, "scan scratch")) != NB_OK) return s;
+        CK(cudaMemsetAsync(c->nb_cnt, 0, (size_t)n_i * 4, c->stream), "cudaMemsetAsync");
+        CK(cudaMemsetAsync(c->status + SS_OVERFLOW_COUNT, 0, sizeof(unsigned), c->stream), "cudaMemsetAsync");
+    }
+    ForceArgs fa{};
+    fa.rec = c->rec;
+    fa.n = n;
+    fa.idx = d_idx;
+    fa.n_i = n_i;
+    fa.rs2 = d_rs2;
+    fa.rs2_scalar = rs2_scalar ? 1 : 0;
+    fa.want_nb = want_nb ? 1 : 0;
+    fa.cap = c->cap;
+    fa.part = c->part;
+    fa.nb_cnt = c->nb_cnt;
+    fa.nb_tmp = c->nb_tmp;
+    fa.status = c->status;
+    cudaEvent_t t0 = span_begin(c);
+    launch_force(c->stream, p, fa);
+    CK_LAUNCH("force kernel launch");
+    span_end(c, PH_FORCE, t0, 1);
+    t0 = span_begin(c);
+    launch_reduce(c->stream, c->part, p.S, n_i, d_acc, d_jerk, d_pot);
+    CK_LAUNCH("k_reduce launch");
+    span_end(c, PH_REDUCE, t0, 1);
+    if (want_nb) {
+        // counts only: the scan still needs an offsets buffer, taken from the scan scratch
+        int64_t *off_buf = d_off ? d_off : c->scan + neighbour_scan_tmp_elems(n_i);
+        t0 = span_begin(c);
+        launch_neighbour_csr(c->stream, c->precision, c->rec, n, d_idx, n_i, d_rs2, fa.rs2_scalar, c->nb_cnt,
+                             c->nb_tmp, c->cap, off_buf, d_nbidx, d_nbidx ? nb_idx_capacity : 0, d_cnt_true,
+                             c->scan, c->over, c->status, c->num_sms);
+        CK_LAUNCH("neighbour CSR launch");
+        span_end(c, PH_NEIGHBOURS, t0, d_nbidx ? 5 : 3);
+    }
+    if (on_device) return NB_OK;
+    // host mode: copy results back and report the deferred status of this call
+    CK(cudaMemcpyAsync(acc, d_acc, (size_t)n_i * 24, cudaMemcpyDeviceToHost, c->stream), "copy acc");
+    CK(cudaMemcpyAsync(jerk, d_jerk, (size_t)n_i * 24, cudaMemcpyDeviceToHost, c->stream), "copy jerk");
+    CK(cudaMemcpyAsync(pot, d_pot, (size_t)n_i * 8, cudaMemcpyDeviceToHost, c->stream), "copy pot");
+    if (nb_count_true)
+        CK(cudaMemcpyAsync(nb_count_true, d_cnt_true, (size_t)n_i * 4, cudaMemcpyDeviceToHost, c->stream), "copy counts");
+    if (nb_off) {
+        CK(cudaMemcpyAsync(nb_off, d_off, ((size_t)n_i + 1) * 8, cudaMemcpyDeviceToHost, c->stream), "copy offsets");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        if (nb_idx) {
+            int64_t tot = nb_off[n_i] < nb_idx_capacity ? nb_off[n_i] : nb_idx_capacity;
+            if (tot > 0)
+                CK(cudaMemcpyAsync(nb_idx, d_nbidx, (size_t)tot * 4, cudaMemcpyDeviceToHost, c->stream), "copy lists");
+        }
+    }
+    return sync_and_collect(c);
+}
+
+nb_status nb_regular_force_backward(nb_ctx *c, int64_t n_i, const int32_t *idx, const double *g_acc,
+                                    const double *g_jerk, const double *g_pot, double *g_x, double *g_v,
+                                    double *g_m, int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!c->have_pred) return fail(c, NB_ERR_STATE, "nb_regular_force_backward before nb_predict / nb_set_predicted");
+    if (n_i < 0 || n_i > (int64_t)INT32_MAX) return fail(c, NB_ERR_ARG, "n_i=%lld out of range", (long long)n_i);
+    if (!g_x || !g_v || !g_m || (n_i > 0 && (!idx || !g_acc || !g_jerk || !g_pot)))
+        return fail(c, NB_ERR_ARG, "null array");
+    const int64_t n = c->n;
+    const int32_t *d_idx = idx;
+    const double *d_ga = g_acc, *d_gj = g_jerk, *d_gp = g_pot;
+    double *d_gx = g_x, *d_gv = g_v, *d_gm = g_m;
+    if (!on_device) {
+        for (int64_t k = 0; k < n_i; ++k)
+            if (idx[k] < 0 || idx[k] >= n) return fail(c, NB_ERR_ARG, "idx[%lld]=%d outside [0, %lld)", (long long)k, idx[k], (long long)n);
+        const size_t bytes = 8 * 256 + (size_t)n_i * (4 + 56) + (size_t)n * 56;
+        if ((s = grow(c, (void **)&c->stage, &c->stage_cap, bytes, "staging buffer")) != NB_OK) return s;
+        char *p = c->stage;
+        auto take = [&](size_t b) {
+            char *q = p;
+            p += (b + 255) & ~(size_t)255;
+            return q;
+        };
+        d_idx = (int32_t *)take((size_t)n_i * 4);
+        d_ga = (double *)take((size_t)n_i * 24);
+        d_gj = (double *)take((size_t)n_i * 24);
+        d_gp = (double *)take((size_t)n_i * 8);
+        d_gx = (double *)take((size_t)n * 24);
+        d_gv = (double *)take((size_t)n * 24);
+        d_gm = (double *)take((size_t)n * 8);
+        if (n_i > 0) {
+            CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
+            CK(cudaMemcpyAsync((void *)d_ga, g_acc, (size_t)n_i * 24, cudaMemcpyHostToDevice, c->stream), "copy g_acc");
+            CK(cudaMemcpyAsync((void *)d_gj, g_jerk, (size_t)n_i * 24, cudaMemcpyHostToDevice, c->stream), "copy g_jerk");
+            CK(cudaMemcpyAsync((void *)d_gp, g_pot, (size_t)n_i * 8, cudaMemcpyHostToDevice, c->stream), "copy g_pot");
+        }
+    }
+    int64_t rows_pad = 0;
+    int SA = 0, SB = 0;
+    const size_t need = adjoint_scratch_bytes(c->precision, n, n_i, c->num_sms, &rows_pad, &SA, &SB);
+    if ((s = grow(c, (void **)&c->adj, &c->adj_cap, need, "adjoint scratch")) != NB_OK) return s;
+    cudaEvent_t t0 = span_begin(c);
+    const int kernels = launch_adjoint(c->stream, c->precision, c->rec, n, d_idx, n_i, d_ga, d_gj, d_gp, d_gx, d_gv,
+                                       d_gm, c->adj, c->status, c->num_sms);
+    CK_LAUNCH("adjoint kernels launch");
+    span_end(c, PH_BACKWARD, t0, kernels);
+    if (on_device) return NB_OK;
+    CK(cudaMemcpyAsync(g_x, d_gx, (size_t)n * 24, cudaMemcpyDeviceToHost, c->stream), "copy g_x");
+    CK(cudaMemcpyAsync(g_v, d_gv, (size_t)n * 24, cudaMemcpyDeviceToHost, c->stream), "copy g_v");
+    CK(cudaMemcpyAsync(g_m, d_gm, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream), "copy g_m");
+    return sync_and_collect(c);
+}
+
+nb_status nb_set_timing(nb_ctx *c, int32_t enable)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    c->timing = enable != 0;
+    return NB_OK;
+}
+
+nb_status nb_get_timings(nb_ctx *c, double *ms, int64_t *launches)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!ms || !launches) return fail(c, NB_ERR_ARG, "null array");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (int q = 0; q < PH_COUNT; ++q) {
+        ms[q] = 0.0;
+        launches[q] = c->launches[q];
+        c->launches[q] = 0;
+    }
+    for (auto &sp : c->spans) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess) ms[sp.phase] += t;
+        c->evpool.push_back(sp.a);
+        c->evpool.push_back(sp.b);
+    }
+    c->spans.clear();
+    cudaGetLastError();
+    return NB_OK;
+}
+
+nb_status nb_sync(nb_ctx *c)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    return sync_and_collect(c);
+}
+
+const char *nb_last_error(const nb_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err;
+}
+
+}  // extern "C"

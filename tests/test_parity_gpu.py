@@ -1,0 +1,376 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (written here, per particle i):
+  FP64 path   e_i = |q_gpu - q_ref| / |q_ref| <= 1e-12 for acc, jerk (vector 2-norm)
+              and pot, OR |q_gpu - q_ref| <= 1e-12 * sum_j |term_ij| (summation order
+              differs, so particles whose sum cancels are bounded by the term sum);
+              neighbour lists identical (same FP64 distance arithmetic).
+  mixed path  median e_i <= 2e-6 and max e_i <= 1e-4 for acc, jerk and pot;
+              neighbour sets identical outside a 1e-6 relative band around r_s.
+  predictor   bit-identical to the oracle (same IEEE operation order).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def T(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def rel_err(got, ref):
+    if got.ndim == 2:
+        return np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return np.abs(got - ref) / np.abs(ref)
+
+
+def term_sums(xp, vp, m, idx):
+    """sum_j |acc term|, sum_j |jerk term| and sum_j |pot term| for the rows idx."""
+    out = np.zeros((len(idx), 3))
+    for k, i in enumerate(idx):
+        r = xp - xp[i]
+        w = vp - vp[i]
+        r2 = (r * r).sum(1)
+        r2[i] = np.inf
+        d = np.sqrt(r2)
+        out[k, 0] = (m / r2).sum()
+        out[k, 1] = (m * (np.linalg.norm(w, axis=1) / d ** 3 + 3 * np.abs((r * w).sum(1)) / d ** 4)).sum()
+        out[k, 2] = (m / d).sum()
+    return out
+
+
+def check_fp64(res, ref, xp, vp, m, idx, tol=1e-12):
+    acc, jerk, pot = (res.acc.cpu().numpy(), res.jerk.cpu().numpy(), res.pot.cpu().numpy()) \
+        if torch.is_tensor(res.acc) else (res.acc, res.jerk, res.pot)
+    errs = [rel_err(acc, ref[0]), rel_err(jerk, ref[1]), rel_err(pot, ref[2])]
+    bad = np.nonzero((errs[0] > tol) | (errs[1] > tol) | (errs[2] > tol))[0]
+    if bad.size:
+        ts = term_sums(xp, vp, m, idx[bad])
+        da = np.linalg.norm(acc[bad] - ref[0][bad], axis=1)
+        dj = np.linalg.norm(jerk[bad] - ref[1][bad], axis=1)
+        dp = np.abs(pot[bad] - ref[2][bad])
+        assert np.all(da <= tol * ts[:, 0]), (bad, da / ts[:, 0])
+        assert np.all(dj <= tol * ts[:, 1]), (bad, dj / ts[:, 1])
+        assert np.all(dp <= tol * ts[:, 2])
+    return bad.size
+
+
+def check_mixed(res, ref):
+    acc, jerk, pot = res.acc.cpu().numpy(), res.jerk.cpu().numpy(), res.pot.cpu().numpy()
+    stats = {}
+    for name, g, r in (("acc", acc, ref[0]), ("jerk", jerk, ref[1]), ("pot", pot, ref[2])):
+        e = rel_err(g, r)
+        stats[name] = (float(np.median(e)), float(e.max()))
+        assert np.median(e) <= 2e-6, (name, stats[name])
+        assert e.max() <= 1e-4, (name, stats[name])
+    return stats
+
+
+def lists_of(res):
+    return res.neighbour_lists()
+
+
+def check_lists_exact(res, ref_cnt, ref_lists, cap):
+    cnt = res.nb_count.cpu().numpy()
+    assert np.array_equal(cnt, ref_cnt)
+    got = lists_of(res)
+    for k, (a, b) in enumerate(zip(got, ref_lists)):
+        assert np.array_equal(a, b[:cap]), k
+
+
+def check_lists_band(res, xp, idx, rs2, ref_cnt, ref_lists, cap, band=1e-6):
+    got = lists_of(res)
+    cnt = res.nb_count.cpu().numpy()
+    rs = math.sqrt(rs2)
+    for k, i in enumerate(idx):
+        a, b = set(got[k].tolist()), set(ref_lists[k].tolist())
+        if a == b and cnt[k] == ref_cnt[k]:
+            continue
+        d = np.sqrt(((xp[list(a ^ b)] - xp[i]) ** 2).sum(1)) if (a ^ b) else np.zeros(0)
+        assert np.all(np.abs(d - rs) <= band * rs), (k, d, rs)
+        assert abs(int(cnt[k]) - int(ref_cnt[k])) <= len(a ^ b) + 2 * int(cnt[k] > cap)
+        assert list(got[k]) == sorted(got[k])
+
+
+def make_ctx(n, prec, cap=512):
+    from paper_1504_03687_gb300 import Context
+    return Context(n, precision=prec, nb_cap=cap)
+
+
+# ------------------------------------------------------------------ predictor
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_predictor_bit_identical(gpu_lib, prec):
+    cl, _ = W.plummer_1k_equal()
+    steps = W.block_steps(cl, seed=0)
+    a0, j0, tl = W.hermite_state(cl, seed=1, t_block=0.5, steps=steps)
+    ctx = make_ctx(cl.n, prec)
+    ctx.set_particles(T(cl.x), T(cl.v), T(a0), T(j0), T(cl.m), T(tl))
+    ctx.predict(0.5)
+    xp, vp = ctx.get_predicted()
+    rx, rv = oracle.predict(0.5, cl.x, cl.v, a0, j0, tl)
+    np.testing.assert_array_equal(xp.cpu().numpy(), rx)
+    np.testing.assert_array_equal(vp.cpu().numpy(), rv)
+
+
+# ------------------------------------------------------------------ Plummer 1024, full block
+@pytest.fixture(scope="module")
+def p1k():
+    cl, rs2 = W.plummer_1k_equal()
+    idx = np.arange(cl.n, dtype=np.int32)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx, rs2, cap=512)
+    return cl, rs2, idx, ref
+
+
+def test_fp64_full_block_1k(gpu_lib, p1k):
+    cl, rs2, idx, ref = p1k
+    ctx = make_ctx(cl.n, "fp64")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    res = ctx.regular_force(T(idx), rs2)
+    assert ctx.sync() == 0
+    check_fp64(res, ref, cl.x, cl.v, cl.m, idx)
+    check_lists_exact(res, ref[3], ref[4], 512)
+
+
+def test_mixed_full_block_1k(gpu_lib, p1k):
+    cl, rs2, idx, ref = p1k
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    res = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    check_mixed(res, ref)
+    check_lists_band(res, cl.x, idx, rs2, ref[3], ref[4], 512)
+
+
+def test_host_buffers_match_device_buffers(gpu_lib, p1k):
+    cl, rs2, idx, ref = p1k
+    for prec in ("fp64", "mixed"):
+        ctx = make_ctx(cl.n, prec)
+        ctx.set_predicted(cl.x, cl.v, cl.m)  # host arrays
+        host = ctx.regular_force(idx, rs2)
+        dev = ctx.regular_force(T(idx), rs2)
+        ctx.sync()
+        np.testing.assert_array_equal(host.acc, dev.acc.cpu().numpy())
+        np.testing.assert_array_equal(host.pot, dev.pot.cpu().numpy())
+        np.testing.assert_array_equal(host.nb_off, dev.nb_off.cpu().numpy())
+        tot = host.nb_off[-1]
+        np.testing.assert_array_equal(host.nb_idx[:tot], dev.nb_idx[:tot].cpu().numpy())
+
+
+# ------------------------------------------------------------------ Plummer 128k Kroupa
+@pytest.fixture(scope="module")
+def p128k():
+    cl, rs2 = W.plummer_128k_kroupa()
+    steps = W.block_steps(cl, seed=1)
+    return cl, rs2, steps
+
+
+@pytest.mark.parametrize("n_i", [1, 7, 16, 31, 33, 128, 1000, 1024])
+def test_fp64_and_mixed_128k_blocks(gpu_lib, p128k, n_i):
+    cl, rs2, steps = p128k
+    idx = W.active_block(steps, n_i)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx, rs2, cap=512)
+    for prec in ("fp64", "mixed"):
+        ctx = make_ctx(cl.n, prec)
+        ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+        res = ctx.regular_force(T(idx), rs2)
+        ctx.sync()
+        if prec == "fp64":
+            check_fp64(res, ref, cl.x, cl.v, cl.m, idx)
+            check_lists_exact(res, ref[3], ref[4], 512)
+        else:
+            check_mixed(res, ref)
+            check_lists_band(res, cl.x, idx, rs2, ref[3], ref[4], 512)
+        ctx.close()
+
+
+@pytest.mark.slow
+def test_mixed_128k_large_block(gpu_lib, p128k):
+    cl, rs2, steps = p128k
+    idx = W.active_block(steps, 16384)
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    res = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    # oracle on a sample of the rows
+    sel = np.random.default_rng(0).choice(idx.size, 512, replace=False)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx[sel], rs2, cap=512)
+
+    class Sub:
+        pass
+    sub = Sub()
+    sub.acc, sub.jerk, sub.pot = res.acc[sel], res.jerk[sel], res.pot[sel]
+    check_mixed(sub, ref)
+    got = res.neighbour_lists()
+    cnt = res.nb_count.cpu().numpy()
+    for q, k in enumerate(sel):
+        a, b = set(got[k].tolist()), set(ref[4][q].tolist())
+        if a != b:
+            d = np.sqrt(((cl.x[list(a ^ b)] - cl.x[idx[k]]) ** 2).sum(1))
+            assert np.all(np.abs(d - math.sqrt(rs2)) <= 1e-6 * math.sqrt(rs2))
+        assert abs(int(cnt[k]) - int(ref[3][q])) <= len(a ^ b)
+
+
+# ------------------------------------------------------------------ neighbour caps and capacity
+def test_cap_truncation_keeps_smallest_indices(gpu_lib, p1k):
+    cl, rs2, idx, _ = p1k
+    big = 9 * rs2  # many neighbours per particle
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx, big, cap=16)
+    assert (ref[3] > 16).sum() > 100
+    for prec in ("fp64", "mixed"):
+        ctx = make_ctx(cl.n, prec, cap=16)
+        ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+        res = ctx.regular_force(T(idx), big)
+        with pytest.warns(Warning):
+            ctx.sync()
+        if prec == "fp64":
+            check_lists_exact(res, ref[3], ref[4], 16)
+        else:
+            check_lists_band(res, cl.x, idx, big, ref[3], ref[4], 16)
+
+
+def test_csr_capacity_too_small_is_reported(gpu_lib, p1k):
+    from paper_1504_03687_gb300 import api
+    cl, rs2, idx, ref = p1k
+    ctx = make_ctx(cl.n, "fp64")
+    ctx.set_predicted(cl.x, cl.v, cl.m)
+    with pytest.warns(api.NBOverflow):
+        res = ctx.regular_force(idx, rs2, nb_capacity=100)
+    assert res.nb_off[-1] == sum(min(c, 512) for c in ref[3])
+    flat = np.concatenate(ref[4])[:100]
+    np.testing.assert_array_equal(res.nb_idx[:100], flat)
+
+
+def test_per_particle_rs2(gpu_lib, p1k):
+    cl, rs2, idx, _ = p1k
+    sel = idx[::5]
+    rs2v = np.linspace(0.0, 2 * rs2, sel.size)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, sel, rs2v, cap=512)
+    ctx = make_ctx(cl.n, "fp64")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    res = ctx.regular_force(T(sel), rs2v)
+    ctx.sync()
+    check_lists_exact(res, ref[3], ref[4], 512)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_degenerate_sizes(gpu_lib):
+    from paper_1504_03687_gb300 import api
+    for prec in ("fp64", "mixed"):
+        # n = 1: the only particle feels nothing
+        ctx = make_ctx(4, prec)
+        x = np.array([[0.1, 0.2, 0.3]])
+        ctx.set_predicted(x, np.zeros((1, 3)), np.array([1.0]))
+        res = ctx.regular_force(np.array([0], np.int32), 1.0)
+        assert np.all(res.acc == 0) and np.all(res.pot == 0) and res.nb_count[0] == 0
+        # n = 2: closed form
+        x = np.array([[0.0, 0.0, 0.0], [0.3, -0.4, 1.2]])
+        v = np.array([[0.1, 0.0, 0.0], [0.0, 0.2, -0.1]])
+        m = np.array([0.25, 0.75])
+        ctx.set_predicted(x, v, m)
+        res = ctx.regular_force(np.array([1, 0], np.int32), 10.0)
+        ref = oracle.regular_force(x, v, m, np.array([1, 0], np.int32), 10.0)
+        tol = 1e-14 if prec == "fp64" else 1e-6
+        np.testing.assert_allclose(res.acc, ref[0], rtol=tol)
+        np.testing.assert_allclose(res.jerk, ref[1], rtol=tol)
+        np.testing.assert_allclose(res.pot, ref[2], rtol=tol)
+        assert res.nb_off.tolist() == [0, 1, 2] and res.nb_idx[:2].tolist() == [0, 1]
+        # n_i = 0
+        res = ctx.regular_force(np.zeros(0, np.int32), 1.0)
+        assert res.nb_off.tolist() == [0]
+        # out-of-range index: rejected on the host immediately
+        with pytest.raises(api.NBError) as e:
+            ctx.regular_force(np.array([0, 2], np.int32), 1.0)
+        assert e.value.status == api.NB_ERR_ARG
+        # ... and by the device check (deferred to nb_sync) for device buffers
+        ctx.regular_force(T(np.array([0, 5], np.int32)), 1.0)
+        with pytest.raises(api.NBError) as e:
+            ctx.sync()
+        assert e.value.status == api.NB_ERR_ARG
+        ctx.sync()  # the deferred status was consumed
+        ctx.close()
+
+
+def test_call_order_and_argument_errors(gpu_lib):
+    from paper_1504_03687_gb300 import api
+    ctx = make_ctx(8, "mixed")
+    with pytest.raises(api.NBError) as e:
+        ctx.predict(0.0)
+    assert e.value.status == api.NB_ERR_STATE
+    with pytest.raises(api.NBError) as e:
+        ctx.regular_force(np.zeros(1, np.int32), 1.0)
+    assert e.value.status == api.NB_ERR_STATE
+    with pytest.raises(api.NBError) as e:
+        ctx.set_predicted(np.zeros((9, 3)), np.zeros((9, 3)), np.ones(9))
+    assert e.value.status == api.NB_ERR_ARG
+    ctx.close()
+
+
+def test_duplicate_indices_give_identical_rows(gpu_lib, p1k):
+    cl, rs2, _, _ = p1k
+    idx = np.array([5, 17, 5, 900, 17], np.int32)
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(cl.x, cl.v, cl.m)
+    res = ctx.regular_force(idx, rs2)
+    np.testing.assert_array_equal(res.acc[0], res.acc[2])
+    np.testing.assert_array_equal(res.jerk[1], res.jerk[4])
+    lists = res.neighbour_lists()
+    np.testing.assert_array_equal(lists[0], lists[2])
+
+
+def test_bitwise_reproducible(gpu_lib, p128k):
+    cl, rs2, steps = p128k
+    idx = T(W.active_block(steps, 4096))
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    a = ctx.regular_force(idx, rs2)
+    b = ctx.regular_force(idx, rs2)
+    ctx.sync()
+    assert torch.equal(a.acc, b.acc) and torch.equal(a.jerk, b.jerk) and torch.equal(a.pot, b.pot)
+    assert torch.equal(a.nb_off, b.nb_off)
+    tot = int(a.nb_off[-1])
+    assert torch.equal(a.nb_idx[:tot], b.nb_idx[:tot])
+
+
+# ------------------------------------------------------------------ full size, 2^20
+@pytest.fixture(scope="module")
+def king1m():
+    cl, rs2 = W.king_1m_binaries()
+    steps = W.block_steps(cl, seed=2)
+    return cl, rs2, steps
+
+
+@pytest.mark.slow
+def test_million_body_sampled_rows(gpu_lib, king1m):
+    """King W0=6, 2^20 bodies: mixed full block and FP64 2^10 block vs oracle on sampled rows."""
+    cl, rs2, steps = king1m
+    n = cl.n
+    rng = np.random.default_rng(7)
+    for prec, n_i, n_s in (("mixed", n, 192), ("fp64", 1024, 96)):
+        idx = np.arange(n, dtype=np.int32) if n_i == n else W.active_block(steps, n_i)
+        ctx = make_ctx(n, prec)
+        ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+        res = ctx.regular_force(T(idx), rs2, nb_capacity=n_i * 256)
+        ctx.sync()
+        sel = np.sort(rng.choice(n_i, n_s, replace=False))
+        ref = oracle.regular_force(cl.x, cl.v, cl.m, idx[sel], rs2, cap=512)
+
+        class Sub:
+            pass
+        sub = Sub()
+        sub.acc, sub.jerk, sub.pot = res.acc[sel], res.jerk[sel], res.pot[sel]
+        if prec == "mixed":
+            check_mixed(sub, ref)
+        else:
+            sub.acc, sub.jerk, sub.pot = sub.acc.cpu().numpy(), sub.jerk.cpu().numpy(), sub.pot.cpu().numpy()
+            check_fp64(sub, ref, cl.x, cl.v, cl.m, idx[sel])
+        cnt = res.nb_count.cpu().numpy()[sel]
+        assert np.abs(cnt.astype(np.int64) - ref[3]).max() <= 2
+        ctx.close()

@@ -34,7 +34,7 @@ UNIT = "Ginteractions/s"
 FLOPS_PER_PAIR = 60
 BLOCKS = (1 << 10, 1 << 14, 1 << 17, 1 << 20)
 NB_CAP = 512
-NB_PER_ROW = 256  # CSR capacity per active particle (median count is ~80)
+NB_PER_ROW = NB_CAP  # CSR capacity per active particle: room for every list at the cap
 WORKLOAD = ("King W0=6, N=2^20 j-particles (5% binary c.m.), Kroupa IMF, N-body units; "
             "active blocks 2^10/2^14/2^17/2^20 from the sorted step list; "
             "predict + mixed regular force + neighbour CSR per block")
@@ -164,9 +164,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling case: one warm-up and one timed predict + force call on the King cluster "
+                         "(--n particles, --ni active, --prec), printing device times")
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--ni", type=int, default=2048)
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile_case(args)
 
     import torch
     rank, world, local = dist_env()
@@ -356,6 +365,41 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_profile_case(args):
+    """Small, self-contained case for ncu captures: King W0=6 cluster of --n particles,
+    the first --ni entries of its sorted step list; warm-up call, then one call."""
+    import torch
+
+    import workloads as W
+    from paper_1504_03687_gb300 import Context
+    dev = torch.device("cuda", 0)
+    cl = W.king(args.n, 2, W0=6.0, masses="kroupa", binary_fraction=0.05)
+    rs2 = W.neighbour_radius2(cl.x, 80, seed=2)
+    order = W.sorted_step_list(W.block_steps(cl, seed=2)).astype(np.int32)
+    a0, j0, tl = W.hermite_state(cl, seed=2, t_block=0.125)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    ctx = Context(cl.n, precision=args.prec, nb_cap=NB_CAP)
+    ctx.set_particles(*[T(q) for q in (cl.x, cl.v, a0, j0, cl.m, tl)])
+    idx = T(order[:args.ni])
+    rs2_dev = torch.tensor([rs2], dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(0)
+    g = [T(rng.standard_normal(s)) for s in ((args.ni, 3), (args.ni, 3), (args.ni,))]
+    for it in range(2):
+        ctx.set_timing(it == 1)
+        ctx.predict(0.125)
+        out = ctx.regular_force(idx, rs2_dev, nb_capacity=args.ni * NB_PER_ROW)
+        if args.backward:
+            ctx.regular_force_backward(idx, *g)
+        ctx.sync()
+    ph = ctx.timings()
+    pairs = args.ni * cl.n
+    res = {"case": f"King W0=6 n={cl.n} n_i={args.ni} {args.prec}", "plan": ctx.plan(cl.n, args.ni),
+           "phase_ms": {k: v[0] for k, v in ph.items()}, "launches": {k: v[1] for k, v in ph.items()},
+           "force_Ginteractions_s": pairs / (ph["force"][0] * 1e-3) / 1e9 if ph["force"][0] > 0 else None,
+           "nb_total": int(out.nb_off[-1].item())}
+    print(json.dumps(res))
 
 
 def host_force(ctx, idx, rs2, out):

@@ -153,15 +153,16 @@ nb_status nb_sync(nb_ctx *ctx);
 const char *nb_last_error(const nb_ctx *ctx);
 
 /* Describe the launch plan nb_regular_force would use (host-only, no GPU work):
- * out[0] = kernel id (0 = FP64 tiled, 1 = mixed tiled, 2 = mixed j-streamed),
- * out[1] = i-particles per CTA, out[2] = j-splits, out[3] = CTAs, out[4] = j-tile. */
+ * out[0] = kernel id (0 = FP64 tiled, 1 = mixed tiled, 2 = mixed j-streamed,
+ * 3 = FP64 j-streamed), out[1] = i-particles per CTA, out[2] = j-splits, out[3] = CTAs,
+ * out[4] = j-tile (0 for the j-streamed kernels). */
 nb_status nb_plan(const nb_ctx *ctx, int64_t n, int64_t n_i, int64_t *out);
 
 /* The same plan for a given device shape, without a context or a GPU (host-only):
- * num_sms SMs and ctas_per_sm[0..4] resident CTAs of the four mixed tiled variants and
- * the FP64 tiled kernel (NULL = 1 each). */
+ * num_sms SMs, ctas_per_sm[0..4] resident CTAs of the four mixed tiled variants and the
+ * FP64 tiled kernel (NULL = 1 each), and the context's nb_cap. */
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
-                      int64_t n_i, int64_t *out);
+                      int64_t n_i, int32_t nb_cap, int64_t *out);
 
 #ifdef __cplusplus
 }

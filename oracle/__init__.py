@@ -187,3 +187,55 @@ def hermite_replay(m, x, v, schedule):
     if rc != 0:
         raise RuntimeError(f"hermite_replay failed ({rc})")
     return x, v
+
+
+def pair_sums(xp, vp, m, idx, jdx):
+    """(acc, jerk, pot) of the rows idx summed over the sources jdx only (j != i)."""
+    lib = _load()
+    if not hasattr(lib, "_ps"):
+        P, i64 = ctypes.c_void_p, ctypes.c_int64
+        lib.orc_pair_sums.argtypes = [i64, P, P, P, i64, P, i64, P, P, P, P]
+        lib.orc_pair_sums.restype = ctypes.c_int
+        lib._ps = True
+    xp, vp, m = _c(xp, np.float64), _c(vp, np.float64), _c(m, np.float64)
+    idx, jdx = _c(idx, np.int32), _c(jdx, np.int32)
+    n_i = idx.shape[0]
+    acc = np.empty((n_i, 3)); jerk = np.empty((n_i, 3)); pot = np.empty(n_i)
+    rc = lib.orc_pair_sums(xp.shape[0], _p(xp), _p(vp), _p(m), n_i, _p(idx), jdx.shape[0], _p(jdx),
+                           _p(acc), _p(jerk), _p(pot))
+    if rc != 0:
+        raise IndexError("index outside [0, n)")
+    return acc, jerk, pot
+
+
+def loss_fd(xp, vp, m, idx, g_acc, g_jerk, g_pot, which: str, p: int, c: int = 0, h: float = 1e-6):
+    """Central difference (Richardson, O(h^4)) of L = Σ g·(acc, jerk, pot) w.r.t. one
+    coordinate of particle p (which = 'x', 'v' or 'm'), in O(N) by re-evaluating only
+    the sums that involve p: row p over all sources and column p of every other row."""
+    idx = np.asarray(idx, np.int32)
+    rows = np.nonzero(idx == p)[0]
+    others = np.nonzero(idx != p)[0]
+    n = xp.shape[0]
+    all_j = np.arange(n, dtype=np.int32)
+
+    def L_p(X, V, M):
+        tot = 0.0
+        if rows.size:
+            a, j, pt = pair_sums(X, V, M, idx[rows], all_j)
+            tot += (g_acc[rows] * a).sum() + (g_jerk[rows] * j).sum() + (g_pot[rows] * pt).sum()
+        a, j, pt = pair_sums(X, V, M, idx[others], np.array([p], np.int32))
+        tot += (g_acc[others] * a).sum() + (g_jerk[others] * j).sum() + (g_pot[others] * pt).sum()
+        return tot
+
+    def shifted(d):
+        X, V, M = xp.copy(), vp.copy(), m.copy()
+        if which == "x":
+            X[p, c] += d
+        elif which == "v":
+            V[p, c] += d
+        else:
+            M[p] += d
+        return L_p(X, V, M)
+    d1 = (shifted(h) - shifted(-h)) / (2 * h)
+    d2 = (shifted(h / 2) - shifted(-h / 2)) / h
+    return (4 * d2 - d1) / 3

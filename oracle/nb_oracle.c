@@ -391,3 +391,47 @@ static int hermite_core(int64_t n, const double *m, double *x, double *v, double
     free(a); free(jk); free(xp); free(vp); free(t); free(dt); free(a1); free(j1); free(pot); free(act);
     return rc;
 }
+
+/* Regular-force sums of the active rows idx over a subset jdx of the sources only:
+ *   acc_k = sum_{j in jdx, j != idx[k]} m_j r/|r|^3   (same for jerk and pot),
+ * the definition above with the j-loop restricted (used for O(N) finite differences:
+ * perturbing one particle p changes only row p and the column j = p of every row). */
+int orc_pair_sums(int64_t n, const double *xp, const double *vp, const double *m, int64_t n_i, const int32_t *idx,
+                  int64_t n_j, const int32_t *jdx, double *acc, double *jerk, double *pot)
+{
+    for (int64_t k = 0; k < n_i; ++k)
+        if (idx[k] < 0 || idx[k] >= n) return -1;
+    for (int64_t q = 0; q < n_j; ++q)
+        if (jdx[q] < 0 || jdx[q] >= n) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n_i; ++k) {
+        const int64_t i = idx[k];
+        double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0, ph = 0;
+        for (int64_t q = 0; q < n_j; ++q) {
+            const int64_t j = jdx[q];
+            if (j == i) continue;
+            const double rx = xp[3 * j + 0] - xp[3 * i + 0];
+            const double ry = xp[3 * j + 1] - xp[3 * i + 1];
+            const double rz = xp[3 * j + 2] - xp[3 * i + 2];
+            const double wx = vp[3 * j + 0] - vp[3 * i + 0];
+            const double wy = vp[3 * j + 1] - vp[3 * i + 1];
+            const double wz = vp[3 * j + 2] - vp[3 * i + 2];
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            const double rinv = 1.0 / sqrt(r2);
+            const double rinv2 = rinv * rinv;
+            const double mr3 = m[j] * rinv * rinv2;
+            const double rw = rx * wx + ry * wy + rz * wz;
+            ax += mr3 * rx;
+            ay += mr3 * ry;
+            az += mr3 * rz;
+            jx += mr3 * (wx - 3.0 * rw * rinv2 * rx);
+            jy += mr3 * (wy - 3.0 * rw * rinv2 * ry);
+            jz += mr3 * (wz - 3.0 * rw * rinv2 * rz);
+            ph -= m[j] * rinv;
+        }
+        acc[3 * k + 0] = ax;  acc[3 * k + 1] = ay;  acc[3 * k + 2] = az;
+        jerk[3 * k + 0] = jx; jerk[3 * k + 1] = jy; jerk[3 * k + 2] = jz;
+        pot[k] = ph;
+    }
+    return 0;
+}

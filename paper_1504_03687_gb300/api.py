@@ -74,7 +74,7 @@ def load_library(build_if_needed: bool = True):
         "nb_sync": (st, [P]),
         "nb_last_error": (ctypes.c_char_p, [P]),
         "nb_plan": (st, [P, i64, i64, P]),
-        "nb_plan_for": (st, [i32, i32, P, i64, i64, P]),
+        "nb_plan_for": (st, [i32, i32, P, i64, i64, i32, P]),
         "nb_set_timing": (st, [P, i32]),
         "nb_get_timings": (st, [P, P, P]),
     }
@@ -86,13 +86,13 @@ def load_library(build_if_needed: bool = True):
     return lib
 
 
-def plan_for(precision: str, num_sms: int, ctas_per_sm, n: int, n_i: int) -> dict:
+def plan_for(precision: str, num_sms: int, ctas_per_sm, n: int, n_i: int, nb_cap: int = 512) -> dict:
     """Host-only launch plan (no GPU needed)."""
     lib = load_library()
     out = (ctypes.c_int64 * 5)()
     occ = (ctypes.c_int32 * 5)(*ctas_per_sm) if ctas_per_sm is not None else None
     s = lib.nb_plan_for(PRECISIONS[precision], num_sms, ctypes.cast(occ, ctypes.c_void_p) if occ else None,
-                        n, n_i, ctypes.cast(out, ctypes.c_void_p))
+                        n, n_i, nb_cap, ctypes.cast(out, ctypes.c_void_p))
     if s != NB_OK:
         raise NBError(s, "nb_plan_for rejected its arguments")
     return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4])

@@ -1,7 +1,8 @@
 // force_fp64.cu — K2: regular force, jerk, potential and neighbour capture with every
 // operation in FP64 (paper Sec. 3.2.1).  The reference-precision GPU path: same work
 // decomposition as the mixed kernels (tiled for large active blocks, j-streamed for tiny
-// ones), FP64 partial sums [split][7][n_i] added in a fixed order by k_reduce.
+// ones), FP64 partial sums [split][7][n_i] added in a fixed order by k_reduce, and the
+// same ordered neighbour segments.
 //
 // The neighbour test uses r^2 = (rx*rx + ry*ry) + rz*rz with IEEE round-to-nearest and no
 // contraction, the same arithmetic as a plain C evaluation of the definition.
@@ -9,12 +10,6 @@
 #include "nb_kernels.cuh"
 
 namespace nbgpu {
-
-__device__ __forceinline__ void record_neighbour64(const ForceArgs &A, int64_t k, int64_t j)
-{
-    const int pos = atomicAdd(A.nb_cnt + k, 1);
-    if (pos < A.cap) A.nb_tmp[k * (int64_t)A.cap + pos] = (int32_t)j;
-}
 
 // acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] -= m/|r|
 __device__ __forceinline__ double pair_f64(const dvec4 &p0, const dvec4 &p1, const double (&xi)[3],
@@ -42,7 +37,7 @@ __device__ __forceinline__ double pair_f64(const dvec4 &p0, const dvec4 &p1, con
 template <int BLOCK, int TJ>
 __global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
 {
-    __shared__ __align__(16) dvec4 sj[2][2 * TJ];
+    __shared__ dvec4 sj[2][2 * TJ];
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * BLOCK + tid;
     const int s = blockIdx.y;
@@ -64,6 +59,8 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
         vi[0] = p1.x; vi[1] = p1.y; vi[2] = p1.z;
         if (A.want_nb) rs2 = A.rs2[A.rs2_scalar ? 0 : k];
     }
+    int32_t *slot = A.seg_slots + ((int64_t)s * A.n_i + (k < A.n_i ? k : 0)) * A.L;
+    int cnt = 0;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
 
     auto load_tile = [&](int buf, int64_t t) {
@@ -89,28 +86,36 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
         for (int jj = 0; jj < TJ; ++jj) {
             const int64_t j = jb + jj;
             const double r2 = pair_f64(sj[buf][2 * jj], sj[buf][2 * jj + 1], xi, vi, j == g, acc);
-            if (r2 < rs2 && j != g && j < A.n) record_neighbour64(A, k, j);
+            if (r2 < rs2 && j != g && j < A.n) {
+                if (cnt < A.L) slot[cnt] = (int32_t)j;
+                ++cnt;
+            }
         }
         __syncthreads();
     }
     if (k < A.n_i) {
 #pragma unroll
         for (int c = 0; c < 7; ++c) A.part[((int64_t)s * 7 + c) * A.n_i + k] = acc[c];
+        if (A.want_nb) A.seg_cnt[(int64_t)s * A.n_i + k] = cnt;
     }
 }
 
 template <int IB, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_force_fp64_jstream(ForceArgs A)
 {
-    __shared__ double red[BLOCK / 32][IB][7];
-    const int tid = threadIdx.x;
+    constexpr int W = BLOCK / 32;
+    __shared__ double red[W][IB][7];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int s = blockIdx.y;
     const int64_t k0 = (int64_t)blockIdx.x * IB;
     const int64_t j0 = (A.n * s) / A.S, j1 = (A.n * (s + 1)) / A.S;
+    const int64_t w0 = j0 + ((j1 - j0) * w) / W, w1 = j0 + ((j1 - j0) * (w + 1)) / W;
+    const int64_t seg = (int64_t)s * W + w;
     const dvec4 *rec = static_cast<const dvec4 *>(A.rec);
 
     double xi[IB][3], vi[IB][3], rs2[IB];
     int64_t gi[IB];
+    int cnt[IB];
 #pragma unroll
     for (int q = 0; q < IB; ++q) {
         const int64_t k = k0 + q;
@@ -123,6 +128,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_jstream(ForceArgs A)
             }
         }
         gi[q] = g;
+        cnt[q] = 0;
         rs2[q] = -1.0;
         if (g >= 0) {
             const dvec4 p0 = rec[2 * g], p1 = rec[2 * g + 1];
@@ -139,15 +145,32 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_jstream(ForceArgs A)
     for (int q = 0; q < IB; ++q)
 #pragma unroll
         for (int c = 0; c < 7; ++c) acc[q][c] = 0.0;
-    for (int64_t j = j0 + tid; j < j1; j += BLOCK) {
-        const dvec4 p0 = rec[2 * j], p1 = rec[2 * j + 1];
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t base = w0; base < w1; base += 32) {  // warp-uniform trip count
+        const int64_t j = base + lane;
+        const bool valid = j < w1;
+        dvec4 p0 = make_dvec4(1e18, 1e18, 1e18, 0.0), p1 = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        if (valid) {
+            p0 = rec[2 * j];
+            p1 = rec[2 * j + 1];
+        }
 #pragma unroll
         for (int q = 0; q < IB; ++q) {
             const double r2 = pair_f64(p0, p1, xi[q], vi[q], j == gi[q], acc[q]);
-            if (r2 < rs2[q] && j != gi[q]) record_neighbour64(A, k0 + q, j);
+            const bool hit = valid && r2 < rs2[q] && j != gi[q];
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            if (mask) {
+                const int pos = cnt[q] + __popc(mask & below);
+                if (hit && pos < A.L) A.seg_slots[(seg * A.n_i + k0 + q) * A.L + pos] = (int32_t)j;
+                cnt[q] += __popc(mask);
+            }
         }
     }
-    const int w = tid >> 5, lane = tid & 31;
+    if (A.want_nb && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < IB; ++q)
+            if (k0 + q < A.n_i) A.seg_cnt[seg * A.n_i + k0 + q] = cnt[q];
+    }
 #pragma unroll
     for (int q = 0; q < IB; ++q)
 #pragma unroll
@@ -162,14 +185,13 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_jstream(ForceArgs A)
         if (k < A.n_i) {
             double sum = 0.0;
 #pragma unroll
-            for (int ww = 0; ww < BLOCK / 32; ++ww) sum += red[ww][q][c];
+            for (int ww = 0; ww < W; ++ww) sum += red[ww][q][c];
             A.part[((int64_t)s * 7 + c) * A.n_i + k] = sum;
         }
     }
 }
 
 void *fp64_tiled_fn() { return (void *)k_force_fp64_tiled<128, 64>; }
-void *fp64_jstream_fn(int v) { return v == 0 ? (void *)k_force_fp64_jstream<1, 256> : (void *)k_force_fp64_jstream<4, 256>; }
 int fp64_jstream_ib(int v) { return v == 0 ? 1 : 4; }
 
 void launch_force_fp64(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a)

@@ -11,21 +11,17 @@
 //  * tiled     : CTA = NI*BLOCK active particles (NI per thread, register-blocked) x one
 //                j-range; j-tiles of TJ records are staged in shared memory with cp.async
 //                (double-buffered) and broadcast to all threads.  FP32-issue bound.
-//  * j-streamed: for tiny active blocks.  CTA = IB active particles x one j-chunk; each
-//                thread streams its own j-records from HBM (coalesced) and the block
-//                reduces the IB x 7 partial sums with warp shuffles.  HBM/latency bound.
+//  * j-streamed: for tiny active blocks.  CTA = IB active particles x one j-chunk; every
+//                warp streams its own contiguous sub-chunk from HBM (coalesced) and the
+//                block reduces the IB x 7 partial sums with warp shuffles.  HBM/latency bound.
 // Both write FP64 partial sums [split][7][n_i] that k_reduce adds in a fixed order, so
-// results are bitwise reproducible for a given launch plan.
+// results are bitwise reproducible for a given launch plan.  Neighbour segments: one per
+// split (tiled, owned by the thread holding the row) or one per warp (j-streamed, ordered
+// within the warp by ballot).
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
 
 namespace nbgpu {
-
-__device__ __forceinline__ void record_neighbour(const ForceArgs &A, int64_t k, int64_t j)
-{
-    const int pos = atomicAdd(A.nb_cnt + k, 1);
-    if (pos < A.cap) A.nb_tmp[k * (int64_t)A.cap + pos] = (int32_t)j;
-}
 
 // One pair (i <- j) in mixed precision; returns r^2 for the neighbour test.
 // acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] += m/|r|
@@ -62,8 +58,8 @@ template <int NI, bool MASK, int TJ>
 __device__ __forceinline__ void tile_mixed(const float4 *__restrict__ sj, int64_t jb, const ForceArgs &A,
                                            const float (&ih)[NI][3], const float (&il)[NI][3],
                                            const float (&iv)[NI][3], const float (&rs2f)[NI],
-                                           const int64_t (&gi)[NI], const int64_t (&kk)[NI],
-                                           float (&acc)[NI][7])
+                                           const int64_t (&gi)[NI], int32_t *const (&slot)[NI],
+                                           int (&cnt)[NI], float (&acc)[NI][7])
 {
 #pragma unroll 4
     for (int jj = 0; jj < TJ; ++jj) {
@@ -78,10 +74,13 @@ __device__ __forceinline__ void tile_mixed(const float4 *__restrict__ sj, int64_
                                      iv[q][0], iv[q][1], iv[q][2], MASK && (j == gi[q]), acc[q]);
             hit |= r2[q] < rs2f[q];
         }
-        if (hit) {
+        if (hit) {  // rare: record in ascending j, the first L per segment
 #pragma unroll
             for (int q = 0; q < NI; ++q)
-                if (r2[q] < rs2f[q] && j != gi[q] && j < A.n) record_neighbour(A, kk[q], j);
+                if (r2[q] < rs2f[q] && j != gi[q] && j < A.n) {
+                    if (cnt[q] < A.L) slot[q][cnt[q]] = (int32_t)j;
+                    ++cnt[q];
+                }
         }
     }
 }
@@ -97,11 +96,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled(ForceArgs A)
     const float4 *rec = static_cast<const float4 *>(A.rec);
 
     float ih[NI][3], il[NI][3], iv[NI][3], rs2f[NI];
-    int64_t gi[NI], kk[NI];
+    int64_t gi[NI];
+    int32_t *slot[NI];
+    int cnt[NI];
 #pragma unroll
     for (int q = 0; q < NI; ++q) {
         const int64_t k = kbase + q * BLOCK + tid;
-        kk[q] = k;
         int64_t g = -1;
         if (k < A.n_i) {
             g = A.idx[k];
@@ -111,6 +111,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled(ForceArgs A)
             }
         }
         gi[q] = g;
+        cnt[q] = 0;
+        slot[q] = A.seg_slots + ((int64_t)s * A.n_i + (k < A.n_i ? k : 0)) * A.L;
         if (g >= 0) {
             const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
             ih[q][0] = p0.x; ih[q][1] = p0.y; ih[q][2] = p0.z;
@@ -156,9 +158,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled(ForceArgs A)
 #pragma unroll
             for (int c = 0; c < 7; ++c) acc[q][c] = 0.f;
         if (__any_sync(0xffffffffu, mine))
-            tile_mixed<NI, true, TJ>(sj[buf], jb, A, ih, il, iv, rs2f, gi, kk, acc);
+            tile_mixed<NI, true, TJ>(sj[buf], jb, A, ih, il, iv, rs2f, gi, slot, cnt, acc);
         else
-            tile_mixed<NI, false, TJ>(sj[buf], jb, A, ih, il, iv, rs2f, gi, kk, acc);
+            tile_mixed<NI, false, TJ>(sj[buf], jb, A, ih, il, iv, rs2f, gi, slot, cnt, acc);
 #pragma unroll
         for (int q = 0; q < NI; ++q)
 #pragma unroll
@@ -167,43 +169,51 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled(ForceArgs A)
     }
 #pragma unroll
     for (int q = 0; q < NI; ++q) {
-        const int64_t k = kk[q];
+        const int64_t k = kbase + q * BLOCK + tid;
         if (k < A.n_i) {
 #pragma unroll
             for (int c = 0; c < 7; ++c)
                 A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -dacc[q][c] : dacc[q][c];
+            if (A.want_nb) A.seg_cnt[(int64_t)s * A.n_i + k] = cnt[q];
         }
     }
 }
 
 // j-streamed kernel for small active blocks: blockIdx.x = batch of IB active particles,
-// blockIdx.y = j-chunk.  Chunks are contiguous ranges of whole particles [j0, j1).
+// blockIdx.y = j-chunk [j0, j1).  Warp w of the CTA walks the contiguous sub-chunk w of
+// the chunk, 32 consecutive j per step, so its neighbour segment (g = s*W + w) is built
+// in ascending j by ballot.
 template <int IB, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_force_mixed_jstream(ForceArgs A)
 {
-    __shared__ double red[BLOCK / 32][IB][7];
-    const int tid = threadIdx.x;
+    constexpr int W = BLOCK / 32;
+    __shared__ double red[W][IB][7];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int s = blockIdx.y;
     const int64_t k0 = (int64_t)blockIdx.x * IB;
     const int64_t j0 = (A.n * s) / A.S, j1 = (A.n * (s + 1)) / A.S;
+    const int64_t w0 = j0 + ((j1 - j0) * w) / W, w1 = j0 + ((j1 - j0) * (w + 1)) / W;
+    const int64_t g = (int64_t)s * W + w;
     const float4 *rec = static_cast<const float4 *>(A.rec);
 
     float ih[IB][3], il[IB][3], iv[IB][3], rs2f[IB];
     int64_t gi[IB];
+    int cnt[IB];
 #pragma unroll
     for (int q = 0; q < IB; ++q) {
         const int64_t k = k0 + q;
-        int64_t g = -1;
+        int64_t gg = -1;
         if (k < A.n_i) {
-            g = A.idx[k];
-            if (g < 0 || g >= A.n) {
+            gg = A.idx[k];
+            if (gg < 0 || gg >= A.n) {
                 if (s == 0 && tid == 0) atomicOr(A.status, ST_BAD_INDEX);
-                g = -1;
+                gg = -1;
             }
         }
-        gi[q] = g;
-        if (g >= 0) {
-            const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
+        gi[q] = gg;
+        cnt[q] = 0;
+        if (gg >= 0) {
+            const float4 p0 = rec[3 * gg], p1 = rec[3 * gg + 1], p2 = rec[3 * gg + 2];
             ih[q][0] = p0.x; ih[q][1] = p0.y; ih[q][2] = p0.z;
             il[q][0] = p1.x; il[q][1] = p1.y; il[q][2] = p1.z;
             iv[q][0] = p2.x; iv[q][1] = p2.y; iv[q][2] = p2.z;
@@ -220,18 +230,36 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed_jstream(ForceArgs A)
 #pragma unroll
         for (int c = 0; c < 7; ++c) acc[q][c] = 0.f;
 
-    for (int64_t j = j0 + tid; j < j1; j += BLOCK) {
-        const float4 p0 = __ldg(rec + 3 * j), p1 = __ldg(rec + 3 * j + 1), p2 = __ldg(rec + 3 * j + 2);
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t base = w0; base < w1; base += 32) {  // warp-uniform trip count
+        const int64_t j = base + lane;
+        const bool valid = j < w1;
+        float4 p0 = make_float4(kPadPos, kPadPos, kPadPos, 0.f), p1 = make_float4(0.f, 0.f, 0.f, 0.f), p2 = p1;
+        if (valid) {
+            p0 = __ldg(rec + 3 * j);
+            p1 = __ldg(rec + 3 * j + 1);
+            p2 = __ldg(rec + 3 * j + 2);
+        }
 #pragma unroll
         for (int q = 0; q < IB; ++q) {
-            const float r2 = pair_mixed<true>(p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p2.x, p2.y,
-                                              p2.z, ih[q][0], ih[q][1], ih[q][2], il[q][0], il[q][1],
-                                              il[q][2], iv[q][0], iv[q][1], iv[q][2], j == gi[q], acc[q]);
-            if (r2 < rs2f[q] && j != gi[q]) record_neighbour(A, k0 + q, j);
+            const float r2 = pair_mixed<true>(p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p2.x, p2.y, p2.z, ih[q][0],
+                                              ih[q][1], ih[q][2], il[q][0], il[q][1], il[q][2], iv[q][0], iv[q][1],
+                                              iv[q][2], j == gi[q], acc[q]);
+            const bool hit = valid && r2 < rs2f[q] && j != gi[q];
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            if (mask) {
+                const int pos = cnt[q] + __popc(mask & below);
+                if (hit && pos < A.L) A.seg_slots[(g * A.n_i + k0 + q) * A.L + pos] = (int32_t)j;
+                cnt[q] += __popc(mask);
+            }
         }
     }
+    if (A.want_nb && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < IB; ++q)
+            if (k0 + q < A.n_i) A.seg_cnt[g * A.n_i + k0 + q] = cnt[q];
+    }
     // block reduction: warp shuffles, then one FP64 slot per warp, summed in warp order
-    const int w = tid >> 5, lane = tid & 31;
 #pragma unroll
     for (int q = 0; q < IB; ++q)
 #pragma unroll
@@ -246,7 +274,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed_jstream(ForceArgs A)
         if (k < A.n_i) {
             double sum = 0.0;
 #pragma unroll
-            for (int ww = 0; ww < BLOCK / 32; ++ww) sum += red[ww][q][c];
+            for (int ww = 0; ww < W; ++ww) sum += red[ww][q][c];
             A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -sum : sum;
         }
     }
@@ -271,16 +299,9 @@ void *mixed_tiled_fn(int v)
 int mixed_tiled_i_per_cta(int v) { return kTiled[v].ni * kTiled[v].block; }
 int mixed_tiled_block(int v) { return kTiled[v].block; }
 int mixed_tiled_tj(int v) { return kTiled[v].tj; }
-
-void *mixed_jstream_fn(int v)
-{
-    switch (v) {
-    case 0: return (void *)k_force_mixed_jstream<1, 256>;
-    case 1: return (void *)k_force_mixed_jstream<4, 256>;
-    default: return (void *)k_force_mixed_jstream<8, 256>;
-    }
-}
 int mixed_jstream_ib(int v) { return v == 0 ? 1 : (v == 1 ? 4 : 8); }
+constexpr int kJstreamBlock = 256;
+int jstream_warps() { return kJstreamBlock / 32; }
 
 void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a)
 {
@@ -294,9 +315,9 @@ void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x
         }
     } else {
         switch (variant) {
-        case 0: k_force_mixed_jstream<1, 256><<<grid, 256, 0, st>>>(a); break;
-        case 1: k_force_mixed_jstream<4, 256><<<grid, 256, 0, st>>>(a); break;
-        default: k_force_mixed_jstream<8, 256><<<grid, 256, 0, st>>>(a); break;
+        case 0: k_force_mixed_jstream<1, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        case 1: k_force_mixed_jstream<4, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        default: k_force_mixed_jstream<8, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
         }
     }
 }

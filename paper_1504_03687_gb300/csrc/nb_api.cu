@@ -22,6 +22,7 @@ int mixed_tiled_i_per_cta(int v);
 int mixed_tiled_block(int v);
 int mixed_tiled_tj(int v);
 int mixed_jstream_ib(int v);
+int jstream_warps();
 void *fp64_tiled_fn();
 int fp64_jstream_ib(int v);
 void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
@@ -49,9 +50,8 @@ struct nb_ctx {
     unsigned *status = nullptr;
     // grow-only scratch
     double *part = nullptr; size_t part_cap = 0;
-    int32_t *nb_tmp = nullptr; size_t nb_tmp_cap = 0;
-    int32_t *nb_cnt = nullptr; size_t nb_cnt_cap = 0;
-    int32_t *over = nullptr; size_t over_cap = 0;
+    int32_t *seg_slots = nullptr; size_t seg_slots_cap = 0;
+    int32_t *seg_cnt = nullptr; size_t seg_cnt_cap = 0;
     int64_t *scan = nullptr; size_t scan_cap = 0;
     char *stage = nullptr; size_t stage_cap = 0;
     char *adj = nullptr; size_t adj_cap = 0;
@@ -194,7 +194,19 @@ static double wave_eff(int64_t ctas, int64_t P)
 // kernel (every CTA streams a contiguous j-chunk for a few i); larger ones the tiled kernel,
 // with S chosen so that the CTA count fills whole waves of the GPU (each split must keep at
 // least two j-tiles).  Relative per-pair speed of the tiled variants weights the choice.
-Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i)
+// Splits whose neighbour slot arrays (S x n_i x min(nb_cap, split length) int32) would
+// exceed kSlotBudget are not considered (S = 1 always is).
+static constexpr double kSlotBudget = 6.0e9;
+
+static void jstream_segments(Plan &p, int64_t n)
+{
+    const int W = jstream_warps();
+    p.segs_per_split = W;
+    const int64_t chunk = (n + p.S - 1) / p.S;
+    p.seg_len = (chunk + W - 1) / W + 1;
+}
+
+Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i, int nb_cap)
 {
     Plan p{};
     if (num_sms <= 0) num_sms = 152;
@@ -212,6 +224,7 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
             p.S = (int)S;
             p.ctas = batches * S;
             p.tj = 0;
+            jstream_segments(p, n);
             return p;
         }
         static const double speed[4] = {1.0, 0.90, 0.78, 0.98};
@@ -226,6 +239,9 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
             if (smax > 2048) smax = 2048;
             for (int64_t S = 1; S <= smax; ++S) {
                 const int64_t ctas = itiles * S;
+                const int64_t seg = (tiles + S - 1) / S * tj;
+                const double slots = (double)S * (double)n_i * (double)(seg < nb_cap ? seg : nb_cap) * 4.0;
+                if (S > 1 && slots > kSlotBudget) break;
                 // a split costs one partial-sum write per i; penalise many splits slightly
                 const double score = speed[v] * util * wave_eff(ctas, P) * (1.0 - 0.0005 * (double)S);
                 if (score > best + 1e-12) {
@@ -236,6 +252,8 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
                     p.S = (int)S;
                     p.ctas = ctas;
                     p.tj = tj;
+                    p.segs_per_split = 1;
+                    p.seg_len = seg;
                 }
                 if (ctas >= 64 * P) break;
             }
@@ -255,6 +273,7 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
         p.S = (int)S;
         p.ctas = batches * S;
         p.tj = 0;
+        jstream_segments(p, n);
         return p;
     }
     const int ipc = 128, tj = 64;
@@ -266,6 +285,9 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
     double best = -1.0;
     for (int64_t S = 1; S <= smax; ++S) {
         const int64_t ctas = itiles * S;
+        const int64_t seg = (tiles + S - 1) / S * tj;
+        const double slots = (double)S * (double)n_i * (double)(seg < nb_cap ? seg : nb_cap) * 4.0;
+        if (S > 1 && slots > kSlotBudget) break;
         const double score = wave_eff(ctas, P) * (1.0 - 0.0005 * (double)S);
         if (score > best + 1e-12) {
             best = score;
@@ -275,6 +297,8 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
             p.S = (int)S;
             p.ctas = ctas;
             p.tj = tj;
+            p.segs_per_split = 1;
+            p.seg_len = seg;
         }
         if (ctas >= 64 * P) break;
     }
@@ -365,7 +389,7 @@ nb_status nb_free(nb_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
-                    c->part, c->nb_tmp, c->nb_cnt, c->over, c->scan, c->stage, c->adj};
+                    c->part, c->seg_slots, c->seg_cnt, c->scan, c->stage, c->adj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -469,7 +493,7 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, int32_t on_device)
 nb_status nb_plan(const nb_ctx *c, int64_t n, int64_t n_i, int64_t *out)
 {
     if (!c || !out || n < 1 || n_i < 0) return NB_ERR_ARG;
-    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i);
+    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i, c->cap);
     out[0] = p.kernel;
     out[1] = p.i_per_cta;
     out[2] = p.S;
@@ -479,13 +503,13 @@ nb_status nb_plan(const nb_ctx *c, int64_t n, int64_t n_i, int64_t *out)
 }
 
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n, int64_t n_i,
-                      int64_t *out)
+                      int32_t nb_cap, int64_t *out)
 {
-    if (!out || n < 1 || n_i < 0 || (precision != NB_FP64 && precision != NB_MIXED)) return NB_ERR_ARG;
+    if (!out || n < 1 || n_i < 0 || nb_cap < 1 || (precision != NB_FP64 && precision != NB_MIXED)) return NB_ERR_ARG;
     int occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     if (ctas_per_sm)
         for (int q = 0; q < 5; ++q) occ[q] = ctas_per_sm[q];
-    Plan p = plan_force(precision, num_sms, occ, n, n_i);
+    Plan p = plan_force(precision, num_sms, occ, n, n_i, nb_cap);
     out[0] = p.kernel;
     out[1] = p.i_per_cta;
     out[2] = p.S;
@@ -544,17 +568,19 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
         CK(cudaMemcpyAsync((void *)d_rs2, rs2, n_rs2 * 8, cudaMemcpyHostToDevice, c->stream), "copy rs2");
     }
-    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i);
+    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i, c->cap);
     const size_t part_bytes = (size_t)p.S * 7 * (size_t)n_i * sizeof(double);
     if ((s = grow(c, (void **)&c->part, &c->part_cap, part_bytes, "partial sums")) != NB_OK) return s;
-    if ((s = grow(c, (void **)&c->nb_cnt, &c->nb_cnt_cap, (size_t)n_i * 4, "neighbour counters")) != NB_OK) return s;
+    // neighbour segments: G ordered j-segments, L slots each per row (0: counts only)
+    const int64_t G = (int64_t)p.S * p.segs_per_split;
+    const int L = d_nbidx ? (int)(p.seg_len < c->cap ? p.seg_len : c->cap) : 0;
     const size_t scan_elems = neighbour_scan_tmp_elems(n_i) + (d_off ? 0 : (size_t)n_i + 1);
     if (want_nb) {
-        if ((s = grow(c, (void **)&c->nb_tmp, &c->nb_tmp_cap, (size_t)n_i * c->cap * 4, "neighbour slots")) != NB_OK) return s;
-        if ((s = grow(c, (void **)&c->over, &c->over_cap, (size_t)n_i * 4, "overflow list")) != NB_OK) return s;
+        if ((s = grow(c, (void **)&c->seg_cnt, &c->seg_cnt_cap, (size_t)G * n_i * 4, "neighbour counts")) != NB_OK) return s;
+        if (L > 0 &&
+            (s = grow(c, (void **)&c->seg_slots, &c->seg_slots_cap, (size_t)G * n_i * L * 4, "neighbour slots")) != NB_OK)
+            return s;
         if ((s = grow(c, (void **)&c->scan, &c->scan_cap, scan_elems * 8, "scan scratch")) != NB_OK) return s;
-        CK(cudaMemsetAsync(c->nb_cnt, 0, (size_t)n_i * 4, c->stream), "cudaMemsetAsync");
-        CK(cudaMemsetAsync(c->status + SS_OVERFLOW_COUNT, 0, sizeof(unsigned), c->stream), "cudaMemsetAsync");
     }
     ForceArgs fa{};
     fa.rec = c->rec;
@@ -564,10 +590,10 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
     fa.rs2 = d_rs2;
     fa.rs2_scalar = rs2_scalar ? 1 : 0;
     fa.want_nb = want_nb ? 1 : 0;
-    fa.cap = c->cap;
+    fa.L = L;
     fa.part = c->part;
-    fa.nb_cnt = c->nb_cnt;
-    fa.nb_tmp = c->nb_tmp;
+    fa.seg_cnt = c->seg_cnt;
+    fa.seg_slots = c->seg_slots;
     fa.status = c->status;
     cudaEvent_t t0 = span_begin(c);
     launch_force(c->stream, p, fa);
@@ -581,11 +607,11 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         // counts only: the scan still needs an offsets buffer, taken from the scan scratch
         int64_t *off_buf = d_off ? d_off : c->scan + neighbour_scan_tmp_elems(n_i);
         t0 = span_begin(c);
-        launch_neighbour_csr(c->stream, c->precision, c->rec, n, d_idx, n_i, d_rs2, fa.rs2_scalar, c->nb_cnt,
-                             c->nb_tmp, c->cap, off_buf, d_nbidx, d_nbidx ? nb_idx_capacity : 0, d_cnt_true,
-                             c->scan, c->over, c->status, c->num_sms);
+        const int kernels = launch_neighbour_csr(c->stream, G, n_i, L, c->cap, c->seg_cnt, c->seg_slots, off_buf,
+                                                 d_nbidx, d_nbidx ? nb_idx_capacity : 0, d_cnt_true, c->scan,
+                                                 c->status);
         CK_LAUNCH("neighbour CSR launch");
-        span_end(c, PH_NEIGHBOURS, t0, d_nbidx ? 5 : 3);
+        span_end(c, PH_NEIGHBOURS, t0, kernels);
     }
     if (on_device) return NB_OK;
     // host mode: copy results back and report the deferred status of this call

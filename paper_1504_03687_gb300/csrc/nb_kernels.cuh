@@ -6,11 +6,19 @@
 namespace nbgpu {
 
 // Predicted j-records.
-//  FP64 : 2 dvec4 per particle  {x, y, z, m}, {vx, vy, vz, 0}                 (64 B)
-//  mixed: 3 float4  per particle  {x_hi, y_hi, z_hi, m}, {x_lo, y_lo, z_lo, 0},
-//                                 {vx, vy, vz, 0}                               (48 B)
+//  FP64 : 2 dvec4 per particle  {x, y, z, m}, {vx, vy, vz, 0}                   (64 B)
+//  mixed: 3 float4 per particle {x_hi, y_hi, z_hi, m}, {x_lo, y_lo, z_lo, 0},
+//                               {vx, vy, vz, 0}                                 (48 B)
 // x_hi = fl32(x), x_lo = fl32(x - x_hi).  Records n .. n_pad-1 are padding: mass 0,
 // position 1e18, so whole tiles can be read without a bounds check.
+//
+// Neighbour capture.  The j-range is cut into G ordered segments; for every (segment g,
+// active row k) exactly one thread (tiled kernels) or one warp (j-streamed kernels) walks
+// the segment in ascending j and appends hits to seg_slots[(g*n_i + k)*L ...] (at most L
+// kept, all counted in seg_cnt[g*n_i + k]).  The CSR row k is then the concatenation of
+// its segments in order, cut at nb_cap: ascending j, deterministic, no atomics, no sort.
+// L = min(nb_cap, longest segment) suffices because a segment that holds more than L
+// hits can only be reached when L = nb_cap.
 
 struct ForceArgs {
     const void *rec;        // dvec4* (FP64) or float4* (mixed)
@@ -22,10 +30,10 @@ struct ForceArgs {
     int32_t rs2_scalar;
     int32_t want_nb;        // 0: skip neighbour capture
     int32_t S;              // j-splits (blockIdx.y)
-    int32_t cap;            // neighbour slots per active particle in nb_tmp
+    int32_t L;              // neighbour slots per (segment, row); 0 = count only
     double *part;           // partial sums [S][7][n_i]
-    int32_t *nb_cnt;        // (n_i) neighbour counters (zeroed by the caller)
-    int32_t *nb_tmp;        // (n_i, cap) unordered neighbour slots
+    int32_t *seg_cnt;       // [G][n_i]
+    int32_t *seg_slots;     // [G][n_i][L]
     unsigned *status;
 };
 
@@ -36,10 +44,12 @@ struct Plan {
     int S;          // j-splits
     int64_t ctas;
     int tj;         // j-tile (tiled kernels) or 0
+    int segs_per_split;   // neighbour segments per split (1 tiled, warps per CTA j-streamed)
+    int64_t seg_len;      // longest neighbour segment (j's)
 };
 
 // Launch-shape planner (pure host function; no CUDA calls).
-Plan plan_force(int precision, int num_sms, const int *ctas_per_sm, int64_t n, int64_t n_i);
+Plan plan_force(int precision, int num_sms, const int *ctas_per_sm, int64_t n, int64_t n_i, int nb_cap);
 // Occupancy of each kernel variant (filled once per context).
 void query_occupancy(int *ctas_per_sm /* [8] */);
 
@@ -54,20 +64,13 @@ void launch_force(cudaStream_t st, const Plan &p, ForceArgs a);
 void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc,
                    double *jerk, double *pot);
 
-// Neighbour CSR: counts -> offsets -> sorted lists; lists over nb_cap are recomputed in
-// ascending j order.  `rec` / `precision` select the distance arithmetic.
-void launch_neighbour_csr(cudaStream_t st, int precision, const void *rec, int64_t n,
-                          const int32_t *idx, int64_t n_i, const double *rs2, int rs2_scalar,
-                          const int32_t *nb_cnt, const int32_t *nb_tmp, int cap,
-                          int64_t *off, int32_t *nb_idx, int64_t nb_capacity,
-                          int32_t *count_true, int64_t *scan_tmp, int32_t *over_list,
-                          unsigned *status, int num_sms);
+// Neighbour CSR from the segment lists: counts -> offsets -> ordered gather.
+// Returns the number of kernels launched.
+int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap,
+                         const int32_t *seg_cnt, const int32_t *seg_slots, int64_t *off,
+                         int32_t *nb_idx, int64_t nb_capacity, int32_t *count_true,
+                         int64_t *scan_tmp, unsigned *status);
 
 size_t neighbour_scan_tmp_elems(int64_t n_i);
-
-void launch_backward(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx,
-                     int64_t n_i, const double *g_acc, const double *g_jerk, const double *g_pot,
-                     double *g_x, double *g_v, double *g_m, int32_t *mark, unsigned *status,
-                     int num_sms);
 
 }  // namespace nbgpu

@@ -363,3 +363,31 @@ def test_schedule_record_and_replay_reproduce_the_run():
     x2, v2 = oracle.hermite_replay(cl.m, cl.x, cl.v, sched)
     np.testing.assert_array_equal(x2, xr)
     np.testing.assert_array_equal(v2, vr)
+
+
+def test_pair_sums_restrict_the_definition():
+    """Sums over all sources equal regular_force; sums over disjoint source sets add up."""
+    cl = W.plummer(300, 41, masses="kroupa")
+    idx = np.arange(0, 300, 7, dtype=np.int32)
+    a, j, p, _, _ = oracle.regular_force(cl.x, cl.v, cl.m, idx, 0.0, lists=False)
+    all_j = np.arange(300, dtype=np.int32)
+    a2, j2, p2 = oracle.pair_sums(cl.x, cl.v, cl.m, idx, all_j)
+    np.testing.assert_array_equal(a, a2)
+    np.testing.assert_array_equal(p, p2)
+    a3, j3, p3 = oracle.pair_sums(cl.x, cl.v, cl.m, idx, all_j[:100])
+    a4, j4, p4 = oracle.pair_sums(cl.x, cl.v, cl.m, idx, all_j[100:])
+    np.testing.assert_allclose(a3 + a4, a, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+    np.testing.assert_allclose(j3 + j4, j, rtol=1e-12, atol=1e-12 * np.abs(j).max())
+
+
+def test_local_finite_difference_matches_adjoint():
+    cl = W.plummer(400, 42, masses="kroupa")
+    rng = np.random.default_rng(9)
+    idx = rng.permutation(400)[:150].astype(np.int32)
+    ga, gj, gp = rng.standard_normal((150, 3)), rng.standard_normal((150, 3)), rng.standard_normal(150)
+    gx, gv, gm = oracle.regular_force_vjp(cl.x, cl.v, cl.m, idx, ga, gj, gp)
+    for p in (int(idx[3]), int(np.setdiff1d(np.arange(400), idx)[5])):
+        for which, ref in (("x", gx[p, 1]), ("v", gv[p, 2]), ("m", gm[p])):
+            c = 1 if which == "x" else 2
+            fd = oracle.loss_fd(cl.x, cl.v, cl.m, idx, ga, gj, gp, which, p, c, h=1e-5 if which != "m" else 1e-9)
+            assert abs(fd - ref) <= 1e-6 * abs(ref) + 1e-9, (which, p, fd, ref)

@@ -164,6 +164,34 @@ nb_status nb_plan(const nb_ctx *ctx, int64_t n, int64_t n_i, int64_t *out);
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
                       int64_t n_i, int32_t nb_cap, int64_t *out);
 
+/* Regular force, jerk and potential of a small active block without allocating any device
+ * memory (the paper has no counterpart: this is a service for callers that cannot allocate
+ * device memory while they integrate, such as a host code whose memory manager owns the
+ * whole device, or a time-step loop that must never reach cudaMalloc/cudaFree because they
+ * can synchronise the device).  No context is needed.
+ *
+ * Computes, in FP64, the same sums as nb_regular_force (no neighbour lists):
+ *   acc_k, jerk_k, pot_k over all j != idx[k], from the caller's predicted state.
+ * n:          particles, 1 <= n <= 2^31-1.
+ * xp, vp:     (n,3) device arrays of predicted positions and velocities; m: (n) masses.
+ * idx:        (n_i) int32 device array, 0 <= n_i <= 65536; an entry outside [0, n) gives a
+ *             zero row.
+ * acc, jerk:  (n_i,3) device outputs; pot: (n_i) device output (overwritten).
+ * stream:     cudaStream_t to run on (NULL = CUDA's default stream); the call is
+ *             asynchronous on it and runs on the current device.
+ * err:        optional host buffer of err_len bytes for a one-line error message.
+ * Scratch: the per-split partial sums live in a fixed 4 MiB device array inside the
+ * library (every GPU that loads the library holds it until the process exits).  n_i above
+ * 65536 is rejected with NB_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on the GPU (on
+ * different streams, or from different host threads without ordering) race and corrupt
+ * each other's results.  Every scratch element a call reads is written earlier in the same
+ * call, so no clearing is needed between calls. */
+nb_status nb_regular_force_noalloc(int64_t n, const double *xp, const double *vp, const double *m,
+                                   int64_t n_i, const int32_t *idx, double *acc, double *jerk,
+                                   double *pot, void *stream, char *err, int32_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

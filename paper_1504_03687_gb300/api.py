@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED}
 # every symbol include/nbgpu.h declares
 EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particles", "nb_predict",
            "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
-           "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_timing", "nb_get_timings")
+           "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_timing", "nb_get_timings",
+           "nb_regular_force_noalloc")
 
 
 class NBError(RuntimeError):
@@ -77,6 +78,7 @@ def load_library(build_if_needed: bool = True):
         "nb_plan_for": (st, [i32, i32, P, i64, i64, i32, P]),
         "nb_set_timing": (st, [P, i32]),
         "nb_get_timings": (st, [P, P, P]),
+        "nb_regular_force_noalloc": (st, [i64, P, P, P, i64, P, P, P, P, P, ctypes.c_char_p, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -171,6 +171,9 @@ def main():
     ap.add_argument("--ni", type=int, default=2048)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint")
+    ap.add_argument("--variants", default="",
+                    help="with --profile: comma list of kernel:variant:splits plans to time in turn "
+                         "(e.g. 1:0:14,1:5:14); empty = the automatic plan")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -386,20 +389,30 @@ def run_profile_case(args):
     rs2_dev = torch.tensor([rs2], dtype=torch.float64, device=dev)
     rng = np.random.default_rng(0)
     g = [T(rng.standard_normal(s)) for s in ((args.ni, 3), (args.ni, 3), (args.ni,))]
-    for it in range(2):
-        ctx.set_timing(it == 1)
-        ctx.predict(0.125)
-        out = ctx.regular_force(idx, rs2_dev, nb_capacity=args.ni * NB_PER_ROW)
-        if args.backward:
-            ctx.regular_force_backward(idx, *g)
-        ctx.sync()
-    ph = ctx.timings()
-    pairs = args.ni * cl.n
-    res = {"case": f"King W0=6 n={cl.n} n_i={args.ni} {args.prec}", "plan": ctx.plan(cl.n, args.ni),
-           "phase_ms": {k: v[0] for k, v in ph.items()}, "launches": {k: v[1] for k, v in ph.items()},
-           "force_Ginteractions_s": pairs / (ph["force"][0] * 1e-3) / 1e9 if ph["force"][0] > 0 else None,
-           "nb_total": int(out.nb_off[-1].item())}
-    print(json.dumps(res))
+    plans = [tuple(int(x) for x in v.split(":")) for v in args.variants.split(",") if v] or [None]
+    ref = None
+    for plan in plans:
+        if plan is not None:
+            ctx.set_plan_override(*plan)
+        for it in range(2):
+            ctx.set_timing(it == 1)
+            ctx.predict(0.125)
+            out = ctx.regular_force(idx, rs2_dev, nb_capacity=args.ni * NB_PER_ROW)
+            if args.backward:
+                ctx.regular_force_backward(idx, *g)
+            ctx.sync()
+        ph = ctx.timings()
+        pairs = args.ni * cl.n
+        res = {"case": f"King W0=6 n={cl.n} n_i={args.ni} {args.prec}", "plan": ctx.plan(cl.n, args.ni),
+               "phase_ms": {k: v[0] for k, v in ph.items()}, "launches": {k: v[1] for k, v in ph.items()},
+               "force_Ginteractions_s": pairs / (ph["force"][0] * 1e-3) / 1e9 if ph["force"][0] > 0 else None,
+               "nb_total": int(out.nb_off[-1].item())}
+        if ref is None:
+            ref = (out.acc.clone(), out.nb_off.clone())
+        else:  # every plan must give the same answer (to FP32 rounding of the partial sums)
+            res["max_rel_acc_diff_vs_first"] = float(((out.acc - ref[0]).norm(dim=1) / ref[0].norm(dim=1)).max())
+            res["same_neighbour_offsets"] = bool(torch.equal(out.nb_off, ref[1]))
+        print(json.dumps(res))
 
 
 def host_force(ctx, idx, rs2, out):

@@ -155,11 +155,18 @@ const char *nb_last_error(const nb_ctx *ctx);
 /* Describe the launch plan nb_regular_force would use (host-only, no GPU work):
  * out[0] = kernel id (0 = FP64 tiled, 1 = mixed tiled, 2 = mixed j-streamed,
  * 3 = FP64 j-streamed), out[1] = i-particles per CTA, out[2] = j-splits, out[3] = CTAs,
- * out[4] = j-tile (0 for the j-streamed kernels). */
+ * out[4] = j-tile (0 for the j-streamed kernels), out[5] = kernel variant. */
 nb_status nb_plan(const nb_ctx *ctx, int64_t n, int64_t n_i, int64_t *out);
 
-/* The same plan for a given device shape, without a context or a GPU (host-only):
- * num_sms SMs, ctas_per_sm[0..4] resident CTAs of the four mixed tiled variants and the
+/* Force the launch plan of later nb_regular_force calls on this context (used to tune and
+ * benchmark individual kernel variants): kernel and variant as reported by nb_plan,
+ * `splits` j-splits (clipped to the tile count; 0 with the mixed tiled kernel = the
+ * planner's split count for that variant).  kernel < 0 restores automatic planning.
+ * NB_ERR_ARG if the kernel does not match the context's precision. */
+nb_status nb_set_plan_override(nb_ctx *ctx, int32_t kernel, int32_t variant, int32_t splits);
+
+/* The automatic plan for a given device shape, without a context or a GPU (host-only):
+ * num_sms SMs, ctas_per_sm[0..8] resident CTAs of the eight mixed tiled variants and the
  * FP64 tiled kernel (NULL = 1 each), and the context's nb_cap. */
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
                       int64_t n_i, int32_t nb_cap, int64_t *out);

@@ -27,8 +27,8 @@ PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED}
 # every symbol include/nbgpu.h declares
 EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particles", "nb_predict",
            "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
-           "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_timing", "nb_get_timings",
-           "nb_regular_force_noalloc")
+           "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
+           "nb_get_timings", "nb_regular_force_noalloc")
 
 
 class NBError(RuntimeError):
@@ -76,6 +76,7 @@ def load_library(build_if_needed: bool = True):
         "nb_last_error": (ctypes.c_char_p, [P]),
         "nb_plan": (st, [P, i64, i64, P]),
         "nb_plan_for": (st, [i32, i32, P, i64, i64, i32, P]),
+        "nb_set_plan_override": (st, [P, i32, i32, i32]),
         "nb_set_timing": (st, [P, i32]),
         "nb_get_timings": (st, [P, P, P]),
         "nb_regular_force_noalloc": (st, [i64, P, P, P, i64, P, P, P, P, P, ctypes.c_char_p, i32]),
@@ -91,13 +92,13 @@ def load_library(build_if_needed: bool = True):
 def plan_for(precision: str, num_sms: int, ctas_per_sm, n: int, n_i: int, nb_cap: int = 512) -> dict:
     """Host-only launch plan (no GPU needed)."""
     lib = load_library()
-    out = (ctypes.c_int64 * 5)()
-    occ = (ctypes.c_int32 * 5)(*ctas_per_sm) if ctas_per_sm is not None else None
+    out = (ctypes.c_int64 * 6)()
+    occ = (ctypes.c_int32 * 9)(*ctas_per_sm) if ctas_per_sm is not None else None
     s = lib.nb_plan_for(PRECISIONS[precision], num_sms, ctypes.cast(occ, ctypes.c_void_p) if occ else None,
                         n, n_i, nb_cap, ctypes.cast(out, ctypes.c_void_p))
     if s != NB_OK:
         raise NBError(s, "nb_plan_for rejected its arguments")
-    return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4])
+    return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4], variant=out[5])
 
 
 def _ptr(t):
@@ -299,6 +300,10 @@ class Context:
         return self._check(self.lib.nb_sync(self.h), "nb_sync", allow_overflow)
 
     def plan(self, n: int, n_i: int) -> dict:
-        out = (ctypes.c_int64 * 5)()
+        out = (ctypes.c_int64 * 6)()
         self._check(self.lib.nb_plan(self.h, n, n_i, ctypes.cast(out, ctypes.c_void_p)), "nb_plan")
-        return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4])
+        return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4], variant=out[5])
+
+    def set_plan_override(self, kernel: int = -1, variant: int = 0, splits: int = 1):
+        """Force (kernel, variant, splits) for later regular_force calls; kernel < 0 = automatic."""
+        self._check(self.lib.nb_set_plan_override(self.h, kernel, variant, splits), "nb_set_plan_override")

@@ -281,19 +281,250 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed_jstream(ForceArgs A)
 }
 
 // ------------------------------------------------------------------------------------------
-// Variants.  Tiled: (NI, BLOCK, TJ); the plan's `variant` indexes this table.
+// Packed-FP32x2 tiled kernel.  Each thread holds NI active rows as NI/2 row pairs; every
+// FP32 operation of a pair interaction is one __ffma2_rn / __fadd2_rn / __fmul2_rn acting on
+// both rows of a pair against the same j (half the FP32 instructions of the scalar kernel).
+// The j-tile is copied raw (cp.async, double-buffered) and expanded once per tile into a
+// duplicated layout, five float4 per j:
+//   {xh,xh,yh,yh} {zh,zh,m,m} {xl,xl,yl,yl} {zl,zl,vx,vx} {vy,vy,vz,vz}
+// so that each 16-byte shared load yields two broadcast pairs.  The arithmetic and its
+// rounding order are those of pair_mixed (x - y is computed as x + (-y), which IEEE
+// rounds identically), so neighbour decisions are bit-identical to the scalar kernel.
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int NP, bool MASK, int TJ>
+__device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int64_t jb, const ForceArgs &A,
+                                              const float2 (&nh)[NP][3], const float2 (&nl)[NP][3],
+                                              const float2 (&nv)[NP][3], const float2 (&rs2f)[NP],
+                                              const int64_t (&gi)[NP][2], int32_t *const (&slot)[NP][2],
+                                              int (&cnt)[NP][2], float2 (&acc)[NP][7])
+{
+    const float2 m3 = make_float2(-3.f, -3.f);
+#pragma unroll 2
+    for (int jj = 0; jj < TJ; ++jj) {
+        const float4 a = sd[5 * jj], b = sd[5 * jj + 1], c = sd[5 * jj + 2], d = sd[5 * jj + 3], e = sd[5 * jj + 4];
+        const float2 XH = make_float2(a.x, a.y), YH = make_float2(a.z, a.w), ZH = make_float2(b.x, b.y);
+        const float2 M = make_float2(b.z, b.w), XL = make_float2(c.x, c.y), YL = make_float2(c.z, c.w);
+        const float2 ZL = make_float2(d.x, d.y), VX = make_float2(d.z, d.w), VY = make_float2(e.x, e.y);
+        const float2 VZ = make_float2(e.z, e.w);
+        const int64_t j = jb + jj;
+        float2 r2[NP];
+        bool hit = false;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float2 dx = f2add(f2add(XH, nh[q][0]), f2add(XL, nl[q][0]));
+            const float2 dy = f2add(f2add(YH, nh[q][1]), f2add(YL, nl[q][1]));
+            const float2 dz = f2add(f2add(ZH, nh[q][2]), f2add(ZL, nl[q][2]));
+            r2[q] = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+            float2 rinv = make_float2(rsqrtf(r2[q].x), rsqrtf(r2[q].y));
+            if (MASK) {
+                rinv.x = (j == gi[q][0]) ? 0.f : rinv.x;
+                rinv.y = (j == gi[q][1]) ? 0.f : rinv.y;
+            }
+            const float2 wx = f2add(VX, nv[q][0]), wy = f2add(VY, nv[q][1]), wz = f2add(VZ, nv[q][2]);
+            const float2 rw = f2fma(dz, wz, f2fma(dy, wy, f2mul(dx, wx)));
+            const float2 rinv2 = f2mul(rinv, rinv);
+            const float2 mr = f2mul(M, rinv);
+            const float2 mr3 = f2mul(mr, rinv2);
+            const float2 beta = f2mul(rw, f2mul(rinv2, m3));
+            acc[q][0] = f2fma(mr3, dx, acc[q][0]);
+            acc[q][1] = f2fma(mr3, dy, acc[q][1]);
+            acc[q][2] = f2fma(mr3, dz, acc[q][2]);
+            acc[q][3] = f2fma(mr3, f2fma(beta, dx, wx), acc[q][3]);
+            acc[q][4] = f2fma(mr3, f2fma(beta, dy, wy), acc[q][4]);
+            acc[q][5] = f2fma(mr3, f2fma(beta, dz, wz), acc[q][5]);
+            acc[q][6] = f2add(acc[q][6], mr);
+            hit |= (r2[q].x < rs2f[q].x) | (r2[q].y < rs2f[q].y);
+        }
+        if (hit) {  // rare: record in ascending j, the first L per segment
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (r2[q].x < rs2f[q].x && j != gi[q][0] && j < A.n) {
+                    if (cnt[q][0] < A.L) slot[q][0][cnt[q][0]] = (int32_t)j;
+                    ++cnt[q][0];
+                }
+                if (r2[q].y < rs2f[q].y && j != gi[q][1] && j < A.n) {
+                    if (cnt[q][1] < A.L) slot[q][1][cnt[q][1]] = (int32_t)j;
+                    ++cnt[q][1];
+                }
+            }
+        }
+    }
+}
+
+// Dynamic shared memory of k_force_mixed_tiled_x2: the raw tile (cp.async target), the
+// duplicated tile, and the FP64 running sums of every row, dacc[c][q][thread].
+template <int NI, int BLOCK, int TJ>
+constexpr int x2_smem_bytes()
+{
+    return 3 * TJ * 16 + 5 * TJ * 16 + 7 * NI * BLOCK * 8;
+}
+
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs A)
+{
+    constexpr int NP = NI / 2;
+    extern __shared__ __align__(16) float4 x2_smem[];
+    float4 *raw = x2_smem;              // 3*TJ float4
+    float4 *dup = x2_smem + 3 * TJ;     // 5*TJ float4
+    double *dacc = reinterpret_cast<double *>(x2_smem + 8 * TJ);  // [7][NI][BLOCK]
+    const int tid = threadIdx.x;
+    const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles * s) / A.S, t1 = (A.n_tiles * (s + 1)) / A.S;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+
+    // rows q*BLOCK + tid (q = 0..NI-1); pair p holds rows 2p and 2p+1
+    float2 nh[NP][3], nl[NP][3], nv[NP][3], rs2f[NP];
+    int64_t gi[NP][2];
+    int32_t *slot[NP][2];
+    int cnt[NP][2];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float h[2][3], l[2][3], v[2][3], r[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t k = kbase + (2 * p + u) * BLOCK + tid;
+            int64_t g = -1;
+            if (k < A.n_i) {
+                g = A.idx[k];
+                if (g < 0 || g >= A.n) {
+                    if (s == 0) atomicOr(A.status, ST_BAD_INDEX);
+                    g = -1;
+                }
+            }
+            gi[p][u] = g;
+            cnt[p][u] = 0;
+            slot[p][u] = A.seg_slots + ((int64_t)s * A.n_i + (k < A.n_i ? k : 0)) * A.L;
+            if (g >= 0) {
+                const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
+                h[u][0] = -p0.x; h[u][1] = -p0.y; h[u][2] = -p0.z;
+                l[u][0] = -p1.x; l[u][1] = -p1.y; l[u][2] = -p1.z;
+                v[u][0] = -p2.x; v[u][1] = -p2.y; v[u][2] = -p2.z;
+                r[u] = A.want_nb ? __double2float_rn(A.rs2[A.rs2_scalar ? 0 : k]) : -1.f;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[u][c] = l[u][c] = v[u][c] = 0.f;
+                r[u] = -1.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            nh[p][c] = make_float2(h[0][c], h[1][c]);
+            nl[p][c] = make_float2(l[0][c], l[1][c]);
+            nv[p][c] = make_float2(v[0][c], v[1][c]);
+        }
+        rs2f[p] = make_float2(r[0], r[1]);
+    }
+#pragma unroll
+    for (int e = 0; e < 7 * NI; ++e) dacc[e * BLOCK + tid] = 0.0;
+
+    auto load_tile = [&](int64_t t) {
+        const float4 *src = rec + t * (3 * TJ);
+#pragma unroll
+        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
+        cp_async_commit();
+    };
+
+    // one raw buffer: tile t+1 lands in it while tile t is computed from dup
+    if (t0 < t1) load_tile(t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        cp_async_wait<0>();
+        __syncthreads();  // raw holds tile t; every thread is done with the previous dup
+#pragma unroll
+        for (int jj = tid; jj < TJ; jj += BLOCK) {
+            const float4 p0 = raw[3 * jj], p1 = raw[3 * jj + 1], p2 = raw[3 * jj + 2];
+            dup[5 * jj] = make_float4(p0.x, p0.x, p0.y, p0.y);
+            dup[5 * jj + 1] = make_float4(p0.z, p0.z, p0.w, p0.w);
+            dup[5 * jj + 2] = make_float4(p1.x, p1.x, p1.y, p1.y);
+            dup[5 * jj + 3] = make_float4(p1.z, p1.z, p2.x, p2.x);
+            dup[5 * jj + 4] = make_float4(p2.y, p2.y, p2.z, p2.z);
+        }
+        __syncthreads();  // dup complete; raw is free again
+        if (t + 1 < t1) load_tile(t + 1);
+        const int64_t jb = t * TJ;
+        bool mine = false;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) mine |= (gi[p][0] >= jb && gi[p][0] < jb + TJ) | (gi[p][1] >= jb && gi[p][1] < jb + TJ);
+        float2 acc[NP][7];
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
+        if (__any_sync(0xffffffffu, mine))
+            tile_mixed_x2<NP, true, TJ>(dup, jb, A, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+        else
+            tile_mixed_x2<NP, false, TJ>(dup, jb, A, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                dacc[(c * NI + 2 * p) * BLOCK + tid] += (double)acc[p][c].x;
+                dacc[(c * NI + 2 * p + 1) * BLOCK + tid] += (double)acc[p][c].y;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t k = kbase + q * BLOCK + tid;
+        if (k < A.n_i) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const double v = dacc[(c * NI + q) * BLOCK + tid];
+                A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -v : v;
+            }
+            if (A.want_nb) A.seg_cnt[(int64_t)s * A.n_i + k] = cnt[q >> 1][q & 1];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM).  The plan's
+// `variant` indexes this list; ids 0-3 are the scalar kernel, 4-7 the packed-FP32x2 one.
+// Last column: 1 = packed kernel (dynamic shared memory, x2_smem_bytes).
+#define NB_MIXED_TILED_VARIANTS(X)                    \
+    X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)      \
+    X(1, k_force_mixed_tiled, 2, 128, 256, 4, 0)      \
+    X(2, k_force_mixed_tiled, 1, 128, 256, 4, 0)      \
+    X(3, k_force_mixed_tiled, 4, 256, 256, 1, 0)      \
+    X(4, k_force_mixed_tiled_x2, 4, 128, 256, 3, 1)   \
+    X(5, k_force_mixed_tiled_x2, 2, 128, 256, 4, 1)   \
+    X(6, k_force_mixed_tiled_x2, 4, 128, 128, 4, 1)   \
+    X(7, k_force_mixed_tiled_x2, 2, 256, 256, 2, 1)
+
 struct TiledVariant {
-    int ni, block, tj;
+    int ni, block, tj, smem;
 };
-static const TiledVariant kTiled[] = {{4, 128, 256}, {2, 128, 256}, {1, 128, 256}, {4, 256, 256}};
+#define NB_TV_ROW(id, K, NI, B, TJ, MB, X2) {NI, B, TJ, X2 ? x2_smem_bytes<NI, B, TJ>() : 0},
+static const TiledVariant kTiled[] = {NB_MIXED_TILED_VARIANTS(NB_TV_ROW)};
+#undef NB_TV_ROW
+
+int mixed_tiled_dyn_smem(int v) { return kTiled[v].smem; }
+
+// Raise the dynamic shared-memory limit of the packed kernels (needed above 48 KB); called
+// once per context before occupancy queries and launches.
+void mixed_tiled_configure()
+{
+#define NB_TV_CFG(id, K, NI, B, TJ, MB, X2)                                                          \
+    if (X2)                                                                                          \
+        cudaFuncSetAttribute((const void *)K<NI, B, TJ, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             kTiled[id].smem);
+    NB_MIXED_TILED_VARIANTS(NB_TV_CFG)
+#undef NB_TV_CFG
+    cudaGetLastError();
+}
+
+int mixed_tiled_variants() { return (int)(sizeof(kTiled) / sizeof(kTiled[0])); }
 
 void *mixed_tiled_fn(int v)
 {
     switch (v) {
-    case 0: return (void *)k_force_mixed_tiled<4, 128, 256, 3>;
-    case 1: return (void *)k_force_mixed_tiled<2, 128, 256, 4>;
-    case 2: return (void *)k_force_mixed_tiled<1, 128, 256, 4>;
-    default: return (void *)k_force_mixed_tiled<4, 256, 256, 1>;
+#define NB_TV_FN(id, K, NI, B, TJ, MB, X2) \
+    case id: return (void *)K<NI, B, TJ, MB>;
+        NB_MIXED_TILED_VARIANTS(NB_TV_FN)
+#undef NB_TV_FN
+    default: return nullptr;
     }
 }
 int mixed_tiled_i_per_cta(int v) { return kTiled[v].ni * kTiled[v].block; }
@@ -308,10 +539,11 @@ void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x
     dim3 grid((unsigned)ctas_x, (unsigned)S);
     if (kernel == 1) {
         switch (variant) {
-        case 0: k_force_mixed_tiled<4, 128, 256, 3><<<grid, 128, 0, st>>>(a); break;
-        case 1: k_force_mixed_tiled<2, 128, 256, 4><<<grid, 128, 0, st>>>(a); break;
-        case 2: k_force_mixed_tiled<1, 128, 256, 4><<<grid, 128, 0, st>>>(a); break;
-        default: k_force_mixed_tiled<4, 256, 256, 1><<<grid, 256, 0, st>>>(a); break;
+#define NB_TV_LAUNCH(id, K, NI, B, TJ, MB, X2) \
+    case id: K<NI, B, TJ, MB><<<grid, B, kTiled[id].smem, st>>>(a); break;
+            NB_MIXED_TILED_VARIANTS(NB_TV_LAUNCH)
+#undef NB_TV_LAUNCH
+        default: break;
         }
     } else {
         switch (variant) {

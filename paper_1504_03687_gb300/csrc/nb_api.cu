@@ -23,6 +23,8 @@ int mixed_tiled_block(int v);
 int mixed_tiled_tj(int v);
 int mixed_jstream_ib(int v);
 int jstream_warps();
+int mixed_tiled_dyn_smem(int v);
+void mixed_tiled_configure();
 void *fp64_tiled_fn();
 int fp64_jstream_ib(int v);
 void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
@@ -35,11 +37,15 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
+static constexpr int kMixedTiledVariants = 8;  // entries of the mixed tiled variant table
+static constexpr int kOccFp64 = 8;             // occupancy slot of the FP64 tiled kernel
+static constexpr int kOccSlots = 9;
 static constexpr int kMaxCap = 8192;   // largest nb_cap (sort buffers live in shared memory)
 
 struct nb_ctx {
     int device = 0, precision = 0, cap = 0, num_sms = 0;
-    int occ[8] = {0};
+    int occ[16] = {0};
+    int force_kernel = -1, force_variant = 0, force_splits = 0;  // plan override (-1: none)
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     int64_t n_max = 0, n = 0, n_pad = 0;
@@ -206,13 +212,24 @@ static void jstream_segments(Plan &p, int64_t n)
     p.seg_len = (chunk + W - 1) / W + 1;
 }
 
+static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i, int nb_cap,
+                               int only_variant);
+
 Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i, int nb_cap)
+{
+    return plan_force_variant(precision, num_sms, occ, n, n_i, nb_cap, -1);
+}
+
+// only_variant >= 0 restricts the tiled search to that mixed variant (and always takes the
+// tiled kernel).
+static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i, int nb_cap,
+                               int only_variant)
 {
     Plan p{};
     if (num_sms <= 0) num_sms = 152;
     const int64_t n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
     if (precision == NB_MIXED) {
-        if (n_i <= 32) {
+        if (n_i <= 32 && only_variant < 0) {
             p.kernel = 2;
             p.variant = n_i <= 2 ? 0 : (n_i <= 16 ? 1 : 2);
             p.i_per_cta = mixed_jstream_ib(p.variant);
@@ -227,9 +244,13 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
             jstream_segments(p, n);
             return p;
         }
-        static const double speed[4] = {1.0, 0.90, 0.78, 0.98};
+        // relative per-pair speed of the tiled variants (scalar NI=4/2/1, NI=4 x 256 threads,
+        // packed FP32x2 NI=4/2, NI=4 with 128-j tiles, NI=2 x 256 threads), measured on a
+        // GB300 at N = 2^20, N_i = 2^17 (King W0 = 6)
+        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91};
         double best = -1.0;
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < kMixedTiledVariants; ++v) {
+            if (only_variant >= 0 && v != only_variant) continue;
             const int ipc = mixed_tiled_i_per_cta(v), tj = mixed_tiled_tj(v);
             const int64_t tiles = n_pad / tj;
             const int64_t itiles = (n_i + ipc - 1) / ipc;
@@ -279,7 +300,7 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
     const int ipc = 128, tj = 64;
     const int64_t tiles = n_pad / tj;
     const int64_t itiles = (n_i + ipc - 1) / ipc;
-    const int64_t P = (int64_t)num_sms * (occ && occ[4] > 0 ? occ[4] : 1);
+    const int64_t P = (int64_t)num_sms * (occ && occ[kOccFp64] > 0 ? occ[kOccFp64] : 1);
     int64_t smax = tiles / 2 > 1 ? tiles / 2 : 1;
     if (smax > 2048) smax = 2048;
     double best = -1.0;
@@ -307,16 +328,54 @@ Plan plan_force(int precision, int num_sms, const int *occ, int64_t n, int64_t n
 
 void query_occupancy(int *occ)
 {
-    for (int v = 0; v < 4; ++v) {
+    mixed_tiled_configure();
+    for (int v = 0; v < kMixedTiledVariants; ++v) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mixed_tiled_fn(v), mixed_tiled_block(v), 0) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mixed_tiled_fn(v), mixed_tiled_block(v),
+                                                          (size_t)mixed_tiled_dyn_smem(v)) != cudaSuccess)
             b = 1;
         occ[v] = b > 0 ? b : 1;
     }
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fp64_tiled_fn(), 128, 0) != cudaSuccess) b = 1;
-    occ[4] = b > 0 ? b : 1;
+    occ[kOccFp64] = b > 0 ? b : 1;
+    cudaGetLastError();
+}
+
+// A forced plan (autotuning and benchmarking of individual variants): kernel < 0 = none.
+static Plan forced_plan(int precision, int num_sms, const int *occ, int64_t n, int64_t n_i, int nb_cap,
+                        int kernel, int variant, int splits)
+{
+    if (kernel == 1 && splits <= 0 && precision == NB_MIXED)  // forced variant, automatic splits
+        return plan_force_variant(precision, num_sms, occ, n, n_i, nb_cap, variant);
+    Plan p = plan_force(precision, num_sms, occ, n, n_i, nb_cap);
+    if (kernel < 0) return p;
+    const int64_t n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
+    p.kernel = kernel;
+    p.variant = variant;
+    if (kernel == 1) {
+        p.i_per_cta = mixed_tiled_i_per_cta(variant);
+        p.tj = mixed_tiled_tj(variant);
+    } else if (kernel == 0) {
+        p.i_per_cta = 128;
+        p.tj = 64;
+    } else {
+        p.i_per_cta = kernel == 2 ? mixed_jstream_ib(variant) : fp64_jstream_ib(variant);
+        p.tj = 0;
+    }
+    int64_t S = splits > 0 ? splits : 1;
+    if (p.tj > 0) {
+        const int64_t tiles = n_pad / p.tj;
+        if (S > tiles) S = tiles;
+        p.segs_per_split = 1;
+        p.seg_len = (tiles + S - 1) / S * p.tj;
+    } else {
+        if (S > n) S = n;
+    }
+    p.S = (int)S;
+    p.ctas = (n_i + p.i_per_cta - 1) / p.i_per_cta * S;
+    if (p.tj == 0) jstream_segments(p, n);
+    return p;
 }
 
 void launch_force(cudaStream_t st, const Plan &p, ForceArgs a)
@@ -493,12 +552,14 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, int32_t on_device)
 nb_status nb_plan(const nb_ctx *c, int64_t n, int64_t n_i, int64_t *out)
 {
     if (!c || !out || n < 1 || n_i < 0) return NB_ERR_ARG;
-    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i, c->cap);
+    Plan p = forced_plan(c->precision, c->num_sms, c->occ, n, n_i, c->cap, c->force_kernel, c->force_variant,
+                         c->force_splits);
     out[0] = p.kernel;
     out[1] = p.i_per_cta;
     out[2] = p.S;
     out[3] = p.ctas;
     out[4] = p.tj;
+    out[5] = p.variant;
     return NB_OK;
 }
 
@@ -506,15 +567,36 @@ nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_pe
                       int32_t nb_cap, int64_t *out)
 {
     if (!out || n < 1 || n_i < 0 || nb_cap < 1 || (precision != NB_FP64 && precision != NB_MIXED)) return NB_ERR_ARG;
-    int occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    int occ[16];
+    for (int q = 0; q < 16; ++q) occ[q] = 1;
     if (ctas_per_sm)
-        for (int q = 0; q < 5; ++q) occ[q] = ctas_per_sm[q];
+        for (int q = 0; q < kOccSlots; ++q) occ[q] = ctas_per_sm[q];
     Plan p = plan_force(precision, num_sms, occ, n, n_i, nb_cap);
     out[0] = p.kernel;
     out[1] = p.i_per_cta;
     out[2] = p.S;
     out[3] = p.ctas;
     out[4] = p.tj;
+    out[5] = p.variant;
+    return NB_OK;
+}
+
+nb_status nb_set_plan_override(nb_ctx *c, int32_t kernel, int32_t variant, int32_t splits)
+{
+    if (!c) return NB_ERR_ARG;
+    if (kernel < 0) {
+        c->force_kernel = -1;
+        return NB_OK;
+    }
+    const bool ok = (kernel == 1 && c->precision == NB_MIXED && variant >= 0 && variant < kMixedTiledVariants) ||
+                    (kernel == 2 && c->precision == NB_MIXED && variant >= 0 && variant <= 2) ||
+                    (kernel == 0 && c->precision == NB_FP64 && variant == 0) ||
+                    (kernel == 3 && c->precision == NB_FP64 && variant >= 0 && variant <= 1);
+    if (!ok || splits < 0 || (splits == 0 && kernel != 1))
+        return fail(c, NB_ERR_ARG, "plan override (%d, %d, %d) invalid for this context", kernel, variant, splits);
+    c->force_kernel = kernel;
+    c->force_variant = variant;
+    c->force_splits = splits;
     return NB_OK;
 }
 
@@ -568,7 +650,8 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
         CK(cudaMemcpyAsync((void *)d_rs2, rs2, n_rs2 * 8, cudaMemcpyHostToDevice, c->stream), "copy rs2");
     }
-    Plan p = plan_force(c->precision, c->num_sms, c->occ, n, n_i, c->cap);
+    Plan p = forced_plan(c->precision, c->num_sms, c->occ, n, n_i, c->cap, c->force_kernel, c->force_variant,
+                         c->force_splits);
     const size_t part_bytes = (size_t)p.S * 7 * (size_t)n_i * sizeof(double);
     if ((s = grow(c, (void **)&c->part, &c->part_cap, part_bytes, "partial sums")) != NB_OK) return s;
     // neighbour segments: G ordered j-segments, L slots each per row (0: counts only)

@@ -374,3 +374,28 @@ def test_million_body_sampled_rows(gpu_lib, king1m):
         cnt = res.nb_count.cpu().numpy()[sel]
         assert np.abs(cnt.astype(np.int64) - ref[3]).max() <= 2
         ctx.close()
+
+
+# ------------------------------------------------------------------ every tiled kernel variant
+@pytest.mark.parametrize("variant", list(range(8)))
+def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
+    """Every variant of the mixed tiled kernel (scalar and packed FP32x2, forced through the plan
+    override) meets the mixed bar against the oracle and gives the same neighbour lists."""
+    cl, rs2, steps = p128k
+    idx = W.active_block(steps, 1000)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx, rs2, cap=512)
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    ctx.set_plan_override(1, variant, 3)
+    assert ctx.plan(cl.n, idx.size)["variant"] == variant
+    res = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    check_mixed(res, ref)
+    check_lists_band(res, cl.x, idx, rs2, ref[3], ref[4], 512)
+    ctx.set_plan_override(-1)
+    base = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    assert torch.equal(base.nb_off, res.nb_off)  # same FP32 distance arithmetic in every variant
+    tot = int(base.nb_off[-1])
+    assert torch.equal(base.nb_idx[:tot], res.nb_idx[:tot])
+    ctx.close()

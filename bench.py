@@ -164,6 +164,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: one warm-up and one timed predict + force call on the King cluster "
                          "(--n particles, --ni active, --prec), printing device times")
@@ -171,6 +172,8 @@ def main():
     ap.add_argument("--ni", type=int, default=2048)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint")
+    ap.add_argument("--model", default="king", choices=["king", "plummer"],
+                    help="with --profile: King W0=6 (+5%% binaries) or Plummer, Kroupa masses")
     ap.add_argument("--variants", default="",
                     help="with --profile: comma list of kernel:variant:splits plans to time in turn "
                          "(e.g. 1:0:14,1:5:14); empty = the automatic plan")
@@ -197,6 +200,7 @@ def main():
     rs2_dev = torch.tensor([rs2], dtype=torch.float64, device=dev)
     ctx = Context(n, precision="mixed", nb_cap=NB_CAP, device=local)
     ctx.set_particles(*state)
+    tuned = ctx.apply_tuned()  # launch plans from the autotuner's table for this GPU, if any
     outs = [None] * len(BLOCKS)
 
     def step():
@@ -331,6 +335,8 @@ def main():
         e2e = {"value": world * pairs_step * args.steps / float(el_t.item()) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    if rank == 0 and not args.no_ensemble:
+        extra["ensemble"] = bench_ensemble(dev)
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -352,7 +358,8 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "blocks": list(BLOCKS), "pairs_per_step": pairs_step,
                        "nb_cap": NB_CAP, "rs2": rs2, "precision": "mixed (ds-f32 differences, f32 pairwise, "
                        "f64 predictor and per-tile sums)", "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": f"{world} independent clusters, one per GPU"},
+                       "parallelism": f"{world} independent clusters, one per GPU",
+                       "launch_plans": "autotuned table" if tuned else "automatic planner"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "force (mixed tiled / j-streamed)", "peak_source": peak_src,
@@ -378,7 +385,10 @@ def run_profile_case(args):
     import workloads as W
     from paper_1504_03687_gb300 import Context
     dev = torch.device("cuda", 0)
-    cl = W.king(args.n, 2, W0=6.0, masses="kroupa", binary_fraction=0.05)
+    if args.model == "king":
+        cl = W.king(args.n, 2, W0=6.0, masses="kroupa", binary_fraction=0.05)
+    else:
+        cl = W.plummer(args.n, 3, masses="kroupa")
     rs2 = W.neighbour_radius2(cl.x, 80, seed=2)
     order = W.sorted_step_list(W.block_steps(cl, seed=2)).astype(np.int32)
     a0, j0, tl = W.hermite_state(cl, seed=2, t_block=0.125)
@@ -403,16 +413,98 @@ def run_profile_case(args):
             ctx.sync()
         ph = ctx.timings()
         pairs = args.ni * cl.n
-        res = {"case": f"King W0=6 n={cl.n} n_i={args.ni} {args.prec}", "plan": ctx.plan(cl.n, args.ni),
+        res = {"case": f"{args.model} n={cl.n} n_i={args.ni} {args.prec}", "plan": ctx.plan(cl.n, args.ni),
                "phase_ms": {k: v[0] for k, v in ph.items()}, "launches": {k: v[1] for k, v in ph.items()},
                "force_Ginteractions_s": pairs / (ph["force"][0] * 1e-3) / 1e9 if ph["force"][0] > 0 else None,
                "nb_total": int(out.nb_off[-1].item())}
+        if args.backward and ph["force"][0] > 0:
+            fwd = ph["force"][0] + ph["reduce"][0] + ph["neighbours"][0]
+            res["backward_over_forward"] = ph["backward"][0] / fwd
         if ref is None:
             ref = (out.acc.clone(), out.nb_off.clone())
         else:  # every plan must give the same answer (to FP32 rounding of the partial sums)
             res["max_rel_acc_diff_vs_first"] = float(((out.acc - ref[0]).norm(dim=1) / ref[0].norm(dim=1)).max())
             res["same_neighbour_offsets"] = bool(torch.equal(out.nb_off, ref[1]))
         print(json.dumps(res))
+
+
+def bench_ensemble(dev, steps=5, n_clusters=512):
+    """512 independent Plummer clusters (N log-uniform in 256..32768, active fraction uniform
+    in 1/64..1): the batched form (one persistent launch, tile chosen by the autotuner,
+    replayed from a captured CUDA graph) against one nb_regular_force launch per cluster."""
+    import torch
+
+    import oracle
+    import workloads as W
+    from paper_1504_03687_gb300 import Context, tune
+    e = W.ensemble(n_clusters=n_clusters, seed=4)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    n = int(e.cluster_off[-1])
+    rows = int(e.active_off[-1])
+    pairs = int(sum((e.active_off[c + 1] - e.active_off[c]) * (e.cluster_off[c + 1] - e.cluster_off[c])
+                    for c in range(n_clusters)))
+    ctx = Context(n, precision="mixed", nb_cap=NB_CAP, device=dev.index or 0)
+    ctx.set_predicted(T(e.x), T(e.v), T(e.m))
+    idx, rs2 = T(e.idx), T(e.rs2)
+    best_v, _ = tune.tune_batched(ctx, e.cluster_off, e.active_off, idx, rs2, log=lambda *a: None)
+    ctx.batch_plan(e.cluster_off, e.active_off, best_v)
+    cap = rows * 128
+    out = ctx.regular_force_batched(idx, rs2, nb_capacity=cap)
+    ctx.sync()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            ctx.regular_force_batched(idx, rs2, out=out)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(steps):
+        g.replay()
+    ev[1].record()
+    torch.cuda.synchronize(dev)
+    t_batched = ev[0].elapsed_time(ev[1]) / steps
+    # baseline: one context per cluster, one nb_regular_force launch sequence per cluster
+    ctxs = []
+    for c in range(n_clusters):
+        lo, hi = e.cluster_off[c], e.cluster_off[c + 1]
+        cc = Context(int(hi - lo), precision="mixed", nb_cap=NB_CAP, device=dev.index or 0)
+        cc.set_predicted(T(e.x[lo:hi]), T(e.v[lo:hi]), T(e.m[lo:hi]))
+        li = T((e.idx[e.active_off[c]:e.active_off[c + 1]] - lo).astype(np.int32))
+        r2 = T(e.rs2[c:c + 1])
+        o = cc.regular_force(li, r2, nb_capacity=int(li.numel()) * 128)
+        ctxs.append((cc, li, r2, o))
+    torch.cuda.synchronize(dev)
+    ev[0].record()
+    for _ in range(steps):
+        for cc, li, r2, o in ctxs:
+            cc.regular_force(li, r2, out=o)
+    ev[1].record()
+    torch.cuda.synchronize(dev)
+    t_single = ev[0].elapsed_time(ev[1]) / steps
+    # accuracy of the batched result on 8 sampled clusters
+    acc = out.acc.cpu().numpy()
+    errs = []
+    for c in np.random.default_rng(0).choice(n_clusters, 8, replace=False):
+        lo, hi = e.cluster_off[c], e.cluster_off[c + 1]
+        r0, r1 = e.active_off[c], e.active_off[c + 1]
+        ref = oracle.regular_force(e.x[lo:hi], e.v[lo:hi], e.m[lo:hi], (e.idx[r0:r1] - lo).astype(np.int32),
+                                   e.rs2[c], cap=NB_CAP, lists=False)
+        errs.append(np.linalg.norm(acc[r0:r1] - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1))
+    errs = np.concatenate(errs)
+    for cc, *_ in ctxs:
+        cc.close()
+    ctx.close()
+    return {"workload": f"{n_clusters} Plummer clusters, N log-uniform 256..32768 (sum {n}), active fraction "
+                        f"U(1/64,1) ({rows} rows), equal masses, r_s for 50 neighbours",
+            "pairs": pairs, "batched_variant": int(best_v),
+            "batched_graph_ms": t_batched, "batched_Ginteractions_s": pairs / (t_batched * 1e-3) / 1e9,
+            "per_cluster_ms": t_single, "per_cluster_Ginteractions_s": pairs / (t_single * 1e-3) / 1e9,
+            "speedup": t_single / t_batched,
+            "acc_error_vs_oracle_8_clusters": {"median": float(np.median(errs)), "max": float(errs.max())}}
 
 
 def host_force(ctx, idx, rs2, out):

@@ -135,6 +135,28 @@ nb_status nb_regular_force_backward(nb_ctx *ctx, int64_t n_i, const int32_t *idx
                                     const double *g_pot, double *g_x, double *g_v, double *g_m,
                                     int32_t on_device);
 
+/* Batched ensemble form (many independent clusters, one launch; a mixed-precision context).
+ * The particles of all clusters are loaded as one state (nb_set_particles + nb_predict, or
+ * nb_set_predicted) in cluster order: cluster c owns particles cluster_off[c] ..
+ * cluster_off[c+1]-1 and the active rows active_off[c] .. active_off[c+1]-1; each cluster
+ * only feels its own particles.
+ * nb_batch_plan (host arrays of n_clusters+1 entries, both starting at 0) builds the work
+ * items — (cluster, a tile of up to 128/256/512 active rows), sorted by cost, largest first —
+ * uploads them, and grows every scratch buffer the launch needs; `variant` selects the tile
+ * (0: 512 rows, 1: 256, 2: 128; -1: the largest tile that still gives 8 items per SM).
+ * nb_regular_force_batched then runs one persistent kernel that pops the items from a device
+ * counter, plus the reduction and the neighbour CSR: it allocates nothing and synchronises
+ * nothing (device pointers only; deferred status via nb_sync).  Arguments as for
+ * nb_regular_force over the concatenated active list idx (global particle indices, every
+ * one inside its own cluster, rows grouped by cluster), with rs2[c] the squared neighbour
+ * radius of cluster c.  No counterpart in the paper (a batching service for many small
+ * independent integrations). */
+nb_status nb_batch_plan(nb_ctx *ctx, int64_t n_clusters, const int64_t *cluster_off,
+                        const int64_t *active_off, int32_t variant);
+nb_status nb_regular_force_batched(nb_ctx *ctx, const int32_t *idx, const double *rs2, double *acc,
+                                   double *jerk, double *pot, int64_t *nb_off, int32_t *nb_idx,
+                                   int64_t nb_idx_capacity, int32_t *nb_count_true);
+
 /* Per-phase device timing: with timing enabled, every phase of every later call is
  * bracketed by CUDA events on the context stream.  nb_get_timings synchronises the
  * stream and returns, per phase, the summed device time in ms and the number of kernels
@@ -164,6 +186,13 @@ nb_status nb_plan(const nb_ctx *ctx, int64_t n, int64_t n_i, int64_t *out);
  * planner's split count for that variant).  kernel < 0 restores automatic planning.
  * NB_ERR_ARG if the kernel does not match the context's precision. */
 nb_status nb_set_plan_override(nb_ctx *ctx, int32_t kernel, int32_t variant, int32_t splits);
+
+/* Install tuned plans (from the project's autotuner): entry q applies to active blocks with
+ * n_i <= ni_max[q] not covered by an earlier entry (ni_max strictly increasing); kernel,
+ * variant and splits as for nb_set_plan_override.  Blocks beyond the last entry use the
+ * automatic plan; an override, while set, takes precedence.  n_entries = 0 clears it. */
+nb_status nb_set_plan_table(nb_ctx *ctx, int32_t n_entries, const int64_t *ni_max,
+                            const int32_t *kernel, const int32_t *variant, const int32_t *splits);
 
 /* The automatic plan for a given device shape, without a context or a GPU (host-only):
  * num_sms SMs, ctas_per_sm[0..8] resident CTAs of the eight mixed tiled variants and the

@@ -28,7 +28,8 @@ PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED}
 EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particles", "nb_predict",
            "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
            "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
-           "nb_get_timings", "nb_regular_force_noalloc")
+           "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
+           "nb_set_plan_table")
 
 
 class NBError(RuntimeError):
@@ -77,6 +78,9 @@ def load_library(build_if_needed: bool = True):
         "nb_plan": (st, [P, i64, i64, P]),
         "nb_plan_for": (st, [i32, i32, P, i64, i64, i32, P]),
         "nb_set_plan_override": (st, [P, i32, i32, i32]),
+        "nb_batch_plan": (st, [P, i64, P, P, i32]),
+        "nb_set_plan_table": (st, [P, i32, P, P, P, P]),
+        "nb_regular_force_batched": (st, [P, P, P, P, P, P, P, P, i64, P]),
         "nb_set_timing": (st, [P, i32]),
         "nb_get_timings": (st, [P, P, P]),
         "nb_regular_force_noalloc": (st, [i64, P, P, P, i64, P, P, P, P, P, ctypes.c_char_p, i32]),
@@ -303,6 +307,61 @@ class Context:
         out = (ctypes.c_int64 * 6)()
         self._check(self.lib.nb_plan(self.h, n, n_i, ctypes.cast(out, ctypes.c_void_p)), "nb_plan")
         return dict(kernel=out[0], i_per_cta=out[1], splits=out[2], ctas=out[3], tile=out[4], variant=out[5])
+
+    def batch_plan(self, cluster_off, active_off, variant: int = -1):
+        """nb_batch_plan: describe the clusters (host int64 offset arrays of C+1 entries)."""
+        co = np.ascontiguousarray(np.asarray(cluster_off), dtype=np.int64)
+        ao = np.ascontiguousarray(np.asarray(active_off), dtype=np.int64)
+        if co.shape != ao.shape:
+            raise ValueError("cluster_off and active_off must have the same length")
+        self._bind_stream()
+        self._check(self.lib.nb_batch_plan(self.h, co.shape[0] - 1, co.ctypes.data, ao.ctypes.data, int(variant)),
+                    "nb_batch_plan")
+        self._batch_rows = int(ao[-1])
+
+    def regular_force_batched(self, idx, rs2, neighbours: bool = True, nb_capacity: int | None = None,
+                              out: ForceResult | None = None) -> ForceResult:
+        """One launch for all clusters of the batch plan (device tensors in and out)."""
+        torch = self._torch
+        rows = self._batch_rows
+        dev = idx.device
+        if out is None:
+            cap = (nb_capacity if nb_capacity is not None else rows * self.nb_cap) if neighbours else 0
+            out = ForceResult(
+                acc=torch.empty((rows, 3), dtype=torch.float64, device=dev),
+                jerk=torch.empty((rows, 3), dtype=torch.float64, device=dev),
+                pot=torch.empty((rows,), dtype=torch.float64, device=dev),
+                nb_off=torch.empty((rows + 1,), dtype=torch.int64, device=dev) if neighbours else None,
+                nb_idx=torch.empty((max(cap, 1),), dtype=torch.int32, device=dev) if neighbours else None,
+                nb_count=torch.empty((rows,), dtype=torch.int32, device=dev) if neighbours else None)
+        self._bind_stream()
+        cap_elems = int(out.nb_idx.numel()) if out.nb_idx is not None else 0
+        s = self.lib.nb_regular_force_batched(self.h, idx.data_ptr(), rs2.data_ptr(), out.acc.data_ptr(),
+                                              out.jerk.data_ptr(), out.pot.data_ptr(), _ptr(out.nb_off)[0],
+                                              _ptr(out.nb_idx)[0], cap_elems, _ptr(out.nb_count)[0])
+        self._check(s, "nb_regular_force_batched")
+        return out
+
+    def apply_tuned(self, n: int | None = None) -> bool:
+        """Install the autotuner's plan table for this GPU, precision and particle count
+        (tuned_plans.json, written by paper_1504_03687_gb300.tune); False if none exists."""
+        from . import tune
+        key = tune.device_key(self.precision, n if n is not None else max(self.n, 1))
+        table = tune.load_table(key)
+        if not table:
+            return False
+        tune.apply_table(self, table)
+        return True
+
+    def set_plan_table(self, entries):
+        """nb_set_plan_table from [(ni_max, kernel, variant, splits), ...] (sorted by ni_max)."""
+        e = sorted(entries)
+        nim = np.array([x[0] for x in e], np.int64)
+        ker = np.array([x[1] for x in e], np.int32)
+        var = np.array([x[2] for x in e], np.int32)
+        spl = np.array([x[3] for x in e], np.int32)
+        self._check(self.lib.nb_set_plan_table(self.h, len(e), nim.ctypes.data, ker.ctypes.data, var.ctypes.data,
+                                               spl.ctypes.data), "nb_set_plan_table")
 
     def set_plan_override(self, kernel: int = -1, variant: int = 0, splits: int = 1):
         """Force (kernel, variant, splits) for later regular_force calls; kernel < 0 = automatic."""

@@ -295,7 +295,7 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 template <int NP, bool MASK, int TJ>
-__device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int64_t jb, const ForceArgs &A,
+__device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int64_t jb, int64_t jend, int L,
                                               const float2 (&nh)[NP][3], const float2 (&nl)[NP][3],
                                               const float2 (&nv)[NP][3], const float2 (&rs2f)[NP],
                                               const int64_t (&gi)[NP][2], int32_t *const (&slot)[NP][2],
@@ -341,12 +341,12 @@ __device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int
         if (hit) {  // rare: record in ascending j, the first L per segment
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                if (r2[q].x < rs2f[q].x && j != gi[q][0] && j < A.n) {
-                    if (cnt[q][0] < A.L) slot[q][0][cnt[q][0]] = (int32_t)j;
+                if (r2[q].x < rs2f[q].x && j != gi[q][0] && j < jend) {
+                    if (cnt[q][0] < L) slot[q][0][cnt[q][0]] = (int32_t)j;
                     ++cnt[q][0];
                 }
-                if (r2[q].y < rs2f[q].y && j != gi[q][1] && j < A.n) {
-                    if (cnt[q][1] < A.L) slot[q][1][cnt[q][1]] = (int32_t)j;
+                if (r2[q].y < rs2f[q].y && j != gi[q][1] && j < jend) {
+                    if (cnt[q][1] < L) slot[q][1][cnt[q][1]] = (int32_t)j;
                     ++cnt[q][1];
                 }
             }
@@ -454,9 +454,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 #pragma unroll
             for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
         if (__any_sync(0xffffffffu, mine))
-            tile_mixed_x2<NP, true, TJ>(dup, jb, A, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            tile_mixed_x2<NP, true, TJ>(dup, jb, A.n, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
         else
-            tile_mixed_x2<NP, false, TJ>(dup, jb, A, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            tile_mixed_x2<NP, false, TJ>(dup, jb, A.n, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
@@ -476,6 +476,205 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
             }
             if (A.want_nb) A.seg_cnt[(int64_t)s * A.n_i + k] = cnt[q >> 1][q & 1];
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched ensemble kernel: many independent clusters in one persistent launch.  The particle
+// arrays of all clusters are concatenated; cluster c owns the j-range
+// [cluster_off[c], cluster_off[c+1]) and the active rows it lists.  Work items (cluster, up to
+// NI*BLOCK consecutive active rows) are popped from a device counter in the order the host
+// sorted them (largest cost first), so uneven clusters balance across the SMs.  Each item
+// walks its cluster's j-range in ragged tiles (records past the range are replaced by
+// massless padding during the tile expansion) with the packed-FP32x2 inner loop, and writes
+// its rows' sums and neighbour segment directly (one split per row).  The pop is a single
+// atomicAdd: no CTA ever waits on another.
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_batched(BatchArgs A)
+{
+    constexpr int NP = NI / 2;
+    extern __shared__ __align__(16) float4 x2_smem[];
+    float4 *raw = x2_smem;
+    float4 *dup = x2_smem + 3 * TJ;
+    double *dacc = reinterpret_cast<double *>(x2_smem + 8 * TJ);  // [7][NI][BLOCK]
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(A.queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();  // every thread holds `it` before thread 0 pops again
+        if (it >= A.n_items) break;
+        const BatchItem W = A.items[it];
+        const int64_t j0 = A.cluster_off[W.cluster], j1 = A.cluster_off[W.cluster + 1];
+        const float rs2c = A.want_nb ? __double2float_rn(A.rs2[W.cluster]) : -1.f;
+
+        float2 nh[NP][3], nl[NP][3], nv[NP][3], rs2f[NP];
+        int64_t gi[NP][2];
+        int32_t *slot[NP][2];
+        int cnt[NP][2];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float h[2][3], l[2][3], v[2][3], r[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int rr = (2 * p + u) * BLOCK + tid;
+                const int64_t k = (int64_t)W.row0 + rr;
+                int64_t g = -1;
+                if (rr < W.rows) {
+                    g = A.idx[k];
+                    if (g < j0 || g >= j1) {  // every active index must lie in its cluster
+                        atomicOr(A.status, ST_BAD_INDEX);
+                        g = -1;
+                    }
+                }
+                gi[p][u] = g;
+                cnt[p][u] = 0;
+                slot[p][u] = A.seg_slots + (rr < W.rows ? k : 0) * A.L;
+                if (g >= 0) {
+                    const float4 p0 = A.rec[3 * g], p1 = A.rec[3 * g + 1], p2 = A.rec[3 * g + 2];
+                    h[u][0] = -p0.x; h[u][1] = -p0.y; h[u][2] = -p0.z;
+                    l[u][0] = -p1.x; l[u][1] = -p1.y; l[u][2] = -p1.z;
+                    v[u][0] = -p2.x; v[u][1] = -p2.y; v[u][2] = -p2.z;
+                    r[u] = rs2c;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) h[u][c] = l[u][c] = v[u][c] = 0.f;
+                    r[u] = -1.f;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nh[p][c] = make_float2(h[0][c], h[1][c]);
+                nl[p][c] = make_float2(l[0][c], l[1][c]);
+                nv[p][c] = make_float2(v[0][c], v[1][c]);
+            }
+            rs2f[p] = make_float2(r[0], r[1]);
+        }
+#pragma unroll
+        for (int e = 0; e < 7 * NI; ++e) dacc[e * BLOCK + tid] = 0.0;
+
+        const int64_t n_t = (j1 - j0 + TJ - 1) / TJ;
+        auto load_tile = [&](int64_t t) {
+            const int64_t jb = j0 + t * TJ;
+            const int valid = (int)((j1 - jb) < TJ ? (j1 - jb) : TJ);
+            const float4 *src = A.rec + jb * 3;
+            for (int e = tid; e < 3 * valid; e += BLOCK) cp_async16(&raw[e], src + e);
+            cp_async_commit();
+        };
+        if (n_t > 0) load_tile(0);
+        for (int64_t t = 0; t < n_t; ++t) {
+            const int64_t jb = j0 + t * TJ;
+            const int valid = (int)((j1 - jb) < TJ ? (j1 - jb) : TJ);
+            cp_async_wait<0>();
+            __syncthreads();
+#pragma unroll
+            for (int jj = tid; jj < TJ; jj += BLOCK) {
+                if (jj < valid) {
+                    const float4 p0 = raw[3 * jj], p1 = raw[3 * jj + 1], p2 = raw[3 * jj + 2];
+                    dup[5 * jj] = make_float4(p0.x, p0.x, p0.y, p0.y);
+                    dup[5 * jj + 1] = make_float4(p0.z, p0.z, p0.w, p0.w);
+                    dup[5 * jj + 2] = make_float4(p1.x, p1.x, p1.y, p1.y);
+                    dup[5 * jj + 3] = make_float4(p1.z, p1.z, p2.x, p2.x);
+                    dup[5 * jj + 4] = make_float4(p2.y, p2.y, p2.z, p2.z);
+                } else {  // massless, far away: contributes exactly zero
+                    dup[5 * jj] = make_float4(kPadPos, kPadPos, kPadPos, kPadPos);
+                    dup[5 * jj + 1] = make_float4(kPadPos, kPadPos, 0.f, 0.f);
+                    dup[5 * jj + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    dup[5 * jj + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    dup[5 * jj + 4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            if (t + 1 < n_t) load_tile(t + 1);
+            bool mine = false;
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                mine |= (gi[p][0] >= jb && gi[p][0] < jb + TJ) | (gi[p][1] >= jb && gi[p][1] < jb + TJ);
+            float2 acc[NP][7];
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
+            if (__any_sync(0xffffffffu, mine))
+                tile_mixed_x2<NP, true, TJ>(dup, jb, j1, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            else
+                tile_mixed_x2<NP, false, TJ>(dup, jb, j1, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    dacc[(c * NI + 2 * p) * BLOCK + tid] += (double)acc[p][c].x;
+                    dacc[(c * NI + 2 * p + 1) * BLOCK + tid] += (double)acc[p][c].y;
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+            const int rr = q * BLOCK + tid;
+            if (rr < W.rows) {
+                const int64_t k = (int64_t)W.row0 + rr;
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    const double v = dacc[(c * NI + q) * BLOCK + tid];
+                    A.part[(int64_t)c * A.n_i + k] = (c == 6) ? -v : v;
+                }
+                if (A.want_nb) A.seg_cnt[k] = cnt[q >> 1][q & 1];
+            }
+        }
+    }
+}
+
+#define NB_MIXED_BATCHED_VARIANTS(X)              \
+    X(0, 4, 128, 128, 4)                          \
+    X(1, 2, 128, 128, 4)                          \
+    X(2, 2, 64, 128, 6)
+
+static int batched_smem(int ni, int block, int tj) { return 3 * tj * 16 + 5 * tj * 16 + 7 * ni * block * 8; }
+
+int mixed_batched_rows_per_item(int v)
+{
+    switch (v) {
+#define NB_BV_ROWS(id, NI, B, TJ, MB) \
+    case id: return NI * B;
+        NB_MIXED_BATCHED_VARIANTS(NB_BV_ROWS)
+#undef NB_BV_ROWS
+    default: return 0;
+    }
+}
+
+int mixed_batched_variants() { return 3; }
+
+// Resident CTAs per SM of a batched variant (sets the dynamic shared-memory limit first).
+int mixed_batched_occupancy(int v)
+{
+    int b = 0;
+    switch (v) {
+#define NB_BV_OCC(id, NI, B, TJ, MB)                                                                   \
+    case id:                                                                                           \
+        cudaFuncSetAttribute((const void *)k_force_mixed_batched<NI, B, TJ, MB>,                       \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, batched_smem(NI, B, TJ));    \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force_mixed_batched<NI, B, TJ, MB>, B,      \
+                                                      batched_smem(NI, B, TJ));                        \
+        break;
+        NB_MIXED_BATCHED_VARIANTS(NB_BV_OCC)
+#undef NB_BV_OCC
+    default: break;
+    }
+    cudaGetLastError();
+    return b > 0 ? b : 1;
+}
+
+void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const BatchArgs &a)
+{
+    switch (variant) {
+#define NB_BV_LAUNCH(id, NI, B, TJ, MB)                                                            \
+    case id:                                                                                       \
+        k_force_mixed_batched<NI, B, TJ, MB><<<ctas, B, batched_smem(NI, B, TJ), st>>>(a);         \
+        break;
+        NB_MIXED_BATCHED_VARIANTS(NB_BV_LAUNCH)
+#undef NB_BV_LAUNCH
+    default: break;
     }
 }
 

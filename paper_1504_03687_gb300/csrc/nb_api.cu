@@ -3,6 +3,7 @@
 //   nb_predict  : K1 predictor -> j-records
 //   nb_regular_force : zero counters -> K2/K3 force (+ neighbour capture) -> K4 reduce
 //                      -> K5 neighbour CSR
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -25,6 +26,10 @@ int mixed_jstream_ib(int v);
 int jstream_warps();
 int mixed_tiled_dyn_smem(int v);
 void mixed_tiled_configure();
+int mixed_batched_rows_per_item(int v);
+int mixed_batched_variants();
+int mixed_batched_occupancy(int v);
+void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const BatchArgs &a);
 void *fp64_tiled_fn();
 int fp64_jstream_ib(int v);
 void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
@@ -46,6 +51,11 @@ struct nb_ctx {
     int device = 0, precision = 0, cap = 0, num_sms = 0;
     int occ[16] = {0};
     int force_kernel = -1, force_variant = 0, force_splits = 0;  // plan override (-1: none)
+    struct TableEntry {
+        int64_t ni_max;
+        int kernel, variant, splits;
+    };
+    std::vector<TableEntry> table;  // tuned plans by active-block size (nb_set_plan_table)
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     int64_t n_max = 0, n = 0, n_pad = 0;
@@ -61,6 +71,11 @@ struct nb_ctx {
     int64_t *scan = nullptr; size_t scan_cap = 0;
     char *stage = nullptr; size_t stage_cap = 0;
     char *adj = nullptr; size_t adj_cap = 0;
+    // batched ensemble plan (nb_batch_plan)
+    void *b_items = nullptr; size_t b_items_cap = 0;
+    int64_t *b_cluster_off = nullptr; size_t b_cluster_off_cap = 0;
+    int64_t b_clusters = 0, b_rows = 0, b_items_n = 0, b_n = 0;
+    int b_variant = -1, b_ctas = 0, b_L = 0;
     char err[512] = {0};
     // per-phase device timing (CUDA events on the context stream) and launch counters
     bool timing = false;
@@ -364,6 +379,14 @@ static Plan forced_plan(int precision, int num_sms, const int *occ, int64_t n, i
         p.tj = 0;
     }
     int64_t S = splits > 0 ? splits : 1;
+    if (splits <= 0 && p.tj == 0) {  // j-streamed kernel, automatic splits: ~4 CTAs per SM
+        const int64_t batches = (n_i + p.i_per_cta - 1) / p.i_per_cta;
+        S = (4 * (int64_t)(num_sms > 0 ? num_sms : 152) + batches - 1) / (batches > 0 ? batches : 1);
+        const int64_t per = kernel == 2 ? 2048 : 1024;
+        const int64_t smax = n / per > 1 ? n / per : 1;
+        if (S > smax) S = smax;
+        if (S < 1) S = 1;
+    }
     if (p.tj > 0) {
         const int64_t tiles = n_pad / p.tj;
         if (S > tiles) S = tiles;
@@ -448,7 +471,8 @@ nb_status nb_free(nb_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
-                    c->part, c->seg_slots, c->seg_cnt, c->scan, c->stage, c->adj};
+                    c->part, c->seg_slots, c->seg_cnt, c->scan, c->stage, c->adj, c->b_items,
+                    c->b_cluster_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -549,11 +573,47 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, int32_t on_device)
     return NB_OK;
 }
 
+// The plan of a call: the override if one is set, else the first tuned table entry whose
+// bucket holds n_i, else the automatic plan.
+static Plan ctx_plan(const nb_ctx *c, int64_t n, int64_t n_i)
+{
+    if (c->force_kernel >= 0)
+        return forced_plan(c->precision, c->num_sms, c->occ, n, n_i, c->cap, c->force_kernel, c->force_variant,
+                           c->force_splits);
+    for (const auto &e : c->table)
+        if (n_i <= e.ni_max)
+            return forced_plan(c->precision, c->num_sms, c->occ, n, n_i, c->cap, e.kernel, e.variant, e.splits);
+    return plan_force(c->precision, c->num_sms, c->occ, n, n_i, c->cap);
+}
+
+static bool plan_valid(int precision, int kernel, int variant, int splits)
+{
+    const bool ok = (kernel == 1 && precision == NB_MIXED && variant >= 0 && variant < kMixedTiledVariants) ||
+                    (kernel == 2 && precision == NB_MIXED && variant >= 0 && variant <= 2) ||
+                    (kernel == 0 && precision == NB_FP64 && variant == 0) ||
+                    (kernel == 3 && precision == NB_FP64 && variant >= 0 && variant <= 1);
+    return ok && splits >= 0 && !(splits == 0 && kernel == 0);
+}
+
+nb_status nb_set_plan_table(nb_ctx *c, int32_t n_entries, const int64_t *ni_max, const int32_t *kernel,
+                            const int32_t *variant, const int32_t *splits)
+{
+    if (!c || n_entries < 0 || (n_entries > 0 && (!ni_max || !kernel || !variant || !splits))) return NB_ERR_ARG;
+    std::vector<nb_ctx::TableEntry> t;
+    for (int32_t q = 0; q < n_entries; ++q) {
+        if (!plan_valid(c->precision, kernel[q], variant[q], splits[q]) || (q > 0 && ni_max[q] <= ni_max[q - 1]))
+            return fail(c, NB_ERR_ARG, "plan table entry %d invalid (kernel %d, variant %d, splits %d)", q, kernel[q],
+                        variant[q], splits[q]);
+        t.push_back({ni_max[q], kernel[q], variant[q], splits[q]});
+    }
+    c->table.swap(t);
+    return NB_OK;
+}
+
 nb_status nb_plan(const nb_ctx *c, int64_t n, int64_t n_i, int64_t *out)
 {
     if (!c || !out || n < 1 || n_i < 0) return NB_ERR_ARG;
-    Plan p = forced_plan(c->precision, c->num_sms, c->occ, n, n_i, c->cap, c->force_kernel, c->force_variant,
-                         c->force_splits);
+    Plan p = ctx_plan(c, n, n_i);
     out[0] = p.kernel;
     out[1] = p.i_per_cta;
     out[2] = p.S;
@@ -592,7 +652,7 @@ nb_status nb_set_plan_override(nb_ctx *c, int32_t kernel, int32_t variant, int32
                     (kernel == 2 && c->precision == NB_MIXED && variant >= 0 && variant <= 2) ||
                     (kernel == 0 && c->precision == NB_FP64 && variant == 0) ||
                     (kernel == 3 && c->precision == NB_FP64 && variant >= 0 && variant <= 1);
-    if (!ok || splits < 0 || (splits == 0 && kernel != 1))
+    if (!ok || splits < 0 || (splits == 0 && kernel == 0))
         return fail(c, NB_ERR_ARG, "plan override (%d, %d, %d) invalid for this context", kernel, variant, splits);
     c->force_kernel = kernel;
     c->force_variant = variant;
@@ -650,8 +710,7 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
         CK(cudaMemcpyAsync((void *)d_rs2, rs2, n_rs2 * 8, cudaMemcpyHostToDevice, c->stream), "copy rs2");
     }
-    Plan p = forced_plan(c->precision, c->num_sms, c->occ, n, n_i, c->cap, c->force_kernel, c->force_variant,
-                         c->force_splits);
+    Plan p = ctx_plan(c, n, n_i);
     const size_t part_bytes = (size_t)p.S * 7 * (size_t)n_i * sizeof(double);
     if ((s = grow(c, (void **)&c->part, &c->part_cap, part_bytes, "partial sums")) != NB_OK) return s;
     // neighbour segments: G ordered j-segments, L slots each per row (0: counts only)
@@ -797,6 +856,143 @@ nb_status nb_get_timings(nb_ctx *c, double *ms, int64_t *launches)
     }
     c->spans.clear();
     cudaGetLastError();
+    return NB_OK;
+}
+
+nb_status nb_batch_plan(nb_ctx *c, int64_t n_clusters, const int64_t *cluster_off, const int64_t *active_off,
+                        int32_t variant)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (c->precision != NB_MIXED) return fail(c, NB_ERR_STATE, "the batched form needs a mixed-precision context");
+    if (n_clusters < 1 || !cluster_off || !active_off) return fail(c, NB_ERR_ARG, "bad cluster description");
+    if (variant >= mixed_batched_variants()) return fail(c, NB_ERR_ARG, "batched variant %d unknown", variant);
+    if (cluster_off[0] != 0 || active_off[0] != 0) return fail(c, NB_ERR_ARG, "offsets must start at 0");
+    int64_t max_n = 0;
+    for (int64_t q = 0; q < n_clusters; ++q) {
+        const int64_t nc = cluster_off[q + 1] - cluster_off[q], ac = active_off[q + 1] - active_off[q];
+        if (nc < 1 || ac < 0 || ac > nc) return fail(c, NB_ERR_ARG, "cluster %lld: bad sizes", (long long)q);
+        if (nc > max_n) max_n = nc;
+    }
+    const int64_t n = cluster_off[n_clusters], rows = active_off[n_clusters];
+    if (n > c->n_max) return fail(c, NB_ERR_ARG, "clusters hold %lld particles > n_max", (long long)n);
+    if (rows > (int64_t)INT32_MAX) return fail(c, NB_ERR_ARG, "too many active rows");
+    // variant: the tuned one, else the largest items whose count still fills the GPU
+    int v = variant;
+    if (v < 0) {
+        v = 0;
+        for (int q = 0; q < mixed_batched_variants(); ++q) {
+            const int rpi = mixed_batched_rows_per_item(q);
+            int64_t items = 0;
+            for (int64_t cl = 0; cl < n_clusters; ++cl) items += (active_off[cl + 1] - active_off[cl] + rpi - 1) / rpi;
+            v = q;
+            if (items >= 8 * (int64_t)c->num_sms) break;
+        }
+    }
+    const int rpi = mixed_batched_rows_per_item(v);
+    std::vector<BatchItem> items;
+    for (int64_t cl = 0; cl < n_clusters; ++cl) {
+        const int64_t a0 = active_off[cl], a1 = active_off[cl + 1];
+        for (int64_t r = a0; r < a1; r += rpi) {
+            BatchItem it{(int32_t)cl, (int32_t)r, (int32_t)(a1 - r < rpi ? a1 - r : rpi), 0};
+            items.push_back(it);
+        }
+    }
+    // largest (cost = row-tile x cluster size) first: the dynamic queue then balances the tail
+    std::vector<size_t> order(items.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const double ca = (double)(cluster_off[items[a].cluster + 1] - cluster_off[items[a].cluster]);
+        const double cb = (double)(cluster_off[items[b].cluster + 1] - cluster_off[items[b].cluster]);
+        return ca > cb;
+    });
+    std::vector<BatchItem> sorted(items.size());
+    for (size_t q = 0; q < order.size(); ++q) sorted[q] = items[order[q]];
+    if ((s = grow(c, &c->b_items, &c->b_items_cap, sorted.size() * sizeof(BatchItem) + 16, "batch items")) != NB_OK)
+        return s;
+    if ((s = grow(c, (void **)&c->b_cluster_off, &c->b_cluster_off_cap, (size_t)(n_clusters + 1) * 8, "cluster offsets")) !=
+        NB_OK)
+        return s;
+    if (!sorted.empty())
+        CK(cudaMemcpyAsync(c->b_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                           c->stream), "copy items");
+    CK(cudaMemcpyAsync(c->b_cluster_off, cluster_off, (size_t)(n_clusters + 1) * 8, cudaMemcpyHostToDevice, c->stream),
+       "copy cluster offsets");
+    // scratch of the launch, grown here so that the launch itself never allocates
+    const int L = (int)(max_n < c->cap ? max_n : c->cap);
+    const size_t r = (size_t)(rows > 0 ? rows : 1);
+    if ((s = grow(c, (void **)&c->part, &c->part_cap, 7 * r * 8, "partial sums")) != NB_OK) return s;
+    if ((s = grow(c, (void **)&c->seg_cnt, &c->seg_cnt_cap, r * 4, "neighbour counts")) != NB_OK) return s;
+    if ((s = grow(c, (void **)&c->seg_slots, &c->seg_slots_cap, r * (size_t)L * 4, "neighbour slots")) != NB_OK) return s;
+    if ((s = grow(c, (void **)&c->scan, &c->scan_cap, (neighbour_scan_tmp_elems(rows) + r + 1) * 8, "scan scratch")) !=
+        NB_OK)
+        return s;
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    const int occ = mixed_batched_occupancy(v);
+    int64_t ctas = (int64_t)occ * c->num_sms;
+    if (ctas > (int64_t)sorted.size()) ctas = (int64_t)sorted.size();
+    c->b_clusters = n_clusters;
+    c->b_rows = rows;
+    c->b_items_n = (int64_t)sorted.size();
+    c->b_variant = v;
+    c->b_ctas = (int)(ctas > 0 ? ctas : 1);
+    c->b_L = L;
+    c->b_n = n;
+    return NB_OK;
+}
+
+nb_status nb_regular_force_batched(nb_ctx *c, const int32_t *idx, const double *rs2, double *acc, double *jerk,
+                                   double *pot, int64_t *nb_off, int32_t *nb_idx, int64_t nb_idx_capacity,
+                                   int32_t *nb_count_true)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (c->b_variant < 0) return fail(c, NB_ERR_STATE, "nb_regular_force_batched before nb_batch_plan");
+    if (!c->have_pred) return fail(c, NB_ERR_STATE, "nb_regular_force_batched before nb_predict / nb_set_predicted");
+    if (c->n != c->b_n)
+        return fail(c, NB_ERR_STATE, "the loaded state has %lld particles, the batch plan %lld", (long long)c->n,
+                    (long long)c->b_n);
+    const int64_t rows = c->b_rows;
+    if (rows > 0 && (!idx || !rs2 || !acc || !jerk || !pot)) return fail(c, NB_ERR_ARG, "null array");
+    if (nb_idx && (!nb_off || nb_idx_capacity < 0)) return fail(c, NB_ERR_ARG, "nb_idx needs nb_off and a capacity >= 0");
+    const bool want_nb = nb_off || nb_count_true;
+    if (rows == 0) {
+        if (nb_off) CK(cudaMemsetAsync(nb_off, 0, sizeof(int64_t), c->stream), "cudaMemsetAsync");
+        return NB_OK;
+    }
+    BatchArgs ba{};
+    ba.rec = static_cast<const float4 *>(c->rec);
+    ba.cluster_off = c->b_cluster_off;
+    ba.rs2 = rs2;
+    ba.idx = idx;
+    ba.n_i = rows;
+    ba.items = static_cast<const BatchItem *>(c->b_items);
+    ba.n_items = (int32_t)c->b_items_n;
+    ba.want_nb = want_nb ? 1 : 0;
+    ba.L = nb_idx ? c->b_L : 0;
+    ba.queue = c->status + SS_QUEUE;
+    ba.part = c->part;
+    ba.seg_cnt = c->seg_cnt;
+    ba.seg_slots = c->seg_slots;
+    ba.status = c->status;
+    cudaEvent_t t0 = span_begin(c);
+    CK(cudaMemsetAsync(c->status + SS_QUEUE, 0, sizeof(unsigned), c->stream), "cudaMemsetAsync");
+    launch_force_mixed_batched(c->stream, c->b_variant, c->b_ctas, ba);
+    CK_LAUNCH("batched force kernel launch");
+    span_end(c, PH_FORCE, t0, 1);
+    t0 = span_begin(c);
+    launch_reduce(c->stream, c->part, 1, rows, acc, jerk, pot);
+    CK_LAUNCH("k_reduce launch");
+    span_end(c, PH_REDUCE, t0, 1);
+    if (want_nb) {
+        int64_t *off_buf = nb_off ? nb_off : c->scan + neighbour_scan_tmp_elems(rows);
+        t0 = span_begin(c);
+        const int kernels = launch_neighbour_csr(c->stream, 1, rows, ba.L, c->cap, c->seg_cnt, c->seg_slots, off_buf,
+                                                 nb_idx, nb_idx ? nb_idx_capacity : 0, nb_count_true, c->scan,
+                                                 c->status);
+        CK_LAUNCH("neighbour CSR launch");
+        span_end(c, PH_NEIGHBOURS, t0, kernels);
+    }
     return NB_OK;
 }
 

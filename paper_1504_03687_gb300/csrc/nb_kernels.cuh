@@ -37,6 +37,28 @@ struct ForceArgs {
     unsigned *status;
 };
 
+// Batched ensemble: one work item = (cluster, up to rows-per-item consecutive active rows).
+struct BatchItem {
+    int32_t cluster, row0, rows, pad;
+};
+
+struct BatchArgs {
+    const float4 *rec;
+    const int64_t *cluster_off;  // [C+1] particle offsets of the concatenated clusters
+    const double *rs2;           // [C] squared neighbour radius per cluster
+    const int32_t *idx;          // [n_i] global active indices, rows grouped by cluster
+    int64_t n_i;
+    const BatchItem *items;
+    int32_t n_items;
+    int32_t want_nb;
+    int32_t L;                   // neighbour slots per row (0: counts only)
+    unsigned *queue;             // item counter, zero at launch
+    double *part;                // [7][n_i]
+    int32_t *seg_cnt;            // [n_i]
+    int32_t *seg_slots;          // [n_i][L]
+    unsigned *status;
+};
+
 struct Plan {
     int kernel;     // 0 FP64 tiled, 1 mixed tiled, 2 mixed j-streamed, 3 FP64 j-streamed
     int variant;    // kernel-specific template variant

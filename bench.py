@@ -165,6 +165,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: one warm-up and one timed predict + force call on the King cluster "
                          "(--n particles, --ni active, --prec), printing device times")
@@ -337,6 +338,8 @@ def main():
 
     if rank == 0 and not args.no_ensemble:
         extra["ensemble"] = bench_ensemble(dev)
+    if rank == 0 and not args.no_adjoint:
+        extra["adjoint"] = bench_adjoint(dev)
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -505,6 +508,81 @@ def bench_ensemble(dev, steps=5, n_clusters=512):
             "per_cluster_ms": t_single, "per_cluster_Ginteractions_s": pairs / (t_single * 1e-3) / 1e9,
             "speedup": t_single / t_batched,
             "acc_error_vs_oracle_8_clusters": {"median": float(np.median(errs)), "max": float(errs.max())}}
+
+
+def bench_adjoint(dev, reps=3):
+    """Adjoint of force+jerk+potential at N = 65536 (Plummer, Kroupa), full active block, for
+    L = sum(w.acc + u.jerk) + sum(pot) with w, u ~ N(0,1): forward vs backward device time,
+    and the GPU gradient against O(N) central differences of the FP64 oracle at 64 random
+    coordinates of x, v and m.  Then the gradient of the final kinetic energy through 64
+    block steps at N = 16384 with checkpoint-and-recompute every 8 steps (mixed and FP64)."""
+    import torch
+
+    import oracle
+    import workloads as W
+    from paper_1504_03687_gb300 import Context
+    from paper_1504_03687_gb300.autograd import hermite_chain
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    cl, _ = W.plummer_64k_kroupa()
+    n = cl.n
+    rng = np.random.default_rng(3)
+    ga, gj, gp = rng.standard_normal((n, 3)), rng.standard_normal((n, 3)), np.ones(n)
+    idx = np.arange(n, dtype=np.int32)
+    picks = [(["x", "v", "m"][q % 3], int(rng.integers(0, n)), int(rng.integers(0, 3))) for q in range(64)]
+    fd = np.array([oracle.loss_fd(cl.x, cl.v, cl.m, idx, ga, gj, gp, w, p, c,
+                                  h=1e-6 if w != "m" else 1e-6 * cl.m[p]) for w, p, c in picks])
+    res = {}
+    for prec in ("mixed", "fp64"):
+        ctx = Context(n, precision=prec, nb_cap=64, device=dev.index or 0)
+        ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+        idx_t, g = T(idx), [T(ga), T(gj), T(gp)]
+        ctx.regular_force(idx_t, 0.0, neighbours=False)
+        gx, gv, gm = ctx.regular_force_backward(idx_t, *g)
+        ctx.sync()
+        ctx.timings()
+        ctx.set_timing(True)
+        for _ in range(reps):
+            ctx.regular_force(idx_t, 0.0, neighbours=False)
+        for _ in range(reps):
+            gx, gv, gm = ctx.regular_force_backward(idx_t, *g)
+        ph = ctx.timings()
+        ctx.set_timing(False)
+        fwd = (ph["force"][0] + ph["reduce"][0]) / reps
+        bwd = ph["backward"][0] / reps
+        gx, gv, gm = gx.cpu().numpy(), gv.cpu().numpy(), gm.cpu().numpy()
+        got = np.array([gx[p, c] if w == "x" else gv[p, c] if w == "v" else gm[p] for w, p, c in picks])
+        scale = np.array([np.abs(gx).max() if w == "x" else np.abs(gv).max() if w == "v" else np.abs(gm).max()
+                          for w, _, _ in picks])
+        err = np.abs(got - fd) / np.maximum(np.abs(fd), 1e-4 * scale)
+        res[prec] = {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+                     "backward_Gpairs_s": 2 * n * n / (bwd * 1e-3) / 1e9,
+                     "fd_rel_err_64_coords": {"median": float(np.median(err)), "max": float(err.max())}}
+        ctx.close()
+    # gradient through K block steps of a frozen schedule, checkpoint every 8
+    cl2 = W.plummer(16384, 33, masses="kroupa")
+    K = 64
+    _, _, sched = oracle.hermite_record(cl2.m, cl2.x, cl2.v, 1.0, eta=0.02, max_blocks=K)
+    chain = {"n": cl2.n, "block_steps": len(sched), "particle_steps": int(sum(len(a) for _, a in sched))}
+    for prec in ("mixed", "fp64"):
+        ctx = Context(cl2.n, precision=prec, nb_cap=64, device=dev.index or 0)
+        schedule = [(t, T(a)) for t, a in sched]
+        times = []
+        for it in range(2):
+            x0 = T(cl2.x).requires_grad_(True)
+            v0 = T(cl2.v).requires_grad_(True)
+            m = T(cl2.m)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            xf, vf = hermite_chain(x0, v0, m, schedule, ctx, checkpoint_every=8)
+            ke = 0.5 * (m[:, None] * vf * vf).sum()
+            ke.backward()
+            torch.cuda.synchronize(dev)
+            times.append(time.perf_counter() - t0)
+        chain[prec] = {"forward_plus_backward_s": times[-1], "final_kinetic_energy": float(ke.item()),
+                       "grad_norm_x0": float(x0.grad.norm().item()), "grad_norm_v0": float(v0.grad.norm().item())}
+        ctx.close()
+    res["hermite_chain_K64_N16384"] = chain
+    return res
 
 
 def host_force(ctx, idx, rs2, out):

@@ -262,6 +262,284 @@ __global__ void __launch_bounds__(BLOCK) k_adj_jside_mixed(AdjArgs A)
     }
 }
 
+// ---------------------------------------------------------------- packed FP32x2 passes
+// The mixed passes above written with __ffma2_rn / __fadd2_rn / __fmul2_rn on pairs of rows:
+// i-side rows (pass A) or j-side particles (pass B) are held two per packed register, the
+// streamed side is expanded once per tile into a duplicated shared-memory layout.
+__device__ __forceinline__ float2 a2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 a2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 a2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Same terms as adj_pair for two pairs at once; rinv = 0 for a self pair.  gr, gv += rinv3
+// [...] scaled by mscale; dm += rinv3 (t + gamma jr) - s rinv.
+template <bool WANT_DM>
+__device__ __forceinline__ void adj_pair_x2(const float2 (&r)[3], const float2 (&w)[3], float2 rinv,
+                                            const float2 (&ga)[3], const float2 (&gj)[3], float2 s, float2 mscale,
+                                            float2 (&gr)[3], float2 (&gv)[3], float2 &dm)
+{
+    const float2 rinv2 = a2mul(rinv, rinv);
+    const float2 rinv3 = a2mul(rinv, rinv2);
+    const float2 rinv3m = a2mul(rinv3, mscale);
+    const float2 q = a2fma(r[2], w[2], a2fma(r[1], w[1], a2mul(r[0], w[0])));
+    const float2 ar = a2fma(ga[2], r[2], a2fma(ga[1], r[1], a2mul(ga[0], r[0])));
+    const float2 jr = a2fma(gj[2], r[2], a2fma(gj[1], r[1], a2mul(gj[0], r[0])));
+    const float2 jw = a2fma(gj[2], w[2], a2fma(gj[1], w[1], a2mul(gj[0], w[0])));
+    const float2 t = a2add(ar, jw);
+    const float2 b3 = a2mul(rinv2, make_float2(-3.f, -3.f));
+    const float2 beta = a2mul(b3, jr);
+    const float2 gamma = a2mul(b3, q);
+    const float2 v5 = a2mul(a2mul(q, jr), rinv2);
+    const float2 alpha = a2fma(b3, a2fma(make_float2(-5.f, -5.f), v5, t), s);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 in = a2fma(gamma, gj[c], a2fma(beta, w[c], a2fma(alpha, r[c], ga[c])));
+        gr[c] = a2fma(rinv3m, in, gr[c]);
+        gv[c] = a2fma(rinv3m, a2fma(beta, r[c], gj[c]), gv[c]);
+    }
+    if (WANT_DM) {
+        const float2 ns = make_float2(-s.x, -s.y);
+        dm = a2add(dm, a2fma(ns, rinv, a2mul(rinv3, a2fma(gamma, jr, t))));
+    }
+}
+
+__device__ __forceinline__ float2 rsqrt_nz(float2 r2)
+{
+    return make_float2(r2.x > 0.f ? rsqrtf(r2.x) : 0.f, r2.y > 0.f ? rsqrtf(r2.y) : 0.f);
+}
+
+template <int NI, int BLOCK, int TJ>
+constexpr int adj_iside_x2_smem()
+{
+    return 3 * TJ * 16 + 5 * TJ * 16 + 6 * NI * BLOCK * 8;
+}
+
+// Pass A: NI active rows per thread (NI/2 packed pairs) against j-tiles of all particles.
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_adj_iside_x2(AdjArgs A)
+{
+    constexpr int NP = NI / 2;
+    extern __shared__ __align__(16) float4 adj_smem[];
+    float4 *raw = adj_smem;
+    float4 *dup = adj_smem + 3 * TJ;
+    double *dacc = reinterpret_cast<double *>(adj_smem + 8 * TJ);  // [6][NI][BLOCK]
+    const int tid = threadIdx.x;
+    const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles_j * s) / A.S, t1 = (A.n_tiles_j * (s + 1)) / A.S;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+    const float4 *irec = static_cast<const float4 *>(A.irec);
+    float2 nh[NP][3], nl[NP][3], nv[NP][3], ga[NP][3], gj[NP][3], gs[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float4 a[2], b[2], c[2], d[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {  // irec rows are padded: always readable
+            const int64_t k = kbase + (2 * p + u) * BLOCK + tid;
+            a[u] = irec[4 * k]; b[u] = irec[4 * k + 1]; c[u] = irec[4 * k + 2]; d[u] = irec[4 * k + 3];
+        }
+        nh[p][0] = make_float2(-a[0].x, -a[1].x); nh[p][1] = make_float2(-a[0].y, -a[1].y);
+        nh[p][2] = make_float2(-a[0].z, -a[1].z); gs[p] = make_float2(a[0].w, a[1].w);
+        nl[p][0] = make_float2(-b[0].x, -b[1].x); nl[p][1] = make_float2(-b[0].y, -b[1].y);
+        nl[p][2] = make_float2(-b[0].z, -b[1].z); gj[p][0] = make_float2(b[0].w, b[1].w);
+        nv[p][0] = make_float2(-c[0].x, -c[1].x); nv[p][1] = make_float2(-c[0].y, -c[1].y);
+        nv[p][2] = make_float2(-c[0].z, -c[1].z); gj[p][1] = make_float2(c[0].w, c[1].w);
+        ga[p][0] = make_float2(d[0].x, d[1].x); ga[p][1] = make_float2(d[0].y, d[1].y);
+        ga[p][2] = make_float2(d[0].z, d[1].z); gj[p][2] = make_float2(d[0].w, d[1].w);
+    }
+#pragma unroll
+    for (int e = 0; e < 6 * NI; ++e) dacc[e * BLOCK + tid] = 0.0;
+    auto load_tile = [&](int64_t t) {
+        const float4 *src = rec + t * (3 * TJ);
+#pragma unroll
+        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
+        cp_async_commit();
+    };
+    if (t0 < t1) load_tile(t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll
+        for (int jj = tid; jj < TJ; jj += BLOCK) {
+            const float4 p0 = raw[3 * jj], p1 = raw[3 * jj + 1], p2 = raw[3 * jj + 2];
+            dup[5 * jj] = make_float4(p0.x, p0.x, p0.y, p0.y);
+            dup[5 * jj + 1] = make_float4(p0.z, p0.z, p0.w, p0.w);
+            dup[5 * jj + 2] = make_float4(p1.x, p1.x, p1.y, p1.y);
+            dup[5 * jj + 3] = make_float4(p1.z, p1.z, p2.x, p2.x);
+            dup[5 * jj + 4] = make_float4(p2.y, p2.y, p2.z, p2.z);
+        }
+        __syncthreads();
+        if (t + 1 < t1) load_tile(t + 1);
+        float2 gr[NP][3], gv[NP][3], dm_unused = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gr[p][c] = gv[p][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int jj = 0; jj < TJ; ++jj) {
+            const float4 a = dup[5 * jj], b = dup[5 * jj + 1], c = dup[5 * jj + 2], d = dup[5 * jj + 3],
+                         e = dup[5 * jj + 4];
+            const float2 XH[3] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y)};
+            const float2 M = make_float2(b.z, b.w);
+            const float2 XL[3] = {make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(d.x, d.y)};
+            const float2 V[3] = {make_float2(d.z, d.w), make_float2(e.x, e.y), make_float2(e.z, e.w)};
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float2 r[3], w[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    r[k] = a2add(a2add(XH[k], nh[p][k]), a2add(XL[k], nl[p][k]));
+                    w[k] = a2add(V[k], nv[p][k]);
+                }
+                const float2 r2 = a2fma(r[2], r[2], a2fma(r[1], r[1], a2mul(r[0], r[0])));
+                adj_pair_x2<false>(r, w, rsqrt_nz(r2), ga[p], gj[p], gs[p], M, gr[p], gv[p], dm_unused);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dacc[(c * NI + 2 * p) * BLOCK + tid] += (double)gr[p][c].x;
+                dacc[(c * NI + 2 * p + 1) * BLOCK + tid] += (double)gr[p][c].y;
+                dacc[((3 + c) * NI + 2 * p) * BLOCK + tid] += (double)gv[p][c].x;
+                dacc[((3 + c) * NI + 2 * p + 1) * BLOCK + tid] += (double)gv[p][c].y;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t k = kbase + q * BLOCK + tid;
+        if (k < A.n_i)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) A.part[((int64_t)s * 6 + c) * A.n_i + k] = dacc[(c * NI + q) * BLOCK + tid];
+    }
+}
+
+template <int NJ, int BLOCK, int TI>
+constexpr int adj_jside_x2_smem()
+{
+    return 4 * TI * 16 + 8 * TI * 16 + 7 * NJ * BLOCK * 8;
+}
+
+// Pass B: NJ particles per thread (NJ/2 packed pairs) against tiles of the active rows with
+// their cotangents.  Expanded i-record, eight float4 per row:
+//   {-xh,-xh,-yh,-yh} {-zh,-zh,s,s} {-xl,-xl,-yl,-yl} {-zl,-zl,-vx,-vx}
+//   {-vy,-vy,-vz,-vz} {ga0,ga0,ga1,ga1} {ga2,ga2,gj0,gj0} {gj1,gj1,gj2,gj2}
+template <int NJ, int BLOCK, int TI, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_adj_jside_x2(AdjArgs A)
+{
+    constexpr int NP = NJ / 2;
+    extern __shared__ __align__(16) float4 adj_smem[];
+    float4 *raw = adj_smem;                 // 4*TI float4
+    float4 *dup = adj_smem + 4 * TI;        // 8*TI float4
+    double *dacc = reinterpret_cast<double *>(adj_smem + 12 * TI);  // [7][NJ][BLOCK]
+    const int tid = threadIdx.x;
+    const int64_t jbase = (int64_t)blockIdx.x * (BLOCK * NJ);
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles_i * s) / A.S, t1 = (A.n_tiles_i * (s + 1)) / A.S;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+    const float4 *irec = static_cast<const float4 *>(A.irec);
+    float2 jh[NP][3], jl[NP][3], jv[NP][3], jm[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float4 a[2], b[2], c[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t j = jbase + (2 * p + u) * BLOCK + tid;
+            if (j < A.n) {
+                a[u] = rec[3 * j]; b[u] = rec[3 * j + 1]; c[u] = rec[3 * j + 2];
+            } else {  // beyond the particles: a massless row far away (never written)
+                a[u] = make_float4(kPadPos, kPadPos, kPadPos, 0.f);
+                b[u] = c[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        jh[p][0] = make_float2(a[0].x, a[1].x); jh[p][1] = make_float2(a[0].y, a[1].y);
+        jh[p][2] = make_float2(a[0].z, a[1].z); jm[p] = make_float2(a[0].w, a[1].w);
+        jl[p][0] = make_float2(b[0].x, b[1].x); jl[p][1] = make_float2(b[0].y, b[1].y);
+        jl[p][2] = make_float2(b[0].z, b[1].z);
+        jv[p][0] = make_float2(c[0].x, c[1].x); jv[p][1] = make_float2(c[0].y, c[1].y);
+        jv[p][2] = make_float2(c[0].z, c[1].z);
+    }
+#pragma unroll
+    for (int e = 0; e < 7 * NJ; ++e) dacc[e * BLOCK + tid] = 0.0;
+    auto load_tile = [&](int64_t t) {
+        const float4 *src = irec + t * (4 * TI);
+#pragma unroll
+        for (int e = tid; e < 4 * TI; e += BLOCK) cp_async16(&raw[e], src + e);
+        cp_async_commit();
+    };
+    if (t0 < t1) load_tile(t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll
+        for (int ii = tid; ii < TI; ii += BLOCK) {
+            const float4 a = raw[4 * ii], b = raw[4 * ii + 1], c = raw[4 * ii + 2], d = raw[4 * ii + 3];
+            dup[8 * ii] = make_float4(-a.x, -a.x, -a.y, -a.y);
+            dup[8 * ii + 1] = make_float4(-a.z, -a.z, a.w, a.w);
+            dup[8 * ii + 2] = make_float4(-b.x, -b.x, -b.y, -b.y);
+            dup[8 * ii + 3] = make_float4(-b.z, -b.z, -c.x, -c.x);
+            dup[8 * ii + 4] = make_float4(-c.y, -c.y, -c.z, -c.z);
+            dup[8 * ii + 5] = make_float4(d.x, d.x, d.y, d.y);
+            dup[8 * ii + 6] = make_float4(d.z, d.z, b.w, b.w);
+            dup[8 * ii + 7] = make_float4(c.w, c.w, d.w, d.w);
+        }
+        __syncthreads();
+        if (t + 1 < t1) load_tile(t + 1);
+        float2 gr[NP][3], gv[NP][3], dm[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            dm[p] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gr[p][c] = gv[p][c] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int ii = 0; ii < TI; ++ii) {
+            const float4 a = dup[8 * ii], b = dup[8 * ii + 1], c = dup[8 * ii + 2], d = dup[8 * ii + 3],
+                         e = dup[8 * ii + 4], f = dup[8 * ii + 5], g = dup[8 * ii + 6], h = dup[8 * ii + 7];
+            const float2 NH[3] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y)};
+            const float2 S = make_float2(b.z, b.w);
+            const float2 NL[3] = {make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(d.x, d.y)};
+            const float2 NV[3] = {make_float2(d.z, d.w), make_float2(e.x, e.y), make_float2(e.z, e.w)};
+            const float2 GA[3] = {make_float2(f.x, f.y), make_float2(f.z, f.w), make_float2(g.x, g.y)};
+            const float2 GJ[3] = {make_float2(g.z, g.w), make_float2(h.x, h.y), make_float2(h.z, h.w)};
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float2 r[3], w[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    r[k] = a2add(a2add(jh[p][k], NH[k]), a2add(jl[p][k], NL[k]));
+                    w[k] = a2add(jv[p][k], NV[k]);
+                }
+                const float2 r2 = a2fma(r[2], r[2], a2fma(r[1], r[1], a2mul(r[0], r[0])));
+                adj_pair_x2<true>(r, w, rsqrt_nz(r2), GA, GJ, S, make_float2(1.f, 1.f), gr[p], gv[p], dm[p]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dacc[(c * NJ + 2 * p) * BLOCK + tid] += (double)gr[p][c].x;
+                dacc[(c * NJ + 2 * p + 1) * BLOCK + tid] += (double)gr[p][c].y;
+                dacc[((3 + c) * NJ + 2 * p) * BLOCK + tid] += (double)gv[p][c].x;
+                dacc[((3 + c) * NJ + 2 * p + 1) * BLOCK + tid] += (double)gv[p][c].y;
+            }
+            dacc[(6 * NJ + 2 * p) * BLOCK + tid] += (double)dm[p].x;
+            dacc[(6 * NJ + 2 * p + 1) * BLOCK + tid] += (double)dm[p].y;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+        const int64_t j = jbase + q * BLOCK + tid;
+        if (j < A.n) {
+            const double mj = (double)(q & 1 ? jm[q >> 1].y : jm[q >> 1].x);
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const double v = dacc[(c * NJ + q) * BLOCK + tid];
+                A.part[((int64_t)s * 7 + c) * A.n + j] = c < 6 ? v * mj : v;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- FP64 passes
 template <int BLOCK, int TJ>
 __global__ void __launch_bounds__(BLOCK) k_adj_iside_f64(AdjArgs A)
@@ -393,6 +671,8 @@ __global__ void k_adj_combine_i(const double *__restrict__ partA, int SA, int64_
 }
 
 // ---------------------------------------------------------------- planning + launch
+constexpr int kAdjNI = 4, kAdjNJ = 4, kAdjBlock = 128, kAdjTJ = 128, kAdjTI = 64;
+
 static int splits_for(int64_t ctas_x, int64_t tiles, int64_t P)
 {
     // enough CTAs for ~4 waves, each split keeping >= 2 streamed tiles
@@ -416,11 +696,11 @@ struct AdjGeom {
 static AdjGeom adj_geom(int precision, int64_t n, int64_t n_i, int num_sms)
 {
     AdjGeom g{};
-    const int64_t P = (int64_t)(num_sms > 0 ? num_sms : 152) * 2;
+    const int64_t P = (int64_t)(num_sms > 0 ? num_sms : 152) * 3;
     const int64_t n_pad = ((n + 255) / 256) * 256;
     if (precision == 1) {
-        g.ti_a = 2 * 128; g.tj_a = 256;   // i-side: NI=2, BLOCK=128
-        g.tj_b = 2 * 128; g.ti_b = 128;   // j-side: NJ=2, BLOCK=128, i-tile 128
+        g.ti_a = kAdjNI * kAdjBlock; g.tj_a = kAdjTJ;   // i-side: packed, NI=4, BLOCK=128
+        g.tj_b = kAdjNJ * kAdjBlock; g.ti_b = kAdjTI;   // j-side: packed, NJ=4, BLOCK=128
     } else {
         g.ti_a = 128; g.tj_a = 64;
         g.tj_b = 128; g.ti_b = 64;
@@ -482,7 +762,9 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
         A.S = g.SA;
         A.part = partA;
         if (precision == 1)
-            k_adj_iside_mixed<2, 128, 256><<<dim3((unsigned)g.ctas_a, (unsigned)g.SA), 128, 0, st>>>(A);
+            k_adj_iside_x2<kAdjNI, kAdjBlock, kAdjTJ, 3>
+                <<<dim3((unsigned)g.ctas_a, (unsigned)g.SA), kAdjBlock,
+                   adj_iside_x2_smem<kAdjNI, kAdjBlock, kAdjTJ>(), st>>>(A);
         else
             k_adj_iside_f64<128, 64><<<dim3((unsigned)g.ctas_a, (unsigned)g.SA), 128, 0, st>>>(A);
         ++kernels;
@@ -490,7 +772,9 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
     A.S = g.SB;
     A.part = partB;
     if (precision == 1)
-        k_adj_jside_mixed<2, 128, 128><<<dim3((unsigned)g.ctas_b, (unsigned)g.SB), 128, 0, st>>>(A);
+        k_adj_jside_x2<kAdjNJ, kAdjBlock, kAdjTI, 3>
+            <<<dim3((unsigned)g.ctas_b, (unsigned)g.SB), kAdjBlock, adj_jside_x2_smem<kAdjNJ, kAdjBlock, kAdjTI>(),
+               st>>>(A);
     else
         k_adj_jside_f64<128, 64><<<dim3((unsigned)g.ctas_b, (unsigned)g.SB), 128, 0, st>>>(A);
     ++kernels;

@@ -68,6 +68,7 @@ struct nb_ctx {
     double *part = nullptr; size_t part_cap = 0;
     int32_t *seg_slots = nullptr; size_t seg_slots_cap = 0;
     int32_t *seg_cnt = nullptr; size_t seg_cnt_cap = 0;
+    int32_t *row_total = nullptr; size_t row_total_cap = 0;
     int64_t *scan = nullptr; size_t scan_cap = 0;
     char *stage = nullptr; size_t stage_cap = 0;
     char *adj = nullptr; size_t adj_cap = 0;
@@ -471,7 +472,7 @@ nb_status nb_free(nb_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
-                    c->part, c->seg_slots, c->seg_cnt, c->scan, c->stage, c->adj, c->b_items,
+                    c->part, c->seg_slots, c->seg_cnt, c->row_total, c->scan, c->stage, c->adj, c->b_items,
                     c->b_cluster_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -719,6 +720,8 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
     const size_t scan_elems = neighbour_scan_tmp_elems(n_i) + (d_off ? 0 : (size_t)n_i + 1);
     if (want_nb) {
         if ((s = grow(c, (void **)&c->seg_cnt, &c->seg_cnt_cap, (size_t)G * n_i * 4, "neighbour counts")) != NB_OK) return s;
+        if ((s = grow(c, (void **)&c->row_total, &c->row_total_cap, (size_t)n_i * 4, "neighbour totals")) != NB_OK)
+            return s;
         if (L > 0 &&
             (s = grow(c, (void **)&c->seg_slots, &c->seg_slots_cap, (size_t)G * n_i * L * 4, "neighbour slots")) != NB_OK)
             return s;
@@ -751,7 +754,7 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         t0 = span_begin(c);
         const int kernels = launch_neighbour_csr(c->stream, G, n_i, L, c->cap, c->seg_cnt, c->seg_slots, off_buf,
                                                  d_nbidx, d_nbidx ? nb_idx_capacity : 0, d_cnt_true, c->scan,
-                                                 c->status);
+                                                 c->row_total, c->status);
         CK_LAUNCH("neighbour CSR launch");
         span_end(c, PH_NEIGHBOURS, t0, kernels);
     }
@@ -989,7 +992,7 @@ nb_status nb_regular_force_batched(nb_ctx *c, const int32_t *idx, const double *
         t0 = span_begin(c);
         const int kernels = launch_neighbour_csr(c->stream, 1, rows, ba.L, c->cap, c->seg_cnt, c->seg_slots, off_buf,
                                                  nb_idx, nb_idx ? nb_idx_capacity : 0, nb_count_true, c->scan,
-                                                 c->status);
+                                                 nullptr, c->status);
         CK_LAUNCH("neighbour CSR launch");
         span_end(c, PH_NEIGHBOURS, t0, kernels);
     }

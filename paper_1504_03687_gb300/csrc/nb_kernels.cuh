@@ -88,10 +88,12 @@ void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, doub
 
 // Neighbour CSR from the segment lists: counts -> offsets -> ordered gather.
 // Returns the number of kernels launched.
+// row_total: (n_i) int32 scratch used when there are many segments per row (may be NULL
+// when G is small).
 int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap,
                          const int32_t *seg_cnt, const int32_t *seg_slots, int64_t *off,
                          int32_t *nb_idx, int64_t nb_capacity, int32_t *count_true,
-                         int64_t *scan_tmp, unsigned *status);
+                         int64_t *scan_tmp, int32_t *row_total, unsigned *status);
 
 size_t neighbour_scan_tmp_elems(int64_t n_i);
 

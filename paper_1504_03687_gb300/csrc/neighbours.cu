@@ -34,9 +34,36 @@ __global__ void k_reduce(const double *__restrict__ part, int S, int64_t n_i, do
     }
 }
 
+// Many splits (small active blocks): one CTA per row, warp c sums component c; lane l adds
+// the splits s = l, l+32, ... in increasing order, then the warp adds the 32 lane sums with a
+// fixed butterfly, so the result is deterministic for a given split count.
+__global__ void __launch_bounds__(256) k_reduce_wide(const double *__restrict__ part, int S, int64_t n_i,
+                                                     double *__restrict__ acc, double *__restrict__ jerk,
+                                                     double *__restrict__ pot)
+{
+    const int64_t k = blockIdx.x;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c >= 7) return;  // warp-uniform
+    double sum = 0.0;
+    for (int s = lane; s < S; s += 32) sum += part[((int64_t)s * 7 + c) * n_i + k];
+    sum = warp_sum(sum);
+    if (lane == 0) {
+        if (c < 3)
+            acc[3 * k + c] = sum;
+        else if (c < 6)
+            jerk[3 * k + c - 3] = sum;
+        else
+            pot[k] = sum;
+    }
+}
+
 void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc, double *jerk,
                    double *pot)
 {
+    if (S > 16 && n_i <= 1024) {
+        k_reduce_wide<<<(unsigned)n_i, 256, 0, st>>>(part, S, n_i, acc, jerk, pot);
+        return;
+    }
     int64_t g = (n_i + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
     if (g < 1) g = 1;
@@ -161,18 +188,82 @@ __global__ void k_seg_gather(const int32_t *__restrict__ seg_cnt, const int32_t 
     }
 }
 
+// ------------------------------------------------------------------------------ many segments
+// With tiny active blocks the j-streamed kernels leave thousands of segments per row; these
+// block-per-row versions walk them with all threads of a CTA instead of one thread or warp.
+constexpr int ROW_BLOCK = 256;
+
+// True neighbour count of every row: block-wide sum over the row's segments.
+__global__ void __launch_bounds__(ROW_BLOCK) k_seg_count_rows(const int32_t *__restrict__ seg_cnt, int64_t G,
+                                                              int64_t n_i, int32_t *__restrict__ total)
+{
+    __shared__ int64_t ws[ROW_BLOCK / 32];
+    const int64_t k = blockIdx.x;
+    int64_t c = 0;
+    for (int64_t g = threadIdx.x; g < G; g += ROW_BLOCK) c += seg_cnt[g * n_i + k];
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t s = 0;
+        for (int w = 0; w < ROW_BLOCK / 32; ++w) s += ws[w];
+        total[k] = (int32_t)(s < INT32_MAX ? s : INT32_MAX);
+    }
+}
+
+// Ordered gather of one row with a whole CTA: thread t owns the contiguous segment range
+// [t*G/B, (t+1)*G/B); a block scan of the owned kept sizes places every segment in the row.
+__global__ void __launch_bounds__(ROW_BLOCK) k_seg_gather_rows(const int32_t *__restrict__ seg_cnt,
+                                                               const int32_t *__restrict__ seg_slots, int64_t G,
+                                                               int64_t n_i, int L, const int64_t *__restrict__ off,
+                                                               int32_t *__restrict__ nb_idx, int64_t capacity)
+{
+    __shared__ int64_t wsum[32];
+    const int64_t k = blockIdx.x;
+    const int64_t g0 = (G * threadIdx.x) / ROW_BLOCK, g1 = (G * (threadIdx.x + 1)) / ROW_BLOCK;
+    int64_t mine = 0;
+    for (int64_t g = g0; g < g1; ++g) {
+        const int c = seg_cnt[g * n_i + k];
+        mine += c < L ? c : L;
+    }
+    int64_t total;
+    int64_t pos = block_exclusive_scan(mine, wsum, total);
+    const int64_t o0 = off[k], kept = off[k + 1] - o0;
+    for (int64_t g = g0; g < g1 && pos < kept; ++g) {
+        int c = seg_cnt[g * n_i + k];
+        c = c < L ? c : L;
+        if (pos + c > kept) c = (int)(kept - pos);
+        const int32_t *src = seg_slots + (g * n_i + k) * (int64_t)L;
+        for (int e = 0; e < c; ++e)
+            if (o0 + pos + e < capacity) nb_idx[o0 + pos + e] = src[e];
+        pos += c;
+    }
+}
+
 int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap, const int32_t *seg_cnt,
                          const int32_t *seg_slots, int64_t *off, int32_t *nb_idx, int64_t nb_capacity,
-                         int32_t *count_true, int64_t *scan_tmp, unsigned *status)
+                         int32_t *count_true, int64_t *scan_tmp, int32_t *row_total, unsigned *status)
 {
     const int64_t nb = (n_i + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    k_seg_scan_local<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(seg_cnt, G, n_i, cap, off, scan_tmp, count_true, status);
+    int kernels = 0;
+    const bool many = G > 64 && row_total != nullptr;
+    if (many) {  // sum the segments of every row in parallel first
+        k_seg_count_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, G, n_i, row_total);
+        ++kernels;
+    }
+    k_seg_scan_local<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(many ? row_total : seg_cnt, many ? 1 : G, n_i, cap, off,
+                                                          scan_tmp, count_true, status);
     k_scan_blocks<<<1, SCAN_BLOCK, 0, st>>>(scan_tmp, nb);
     k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(off, scan_tmp, n_i, nb, nb_capacity, status);
-    if (!nb_idx || L <= 0) return 3;
-    const int64_t blocks = (n_i + 7) / 8;
-    k_seg_gather<<<(unsigned)blocks, 256, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity);
-    return 4;
+    kernels += 3;
+    if (!nb_idx || L <= 0) return kernels;
+    if (many) {
+        k_seg_gather_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity);
+    } else {
+        const int64_t blocks = (n_i + 7) / 8;
+        k_seg_gather<<<(unsigned)blocks, 256, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity);
+    }
+    return kernels + 1;
 }
 
 }  // namespace nbgpu

@@ -107,7 +107,9 @@ def make_ctx(n, prec, cap=512):
 
 # ------------------------------------------------------------------ predictor
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_predictor_bit_identical(gpu_lib, prec):
+def test_predictor_within_rounding(gpu_lib, prec):
+    """The GPU predictor (Horner, FMA) agrees with the oracle's term-by-term Taylor sum to
+    within 4 ulp of the sum of the magnitudes of its terms."""
     cl, _ = W.plummer_1k_equal()
     steps = W.block_steps(cl, seed=0)
     a0, j0, tl = W.hermite_state(cl, seed=1, t_block=0.5, steps=steps)
@@ -116,8 +118,13 @@ def test_predictor_bit_identical(gpu_lib, prec):
     ctx.predict(0.5)
     xp, vp = ctx.get_predicted()
     rx, rv = oracle.predict(0.5, cl.x, cl.v, a0, j0, tl)
-    np.testing.assert_array_equal(xp.cpu().numpy(), rx)
-    np.testing.assert_array_equal(vp.cpu().numpy(), rv)
+    dt = (0.5 - tl)[:, None]
+    eps = np.finfo(float).eps
+    bx = np.abs(cl.x) + np.abs(cl.v * dt) + np.abs(a0 * dt ** 2 / 2) + np.abs(j0 * dt ** 3 / 6)
+    bv = np.abs(cl.v) + np.abs(a0 * dt) + np.abs(j0 * dt ** 2 / 2)
+    assert np.all(np.abs(xp.cpu().numpy() - rx) <= 4 * eps * bx)
+    assert np.all(np.abs(vp.cpu().numpy() - rv) <= 4 * eps * bv)
+    assert (xp.cpu().numpy() != rx).mean() < 0.5  # mostly bit-identical anyway
 
 
 # ------------------------------------------------------------------ Plummer 1024, full block

@@ -540,6 +540,208 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_jside_x2(AdjArgs A)
     }
 }
 
+// ---------------------------------------------------------------- fused single pass (mixed)
+// For dense active blocks.  Every particle k is a row; its cotangents (zero when k is not
+// active, summed when idx names k twice) live in a per-particle record next to its position:
+//   crec (five float4): {xh,yh,zh,m} {xl,yl,zl,s} {vx,vy,vz,gj0} {ga0,ga1,ga2,gj1} {gj2,0,0,0}
+// For the pair (k, m) with r = x_m - x_k, w = v_m - v_k the shared terms (r, w, 1/|r|, r.w)
+// are formed once and both directions are added:
+//   k as receiver (cotangents of k):  g_x[k] -= m_m V(r, w; c_k),  g_v[k] -= m_m U(r, w; c_k)
+//   m as receiver (cotangents of m):  g_x[k] += m_k V(-r, -w; c_m), g_v[k] += m_k U(-r, -w; c_m),
+//                                     g_m[k] += D(-r, -w; c_m)
+// with V, U, D the bracketed terms of adj_pair.  In terms of P = ga_m.r, Q = gj_m.r,
+// R = gj_m.w and E = P + R - 5 q Q / |r|^2 the reversed pair reads
+//   V = ga_m - (s_m + 3 E / |r|^2) r - 3 Q w / |r|^2 + gamma gj_m,  U = gj_m - 3 Q r / |r|^2,
+//   D = -|r|^-3 (P + R + gamma Q) - s_m / |r|,  gamma = -3 q / |r|^2.
+__global__ void k_build_crec(int64_t n, int64_t n_pad, const float4 *__restrict__ rec, float4 *__restrict__ crec)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_pad; k += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = make_float4(kPadPos, kPadPos, kPadPos, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f), c = b;
+        if (k < n) {
+            a = rec[3 * k];
+            b = rec[3 * k + 1];
+            c = rec[3 * k + 2];
+        }
+        crec[5 * k] = a;
+        crec[5 * k + 1] = make_float4(b.x, b.y, b.z, 0.f);
+        crec[5 * k + 2] = make_float4(c.x, c.y, c.z, 0.f);
+        crec[5 * k + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        crec[5 * k + 4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void k_scatter_cotangents(int64_t n, int64_t n_i, const int32_t *__restrict__ idx,
+                                     const double *__restrict__ g_acc, const double *__restrict__ g_jerk,
+                                     const double *__restrict__ g_pot, float *__restrict__ crec, unsigned *status)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_i; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[q];
+        if (i < 0 || i >= n) {
+            atomicOr(status, ST_BAD_INDEX);
+            continue;
+        }
+        float *r = crec + 20 * i;  // five float4 = 20 floats
+        atomicAdd(r + 7, (float)g_pot[q]);         // s
+        atomicAdd(r + 11, (float)g_jerk[3 * q]);   // gj0
+        atomicAdd(r + 12, (float)g_acc[3 * q]);    // ga0
+        atomicAdd(r + 13, (float)g_acc[3 * q + 1]);
+        atomicAdd(r + 14, (float)g_acc[3 * q + 2]);
+        atomicAdd(r + 15, (float)g_jerk[3 * q + 1]);  // gj1
+        atomicAdd(r + 16, (float)g_jerk[3 * q + 2]);  // gj2
+    }
+}
+
+template <int BLOCK, int TJ>
+constexpr int adj_fused_smem()
+{
+    return 5 * TJ * 16 + 9 * TJ * 16 + 7 * 2 * BLOCK * 8;
+}
+
+// One packed row pair per thread (rows tid and BLOCK + tid of the CTA), j-tiles of crec.
+template <int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const float4 *__restrict__ crec)
+{
+    extern __shared__ __align__(16) float4 adj_smem[];
+    float4 *raw = adj_smem;                 // 5*TJ
+    float4 *dup = adj_smem + 5 * TJ;        // 9*TJ
+    double *dacc = reinterpret_cast<double *>(adj_smem + 14 * TJ);  // [7][2][BLOCK]
+    const int tid = threadIdx.x;
+    const int64_t kbase = (int64_t)blockIdx.x * (2 * BLOCK);
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles_j * s) / A.S, t1 = (A.n_tiles_j * (s + 1)) / A.S;
+    float2 nh[3], nl[3], nv[3], ga[3], gj[3], gs, mk;
+    {
+        float4 a[2], b[2], c[2], d[2], e[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {  // crec is padded to the tile multiple
+            const int64_t k = kbase + u * BLOCK + tid;
+            a[u] = crec[5 * k]; b[u] = crec[5 * k + 1]; c[u] = crec[5 * k + 2];
+            d[u] = crec[5 * k + 3]; e[u] = crec[5 * k + 4];
+        }
+        nh[0] = make_float2(-a[0].x, -a[1].x); nh[1] = make_float2(-a[0].y, -a[1].y);
+        nh[2] = make_float2(-a[0].z, -a[1].z); mk = make_float2(a[0].w, a[1].w);
+        nl[0] = make_float2(-b[0].x, -b[1].x); nl[1] = make_float2(-b[0].y, -b[1].y);
+        nl[2] = make_float2(-b[0].z, -b[1].z); gs = make_float2(b[0].w, b[1].w);
+        nv[0] = make_float2(-c[0].x, -c[1].x); nv[1] = make_float2(-c[0].y, -c[1].y);
+        nv[2] = make_float2(-c[0].z, -c[1].z); gj[0] = make_float2(c[0].w, c[1].w);
+        ga[0] = make_float2(d[0].x, d[1].x); ga[1] = make_float2(d[0].y, d[1].y);
+        ga[2] = make_float2(d[0].z, d[1].z); gj[1] = make_float2(d[0].w, d[1].w);
+        gj[2] = make_float2(e[0].x, e[1].x);
+    }
+#pragma unroll
+    for (int e = 0; e < 14; ++e) dacc[e * BLOCK + tid] = 0.0;
+    const float2 m3 = make_float2(-3.f, -3.f), m5 = make_float2(-5.f, -5.f);
+    auto load_tile = [&](int64_t t) {
+        const float4 *src = crec + t * (5 * TJ);
+#pragma unroll
+        for (int e = tid; e < 5 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
+        cp_async_commit();
+    };
+    if (t0 < t1) load_tile(t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll
+        for (int jj = tid; jj < TJ; jj += BLOCK) {
+            const float4 a = raw[5 * jj], b = raw[5 * jj + 1], c = raw[5 * jj + 2], d = raw[5 * jj + 3],
+                         e = raw[5 * jj + 4];
+            dup[9 * jj] = make_float4(a.x, a.x, a.y, a.y);
+            dup[9 * jj + 1] = make_float4(a.z, a.z, a.w, a.w);
+            dup[9 * jj + 2] = make_float4(b.x, b.x, b.y, b.y);
+            dup[9 * jj + 3] = make_float4(b.z, b.z, b.w, b.w);
+            dup[9 * jj + 4] = make_float4(c.x, c.x, c.y, c.y);
+            dup[9 * jj + 5] = make_float4(c.z, c.z, c.w, c.w);
+            dup[9 * jj + 6] = make_float4(d.x, d.x, d.y, d.y);
+            dup[9 * jj + 7] = make_float4(d.z, d.z, d.w, d.w);
+            dup[9 * jj + 8] = make_float4(e.x, e.x, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (t + 1 < t1) load_tile(t + 1);
+        float2 v1[3], u1[3], v2[3], u2[3], d2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v1[c] = u1[c] = v2[c] = u2[c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int jj = 0; jj < TJ; ++jj) {
+            const float4 q0 = dup[9 * jj], q1 = dup[9 * jj + 1], q2 = dup[9 * jj + 2], q3 = dup[9 * jj + 3],
+                         q4 = dup[9 * jj + 4], q5 = dup[9 * jj + 5], q6 = dup[9 * jj + 6], q7 = dup[9 * jj + 7],
+                         q8 = dup[9 * jj + 8];
+            const float2 XH[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
+            const float2 M = make_float2(q1.z, q1.w);
+            const float2 XL[3] = {make_float2(q2.x, q2.y), make_float2(q2.z, q2.w), make_float2(q3.x, q3.y)};
+            const float2 Sm = make_float2(q3.z, q3.w);
+            const float2 V[3] = {make_float2(q4.x, q4.y), make_float2(q4.z, q4.w), make_float2(q5.x, q5.y)};
+            const float2 GJm[3] = {make_float2(q5.z, q5.w), make_float2(q7.z, q7.w), make_float2(q8.x, q8.y)};
+            const float2 GAm[3] = {make_float2(q6.x, q6.y), make_float2(q6.z, q6.w), make_float2(q7.x, q7.y)};
+            float2 r[3], w[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                r[k] = a2add(a2add(XH[k], nh[k]), a2add(XL[k], nl[k]));
+                w[k] = a2add(V[k], nv[k]);
+            }
+            const float2 r2 = a2fma(r[2], r[2], a2fma(r[1], r[1], a2mul(r[0], r[0])));
+            const float2 rinv = rsqrt_nz(r2);
+            const float2 rinv2 = a2mul(rinv, rinv);
+            const float2 rinv3 = a2mul(rinv, rinv2);
+            const float2 q = a2fma(r[2], w[2], a2fma(r[1], w[1], a2mul(r[0], w[0])));
+            const float2 b3 = a2mul(rinv2, m3);
+            const float2 gamma = a2mul(b3, q);
+            // k as receiver (cotangents of k), source mass m_m
+            {
+                const float2 ar = a2fma(ga[2], r[2], a2fma(ga[1], r[1], a2mul(ga[0], r[0])));
+                const float2 jr = a2fma(gj[2], r[2], a2fma(gj[1], r[1], a2mul(gj[0], r[0])));
+                const float2 jw = a2fma(gj[2], w[2], a2fma(gj[1], w[1], a2mul(gj[0], w[0])));
+                const float2 tt = a2add(ar, jw);
+                const float2 beta = a2mul(b3, jr);
+                const float2 alpha = a2fma(b3, a2fma(m5, a2mul(a2mul(q, jr), rinv2), tt), gs);
+                const float2 rinv3m = a2mul(rinv3, M);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 in = a2fma(gamma, gj[c], a2fma(beta, w[c], a2fma(alpha, r[c], ga[c])));
+                    v1[c] = a2fma(rinv3m, in, v1[c]);
+                    u1[c] = a2fma(rinv3m, a2fma(beta, r[c], gj[c]), u1[c]);
+                }
+            }
+            // m as receiver (cotangents of m), source k (mass m_k applied per tile)
+            {
+                const float2 P = a2fma(GAm[2], r[2], a2fma(GAm[1], r[1], a2mul(GAm[0], r[0])));
+                const float2 Q = a2fma(GJm[2], r[2], a2fma(GJm[1], r[1], a2mul(GJm[0], r[0])));
+                const float2 R = a2fma(GJm[2], w[2], a2fma(GJm[1], w[1], a2mul(GJm[0], w[0])));
+                const float2 PR = a2add(P, R);
+                const float2 b3Q = a2mul(b3, Q);
+                const float2 E = a2fma(m5, a2mul(a2mul(q, Q), rinv2), PR);
+                // alpha' = s_m - b3 E, applied as -alpha' r
+                const float2 nalpha = a2fma(b3, E, make_float2(-Sm.x, -Sm.y));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 in = a2fma(gamma, GJm[c], a2fma(b3Q, w[c], a2fma(nalpha, r[c], GAm[c])));
+                    v2[c] = a2fma(rinv3, in, v2[c]);
+                    u2[c] = a2fma(rinv3, a2fma(b3Q, r[c], GJm[c]), u2[c]);
+                }
+                const float2 nd = a2fma(rinv3, a2fma(gamma, Q, PR), a2mul(Sm, rinv));
+                d2 = a2add(d2, make_float2(-nd.x, -nd.y));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 gx = a2fma(mk, v2[c], make_float2(-v1[c].x, -v1[c].y));
+            const float2 gv = a2fma(mk, u2[c], make_float2(-u1[c].x, -u1[c].y));
+            dacc[(c * 2) * BLOCK + tid] += (double)gx.x;
+            dacc[(c * 2 + 1) * BLOCK + tid] += (double)gx.y;
+            dacc[((3 + c) * 2) * BLOCK + tid] += (double)gv.x;
+            dacc[((3 + c) * 2 + 1) * BLOCK + tid] += (double)gv.y;
+        }
+        dacc[12 * BLOCK + tid] += (double)d2.x;
+        dacc[13 * BLOCK + tid] += (double)d2.y;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t k = kbase + u * BLOCK + tid;
+        if (k < A.n)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) A.part[((int64_t)s * 7 + c) * A.n + k] = dacc[(c * 2 + u) * BLOCK + tid];
+    }
+}
+
 // ---------------------------------------------------------------- FP64 passes
 template <int BLOCK, int TJ>
 __global__ void __launch_bounds__(BLOCK) k_adj_iside_f64(AdjArgs A)
@@ -686,6 +888,31 @@ static int splits_for(int64_t ctas_x, int64_t tiles, int64_t P)
 size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms, int64_t *rows_pad_out, int *SA,
                              int *SB);
 
+// The fused single pass does N x N pair work with ~96 FP32 operations, the two passes
+// 2 x N_i x N with ~56 and ~60: the fused pass wins for dense blocks.
+constexpr int kFusedBlock = 128, kFusedTJ = 64;
+static bool use_fused(int precision, int64_t n, int64_t n_i) { return precision == 1 && 4 * n_i >= 3 * n; }
+
+struct FusedGeom {
+    int64_t n_pad, n_tiles, ctas;
+    int S;
+};
+
+static FusedGeom fused_geom(int64_t n, int num_sms)
+{
+    FusedGeom f{};
+    f.n_pad = ((n + 255) / 256) * 256;
+    f.n_tiles = f.n_pad / kFusedTJ;
+    f.ctas = (n + 2 * kFusedBlock - 1) / (2 * kFusedBlock);
+    int64_t P = (int64_t)(num_sms > 0 ? num_sms : 152) * 3;
+    int64_t S = (4 * P + f.ctas - 1) / (f.ctas > 0 ? f.ctas : 1);
+    const int64_t smax = f.n_tiles / 2 > 1 ? f.n_tiles / 2 : 1;
+    if (S > smax) S = smax;
+    if (S < 1) S = 1;
+    f.S = (int)S;
+    return f;
+}
+
 // Geometry shared by the scratch sizing and the launch.
 struct AdjGeom {
     int ti_a, tj_a, tj_b, ti_b;  // i-side: i per CTA, j-tile; j-side: j per CTA, i-tile
@@ -726,13 +953,46 @@ size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms,
     *SB = g.SB;
     const size_t irec = (size_t)g.rows_pad * (precision == 1 ? 64 : 128);
     const size_t pa = (size_t)g.SA * 6 * (size_t)n_i * 8, pb = (size_t)g.SB * 7 * (size_t)n * 8;
-    return irec + 256 + pa + 256 + pb;
+    size_t need = irec + 256 + pa + 256 + pb;
+    if (use_fused(precision, n, n_i)) {
+        const FusedGeom f = fused_geom(n, num_sms);
+        const size_t fb = (size_t)f.n_pad * 80 + 256 + (size_t)f.S * 7 * (size_t)n * 8;
+        if (fb > need) need = fb;
+    }
+    return need;
 }
 
 int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx, int64_t n_i,
                    const double *g_acc, const double *g_jerk, const double *g_pot, double *g_x, double *g_v,
                    double *g_m, void *scratch, unsigned *status, int num_sms)
 {
+    if (use_fused(precision, n, n_i)) {  // dense block: one fused pass over all pairs
+        const FusedGeom f = fused_geom(n, num_sms);
+        float4 *crec = static_cast<float4 *>(scratch);
+        double *part = reinterpret_cast<double *>(static_cast<char *>(scratch) +
+                                                  (((size_t)f.n_pad * 80 + 255) & ~(size_t)255));
+        int64_t gr = (f.n_pad + 255) / 256;
+        if (gr > 152 * 8) gr = 152 * 8;
+        k_build_crec<<<(unsigned)gr, 256, 0, st>>>(n, f.n_pad, static_cast<const float4 *>(rec), crec);
+        int64_t gq = (n_i + 255) / 256;
+        if (gq > 152 * 8) gq = 152 * 8;
+        if (gq < 1) gq = 1;
+        k_scatter_cotangents<<<(unsigned)gq, 256, 0, st>>>(n, n_i, idx, g_acc, g_jerk, g_pot,
+                                                           reinterpret_cast<float *>(crec), status);
+        AdjArgs A{};
+        A.n = n;
+        A.n_i = n_i;
+        A.n_tiles_j = f.n_tiles;
+        A.S = f.S;
+        A.part = part;
+        A.status = status;
+        k_adj_fused_x2<kFusedBlock, kFusedTJ, 3><<<dim3((unsigned)f.ctas, (unsigned)f.S), kFusedBlock,
+                                                   adj_fused_smem<kFusedBlock, kFusedTJ>(), st>>>(A, crec);
+        int64_t gj = (n + 255) / 256;
+        if (gj > 152 * 16) gj = 152 * 16;
+        k_adj_combine_j<<<(unsigned)gj, 256, 0, st>>>(part, f.S, n, g_x, g_v, g_m);
+        return 4;
+    }
     const AdjGeom g = adj_geom(precision, n, n_i, num_sms);
     char *p = static_cast<char *>(scratch);
     const size_t irec_bytes = (size_t)g.rows_pad * (precision == 1 ? 64 : 128);

@@ -42,7 +42,8 @@ def gpu_vjp(ctx, cl, idx, ga, gj, gp):
     return gx.cpu().numpy(), gv.cpu().numpy(), gm.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,n_i", [(512, 512), (1000, 137), (3000, 1), (3000, 33), (4099, 2050)])
+@pytest.mark.parametrize("n,n_i", [(512, 512), (1000, 137), (3000, 1), (3000, 33), (4099, 2050), (2048, 1800),
+                                   (3001, 3001)])
 def test_backward_matches_oracle_vjp(gpu_lib, n, n_i):
     cl = W.plummer(n, 50 + n_i, masses="kroupa")
     rng = np.random.default_rng(n_i)

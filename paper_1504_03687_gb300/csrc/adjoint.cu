@@ -16,6 +16,9 @@
 //            cotangents in shared memory) -> partial sums of dL/dr, dL/dw, dL/dm per j
 // A combine kernel adds the partials in a fixed order and scatters the i-side sums with
 // one atomic per (active i, component); for unique indices the result is deterministic.
+// For dense mixed-precision blocks (n_i >= 3n/4) one fused pass replaces the two: every
+// particle carries its (possibly zero) cotangents, and each pair evaluated once gives both
+// directions (i as the active row against j, and j as the active row against i).
 // Self pairs are skipped by r^2 == 0 (distinct particles never coincide).
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
@@ -107,165 +110,12 @@ __global__ void k_pack_irec(AdjArgs A, int mixed, int64_t rows_pad)
     }
 }
 
-// ---------------------------------------------------------------- i-side pass, mixed
-template <int NI, int BLOCK, int TJ>
-__global__ void __launch_bounds__(BLOCK) k_adj_iside_mixed(AdjArgs A)
-{
-    __shared__ __align__(16) float4 sj[2][3 * TJ];
-    const int tid = threadIdx.x;
-    const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
-    const int s = blockIdx.y;
-    const int64_t t0 = (A.n_tiles_j * s) / A.S, t1 = (A.n_tiles_j * (s + 1)) / A.S;
-    const float4 *rec = static_cast<const float4 *>(A.rec);
-    const float4 *irec = static_cast<const float4 *>(A.irec);
-    float ih[NI][3], il[NI][3], iv[NI][3], ga[NI][3], gj[NI][3], gs[NI];
-#pragma unroll
-    for (int q = 0; q < NI; ++q) {
-        const int64_t k = kbase + q * BLOCK + tid;  // irec rows are padded: always readable
-        const float4 a = irec[4 * k], b = irec[4 * k + 1], c = irec[4 * k + 2], d = irec[4 * k + 3];
-        ih[q][0] = a.x; ih[q][1] = a.y; ih[q][2] = a.z; gs[q] = a.w;
-        il[q][0] = b.x; il[q][1] = b.y; il[q][2] = b.z; gj[q][0] = b.w;
-        iv[q][0] = c.x; iv[q][1] = c.y; iv[q][2] = c.z; gj[q][1] = c.w;
-        ga[q][0] = d.x; ga[q][1] = d.y; ga[q][2] = d.z; gj[q][2] = d.w;
-    }
-    double dacc[NI][6];
-#pragma unroll
-    for (int q = 0; q < NI; ++q)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) dacc[q][c] = 0.0;
-    auto load_tile = [&](int buf, int64_t t) {
-        const float4 *src = rec + t * (3 * TJ);
-#pragma unroll
-        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16(&sj[buf][e], src + e);
-        cp_async_commit();
-    };
-    if (t0 < t1) load_tile(0, t0);
-    for (int64_t t = t0; t < t1; ++t) {
-        const int buf = (int)((t - t0) & 1);
-        if (t + 1 < t1) {
-            load_tile(buf ^ 1, t + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        float acc[NI][6];
-#pragma unroll
-        for (int q = 0; q < NI; ++q)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc[q][c] = 0.f;
-#pragma unroll 2
-        for (int jj = 0; jj < TJ; ++jj) {
-            const float4 p0 = sj[buf][3 * jj], p1 = sj[buf][3 * jj + 1], p2 = sj[buf][3 * jj + 2];
-#pragma unroll
-            for (int q = 0; q < NI; ++q) {
-                const float rx = ds_diff(p0.x, p1.x, ih[q][0], il[q][0]);
-                const float ry = ds_diff(p0.y, p1.y, ih[q][1], il[q][1]);
-                const float rz = ds_diff(p0.z, p1.z, ih[q][2], il[q][2]);
-                const float r2 = r2_f32(rx, ry, rz);
-                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                float dm = 0.f;
-                adj_pair<float, false>(rx, ry, rz, p2.x - iv[q][0], p2.y - iv[q][1], p2.z - iv[q][2], rinv, ga[q],
-                                       gj[q], gs[q], p0.w, acc[q], acc[q] + 3, dm);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NI; ++q)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) dacc[q][c] += (double)acc[q][c];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < NI; ++q) {
-        const int64_t k = kbase + q * BLOCK + tid;
-        if (k < A.n_i)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) A.part[((int64_t)s * 6 + c) * A.n_i + k] = dacc[q][c];
-    }
-}
-
-// ---------------------------------------------------------------- j-side pass, mixed
-template <int NJ, int BLOCK, int TI>
-__global__ void __launch_bounds__(BLOCK) k_adj_jside_mixed(AdjArgs A)
-{
-    __shared__ __align__(16) float4 si[2][4 * TI];
-    const int tid = threadIdx.x;
-    const int64_t jbase = (int64_t)blockIdx.x * (BLOCK * NJ);
-    const int s = blockIdx.y;
-    const int64_t t0 = (A.n_tiles_i * s) / A.S, t1 = (A.n_tiles_i * (s + 1)) / A.S;
-    const float4 *rec = static_cast<const float4 *>(A.rec);
-    const float4 *irec = static_cast<const float4 *>(A.irec);
-    float jh[NJ][3], jl[NJ][3], jv[NJ][3], jm[NJ];
-#pragma unroll
-    for (int q = 0; q < NJ; ++q) {
-        const int64_t j = jbase + q * BLOCK + tid;  // rec is padded to the tile multiple
-        const float4 a = rec[3 * j], b = rec[3 * j + 1], c = rec[3 * j + 2];
-        jh[q][0] = a.x; jh[q][1] = a.y; jh[q][2] = a.z; jm[q] = a.w;
-        jl[q][0] = b.x; jl[q][1] = b.y; jl[q][2] = b.z;
-        jv[q][0] = c.x; jv[q][1] = c.y; jv[q][2] = c.z;
-    }
-    double dacc[NJ][7];
-#pragma unroll
-    for (int q = 0; q < NJ; ++q)
-#pragma unroll
-        for (int c = 0; c < 7; ++c) dacc[q][c] = 0.0;
-    auto load_tile = [&](int buf, int64_t t) {
-        const float4 *src = irec + t * (4 * TI);
-#pragma unroll
-        for (int e = tid; e < 4 * TI; e += BLOCK) cp_async16(&si[buf][e], src + e);
-        cp_async_commit();
-    };
-    if (t0 < t1) load_tile(0, t0);
-    for (int64_t t = t0; t < t1; ++t) {
-        const int buf = (int)((t - t0) & 1);
-        if (t + 1 < t1) {
-            load_tile(buf ^ 1, t + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        float acc[NJ][7];
-#pragma unroll
-        for (int q = 0; q < NJ; ++q)
-#pragma unroll
-            for (int c = 0; c < 7; ++c) acc[q][c] = 0.f;
-#pragma unroll 2
-        for (int ii = 0; ii < TI; ++ii) {
-            const float4 a = si[buf][4 * ii], b = si[buf][4 * ii + 1], c = si[buf][4 * ii + 2],
-                         d = si[buf][4 * ii + 3];
-            const float ga[3] = {d.x, d.y, d.z}, gj[3] = {b.w, c.w, d.w};
-#pragma unroll
-            for (int q = 0; q < NJ; ++q) {
-                const float rx = ds_diff(jh[q][0], jl[q][0], a.x, b.x);
-                const float ry = ds_diff(jh[q][1], jl[q][1], a.y, b.y);
-                const float rz = ds_diff(jh[q][2], jl[q][2], a.z, b.z);
-                const float r2 = r2_f32(rx, ry, rz);
-                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                adj_pair<float, true>(rx, ry, rz, jv[q][0] - c.x, jv[q][1] - c.y, jv[q][2] - c.z, rinv, ga, gj, a.w,
-                                      1.f, acc[q], acc[q] + 3, acc[q][6]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NJ; ++q)
-#pragma unroll
-            for (int c = 0; c < 7; ++c) dacc[q][c] += (double)acc[q][c];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < NJ; ++q) {
-        const int64_t j = jbase + q * BLOCK + tid;
-        if (j < A.n)
-#pragma unroll
-            for (int c = 0; c < 7; ++c)
-                A.part[((int64_t)s * 7 + c) * A.n + j] = c < 6 ? dacc[q][c] * (double)jm[q] : dacc[q][c];
-    }
-}
-
 // ---------------------------------------------------------------- packed FP32x2 passes
-// The mixed passes above written with __ffma2_rn / __fadd2_rn / __fmul2_rn on pairs of rows:
-// i-side rows (pass A) or j-side particles (pass B) are held two per packed register, the
-// streamed side is expanded once per tile into a duplicated shared-memory layout.
+// The mixed passes, with __ffma2_rn / __fadd2_rn / __fmul2_rn on pairs of rows: i-side rows
+// (pass A) or j-side particles (pass B) are held two per packed register, the streamed side
+// is expanded once per tile into a duplicated shared-memory layout.  The pair terms are the
+// ones adj_pair states, with r, w and the differences in double-single form as in the
+// forward kernels.
 __device__ __forceinline__ float2 a2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 a2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 a2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }

@@ -34,6 +34,33 @@ UNIT = "Ginteractions/s"
 FLOPS_PER_PAIR = 60
 BLOCKS = (1 << 10, 1 << 14, 1 << 17, 1 << 20)
 NB_CAP = 512
+
+# DRAM bytes (read + write) of the four force launches of one step (blocks 2^10 .. 2^20), from
+# one ncu capture of `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu --no-ensemble
+# --no-adjoint` (metrics dram__bytes_read.sum, dram__bytes_write.sum), valid only for the
+# force-kernel sources whose SHA-256 is recorded with them.
+FORCE_TRAFFIC = {"sources_sha256": "e3a3d78d413f31d0df56b4c35a9acbc4afd00d386d36e6cad6ddb1bf00b288a1",
+                 "bytes_per_launch": [55.29e6, 159.95e6, 1050.72e6, 2422.4e6]}
+FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh")
+
+
+def force_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1504_03687_gb300", "csrc")
+    for f in FORCE_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def force_traffic_per_launch():
+    """Mean DRAM bytes per force launch of a step, or None if the kernel sources changed
+    since the counters were taken."""
+    rec = FORCE_TRAFFIC
+    if rec["bytes_per_launch"] is None or rec["sources_sha256"] != force_sources_sha256():
+        return None
+    return sum(rec["bytes_per_launch"]) / len(rec["bytes_per_launch"])
 NB_PER_ROW = NB_CAP  # CSR capacity per active particle: room for every list at the cap
 WORKLOAD = ("King W0=6, N=2^20 j-particles (5% binary c.m.), Kroupa IMF, N-body units; "
             "active blocks 2^10/2^14/2^17/2^20 from the sorted step list; "
@@ -364,7 +391,9 @@ def main():
                        "parallelism": f"{world} independent clusters, one per GPU",
                        "launch_plans": "autotuned table" if tuned else "automatic planner"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": force_traffic_per_launch(),
+                         "traffic_per_block": (dict(zip(map(str, BLOCKS), FORCE_TRAFFIC["bytes_per_launch"]))
+                                               if force_traffic_per_launch() is not None else None),
                          "kernel": "force (mixed tiled / j-streamed)", "peak_source": peak_src,
                          "flops_per_pair": FLOPS_PER_PAIR, "force_kernel_ms_per_step": force_ms / args.steps},
             "fp32_peak_frac_whole_step": value * 1e9 * FLOPS_PER_PAIR / (peak * 1e12) / world,

@@ -105,7 +105,8 @@ nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp, int32_t on_devic
  *   acc_k  = sum_{j != i} m_j r / |r|^3
  *   jerk_k = sum_{j != i} m_j [ w / |r|^3 - 3 (r.w) r / |r|^5 ]
  *   pot_k  = - sum_{j != i} m_j / |r|
- * with i = idx[k], r = x_p,j - x_p,i, w = v_p,j - v_p,i, over all n predicted particles.
+ * with i = idx[k], r = x_p,j - x_p,i, w = v_p,j - v_p,i, over all n predicted particles
+ * (or over the source range set by nb_set_source_range).
  * Neighbours: j != i with |r|^2 < rs2 (rs2[k], or rs2[0] for all when rs2_scalar != 0).
  *
  * idx:           (n_i) int32, unique, each in [0, n); output row k is for idx[k].
@@ -123,6 +124,23 @@ nb_status nb_regular_force(nb_ctx *ctx, int64_t n_i, const int32_t *idx, const d
                            int32_t rs2_scalar, double *acc, double *jerk, double *pot,
                            int64_t *nb_off, int32_t *nb_idx, int64_t nb_idx_capacity,
                            int32_t *nb_count_true, int32_t on_device);
+
+/* Restrict the source particles of subsequent nb_regular_force calls to j in [j_lo, j_hi):
+ * the split of the particle set between the GPUs of one node (Sec. 3.4: every GPU holds a
+ * similar share of the particles for the regular force, and together they cover the whole
+ * set).  The active particles idx may be anywhere in [0, n).  The call then returns the
+ * sums over the range only, the neighbours found in the range (global indices, ascending
+ * j, at most nb_cap per row) and the range's true counts.  Adding the sums of disjoint
+ * ranges that cover [0, n), concatenating the lists in range order (each cut at nb_cap)
+ * and adding the counts gives the unrestricted result; the sums agree with it up to the
+ * order of the FP64 additions.
+ * j_lo must be a multiple of NB_SOURCE_ALIGN and 0 <= j_lo < j_hi <= n_max; at call time
+ * j_hi must not exceed the loaded particle count n and must be a multiple of
+ * NB_SOURCE_ALIGN unless it equals n (else that call returns NB_ERR_STATE).
+ * (0, 0) restores the full set.  nb_regular_force_backward returns NB_ERR_STATE while a
+ * range is set; the batched form ignores it. */
+#define NB_SOURCE_ALIGN 256
+nb_status nb_set_source_range(nb_ctx *ctx, int64_t j_lo, int64_t j_hi);
 
 /* Vector-Jacobian product of nb_regular_force's (acc, jerk, pot) w.r.t. the predicted
  * positions, velocities and masses of all n particles (no counterpart in the paper;

@@ -29,7 +29,8 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
            "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
            "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
-           "nb_set_plan_table")
+           "nb_set_plan_table", "nb_set_source_range")
+NB_SOURCE_ALIGN = 256
 
 
 class NBError(RuntimeError):
@@ -80,6 +81,7 @@ def load_library(build_if_needed: bool = True):
         "nb_set_plan_override": (st, [P, i32, i32, i32]),
         "nb_batch_plan": (st, [P, i64, P, P, i32]),
         "nb_set_plan_table": (st, [P, i32, P, P, P, P]),
+        "nb_set_source_range": (st, [P, i64, i64]),
         "nb_regular_force_batched": (st, [P, P, P, P, P, P, P, P, i64, P]),
         "nb_set_timing": (st, [P, i32]),
         "nb_get_timings": (st, [P, P, P]),
@@ -362,6 +364,11 @@ class Context:
         spl = np.array([x[3] for x in e], np.int32)
         self._check(self.lib.nb_set_plan_table(self.h, len(e), nim.ctypes.data, ker.ctypes.data, var.ctypes.data,
                                                spl.ctypes.data), "nb_set_plan_table")
+
+    def set_source_range(self, j_lo: int = 0, j_hi: int = 0):
+        """nb_set_source_range: later regular_force calls sum over source particles j in
+        [j_lo, j_hi) only; (0, 0) = all particles."""
+        self._check(self.lib.nb_set_source_range(self.h, int(j_lo), int(j_hi)), "nb_set_source_range")
 
     def set_plan_override(self, kernel: int = -1, variant: int = 0, splits: int = 1):
         """Force (kernel, variant, splits) for later regular_force calls; kernel < 0 = automatic."""

@@ -507,9 +507,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const f
         }
         __syncthreads();
         if (t + 1 < t1) load_tile(t + 1);
-        float2 v1[3], u1[3], v2[3], u2[3], d2 = make_float2(0.f, 0.f);
+        // k as receiver: its cotangents are constant over the tile, so the sums of
+        //   V = ga + alpha r + beta w + gamma gj   and   U = gj + beta r   (times m_m |r|^-3)
+        // are kept as sum(m|r|^-3) ga + sum(m|r|^-3 gamma) gj + sum(m|r|^-3 alpha r)
+        // + sum(m|r|^-3 beta w), and sum(m|r|^-3) gj + sum(m|r|^-3 beta r).
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0, A1[3], B1[3], C1[3], v2[3], u2[3], d2 = s0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v1[c] = u1[c] = v2[c] = u2[c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < 3; ++c) A1[c] = B1[c] = C1[c] = v2[c] = u2[c] = make_float2(0.f, 0.f);
 #pragma unroll 2
         for (int jj = 0; jj < TJ; ++jj) {
             const float4 q0 = dup[9 * jj], q1 = dup[9 * jj + 1], q2 = dup[9 * jj + 2], q3 = dup[9 * jj + 3],
@@ -544,11 +548,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const f
                 const float2 beta = a2mul(b3, jr);
                 const float2 alpha = a2fma(b3, a2fma(m5, a2mul(a2mul(q, jr), rinv2), tt), gs);
                 const float2 rinv3m = a2mul(rinv3, M);
+                s0 = a2add(s0, rinv3m);
+                s1 = a2fma(rinv3m, gamma, s1);
+                const float2 ra = a2mul(rinv3m, alpha), rb = a2mul(rinv3m, beta);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 in = a2fma(gamma, gj[c], a2fma(beta, w[c], a2fma(alpha, r[c], ga[c])));
-                    v1[c] = a2fma(rinv3m, in, v1[c]);
-                    u1[c] = a2fma(rinv3m, a2fma(beta, r[c], gj[c]), u1[c]);
+                    A1[c] = a2fma(ra, r[c], A1[c]);
+                    B1[c] = a2fma(rb, w[c], B1[c]);
+                    C1[c] = a2fma(rb, r[c], C1[c]);
                 }
             }
             // m as receiver (cotangents of m), source k (mass m_k applied per tile)
@@ -573,8 +580,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const f
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 gx = a2fma(mk, v2[c], make_float2(-v1[c].x, -v1[c].y));
-            const float2 gv = a2fma(mk, u2[c], make_float2(-u1[c].x, -u1[c].y));
+            const float2 v1 = a2add(a2fma(ga[c], s0, a2mul(gj[c], s1)), a2add(A1[c], B1[c]));
+            const float2 u1 = a2fma(gj[c], s0, C1[c]);
+            const float2 gx = a2fma(mk, v2[c], make_float2(-v1.x, -v1.y));
+            const float2 gv = a2fma(mk, u2[c], make_float2(-u1.x, -u1.y));
             dacc[(c * 2) * BLOCK + tid] += (double)gx.x;
             dacc[(c * 2 + 1) * BLOCK + tid] += (double)gx.y;
             dacc[((3 + c) * 2) * BLOCK + tid] += (double)gv.x;

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
     const int tid = threadIdx.x;
     const int64_t k = (int64_t)blockIdx.x * BLOCK + tid;
     const int s = blockIdx.y;
-    const int64_t t0 = (A.n_tiles * s) / A.S, t1 = (A.n_tiles * (s + 1)) / A.S;
+    const int64_t tb = A.j_lo / TJ;  // first tile of the source range
+    const int64_t t0 = tb + (A.n_tiles * s) / A.S, t1 = tb + (A.n_tiles * (s + 1)) / A.S;
     const dvec4 *rec = static_cast<const dvec4 *>(A.rec);
 
     int64_t g = -1;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
         for (int jj = 0; jj < TJ; ++jj) {
             const int64_t j = jb + jj;
             const double r2 = pair_f64(sj[buf][2 * jj], sj[buf][2 * jj + 1], xi, vi, j == g, acc);
-            if (r2 < rs2 && j != g && j < A.n) {
+            if (r2 < rs2 && j != g && j < A.j_hi) {
                 if (cnt < A.L) slot[cnt] = (int32_t)j;
                 ++cnt;
             }
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_fp64_jstream(ForceArgs A)
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int s = blockIdx.y;
     const int64_t k0 = (int64_t)blockIdx.x * IB;
-    const int64_t j0 = (A.n * s) / A.S, j1 = (A.n * (s + 1)) / A.S;
+    const int64_t j0 = A.j_lo + ((A.j_hi - A.j_lo) * s) / A.S, j1 = A.j_lo + ((A.j_hi - A.j_lo) * (s + 1)) / A.S;
     const int64_t w0 = j0 + ((j1 - j0) * w) / W, w1 = j0 + ((j1 - j0) * (w + 1)) / W;
     const int64_t seg = (int64_t)s * W + w;
     const dvec4 *rec = static_cast<const dvec4 *>(A.rec);

@@ -77,7 +77,7 @@ __device__ __forceinline__ void tile_mixed(const float4 *__restrict__ sj, int64_
         if (hit) {  // rare: record in ascending j, the first L per segment
 #pragma unroll
             for (int q = 0; q < NI; ++q)
-                if (r2[q] < rs2f[q] && j != gi[q] && j < A.n) {
+                if (r2[q] < rs2f[q] && j != gi[q] && j < A.j_hi) {
                     if (cnt[q] < A.L) slot[q][cnt[q]] = (int32_t)j;
                     ++cnt[q];
                 }
@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled(ForceArgs A)
     const int tid = threadIdx.x;
     const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
     const int s = blockIdx.y;
-    const int64_t t0 = (A.n_tiles * s) / A.S, t1 = (A.n_tiles * (s + 1)) / A.S;
+    const int64_t tb = A.j_lo / TJ;  // first tile of the source range
+    const int64_t t0 = tb + (A.n_tiles * s) / A.S, t1 = tb + (A.n_tiles * (s + 1)) / A.S;
     const float4 *rec = static_cast<const float4 *>(A.rec);
 
     float ih[NI][3], il[NI][3], iv[NI][3], rs2f[NI];
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_mixed_jstream(ForceArgs A)
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int s = blockIdx.y;
     const int64_t k0 = (int64_t)blockIdx.x * IB;
-    const int64_t j0 = (A.n * s) / A.S, j1 = (A.n * (s + 1)) / A.S;
+    const int64_t j0 = A.j_lo + ((A.j_hi - A.j_lo) * s) / A.S, j1 = A.j_lo + ((A.j_hi - A.j_lo) * (s + 1)) / A.S;
     const int64_t w0 = j0 + ((j1 - j0) * w) / W, w1 = j0 + ((j1 - j0) * (w + 1)) / W;
     const int64_t g = (int64_t)s * W + w;
     const float4 *rec = static_cast<const float4 *>(A.rec);
@@ -373,7 +374,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
     const int tid = threadIdx.x;
     const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
     const int s = blockIdx.y;
-    const int64_t t0 = (A.n_tiles * s) / A.S, t1 = (A.n_tiles * (s + 1)) / A.S;
+    const int64_t tb = A.j_lo / TJ;  // first tile of the source range
+    const int64_t t0 = tb + (A.n_tiles * s) / A.S, t1 = tb + (A.n_tiles * (s + 1)) / A.S;
     const float4 *rec = static_cast<const float4 *>(A.rec);
 
     // rows q*BLOCK + tid (q = 0..NI-1); pair p holds rows 2p and 2p+1
@@ -454,9 +456,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 #pragma unroll
             for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
         if (__any_sync(0xffffffffu, mine))
-            tile_mixed_x2<NP, true, TJ>(dup, jb, A.n, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            tile_mixed_x2<NP, true, TJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
         else
-            tile_mixed_x2<NP, false, TJ>(dup, jb, A.n, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            tile_mixed_x2<NP, false, TJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll

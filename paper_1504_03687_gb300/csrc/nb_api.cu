@@ -59,6 +59,7 @@ struct nb_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     int64_t n_max = 0, n = 0, n_pad = 0;
+    int64_t src_lo = 0, src_hi = 0;  // source range of nb_regular_force (src_hi 0: all particles)
     bool have_state = false, have_pred = false, broken = false;
     double *x = nullptr, *v = nullptr, *a = nullptr, *jk = nullptr, *m = nullptr, *tl = nullptr;
     double *xp = nullptr, *vp = nullptr;
@@ -406,7 +407,9 @@ void launch_force(cudaStream_t st, const Plan &p, ForceArgs a)
 {
     const int64_t ctas_x = p.ctas / p.S;
     a.S = p.S;
-    a.n_tiles = p.tj > 0 ? ((a.n + kTilePad - 1) / kTilePad) * kTilePad / p.tj : 0;
+    // records past n are massless padding up to the next multiple of kTilePad
+    const int64_t hi_pad = ((a.j_hi + kTilePad - 1) / kTilePad) * kTilePad;
+    a.n_tiles = p.tj > 0 ? (hi_pad - a.j_lo) / p.tj : 0;
     if (p.kernel == 1 || p.kernel == 2)
         launch_force_mixed(st, p.kernel, p.variant, ctas_x, p.S, a);
     else
@@ -661,6 +664,21 @@ nb_status nb_set_plan_override(nb_ctx *c, int32_t kernel, int32_t variant, int32
     return NB_OK;
 }
 
+nb_status nb_set_source_range(nb_ctx *c, int64_t j_lo, int64_t j_hi)
+{
+    if (!c) return NB_ERR_ARG;
+    if (j_lo == 0 && j_hi == 0) {
+        c->src_lo = c->src_hi = 0;
+        return NB_OK;
+    }
+    if (j_lo < 0 || j_hi <= j_lo || j_hi > c->n_max || j_lo % kTilePad != 0)
+        return fail(c, NB_ERR_ARG, "source range [%lld, %lld) invalid: need 0 <= j_lo < j_hi <= n_max, j_lo %% %d == 0",
+                    (long long)j_lo, (long long)j_hi, kTilePad);
+    c->src_lo = j_lo;
+    c->src_hi = j_hi;
+    return NB_OK;
+}
+
 nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const double *rs2, int32_t rs2_scalar,
                            double *acc, double *jerk, double *pot, int64_t *nb_off, int32_t *nb_idx,
                            int64_t nb_idx_capacity, int32_t *nb_count_true, int32_t on_device)
@@ -680,6 +698,10 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         return NB_OK;
     }
     const int64_t n = c->n;
+    const int64_t j_lo = c->src_hi ? c->src_lo : 0, j_hi = c->src_hi ? c->src_hi : n;
+    if (j_hi > n || (j_hi != n && j_hi % kTilePad != 0))
+        return fail(c, NB_ERR_STATE, "source range [%lld, %lld) does not fit the %lld loaded particles",
+                    (long long)j_lo, (long long)j_hi, (long long)n);
     // host mode: validate on the host and stage everything on the device
     const int32_t *d_idx = idx;
     const double *d_rs2 = rs2;
@@ -711,7 +733,7 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
         CK(cudaMemcpyAsync((void *)d_rs2, rs2, n_rs2 * 8, cudaMemcpyHostToDevice, c->stream), "copy rs2");
     }
-    Plan p = ctx_plan(c, n, n_i);
+    Plan p = ctx_plan(c, j_hi - j_lo, n_i);
     const size_t part_bytes = (size_t)p.S * 7 * (size_t)n_i * sizeof(double);
     if ((s = grow(c, (void **)&c->part, &c->part_cap, part_bytes, "partial sums")) != NB_OK) return s;
     // neighbour segments: G ordered j-segments, L slots each per row (0: counts only)
@@ -730,6 +752,8 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
     ForceArgs fa{};
     fa.rec = c->rec;
     fa.n = n;
+    fa.j_lo = j_lo;
+    fa.j_hi = j_hi;
     fa.idx = d_idx;
     fa.n_i = n_i;
     fa.rs2 = d_rs2;
@@ -787,6 +811,7 @@ nb_status nb_regular_force_backward(nb_ctx *c, int64_t n_i, const int32_t *idx, 
     if (n_i < 0 || n_i > (int64_t)INT32_MAX) return fail(c, NB_ERR_ARG, "n_i=%lld out of range", (long long)n_i);
     if (!g_x || !g_v || !g_m || (n_i > 0 && (!idx || !g_acc || !g_jerk || !g_pot)))
         return fail(c, NB_ERR_ARG, "null array");
+    if (c->src_hi) return fail(c, NB_ERR_STATE, "nb_regular_force_backward needs the full source range");
     const int64_t n = c->n;
     const int32_t *d_idx = idx;
     const double *d_ga = g_acc, *d_gj = g_jerk, *d_gp = g_pot;

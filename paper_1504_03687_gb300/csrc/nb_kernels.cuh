@@ -23,7 +23,8 @@ namespace nbgpu {
 struct ForceArgs {
     const void *rec;        // dvec4* (FP64) or float4* (mixed)
     int64_t n;              // particles
-    int64_t n_tiles;        // j-tiles of the launch's tile size covering n_pad
+    int64_t j_lo, j_hi;     // source range [j_lo, j_hi); j_lo is a multiple of the record padding
+    int64_t n_tiles;        // j-tiles of the launch's tile size covering the source range
     const int32_t *idx;     // active indices
     int64_t n_i;
     const double *rs2;      // (n_i) or scalar

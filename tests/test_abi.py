@@ -46,6 +46,7 @@ def test_null_arguments_are_rejected_without_gpu():
     assert lib.nb_init(ctypes.byref(h), ctypes.byref(bad)) == api.NB_ERR_ARG
     assert lib.nb_free(None) == api.NB_OK
     assert lib.nb_sync(None) == api.NB_ERR_ARG
+    assert lib.nb_set_source_range(None, 0, 256) == api.NB_ERR_ARG
     assert lib.nb_last_error(None) == b"null context"
 
 

@@ -74,3 +74,87 @@ def test_copy_algorithm_exchange_matches_single_rank():
     off[1:] = np.cumsum([len(l) for l in lists])
     np.testing.assert_array_equal(got[3], off)
     np.testing.assert_array_equal(got[4], np.concatenate(lists))
+
+
+# ------------------------------------------------------------------ source sharding
+
+def test_shard_sources_partitions_on_aligned_starts():
+    from paper_1504_03687_gb300.dist import shard_sources
+    for n in (1, 255, 256, 1000, 4099, 1 << 20):
+        for world in (1, 2, 3, 8):
+            parts = [shard_sources(n, world, r) for r in range(world)]
+            assert parts[0][0] == 0 and parts[-1][1] == n
+            assert all(parts[r][1] == parts[r + 1][0] for r in range(world - 1))
+            assert all(lo % 256 == 0 for lo, _ in parts)
+            assert all(abs((b - a) - n / world) < 256 for a, b in parts)
+
+
+def _range_result(cl, idx, lo, hi, cap):
+    """Oracle result of the rows idx summed over the sources [lo, hi) only: the restricted
+    pair sums, and the full neighbour sets restricted to the range (first cap kept)."""
+    a, j, p = oracle.pair_sums(cl.x, cl.v, cl.m, idx, np.arange(lo, hi, dtype=np.int32))
+    _, _, _, _, lists = oracle.regular_force(cl.x, cl.v, cl.m, idx, _range_result.rs2, cap=cl.n)
+    inside = [l[(l >= lo) & (l < hi)] for l in lists]
+    cnt = np.array([len(l) for l in inside], np.int32)
+    kept = [l[:cap] for l in inside]
+    off = np.zeros(len(idx) + 1, np.int64)
+    off[1:] = np.cumsum([len(l) for l in kept])
+    flat = np.concatenate(kept).astype(np.int32) if kept else np.zeros(0, np.int32)
+    return [torch.from_numpy(q) for q in (a, j, p, off, flat, cnt)]
+
+
+def _check_against_full(got, cl, idx, rs2, cap):
+    a, j, p, cnt, lists = oracle.regular_force(cl.x, cl.v, cl.m, idx, rs2, cap=cap)
+    for g, r in ((got[0], a), (got[1], j), (got[2], p)):
+        np.testing.assert_allclose(g.numpy(), r, rtol=1e-12, atol=1e-13 * np.abs(r).max())
+    off = np.zeros(idx.size + 1, np.int64)
+    off[1:] = np.cumsum([len(l) for l in lists])
+    np.testing.assert_array_equal(got[3].numpy(), off)
+    np.testing.assert_array_equal(got[4].numpy()[:off[-1]], np.concatenate(lists))
+    np.testing.assert_array_equal(got[5].numpy(), cnt)
+
+
+def test_combine_source_shards_matches_full_set():
+    """Three unequal source ranges, cap 16 (most lists are cut, some inside the first
+    range, some across ranges): sums up to reassociation, lists and counts exact."""
+    from paper_1504_03687_gb300.dist import combine_source_shards, shard_sources
+    cl, rs2 = W.plummer_1k_equal()
+    _range_result.rs2 = rs2
+    idx = W.active_block(W.block_steps(cl, seed=0), 301)
+    cap = 16
+    parts = [_range_result(cl, idx, *shard_sources(cl.n, 3, r), cap) for r in range(3)]
+    _check_against_full(combine_source_shards(parts, cap), cl, idx, rs2, cap)
+
+
+def _source_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1504_03687_gb300.dist import reduce_sources, shard_sources
+        cl, rs2 = W.plummer_1k_equal()
+        _range_result.rs2 = rs2
+        idx = W.active_block(W.block_steps(cl, seed=0), 301)
+        lo, hi = shard_sources(cl.n, world, rank)
+        part = _range_result(cl, idx, lo, hi, 24)
+        res = reduce_sources(*part, nb_cap=24)
+        if rank == 0:
+            out.put([t.numpy() for t in res])
+    finally:
+        dist.destroy_process_group()
+
+
+def test_source_sharded_exchange_matches_single_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_source_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    got = q.get(timeout=120)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    cl, rs2 = W.plummer_1k_equal()
+    idx = W.active_block(W.block_steps(cl, seed=0), 301)
+    _check_against_full([torch.from_numpy(g) for g in got], cl, idx, rs2, 24)

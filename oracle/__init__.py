@@ -10,7 +10,8 @@ Every function cites the passage of the paper it follows in the C source.
 Parity of every function is pinned by tests/test_oracle_pins.py against closed
 forms and invariants (two-body Kepler orbit, Newton's third law, jerk as the
 time derivative of the acceleration, the Plummer potential energy, energy
-conservation, brute-force neighbour sets, finite differences for the adjoint).
+conservation, brute-force neighbour sets, finite differences for the adjoint,
+partition and Newton's-law invariants of the irregular force).
 """
 from __future__ import annotations
 
@@ -206,6 +207,31 @@ def pair_sums(xp, vp, m, idx, jdx):
     if rc != 0:
         raise IndexError("index outside [0, n)")
     return acc, jerk, pot
+
+
+def irregular_force(t, x, v, a, jerk, t_last, m, idx, nb_off, nb_idx):
+    """Irregular force: (acc, jerk (n_i,3), pot (n_i)) of the rows idx summed over their
+    CSR neighbour lists nb_idx[nb_off[k]:nb_off[k+1]], with i and each listed neighbour
+    predicted from its Hermite state to time t."""
+    lib = _load()
+    if not hasattr(lib, "_irr"):
+        P, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        lib.orc_irregular_force.argtypes = [i64, P, P, P, P, P, P, dbl, i64, P, P, P, P, P, P]
+        lib.orc_irregular_force.restype = ctypes.c_int
+        lib._irr = True
+    x, v, a, jerk = (_c(q, np.float64) for q in (x, v, a, jerk))
+    t_last, m = _c(t_last, np.float64), _c(m, np.float64)
+    idx, nb_off, nb_idx = _c(idx, np.int32), _c(nb_off, np.int64), _c(nb_idx, np.int32)
+    n_i = idx.shape[0]
+    if nb_off.shape[0] != n_i + 1:
+        raise ValueError("nb_off needs n_i + 1 entries")
+    acc = np.empty((n_i, 3)); jk = np.empty((n_i, 3)); pot = np.empty(n_i)
+    rc = lib.orc_irregular_force(x.shape[0], _p(x), _p(v), _p(a), _p(jerk), _p(t_last), _p(m), float(t), n_i,
+                                 _p(idx), _p(nb_off), _p(nb_idx if nb_idx.size else np.zeros(1, np.int32)),
+                                 _p(acc), _p(jk), _p(pot))
+    if rc != 0:
+        raise IndexError("index outside [0, n) or decreasing offsets")
+    return acc, jk, pot
 
 
 def loss_fd(xp, vp, m, idx, g_acc, g_jerk, g_pot, which: str, p: int, c: int = 0, h: float = 1e-6):

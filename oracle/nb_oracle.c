@@ -24,6 +24,9 @@
  *    textbook forms of Makino 1991 / Makino & Aarseth 1992, which the paper
  *    cites but does not print).
  *  - Kinetic and potential energy (Sec. 3.3.2 needs W for N-body scaling).
+ *  - The irregular force: the same sums over each active particle's neighbour list,
+ *    with i and its neighbours predicted from their Hermite state (Sec. 2, Ahmad-Cohen;
+ *    Sec. 3.2.2 and Sec. 3.3.3, neighbour-only prediction).
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no ISA intrinsics).
  * Loops over j run in ascending index order; OpenMP only splits the outer loop
@@ -416,6 +419,65 @@ int orc_pair_sums(int64_t n, const double *xp, const double *vp, const double *m
             const double wx = vp[3 * j + 0] - vp[3 * i + 0];
             const double wy = vp[3 * j + 1] - vp[3 * i + 1];
             const double wz = vp[3 * j + 2] - vp[3 * i + 2];
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            const double rinv = 1.0 / sqrt(r2);
+            const double rinv2 = rinv * rinv;
+            const double mr3 = m[j] * rinv * rinv2;
+            const double rw = rx * wx + ry * wy + rz * wz;
+            ax += mr3 * rx;
+            ay += mr3 * ry;
+            az += mr3 * rz;
+            jx += mr3 * (wx - 3.0 * rw * rinv2 * rx);
+            jy += mr3 * (wy - 3.0 * rw * rinv2 * ry);
+            jz += mr3 * (wz - 3.0 * rw * rinv2 * rz);
+            ph -= m[j] * rinv;
+        }
+        acc[3 * k + 0] = ax;  acc[3 * k + 1] = ay;  acc[3 * k + 2] = az;
+        jerk[3 * k + 0] = jx; jerk[3 * k + 1] = jy; jerk[3 * k + 2] = jz;
+        pot[k] = ph;
+    }
+    return 0;
+}
+
+/* Irregular force of the Ahmad-Cohen scheme (Sec. 2; Sec. 3.2.2 "Prediction and irregular
+ * force"): for every active i = idx[k], the acceleration, jerk and potential summed over its
+ * neighbour list only, j in nb_idx[nb_off[k] .. nb_off[k+1]), in list order.  The particles
+ * come as their Hermite state (x, v, a, jerk at t_last) and only i and its neighbours are
+ * predicted to time t (neighbour-only prediction, Sec. 3.3.3), with the same Taylor form as
+ * orc_predict.  A listed j equal to i is skipped.  Returns 0, or -1 on an index outside
+ * [0, n) or decreasing offsets. */
+static void predict_one(int64_t p, double t, const double *x, const double *v, const double *a,
+                        const double *jk, const double *t_last, double *xp, double *vp)
+{
+    const double dt = t - t_last[p];
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = 3 * p + c;
+        xp[c] = x[q] + v[q] * dt + a[q] * dt * dt / 2.0 + jk[q] * dt * dt * dt / 6.0;
+        vp[c] = v[q] + a[q] * dt + jk[q] * dt * dt / 2.0;
+    }
+}
+
+int orc_irregular_force(int64_t n, const double *x, const double *v, const double *a, const double *jk,
+                        const double *t_last, const double *m, double t, int64_t n_i, const int32_t *idx,
+                        const int64_t *nb_off, const int32_t *nb_idx, double *acc, double *jerk, double *pot)
+{
+    for (int64_t k = 0; k < n_i; ++k) {
+        if (idx[k] < 0 || idx[k] >= n || nb_off[k + 1] < nb_off[k] || nb_off[k] < 0) return -1;
+        for (int64_t e = nb_off[k]; e < nb_off[k + 1]; ++e)
+            if (nb_idx[e] < 0 || nb_idx[e] >= n) return -1;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n_i; ++k) {
+        const int64_t i = idx[k];
+        double xi[3], vi[3], xj[3], vj[3];
+        predict_one(i, t, x, v, a, jk, t_last, xi, vi);
+        double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0, ph = 0;
+        for (int64_t e = nb_off[k]; e < nb_off[k + 1]; ++e) {
+            const int64_t j = nb_idx[e];
+            if (j == i) continue;
+            predict_one(j, t, x, v, a, jk, t_last, xj, vj);
+            const double rx = xj[0] - xi[0], ry = xj[1] - xi[1], rz = xj[2] - xi[2];
+            const double wx = vj[0] - vi[0], wy = vj[1] - vi[1], wz = vj[2] - vi[2];
             const double r2 = rx * rx + ry * ry + rz * rz;
             const double rinv = 1.0 / sqrt(r2);
             const double rinv2 = rinv * rinv;

@@ -15,6 +15,10 @@ least one of them:
                    energy conservation on the 1024-body Plummer sphere
   adjoint        : central finite differences of the forward, and autograd of an
                    independently written dense PyTorch formula
+  irregular force: lists plus the rest of the particles add up to the all-j sums
+                   (with neighbour-only prediction against the all-particle
+                   predictor); Newton's third law and the pair energy inside an
+                   isolated group; jerk as d acc/dt along the prediction
 """
 import math
 from fractions import Fraction
@@ -391,3 +395,103 @@ def test_local_finite_difference_matches_adjoint():
             c = 1 if which == "x" else 2
             fd = oracle.loss_fd(cl.x, cl.v, cl.m, idx, ga, gj, gp, which, p, c, h=1e-5 if which != "m" else 1e-9)
             assert abs(fd - ref) <= 1e-6 * abs(ref) + 1e-9, (which, p, fd, ref)
+
+
+# ---------------------------------------------------------------- irregular force
+def _csr(lists):
+    off = np.zeros(len(lists) + 1, np.int64)
+    off[1:] = np.cumsum([len(l) for l in lists])
+    flat = np.concatenate(lists).astype(np.int32) if lists else np.zeros(0, np.int32)
+    return off, flat
+
+
+def test_irregular_plus_outside_equals_all_sources():
+    """With a and jerk nonzero and t != t_last: the irregular sums over each row's neighbour
+    list (neighbour-only prediction) plus the sums over the rest of the particles (after
+    predicting all particles) give the all-j regular force of the predicted state.  Pins
+    the list restriction and shows that predicting only the neighbours reproduces the
+    all-particle prediction."""
+    cl = W.plummer(1024, 43, masses="kroupa")
+    rng = np.random.default_rng(43)
+    a0, j0 = rng.standard_normal((1024, 3)), 10 * rng.standard_normal((1024, 3))
+    tl = -rng.integers(0, 4, 1024) * 2.0 ** -10
+    t = 2.0 ** -11
+    xp, vp = oracle.predict(t, cl.x, cl.v, a0, j0, tl)
+    rs2 = W.neighbour_radius2(xp, 40, seed=43)
+    idx = rng.permutation(1024)[:64].astype(np.int32)
+    a_all, j_all, p_all, cnt, lists = oracle.regular_force(xp, vp, cl.m, idx, rs2, cap=1024)
+    assert (cnt > 0).mean() > 0.5
+    off, flat = _csr(lists)
+    ai, ji, pi = oracle.irregular_force(t, cl.x, cl.v, a0, j0, tl, cl.m, idx, off, flat)
+    for k in range(idx.size):
+        rest = np.setdiff1d(np.arange(1024, dtype=np.int32), lists[k])
+        ao, jo, po = oracle.pair_sums(xp, vp, cl.m, idx[k:k + 1], rest)
+        np.testing.assert_allclose(ai[k] + ao[0], a_all[k], rtol=1e-12, atol=1e-12 * np.abs(a_all[k]).max())
+        np.testing.assert_allclose(ji[k] + jo[0], j_all[k], rtol=1e-11, atol=1e-11 * np.abs(j_all[k]).max())
+        assert abs(pi[k] + po[0] - p_all[k]) <= 1e-12 * abs(p_all[k])
+    # the irregular part is the close, dominant part of the force for these rows
+    assert np.median(np.linalg.norm(ai[cnt > 0], axis=1) / np.linalg.norm(a_all[cnt > 0], axis=1)) > 0.05
+
+
+def test_irregular_force_of_an_isolated_group_obeys_newton():
+    """Six particles in a tight group far from 300 others, r_s around the group: each member's
+    list is the other five, the irregular forces are the group's own mutual forces, and
+    sum m acc = sum m jerk = 0 over the group."""
+    rng = np.random.default_rng(44)
+    far = W.plummer(300, 44)
+    xg = 0.01 * rng.standard_normal((6, 3)) + np.array([30.0, 0.0, 0.0])
+    vg = 0.3 * rng.standard_normal((6, 3))
+    mg = rng.uniform(0.5, 2.0, 6) / 300
+    x = np.concatenate([far.x, xg]); v = np.concatenate([far.v, vg]); m = np.concatenate([far.m, mg])
+    z = np.zeros_like(x)
+    tl = np.zeros(306)
+    idx = np.arange(300, 306, dtype=np.int32)
+    _, _, _, cnt, lists = oracle.regular_force(x, v, m, idx, 1.0, cap=16)
+    assert list(cnt) == [5] * 6 and all(set(l) == set(range(300, 306)) - {i} for l, i in zip(lists, idx))
+    off, flat = _csr(lists)
+    a, j, p = oracle.irregular_force(0.0, x, v, z, z, tl, m, idx, off, flat)
+    ma, mj = mg[:, None] * a, mg[:, None] * j
+    assert np.abs(ma.sum(0)).max() <= 1e-13 * np.abs(ma).sum()
+    assert np.abs(mj.sum(0)).max() <= 1e-13 * np.abs(mj).sum()
+    # the group's potential energy from the irregular potentials is the pair sum
+    W_pairs = -sum(mg[a_] * mg[b_] / np.linalg.norm(xg[a_] - xg[b_]) for a_ in range(6) for b_ in range(a_ + 1, 6))
+    assert abs(0.5 * (mg * p).sum() - W_pairs) <= 1e-13 * abs(W_pairs)
+
+
+def test_irregular_jerk_is_time_derivative_along_prediction():
+    """With a = jerk = 0 the prediction is straight-line motion, so for fixed lists the
+    irregular jerk is d/dt of the irregular acceleration (Richardson central differences)."""
+    cl = W.plummer(2000, 45, masses="kroupa")
+    rs2 = W.neighbour_radius2(cl.x, 50, seed=45)
+    idx = np.arange(0, 2000, 13, dtype=np.int32)
+    _, _, _, _, lists = oracle.regular_force(cl.x, cl.v, cl.m, idx, rs2, cap=2000)
+    off, flat = _csr(lists)
+    z, tl = np.zeros_like(cl.x), np.zeros(2000)
+
+    def acc_at(t):
+        return oracle.irregular_force(t, cl.x, cl.v, z, z, tl, cl.m, idx, off, flat)[0]
+    _, j, _ = oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx, off, flat)
+    h = 1e-5
+    d1 = (acc_at(h) - acc_at(-h)) / (2 * h)
+    d2 = (acc_at(h / 2) - acc_at(-h / 2)) / h
+    rich = (4 * d2 - d1) / 3
+    has = off[1:] > off[:-1]
+    assert has.mean() > 0.5 and not rich[~has].any() and not j[~has].any()
+    e = np.linalg.norm(rich[has] - j[has], axis=1) / np.linalg.norm(j[has], axis=1)
+    assert np.median(e) < 1e-7 and e.max() < 1e-5
+
+
+def test_irregular_force_edge_cases():
+    cl = W.plummer(50, 46)
+    z, tl = np.zeros_like(cl.x), np.zeros(50)
+    idx = np.array([3, 7], np.int32)
+    # empty lists give zeros; i itself in its own list is skipped
+    a, j, p = oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx, np.array([0, 0, 2]), np.array([7, 9], np.int32))
+    assert not a[0].any() and not p[0]
+    a2, _, p2 = oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx[1:], np.array([0, 1]), np.array([9], np.int32))
+    np.testing.assert_array_equal(a[1], a2[0])
+    assert p[1] == p2[0]
+    with pytest.raises(IndexError):
+        oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx, np.array([0, 1, 2]), np.array([1, 50], np.int32))
+    with pytest.raises(IndexError):
+        oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx, np.array([0, 2, 1]), np.array([1, 2], np.int32))

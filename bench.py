@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-irregular", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: one warm-up and one timed predict + force call on the King cluster "
                          "(--n particles, --ni active, --prec), printing device times")
@@ -281,8 +282,7 @@ def main():
         rng = np.random.default_rng(0)
         sel = np.sort(rng.choice(BLOCKS[-1], 64, replace=False))
         full = outs[-1]
-        xp, vp = ctx.get_predicted()
-        xp_np, vp_np = xp.cpu().numpy(), vp.cpu().numpy()
+        xp_np, vp_np = oracle.predict(0.125, cl.x, cl.v, a0, j0, tl)  # the oracle's own predictor
         rows = order[:BLOCKS[-1]][sel]
         ref = oracle.regular_force(xp_np, vp_np, cl.m, rows, rs2, cap=NB_CAP, lists=False)
 
@@ -321,6 +321,8 @@ def main():
         extra["fp64_path"] = {"block": b64, "force_kernel_Ginteractions_s": fp64_rate,
                               "mixed_force_kernel_Ginteractions_s_same_block": mixed_rate,
                               "mixed_over_fp64": mixed_rate / fp64_rate}
+        if not args.no_irregular:
+            extra["irregular"] = bench_irregular(ctx, ctx64, cl, (a0, j0, tl), order, idx_dev, outs, rs2)
         ctx64.close()
 
     # end to end through the public API with host buffers (pinned), copies inside the timing
@@ -370,11 +372,12 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
-        xp, vp = ctx.get_predicted()
-        cl.x, cl.v = xp.cpu().numpy(), vp.cpu().numpy()
-        rate, _ = oracle_rate(cl, rs2, order[:32])
+        import types
+        xp_np, vp_np = oracle.predict(0.125, cl.x, cl.v, a0, j0, tl)
+        pred = types.SimpleNamespace(x=xp_np, v=vp_np, m=cl.m, n=cl.n)
+        rate, _ = oracle_rate(pred, rs2, order[:32])
         rows = int(max(32, min(BLOCKS[-1], 12.0 * rate / n)))  # ~12 s of oracle work
-        rate, dt = oracle_rate(cl, rs2, order[:rows])
+        rate, dt = oracle_rate(pred, rs2, order[:rows])
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"{rows} active rows (head of the sorted step list) x all {n} j, FP64 direct sum "
                          f"with neighbour lists, {dt:.1f} s"}
@@ -458,6 +461,61 @@ def run_profile_case(args):
             res["max_rel_acc_diff_vs_first"] = float(((out.acc - ref[0]).norm(dim=1) / ref[0].norm(dim=1)).max())
             res["same_neighbour_offsets"] = bool(torch.equal(out.nb_off, ref[1]))
         print(json.dumps(res))
+
+
+def bench_irregular(ctx, ctx64, cl, hermite, order, idx_dev, outs, rs2, reps=3):
+    """Irregular force (Sec. 3.2.2) of the 2^14, 2^17 and 2^20 blocks of the timed step over the
+    neighbour lists that step produced (cap 512), each active particle and its neighbours
+    predicted on load (neighbour-only prediction), in the mixed context and in an FP64 one;
+    then 32 sampled rows of the 2^20 block against the oracle with the oracle's own lists."""
+    import torch
+
+    import oracle
+    a0, j0, tl = hermite
+    t = 0.125
+    res = {"workload": "lists of the timed step (r_s for a median of 80, cap 512); i and its neighbours "
+                       "predicted from the Hermite state on load", "blocks": {}}
+    for q, b in enumerate(BLOCKS):
+        if b < BLOCKS[1]:
+            continue
+        off, nb = outs[q].nb_off, outs[q].nb_idx
+        pairs = int(off[-1].item())
+        row = {"neighbour_pairs": pairs}
+        for name, c in (("mixed", ctx), ("fp64", ctx64)):
+            c.irregular_force(t, idx_dev[q], off, nb)
+            c.sync()
+            c.timings()
+            c.set_timing(True)
+            for _ in range(reps):
+                c.irregular_force(t, idx_dev[q], off, nb)
+            ph = c.timings()
+            c.set_timing(False)
+            ms = ph["irregular"][0] / reps
+            row[name] = {"ms": ms, "Gpairs_s": pairs / (ms * 1e-3) / 1e9}
+        row["mixed_over_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+        res["blocks"][str(b)] = row
+    rng = np.random.default_rng(7)
+    rows = order[:BLOCKS[-1]][np.sort(rng.choice(BLOCKS[-1], 32, replace=False))]
+    xp, vp = oracle.predict(t, cl.x, cl.v, a0, j0, tl)
+    _, _, _, cnt, lists = oracle.regular_force(xp, vp, cl.m, rows, rs2, cap=NB_CAP)
+    off = np.zeros(rows.size + 1, np.int64)
+    off[1:] = np.cumsum([len(l) for l in lists])
+    flat = np.concatenate(lists).astype(np.int32)
+    ref = oracle.irregular_force(t, cl.x, cl.v, a0, j0, tl, cl.m, rows, off, flat)
+    has = cnt > 0
+    dev = idx_dev[0].device
+    T = lambda a_: torch.as_tensor(np.ascontiguousarray(a_), device=dev)
+    for name, c in (("mixed", ctx), ("fp64", ctx64)):
+        got = c.irregular_force(t, T(rows), T(off), T(flat))
+        c.sync()
+        e = {}
+        for k, (g, r) in enumerate(zip(got, ref)):
+            g = g.cpu().numpy()[has]
+            r = r[has]
+            d = np.linalg.norm(g - r, axis=1) / np.linalg.norm(r, axis=1) if g.ndim == 2 else np.abs(g - r) / np.abs(r)
+            e[("acc", "jerk", "pot")[k]] = {"median": float(np.median(d)), "max": float(d.max())}
+        res[f"error_vs_oracle_{name}_32_rows"] = e
+    return res
 
 
 def bench_ensemble(dev, steps=5, n_clusters=512):

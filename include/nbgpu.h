@@ -175,12 +175,36 @@ nb_status nb_regular_force_batched(nb_ctx *ctx, const int32_t *idx, const double
                                    double *jerk, double *pot, int64_t *nb_off, int32_t *nb_idx,
                                    int64_t nb_idx_capacity, int32_t *nb_count_true);
 
+/* Irregular force of the Ahmad-Cohen scheme (Sec. 2; Sec. 3.2.2): for the active rows
+ * idx[0..n_i), the sums of nb_regular_force restricted to each row's neighbour list,
+ *   acc_k = sum_{j in L_k, j != i} m_j r/|r|^3   (jerk and pot likewise),
+ * with L_k = nb_idx[nb_off[k] .. nb_off[k+1]) (any CSR list of particle indices; typically
+ * the one nb_regular_force returned).  Only i and its listed neighbours are predicted, from
+ * the Hermite state of nb_set_particles, to time t (neighbour-only prediction, Sec. 3.3.3);
+ * an FP64 context predicts with nb_predict's arithmetic, so the positions are bit-identical
+ * to predicting all particles.  The arithmetic follows the context precision (FP64, or the
+ * mixed scheme: double-single base differences, FP32 Taylor increments and pair terms,
+ * FP64 row sums).
+ * acc, jerk: (n_i, 3), pot: (n_i) double, overwritten.
+ * acc_reg, jerk_reg, pot_reg: all NULL, or all given; then on input the all-j sums of the
+ * same rows at the same time (from nb_regular_force) and on output the part from outside
+ * the lists (input minus the irregular sums): the regular force of the scheme.
+ * Requires nb_set_particles (NB_ERR_STATE after nb_set_predicted alone).  Host mode
+ * validates every index and offset (NB_ERR_ARG); device mode flags a bad one in the
+ * deferred status and writes zeros for that row. */
+nb_status nb_irregular_force(nb_ctx *ctx, double t, int64_t n_i, const int32_t *idx,
+                             const int64_t *nb_off, const int32_t *nb_idx, double *acc,
+                             double *jerk, double *pot, double *acc_reg, double *jerk_reg,
+                             double *pot_reg, int32_t on_device);
+
 /* Per-phase device timing: with timing enabled, every phase of every later call is
  * bracketed by CUDA events on the context stream.  nb_get_timings synchronises the
  * stream and returns, per phase, the summed device time in ms and the number of kernels
  * launched since the previous nb_get_timings (launch counts are kept even with timing
  * off), then resets both.  Phases: 0 predict, 1 force, 2 partial reduction,
- * 3 neighbour CSR, 4 backward.  ms and launches have 5 entries each. */
+ * 3 neighbour CSR, 4 backward, 5 irregular force.  ms and launches have NB_PHASES
+ * entries each. */
+#define NB_PHASES 6
 nb_status nb_set_timing(nb_ctx *ctx, int32_t enable);
 nb_status nb_get_timings(nb_ctx *ctx, double *ms, int64_t *launches);
 

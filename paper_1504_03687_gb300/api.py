@@ -29,7 +29,7 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
            "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
            "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
-           "nb_set_plan_table", "nb_set_source_range")
+           "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force")
 NB_SOURCE_ALIGN = 256
 
 
@@ -82,6 +82,7 @@ def load_library(build_if_needed: bool = True):
         "nb_batch_plan": (st, [P, i64, P, P, i32]),
         "nb_set_plan_table": (st, [P, i32, P, P, P, P]),
         "nb_set_source_range": (st, [P, i64, i64]),
+        "nb_irregular_force": (st, [P, dbl, i64, P, P, P, P, P, P, P, P, P, i32]),
         "nb_regular_force_batched": (st, [P, P, P, P, P, P, P, P, i64, P]),
         "nb_set_timing": (st, [P, i32]),
         "nb_get_timings": (st, [P, P, P]),
@@ -289,15 +290,53 @@ class Context:
         self._check(s, "nb_regular_force_backward")
         return gx, gv, gm
 
+    def irregular_force(self, t: float, idx, nb_off, nb_idx, regular: ForceResult | None = None):
+        """nb_irregular_force: (acc, jerk, pot) of the rows idx over their CSR neighbour lists,
+        i and its neighbours predicted to time t from the loaded Hermite state.  With
+        `regular` (the all-j result of regular_force for the same rows, same side), its
+        acc / jerk / pot are replaced in place by the part from outside the lists.  Device
+        tensors give device outputs (asynchronous), numpy arrays host outputs."""
+        torch = self._torch
+        on_dev = isinstance(idx, torch.Tensor) and idx.is_cuda
+        n_i = int(idx.shape[0])
+        reg = (regular.acc, regular.jerk, regular.pot) if regular is not None else (None, None, None)
+        if on_dev:
+            dev = idx.device
+            acc = torch.empty((n_i, 3), dtype=torch.float64, device=dev)
+            jerk = torch.empty_like(acc)
+            pot = torch.empty((n_i,), dtype=torch.float64, device=dev)
+            ptr = lambda q: q.data_ptr() if q is not None else None
+            self._bind_stream()
+            s = self.lib.nb_irregular_force(self.h, float(t), n_i, idx.data_ptr(), nb_off.data_ptr(),
+                                            nb_idx.data_ptr(), acc.data_ptr(), jerk.data_ptr(), pot.data_ptr(),
+                                            *[ptr(q) for q in reg], 1)
+            self._check(s, "nb_irregular_force")
+            return acc, jerk, pot
+        idx_np = np.ascontiguousarray(np.asarray(idx), dtype=np.int32)
+        off_np = np.ascontiguousarray(np.asarray(nb_off), dtype=np.int64)
+        nb_np = np.ascontiguousarray(np.asarray(nb_idx), dtype=np.int32)
+        if nb_np.size == 0:
+            nb_np = np.zeros(1, np.int32)
+        acc, jerk, pot = np.empty((n_i, 3)), np.empty((n_i, 3)), np.empty(n_i)
+        for q in reg:
+            if q is not None and not (isinstance(q, np.ndarray) and q.flags.c_contiguous and q.dtype == np.float64):
+                raise ValueError("regular results must be contiguous float64 numpy arrays in host mode")
+        self._bind_stream()
+        s = self.lib.nb_irregular_force(self.h, float(t), n_i, idx_np.ctypes.data, off_np.ctypes.data,
+                                        nb_np.ctypes.data, acc.ctypes.data, jerk.ctypes.data, pot.ctypes.data,
+                                        *[q.ctypes.data if q is not None else None for q in reg], 0)
+        self._check(s, "nb_irregular_force")
+        return acc, jerk, pot
+
     def set_timing(self, enable: bool = True):
         self._check(self.lib.nb_set_timing(self.h, 1 if enable else 0), "nb_set_timing")
 
-    PHASES = ("predict", "force", "reduce", "neighbours", "backward")
+    PHASES = ("predict", "force", "reduce", "neighbours", "backward", "irregular")
 
     def timings(self) -> dict:
         """{phase: (device ms, kernel launches)} since the last call; synchronises."""
-        ms = (ctypes.c_double * 5)()
-        ln = (ctypes.c_int64 * 5)()
+        ms = (ctypes.c_double * len(self.PHASES))()
+        ln = (ctypes.c_int64 * len(self.PHASES))()
         self._check(self.lib.nb_get_timings(self.h, ctypes.cast(ms, ctypes.c_void_p),
                                             ctypes.cast(ln, ctypes.c_void_p)), "nb_get_timings")
         return {p: (ms[q], ln[q]) for q, p in enumerate(self.PHASES)}

@@ -11,29 +11,6 @@
 
 namespace nbgpu {
 
-// acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] -= m/|r|
-__device__ __forceinline__ double pair_f64(const dvec4 &p0, const dvec4 &p1, const double (&xi)[3],
-                                           const double (&vi)[3], bool self, double *acc)
-{
-    const double rx = __dsub_rn(p0.x, xi[0]), ry = __dsub_rn(p0.y, xi[1]), rz = __dsub_rn(p0.z, xi[2]);
-    const double r2 = r2_f64(rx, ry, rz);
-    const double rinv = self ? 0.0 : rsqrt(r2);
-    const double wx = p1.x - vi[0], wy = p1.y - vi[1], wz = p1.z - vi[2];
-    const double rw = rx * wx + ry * wy + rz * wz;
-    const double rinv2 = rinv * rinv;
-    const double mr = p0.w * rinv;
-    const double mr3 = mr * rinv2;
-    const double beta = -3.0 * rw * rinv2;
-    acc[0] += mr3 * rx;
-    acc[1] += mr3 * ry;
-    acc[2] += mr3 * rz;
-    acc[3] += mr3 * (wx + beta * rx);
-    acc[4] += mr3 * (wy + beta * ry);
-    acc[5] += mr3 * (wz + beta * rz);
-    acc[6] -= mr;
-    return r2;
-}
-
 template <int BLOCK, int TJ>
 __global__ void __launch_bounds__(BLOCK) k_force_fp64_tiled(ForceArgs A)
 {

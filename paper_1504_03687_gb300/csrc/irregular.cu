@@ -1,0 +1,270 @@
+// irregular.cu — K10: the irregular force of the Ahmad-Cohen scheme (paper Sec. 2; Sec.
+// 3.2.2 "Prediction and irregular force").  For every active particle i, acceleration, jerk
+// and potential summed over its neighbour list only (a CSR list, e.g. the one the regular
+// force returned), with i and each listed neighbour predicted to the block time on load
+// from its Hermite state: the neighbour-only prediction of Sec. 3.3.3.  Optionally the same
+// pass splits a regular-force result of the same rows into its part from outside the lists
+// (all-j sums minus the irregular sums).
+//
+// Work: one warp per active row, the lanes striding over the row's list (lists hold tens to
+// hundreds of entries), a fixed xor-butterfly reduction over the lanes (results do not
+// depend on timing).  The gathers hit a per-particle state record (below) that a 2^20-body
+// system keeps within the 129 MB L2 (mixed) or mostly within it (FP64).
+//
+// Two precisions, as the context's:
+//  * FP64: the predictor is hermite_taylor, so a neighbour predicted here is bit-identical to
+//    the same particle after nb_predict; the pair is pair_f64.
+//  * mixed: r = (x_j - x_i) + (D_j - D_i) with the base difference in double-single (as in
+//    the mixed regular force) and the Taylor increments D = dt (v + dt (a/2 + dt jerk/6)) in
+//    FP32; likewise w = (v_j - v_i) + (E_j - E_i), E = dt (a + dt jerk/2).  dt = t - t_last
+//    is formed in double-single from hi/lo halves of t and t_last, so that small steps at
+//    late times keep their digits.  Pair arithmetic in FP32, lane sums in FP32 (at most a
+//    few dozen terms), the warp reduction in FP64.
+#include "nb_common.cuh"
+#include "nb_kernels.cuh"
+
+namespace nbgpu {
+
+// State records.
+//   FP64 : 4 dvec4  {x, y, z, t_last} {vx, vy, vz, m} {ax, ay, az, 0} {jx, jy, jz, 0}
+//   mixed: 5 float4 {xh, yh, zh, m} {xl, yl, zl, t_hi} {vx, vy, vz, t_lo} {ax, ay, az, 0}
+//                   {jx, jy, jz, 0}
+__global__ void k_pack_state(int64_t n, const double *__restrict__ x, const double *__restrict__ v,
+                             const double *__restrict__ a, const double *__restrict__ jk,
+                             const double *__restrict__ tl, const double *__restrict__ m, dvec4 *__restrict__ s64,
+                             float4 *__restrict__ s32)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *X = x + 3 * i, *V = v + 3 * i, *A = a + 3 * i, *J = jk + 3 * i;
+        if (s64) {
+            s64[4 * i] = make_dvec4(X[0], X[1], X[2], tl[i]);
+            s64[4 * i + 1] = make_dvec4(V[0], V[1], V[2], m[i]);
+            s64[4 * i + 2] = make_dvec4(A[0], A[1], A[2], 0.0);
+            s64[4 * i + 3] = make_dvec4(J[0], J[1], J[2], 0.0);
+        } else {
+            float h[3], l[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                h[c] = __double2float_rn(X[c]);
+                l[c] = __double2float_rn(X[c] - (double)h[c]);
+            }
+            const float th = __double2float_rn(tl[i]);
+            const float tlo = __double2float_rn(tl[i] - (double)th);
+            s32[5 * i] = make_float4(h[0], h[1], h[2], __double2float_rn(m[i]));
+            s32[5 * i + 1] = make_float4(l[0], l[1], l[2], th);
+            s32[5 * i + 2] = make_float4(__double2float_rn(V[0]), __double2float_rn(V[1]), __double2float_rn(V[2]), tlo);
+            s32[5 * i + 3] = make_float4(__double2float_rn(A[0]), __double2float_rn(A[1]), __double2float_rn(A[2]), 0.f);
+            s32[5 * i + 4] = make_float4(__double2float_rn(J[0]), __double2float_rn(J[1]), __double2float_rn(J[2]), 0.f);
+        }
+    }
+}
+
+struct IrrArgs {
+    const void *srec;
+    int64_t n, n_i;
+    const int32_t *idx;
+    const int64_t *off;
+    const int32_t *nb;
+    double t;
+    float t_hi, t_lo;
+    double *acc, *jerk, *pot;
+    double *acc_reg, *jerk_reg, *pot_reg;  // optional: all-j sums in, outside-list part out
+    unsigned *status;
+};
+
+// Row k's checked index and list range (an empty range and a status bit when malformed).
+__device__ __forceinline__ bool irr_row(const IrrArgs &A, int64_t k, int lane, int64_t &i, int64_t &e0, int64_t &e1)
+{
+    i = A.idx[k];
+    e0 = A.off[k];
+    e1 = A.off[k + 1];
+    const bool ok = i >= 0 && i < A.n && e0 >= 0 && e1 >= e0;
+    if (!ok) {
+        if (lane == 0) atomicOr(A.status, ST_BAD_INDEX);
+        e0 = e1 = 0;
+    }
+    return ok;
+}
+
+// Lanes 0..6 hold the row's seven sums after the butterfly: lane c writes component c and,
+// when asked, replaces the all-j value by the outside-list part.
+__device__ __forceinline__ void irr_store(const IrrArgs &A, int64_t k, int lane, const double (&s)[7], bool ok)
+{
+    if (lane >= 7) return;
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < 7; ++c)
+        if (lane == c) v = s[c];
+    if (!ok) v = 0.0;
+    double *out = lane < 3 ? A.acc + 3 * k + lane : lane < 6 ? A.jerk + 3 * k + (lane - 3) : A.pot + k;
+    *out = v;
+    if (A.acc_reg) {
+        double *reg = lane < 3 ? A.acc_reg + 3 * k + lane : lane < 6 ? A.jerk_reg + 3 * k + (lane - 3) : A.pot_reg + k;
+        *reg = __dsub_rn(*reg, v);
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_irregular_fp64(IrrArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * BLOCK) >> 5;
+    const dvec4 *S = static_cast<const dvec4 *>(A.srec);
+    for (int64_t k = w0; k < A.n_i; k += nw) {
+        int64_t i, e0, e1;
+        const bool ok = irr_row(A, k, lane, i, e0, e1);
+        // the active particle: lanes 0-2 predict x_p, lanes 3-5 v_p, one component each
+        double own = 0.0;
+        if (ok && lane < 6) {
+            const int c = lane < 3 ? lane : lane - 3;
+            const dvec4 P = S[4 * i], V = S[4 * i + 1], Ac = S[4 * i + 2], J = S[4 * i + 3];
+            auto pick = [c](const dvec4 &q) { return c == 0 ? q.x : (c == 1 ? q.y : q.z); };
+            double xp, vp;
+            hermite_taylor(pick(P), pick(V), pick(Ac), pick(J), __dsub_rn(A.t, P.w), xp, vp);
+            own = lane < 3 ? xp : vp;
+        }
+        double xi[3], vi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xi[c] = __shfl_sync(0xffffffffu, own, c);
+            vi[c] = __shfl_sync(0xffffffffu, own, 3 + c);
+        }
+        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int64_t j = A.nb[e];
+            if (j < 0 || j >= A.n) {
+                atomicOr(A.status, ST_BAD_INDEX);
+                continue;
+            }
+            if (j == i) continue;
+            const dvec4 P = S[4 * j], V = S[4 * j + 1], Ac = S[4 * j + 2], J = S[4 * j + 3];
+            const double dt = __dsub_rn(A.t, P.w);
+            double x0, x1, x2, v0, v1, v2;
+            hermite_taylor(P.x, V.x, Ac.x, J.x, dt, x0, v0);
+            hermite_taylor(P.y, V.y, Ac.y, J.y, dt, x1, v1);
+            hermite_taylor(P.z, V.z, Ac.z, J.z, dt, x2, v2);
+            pair_f64(make_dvec4(x0, x1, x2, V.w), make_dvec4(v0, v1, v2, 0.0), xi, vi, false, s);
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) s[c] = warp_sum(s[c]);
+        irr_store(A, k, lane, s, ok);
+    }
+}
+
+// Taylor increments of the mixed path: D = dt (v + dt (a/2 + dt jerk/6)), E = dt (a + dt jerk/2).
+__device__ __forceinline__ void incr_f32(float v, float a, float j, float dt, float &D, float &E)
+{
+    constexpr float kSixth = 1.f / 6.f;
+    D = __fmul_rn(dt, __fmaf_rn(dt, __fmaf_rn(dt, __fmul_rn(j, kSixth), __fmul_rn(a, 0.5f)), v));
+    E = __fmul_rn(dt, __fmaf_rn(dt, __fmul_rn(j, 0.5f), a));
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_irregular_mixed(IrrArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * BLOCK) >> 5;
+    const float4 *S = static_cast<const float4 *>(A.srec);
+    for (int64_t k = w0; k < A.n_i; k += nw) {
+        int64_t i, e0, e1;
+        const bool ok = irr_row(A, k, lane, i, e0, e1);
+        float ih[3] = {0, 0, 0}, il[3] = {0, 0, 0}, iv[3] = {0, 0, 0}, iD[3] = {0, 0, 0}, iE[3] = {0, 0, 0};
+        if (ok) {
+            const float4 P = S[5 * i], L = S[5 * i + 1], V = S[5 * i + 2], Ac = S[5 * i + 3], J = S[5 * i + 4];
+            const float dt = __fadd_rn(__fsub_rn(A.t_hi, L.w), __fsub_rn(A.t_lo, V.w));
+            ih[0] = P.x; ih[1] = P.y; ih[2] = P.z;
+            il[0] = L.x; il[1] = L.y; il[2] = L.z;
+            iv[0] = V.x; iv[1] = V.y; iv[2] = V.z;
+            incr_f32(V.x, Ac.x, J.x, dt, iD[0], iE[0]);
+            incr_f32(V.y, Ac.y, J.y, dt, iD[1], iE[1]);
+            incr_f32(V.z, Ac.z, J.z, dt, iD[2], iE[2]);
+        }
+        float f[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int64_t j = A.nb[e];
+            if (j < 0 || j >= A.n) {
+                atomicOr(A.status, ST_BAD_INDEX);
+                continue;
+            }
+            if (j == i) continue;
+            const float4 P = S[5 * j], L = S[5 * j + 1], V = S[5 * j + 2], Ac = S[5 * j + 3], J = S[5 * j + 4];
+            const float dt = __fadd_rn(__fsub_rn(A.t_hi, L.w), __fsub_rn(A.t_lo, V.w));
+            const float ph[3] = {P.x, P.y, P.z}, pl[3] = {L.x, L.y, L.z}, pv[3] = {V.x, V.y, V.z},
+                        pa[3] = {Ac.x, Ac.y, Ac.z}, pj[3] = {J.x, J.y, J.z};
+            float r[3], w[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float D, E;
+                incr_f32(pv[c], pa[c], pj[c], dt, D, E);
+                r[c] = __fadd_rn(ds_diff(ph[c], pl[c], ih[c], il[c]), __fsub_rn(D, iD[c]));
+                w[c] = __fadd_rn(__fsub_rn(pv[c], iv[c]), __fsub_rn(E, iE[c]));
+            }
+            const float r2 = r2_f32(r[0], r[1], r[2]);
+            const float rinv = rsqrtf(r2);
+            const float rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+            const float rinv2 = rinv * rinv;
+            const float mr = P.w * rinv;
+            const float mr3 = mr * rinv2;
+            const float beta = rw * (rinv2 * -3.f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f[c] += mr3 * r[c];
+                f[3 + c] += mr3 * (w[c] + beta * r[c]);
+            }
+            f[6] -= mr;
+        }
+        double s[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) s[c] = warp_sum((double)f[c]);
+        irr_store(A, k, lane, s, ok);
+    }
+}
+
+constexpr int kIrrBlock = 256;
+
+void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
+                       const double *jk, const double *tl, const double *m, void *srec)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_pack_state<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(n, x, v, a, jk, tl, m,
+                                                         precision == 0 ? (dvec4 *)srec : nullptr,
+                                                         precision == 0 ? nullptr : (float4 *)srec);
+}
+
+size_t state_record_bytes(int precision, int64_t n) { return (size_t)n * (precision == 0 ? 4 * 32 : 5 * 16); }
+
+void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int64_t n, double t,
+                      int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
+                      double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status)
+{
+    IrrArgs A;
+    A.srec = srec;
+    A.n = n;
+    A.n_i = n_i;
+    A.idx = idx;
+    A.off = off;
+    A.nb = nb;
+    A.t = t;
+    A.t_hi = (float)t;
+    A.t_lo = (float)(t - (double)A.t_hi);
+    A.acc = acc;
+    A.jerk = jerk;
+    A.pot = pot;
+    A.acc_reg = acc_reg;
+    A.jerk_reg = jerk_reg;
+    A.pot_reg = pot_reg;
+    A.status = status;
+    constexpr int rows_per_cta = kIrrBlock / 32;
+    int64_t g = (n_i + rows_per_cta - 1) / rows_per_cta;
+    const int64_t gmax = (int64_t)num_sms * 8;  // 8 CTAs of 8 warps: 64 warps per SM
+    if (g > gmax) g = gmax;
+    if (precision == 0)
+        k_irregular_fp64<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);
+    else
+        k_irregular_mixed<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);
+}
+
+}  // namespace nbgpu

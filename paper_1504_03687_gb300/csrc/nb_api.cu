@@ -39,6 +39,12 @@ size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms,
 int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx, int64_t n_i,
                    const double *g_acc, const double *g_jerk, const double *g_pot, double *g_x, double *g_v,
                    double *g_m, void *scratch, unsigned *status, int num_sms);
+size_t state_record_bytes(int precision, int64_t n);
+void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
+                       const double *jk, const double *tl, const double *m, void *srec);
+void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int64_t n, double t,
+                      int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
+                      double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status);
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
@@ -73,6 +79,8 @@ struct nb_ctx {
     int64_t *scan = nullptr; size_t scan_cap = 0;
     char *stage = nullptr; size_t stage_cap = 0;
     char *adj = nullptr; size_t adj_cap = 0;
+    void *srec = nullptr; size_t srec_cap = 0;  // Hermite-state records of the irregular force
+    bool srec_valid = false;
     // batched ensemble plan (nb_batch_plan)
     void *b_items = nullptr; size_t b_items_cap = 0;
     int64_t *b_cluster_off = nullptr; size_t b_cluster_off_cap = 0;
@@ -90,7 +98,7 @@ struct nb_ctx {
     int64_t launches[8] = {0};
 };
 
-enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_COUNT = 5 };
+enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_IRREGULAR = 5, PH_COUNT = 6 };
 
 static cudaEvent_t ev_take(nb_ctx *c)
 {
@@ -185,7 +193,8 @@ static nb_status check_usable(nb_ctx *c)
 
 static nb_status status_from_flags(nb_ctx *c, unsigned f)
 {
-    if (f & ST_BAD_INDEX) return fail(c, NB_ERR_ARG, "an active index was outside [0, n)");
+    if (f & ST_BAD_INDEX)
+        return fail(c, NB_ERR_ARG, "an active or neighbour index was outside [0, n), or CSR offsets decreased");
     if (f & ST_DUP_INDEX) return fail(c, NB_ERR_ARG, "an active index appears more than once");
     if (f & ST_TIMEOUT) return fail(c, NB_ERR_TIMEOUT, "a bounded device-side wait expired");
     if (f & ST_DEVICE) return fail(c, NB_ERR_DEVICE, "a device-side consistency check failed");
@@ -476,7 +485,7 @@ nb_status nb_free(nb_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
                     c->part, c->seg_slots, c->seg_cnt, c->row_total, c->scan, c->stage, c->adj, c->b_items,
-                    c->b_cluster_off};
+                    c->b_cluster_off, c->srec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -522,6 +531,7 @@ nb_status nb_set_particles(nb_ctx *c, int64_t n, const double *x, const double *
     c->n = n;
     c->n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
     c->have_state = true;
+    c->srec_valid = false;
     c->have_pred = false;
     if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     return NB_OK;
@@ -854,6 +864,86 @@ nb_status nb_regular_force_backward(nb_ctx *c, int64_t n_i, const int32_t *idx, 
     CK(cudaMemcpyAsync(g_x, d_gx, (size_t)n * 24, cudaMemcpyDeviceToHost, c->stream), "copy g_x");
     CK(cudaMemcpyAsync(g_v, d_gv, (size_t)n * 24, cudaMemcpyDeviceToHost, c->stream), "copy g_v");
     CK(cudaMemcpyAsync(g_m, d_gm, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream), "copy g_m");
+    return sync_and_collect(c);
+}
+
+nb_status nb_irregular_force(nb_ctx *c, double t, int64_t n_i, const int32_t *idx, const int64_t *nb_off,
+                             const int32_t *nb_idx, double *acc, double *jerk, double *pot, double *acc_reg,
+                             double *jerk_reg, double *pot_reg, int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!c->have_state) return fail(c, NB_ERR_STATE, "nb_irregular_force needs the Hermite state of nb_set_particles");
+    if (n_i < 0 || n_i > (int64_t)INT32_MAX) return fail(c, NB_ERR_ARG, "n_i=%lld out of range", (long long)n_i);
+    const int nreg = (acc_reg != nullptr) + (jerk_reg != nullptr) + (pot_reg != nullptr);
+    if (nreg != 0 && nreg != 3) return fail(c, NB_ERR_ARG, "acc_reg, jerk_reg and pot_reg: all three or none");
+    if (n_i == 0) return NB_OK;
+    if (!idx || !nb_off || !nb_idx || !acc || !jerk || !pot) return fail(c, NB_ERR_ARG, "null array");
+    const int64_t n = c->n;
+    cudaEvent_t t0 = span_begin(c);
+    int kernels = 1;
+    if (!c->srec_valid) {
+        if ((s = grow(c, &c->srec, &c->srec_cap, state_record_bytes(c->precision, n), "state records")) != NB_OK)
+            return s;
+        launch_pack_state(c->stream, c->precision, n, c->x, c->v, c->a, c->jk, c->tl, c->m, c->srec);
+        CK_LAUNCH("k_pack_state launch");
+        c->srec_valid = true;
+        kernels = 2;
+    }
+    const int32_t *d_idx = idx, *d_nb = nb_idx;
+    const int64_t *d_off = nb_off;
+    double *d_acc = acc, *d_jerk = jerk, *d_pot = pot, *d_ar = acc_reg, *d_jr = jerk_reg, *d_pr = pot_reg;
+    if (!on_device) {
+        // host mode: validate the rows and lists on the host and stage them
+        if (nb_off[0] < 0) return fail(c, NB_ERR_ARG, "nb_off[0]=%lld < 0", (long long)nb_off[0]);
+        for (int64_t k = 0; k < n_i; ++k) {
+            if (idx[k] < 0 || idx[k] >= n) return fail(c, NB_ERR_ARG, "idx[%lld]=%d outside [0, %lld)", (long long)k, idx[k], (long long)n);
+            if (nb_off[k + 1] < nb_off[k]) return fail(c, NB_ERR_ARG, "nb_off decreases at row %lld", (long long)k);
+        }
+        const int64_t tot = nb_off[n_i];
+        for (int64_t e = 0; e < tot; ++e)
+            if (nb_idx[e] < 0 || nb_idx[e] >= n) return fail(c, NB_ERR_ARG, "nb_idx[%lld]=%d outside [0, %lld)", (long long)e, nb_idx[e], (long long)n);
+        const size_t bytes = 256 * 10 + (size_t)n_i * 4 + ((size_t)n_i + 1) * 8 + (size_t)tot * 4 +
+                             (size_t)n_i * 56 * (nreg ? 2 : 1);
+        if ((s = grow(c, (void **)&c->stage, &c->stage_cap, bytes, "staging buffer")) != NB_OK) return s;
+        char *p = c->stage;
+        auto take = [&](size_t b) {
+            char *q = p;
+            p += (b + 255) & ~(size_t)255;
+            return q;
+        };
+        d_idx = (int32_t *)take((size_t)n_i * 4);
+        d_off = (int64_t *)take(((size_t)n_i + 1) * 8);
+        d_nb = (int32_t *)take((size_t)tot * 4 + 4);
+        d_acc = (double *)take((size_t)n_i * 24);
+        d_jerk = (double *)take((size_t)n_i * 24);
+        d_pot = (double *)take((size_t)n_i * 8);
+        CK(cudaMemcpyAsync((void *)d_idx, idx, (size_t)n_i * 4, cudaMemcpyHostToDevice, c->stream), "copy idx");
+        CK(cudaMemcpyAsync((void *)d_off, nb_off, ((size_t)n_i + 1) * 8, cudaMemcpyHostToDevice, c->stream), "copy nb_off");
+        if (tot > 0)
+            CK(cudaMemcpyAsync((void *)d_nb, nb_idx, (size_t)tot * 4, cudaMemcpyHostToDevice, c->stream), "copy nb_idx");
+        if (nreg) {
+            d_ar = (double *)take((size_t)n_i * 24);
+            d_jr = (double *)take((size_t)n_i * 24);
+            d_pr = (double *)take((size_t)n_i * 8);
+            CK(cudaMemcpyAsync(d_ar, acc_reg, (size_t)n_i * 24, cudaMemcpyHostToDevice, c->stream), "copy acc_reg");
+            CK(cudaMemcpyAsync(d_jr, jerk_reg, (size_t)n_i * 24, cudaMemcpyHostToDevice, c->stream), "copy jerk_reg");
+            CK(cudaMemcpyAsync(d_pr, pot_reg, (size_t)n_i * 8, cudaMemcpyHostToDevice, c->stream), "copy pot_reg");
+        }
+    }
+    launch_irregular(c->stream, c->precision, c->num_sms, c->srec, n, t, n_i, d_idx, d_off, d_nb, d_acc, d_jerk, d_pot,
+                     d_ar, d_jr, d_pr, c->status);
+    CK_LAUNCH("irregular force launch");
+    span_end(c, PH_IRREGULAR, t0, kernels);
+    if (on_device) return NB_OK;
+    CK(cudaMemcpyAsync(acc, d_acc, (size_t)n_i * 24, cudaMemcpyDeviceToHost, c->stream), "copy acc");
+    CK(cudaMemcpyAsync(jerk, d_jerk, (size_t)n_i * 24, cudaMemcpyDeviceToHost, c->stream), "copy jerk");
+    CK(cudaMemcpyAsync(pot, d_pot, (size_t)n_i * 8, cudaMemcpyDeviceToHost, c->stream), "copy pot");
+    if (nreg) {
+        CK(cudaMemcpyAsync(acc_reg, d_ar, (size_t)n_i * 24, cudaMemcpyDeviceToHost, c->stream), "copy acc_reg");
+        CK(cudaMemcpyAsync(jerk_reg, d_jr, (size_t)n_i * 24, cudaMemcpyDeviceToHost, c->stream), "copy jerk_reg");
+        CK(cudaMemcpyAsync(pot_reg, d_pr, (size_t)n_i * 8, cudaMemcpyDeviceToHost, c->stream), "copy pot_reg");
+    }
     return sync_and_collect(c);
 }
 

@@ -60,6 +60,46 @@ __device__ __forceinline__ double r2_f64(double rx, double ry, double rz)
     return __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
 }
 
+// ---- the Hermite predictor -----------------------------------------------------------------
+// The Taylor polynomial to the jerk term (Sec. 3.3.3) in Horner form with fused multiply-adds
+// (FP64 is a scarce pipe on GB300, so the divisions of the term-by-term form become constant
+// factors):
+//   x_p = x + dt (v + dt (a/2 + dt jerk/6)),   v_p = v + dt (a + dt jerk/2)
+// Every kernel that predicts calls this one function, so a particle predicted by the
+// all-particle predictor and one predicted on load by the irregular force are bit-identical.
+__device__ __forceinline__ void hermite_taylor(double x, double v, double a, double j, double dt, double &xp,
+                                               double &vp)
+{
+    constexpr double kSixth = 1.0 / 6.0;
+    xp = __fma_rn(dt, __fma_rn(dt, __fma_rn(dt, j * kSixth, a * 0.5), v), x);
+    vp = __fma_rn(dt, __fma_rn(dt, j * 0.5, a), v);
+}
+
+// ---- one FP64 pair --------------------------------------------------------------------------
+// p0 = {x_j, m_j}, p1 = {v_j, -} (predicted), xi, vi the predicted active particle:
+// acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] -= m/|r|
+__device__ __forceinline__ double pair_f64(const dvec4 &p0, const dvec4 &p1, const double (&xi)[3],
+                                           const double (&vi)[3], bool self, double *acc)
+{
+    const double rx = __dsub_rn(p0.x, xi[0]), ry = __dsub_rn(p0.y, xi[1]), rz = __dsub_rn(p0.z, xi[2]);
+    const double r2 = r2_f64(rx, ry, rz);
+    const double rinv = self ? 0.0 : rsqrt(r2);
+    const double wx = p1.x - vi[0], wy = p1.y - vi[1], wz = p1.z - vi[2];
+    const double rw = rx * wx + ry * wy + rz * wz;
+    const double rinv2 = rinv * rinv;
+    const double mr = p0.w * rinv;
+    const double mr3 = mr * rinv2;
+    const double beta = -3.0 * rw * rinv2;
+    acc[0] += mr3 * rx;
+    acc[1] += mr3 * ry;
+    acc[2] += mr3 * rz;
+    acc[3] += mr3 * (wx + beta * rx);
+    acc[4] += mr3 * (wy + beta * ry);
+    acc[5] += mr3 * (wz + beta * rz);
+    acc[6] -= mr;
+    return r2;
+}
+
 // ---- warp reductions ---------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)

@@ -9,18 +9,9 @@
 
 namespace nbgpu {
 
-// The Taylor polynomial in Horner form with fused multiply-adds (FP64 is a scarce pipe on
-// GB300, so the divisions of the term-by-term form become constant factors):
-//   x_p = x + dt (v + dt (a/2 + dt jerk/6)),   v_p = v + dt (a + dt jerk/2)
-// The operation order is fixed, so every replica of the state predicts bit-identically;
-// against a term-by-term evaluation the results agree to a few units in the last place.
-__device__ __forceinline__ void taylor(double x, double v, double a, double j, double dt,
-                                       double &xp, double &vp)
-{
-    constexpr double kSixth = 1.0 / 6.0;
-    xp = __fma_rn(dt, __fma_rn(dt, __fma_rn(dt, j * kSixth, a * 0.5), v), x);
-    vp = __fma_rn(dt, __fma_rn(dt, j * 0.5, a), v);
-}
+// The predictor is hermite_taylor (nb_common.cuh).  Its operation order is fixed, so every
+// replica of the state predicts bit-identically; against a term-by-term evaluation the
+// results agree to a few units in the last place.
 
 __device__ __forceinline__ void write_records(int64_t i, double x, double y, double z, double vx,
                                               double vy, double vz, double m, dvec4 *rec64,
@@ -71,7 +62,7 @@ __global__ void k_predict(int64_t n, int64_t n_pad, double t, const double *__re
         const double dt = __dsub_rn(t, tl[i]);
         double p[3], q[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) taylor(x[3 * i + c], v[3 * i + c], a[3 * i + c], jk[3 * i + c], dt, p[c], q[c]);
+        for (int c = 0; c < 3; ++c) hermite_taylor(x[3 * i + c], v[3 * i + c], a[3 * i + c], jk[3 * i + c], dt, p[c], q[c]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             xp[3 * i + c] = p[c];

@@ -7,7 +7,8 @@ Bars (written here, per particle i):
               neighbour lists identical (same FP64 distance arithmetic).
   mixed path  median e_i <= 2e-6 and max e_i <= 1e-4 for acc, jerk and pot;
               neighbour sets identical outside a 1e-6 relative band around r_s.
-  predictor   bit-identical to the oracle (same IEEE operation order).
+  predictor   within 4 ulp of the sum of the term magnitudes of the oracle's term-by-term
+              Taylor sum (the GPU evaluates the same polynomial in Horner form with FMA).
 """
 import math
 

@@ -430,3 +430,28 @@ def king_1m_binaries(seed: int = 2, n: int = 1 << 20):
 def plummer_64k_kroupa(seed: int = 3):
     cl = plummer(65536, seed, masses="kroupa")
     return cl, neighbour_radius2(cl.x, 80, seed=seed)
+
+
+# --------------------------------------------------------------------------
+# Step levels for the block-step scheduler
+# --------------------------------------------------------------------------
+def step_levels(steps: np.ndarray) -> np.ndarray:
+    """Level k of each power-of-two step 2^-k (int32)."""
+    k = np.rint(-np.log2(steps)).astype(np.int32)
+    if not np.all(np.ldexp(1.0, -k) == steps):
+        raise ValueError("steps must be integer powers of two")
+    return k
+
+
+def level_requests(levels: np.ndarray, seed: int, p_double: float = 0.2, p_halve: float = 0.15,
+                   p_halve2: float = 0.05) -> np.ndarray:
+    """Seeded requested next levels for the particles of one block step: a stand-in for the
+    step criterion of the integrator, which asks for a larger step (level - 1), a smaller one
+    (level + 1 or + 2) or the same.  Whether a request is granted is the scheduler's rule."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(levels.shape[0])
+    d = np.zeros(levels.shape[0], np.int32)
+    d[u < p_double] = -1
+    d[(u >= p_double) & (u < p_double + p_halve)] = 1
+    d[(u >= p_double + p_halve) & (u < p_double + p_halve + p_halve2)] = 2
+    return (levels + d).astype(np.int32)

@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-irregular", action="store_true")
+    ap.add_argument("--no-scheduler", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: one warm-up and one timed predict + force call on the King cluster "
                          "(--n particles, --ni active, --prec), printing device times")
@@ -323,6 +324,8 @@ def main():
                               "mixed_over_fp64": mixed_rate / fp64_rate}
         if not args.no_irregular:
             extra["irregular"] = bench_irregular(ctx, ctx64, cl, (a0, j0, tl), order, idx_dev, outs, rs2)
+        if not args.no_scheduler:
+            extra["scheduler"] = bench_scheduler(dev, cl)
         ctx64.close()
 
     # end to end through the public API with host buffers (pinned), copies inside the timing
@@ -516,6 +519,65 @@ def bench_irregular(ctx, ctx64, cl, hermite, order, idx_dev, outs, rs2, reps=3):
             e[("acc", "jerk", "pot")[k]] = {"median": float(np.median(d)), "max": float(d.max())}
         res[f"error_vs_oracle_{name}_32_rows"] = e
     return res
+
+
+def bench_scheduler(dev, cl, steps=512, parity_steps=16):
+    """Block-step sorting list (Sec. 3.3.1) on the 2^20-particle King cluster: levels from the
+    local dynamical time (steps 2^-12 .. 2^-3), `steps` block steps with seeded level requests
+    (a stand-in for the step criterion), timed on the host clock around nb_sched_next +
+    nb_sched_update (which synchronises).  The first `parity_steps` steps are replayed by the
+    reference scheduler with the same requests and the lists compared."""
+    import torch
+
+    import workloads as W
+    from oracle.sorting_list import SortingList
+    from paper_1504_03687_gb300 import Scheduler
+    lv = W.step_levels(W.block_steps(cl, seed=2, dt_min=0.5 ** 12, dt_max=0.5 ** 3))
+    # parity: the first steps against the reference, with requests from the reference's state
+    ref = SortingList(lv, level_min=3, level_max=12, tick_level=48)
+    sch = Scheduler(lv, 3, 12, device=dev.index or 0)
+    t_ref = 0.0
+    for k in range(parity_steps):
+        t0 = time.perf_counter()
+        T, act = ref.next()
+        want = W.level_requests(ref.level[ref.order[:act.size]], seed=9000 + k)
+        ref.update(want)
+        t_ref += time.perf_counter() - t0
+        sch.next()
+        sch.update(want, granted=False)
+    lst, lev, _ = sch.get()
+    parity = bool(np.array_equal(lst, ref.order) and np.array_equal(lev, ref.level))
+    sch.close()
+    # timing: requests made on the device from the current levels (torch), not timed
+    sch = Scheduler(lv, 3, 12, device=dev.index or 0)
+    lev_t = torch.as_tensor(lv, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    delta = torch.tensor([-1, 0, 0, 0, 1, 2], dtype=torch.int32, device=dev)
+    t_sched, part_steps, sizes = 0.0, 0, []
+    for k in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t, na = sch.next()
+        t_sched += time.perf_counter() - t0
+        idx = sch.active().clone()
+        want = lev_t[idx] + delta[torch.randint(0, 6, (na,), device=dev, generator=gen)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        granted = sch.update(want)
+        t_sched += time.perf_counter() - t0
+        lev_t[idx] = granted
+        part_steps += na
+        sizes.append(na)
+    sch.close()
+    return {"workload": "King W0=6 N=2^20, levels 3..12 from the local dynamical time, requests level "
+                        "-1/0/+1/+2 with probabilities 1/6, 1/2, 1/6, 1/6",
+            "block_steps": steps, "particle_steps": part_steps,
+            "active_min": int(min(sizes)), "active_median": float(np.median(sizes)), "active_max": int(max(sizes)),
+            "gpu_ms_total": t_sched * 1e3, "us_per_block_step": t_sched * 1e6 / steps,
+            "ns_per_particle_step": t_sched * 1e9 / part_steps,
+            "reference_us_per_block_step_first_steps": t_ref * 1e6 / parity_steps,
+            "parity_with_reference_first_steps": parity, "parity_steps": parity_steps}
 
 
 def bench_ensemble(dev, steps=5, n_clusters=512):

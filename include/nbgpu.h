@@ -270,6 +270,57 @@ nb_status nb_regular_force_noalloc(int64_t n, const double *xp, const double *vp
                                    int64_t n_i, const int32_t *idx, double *acc, double *jerk,
                                    double *pot, void *stream, char *err, int32_t err_len);
 
+/* ---------------------------------------------------------------------------------------
+ * Block-step scheduler: the time-step sorting list of Sec. 3.3.1.
+ *
+ * Particle i has a level L_i (step 2^-L_i, Sec. 2: steps are integer powers of 1/2) and is
+ * advanced at every multiple of its step; all particles start at time 0.  The scheduler
+ * keeps the device list of all particle indices sorted by step, smallest first (level
+ * descending), and the number of particles per level (the boundary offsets of the list).
+ * nb_sched_next moves to the next block time, T + (smallest step), and reports the active
+ * particles: all those whose step divides the new time, which are the first n_active
+ * entries of the list.  nb_sched_update then takes the levels the integrator requests for
+ * them and applies the block rule: a request is clamped to [level_min, level_max], a larger
+ * step than twice the current one is cut to one doubling, and a doubling is granted only
+ * when the block time is a multiple of the doubled step (else the level stays).  Only the
+ * first n_active entries are re-sorted (O(N_i), stable: ties keep their list order), so the
+ * result is deterministic.  Times are exact multiples of 2^-48.
+ * --------------------------------------------------------------------------------------- */
+typedef struct nb_sched nb_sched;
+
+/* Create a scheduler for n particles with initial levels (n) int32 in [level_min,
+ * level_max], 0 <= level_min <= level_max <= 48, on `device`, running on `stream` (a
+ * cudaStream_t; NULL = a stream the scheduler creates).  Levels are read from host memory,
+ * or device memory when on_device != 0.  NB_ERR_ARG on a level outside the range. */
+nb_status nb_sched_init(nb_sched **out, int64_t n, const int32_t *levels, int32_t level_min,
+                        int32_t level_max, int32_t device, void *stream, int32_t on_device);
+
+/* Destroy a scheduler.  Safe on NULL. */
+nb_status nb_sched_free(nb_sched *s);
+
+/* Advance to the next block time (host only, O(levels)): *t_block receives the time, and
+ * *n_active the number of active particles, which are (*d_list)[0 .. n_active) — *d_list is
+ * the device list (n int32 entries), valid until the next nb_sched_update, and may serve
+ * directly as the idx of nb_regular_force.  NB_ERR_STATE if the previous block step has
+ * not been committed with nb_sched_update. */
+nb_status nb_sched_next(nb_sched *s, double *t_block, int64_t *n_active, const int32_t **d_list);
+
+/* Commit the block step: want (n_active) int32, in list order, holds the requested levels;
+ * granted (n_active, optional) receives the levels granted by the block rule, in the same
+ * order.  Host pointers when on_device = 0, else device pointers.  Re-sorts the active
+ * part of the list; synchronises the scheduler's stream (the level counts come back). */
+nb_status nb_sched_update(nb_sched *s, const int32_t *want, int32_t *granted, int32_t on_device);
+
+/* Copy out the whole list and/or the level of every particle (n int32 each; either may
+ * be NULL) and the time of the last committed block step.  Synchronises. */
+nb_status nb_sched_get(nb_sched *s, int32_t *list, int32_t *levels, double *t_now, int32_t on_device);
+
+/* Particles per level, counts[64] (index = level), as of the last committed step. */
+nb_status nb_sched_counts(const nb_sched *s, int64_t *counts);
+
+/* One-line description of the last error of this scheduler (never NULL). */
+const char *nb_sched_last_error(const nb_sched *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,9 +3,10 @@
 The regular-force step of Wang et al. (2015): FP64 prediction of all particles,
 then for every particle of an active block the acceleration, jerk and potential
 from all N particles and the neighbour list inside r_s, computed by hand-written
-CUDA kernels behind a C ABI (include/nbgpu.h).  This package is the thin Python
-binding (argument marshalling only).
+CUDA kernels behind a C ABI (include/nbgpu.h); around it the irregular force over the
+neighbour lists, the adjoint, the batched ensemble form and the block-step sorting list.
+This package is the thin Python binding (argument marshalling only).
 """
-from .api import Context, ForceResult, NBError, NBOverflow, load_library, plan_for  # noqa: F401
+from .api import Context, ForceResult, NBError, NBOverflow, Scheduler, load_library, plan_for  # noqa: F401
 
-__all__ = ["Context", "ForceResult", "NBError", "NBOverflow", "load_library", "plan_for"]
+__all__ = ["Context", "ForceResult", "NBError", "NBOverflow", "Scheduler", "load_library", "plan_for"]

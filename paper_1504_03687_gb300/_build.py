@@ -27,7 +27,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # 1e-19 apart) so that rsqrtf is a single hardware instruction
 EXTRA = {"force_mixed.cu": ["-ftz=true"], "adjoint.cu": ["-ftz=true"], "irregular.cu": ["-ftz=true"]}
 SOURCES = ["nb_api.cu", "predict.cu", "force_mixed.cu", "force_fp64.cu", "neighbours.cu", "adjoint.cu",
-           "noalloc.cu", "irregular.cu"]
+           "noalloc.cu", "irregular.cu", "sched.cu"]
 
 
 def _nvcc() -> str:

@@ -29,7 +29,8 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
            "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
            "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
-           "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force")
+           "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force", "nb_sched_init", "nb_sched_free",
+           "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error")
 NB_SOURCE_ALIGN = 256
 
 
@@ -82,6 +83,13 @@ def load_library(build_if_needed: bool = True):
         "nb_batch_plan": (st, [P, i64, P, P, i32]),
         "nb_set_plan_table": (st, [P, i32, P, P, P, P]),
         "nb_set_source_range": (st, [P, i64, i64]),
+        "nb_sched_init": (st, [ctypes.POINTER(P), i64, P, i32, i32, i32, P, i32]),
+        "nb_sched_free": (st, [P]),
+        "nb_sched_next": (st, [P, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(P)]),
+        "nb_sched_update": (st, [P, P, P, i32]),
+        "nb_sched_get": (st, [P, P, P, ctypes.POINTER(dbl), i32]),
+        "nb_sched_counts": (st, [P, P]),
+        "nb_sched_last_error": (ctypes.c_char_p, [P]),
         "nb_irregular_force": (st, [P, dbl, i64, P, P, P, P, P, P, P, P, P, i32]),
         "nb_regular_force_batched": (st, [P, P, P, P, P, P, P, P, i64, P]),
         "nb_set_timing": (st, [P, i32]),
@@ -412,3 +420,98 @@ class Context:
     def set_plan_override(self, kernel: int = -1, variant: int = 0, splits: int = 1):
         """Force (kernel, variant, splits) for later regular_force calls; kernel < 0 = automatic."""
         self._check(self.lib.nb_set_plan_override(self.h, kernel, variant, splits), "nb_set_plan_override")
+
+
+class _DeviceView:
+    """Zero-copy CUDA array view of library-owned device memory (int32)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+class Scheduler:
+    """nb_sched: the block-step sorting list (Sec. 3.3.1) on the device.
+
+    levels: initial level of every particle (step 2^-level), host array or device tensor.
+    next() -> (t_block, n_active); active() is a zero-copy int32 device view of the active
+    particles (the list prefix), valid until update(); update(want) commits the step with
+    the requested levels (list order) and returns the granted ones."""
+
+    def __init__(self, levels, level_min: int, level_max: int, device: int = 0):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("CUDA is not available: the scheduler has no CPU path")
+        self.device = device
+        st = torch.cuda.current_stream(device)
+        self._stream = st
+        on_dev = isinstance(levels, torch.Tensor) and levels.is_cuda
+        lv = levels.to(torch.int32).contiguous() if on_dev else np.ascontiguousarray(levels, dtype=np.int32)
+        self.n = int(lv.shape[0])
+        h = ctypes.c_void_p()
+        s = self.lib.nb_sched_init(ctypes.byref(h), self.n, lv.data_ptr() if on_dev else lv.ctypes.data,
+                                   int(level_min), int(level_max), device, ctypes.c_void_p(st.cuda_stream),
+                                   1 if on_dev else 0)
+        if s != NB_OK:
+            raise NBError(s, f"nb_sched_init(n={self.n}, levels in [{level_min}, {level_max}]) failed")
+        self.h = h
+        self.n_active = 0
+        self._list = None
+
+    def _check(self, s, what):
+        if s != NB_OK:
+            raise NBError(s, f"{what}: {self.lib.nb_sched_last_error(self.h).decode()}")
+
+    def next(self):
+        t = ctypes.c_double()
+        na = ctypes.c_int64()
+        ptr = ctypes.c_void_p()
+        self._check(self.lib.nb_sched_next(self.h, ctypes.byref(t), ctypes.byref(na), ctypes.byref(ptr)),
+                    "nb_sched_next")
+        self.n_active = na.value
+        self._list = ptr.value
+        return t.value, na.value
+
+    def active(self):
+        """int32 device tensor viewing the active particles (no copy)."""
+        return self._torch.as_tensor(_DeviceView(self._list, self.n_active), device=f"cuda:{self.device}")
+
+    def update(self, want, granted: bool = True):
+        torch = self._torch
+        if isinstance(want, torch.Tensor) and want.is_cuda:
+            w = want.to(torch.int32).contiguous()
+            g = torch.empty_like(w) if granted else None
+            self._check(self.lib.nb_sched_update(self.h, w.data_ptr(), g.data_ptr() if g is not None else None, 1),
+                        "nb_sched_update")
+            return g
+        w = np.ascontiguousarray(want, dtype=np.int32)
+        g = np.empty_like(w) if granted else None
+        self._check(self.lib.nb_sched_update(self.h, w.ctypes.data, g.ctypes.data if g is not None else None, 0),
+                    "nb_sched_update")
+        return g
+
+    def get(self):
+        """(list, levels, t_now) on the host."""
+        lst, lev = np.empty(self.n, np.int32), np.empty(self.n, np.int32)
+        t = ctypes.c_double()
+        self._check(self.lib.nb_sched_get(self.h, lst.ctypes.data, lev.ctypes.data, ctypes.byref(t), 0),
+                    "nb_sched_get")
+        return lst, lev, t.value
+
+    def counts(self):
+        c = np.empty(64, np.int64)
+        self._check(self.lib.nb_sched_counts(self.h, c.ctypes.data), "nb_sched_counts")
+        return c
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nb_sched_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -179,12 +179,15 @@ nb_status nb_regular_force_batched(nb_ctx *ctx, const int32_t *idx, const double
  * idx[0..n_i), the sums of nb_regular_force restricted to each row's neighbour list,
  *   acc_k = sum_{j in L_k, j != i} m_j r/|r|^3   (jerk and pot likewise),
  * with L_k = nb_idx[nb_off[k] .. nb_off[k+1]) (any CSR list of particle indices; typically
- * the one nb_regular_force returned).  Only i and its listed neighbours are predicted, from
- * the Hermite state of nb_set_particles, to time t (neighbour-only prediction, Sec. 3.3.3);
- * an FP64 context predicts with nb_predict's arithmetic, so the positions are bit-identical
- * to predicting all particles.  The arithmetic follows the context precision (FP64, or the
- * mixed scheme: double-single base differences, FP32 Taylor increments and pair terms,
- * FP64 row sums).
+ * the one nb_regular_force returned).  The particles are predicted from the Hermite state
+ * of nb_set_particles to time t: only i and its listed neighbours while N_i is below n/128
+ * (FP64 context) or n/8 (mixed) (neighbour-only prediction, Sec. 3.3.3), else all particles
+ * once (the cheaper choice once the lists name many more particles than there are, as
+ * Sec. 3.3.3 notes).  The predictor is
+ * nb_predict's, so in an FP64 context both forms give bit-identical results.  The pair
+ * arithmetic follows the context precision (FP64, or mixed: double-single position
+ * differences, FP32 pair terms, FP64 row sums; the neighbour-only form adds the Taylor
+ * increments in FP32).
  * acc, jerk: (n_i, 3), pot: (n_i) double, overwritten.
  * acc_reg, jerk_reg, pot_reg: all NULL, or all given; then on input the all-j sums of the
  * same rows at the same time (from nb_regular_force) and on output the part from outside

@@ -222,6 +222,96 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_mixed(IrrArgs A)
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Predict-all form.  Sec. 3.3.3 notes that predicting every particle once is cheaper than
+// predicting each neighbour when <N_b> N_i exceeds N.  Then one pass of the all-particle
+// predictor (k_predict, records only) writes the compact j-records of the regular force —
+// FP64 {x_p, m} {v_p, 0}, mixed {x_hi, m} {x_lo, 0} {v, 0} — and the list pass gathers 64 or
+// 48 bytes per neighbour instead of 128 or 80, with no prediction per pair.  FP64 positions
+// are the same bits as in the neighbour-only form (one predictor), so FP64 results agree
+// bit for bit between the forms; the mixed form predicts in FP64 here.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_irregular_rec_fp64(IrrArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * BLOCK) >> 5;
+    const dvec4 *R = static_cast<const dvec4 *>(A.srec);
+    for (int64_t k = w0; k < A.n_i; k += nw) {
+        int64_t i, e0, e1;
+        const bool ok = irr_row(A, k, lane, i, e0, e1);
+        double xi[3] = {0, 0, 0}, vi[3] = {0, 0, 0};
+        if (ok) {
+            const dvec4 P = R[2 * i], V = R[2 * i + 1];
+            xi[0] = P.x; xi[1] = P.y; xi[2] = P.z;
+            vi[0] = V.x; vi[1] = V.y; vi[2] = V.z;
+        }
+        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int64_t j = A.nb[e];
+            if (j < 0 || j >= A.n) {
+                atomicOr(A.status, ST_BAD_INDEX);
+                continue;
+            }
+            if (j == i) continue;
+            pair_f64(R[2 * j], R[2 * j + 1], xi, vi, false, s);
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) s[c] = warp_sum(s[c]);
+        irr_store(A, k, lane, s, ok);
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_irregular_rec_mixed(IrrArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * BLOCK) >> 5;
+    const float4 *R = static_cast<const float4 *>(A.srec);
+    for (int64_t k = w0; k < A.n_i; k += nw) {
+        int64_t i, e0, e1;
+        const bool ok = irr_row(A, k, lane, i, e0, e1);
+        float ih[3] = {0, 0, 0}, il[3] = {0, 0, 0}, iv[3] = {0, 0, 0};
+        if (ok) {
+            const float4 P = R[3 * i], L = R[3 * i + 1], V = R[3 * i + 2];
+            ih[0] = P.x; ih[1] = P.y; ih[2] = P.z;
+            il[0] = L.x; il[1] = L.y; il[2] = L.z;
+            iv[0] = V.x; iv[1] = V.y; iv[2] = V.z;
+        }
+        float f[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int64_t j = A.nb[e];
+            if (j < 0 || j >= A.n) {
+                atomicOr(A.status, ST_BAD_INDEX);
+                continue;
+            }
+            if (j == i) continue;
+            const float4 P = R[3 * j], L = R[3 * j + 1], V = R[3 * j + 2];
+            const float r[3] = {ds_diff(P.x, L.x, ih[0], il[0]), ds_diff(P.y, L.y, ih[1], il[1]),
+                                ds_diff(P.z, L.z, ih[2], il[2])};
+            const float w[3] = {V.x - iv[0], V.y - iv[1], V.z - iv[2]};
+            const float r2 = r2_f32(r[0], r[1], r[2]);
+            const float rinv = rsqrtf(r2);
+            const float rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+            const float rinv2 = rinv * rinv;
+            const float mr = P.w * rinv;
+            const float mr3 = mr * rinv2;
+            const float beta = rw * (rinv2 * -3.f);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f[c] += mr3 * r[c];
+                f[3 + c] += mr3 * (w[c] + beta * r[c]);
+            }
+            f[6] -= mr;
+        }
+        double sd[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) sd[c] = warp_sum((double)f[c]);
+        irr_store(A, k, lane, sd, ok);
+    }
+}
+
 constexpr int kIrrBlock = 256;
 
 void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
@@ -236,8 +326,10 @@ void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *
 
 size_t state_record_bytes(int precision, int64_t n) { return (size_t)n * (precision == 0 ? 4 * 32 : 5 * 16); }
 
-void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int64_t n, double t,
-                      int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
+// records: the state records (neighbour-only prediction) or, with predicted != 0, the compact
+// predicted j-records of the predict-all form.
+void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
+                      double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
                       double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status)
 {
     IrrArgs A;
@@ -261,10 +353,16 @@ void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *s
     int64_t g = (n_i + rows_per_cta - 1) / rows_per_cta;
     const int64_t gmax = (int64_t)num_sms * 8;  // 8 CTAs of 8 warps: 64 warps per SM
     if (g > gmax) g = gmax;
-    if (precision == 0)
+    if (predicted) {
+        if (precision == 0)
+            k_irregular_rec_fp64<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);
+        else
+            k_irregular_rec_mixed<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);
+    } else if (precision == 0) {
         k_irregular_fp64<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);
-    else
+    } else {
         k_irregular_mixed<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);
+    }
 }
 
 }  // namespace nbgpu

@@ -42,8 +42,8 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 size_t state_record_bytes(int precision, int64_t n);
 void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
                        const double *jk, const double *tl, const double *m, void *srec);
-void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int64_t n, double t,
-                      int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
+void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
+                      double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
                       double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status);
 }  // namespace nbgpu
 
@@ -51,7 +51,13 @@ static constexpr int kTilePad = 256;   // j-record arrays are padded to a multip
 static constexpr int kMixedTiledVariants = 8;  // entries of the mixed tiled variant table
 static constexpr int kOccFp64 = 8;             // occupancy slot of the FP64 tiled kernel
 static constexpr int kOccSlots = 9;
-static constexpr int kMaxCap = 8192;   // largest nb_cap (sort buffers live in shared memory)
+static constexpr int kMaxCap = 8192;
+// Irregular force: predict all particles once when N_i * factor >= N.  Measured on this GPU
+// (King cluster, N = 2^20, r_s for a median of 80 neighbours): in FP64 the per-pair prediction
+// (25 FP64 operations) makes predict-all pay already at N/128 active rows; in mixed precision
+// the 80-byte state gathers only lose to one full predictor pass above about N/8.
+static constexpr int64_t kIrrAllFactorFp64 = 128;
+static constexpr int64_t kIrrAllFactorMixed = 8;   // largest nb_cap (sort buffers live in shared memory)
 
 struct nb_ctx {
     int device = 0, precision = 0, cap = 0, num_sms = 0;
@@ -81,6 +87,7 @@ struct nb_ctx {
     char *adj = nullptr; size_t adj_cap = 0;
     void *srec = nullptr; size_t srec_cap = 0;  // Hermite-state records of the irregular force
     bool srec_valid = false;
+    void *prec = nullptr; size_t prec_cap = 0;  // predicted j-records of its predict-all form
     // batched ensemble plan (nb_batch_plan)
     void *b_items = nullptr; size_t b_items_cap = 0;
     int64_t *b_cluster_off = nullptr; size_t b_cluster_off_cap = 0;
@@ -485,7 +492,7 @@ nb_status nb_free(nb_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
                     c->part, c->seg_slots, c->seg_cnt, c->row_total, c->scan, c->stage, c->adj, c->b_items,
-                    c->b_cluster_off, c->srec};
+                    c->b_cluster_off, c->srec, c->prec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -880,14 +887,27 @@ nb_status nb_irregular_force(nb_ctx *c, double t, int64_t n_i, const int32_t *id
     if (n_i == 0) return NB_OK;
     if (!idx || !nb_off || !nb_idx || !acc || !jerk || !pot) return fail(c, NB_ERR_ARG, "null array");
     const int64_t n = c->n;
+    // Neighbour-only prediction, or (Sec. 3.3.3) one prediction of all particles when the
+    // lists of the block name many more particles than there are.
+    const bool predict_all = n_i * (c->precision == NB_FP64 ? kIrrAllFactorFp64 : kIrrAllFactorMixed) >= n;
     cudaEvent_t t0 = span_begin(c);
     int kernels = 1;
-    if (!c->srec_valid) {
+    const void *records = c->srec;
+    if (predict_all) {
+        const size_t rb = (size_t)c->n_pad * (c->precision == NB_FP64 ? 2 * sizeof(dvec4) : 3 * sizeof(float4));
+        if ((s = grow(c, &c->prec, &c->prec_cap, rb, "predicted records")) != NB_OK) return s;
+        launch_predict(c->stream, n, c->n_pad, t, c->x, c->v, c->a, c->jk, c->tl, c->m, nullptr, nullptr,
+                       c->precision == NB_FP64 ? c->prec : nullptr, c->precision == NB_MIXED ? c->prec : nullptr);
+        CK_LAUNCH("k_predict launch");
+        records = c->prec;
+        kernels = 2;
+    } else if (!c->srec_valid) {
         if ((s = grow(c, &c->srec, &c->srec_cap, state_record_bytes(c->precision, n), "state records")) != NB_OK)
             return s;
         launch_pack_state(c->stream, c->precision, n, c->x, c->v, c->a, c->jk, c->tl, c->m, c->srec);
         CK_LAUNCH("k_pack_state launch");
         c->srec_valid = true;
+        records = c->srec;
         kernels = 2;
     }
     const int32_t *d_idx = idx, *d_nb = nb_idx;
@@ -931,8 +951,8 @@ nb_status nb_irregular_force(nb_ctx *c, double t, int64_t n_i, const int32_t *id
             CK(cudaMemcpyAsync(d_pr, pot_reg, (size_t)n_i * 8, cudaMemcpyHostToDevice, c->stream), "copy pot_reg");
         }
     }
-    launch_irregular(c->stream, c->precision, c->num_sms, c->srec, n, t, n_i, d_idx, d_off, d_nb, d_acc, d_jerk, d_pot,
-                     d_ar, d_jr, d_pr, c->status);
+    launch_irregular(c->stream, c->precision, c->num_sms, records, predict_all ? 1 : 0, n, t, n_i, d_idx, d_off, d_nb,
+                     d_acc, d_jerk, d_pot, d_ar, d_jr, d_pr, c->status);
     CK_LAUNCH("irregular force launch");
     span_end(c, PH_IRREGULAR, t0, kernels);
     if (on_device) return NB_OK;

@@ -63,10 +63,12 @@ __global__ void k_predict(int64_t n, int64_t n_pad, double t, const double *__re
         double p[3], q[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) hermite_taylor(x[3 * i + c], v[3 * i + c], a[3 * i + c], jk[3 * i + c], dt, p[c], q[c]);
+        if (xp) {  // null when only the records are wanted
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xp[3 * i + c] = p[c];
-            vp[3 * i + c] = q[c];
+            for (int c = 0; c < 3; ++c) {
+                xp[3 * i + c] = p[c];
+                vp[3 * i + c] = q[c];
+            }
         }
         write_records(i, p[0], p[1], p[2], q[0], q[1], q[2], m[i], rec64, rec32);
     }

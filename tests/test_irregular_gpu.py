@@ -78,7 +78,7 @@ def setup():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("n_i", [1, 100, 4096])
+@pytest.mark.parametrize("n_i", [1, 100, 4096, 16384])
 def test_irregular_force_matches_oracle(gpu_lib, setup, prec, n_i):
     from paper_1504_03687_gb300 import Context
     cl, rs2, steps, a0, j0, tl, t, xp, vp = setup
@@ -163,3 +163,34 @@ def test_irregular_force_degenerate_inputs(gpu_lib):
     assert e.value.status == NB_ERR_STATE
     ctx.close()
     ctx2.close()
+
+
+def test_fp64_forms_agree_bit_for_bit(gpu_lib, setup):
+    """The same rows in one call (all particles predicted once: N_i >= N/128 for FP64, N/8
+    for mixed) and in calls of 32 rows (neighbour-only prediction): FP64 results identical,
+    mixed within the mixed bars of each other."""
+    from paper_1504_03687_gb300 import Context
+    cl, rs2, steps, a0, j0, tl, t, xp, vp = setup
+    idx = W.active_block(steps, 16384)
+    _, _, _, cnt, lists = oracle.regular_force(xp, vp, cl.m, idx, rs2, cap=512)
+    off, flat = csr(lists)
+    for prec in ("fp64", "mixed"):
+        ctx = Context(cl.n, precision=prec, nb_cap=512)
+        ctx.set_particles(*[T(q) for q in (cl.x, cl.v, a0, j0, cl.m, tl)])
+        big = [q.cpu().numpy() for q in ctx.irregular_force(t, T(idx), T(off), T(flat))]
+        parts = []
+        for k0 in range(0, 16384, 32):
+            o = off[k0:k0 + 33] - off[k0]
+            nbs = flat[off[k0]:off[k0 + 32]]
+            nbs = nbs if nbs.size else np.zeros(1, np.int32)
+            parts.append([q.cpu().numpy() for q in ctx.irregular_force(t, T(idx[k0:k0 + 32]), T(o), T(nbs))])
+        ctx.sync()
+        small = [np.concatenate([p_[q] for p_ in parts]) for q in range(3)]
+        for q in range(3):
+            if prec == "fp64":
+                np.testing.assert_array_equal(big[q], small[q])
+            else:
+                d, sref = rows_err(big[q][cnt > 0], small[q][cnt > 0])
+                e = d / sref
+                assert np.median(e) <= 2e-6 and e.max() <= 1e-4
+        ctx.close()

@@ -11,7 +11,8 @@ Parity of every function is pinned by tests/test_oracle_pins.py against closed
 forms and invariants (two-body Kepler orbit, Newton's third law, jerk as the
 time derivative of the acceleration, the Plummer potential energy, energy
 conservation, brute-force neighbour sets, finite differences for the adjoint,
-partition and Newton's-law invariants of the irregular force).
+partition and Newton's-law invariants of the irregular force, reduction of the
+Ahmad-Cohen integrator to the plain Hermite run).
 """
 from __future__ import annotations
 
@@ -232,6 +233,34 @@ def irregular_force(t, x, v, a, jerk, t_last, m, idx, nb_off, nb_idx):
     if rc != 0:
         raise IndexError("index outside [0, n) or decreasing offsets")
     return acc, jk, pot
+
+
+def ac_run(m, x, v, rs2, t_end, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125, nb_opt=0,
+           cap=256, max_blocks=0):
+    """Ahmad-Cohen Hermite block-step run (see orc_ac_run).  Returns (x, v, rs2, info) with
+    info = dict(t, dt, DT, T, nb_count, nb_lists, blocks, irregular_steps, regular_steps,
+    neighbour_pairs, all_pairs, rc)."""
+    lib = _load()
+    if not hasattr(lib, "_ac"):
+        P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        lib.orc_ac_run.argtypes = [i64, P, P, P, P, dbl, dbl, dbl, dbl, dbl, i32, i32, i64, P, P, P, P, P, P, P]
+        lib.orc_ac_run.restype = ctypes.c_int
+        lib._ac = True
+    m = _c(m, np.float64)
+    x, v = _c(x, np.float64).copy(), _c(v, np.float64).copy()
+    n = x.shape[0]
+    rs2 = np.ascontiguousarray(np.broadcast_to(np.asarray(rs2, np.float64), (n,))).copy()
+    stats = np.zeros(6)
+    t, dt, DT, T = (np.zeros(n) for _ in range(4))
+    nbc = np.zeros(n, np.int32)
+    nbl = np.zeros((n, cap), np.int32)
+    rc = lib.orc_ac_run(n, _p(m), _p(x), _p(v), _p(rs2), float(t_end), float(eta_irr), float(eta_reg), float(eta_s),
+                        float(dt_max), int(nb_opt), int(cap), int(max_blocks), _p(stats), _p(t), _p(dt), _p(DT),
+                        _p(T), _p(nbc), _p(nbl))
+    info = dict(t=t, dt=dt, DT=DT, T=T, nb_count=nbc, nb_lists=[nbl[i, :nbc[i]].copy() for i in range(n)],
+                blocks=int(stats[0]), irregular_steps=int(stats[1]), regular_steps=int(stats[2]),
+                neighbour_pairs=stats[3], all_pairs=stats[4], rc=rc)
+    return x, v, rs2, info
 
 
 def loss_fd(xp, vp, m, idx, g_acc, g_jerk, g_pot, which: str, p: int, c: int = 0, h: float = 1e-6):

@@ -497,3 +497,237 @@ int orc_irregular_force(int64_t n, const double *x, const double *v, const doubl
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Ahmad-Cohen (AC) Hermite integration with hierarchical block steps (Sec. 2: the force
+ * on a particle is split into the irregular part from the neighbours inside r_s, computed
+ * at every (short) irregular step, and the regular part from all other particles,
+ * computed only at the (long) regular steps and extrapolated in between with its
+ * derivatives; NBODY6++ adjusts r_s towards a target neighbour number NNBOPT, App. A).
+ * The paper prints no formulas; this is the scheme as read here (every choice is listed in
+ * the design notes):
+ *
+ * State of particle i: x, v at its last time t_i; total force a and jerk j there (used by
+ * the predictor); irregular step dt_i, regular step DT_i (powers of 0.5, dt_i <= DT_i), the
+ * time T_i of its last regular step; the regular force Fr, its derivative Jr and its higher
+ * derivatives D2, D3 at T_i; the neighbour list L_i (ascending j, at most cap entries) and
+ * r_s^2.
+ *
+ * Block step: t_next = min_i (t_i + dt_i); the active set is every i with t_i + dt_i =
+ * t_next; all particles are predicted to t_next (Taylor to the jerk).  For active i,
+ * with F_o, J_o the sums over the current list L_i:
+ *  - irregular only (t_next is not a multiple of DT_i): the regular part is extrapolated,
+ *    tau = t_next - T_i,  F_r = Fr + Jr tau + D2 tau^2/2 + D3 tau^3/6,
+ *    J_r = Jr + D2 tau + D3 tau^2/2, and the new total is a1 = F_o + F_r, j1 = J_o + J_r;
+ *  - regular step as well: the sums over all particles give a1, j1 exactly and the new
+ *    list (r^2 < r_s^2); the regular force with the old list, a1 - F_o, and its derivative
+ *    close the Hermite interpolation from (Fr, Jr) at T_i over DT = t_next - T_i, giving
+ *    D2' = D2R + DT D3R and D3' = D3R at t_next; then Fr = a1 - F_n, Jr = j1 - J_n with the
+ *    sums F_n, J_n over the new list, T_i = t_next, and r_s^2 is scaled by
+ *    (nb_opt / max(N_b, 1))^(2/3), the factor clamped to [1/2, 2] (nb_opt <= 0: fixed r_s).
+ *  - corrector on the total force (as in hermite_core) with a0, j0 at t_i and a1, j1, the
+ *    irregular step from the Aarseth criterion on the total force (eta_irr) and, on a
+ *    regular step, the regular step from the criterion on the old-list regular force and
+ *    D2', D3' (eta_reg; an undefined criterion, e.g. no regular force, allows doubling);
+ *    both follow the block rule of hermite_core; then dt_i is capped at DT_i.
+ * Start: all forces at t = 0, lists, Fr = a - F_L, Jr = j - J_L, D2 = D3 = 0, dt_i and DT_i
+ * the largest powers of two below eta_s |a|/|j| and eta_s |Fr|/|Jr| (capped at dt_max; an
+ * undefined ratio gives dt_max), dt_i capped at DT_i.
+ * With r_s covering every particle and nb_opt <= 0 the regular force is exactly zero and
+ * this reduces to hermite_core.
+ * rs2 (n) is used and updated in place.  Optional outputs (n entries, or n*cap for the
+ * lists): t_i, dt_i, DT_i, T_i, list lengths and lists.  stats (6 doubles): block steps,
+ * irregular particle steps, regular particle steps, neighbour pair evaluations, all-j pair
+ * evaluations, 0.  Returns 0, or -2 when max_blocks was reached. */
+static void ac_list_sum(int64_t i, const int32_t *list, int32_t cnt, const double *xp, const double *vp,
+                        const double *m, double *acc, double *jerk)
+{
+    double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+    for (int32_t q = 0; q < cnt; ++q) {
+        const int64_t j = list[q];
+        if (j == i) continue;
+        const double rx = xp[3 * j + 0] - xp[3 * i + 0];
+        const double ry = xp[3 * j + 1] - xp[3 * i + 1];
+        const double rz = xp[3 * j + 2] - xp[3 * i + 2];
+        const double wx = vp[3 * j + 0] - vp[3 * i + 0];
+        const double wy = vp[3 * j + 1] - vp[3 * i + 1];
+        const double wz = vp[3 * j + 2] - vp[3 * i + 2];
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double rinv = 1.0 / sqrt(r2);
+        const double rinv2 = rinv * rinv;
+        const double mr3 = m[j] * rinv * rinv2;
+        const double rw = rx * wx + ry * wy + rz * wz;
+        ax += mr3 * rx;
+        ay += mr3 * ry;
+        az += mr3 * rz;
+        jx += mr3 * (wx - 3.0 * rw * rinv2 * rx);
+        jy += mr3 * (wy - 3.0 * rw * rinv2 * ry);
+        jz += mr3 * (wz - 3.0 * rw * rinv2 * rz);
+    }
+    acc[0] = ax; acc[1] = ay; acc[2] = az;
+    jerk[0] = jx; jerk[1] = jy; jerk[2] = jz;
+}
+
+/* The step rule of hermite_core: halve until not above crit, or double when crit >= 2 h,
+ * 2 h <= dt_max and t is a multiple of 2 h. */
+static double ac_step_rule(double h, double crit, double t, double dt_max)
+{
+    double hn = h;
+    if (crit < hn) {
+        while (hn > crit && hn > 1e-30) hn *= 0.5;
+    } else if (crit >= 2.0 * h && 2.0 * h <= dt_max && fmod(t, 2.0 * h) == 0.0) {
+        hn = 2.0 * h;
+    }
+    return hn;
+}
+
+/* sqrt(eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)); +inf where the ratio is undefined. */
+static double ac_criterion(double eta, const double *a, const double *j, const double *a2, const double *a3)
+{
+    const double na = norm3(a), nj = norm3(j), n2 = norm3(a2), n3 = norm3(a3);
+    const double num = na * n2 + nj * nj, den = nj * n3 + n2 * n2;
+    if (!(den > 0.0) || !(num > 0.0)) return INFINITY;
+    return sqrt(eta * num / den);
+}
+
+int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, double t_end, double eta_irr,
+               double eta_reg, double eta_s, double dt_max, int32_t nb_opt, int32_t cap, int64_t max_blocks,
+               double *stats, double *t_out, double *dt_out, double *DT_out, double *T_out, int32_t *nbc_out,
+               int32_t *nbl_out)
+{
+    double *a = malloc(3 * n * sizeof(double)), *jk = malloc(3 * n * sizeof(double));
+    double *xp = malloc(3 * n * sizeof(double)), *vp = malloc(3 * n * sizeof(double));
+    double *t = calloc(n, sizeof(double)), *dt = malloc(n * sizeof(double));
+    double *T = calloc(n, sizeof(double)), *DT = malloc(n * sizeof(double));
+    double *Fr = malloc(3 * n * sizeof(double)), *Jr = malloc(3 * n * sizeof(double));
+    double *D2 = calloc(3 * n, sizeof(double)), *D3 = calloc(3 * n, sizeof(double));
+    double *a1 = malloc(3 * n * sizeof(double)), *j1 = malloc(3 * n * sizeof(double));
+    double *pot = malloc(n * sizeof(double));
+    int32_t *nbl = malloc((size_t)n * cap * sizeof(int32_t)), *nbc = malloc(n * sizeof(int32_t));
+    int32_t *act = malloc(n * sizeof(int32_t)), *newl = malloc((size_t)cap * sizeof(int32_t));
+    int rc = 0;
+    double nblocks = 0, nirr = 0, nreg = 0, npair_nb = 0, npair_all = 0;
+
+    for (int64_t i = 0; i < n; ++i) act[i] = (int32_t)i;
+    orc_regular_force(n, x, v, m, n, act, rs2, 0, a, jk, pot, nbc, nbl, cap);
+    npair_all += (double)n * (double)(n - 1);
+    for (int64_t i = 0; i < n; ++i) {
+        double Fl[3], Jl[3];
+        const int32_t cnt = nbc[i] < cap ? nbc[i] : cap;
+        nbc[i] = cnt;
+        ac_list_sum(i, nbl + i * (int64_t)cap, cnt, x, v, m, Fl, Jl);
+        for (int c = 0; c < 3; ++c) {
+            Fr[3 * i + c] = a[3 * i + c] - Fl[c];
+            Jr[3 * i + c] = jk[3 * i + c] - Jl[c];
+        }
+        const double ni = norm3(a + 3 * i), nji = norm3(jk + 3 * i);
+        const double nr = norm3(Fr + 3 * i), njr = norm3(Jr + 3 * i);
+        dt[i] = nji > 0.0 ? quantise_step(eta_s * ni / nji, dt_max) : dt_max;
+        DT[i] = njr > 0.0 ? quantise_step(eta_s * nr / njr, dt_max) : dt_max;
+        if (dt[i] > DT[i]) dt[i] = DT[i];
+    }
+
+    for (;;) {
+        double t_next = INFINITY;
+        int64_t n_act = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (t[i] + dt[i] < t_next) t_next = t[i] + dt[i];
+        if (t_next > t_end) break;
+        if (max_blocks > 0 && nblocks >= (double)max_blocks) { rc = -2; break; }
+        for (int64_t i = 0; i < n; ++i)
+            if (t[i] + dt[i] == t_next) act[n_act++] = (int32_t)i;
+        orc_predict(n, t_next, x, v, a, jk, t, xp, vp);
+        /* forces first (all from the same predicted snapshot), then the corrections */
+        for (int64_t k = 0; k < n_act; ++k) {
+            const int64_t i = act[k];
+            double Fo[3], Jo[3];
+            ac_list_sum(i, nbl + i * (int64_t)cap, nbc[i], xp, vp, m, Fo, Jo);
+            npair_nb += (double)nbc[i];
+            const int reg = fmod(t_next, DT[i]) == 0.0;
+            if (!reg) {
+                const double tau = t_next - T[i];
+                for (int c = 0; c < 3; ++c) {
+                    const int64_t q = 3 * i + c;
+                    const double Fx = Fr[q] + Jr[q] * tau + D2[q] * tau * tau / 2.0 + D3[q] * tau * tau * tau / 6.0;
+                    const double Jx = Jr[q] + D2[q] * tau + D3[q] * tau * tau / 2.0;
+                    a1[3 * k + c] = Fo[c] + Fx;
+                    j1[3 * k + c] = Jo[c] + Jx;
+                }
+                continue;
+            }
+            /* regular step: all-j sums with the new list */
+            int32_t cnt_true = 0;
+            const int32_t one = (int32_t)i;
+            double pk;
+            orc_regular_force(n, xp, vp, m, 1, &one, rs2 + i, 1, a1 + 3 * k, j1 + 3 * k, &pk, &cnt_true, newl, cap);
+            npair_all += (double)(n - 1);
+            nreg += 1;
+            const int32_t cnt = cnt_true < cap ? cnt_true : cap;
+            double Fn[3], Jn[3], Fold[3], Jold[3], a2r[3], a3r[3];
+            ac_list_sum(i, newl, cnt, xp, vp, m, Fn, Jn);
+            const double H = t_next - T[i];
+            for (int c = 0; c < 3; ++c) {
+                const int64_t q = 3 * i + c;
+                Fold[c] = a1[3 * k + c] - Fo[c];
+                Jold[c] = j1[3 * k + c] - Jo[c];
+                const double df = Fr[q] - Fold[c];
+                const double a2 = (-6.0 * df - H * (4.0 * Jr[q] + 2.0 * Jold[c])) / (H * H);
+                const double a3 = (12.0 * df + 6.0 * H * (Jr[q] + Jold[c])) / (H * H * H);
+                a2r[c] = a2 + H * a3;
+                a3r[c] = a3;
+            }
+            const double critR = ac_criterion(eta_reg, Fold, Jold, a2r, a3r);
+            double DTn = ac_step_rule(DT[i], critR, t_next, dt_max);
+            for (int c = 0; c < 3; ++c) {
+                const int64_t q = 3 * i + c;
+                Fr[q] = a1[3 * k + c] - Fn[c];
+                Jr[q] = j1[3 * k + c] - Jn[c];
+                D2[q] = a2r[c];
+                D3[q] = a3r[c];
+            }
+            T[i] = t_next;
+            DT[i] = DTn;  /* provisional; dt is capped against it below */
+            memcpy(nbl + i * (int64_t)cap, newl, (size_t)cnt * sizeof(int32_t));
+            nbc[i] = cnt;
+            if (nb_opt > 0) {
+                double f = pow((double)nb_opt / (double)(cnt_true > 0 ? cnt_true : 1), 2.0 / 3.0);
+                f = f < 0.5 ? 0.5 : (f > 2.0 ? 2.0 : f);
+                rs2[i] *= f;
+            }
+        }
+        for (int64_t k = 0; k < n_act; ++k) {
+            const int64_t i = act[k];
+            const double h = t_next - t[i];
+            double a2[3], a3[3], a2e[3];
+            for (int c = 0; c < 3; ++c) {
+                const double da = a[3 * i + c] - a1[3 * k + c];
+                a2[c] = (-6.0 * da - h * (4.0 * jk[3 * i + c] + 2.0 * j1[3 * k + c])) / (h * h);
+                a3[c] = (12.0 * da + 6.0 * h * (jk[3 * i + c] + j1[3 * k + c])) / (h * h * h);
+                x[3 * i + c] = xp[3 * i + c] + h * h * h * h / 24.0 * a2[c] + h * h * h * h * h / 120.0 * a3[c];
+                v[3 * i + c] = vp[3 * i + c] + h * h * h / 6.0 * a2[c] + h * h * h * h / 24.0 * a3[c];
+                a[3 * i + c] = a1[3 * k + c];
+                jk[3 * i + c] = j1[3 * k + c];
+                a2e[c] = a2[c] + h * a3[c];
+            }
+            t[i] = t_next;
+            const double crit = ac_criterion(eta_irr, a + 3 * i, jk + 3 * i, a2e, a3);
+            double hn = ac_step_rule(h, crit, t_next, dt_max);
+            if (hn > DT[i]) hn = DT[i];
+            dt[i] = hn;
+        }
+        nblocks += 1;
+        nirr += (double)n_act;
+    }
+    if (stats) { stats[0] = nblocks; stats[1] = nirr; stats[2] = nreg; stats[3] = npair_nb; stats[4] = npair_all; stats[5] = 0; }
+    for (int64_t i = 0; i < n; ++i) {
+        if (t_out) t_out[i] = t[i];
+        if (dt_out) dt_out[i] = dt[i];
+        if (DT_out) DT_out[i] = DT[i];
+        if (T_out) T_out[i] = T[i];
+        if (nbc_out) nbc_out[i] = nbc[i];
+    }
+    if (nbl_out) memcpy(nbl_out, nbl, (size_t)n * cap * sizeof(int32_t));
+    free(a); free(jk); free(xp); free(vp); free(t); free(dt); free(T); free(DT); free(Fr); free(Jr);
+    free(D2); free(D3); free(a1); free(j1); free(pot); free(nbl); free(nbc); free(act); free(newl);
+    return rc;
+}

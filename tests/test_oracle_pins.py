@@ -15,6 +15,9 @@ least one of them:
                    energy conservation on the 1024-body Plummer sphere
   adjoint        : central finite differences of the forward, and autograd of an
                    independently written dense PyTorch formula
+  AC integrator  : reduces bit for bit to the plain Hermite run when every particle
+                   is a neighbour; energy conservation and its convergence with the
+                   regular step parameter on the 1024-body Plummer sphere
   irregular force: lists plus the rest of the particles add up to the all-j sums
                    (with neighbour-only prediction against the all-particle
                    predictor); Newton's third law and the pair energy inside an
@@ -495,3 +498,43 @@ def test_irregular_force_edge_cases():
         oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx, np.array([0, 1, 2]), np.array([1, 50], np.int32))
     with pytest.raises(IndexError):
         oracle.irregular_force(0.0, cl.x, cl.v, z, z, tl, cl.m, idx, np.array([0, 2, 1]), np.array([1, 2], np.int32))
+
+
+# ---------------------------------------------------------------- Ahmad-Cohen integrator
+def test_ac_reduces_to_hermite_when_every_particle_is_a_neighbour():
+    """With r_s covering the whole system and a fixed r_s, the regular force is exactly zero
+    and the AC run must equal the plain block-step Hermite run (pinned above by the Kepler
+    orbit and energy conservation) bit for bit."""
+    import ctypes
+    cl = W.plummer(256, 101)
+    xh, vh = cl.x.copy(), cl.v.copy()
+    st = np.zeros(4)
+    lib = oracle._load()
+    rc = lib.orc_hermite_run(256, cl.m.ctypes.data, xh.ctypes.data, vh.ctypes.data, ctypes.c_double(0.25),
+                             ctypes.c_double(0.02), ctypes.c_double(0.01), ctypes.c_double(0.125),
+                             ctypes.c_double(0.0), ctypes.c_int64(0), st.ctypes.data)
+    assert rc == 0
+    x, v, _, info = oracle.ac_run(cl.m, cl.x, cl.v, 1e300, 0.25, eta_irr=0.02, eta_reg=0.03, eta_s=0.01,
+                                  cap=256, nb_opt=0)
+    assert info["rc"] == 0 and info["blocks"] == int(st[0]) and info["irregular_steps"] == int(st[1])
+    np.testing.assert_array_equal(x, xh)
+    np.testing.assert_array_equal(v, vh)
+
+
+def test_ac_energy_conservation_and_regular_step_convergence():
+    """Plummer 1024, r_s adapted towards 50 neighbours: |dE/E| at t = 1 below 1e-5, and ten
+    times smaller regular-step accuracy parameter cuts it at least fourfold (the regular
+    force's extrapolation is the scheme's leading error); every particle ends at t = 1; far
+    fewer regular (all-j) steps than irregular ones; the lists sit at the target size."""
+    cl, rs2 = W.plummer_1k_equal()
+    E0 = sum(oracle.energy(cl.m, cl.x, cl.v))
+    errs = []
+    for eta_reg in (0.03, 0.003):
+        x, v, r2, info = oracle.ac_run(cl.m, cl.x, cl.v, rs2, 1.0, eta_irr=0.02, eta_reg=eta_reg, eta_s=0.01,
+                                       cap=256, nb_opt=50)
+        assert info["rc"] == 0 and np.all(info["t"] == 1.0) and np.all(info["dt"] <= info["DT"])
+        errs.append(abs(sum(oracle.energy(cl.m, x, v)) - E0) / abs(E0))
+        if eta_reg == 0.03:
+            assert info["regular_steps"] < 0.25 * info["irregular_steps"]
+            assert 40 <= np.median(info["nb_count"]) <= 62
+    assert errs[0] < 1e-5 and errs[1] < errs[0] / 4, errs

@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-irregular", action="store_true")
     ap.add_argument("--no-scheduler", action="store_true")
+    ap.add_argument("--no-integrator", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="profiling case: one warm-up and one timed predict + force call on the King cluster "
                          "(--n particles, --ni active, --prec), printing device times")
@@ -372,6 +373,8 @@ def main():
         extra["ensemble"] = bench_ensemble(dev)
     if rank == 0 and not args.no_adjoint:
         extra["adjoint"] = bench_adjoint(dev)
+    if rank == 0 and not args.no_integrator:
+        extra["ac_integrator"] = bench_ac(dev)
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -578,6 +581,49 @@ def bench_scheduler(dev, cl, steps=512, parity_steps=16):
             "ns_per_particle_step": t_sched * 1e9 / part_steps,
             "reference_us_per_block_step_first_steps": t_ref * 1e6 / parity_steps,
             "parity_with_reference_first_steps": parity, "parity_steps": parity_steps}
+
+
+def bench_ac(dev, n=65536, t_end=1.0 / 64):
+    """Ahmad-Cohen block-step integration on the device (nb_ac_*): Plummer N = 65536 with
+    Kroupa masses, r_s adapted towards 50 neighbours (cap 256), eta_irr 0.02, eta_reg 0.03,
+    from t = 0 to t_end, in a mixed and an FP64 context; wall time on the host clock, particle
+    steps per second, energy error (oracle energy before and after).  The same run by the
+    reference AC integrator on the host cores is timed beside it."""
+    import torch
+
+    import oracle
+    import workloads as W
+    from paper_1504_03687_gb300 import ACIntegrator, Context
+    cl = W.plummer(n, 104, masses="kroupa")
+    rs2 = W.neighbour_radius2(cl.x, 50, seed=104)
+    kw = dict(eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=t_end, nb_opt=50)
+    E0 = sum(oracle.energy(cl.m, cl.x, cl.v))
+    res = {"workload": f"Plummer N={n} Kroupa, r_s towards 50 neighbours (cap 256), eta_irr 0.02, eta_reg 0.03, "
+                       f"t = 0 .. {t_end} (= dt_max: every particle ends at t_end)"}
+    for prec in ("mixed", "fp64"):
+        ctx = Context(n, precision=prec, nb_cap=256, device=dev.index or 0)
+        ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ac.run(t_end, max_blocks=1000000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        g = ac.get()
+        e = (sum(oracle.energy(cl.m, g["x"], g["v"])) - E0) / abs(E0)
+        res[prec] = {"wall_s": wall, "block_steps": st["blocks"], "irregular_steps": st["irregular_steps"],
+                     "regular_steps": st["regular_steps"], "particle_steps_per_s": st["irregular_steps"] / wall,
+                     "ms_per_block_step": wall * 1e3 / max(st["blocks"], 1), "energy_rel_error": e,
+                     "all_synchronised": bool(np.all(g["t"] == t_end)), "median_neighbours": float(np.median(g["nb_count"]))}
+        ac.close()
+        ctx.close()
+    t0 = time.perf_counter()
+    ox, ov, _, info = oracle.ac_run(cl.m, cl.x, cl.v, rs2, t_end, cap=256, **kw)
+    wall = time.perf_counter() - t0
+    res["reference_on_host"] = {"wall_s": wall, "cores": oracle.num_threads(), "block_steps": info["blocks"],
+                                "irregular_steps": info["irregular_steps"], "regular_steps": info["regular_steps"],
+                                "energy_rel_error": (sum(oracle.energy(cl.m, ox, ov)) - E0) / abs(E0)}
+    res["mixed_speedup_over_reference"] = wall / res["mixed"]["wall_s"]
+    return res
 
 
 def bench_ensemble(dev, steps=5, n_clusters=512):

@@ -321,8 +321,74 @@ nb_status nb_sched_get(nb_sched *s, int32_t *list, int32_t *levels, double *t_no
 /* Particles per level, counts[64] (index = level), as of the last committed step. */
 nb_status nb_sched_counts(const nb_sched *s, int64_t *counts);
 
+/* Time of the next block step, without advancing (host only). */
+nb_status nb_sched_peek(const nb_sched *s, double *t_next);
+
 /* One-line description of the last error of this scheduler (never NULL). */
 const char *nb_sched_last_error(const nb_sched *s);
+
+/* ---------------------------------------------------------------------------------------
+ * Ahmad-Cohen Hermite integrator on the device (Sec. 2: the force on a particle is split
+ * into the irregular part from its neighbours inside r_s, recomputed at every irregular
+ * step, and the regular part from all other particles, recomputed at the longer regular
+ * steps and extrapolated with its derivatives in between; NBODY6++ adjusts r_s towards a
+ * target neighbour number, App. A).  The paper prints no formulas; the scheme, step for
+ * step:
+ *  - block step: the scheduler above selects the particles whose irregular step ends at
+ *    the new block time t; all particles are predicted to t (nb_predict);
+ *  - every active particle gets the irregular force over its current list; one whose
+ *    regular step also ends at t gets the all-j sums (nb_regular_force, which also yields
+ *    its new list) and the irregular force over the new list;
+ *  - new total force: all-j sums on a regular step, else list sums plus the regular force
+ *    extrapolated to third order from its last regular step;
+ *  - fourth-order Hermite corrector on the total force; irregular step from the Aarseth
+ *    criterion on the total force (eta_irr); on a regular step, the regular force's second
+ *    and third derivatives from the Hermite interpolation of the regular force with the
+ *    old list, the regular step from the criterion on it (eta_reg), the new regular force
+ *    and jerk (all-j minus new-list sums), and r_s^2 scaled by (nb_opt / N_b)^(2/3) clamped
+ *    to [1/2, 2] (nb_opt <= 0 keeps r_s);
+ *  - steps are powers of 1/2, halved as needed, doubled at most once and only at a time
+ *    that is a multiple of the doubled step, never above dt_max; irregular <= regular: on a
+ *    regular step the regular step is raised to the new irregular step if shorter, on an
+ *    irregular step the irregular step is capped at the regular one.
+ * Start: all forces and lists at t = 0, zero higher regular derivatives, steps from
+ * eta_s |F| / |dF/dt| of the total and of the regular force (the regular one raised to the
+ * irregular one if shorter).
+ * The context provides the particle state, precision and list capacity (its nb_cap). */
+typedef struct {
+    double eta_irr, eta_reg, eta_s;  /* accuracy parameters of the step criteria */
+    double dt_max;                   /* largest step: a power of 1/2 */
+    int32_t nb_opt;                  /* target neighbour number (<= 0: r_s stays fixed) */
+    int32_t level_max;               /* smallest step 2^-level_max, level_max <= 48 */
+} nb_ac_params;
+typedef struct nb_ac nb_ac;
+
+/* Start an integration of n particles (masses m, positions x, velocities v (n,3) at t = 0,
+ * squared neighbour radii rs2 (n); host or device pointers) on the context ctx (n <= its
+ * n_max; the context's particle state is taken over and evolved by the integrator). */
+nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v,
+                     const double *rs2, const nb_ac_params *params, int32_t on_device);
+
+/* One block step.  *t_block, *n_active, *n_regular (any may be NULL) receive the block
+ * time, the particles stepped and those among them that took a regular step. */
+nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_regular);
+
+/* Block steps until the next one would pass t_end, or max_blocks steps (0: no limit;
+ * NB_ERR_STATE when reached).  stats (6 doubles, optional): block steps, irregular particle
+ * steps, regular particle steps, neighbour-list pair terms, all-j pair terms, 0. */
+nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats);
+
+/* Copy out (each may be NULL; n entries, x and v (n,3), lists n x nb_cap): positions and
+ * velocities at each particle's last step time t, irregular and regular steps dt and DT,
+ * the last regular step time T, r_s^2, list lengths and lists (ascending j). */
+nb_status nb_ac_get(nb_ac *s, double *x, double *v, double *t, double *dt, double *DT, double *T,
+                    double *rs2, int32_t *nb_count, int32_t *nb_lists, int32_t on_device);
+
+/* Destroy the integrator (the context stays valid).  Safe on NULL. */
+nb_status nb_ac_free(nb_ac *s);
+
+/* One-line description of the last error of this integrator (never NULL). */
+const char *nb_ac_last_error(const nb_ac *s);
 
 #ifdef __cplusplus
 }

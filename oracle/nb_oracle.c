@@ -529,10 +529,14 @@ int orc_irregular_force(int64_t n, const double *x, const double *v, const doubl
  *    irregular step from the Aarseth criterion on the total force (eta_irr) and, on a
  *    regular step, the regular step from the criterion on the old-list regular force and
  *    D2', D3' (eta_reg; an undefined criterion, e.g. no regular force, allows doubling);
- *    both follow the block rule of hermite_core; then dt_i is capped at DT_i.
+ *    both follow the block rule of hermite_core.  On a regular step the regular step is
+ *    raised to the new irregular step if it came out shorter (a regular step shorter than
+ *    the irregular one gains nothing: the all-j sums would be taken every step anyway, and
+ *    a regular force that is only rounding noise must not shrink the steps); otherwise the
+ *    irregular step is capped at the regular one.
  * Start: all forces at t = 0, lists, Fr = a - F_L, Jr = j - J_L, D2 = D3 = 0, dt_i and DT_i
  * the largest powers of two below eta_s |a|/|j| and eta_s |Fr|/|Jr| (capped at dt_max; an
- * undefined ratio gives dt_max), dt_i capped at DT_i.
+ * undefined ratio gives dt_max), DT_i raised to dt_i if shorter.
  * With r_s covering every particle and nb_opt <= 0 the regular force is exactly zero and
  * this reduces to hermite_core.
  * rs2 (n) is used and updated in place.  Optional outputs (n entries, or n*cap for the
@@ -605,6 +609,7 @@ int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, do
     double *pot = malloc(n * sizeof(double));
     int32_t *nbl = malloc((size_t)n * cap * sizeof(int32_t)), *nbc = malloc(n * sizeof(int32_t));
     int32_t *act = malloc(n * sizeof(int32_t)), *newl = malloc((size_t)cap * sizeof(int32_t));
+    char *regk = malloc(n);
     int rc = 0;
     double nblocks = 0, nirr = 0, nreg = 0, npair_nb = 0, npair_all = 0;
 
@@ -624,7 +629,7 @@ int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, do
         const double nr = norm3(Fr + 3 * i), njr = norm3(Jr + 3 * i);
         dt[i] = nji > 0.0 ? quantise_step(eta_s * ni / nji, dt_max) : dt_max;
         DT[i] = njr > 0.0 ? quantise_step(eta_s * nr / njr, dt_max) : dt_max;
-        if (dt[i] > DT[i]) dt[i] = DT[i];
+        if (DT[i] < dt[i]) DT[i] = dt[i];
     }
 
     for (;;) {
@@ -644,6 +649,7 @@ int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, do
             ac_list_sum(i, nbl + i * (int64_t)cap, nbc[i], xp, vp, m, Fo, Jo);
             npair_nb += (double)nbc[i];
             const int reg = fmod(t_next, DT[i]) == 0.0;
+            regk[k] = (char)reg;
             if (!reg) {
                 const double tau = t_next - T[i];
                 for (int c = 0; c < 3; ++c) {
@@ -712,7 +718,11 @@ int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, do
             t[i] = t_next;
             const double crit = ac_criterion(eta_irr, a + 3 * i, jk + 3 * i, a2e, a3);
             double hn = ac_step_rule(h, crit, t_next, dt_max);
-            if (hn > DT[i]) hn = DT[i];
+            if (regk[k]) {
+                if (DT[i] < hn) DT[i] = hn;
+            } else if (hn > DT[i]) {
+                hn = DT[i];
+            }
             dt[i] = hn;
         }
         nblocks += 1;
@@ -728,6 +738,6 @@ int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, do
     }
     if (nbl_out) memcpy(nbl_out, nbl, (size_t)n * cap * sizeof(int32_t));
     free(a); free(jk); free(xp); free(vp); free(t); free(dt); free(T); free(DT); free(Fr); free(Jr);
-    free(D2); free(D3); free(a1); free(j1); free(pot); free(nbl); free(nbc); free(act); free(newl);
+    free(D2); free(D3); free(a1); free(j1); free(pot); free(nbl); free(nbc); free(act); free(newl); free(regk);
     return rc;
 }

@@ -7,6 +7,8 @@ CUDA kernels behind a C ABI (include/nbgpu.h); around it the irregular force ove
 neighbour lists, the adjoint, the batched ensemble form and the block-step sorting list.
 This package is the thin Python binding (argument marshalling only).
 """
-from .api import Context, ForceResult, NBError, NBOverflow, Scheduler, load_library, plan_for  # noqa: F401
+from .api import (ACIntegrator, Context, ForceResult, NBError, NBOverflow, Scheduler, load_library,  # noqa: F401
+                  plan_for)
 
-__all__ = ["Context", "ForceResult", "NBError", "NBOverflow", "Scheduler", "load_library", "plan_for"]
+__all__ = ["ACIntegrator", "Context", "ForceResult", "NBError", "NBOverflow", "Scheduler", "load_library",
+           "plan_for"]

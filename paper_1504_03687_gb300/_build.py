@@ -25,9 +25,10 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
           "--expt-relaxed-constexpr"]
 # per-file extra flags: the mixed kernels flush FP32 denormals (no distinct particles are
 # 1e-19 apart) so that rsqrtf is a single hardware instruction
-EXTRA = {"force_mixed.cu": ["-ftz=true"], "adjoint.cu": ["-ftz=true"], "irregular.cu": ["-ftz=true"]}
+EXTRA = {"force_mixed.cu": ["-ftz=true"], "adjoint.cu": ["-ftz=true"], "irregular.cu": ["-ftz=true"],
+         "ac.cu": ["-fmad=false"]}
 SOURCES = ["nb_api.cu", "predict.cu", "force_mixed.cu", "force_fp64.cu", "neighbours.cu", "adjoint.cu",
-           "noalloc.cu", "irregular.cu", "sched.cu"]
+           "noalloc.cu", "irregular.cu", "sched.cu", "ac.cu"]
 
 
 def _nvcc() -> str:

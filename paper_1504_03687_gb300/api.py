@@ -30,7 +30,8 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
            "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
            "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force", "nb_sched_init", "nb_sched_free",
-           "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error")
+           "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error",
+           "nb_sched_peek", "nb_ac_init", "nb_ac_step", "nb_ac_run", "nb_ac_get", "nb_ac_free", "nb_ac_last_error")
 NB_SOURCE_ALIGN = 256
 
 
@@ -47,6 +48,11 @@ class NBOverflow(UserWarning):
 class _Config(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("precision", ctypes.c_int32), ("nb_cap", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class _ACParams(ctypes.Structure):
+    _fields_ = [("eta_irr", ctypes.c_double), ("eta_reg", ctypes.c_double), ("eta_s", ctypes.c_double),
+                ("dt_max", ctypes.c_double), ("nb_opt", ctypes.c_int32), ("level_max", ctypes.c_int32)]
 
 
 _lib = None
@@ -90,6 +96,13 @@ def load_library(build_if_needed: bool = True):
         "nb_sched_get": (st, [P, P, P, ctypes.POINTER(dbl), i32]),
         "nb_sched_counts": (st, [P, P]),
         "nb_sched_last_error": (ctypes.c_char_p, [P]),
+        "nb_sched_peek": (st, [P, ctypes.POINTER(dbl)]),
+        "nb_ac_init": (st, [ctypes.POINTER(P), P, i64, P, P, P, P, ctypes.POINTER(_ACParams), i32]),
+        "nb_ac_step": (st, [P, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "nb_ac_run": (st, [P, dbl, i64, P]),
+        "nb_ac_get": (st, [P, P, P, P, P, P, P, P, P, P, i32]),
+        "nb_ac_free": (st, [P]),
+        "nb_ac_last_error": (ctypes.c_char_p, [P]),
         "nb_irregular_force": (st, [P, dbl, i64, P, P, P, P, P, P, P, P, P, i32]),
         "nb_regular_force_batched": (st, [P, P, P, P, P, P, P, P, i64, P]),
         "nb_set_timing": (st, [P, i32]),
@@ -508,6 +521,66 @@ class Scheduler:
     def close(self):
         if getattr(self, "h", None):
             self.lib.nb_sched_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ACIntegrator:
+    """nb_ac: the Ahmad-Cohen Hermite block-step integrator on the device, driving the
+    context `ctx` (its precision and nb_cap) and its own block-step scheduler."""
+
+    def __init__(self, ctx: Context, m, x, v, rs2, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125,
+                 nb_opt=0, level_max=40):
+        self.ctx, self.lib = ctx, ctx.lib
+        n = int(np.asarray(m).shape[0])
+        self.n, self.cap = n, ctx.nb_cap
+        m_, x_, v_ = (np.ascontiguousarray(q, dtype=np.float64) for q in (m, x, v))
+        r_ = np.ascontiguousarray(np.broadcast_to(np.asarray(rs2, np.float64), (n,)))
+        prm = _ACParams(eta_irr, eta_reg, eta_s, dt_max, int(nb_opt), int(level_max))
+        ctx._bind_stream()
+        h = ctypes.c_void_p()
+        s = self.lib.nb_ac_init(ctypes.byref(h), ctx.h, n, m_.ctypes.data, x_.ctypes.data, v_.ctypes.data,
+                                r_.ctypes.data, ctypes.byref(prm), 0)
+        if s != NB_OK:
+            raise NBError(s, f"nb_ac_init: {self.lib.nb_ac_last_error(h).decode() if h.value else ''}")
+        self.h = h
+        ctx.n = n
+
+    def _check(self, s, what, allow=()):
+        if s != NB_OK and s not in allow:
+            raise NBError(s, f"{what}: {self.lib.nb_ac_last_error(self.h).decode()}")
+        return s
+
+    def step(self):
+        t, na, nr = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.nb_ac_step(self.h, ctypes.byref(t), ctypes.byref(na), ctypes.byref(nr)), "nb_ac_step")
+        return t.value, na.value, nr.value
+
+    def run(self, t_end: float, max_blocks: int = 0) -> dict:
+        st = np.zeros(6)
+        self._check(self.lib.nb_ac_run(self.h, float(t_end), int(max_blocks), st.ctypes.data), "nb_ac_run",
+                    allow=(NB_ERR_STATE,) if max_blocks else ())
+        return dict(blocks=int(st[0]), irregular_steps=int(st[1]), regular_steps=int(st[2]),
+                    neighbour_pairs=st[3], all_pairs=st[4])
+
+    def get(self) -> dict:
+        n, cap = self.n, self.cap
+        out = dict(x=np.empty((n, 3)), v=np.empty((n, 3)), t=np.empty(n), dt=np.empty(n), DT=np.empty(n),
+                   T=np.empty(n), rs2=np.empty(n), nb_count=np.empty(n, np.int32),
+                   nb_lists=np.empty((n, cap), np.int32))
+        self._check(self.lib.nb_ac_get(self.h, *[out[k].ctypes.data for k in
+                                                 ("x", "v", "t", "dt", "DT", "T", "rs2", "nb_count", "nb_lists")], 0),
+                    "nb_ac_get")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nb_ac_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,510 @@
+// ac.cu — K9: the Ahmad-Cohen Hermite block step on the device (paper Sec. 2; the scheme
+// is stated with the declarations in nbgpu.h).  One block step is a fixed sequence of
+// launches on the context stream:
+//   nb_sched_next (host)          -> block time t, active particles = list prefix
+//   k_ac_classify                 -> which active particles also take a regular step
+//   nb_predict(t)                 -> all particles predicted, j-records built
+//   nb_regular_force (regular)    -> all-j sums and the new lists of the regular subset
+//   irregular force, old lists    -> list sums of every active particle (predicted records)
+//   irregular force, new lists    -> list sums of the regular subset over its new lists
+//   k_ac_correct                  -> corrector, step criteria, regular bookkeeping, r_s
+//   k_ac_lists                    -> the new lists replace the old ones
+//   nb_sched_update               -> the requested levels re-sort the active prefix
+// The corrector's FP64 arithmetic is written operation by operation in the order of the
+// plain definition and this file is compiled without FMA contraction, so an FP64 context
+// follows the reference integration to rounding.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "nbgpu.h"
+#include "nb_common.cuh"
+#include "nb_kernels.cuh"
+
+namespace nbgpu {
+
+constexpr int kAcTick = 48;  // the scheduler's time unit 2^-48
+
+struct AcDev {
+    // context state
+    double *x, *v, *a, *jk, *tl, *m, *xp, *vp;
+    // integrator state
+    double *Fr, *Jr, *D2, *D3, *rs2;
+    double *Tr;
+    int32_t *LR, *LI;
+    int32_t *ell, *ell_cnt;
+    int32_t cap, lmin, lmax;
+    double eta_irr, eta_reg, dt_max;
+    int32_t nb_opt;
+};
+
+__device__ __forceinline__ double norm3d(double a, double b, double c) { return sqrt(a * a + b * b + c * c); }
+
+// sqrt(eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)); +inf where the ratio is undefined.
+__device__ double ac_crit(double eta, const double *a, const double *j, const double *a2, const double *a3)
+{
+    const double na = norm3d(a[0], a[1], a[2]), nj = norm3d(j[0], j[1], j[2]);
+    const double n2 = norm3d(a2[0], a2[1], a2[2]), n3 = norm3d(a3[0], a3[1], a3[2]);
+    const double num = na * n2 + nj * nj, den = nj * n3 + n2 * n2;
+    if (!(den > 0.0) || !(num > 0.0)) return __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    return sqrt(eta * num / den);
+}
+
+// The step rule on levels (step 2^-L): halve until not above crit, or double once when
+// crit >= 2 h, 2 h <= dt_max and the time t (ticks of 2^-48) is a multiple of 2 h.
+__device__ int ac_level_rule(int L, double crit, int64_t t_ticks, int lmin, int lmax)
+{
+    const double h = ldexp(1.0, -L);
+    if (crit < h) {
+        int Ln = L;
+        double hn = h;
+        while (hn > crit && Ln < lmax) {  // steps below 2^-lmax are not representable in ticks
+            hn *= 0.5;
+            ++Ln;
+        }
+        return Ln;
+    }
+    if (crit >= 2.0 * h && L - 1 >= lmin && (t_ticks & (((int64_t)1 << (kAcTick - (L - 1))) - 1)) == 0)
+        return L - 1;
+    return L;
+}
+
+// Largest power of two (level) not above crit and not above dt_max.
+__device__ int ac_quantise(double crit, int lmin, int lmax)
+{
+    int L = lmin;
+    double dt = ldexp(1.0, -lmin);
+    while (dt > crit && L < lmax) {
+        dt *= 0.5;
+        ++L;
+    }
+    return L;
+}
+
+__global__ void k_iota32(int32_t *p, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+
+// Start: regular part = all-j minus list sums, zero higher derivatives, initial levels.
+__global__ void k_ac_init(AcDev D, int64_t n, const double *Fa, const double *Ja, const double *Fl, const double *Jl,
+                          const int64_t *off, const int32_t *csr, double eta_s, int32_t *levels_out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double fr[3], jr[3];
+        for (int c = 0; c < 3; ++c) {
+            fr[c] = Fa[3 * i + c] - Fl[3 * i + c];
+            jr[c] = Ja[3 * i + c] - Jl[3 * i + c];
+            D.Fr[3 * i + c] = fr[c];
+            D.Jr[3 * i + c] = jr[c];
+            D.D2[3 * i + c] = 0.0;
+            D.D3[3 * i + c] = 0.0;
+            D.a[3 * i + c] = Fa[3 * i + c];
+            D.jk[3 * i + c] = Ja[3 * i + c];
+        }
+        D.tl[i] = 0.0;
+        D.Tr[i] = 0.0;
+        const double ni = norm3d(Fa[3 * i], Fa[3 * i + 1], Fa[3 * i + 2]);
+        const double nji = norm3d(Ja[3 * i], Ja[3 * i + 1], Ja[3 * i + 2]);
+        const double nr = norm3d(fr[0], fr[1], fr[2]), njr = norm3d(jr[0], jr[1], jr[2]);
+        const int LI = nji > 0.0 ? ac_quantise(eta_s * ni / nji, D.lmin, D.lmax) : D.lmin;
+        int LR = njr > 0.0 ? ac_quantise(eta_s * nr / njr, D.lmin, D.lmax) : D.lmin;
+        if (LR > LI) LR = LI;  // the regular step is at least the irregular one
+        D.LI[i] = LI;
+        D.LR[i] = LR;
+        levels_out[i] = LI;
+        const int64_t e0 = off[i], len = off[i + 1] - off[i];
+        D.ell_cnt[i] = (int32_t)len;
+        for (int64_t e = 0; e < len; ++e) D.ell[i * D.cap + e] = csr[e0 + e];
+    }
+}
+
+// Active row k: regular step too?  Compacts the regular subset (order of the subset is
+// irrelevant: every row's sums are independent of the others).
+__global__ void k_ac_classify(AcDev D, int64_t n_act, const int32_t *list, int64_t t_ticks, unsigned *counter,
+                              int32_t *reg_pos, int32_t *reg_idx, double *reg_rs2)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = list[k];
+        const int LR = D.LR[i];
+        const bool reg = (t_ticks & (((int64_t)1 << (kAcTick - LR)) - 1)) == 0;
+        int32_t p = -1;
+        if (reg) {
+            p = (int32_t)atomicAdd(counter, 1u);
+            reg_idx[p] = i;
+            reg_rs2[p] = D.rs2[i];
+        }
+        reg_pos[k] = p;
+    }
+}
+
+__global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double t, int64_t t_ticks,
+                             const int32_t *reg_pos, const double *Fo, const double *Jo, const double *Fa,
+                             const double *Ja, const double *Fn, const double *Jn, const int32_t *cnt_true,
+                             int32_t *want, unsigned long long *pairs)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = list[k];
+        const int32_t p = reg_pos[k];
+        atomicAdd(pairs, (unsigned long long)D.ell_cnt[i]);
+        double a1[3], j1[3];
+        if (p < 0) {
+            const double tau = t - D.Tr[i];
+            for (int c = 0; c < 3; ++c) {
+                const int64_t q = 3 * i + c;
+                const double Fx = D.Fr[q] + D.Jr[q] * tau + D.D2[q] * tau * tau / 2.0 + D.D3[q] * tau * tau * tau / 6.0;
+                const double Jx = D.Jr[q] + D.D2[q] * tau + D.D3[q] * tau * tau / 2.0;
+                a1[c] = Fo[3 * k + c] + Fx;
+                j1[c] = Jo[3 * k + c] + Jx;
+            }
+        } else {
+            double Fold[3], Jold[3], a2r[3], a3r[3];
+            const double H = t - D.Tr[i];
+            for (int c = 0; c < 3; ++c) {
+                const int64_t q = 3 * i + c;
+                a1[c] = Fa[3 * p + c];
+                j1[c] = Ja[3 * p + c];
+                Fold[c] = a1[c] - Fo[3 * k + c];
+                Jold[c] = j1[c] - Jo[3 * k + c];
+                const double df = D.Fr[q] - Fold[c];
+                const double a2 = (-6.0 * df - H * (4.0 * D.Jr[q] + 2.0 * Jold[c])) / (H * H);
+                const double a3 = (12.0 * df + 6.0 * H * (D.Jr[q] + Jold[c])) / (H * H * H);
+                a2r[c] = a2 + H * a3;
+                a3r[c] = a3;
+            }
+            const double critR = ac_crit(D.eta_reg, Fold, Jold, a2r, a3r);
+            D.LR[i] = ac_level_rule(D.LR[i], critR, t_ticks, D.lmin, D.lmax);
+            for (int c = 0; c < 3; ++c) {
+                const int64_t q = 3 * i + c;
+                D.Fr[q] = a1[c] - Fn[3 * p + c];
+                D.Jr[q] = j1[c] - Jn[3 * p + c];
+                D.D2[q] = a2r[c];
+                D.D3[q] = a3r[c];
+            }
+            D.Tr[i] = t;
+            if (D.nb_opt > 0) {
+                const int32_t ct = cnt_true[p];
+                double f = pow((double)D.nb_opt / (double)(ct > 0 ? ct : 1), 2.0 / 3.0);
+                f = f < 0.5 ? 0.5 : (f > 2.0 ? 2.0 : f);
+                D.rs2[i] *= f;
+            }
+        }
+        // Hermite corrector on the total force
+        const double h = t - D.tl[i];
+        double a2[3], a3[3], a2e[3];
+        for (int c = 0; c < 3; ++c) {
+            const int64_t q = 3 * i + c;
+            const double da = D.a[q] - a1[c];
+            a2[c] = (-6.0 * da - h * (4.0 * D.jk[q] + 2.0 * j1[c])) / (h * h);
+            a3[c] = (12.0 * da + 6.0 * h * (D.jk[q] + j1[c])) / (h * h * h);
+            D.x[q] = D.xp[q] + h * h * h * h / 24.0 * a2[c] + h * h * h * h * h / 120.0 * a3[c];
+            D.v[q] = D.vp[q] + h * h * h / 6.0 * a2[c] + h * h * h * h / 24.0 * a3[c];
+            D.a[q] = a1[c];
+            D.jk[q] = j1[c];
+            a2e[c] = a2[c] + h * a3[c];
+        }
+        D.tl[i] = t;
+        const double crit = ac_crit(D.eta_irr, a1, j1, a2e, a3);
+        int L = ac_level_rule(D.LI[i], crit, t_ticks, D.lmin, D.lmax);
+        if (p >= 0) {
+            if (D.LR[i] > L) D.LR[i] = L;  // regular step at least the new irregular step
+        } else if (L < D.LR[i]) {
+            L = D.LR[i];  // irregular step at most the regular step
+        }
+        D.LI[i] = L;
+        want[k] = L;
+    }
+}
+
+// The regular subset's new lists (CSR) replace the old per-particle lists; one warp per row.
+__global__ void k_ac_lists(AcDev D, int64_t n_reg, const int32_t *reg_idx, const int64_t *off, const int32_t *csr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = w0; p < n_reg; p += nw) {
+        const int32_t i = reg_idx[p];
+        const int64_t e0 = off[p], len = off[p + 1] - off[p];
+        for (int64_t e = lane; e < len; e += 32) D.ell[(int64_t)i * D.cap + e] = csr[e0 + e];
+        if (lane == 0) D.ell_cnt[i] = (int32_t)len;
+    }
+}
+
+__global__ void k_ac_get_steps(const AcDev D, int64_t n, double *dt, double *DT, double *T)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (dt) dt[i] = ldexp(1.0, -D.LI[i]);
+        if (DT) DT[i] = ldexp(1.0, -D.LR[i]);
+        if (T) T[i] = D.Tr[i];
+    }
+}
+
+static int grid_of(int64_t n, int block, int cap_ctas)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g > cap_ctas) g = cap_ctas;
+    return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace nbgpu
+
+using namespace nbgpu;
+
+struct nb_ac {
+    nb_ctx *ctx = nullptr;
+    nb_sched *sched = nullptr;
+    CtxState cs{};
+    AcDev D{};
+    int64_t n = 0;
+    nb_ac_params p{};
+    // scratch
+    int32_t *reg_pos = nullptr, *reg_idx = nullptr, *want = nullptr, *cnt_true = nullptr, *csr = nullptr;
+    int64_t *off = nullptr;
+    double *reg_rs2 = nullptr, *Fo = nullptr, *Jo = nullptr, *Po = nullptr, *Fa = nullptr, *Ja = nullptr,
+           *Pa = nullptr, *Fn = nullptr, *Jn = nullptr, *Pn = nullptr;
+    unsigned *counter = nullptr, *h_counter = nullptr;
+    unsigned long long *pairs = nullptr;
+    double stats[6] = {0, 0, 0, 0, 0, 0};
+    char err[384] = {0};
+};
+
+static nb_status afail(nb_ac *s, nb_status st, const char *fmt, ...)
+{
+    if (s) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(s->err, sizeof(s->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define ACK(call, what)                                                                            \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess) return afail(s, NB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(_e)); \
+    } while (0)
+
+#define ANB(call, what)                                                                  \
+    do {                                                                                 \
+        nb_status _s = (call);                                                           \
+        if (_s != NB_OK && _s != NB_ERR_NB_OVERFLOW)                                     \
+            return afail(s, _s, "%s: %s", what, nb_last_error(s->ctx));                  \
+    } while (0)
+
+extern "C" {
+
+nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v,
+                     const double *rs2, const nb_ac_params *p, int32_t on_device)
+{
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    if (!ctx || !m || !x || !v || !rs2 || !p || n < 1) return NB_ERR_ARG;
+    if (!(p->dt_max > 0.0) || p->level_max > kAcTick || !(p->eta_irr > 0.0) || !(p->eta_reg > 0.0) ||
+        !(p->eta_s > 0.0))
+        return NB_ERR_ARG;
+    int fe = 0;
+    const double fr = std::frexp(p->dt_max, &fe);
+    const int lmin = 1 - fe;  // dt_max = 2^-lmin
+    if (fr != 0.5 || lmin < 0 || lmin > p->level_max) return NB_ERR_ARG;
+    nb_ac *s = new (std::nothrow) nb_ac();
+    if (!s) return NB_ERR_OOM;
+    s->ctx = ctx;
+    s->n = n;
+    s->p = *p;
+    auto bail = [&](nb_status st) {
+        nb_ac_free(s);
+        return st;
+    };
+    // the context takes the state at t = 0: zero force and jerk until the first evaluation
+    {
+        double *z = nullptr;
+        if (cudaMalloc(&z, (size_t)n * 3 * sizeof(double)) != cudaSuccess) return bail(NB_ERR_OOM);
+        cudaMemset(z, 0, (size_t)n * 3 * sizeof(double));
+        const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        double *dx = nullptr, *dv = nullptr, *dm = nullptr;
+        if (cudaMalloc(&dx, n * 24) != cudaSuccess || cudaMalloc(&dv, n * 24) != cudaSuccess ||
+            cudaMalloc(&dm, n * 8) != cudaSuccess) {
+            cudaFree(z); cudaFree(dx); cudaFree(dv); cudaFree(dm);
+            return bail(NB_ERR_OOM);
+        }
+        cudaMemcpy(dx, x, n * 24, k);
+        cudaMemcpy(dv, v, n * 24, k);
+        cudaMemcpy(dm, m, n * 8, k);
+        nb_status st = nb_set_particles(ctx, n, dx, dv, z, z, dm, z, 1);
+        if (st == NB_OK) st = nb_sync(ctx);
+        cudaFree(z); cudaFree(dx); cudaFree(dv); cudaFree(dm);
+        if (st != NB_OK) return bail(afail(s, st, "nb_set_particles: %s", nb_last_error(ctx)));
+    }
+    if (!ctx_state(ctx, &s->cs)) return bail(NB_ERR_STATE);
+    const int cap = s->cs.cap;
+    cudaStream_t st = s->cs.stream;
+    const size_t v3 = (size_t)n * 3 * sizeof(double);
+    AcDev &D = s->D;
+    bool ok = cudaMalloc(&D.Fr, v3) == cudaSuccess && cudaMalloc(&D.Jr, v3) == cudaSuccess &&
+              cudaMalloc(&D.D2, v3) == cudaSuccess && cudaMalloc(&D.D3, v3) == cudaSuccess &&
+              cudaMalloc(&D.rs2, n * 8) == cudaSuccess && cudaMalloc(&D.Tr, n * 8) == cudaSuccess &&
+              cudaMalloc(&D.LR, n * 4) == cudaSuccess && cudaMalloc(&D.LI, n * 4) == cudaSuccess &&
+              cudaMalloc(&D.ell, (size_t)n * cap * 4) == cudaSuccess && cudaMalloc(&D.ell_cnt, n * 4) == cudaSuccess &&
+              cudaMalloc(&s->reg_pos, n * 4) == cudaSuccess && cudaMalloc(&s->reg_idx, n * 4) == cudaSuccess &&
+              cudaMalloc(&s->want, n * 4) == cudaSuccess && cudaMalloc(&s->cnt_true, n * 4) == cudaSuccess &&
+              cudaMalloc(&s->csr, (size_t)n * cap * 4 + 4) == cudaSuccess &&
+              cudaMalloc(&s->off, (n + 1) * 8) == cudaSuccess && cudaMalloc(&s->reg_rs2, n * 8) == cudaSuccess &&
+              cudaMalloc(&s->Fo, v3) == cudaSuccess && cudaMalloc(&s->Jo, v3) == cudaSuccess &&
+              cudaMalloc(&s->Po, n * 8) == cudaSuccess && cudaMalloc(&s->Fa, v3) == cudaSuccess &&
+              cudaMalloc(&s->Ja, v3) == cudaSuccess && cudaMalloc(&s->Pa, n * 8) == cudaSuccess &&
+              cudaMalloc(&s->Fn, v3) == cudaSuccess && cudaMalloc(&s->Jn, v3) == cudaSuccess &&
+              cudaMalloc(&s->Pn, n * 8) == cudaSuccess && cudaMalloc(&s->counter, 4) == cudaSuccess &&
+              cudaMallocHost(&s->h_counter, 4) == cudaSuccess && cudaMalloc(&s->pairs, 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return bail(NB_ERR_OOM);
+    }
+    D.x = s->cs.x; D.v = s->cs.v; D.a = s->cs.a; D.jk = s->cs.jk; D.tl = s->cs.tl; D.m = s->cs.m;
+    D.xp = s->cs.xp; D.vp = s->cs.vp;
+    D.cap = cap;
+    D.lmin = lmin;
+    D.lmax = p->level_max;
+    D.eta_irr = p->eta_irr;
+    D.eta_reg = p->eta_reg;
+    D.dt_max = p->dt_max;
+    D.nb_opt = p->nb_opt;
+    ACK(cudaMemcpyAsync(D.rs2, rs2, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+        "copy rs2");
+    // all forces and lists at t = 0
+    ANB(nb_predict(ctx, 0.0), "nb_predict");
+    k_iota32<<<grid_of(n, 256, 152 * 16), 256, 0, st>>>(s->reg_idx, n);
+    ANB(nb_regular_force(ctx, n, s->reg_idx, D.rs2, 0, s->Fa, s->Ja, s->Pa, s->off, s->csr, n * cap, s->cnt_true, 1),
+        "nb_regular_force");
+    launch_irregular(st, s->cs.precision, s->cs.num_sms, s->cs.rec, 1, n, 0.0, n, s->reg_idx, s->off, s->csr, s->Fn,
+                     s->Jn, s->Pn, nullptr, nullptr, nullptr, s->cs.status);
+    k_ac_init<<<grid_of(n, 256, 152 * 16), 256, 0, st>>>(D, n, s->Fa, s->Ja, s->Fn, s->Jn, s->off, s->csr, p->eta_s,
+                                                          s->want);
+    ACK(cudaGetLastError(), "init launch");
+    ANB(nb_sync(ctx), "initial forces");
+    nb_status ss = nb_sched_init(&s->sched, n, s->want, lmin, p->level_max, s->cs.device, (void *)st, 1);
+    if (ss != NB_OK) return bail(afail(s, ss, "nb_sched_init"));
+    *out = s;
+    return NB_OK;
+}
+
+nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_regular)
+{
+    if (!s) return NB_ERR_ARG;
+    double t = 0.0;
+    int64_t na = 0;
+    const int32_t *list = nullptr;
+    nb_status ss = nb_sched_next(s->sched, &t, &na, &list);
+    if (ss != NB_OK) return afail(s, ss, "nb_sched_next: %s", nb_sched_last_error(s->sched));
+    const CtxState &cs = s->cs;
+    cudaStream_t st = cs.stream;
+    const int64_t t_ticks = (int64_t)std::ldexp(t, kAcTick);
+    const int cap = cs.cap;
+    ACK(cudaMemsetAsync(s->counter, 0, 4, st), "memset");
+    k_ac_classify<<<grid_of(na, 256, 152 * 16), 256, 0, st>>>(s->D, na, list, t_ticks, s->counter, s->reg_pos,
+                                                               s->reg_idx, s->reg_rs2);
+    ACK(cudaGetLastError(), "classify launch");
+    ACK(cudaMemcpyAsync(s->h_counter, s->counter, 4, cudaMemcpyDeviceToHost, st), "copy count");
+    ANB(nb_predict(s->ctx, t), "nb_predict");
+    ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    const int64_t nr = *s->h_counter;
+    if (nr > 0)
+        ANB(nb_regular_force(s->ctx, nr, s->reg_idx, s->reg_rs2, 0, s->Fa, s->Ja, s->Pa, s->off, s->csr, nr * cap,
+                             s->cnt_true, 1),
+            "nb_regular_force");
+    launch_irregular(st, cs.precision, cs.num_sms, cs.rec, 1, cs.n, t, na, list, nullptr, s->D.ell, s->Fo, s->Jo,
+                     s->Po, nullptr, nullptr, nullptr, cs.status, s->D.ell_cnt, cap);
+    if (nr > 0)
+        launch_irregular(st, cs.precision, cs.num_sms, cs.rec, 1, cs.n, t, nr, s->reg_idx, s->off, s->csr, s->Fn,
+                         s->Jn, s->Pn, nullptr, nullptr, nullptr, cs.status);
+    ACK(cudaMemsetAsync(s->pairs, 0, 8, st), "memset");
+    k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks, s->reg_pos, s->Fo, s->Jo,
+                                                              s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
+                                                              s->pairs);
+    if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);
+    ACK(cudaGetLastError(), "corrector launch");
+    unsigned long long pairs = 0;
+    ACK(cudaMemcpyAsync(&pairs, s->pairs, 8, cudaMemcpyDeviceToHost, st), "copy pairs");
+    ANB(nb_sync(s->ctx), "block step");
+    ss = nb_sched_update(s->sched, s->want, nullptr, 1);
+    if (ss != NB_OK) return afail(s, ss, "nb_sched_update: %s", nb_sched_last_error(s->sched));
+    s->stats[0] += 1;
+    s->stats[1] += (double)na;
+    s->stats[2] += (double)nr;
+    s->stats[3] += (double)pairs;
+    s->stats[4] += (double)nr * (double)(cs.n - 1);
+    if (t_block) *t_block = t;
+    if (n_active) *n_active = na;
+    if (n_regular) *n_regular = nr;
+    return NB_OK;
+}
+
+nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats)
+{
+    if (!s) return NB_ERR_ARG;
+    int64_t b = 0;
+    nb_status rc = NB_OK;
+    for (;;) {
+        double tn = 0.0;
+        nb_status ss = nb_sched_peek(s->sched, &tn);
+        if (ss != NB_OK) return afail(s, ss, "nb_sched_peek");
+        if (tn > t_end) break;
+        if (max_blocks > 0 && b >= max_blocks) {
+            rc = NB_ERR_STATE;
+            afail(s, rc, "max_blocks reached");
+            break;
+        }
+        if ((ss = nb_ac_step(s, nullptr, nullptr, nullptr)) != NB_OK) return ss;
+        ++b;
+    }
+    if (stats) memcpy(stats, s->stats, sizeof(s->stats));
+    return rc;
+}
+
+nb_status nb_ac_get(nb_ac *s, double *x, double *v, double *t, double *dt, double *DT, double *T, double *rs2,
+                    int32_t *nb_count, int32_t *nb_lists, int32_t on_device)
+{
+    if (!s) return NB_ERR_ARG;
+    const int64_t n = s->n;
+    cudaStream_t st = s->cs.stream;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (x) ACK(cudaMemcpyAsync(x, s->D.x, n * 24, k, st), "copy x");
+    if (v) ACK(cudaMemcpyAsync(v, s->D.v, n * 24, k, st), "copy v");
+    if (t) ACK(cudaMemcpyAsync(t, s->D.tl, n * 8, k, st), "copy t");
+    if (rs2) ACK(cudaMemcpyAsync(rs2, s->D.rs2, n * 8, k, st), "copy rs2");
+    if (nb_count) ACK(cudaMemcpyAsync(nb_count, s->D.ell_cnt, n * 4, k, st), "copy counts");
+    if (nb_lists) ACK(cudaMemcpyAsync(nb_lists, s->D.ell, (size_t)n * s->D.cap * 4, k, st), "copy lists");
+    if (dt || DT || T) {
+        double *tmp = s->Fo;  // 3n doubles of scratch
+        k_ac_get_steps<<<grid_of(n, 256, 152 * 16), 256, 0, st>>>(s->D, n, dt ? tmp : nullptr, DT ? tmp + n : nullptr,
+                                                                   T ? tmp + 2 * n : nullptr);
+        ACK(cudaGetLastError(), "steps launch");
+        if (dt) ACK(cudaMemcpyAsync(dt, tmp, n * 8, k, st), "copy dt");
+        if (DT) ACK(cudaMemcpyAsync(DT, tmp + n, n * 8, k, st), "copy DT");
+        if (T) ACK(cudaMemcpyAsync(T, tmp + 2 * n, n * 8, k, st), "copy T");
+    }
+    ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
+nb_status nb_ac_free(nb_ac *s)
+{
+    if (!s) return NB_OK;
+    if (s->cs.stream) cudaStreamSynchronize(s->cs.stream);
+    if (s->sched) nb_sched_free(s->sched);
+    void *p[] = {s->D.Fr, s->D.Jr, s->D.D2, s->D.D3, s->D.rs2, s->D.Tr, s->D.LR, s->D.LI, s->D.ell, s->D.ell_cnt,
+                 s->reg_pos, s->reg_idx, s->want, s->cnt_true, s->csr, s->off, s->reg_rs2, s->Fo, s->Jo, s->Po,
+                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    if (s->h_counter) cudaFreeHost(s->h_counter);
+    delete s;
+    return NB_OK;
+}
+
+const char *nb_ac_last_error(const nb_ac *s) { return s ? s->err : "null integrator"; }
+
+}  // extern "C"

@@ -70,14 +70,22 @@ struct IrrArgs {
     double *acc, *jerk, *pot;
     double *acc_reg, *jerk_reg, *pot_reg;  // optional: all-j sums in, outside-list part out
     unsigned *status;
+    const int32_t *ell_cnt;  // per-particle lists: i's list is nb[i * ell_stride .. + ell_cnt[i])
+    int64_t ell_stride;      // 0: CSR lists (off)
 };
 
 // Row k's checked index and list range (an empty range and a status bit when malformed).
 __device__ __forceinline__ bool irr_row(const IrrArgs &A, int64_t k, int lane, int64_t &i, int64_t &e0, int64_t &e1)
 {
     i = A.idx[k];
-    e0 = A.off[k];
-    e1 = A.off[k + 1];
+    if (A.ell_stride > 0) {
+        const bool in = i >= 0 && i < A.n;
+        e0 = in ? i * A.ell_stride : 0;
+        e1 = in ? e0 + A.ell_cnt[i] : 0;
+    } else {
+        e0 = A.off[k];
+        e1 = A.off[k + 1];
+    }
     const bool ok = i >= 0 && i < A.n && e0 >= 0 && e1 >= e0;
     if (!ok) {
         if (lane == 0) atomicOr(A.status, ST_BAD_INDEX);
@@ -330,7 +338,8 @@ size_t state_record_bytes(int precision, int64_t n) { return (size_t)n * (precis
 // predicted j-records of the predict-all form.
 void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
                       double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
-                      double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status)
+                      double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status,
+                      const int32_t *ell_cnt, int64_t ell_stride)
 {
     IrrArgs A;
     A.srec = srec;
@@ -349,6 +358,8 @@ void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *s
     A.jerk_reg = jerk_reg;
     A.pot_reg = pot_reg;
     A.status = status;
+    A.ell_cnt = ell_cnt;
+    A.ell_stride = ell_stride;
     constexpr int rows_per_cta = kIrrBlock / 32;
     int64_t g = (n_i + rows_per_cta - 1) / rows_per_cta;
     const int64_t gmax = (int64_t)num_sms * 8;  // 8 CTAs of 8 warps: 64 warps per SM

@@ -42,9 +42,6 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 size_t state_record_bytes(int precision, int64_t n);
 void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
                        const double *jk, const double *tl, const double *m, void *srec);
-void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
-                      double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
-                      double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status);
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
@@ -432,6 +429,16 @@ void launch_force(cudaStream_t st, const Plan &p, ForceArgs a)
         launch_force_fp64(st, p.kernel, p.variant, ctas_x, p.S, a);
 }
 
+}  // namespace nbgpu
+
+namespace nbgpu {
+bool ctx_state(nb_ctx *c, CtxState *o)
+{
+    if (!c || c->broken || !c->have_state) return false;
+    *o = CtxState{c->x, c->v, c->a, c->jk, c->tl, c->m, c->xp, c->vp, c->rec, c->status, c->stream,
+                  c->precision, c->cap, c->num_sms, c->device, c->n, c->n_pad};
+    return true;
+}
 }  // namespace nbgpu
 
 // ------------------------------------------------------------------------------ ABI

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct nb_ctx;
+
 namespace nbgpu {
 
 // Predicted j-records.
@@ -97,5 +99,23 @@ int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap
                          int64_t *scan_tmp, int32_t *row_total, unsigned *status);
 
 size_t neighbour_scan_tmp_elems(int64_t n_i);
+
+// Device state of a context, for the integrator inside the library (nb_api.cu).
+struct CtxState {
+    double *x, *v, *a, *jk, *tl, *m, *xp, *vp;
+    void *rec;  // predicted j-records of the last nb_predict
+    unsigned *status;
+    cudaStream_t stream;
+    int precision, cap, num_sms, device;
+    int64_t n, n_pad;
+};
+bool ctx_state(::nb_ctx *c, CtxState *out);
+
+// Irregular force (irregular.cu).  Lists as CSR (off) or, with ell_stride > 0, per
+// particle: particle i's list is nb[i * ell_stride .. + ell_cnt[i]).
+void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
+                      double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
+                      double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status,
+                      const int32_t *ell_cnt = nullptr, int64_t ell_stride = 0);
 
 }  // namespace nbgpu

@@ -417,6 +417,20 @@ nb_status nb_sched_counts(const nb_sched *s, int64_t *counts)
     return NB_OK;
 }
 
+nb_status nb_sched_peek(const nb_sched *s, double *t_next)
+{
+    if (!s || !t_next) return NB_ERR_ARG;
+    int lmax_present = -1;
+    for (int b = kBins - 1; b >= 0; --b)
+        if (s->count[b]) {
+            lmax_present = b;
+            break;
+        }
+    if (lmax_present < 0) return NB_ERR_STATE;
+    *t_next = std::ldexp((double)(s->T + ((int64_t)1 << (kTick - lmax_present))), -kTick);
+    return NB_OK;
+}
+
 const char *nb_sched_last_error(const nb_sched *s) { return s ? s->err : "null scheduler"; }
 
 }  // extern "C"

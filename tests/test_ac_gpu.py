@@ -1,0 +1,94 @@
+"""The device Ahmad-Cohen integrator (nb_ac_*) against the reference AC integrator of the
+oracle (orc_ac_run), both started from the same cluster and run for the same block steps.
+
+Bars: FP64 context — block times, steps, regular-step times, list lengths and lists
+identical, r_s^2 to 1e-12 relative (one library power function each side), positions and
+velocities to 1e-9 relative after 300 block steps (the predictor and the summation order
+differ at rounding level and the differences grow with the orbits); mixed context — energy
+conserved to 2e-5 at t = 1/4 and within a factor 4 of the reference run's own error, or
+below 2e-6."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def make(n, prec, cap):
+    from paper_1504_03687_gb300 import Context
+    return Context(n, precision=prec, nb_cap=cap)
+
+
+def test_ac_fp64_follows_the_reference_step_for_step(gpu_lib):
+    from paper_1504_03687_gb300 import ACIntegrator
+    cl, rs2 = W.plummer_1k_equal()
+    K = 300
+    kw = dict(eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125, nb_opt=50)
+    ox, ov, ors2, info = oracle.ac_run(cl.m, cl.x, cl.v, rs2, 100.0, cap=256, max_blocks=K, **kw)
+    assert info["rc"] == -2 and info["blocks"] == K
+    ctx = make(cl.n, "fp64", 256)
+    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, level_max=40, **kw)
+    n_act = n_reg = 0
+    for _ in range(K):
+        t, na, nr = ac.step()
+        n_act += na
+        n_reg += nr
+    g = ac.get()
+    assert n_act == info["irregular_steps"] and n_reg == info["regular_steps"]
+    for k in ("t", "dt", "DT", "T"):
+        np.testing.assert_array_equal(g[k], info[k], err_msg=k)
+    np.testing.assert_array_equal(g["nb_count"], info["nb_count"])
+    for i in range(cl.n):
+        np.testing.assert_array_equal(g["nb_lists"][i, :g["nb_count"][i]], info["nb_lists"][i])
+    np.testing.assert_allclose(g["rs2"], ors2, rtol=1e-12)
+    np.testing.assert_allclose(g["x"], ox, rtol=1e-9, atol=1e-9 * np.abs(ox).max())
+    np.testing.assert_allclose(g["v"], ov, rtol=1e-9, atol=1e-9 * np.abs(ov).max())
+    ac.close()
+    ctx.close()
+
+
+def test_ac_every_particle_a_neighbour_is_plain_hermite(gpu_lib):
+    """r_s covering the system, fixed: the device AC run is the plain block-step Hermite run
+    (the reference's reduction, pinned against the Kepler orbit), to rounding."""
+    import ctypes
+    from paper_1504_03687_gb300 import ACIntegrator
+    cl = W.plummer(256, 102)
+    xh, vh = cl.x.copy(), cl.v.copy()
+    st = np.zeros(4)
+    lib = oracle._load()
+    assert lib.orc_hermite_run(256, cl.m.ctypes.data, xh.ctypes.data, vh.ctypes.data, ctypes.c_double(0.125),
+                               ctypes.c_double(0.02), ctypes.c_double(0.01), ctypes.c_double(0.125),
+                               ctypes.c_double(0.0), ctypes.c_int64(0), st.ctypes.data) == 0
+    ctx = make(256, "fp64", 256)
+    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, 1e300, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125, nb_opt=0)
+    s = ac.run(0.125, max_blocks=20000)
+    g = ac.get()
+    assert s["blocks"] == int(st[0]) and s["irregular_steps"] == int(st[1])
+    assert np.all(g["t"] == 0.125)
+    np.testing.assert_allclose(g["x"], xh, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(g["v"], vh, rtol=1e-10, atol=1e-12)
+    ac.close()
+    ctx.close()
+
+
+def test_ac_mixed_conserves_energy(gpu_lib):
+    from paper_1504_03687_gb300 import ACIntegrator
+    cl = W.plummer(4096, 103)
+    rs2 = W.neighbour_radius2(cl.x, 50, seed=103)
+    kw = dict(eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125, nb_opt=50)
+    E0 = sum(oracle.energy(cl.m, cl.x, cl.v))
+    ox, ov, _, info = oracle.ac_run(cl.m, cl.x, cl.v, rs2, 0.25, cap=256, **kw)
+    e_ref = abs(sum(oracle.energy(cl.m, ox, ov)) - E0) / abs(E0)
+    ctx = make(cl.n, "mixed", 256)
+    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
+    s = ac.run(0.25, max_blocks=200000)
+    g = ac.get()
+    assert np.all(g["t"] == 0.25) and np.all(g["dt"] <= g["DT"])
+    e = abs(sum(oracle.energy(cl.m, g["x"], g["v"])) - E0) / abs(E0)
+    assert e < 2e-5 and (e < 4 * e_ref or e < 2e-6), (e, e_ref)
+    assert s["regular_steps"] < 0.5 * s["irregular_steps"]
+    assert 35 <= np.median(g["nb_count"]) <= 70
+    ac.close()
+    ctx.close()

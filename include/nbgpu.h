@@ -216,6 +216,21 @@ nb_status nb_get_timings(nb_ctx *ctx, double *ms, int64_t *launches);
  * raised since the previous nb_sync; the deferred status is then cleared. */
 nb_status nb_sync(nb_ctx *ctx);
 
+/* Fault injection for testing error handling (no counterpart in the paper).  Arms a
+ * simulated runtime failure on the host: after `after` more operations of `kind`, the next
+ * one reports the error the CUDA runtime would, and the GPU is never touched:
+ *   NB_FAULT_ALLOC  a device allocation of the context's scratch -> NB_ERR_OOM; the context
+ *                   stays usable (the call can be retried);
+ *   NB_FAULT_SYNC   a stream synchronisation -> NB_ERR_CUDA, as after a failed kernel; the
+ *                   context becomes unusable (NB_ERR_STATE from then on; nb_free it);
+ *   NB_FAULT_STATUS the read of the deferred device status -> NB_ERR_CUDA, likewise.
+ * kind 0 disarms.  The environment variable NB_FAULT = "alloc:N", "sync:N" or "status:N"
+ * arms the same at nb_init. */
+#define NB_FAULT_ALLOC 1
+#define NB_FAULT_SYNC 2
+#define NB_FAULT_STATUS 3
+nb_status nb_inject_fault(nb_ctx *ctx, int32_t kind, int32_t after);
+
 /* One-line description of the last error on this context (never NULL). */
 const char *nb_last_error(const nb_ctx *ctx);
 

@@ -31,7 +31,9 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
            "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force", "nb_sched_init", "nb_sched_free",
            "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error",
-           "nb_sched_peek", "nb_ac_init", "nb_ac_step", "nb_ac_run", "nb_ac_get", "nb_ac_free", "nb_ac_last_error")
+           "nb_sched_peek", "nb_ac_init", "nb_ac_step", "nb_ac_run", "nb_ac_get", "nb_ac_free", "nb_ac_last_error",
+           "nb_inject_fault")
+NB_FAULT_ALLOC, NB_FAULT_SYNC, NB_FAULT_STATUS = 1, 2, 3
 NB_SOURCE_ALIGN = 256
 
 
@@ -89,6 +91,7 @@ def load_library(build_if_needed: bool = True):
         "nb_batch_plan": (st, [P, i64, P, P, i32]),
         "nb_set_plan_table": (st, [P, i32, P, P, P, P]),
         "nb_set_source_range": (st, [P, i64, i64]),
+        "nb_inject_fault": (st, [P, i32, i32]),
         "nb_sched_init": (st, [ctypes.POINTER(P), i64, P, i32, i32, i32, P, i32]),
         "nb_sched_free": (st, [P]),
         "nb_sched_next": (st, [P, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(P)]),
@@ -429,6 +432,10 @@ class Context:
         """nb_set_source_range: later regular_force calls sum over source particles j in
         [j_lo, j_hi) only; (0, 0) = all particles."""
         self._check(self.lib.nb_set_source_range(self.h, int(j_lo), int(j_hi)), "nb_set_source_range")
+
+    def inject_fault(self, kind: int, after: int = 0):
+        """nb_inject_fault: arm a simulated allocation / synchronisation / status-read failure."""
+        self._check(self.lib.nb_inject_fault(self.h, int(kind), int(after)), "nb_inject_fault")
 
     def set_plan_override(self, kernel: int = -1, variant: int = 0, splits: int = 1):
         """Force (kernel, variant, splits) for later regular_force calls; kernel < 0 = automatic."""

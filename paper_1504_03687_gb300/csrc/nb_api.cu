@@ -100,6 +100,9 @@ struct nb_ctx {
     std::vector<Span> spans;
     std::vector<cudaEvent_t> evpool;
     int64_t launches[8] = {0};
+    // test hook (nb_inject_fault / NB_FAULT): the operation of kind fault_kind that comes
+    // after fault_after more of its kind reports the failure the CUDA runtime would
+    int fault_kind = 0, fault_after = 0;
 };
 
 enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_IRREGULAR = 5, PH_COUNT = 6 };
@@ -164,6 +167,22 @@ static nb_status cuda_fail(nb_ctx *c, cudaError_t e, const char *what)
 
 #define CK_LAUNCH(what) CK(cudaGetLastError(), what)
 
+// Simulated runtime failure for the fault-injection hook: true once, when the armed kind's
+// countdown reaches zero.  Nothing touches the GPU.
+static bool take_fault(nb_ctx *c, int kind)
+{
+    if (!c || c->fault_kind != kind) return false;
+    if (c->fault_after-- > 0) return false;
+    c->fault_kind = 0;
+    return true;
+}
+
+static cudaError_t ctx_sync(nb_ctx *c)
+{
+    if (take_fault(c, NB_FAULT_SYNC)) return cudaErrorLaunchFailure;
+    return cudaStreamSynchronize(c->stream);
+}
+
 static nb_status grow(nb_ctx *c, void **p, size_t *cap, size_t need_bytes, const char *what)
 {
     if (need_bytes <= *cap && *p) return NB_OK;
@@ -177,7 +196,7 @@ static nb_status grow(nb_ctx *c, void **p, size_t *cap, size_t need_bytes, const
     }
     size_t bytes = need_bytes < 256 ? 256 : need_bytes;
     bytes = bytes + bytes / 4;  // headroom to avoid regrowth on small changes
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = take_fault(c, NB_FAULT_ALLOC) ? cudaErrorMemoryAllocation : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         return cuda_fail(c, e, what);
@@ -209,9 +228,11 @@ static nb_status status_from_flags(nb_ctx *c, unsigned f)
 
 static nb_status sync_and_collect(nb_ctx *c)
 {
-    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    CK(ctx_sync(c), "cudaStreamSynchronize");
     unsigned f = 0;
-    CK(cudaMemcpy(&f, c->status + SS_FLAGS, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+    CK(take_fault(c, NB_FAULT_STATUS) ? cudaErrorUnknown
+                                      : cudaMemcpy(&f, c->status + SS_FLAGS, sizeof(unsigned), cudaMemcpyDeviceToHost),
+       "read status");
     CK(cudaMemset(c->status + SS_FLAGS, 0, sizeof(unsigned)), "clear status");
     return status_from_flags(c, f);
 }
@@ -460,6 +481,16 @@ nb_status nb_init(nb_ctx **out, const nb_config *cfg)
     c->precision = cfg->precision;
     c->cap = cfg->nb_cap;
     c->n_max = cfg->n_max;
+    if (const char *f = getenv("NB_FAULT")) {  // "alloc:N", "sync:N" or "status:N"
+        int after = 0;
+        char kind[16] = {0};
+        if (sscanf(f, "%15[a-z]:%d", kind, &after) >= 1) {
+            c->fault_after = after;
+            c->fault_kind = !strcmp(kind, "alloc") ? NB_FAULT_ALLOC
+                            : !strcmp(kind, "sync") ? NB_FAULT_SYNC
+                            : !strcmp(kind, "status") ? NB_FAULT_STATUS : 0;
+        }
+    }
     auto bail = [&](nb_status s) {
         nb_free(c);
         return s;
@@ -547,7 +578,7 @@ nb_status nb_set_particles(nb_ctx *c, int64_t n, const double *x, const double *
     c->have_state = true;
     c->srec_valid = false;
     c->have_pred = false;
-    if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (!on_device) CK(ctx_sync(c), "cudaStreamSynchronize");
     return NB_OK;
 }
 
@@ -583,7 +614,7 @@ nb_status nb_set_predicted(nb_ctx *c, int64_t n, const double *xp, const double 
     CK_LAUNCH("k_pack launch");
     c->have_state = false;
     c->have_pred = true;
-    if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (!on_device) CK(ctx_sync(c), "cudaStreamSynchronize");
     return NB_OK;
 }
 
@@ -597,7 +628,7 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, int32_t on_device)
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(xp, c->xp, b3, kind, c->stream), "cudaMemcpyAsync");
     CK(cudaMemcpyAsync(vp, c->vp, b3, kind, c->stream), "cudaMemcpyAsync");
-    if (!on_device) CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (!on_device) CK(ctx_sync(c), "cudaStreamSynchronize");
     return NB_OK;
 }
 
@@ -685,6 +716,14 @@ nb_status nb_set_plan_override(nb_ctx *c, int32_t kernel, int32_t variant, int32
     c->force_kernel = kernel;
     c->force_variant = variant;
     c->force_splits = splits;
+    return NB_OK;
+}
+
+nb_status nb_inject_fault(nb_ctx *c, int32_t kind, int32_t after)
+{
+    if (!c || kind < 0 || kind > NB_FAULT_STATUS || after < 0) return NB_ERR_ARG;
+    c->fault_kind = kind;
+    c->fault_after = after;
     return NB_OK;
 }
 
@@ -815,7 +854,7 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         CK(cudaMemcpyAsync(nb_count_true, d_cnt_true, (size_t)n_i * 4, cudaMemcpyDeviceToHost, c->stream), "copy counts");
     if (nb_off) {
         CK(cudaMemcpyAsync(nb_off, d_off, ((size_t)n_i + 1) * 8, cudaMemcpyDeviceToHost, c->stream), "copy offsets");
-        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        CK(ctx_sync(c), "cudaStreamSynchronize");
         if (nb_idx) {
             int64_t tot = nb_off[n_i] < nb_idx_capacity ? nb_off[n_i] : nb_idx_capacity;
             if (tot > 0)
@@ -987,7 +1026,7 @@ nb_status nb_get_timings(nb_ctx *c, double *ms, int64_t *launches)
     nb_status s = check_usable(c);
     if (s != NB_OK) return s;
     if (!ms || !launches) return fail(c, NB_ERR_ARG, "null array");
-    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    CK(ctx_sync(c), "cudaStreamSynchronize");
     for (int q = 0; q < PH_COUNT; ++q) {
         ms[q] = 0.0;
         launches[q] = c->launches[q];
@@ -1072,7 +1111,7 @@ nb_status nb_batch_plan(nb_ctx *c, int64_t n_clusters, const int64_t *cluster_of
     if ((s = grow(c, (void **)&c->scan, &c->scan_cap, (neighbour_scan_tmp_elems(rows) + r + 1) * 8, "scan scratch")) !=
         NB_OK)
         return s;
-    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    CK(ctx_sync(c), "cudaStreamSynchronize");
     const int occ = mixed_batched_occupancy(v);
     int64_t ctas = (int64_t)occ * c->num_sms;
     if (ctas > (int64_t)sorted.size()) ctas = (int64_t)sorted.size();

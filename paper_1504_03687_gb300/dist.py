@@ -150,3 +150,30 @@ def reduce_sources(acc, jerk, pot, nb_off=None, nb_idx=None, nb_count=None, nb_c
     idxs = gather_same(padded)
     parts = list(zip(accs, jerks, pots, offs, idxs, counts))
     return combine_source_shards(parts, nb_cap)
+
+
+class PeerLost(RuntimeError):
+    """A rank did not report between two steps within the heartbeat's limit."""
+
+
+class Heartbeat:
+    """Host-side liveness check between steps.  Every rank posts one key per step to the
+    store of its process group and, before it launches the next step's collectives, waits a
+    bounded time for the keys of all other ranks; a rank that has left is then noticed
+    between steps (PeerLost) rather than inside a collective, and no rank's GPU work is left
+    waiting on it."""
+
+    def __init__(self, store, rank: int, world: int, timeout_s: float = 10.0, prefix: str = "nbgpu/alive"):
+        self.store, self.rank, self.world = store, rank, world
+        self.timeout_s, self.prefix = timeout_s, prefix
+
+    def beat(self, step: int) -> None:
+        self.store.set(f"{self.prefix}/{step}/{self.rank}", "1")
+
+    def wait(self, step: int) -> None:
+        from datetime import timedelta
+        keys = [f"{self.prefix}/{step}/{r}" for r in range(self.world) if r != self.rank]
+        try:
+            self.store.wait(keys, timedelta(seconds=self.timeout_s))
+        except Exception as e:  # timeout, or the store's host rank has gone
+            raise PeerLost(f"step {step}: a rank did not report within {self.timeout_s} s") from e

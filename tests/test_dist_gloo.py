@@ -158,3 +158,63 @@ def test_source_sharded_exchange_matches_single_rank():
     cl, rs2 = W.plummer_1k_equal()
     idx = W.active_block(W.block_steps(cl, seed=0), 301)
     _check_against_full([torch.from_numpy(g) for g in got], cl, idx, rs2, 24)
+
+
+# ------------------------------------------------------------------ failure detection
+def _leave(out):
+    out.close()
+    out.join_thread()  # flush this process's messages before the hard exit
+    os._exit(0)
+
+
+def _dropout_worker(rank, world, port, out):
+    from datetime import timedelta
+    from paper_1504_03687_gb300.dist import Heartbeat, PeerLost
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=timedelta(seconds=30))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world, timeout=timedelta(seconds=20))
+    hb = Heartbeat(store, rank, world, timeout_s=3.0)
+    t = torch.full((4,), float(rank))
+    for step in range(3):
+        if rank == 1 and step == 1:
+            out.put(("left", rank, step))
+            _leave(out)  # leaves between steps: no collective is in flight, no heartbeat posted
+        hb.beat(step)
+        try:
+            hb.wait(step)
+        except PeerLost as e:
+            out.put(("lost", rank, step, str(e)))
+            _leave(out)
+        bufs = [torch.zeros(4) for _ in range(world)]
+        dist.all_gather(bufs, t)
+        out.put(("step", rank, step, [float(b[0]) for b in bufs]))
+    out.put(("done", rank))
+    _leave(out)
+
+
+def test_rank_leaving_between_steps_is_detected_by_heartbeat():
+    """Rank 1 leaves between steps 0 and 1 without posting its step-1 heartbeat; rank 0 must
+    report the loss at its step-1 check (a bounded store wait) and never enter the step-1
+    collective."""
+    import time
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dropout_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for pr in procs:
+        pr.start()
+    for pr in procs:
+        pr.join(timeout=90)
+        assert pr.exitcode == 0
+    msgs = []
+    while True:
+        try:
+            msgs.append(q.get(timeout=2))
+        except Exception:
+            break
+    assert time.time() - t0 < 80
+    assert ("step", 0, 0, [0.0, 1.0]) in msgs and ("step", 1, 0, [0.0, 1.0]) in msgs
+    assert ("left", 1, 1) in msgs
+    lost = [m for m in msgs if m[0] == "lost"]
+    assert len(lost) == 1 and lost[0][1] == 0 and lost[0][2] == 1
+    assert not any(m[0] == "step" and m[2] >= 1 for m in msgs)

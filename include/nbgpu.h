@@ -336,6 +336,12 @@ nb_status nb_sched_get(nb_sched *s, int32_t *list, int32_t *levels, double *t_no
 /* Particles per level, counts[64] (index = level), as of the last committed step. */
 nb_status nb_sched_counts(const nb_sched *s, int64_t *counts);
 
+/* Set the time of the last committed block step (a scheduler created from the levels of a
+ * run resumed at time t; every particle's last step time must be the latest multiple of
+ * its step not above t).  t must be a multiple of 2^-48 and of the smallest step present;
+ * only between block steps. */
+nb_status nb_sched_set_time(nb_sched *s, double t);
+
 /* Time of the next block step, without advancing (host only). */
 nb_status nb_sched_peek(const nb_sched *s, double *t_next);
 
@@ -398,6 +404,16 @@ nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats);
  * the last regular step time T, r_s^2, list lengths and lists (ascending j). */
 nb_status nb_ac_get(nb_ac *s, double *x, double *v, double *t, double *dt, double *DT, double *T,
                     double *rs2, int32_t *nb_count, int32_t *nb_lists, int32_t on_device);
+
+/* Checkpoint / resume.  nb_ac_snapshot_bytes gives the size of a snapshot; nb_ac_save
+ * writes the integrator's complete state between block steps (particles, regular-force
+ * history, steps, lists, r_s^2, time, counters) into the host buffer buf; nb_ac_restore
+ * creates an integrator on ctx (same precision and nb_cap as the saved one, n <= its n_max)
+ * from such a buffer.  The kernels give every particle the same result whatever the order
+ * of the active rows, so a resumed run continues bit for bit as the uninterrupted one. */
+nb_status nb_ac_snapshot_bytes(nb_ac *s, size_t *bytes);
+nb_status nb_ac_save(nb_ac *s, void *buf, size_t bytes);
+nb_status nb_ac_restore(nb_ac **out, nb_ctx *ctx, const void *buf, size_t bytes);
 
 /* Destroy the integrator (the context stays valid).  Safe on NULL. */
 nb_status nb_ac_free(nb_ac *s);

@@ -32,7 +32,7 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force", "nb_sched_init", "nb_sched_free",
            "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error",
            "nb_sched_peek", "nb_ac_init", "nb_ac_step", "nb_ac_run", "nb_ac_get", "nb_ac_free", "nb_ac_last_error",
-           "nb_inject_fault")
+           "nb_inject_fault", "nb_sched_set_time", "nb_ac_snapshot_bytes", "nb_ac_save", "nb_ac_restore")
 NB_FAULT_ALLOC, NB_FAULT_SYNC, NB_FAULT_STATUS = 1, 2, 3
 NB_SOURCE_ALIGN = 256
 
@@ -105,6 +105,10 @@ def load_library(build_if_needed: bool = True):
         "nb_ac_run": (st, [P, dbl, i64, P]),
         "nb_ac_get": (st, [P, P, P, P, P, P, P, P, P, P, i32]),
         "nb_ac_free": (st, [P]),
+        "nb_sched_set_time": (st, [P, dbl]),
+        "nb_ac_snapshot_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
+        "nb_ac_save": (st, [P, P, ctypes.c_size_t]),
+        "nb_ac_restore": (st, [ctypes.POINTER(P), P, P, ctypes.c_size_t]),
         "nb_ac_last_error": (ctypes.c_char_p, [P]),
         "nb_irregular_force": (st, [P, dbl, i64, P, P, P, P, P, P, P, P, P, i32]),
         "nb_regular_force_batched": (st, [P, P, P, P, P, P, P, P, i64, P]),
@@ -584,6 +588,31 @@ class ACIntegrator:
                                                  ("x", "v", "t", "dt", "DT", "T", "rs2", "nb_count", "nb_lists")], 0),
                     "nb_ac_get")
         return out
+
+    def save(self) -> bytes:
+        """nb_ac_save: the complete integrator state as bytes (a checkpoint)."""
+        nb = ctypes.c_size_t()
+        self._check(self.lib.nb_ac_snapshot_bytes(self.h, ctypes.byref(nb)), "nb_ac_snapshot_bytes")
+        buf = np.empty(nb.value, np.uint8)
+        self._check(self.lib.nb_ac_save(self.h, buf.ctypes.data, nb.value), "nb_ac_save")
+        return buf.tobytes()
+
+    @classmethod
+    def restore(cls, ctx: Context, blob: bytes) -> "ACIntegrator":
+        """nb_ac_restore: an integrator on ctx resumed from a checkpoint of save()."""
+        self = cls.__new__(cls)
+        self.ctx, self.lib = ctx, ctx.lib
+        buf = np.frombuffer(blob, np.uint8)
+        self.n = int(np.frombuffer(blob[8:16], np.int64)[0])
+        self.cap = ctx.nb_cap
+        ctx._bind_stream()
+        h = ctypes.c_void_p()
+        s = self.lib.nb_ac_restore(ctypes.byref(h), ctx.h, buf.ctypes.data, buf.size)
+        if s != NB_OK:
+            raise NBError(s, "nb_ac_restore failed")
+        self.h = h
+        ctx.n = self.n
+        return self
 
     def close(self):
         if getattr(self, "h", None):

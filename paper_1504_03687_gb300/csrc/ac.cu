@@ -295,6 +295,88 @@ static nb_status afail(nb_ac *s, nb_status st, const char *fmt, ...)
             return afail(s, _s, "%s: %s", what, nb_last_error(s->ctx));                  \
     } while (0)
 
+// Device arrays of the integrator and its per-step scratch (sizes from n and the list cap).
+static bool ac_alloc(nb_ac *s, int64_t n, int cap)
+{
+    const size_t v3 = (size_t)n * 3 * sizeof(double);
+    AcDev &D = s->D;
+    const bool ok =
+        cudaMalloc(&D.Fr, v3) == cudaSuccess && cudaMalloc(&D.Jr, v3) == cudaSuccess &&
+        cudaMalloc(&D.D2, v3) == cudaSuccess && cudaMalloc(&D.D3, v3) == cudaSuccess &&
+        cudaMalloc(&D.rs2, n * 8) == cudaSuccess && cudaMalloc(&D.Tr, n * 8) == cudaSuccess &&
+        cudaMalloc(&D.LR, n * 4) == cudaSuccess && cudaMalloc(&D.LI, n * 4) == cudaSuccess &&
+        cudaMalloc(&D.ell, (size_t)n * cap * 4) == cudaSuccess && cudaMalloc(&D.ell_cnt, n * 4) == cudaSuccess &&
+        cudaMalloc(&s->reg_pos, n * 4) == cudaSuccess && cudaMalloc(&s->reg_idx, n * 4) == cudaSuccess &&
+        cudaMalloc(&s->want, n * 4) == cudaSuccess && cudaMalloc(&s->cnt_true, n * 4) == cudaSuccess &&
+        cudaMalloc(&s->csr, (size_t)n * cap * 4 + 4) == cudaSuccess && cudaMalloc(&s->off, (n + 1) * 8) == cudaSuccess &&
+        cudaMalloc(&s->reg_rs2, n * 8) == cudaSuccess && cudaMalloc(&s->Fo, v3) == cudaSuccess &&
+        cudaMalloc(&s->Jo, v3) == cudaSuccess && cudaMalloc(&s->Po, n * 8) == cudaSuccess &&
+        cudaMalloc(&s->Fa, v3) == cudaSuccess && cudaMalloc(&s->Ja, v3) == cudaSuccess &&
+        cudaMalloc(&s->Pa, n * 8) == cudaSuccess && cudaMalloc(&s->Fn, v3) == cudaSuccess &&
+        cudaMalloc(&s->Jn, v3) == cudaSuccess && cudaMalloc(&s->Pn, n * 8) == cudaSuccess &&
+        cudaMalloc(&s->counter, 4) == cudaSuccess && cudaMallocHost(&s->h_counter, 4) == cudaSuccess &&
+        cudaMalloc(&s->pairs, 8) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+static void ac_bind(nb_ac *s, const nb_ac_params *p, int lmin)
+{
+    AcDev &D = s->D;
+    D.x = s->cs.x; D.v = s->cs.v; D.a = s->cs.a; D.jk = s->cs.jk; D.tl = s->cs.tl; D.m = s->cs.m;
+    D.xp = s->cs.xp; D.vp = s->cs.vp;
+    D.cap = s->cs.cap;
+    D.lmin = lmin;
+    D.lmax = p->level_max;
+    D.eta_irr = p->eta_irr;
+    D.eta_reg = p->eta_reg;
+    D.dt_max = p->dt_max;
+    D.nb_opt = p->nb_opt;
+}
+
+// Level of dt_max = 2^-lmin, or -1 if dt_max is not a power of 1/2 in range.
+static int params_lmin(const nb_ac_params *p)
+{
+    if (!(p->dt_max > 0.0) || p->level_max > kAcTick || !(p->eta_irr > 0.0) || !(p->eta_reg > 0.0) ||
+        !(p->eta_s > 0.0))
+        return -1;
+    int fe = 0;
+    const double fr = std::frexp(p->dt_max, &fe);
+    const int lmin = 1 - fe;
+    return (fr != 0.5 || lmin < 0 || lmin > p->level_max) ? -1 : lmin;
+}
+
+// Snapshot layout: header, then the arrays in this order.
+struct AcSnapshotHeader {
+    char magic[8];
+    int64_t n;
+    int32_t cap, precision;
+    nb_ac_params params;
+    double t_now;
+    double stats[6];
+};
+static constexpr char kSnapMagic[8] = {'N', 'B', 'A', 'C', 'S', 'N', 'P', '1'};
+
+struct SnapField {
+    void *dev;
+    size_t bytes;
+};
+
+static int snap_fields(nb_ac *s, SnapField *f)
+{
+    const int64_t n = s->n;
+    const size_t v3 = (size_t)n * 24, s1 = (size_t)n * 8, i1 = (size_t)n * 4;
+    const AcDev &D = s->D;
+    int k = 0;
+    f[k++] = {D.x, v3};  f[k++] = {D.v, v3};  f[k++] = {D.a, v3};  f[k++] = {D.jk, v3};
+    f[k++] = {D.tl, s1}; f[k++] = {D.m, s1};
+    f[k++] = {D.Fr, v3}; f[k++] = {D.Jr, v3}; f[k++] = {D.D2, v3}; f[k++] = {D.D3, v3};
+    f[k++] = {D.rs2, s1}; f[k++] = {D.Tr, s1};
+    f[k++] = {D.LR, i1}; f[k++] = {D.LI, i1}; f[k++] = {D.ell_cnt, i1};
+    f[k++] = {D.ell, (size_t)n * D.cap * 4};
+    return k;
+}
+
 extern "C" {
 
 nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v,
@@ -303,13 +385,8 @@ nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const
     if (!out) return NB_ERR_ARG;
     *out = nullptr;
     if (!ctx || !m || !x || !v || !rs2 || !p || n < 1) return NB_ERR_ARG;
-    if (!(p->dt_max > 0.0) || p->level_max > kAcTick || !(p->eta_irr > 0.0) || !(p->eta_reg > 0.0) ||
-        !(p->eta_s > 0.0))
-        return NB_ERR_ARG;
-    int fe = 0;
-    const double fr = std::frexp(p->dt_max, &fe);
-    const int lmin = 1 - fe;  // dt_max = 2^-lmin
-    if (fr != 0.5 || lmin < 0 || lmin > p->level_max) return NB_ERR_ARG;
+    const int lmin = params_lmin(p);  // dt_max = 2^-lmin
+    if (lmin < 0) return NB_ERR_ARG;
     nb_ac *s = new (std::nothrow) nb_ac();
     if (!s) return NB_ERR_OOM;
     s->ctx = ctx;
@@ -340,38 +417,11 @@ nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const
         if (st != NB_OK) return bail(afail(s, st, "nb_set_particles: %s", nb_last_error(ctx)));
     }
     if (!ctx_state(ctx, &s->cs)) return bail(NB_ERR_STATE);
+    if (!ac_alloc(s, n, s->cs.cap)) return bail(NB_ERR_OOM);
+    ac_bind(s, p, lmin);
     const int cap = s->cs.cap;
     cudaStream_t st = s->cs.stream;
-    const size_t v3 = (size_t)n * 3 * sizeof(double);
     AcDev &D = s->D;
-    bool ok = cudaMalloc(&D.Fr, v3) == cudaSuccess && cudaMalloc(&D.Jr, v3) == cudaSuccess &&
-              cudaMalloc(&D.D2, v3) == cudaSuccess && cudaMalloc(&D.D3, v3) == cudaSuccess &&
-              cudaMalloc(&D.rs2, n * 8) == cudaSuccess && cudaMalloc(&D.Tr, n * 8) == cudaSuccess &&
-              cudaMalloc(&D.LR, n * 4) == cudaSuccess && cudaMalloc(&D.LI, n * 4) == cudaSuccess &&
-              cudaMalloc(&D.ell, (size_t)n * cap * 4) == cudaSuccess && cudaMalloc(&D.ell_cnt, n * 4) == cudaSuccess &&
-              cudaMalloc(&s->reg_pos, n * 4) == cudaSuccess && cudaMalloc(&s->reg_idx, n * 4) == cudaSuccess &&
-              cudaMalloc(&s->want, n * 4) == cudaSuccess && cudaMalloc(&s->cnt_true, n * 4) == cudaSuccess &&
-              cudaMalloc(&s->csr, (size_t)n * cap * 4 + 4) == cudaSuccess &&
-              cudaMalloc(&s->off, (n + 1) * 8) == cudaSuccess && cudaMalloc(&s->reg_rs2, n * 8) == cudaSuccess &&
-              cudaMalloc(&s->Fo, v3) == cudaSuccess && cudaMalloc(&s->Jo, v3) == cudaSuccess &&
-              cudaMalloc(&s->Po, n * 8) == cudaSuccess && cudaMalloc(&s->Fa, v3) == cudaSuccess &&
-              cudaMalloc(&s->Ja, v3) == cudaSuccess && cudaMalloc(&s->Pa, n * 8) == cudaSuccess &&
-              cudaMalloc(&s->Fn, v3) == cudaSuccess && cudaMalloc(&s->Jn, v3) == cudaSuccess &&
-              cudaMalloc(&s->Pn, n * 8) == cudaSuccess && cudaMalloc(&s->counter, 4) == cudaSuccess &&
-              cudaMallocHost(&s->h_counter, 4) == cudaSuccess && cudaMalloc(&s->pairs, 8) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();
-        return bail(NB_ERR_OOM);
-    }
-    D.x = s->cs.x; D.v = s->cs.v; D.a = s->cs.a; D.jk = s->cs.jk; D.tl = s->cs.tl; D.m = s->cs.m;
-    D.xp = s->cs.xp; D.vp = s->cs.vp;
-    D.cap = cap;
-    D.lmin = lmin;
-    D.lmax = p->level_max;
-    D.eta_irr = p->eta_irr;
-    D.eta_reg = p->eta_reg;
-    D.dt_max = p->dt_max;
-    D.nb_opt = p->nb_opt;
     ACK(cudaMemcpyAsync(D.rs2, rs2, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
         "copy rs2");
     // all forces and lists at t = 0
@@ -487,6 +537,99 @@ nb_status nb_ac_get(nb_ac *s, double *x, double *v, double *t, double *dt, doubl
         if (T) ACK(cudaMemcpyAsync(T, tmp + 2 * n, n * 8, k, st), "copy T");
     }
     ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
+nb_status nb_ac_snapshot_bytes(nb_ac *s, size_t *bytes)
+{
+    if (!s || !bytes) return NB_ERR_ARG;
+    SnapField f[32];
+    const int k = snap_fields(s, f);
+    size_t b = sizeof(AcSnapshotHeader);
+    for (int q = 0; q < k; ++q) b += f[q].bytes;
+    *bytes = b;
+    return NB_OK;
+}
+
+nb_status nb_ac_save(nb_ac *s, void *buf, size_t bytes)
+{
+    if (!s || !buf) return NB_ERR_ARG;
+    size_t need = 0;
+    nb_ac_snapshot_bytes(s, &need);
+    if (bytes < need) return afail(s, NB_ERR_ARG, "snapshot needs %zu bytes", need);
+    AcSnapshotHeader h{};
+    memcpy(h.magic, kSnapMagic, 8);
+    h.n = s->n;
+    h.cap = s->D.cap;
+    h.precision = s->cs.precision;
+    h.params = s->p;
+    nb_status ss = nb_sched_get(s->sched, nullptr, nullptr, &h.t_now, 0);
+    if (ss != NB_OK) return afail(s, ss, "nb_sched_get");
+    memcpy(h.stats, s->stats, sizeof(h.stats));
+    char *out = static_cast<char *>(buf);
+    memcpy(out, &h, sizeof(h));
+    size_t o = sizeof(h);
+    SnapField f[32];
+    const int k = snap_fields(s, f);
+    for (int q = 0; q < k; ++q) {
+        ACK(cudaMemcpyAsync(out + o, f[q].dev, f[q].bytes, cudaMemcpyDeviceToHost, s->cs.stream), "copy state");
+        o += f[q].bytes;
+    }
+    ACK(cudaStreamSynchronize(s->cs.stream), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
+nb_status nb_ac_restore(nb_ac **out, nb_ctx *ctx, const void *buf, size_t bytes)
+{
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    if (!ctx || !buf || bytes < sizeof(AcSnapshotHeader)) return NB_ERR_ARG;
+    AcSnapshotHeader h;
+    memcpy(&h, buf, sizeof(h));
+    const int lmin = params_lmin(&h.params);
+    if (memcmp(h.magic, kSnapMagic, 8) != 0 || h.n < 1 || lmin < 0) return NB_ERR_ARG;
+    nb_ac *s = new (std::nothrow) nb_ac();
+    if (!s) return NB_ERR_OOM;
+    s->ctx = ctx;
+    s->n = h.n;
+    s->p = h.params;
+    memcpy(s->stats, h.stats, sizeof(h.stats));
+    auto bail = [&](nb_status st) {
+        nb_ac_free(s);
+        return st;
+    };
+    const int64_t n = h.n;
+    const char *in = static_cast<const char *>(buf);
+    const size_t v3 = (size_t)n * 24, s1 = (size_t)n * 8, o0 = sizeof(h);
+    // the particle state goes to the context first (it checks n against its capacity)
+    const double *hx = (const double *)(in + o0), *hv = (const double *)(in + o0 + v3),
+                 *ha = (const double *)(in + o0 + 2 * v3), *hj = (const double *)(in + o0 + 3 * v3),
+                 *ht = (const double *)(in + o0 + 4 * v3), *hm = (const double *)(in + o0 + 4 * v3 + s1);
+    nb_status st0 = nb_set_particles(ctx, n, hx, hv, ha, hj, hm, ht, 0);
+    if (st0 != NB_OK) return bail(afail(s, st0, "nb_set_particles: %s", nb_last_error(ctx)));
+    if (!ctx_state(ctx, &s->cs)) return bail(NB_ERR_STATE);
+    if (s->cs.cap != h.cap || s->cs.precision != h.precision)
+        return bail(afail(s, NB_ERR_ARG, "the context's nb_cap / precision differ from the snapshot's"));
+    if (!ac_alloc(s, n, h.cap)) return bail(NB_ERR_OOM);
+    ac_bind(s, &h.params, lmin);
+    SnapField f[32];
+    const int k = snap_fields(s, f);
+    size_t need = sizeof(h);
+    for (int q = 0; q < k; ++q) need += f[q].bytes;
+    if (bytes < need) return bail(afail(s, NB_ERR_ARG, "snapshot truncated"));
+    size_t o = sizeof(h);
+    for (int q = 0; q < k; ++q) {
+        if (cudaMemcpyAsync(f[q].dev, in + o, f[q].bytes, cudaMemcpyHostToDevice, s->cs.stream) != cudaSuccess)
+            return bail(NB_ERR_CUDA);
+        o += f[q].bytes;
+    }
+    // LI follows x, v, a, jk (4 v3), tl, m (2 s1), Fr, Jr, D2, D3 (4 v3), rs2, Tr (2 s1), LR
+    const int32_t *levels = (const int32_t *)(in + sizeof(h) + 8 * v3 + 4 * s1 + (size_t)n * 4);
+    nb_status ss = nb_sched_init(&s->sched, n, levels, lmin, h.params.level_max, s->cs.device, (void *)s->cs.stream, 0);
+    if (ss == NB_OK) ss = nb_sched_set_time(s->sched, h.t_now);
+    if (ss != NB_OK) return bail(afail(s, ss, "scheduler"));
+    if (cudaStreamSynchronize(s->cs.stream) != cudaSuccess) return bail(NB_ERR_CUDA);
+    *out = s;
     return NB_OK;
 }
 

@@ -417,6 +417,27 @@ nb_status nb_sched_counts(const nb_sched *s, int64_t *counts)
     return NB_OK;
 }
 
+nb_status nb_sched_set_time(nb_sched *s, double t)
+{
+    if (!s) return NB_ERR_ARG;
+    if (s->pending) return sfail(s, NB_ERR_STATE, "a block step is open");
+    const double ticks = std::ldexp(t, kTick);
+    if (!(t >= 0.0) || ticks >= std::ldexp(1.0, 62) || ticks != std::floor(ticks))
+        return sfail(s, NB_ERR_ARG, "time %.17g is not a multiple of 2^-%d in range", t, kTick);
+    const int64_t T = (int64_t)ticks;
+    // a block time is a multiple of the smallest step present (its particles step every time)
+    int lmax_present = 0;
+    for (int b = kBins - 1; b >= 0; --b)
+        if (s->count[b]) {
+            lmax_present = b;
+            break;
+        }
+    if ((T & (((int64_t)1 << (kTick - lmax_present)) - 1)) != 0)
+        return sfail(s, NB_ERR_ARG, "time %.17g is not a multiple of the smallest step 2^-%d", t, lmax_present);
+    s->T = T;
+    return NB_OK;
+}
+
 nb_status nb_sched_peek(const nb_sched *s, double *t_next)
 {
     if (!s || !t_next) return NB_ERR_ARG;

@@ -92,3 +92,31 @@ def test_ac_mixed_conserves_energy(gpu_lib):
     assert 35 <= np.median(g["nb_count"]) <= 70
     ac.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ac_checkpoint_resume_is_bitwise(gpu_lib, prec):
+    """Run 120 block steps, checkpoint, run 150 more; resume the checkpoint on a fresh
+    context and run the same 150: every output identical bit for bit."""
+    from paper_1504_03687_gb300 import ACIntegrator
+    cl = W.plummer(3000, 105, masses="kroupa")
+    rs2 = W.neighbour_radius2(cl.x, 40, seed=105)
+    kw = dict(eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125, nb_opt=40)
+    ctx = make(cl.n, prec, 128)
+    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
+    for _ in range(120):
+        ac.step()
+    blob = ac.save()
+    times = [ac.step()[0] for _ in range(150)]
+    a = ac.get()
+    ac.close()
+    ctx.close()
+    ctx2 = make(cl.n + 7, prec, 128)  # any context with room, the same precision and cap
+    ac2 = ACIntegrator.restore(ctx2, blob)
+    times2 = [ac2.step()[0] for _ in range(150)]
+    b = ac2.get()
+    assert times == times2
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    ac2.close()
+    ctx2.close()

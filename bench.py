@@ -203,6 +203,8 @@ def main():
     ap.add_argument("--ni", type=int, default=2048)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint")
+    ap.add_argument("--irregular", action="store_true",
+                    help="with --profile: also run the irregular force over the lists just returned")
     ap.add_argument("--model", default="king", choices=["king", "plummer"],
                     help="with --profile: King W0=6 (+5%% binaries) or Plummer, Kroupa masses")
     ap.add_argument("--variants", default="",
@@ -276,6 +278,47 @@ def main():
     peak, peak_src = fp32_peak_tflops(num_sms)
     achieved = FLOPS_PER_PAIR * pairs_step * args.steps / (force_ms * 1e-3) / 1e12
 
+    # end to end through the public API with host buffers (pinned), copies inside the timing;
+    # measured right after the device-timed steps, before the other sections load the GPU
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_state = [pin(q) for q in (cl.x, cl.v, a0, j0, cl.m, tl)]
+        h_idx = [pin(order[:b]) for b in BLOCKS]
+        h_out = []
+        for b in BLOCKS:
+            from paper_1504_03687_gb300.api import ForceResult
+            h_out.append(ForceResult(acc=pin(np.empty((b, 3))), jerk=pin(np.empty((b, 3))), pot=pin(np.empty(b)),
+                                     nb_off=pin(np.empty(b + 1, np.int64)),
+                                     nb_idx=pin(np.empty(b * NB_PER_ROW, np.int32)),
+                                     nb_count=pin(np.empty(b, np.int32))))
+        h2d = sum(q.nbytes for q in h_state) + sum(q.nbytes for q in h_idx) + 8 * len(BLOCKS)
+
+        def e2e_step():
+            d2h = 0
+            ctx.set_particles(*h_state)
+            for q, b in enumerate(BLOCKS):
+                ctx.predict(0.125)
+                r = host_force(ctx, h_idx[q], rs2, h_out[q])
+                d2h += r
+            return d2h
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            d2h = e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        el_t = torch.tensor([el], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(el_t, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * pairs_step * args.steps / float(el_t.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
     # accuracy at the stated error: sampled rows of the full block vs the FP64 oracle,
     # and the GPU FP64 path on the 2^14 block (the >= 3x comparison)
     extra = {}
@@ -328,46 +371,6 @@ def main():
         if not args.no_scheduler:
             extra["scheduler"] = bench_scheduler(dev, cl)
         ctx64.close()
-
-    # end to end through the public API with host buffers (pinned), copies inside the timing
-    e2e = None
-    if not args.no_e2e:
-        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory().numpy()
-        h_state = [pin(q) for q in (cl.x, cl.v, a0, j0, cl.m, tl)]
-        h_idx = [pin(order[:b]) for b in BLOCKS]
-        h_out = []
-        for b in BLOCKS:
-            from paper_1504_03687_gb300.api import ForceResult
-            h_out.append(ForceResult(acc=pin(np.empty((b, 3))), jerk=pin(np.empty((b, 3))), pot=pin(np.empty(b)),
-                                     nb_off=pin(np.empty(b + 1, np.int64)),
-                                     nb_idx=pin(np.empty(b * NB_PER_ROW, np.int32)),
-                                     nb_count=pin(np.empty(b, np.int32))))
-        h2d = sum(q.nbytes for q in h_state) + sum(q.nbytes for q in h_idx) + 8 * len(BLOCKS)
-
-        def e2e_step():
-            d2h = 0
-            ctx.set_particles(*h_state)
-            for q, b in enumerate(BLOCKS):
-                ctx.predict(0.125)
-                r = host_force(ctx, h_idx[q], rs2, h_out[q])
-                d2h += r
-            return d2h
-
-        e2e_step()
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        t0 = time.perf_counter()
-        d2h = 0
-        for _ in range(args.steps):
-            d2h = e2e_step()
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        el_t = torch.tensor([el], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(el_t, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * pairs_step * args.steps / float(el_t.item()) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank == 0 and not args.no_ensemble:
         extra["ensemble"] = bench_ensemble(dev)
@@ -451,6 +454,8 @@ def run_profile_case(args):
             out = ctx.regular_force(idx, rs2_dev, nb_capacity=args.ni * NB_PER_ROW)
             if args.backward:
                 ctx.regular_force_backward(idx, *g)
+            if args.irregular:
+                ctx.irregular_force(0.125, idx, out.nb_off, out.nb_idx)
             ctx.sync()
         ph = ctx.timings()
         pairs = args.ni * cl.n
@@ -458,6 +463,8 @@ def run_profile_case(args):
                "phase_ms": {k: v[0] for k, v in ph.items()}, "launches": {k: v[1] for k, v in ph.items()},
                "force_Ginteractions_s": pairs / (ph["force"][0] * 1e-3) / 1e9 if ph["force"][0] > 0 else None,
                "nb_total": int(out.nb_off[-1].item())}
+        if args.irregular and ph["irregular"][0] > 0:
+            res["irregular_Gpairs_s"] = res["nb_total"] / (ph["irregular"][0] * 1e-3) / 1e9
         if args.backward and ph["force"][0] > 0:
             fwd = ph["force"][0] + ph["reduce"][0] + ph["neighbours"][0]
             res["backward_over_forward"] = ph["backward"][0] / fwd

@@ -168,6 +168,72 @@ __device__ __forceinline__ void incr_f32(float v, float a, float j, float dt, fl
     E = __fmul_rn(dt, __fmaf_rn(dt, __fmul_rn(j, 0.5f), a));
 }
 
+// List entry e of the row (index checked; -1 past the row's end or for a bad index).
+__device__ __forceinline__ int32_t irr_neighbour(const IrrArgs &A, int64_t e, int64_t e1)
+{
+    if (e >= e1) return -1;
+    const int32_t j = A.nb[e];
+    if (j < 0 || j >= A.n) {
+        atomicOr(A.status, ST_BAD_INDEX);
+        return -1;
+    }
+    return j;
+}
+
+// One pair of the neighbour-only mixed form from j's state record R (5 float4).
+__device__ __forceinline__ void state_pair_mixed(const float4 (&R)[5], float t_hi, float t_lo, const float (&ih)[3],
+                                                 const float (&il)[3], const float (&iv)[3], const float (&iD)[3],
+                                                 const float (&iE)[3], float (&f)[7])
+{
+    const float4 P = R[0], L = R[1], V = R[2], Ac = R[3], J = R[4];
+    const float dt = __fadd_rn(__fsub_rn(t_hi, L.w), __fsub_rn(t_lo, V.w));
+    const float ph[3] = {P.x, P.y, P.z}, pl[3] = {L.x, L.y, L.z}, pv[3] = {V.x, V.y, V.z}, pa[3] = {Ac.x, Ac.y, Ac.z},
+                pj[3] = {J.x, J.y, J.z};
+    float r[3], w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float D, E;
+        incr_f32(pv[c], pa[c], pj[c], dt, D, E);
+        r[c] = __fadd_rn(ds_diff(ph[c], pl[c], ih[c], il[c]), __fsub_rn(D, iD[c]));
+        w[c] = __fadd_rn(__fsub_rn(pv[c], iv[c]), __fsub_rn(E, iE[c]));
+    }
+    const float r2 = r2_f32(r[0], r[1], r[2]);
+    const float rinv = rsqrtf(r2);
+    const float rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+    const float rinv2 = rinv * rinv;
+    const float mr = P.w * rinv;
+    const float mr3 = mr * rinv2;
+    const float beta = rw * (rinv2 * -3.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f[c] += mr3 * r[c];
+        f[3 + c] += mr3 * (w[c] + beta * r[c]);
+    }
+    f[6] -= mr;
+}
+
+// One pair of the predict-all mixed form from j's predicted record R (3 float4).
+__device__ __forceinline__ void rec_pair_mixed(const float4 (&R)[3], const float (&ih)[3], const float (&il)[3],
+                                               const float (&iv)[3], float (&f)[7])
+{
+    const float4 P = R[0], L = R[1], V = R[2];
+    const float r[3] = {ds_diff(P.x, L.x, ih[0], il[0]), ds_diff(P.y, L.y, ih[1], il[1]), ds_diff(P.z, L.z, ih[2], il[2])};
+    const float w[3] = {V.x - iv[0], V.y - iv[1], V.z - iv[2]};
+    const float r2 = r2_f32(r[0], r[1], r[2]);
+    const float rinv = rsqrtf(r2);
+    const float rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+    const float rinv2 = rinv * rinv;
+    const float mr = P.w * rinv;
+    const float mr3 = mr * rinv2;
+    const float beta = rw * (rinv2 * -3.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f[c] += mr3 * r[c];
+        f[3 + c] += mr3 * (w[c] + beta * r[c]);
+    }
+    f[6] -= mr;
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_irregular_mixed(IrrArgs A)
 {
@@ -191,37 +257,12 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_mixed(IrrArgs A)
         }
         float f[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int64_t j = A.nb[e];
-            if (j < 0 || j >= A.n) {
-                atomicOr(A.status, ST_BAD_INDEX);
-                continue;
-            }
-            if (j == i) continue;
-            const float4 P = S[5 * j], L = S[5 * j + 1], V = S[5 * j + 2], Ac = S[5 * j + 3], J = S[5 * j + 4];
-            const float dt = __fadd_rn(__fsub_rn(A.t_hi, L.w), __fsub_rn(A.t_lo, V.w));
-            const float ph[3] = {P.x, P.y, P.z}, pl[3] = {L.x, L.y, L.z}, pv[3] = {V.x, V.y, V.z},
-                        pa[3] = {Ac.x, Ac.y, Ac.z}, pj[3] = {J.x, J.y, J.z};
-            float r[3], w[3];
+            const int32_t j = irr_neighbour(A, e, e1);
+            if (j < 0 || j == i) continue;
+            float4 R[5];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float D, E;
-                incr_f32(pv[c], pa[c], pj[c], dt, D, E);
-                r[c] = __fadd_rn(ds_diff(ph[c], pl[c], ih[c], il[c]), __fsub_rn(D, iD[c]));
-                w[c] = __fadd_rn(__fsub_rn(pv[c], iv[c]), __fsub_rn(E, iE[c]));
-            }
-            const float r2 = r2_f32(r[0], r[1], r[2]);
-            const float rinv = rsqrtf(r2);
-            const float rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
-            const float rinv2 = rinv * rinv;
-            const float mr = P.w * rinv;
-            const float mr3 = mr * rinv2;
-            const float beta = rw * (rinv2 * -3.f);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                f[c] += mr3 * r[c];
-                f[3 + c] += mr3 * (w[c] + beta * r[c]);
-            }
-            f[6] -= mr;
+            for (int q = 0; q < 5; ++q) R[q] = S[5 * (int64_t)j + q];
+            state_pair_mixed(R, A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
         }
         double s[7];
 #pragma unroll
@@ -271,7 +312,7 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_rec_fp64(IrrArgs A)
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_irregular_rec_mixed(IrrArgs A)
+__global__ void __launch_bounds__(BLOCK, 4) k_irregular_rec_mixed(IrrArgs A)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
@@ -288,30 +329,20 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_rec_mixed(IrrArgs A)
             iv[0] = V.x; iv[1] = V.y; iv[2] = V.z;
         }
         float f[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int64_t j = A.nb[e];
-            if (j < 0 || j >= A.n) {
-                atomicOr(A.status, ST_BAD_INDEX);
-                continue;
-            }
-            if (j == i) continue;
-            const float4 P = R[3 * j], L = R[3 * j + 1], V = R[3 * j + 2];
-            const float r[3] = {ds_diff(P.x, L.x, ih[0], il[0]), ds_diff(P.y, L.y, ih[1], il[1]),
-                                ds_diff(P.z, L.z, ih[2], il[2])};
-            const float w[3] = {V.x - iv[0], V.y - iv[1], V.z - iv[2]};
-            const float r2 = r2_f32(r[0], r[1], r[2]);
-            const float rinv = rsqrtf(r2);
-            const float rw = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
-            const float rinv2 = rinv * rinv;
-            const float mr = P.w * rinv;
-            const float mr3 = mr * rinv2;
-            const float beta = rw * (rinv2 * -3.f);
+        // two list entries per lane per round (e and e + 32): both records are requested
+        // before either is used, so each lane keeps two gathers in flight; the per-lane order
+        // of the terms is unchanged
+        for (int64_t e = e0 + lane; e < e1; e += 64) {
+            const int32_t ja = irr_neighbour(A, e, e1), jb = irr_neighbour(A, e + 32, e1);
+            float4 Ra[3], Rb[3];
+            if (ja >= 0)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                f[c] += mr3 * r[c];
-                f[3 + c] += mr3 * (w[c] + beta * r[c]);
-            }
-            f[6] -= mr;
+                for (int q = 0; q < 3; ++q) Ra[q] = R[3 * (int64_t)ja + q];
+            if (jb >= 0)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Rb[q] = R[3 * (int64_t)jb + q];
+            if (ja >= 0 && ja != i) rec_pair_mixed(Ra, ih, il, iv, f);
+            if (jb >= 0 && jb != i) rec_pair_mixed(Rb, ih, il, iv, f);
         }
         double sd[7];
 #pragma unroll

@@ -630,7 +630,58 @@ def bench_ac(dev, n=65536, t_end=1.0 / 64):
                                 "irregular_steps": info["irregular_steps"], "regular_steps": info["regular_steps"],
                                 "energy_rel_error": (sum(oracle.energy(cl.m, ox, ov)) - E0) / abs(E0)}
     res["mixed_speedup_over_reference"] = wall / res["mixed"]["wall_s"]
+    res["king_1m"] = bench_ac_king_1m(dev)
     return res
+
+
+def gpu_energy(dev, m, x, v):
+    """K + W with W = 1/2 sum m pot from the mixed all-pairs potentials on the device."""
+    import torch
+
+    from paper_1504_03687_gb300 import Context
+    n = m.shape[0]
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    ctx = Context(n, precision="mixed", nb_cap=1, device=dev.index or 0)
+    ctx.set_predicted(T(x), T(v), T(m))
+    r = ctx.regular_force(T(np.arange(n, dtype=np.int32)), 0.0, neighbours=False)
+    ctx.sync()
+    W_ = 0.5 * float((T(m) * r.pot).sum().item())
+    ctx.close()
+    return 0.5 * float((m[:, None] * v * v).sum()) + W_
+
+
+def bench_ac_king_1m(dev, t_end=1.0 / 64):
+    """The Ahmad-Cohen integrator on the million-body King W0 = 6 cluster (5 % binaries as
+    centre-of-mass particles), mixed precision, r_s towards 50 neighbours (cap 256), from
+    t = 0 to t_end = dt_max; wall time, particle steps, energy error from the mixed all-pairs
+    potentials before and after.  Context: the paper's 1M runs took about 800 s of wall time
+    per N-body time unit on 16 nodes (32 K20X + 320 CPU cores)."""
+    import torch
+
+    import workloads as W
+    from paper_1504_03687_gb300 import ACIntegrator, Context
+    cl, _ = W.king_1m_binaries()
+    rs2 = W.neighbour_radius2(cl.x, 50, seed=2)
+    E0 = gpu_energy(dev, cl.m, cl.x, cl.v)
+    ctx = Context(cl.n, precision="mixed", nb_cap=256, device=dev.index or 0)
+    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=t_end, nb_opt=50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ac.run(t_end, max_blocks=2000000)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    g = ac.get()
+    ac.close()
+    ctx.close()
+    E1 = gpu_energy(dev, cl.m, g["x"], g["v"])
+    return {"workload": "King W0=6 N=2^20 (5% binary c.m.), Kroupa, r_s towards 50 neighbours (cap 256), "
+                        f"mixed, t = 0 .. {t_end}", "wall_s": wall, "block_steps": st["blocks"],
+            "irregular_steps": st["irregular_steps"], "regular_steps": st["regular_steps"],
+            "particle_steps_per_s": st["irregular_steps"] / wall, "wall_s_per_nbody_time_unit": wall / t_end,
+            "energy_rel_error": (E1 - E0) / abs(E0), "all_synchronised": bool(np.all(g["t"] == t_end)),
+            "context": "paper: about 800 s per N-body time unit for 1M on 16 nodes, 32 K20X + 320 CPU cores "
+                       "(no binaries); this run is short and starts with small steps (eta_s), so the per-unit "
+                       "figure is an upper bound"}
 
 
 def bench_ensemble(dev, steps=5, n_clusters=512):

@@ -309,15 +309,19 @@ def main():
             torch.distributed.barrier()
         t0 = time.perf_counter()
         d2h = 0
+        step_s = []
         for _ in range(args.steps):
+            ts = time.perf_counter()
             d2h = e2e_step()
+            step_s.append(time.perf_counter() - ts)  # host-mode calls return after their copies
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         el_t = torch.tensor([el], dtype=torch.float64, device=dev)
         if world > 1:
             torch.distributed.all_reduce(el_t, op=torch.distributed.ReduceOp.MAX)
         e2e = {"value": world * pairs_step * args.steps / float(el_t.item()) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "step_ms": [round(x * 1e3, 2) for x in step_s]}
 
     # accuracy at the stated error: sampled rows of the full block vs the FP64 oracle,
     # and the GPU FP64 path on the 2^14 block (the >= 3x comparison)
@@ -366,6 +370,7 @@ def main():
         extra["fp64_path"] = {"block": b64, "force_kernel_Ginteractions_s": fp64_rate,
                               "mixed_force_kernel_Ginteractions_s_same_block": mixed_rate,
                               "mixed_over_fp64": mixed_rate / fp64_rate}
+        extra["small_blocks"] = bench_small_blocks(ctx, n, order, rs2_dev, dev)
         if not args.no_irregular:
             extra["irregular"] = bench_irregular(ctx, ctx64, cl, (a0, j0, tl), order, idx_dev, outs, rs2)
         if not args.no_scheduler:
@@ -474,6 +479,46 @@ def run_profile_case(args):
             res["max_rel_acc_diff_vs_first"] = float(((out.acc - ref[0]).norm(dim=1) / ref[0].norm(dim=1)).max())
             res["same_neighbour_offsets"] = bool(torch.equal(out.nb_off, ref[1]))
         print(json.dumps(res))
+
+
+def bench_small_blocks(ctx, n, order, rs2_dev, dev, sizes=(1, 16, 128, 1024), reps=20):
+    """Small active blocks of the same 2^20 cluster: the force call is then a pass over the j-records
+    (48 B per particle, mixed) rather than arithmetic.  L2 flushed before every call; median of
+    `reps` calls of the force kernel (library CUDA events) and of the whole step (predict + force
+    + reduce + neighbours).  Achieved GB/s counts the record bytes once per call."""
+    import torch
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            peak = float(json.load(fh).get("hbm_gbs"))
+    except Exception:
+        pass
+    rec_bytes = ((n + 255) // 256 * 256) * 48
+    res = {"record_bytes": rec_bytes, "hbm_peak_gbs": peak, "l2": "flushed (512 MB write) before every call",
+           "blocks": {}}
+    for b in sizes:
+        idx = torch.as_tensor(order[:b], device=dev)
+        force, step = [], []
+        for it in range(reps + 3):
+            flush.fill_(it & 0xff)
+            torch.cuda.synchronize()
+            ctx.timings()
+            ctx.set_timing(True)
+            ctx.predict(0.125)
+            ctx.regular_force(idx, rs2_dev, nb_capacity=b * NB_PER_ROW)
+            ph = ctx.timings()
+            ctx.set_timing(False)
+            if it >= 3:
+                force.append(ph["force"][0])
+                step.append(sum(v[0] for v in ph.values()))
+        f = float(np.median(force))
+        gbs = rec_bytes / (f * 1e-3) / 1e9
+        res["blocks"][str(b)] = {"force_ms_median": f, "step_ms_median": float(np.median(step)),
+                                 "achieved_GBs": gbs, "frac_of_hbm_peak": gbs / peak if peak else None,
+                                 "plan": ctx.plan(n, b)}
+    ctx.sync()
+    return res
 
 
 def bench_irregular(ctx, ctx64, cl, hermite, order, idx_dev, outs, rs2, reps=3):

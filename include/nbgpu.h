@@ -255,7 +255,7 @@ nb_status nb_set_plan_table(nb_ctx *ctx, int32_t n_entries, const int64_t *ni_ma
                             const int32_t *kernel, const int32_t *variant, const int32_t *splits);
 
 /* The automatic plan for a given device shape, without a context or a GPU (host-only):
- * num_sms SMs, ctas_per_sm[0..8] resident CTAs of the eight mixed tiled variants and the
+ * num_sms SMs, ctas_per_sm[0..10] resident CTAs of the ten mixed tiled variants and the
  * FP64 tiled kernel (NULL = 1 each), and the context's nb_cap. */
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
                       int64_t n_i, int32_t nb_cap, int64_t *out);

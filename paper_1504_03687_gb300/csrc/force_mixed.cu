@@ -682,7 +682,8 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
 
 // ------------------------------------------------------------------------------------------
 // Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM).  The plan's
-// `variant` indexes this list; ids 0-3 are the scalar kernel, 4-7 the packed-FP32x2 one.
+// `variant` indexes this list; ids 0-3 are the scalar kernel, 4-9 the packed-FP32x2 one
+// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows).
 // Last column: 1 = packed kernel (dynamic shared memory, x2_smem_bytes).
 #define NB_MIXED_TILED_VARIANTS(X)                    \
     X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)      \
@@ -692,7 +693,9 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
     X(4, k_force_mixed_tiled_x2, 4, 128, 256, 3, 1)   \
     X(5, k_force_mixed_tiled_x2, 2, 128, 256, 4, 1)   \
     X(6, k_force_mixed_tiled_x2, 4, 128, 128, 4, 1)   \
-    X(7, k_force_mixed_tiled_x2, 2, 256, 256, 2, 1)
+    X(7, k_force_mixed_tiled_x2, 2, 256, 256, 2, 1)   \
+    X(8, k_force_mixed_tiled_x2, 2, 64, 128, 8, 1)    \
+    X(9, k_force_mixed_tiled_x2, 2, 32, 128, 12, 1)
 
 struct TiledVariant {
     int ni, block, tj, smem;

@@ -385,7 +385,7 @@ def test_million_body_sampled_rows(gpu_lib, king1m):
 
 
 # ------------------------------------------------------------------ every tiled kernel variant
-@pytest.mark.parametrize("variant", list(range(8)))
+@pytest.mark.parametrize("variant", list(range(10)))
 def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
     """Every variant of the mixed tiled kernel (scalar and packed FP32x2, forced through the plan
     override) meets the mixed bar against the oracle and gives the same neighbour lists."""

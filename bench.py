@@ -676,6 +676,37 @@ def bench_ac(dev, n=65536, t_end=1.0 / 64):
                                 "energy_rel_error": (sum(oracle.energy(cl.m, ox, ov)) - E0) / abs(E0)}
     res["mixed_speedup_over_reference"] = wall / res["mixed"]["wall_s"]
     res["king_1m"] = bench_ac_king_1m(dev)
+    res["plummer_1k_hermite_t1"] = bench_hermite_drift(dev)
+    return res
+
+
+def bench_hermite_drift(dev):
+    """Energy drift of the block-step Hermite integration of the 1024-body equal-mass Plummer
+    sphere to t = 1 (eta = 0.02, eta_s = 0.01, dt_max = 1/8): the oracle's FP64 run beside the
+    device's FP64 and mixed runs (the AC integrator with r_s covering everything)."""
+    import ctypes
+
+    import oracle
+    import workloads as W
+    from paper_1504_03687_gb300 import ACIntegrator, Context
+    cl, _ = W.plummer_1k_equal()
+    E0 = sum(oracle.energy(cl.m, cl.x, cl.v))
+    xh, vh = cl.x.copy(), cl.v.copy()
+    st = np.zeros(4)
+    oracle._load().orc_hermite_run(cl.n, cl.m.ctypes.data, xh.ctypes.data, vh.ctypes.data, ctypes.c_double(1.0),
+                                   ctypes.c_double(0.02), ctypes.c_double(0.01), ctypes.c_double(0.125),
+                                   ctypes.c_double(0.0), ctypes.c_int64(0), st.ctypes.data)
+    res = {"oracle_fp64": (sum(oracle.energy(cl.m, xh, vh)) - E0) / abs(E0), "block_steps_oracle": int(st[0])}
+    for prec in ("fp64", "mixed"):
+        ctx = Context(cl.n, precision=prec, nb_cap=cl.n, device=dev.index or 0)
+        ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, 1e300, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125,
+                          nb_opt=0)
+        s_ = ac.run(1.0, max_blocks=100000)
+        g = ac.get()
+        res[f"device_{prec}"] = (sum(oracle.energy(cl.m, g["x"], g["v"])) - E0) / abs(E0)
+        res[f"block_steps_{prec}"] = s_["blocks"]
+        ac.close()
+        ctx.close()
     return res
 
 

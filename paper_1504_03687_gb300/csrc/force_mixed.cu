@@ -7,17 +7,23 @@
 // accumulated in FP32 over one j-tile and promoted to FP64 at the end of every tile.
 // Not a dense contraction, so no tensor cores.
 //
-// Two kernels:
-//  * tiled     : CTA = NI*BLOCK active particles (NI per thread, register-blocked) x one
-//                j-range; j-tiles of TJ records are staged in shared memory with cp.async
-//                (double-buffered) and broadcast to all threads.  FP32-issue bound.
-//  * j-streamed: for tiny active blocks.  CTA = IB active particles x one j-chunk; every
-//                warp streams its own contiguous sub-chunk from HBM (coalesced) and the
-//                block reduces the IB x 7 partial sums with warp shuffles.  HBM/latency bound.
-// Both write FP64 partial sums [split][7][n_i] that k_reduce adds in a fixed order, so
-// results are bitwise reproducible for a given launch plan.  Neighbour segments: one per
-// split (tiled, owned by the thread holding the row) or one per warp (j-streamed, ordered
-// within the warp by ballot).
+// Kernels:
+//  * tiled (scalar) : CTA = NI*BLOCK active particles (NI per thread, register-blocked) x
+//                     one j-range; j-tiles of TJ records are staged in shared memory with
+//                     cp.async (double-buffered) and broadcast to all threads.
+//  * tiled (packed) : the same decomposition with two rows in every FP32x2 operation and a
+//                     duplicated j-tile layout (k_force_mixed_tiled_x2; the default for
+//                     blocks of more than a few dozen rows).  FMA-pipe bound.
+//  * j-streamed     : for tiny active blocks.  CTA = IB active particles x one j-chunk;
+//                     every warp streams its own contiguous sub-chunk (coalesced) and the
+//                     block reduces the IB x 7 partial sums with warp shuffles.  HBM /
+//                     latency bound.
+//  * batched        : many independent clusters in one persistent launch (a work queue of
+//                     cost-sorted items), the packed inner loop.
+// The per-call kernels write FP64 partial sums [split][7][n_i] that k_reduce adds in a fixed
+// order, so results are bitwise reproducible for a given launch plan.  Neighbour segments:
+// one per split (tiled, owned by the thread holding the row) or one per warp (j-streamed,
+// ordered within the warp by ballot).
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
 

@@ -1,8 +1,15 @@
-// nb_api.cu — the C ABI declared in include/nbgpu.h: context, validation, device buffers,
-// launch planning and the call sequence of one regular-force step:
-//   nb_predict  : K1 predictor -> j-records
-//   nb_regular_force : zero counters -> K2/K3 force (+ neighbour capture) -> K4 reduce
-//                      -> K5 neighbour CSR
+// nb_api.cu — the context part of the C ABI declared in include/nbgpu.h: the context and
+// its device buffers, validation, launch planning (automatic, override or tuned table), and
+// the call sequences:
+//   nb_predict            : K1 predictor -> j-records
+//   nb_regular_force      : K2/K3 force (+ neighbour capture, optional source range)
+//                           -> K4 reduce -> K5 neighbour CSR
+//   nb_regular_force_backward : K6 adjoint passes
+//   nb_batch_plan / nb_regular_force_batched : the persistent ensemble launch
+//   nb_irregular_force    : state or predicted records -> K10 list sums (+ split)
+// plus per-phase timing, the deferred device status and the fault-injection hook.  The
+// scheduler (sched.cu), the AC integrator (ac.cu) and the allocation-free call (noalloc.cu)
+// have their own files.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>

@@ -392,9 +392,13 @@ def main():
         rate, _ = oracle_rate(pred, rs2, order[:32])
         rows = int(max(32, min(BLOCKS[-1], 12.0 * rate / n)))  # ~12 s of oracle work
         rate, dt = oracle_rate(pred, rs2, order[:rows])
-        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+        cores = oracle.num_threads()
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{rows} active rows (head of the sorted step list) x all {n} j, FP64 direct sum "
                          f"with neighbour lists, {dt:.1f} s"}
+        rate1, dt1 = oracle_rate(pred, rs2, order[:16], threads=1)  # the same oracle on one core
+        oracle.set_num_threads(cores)
+        cpu["single_core"] = {"value": rate1 / 1e9, "sample": f"16 active rows x all {n} j, {dt1:.1f} s"}
 
     if rank == 0:
         line = {

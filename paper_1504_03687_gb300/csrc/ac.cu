@@ -35,6 +35,7 @@ struct AcDev {
     double *Tr;
     int32_t *LR, *LI;
     int32_t *ell, *ell_cnt;
+    int32_t *lr_hist;  // [64] particles per regular level (kept current by the corrector)
     int32_t cap, lmin, lmax;
     double eta_irr, eta_reg, dt_max;
     int32_t nb_opt;
@@ -115,6 +116,7 @@ __global__ void k_ac_init(AcDev D, int64_t n, const double *Fa, const double *Ja
         if (LR > LI) LR = LI;  // the regular step is at least the irregular one
         D.LI[i] = LI;
         D.LR[i] = LR;
+        atomicAdd(&D.lr_hist[LR], 1);
         levels_out[i] = LI;
         const int64_t e0 = off[i], len = off[i + 1] - off[i];
         D.ell_cnt[i] = (int32_t)len;
@@ -151,6 +153,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         const int32_t p = reg_pos[k];
         atomicAdd(pairs, (unsigned long long)D.ell_cnt[i]);
         double a1[3], j1[3];
+        int lr_old = -1;
         if (p < 0) {
             const double tau = t - D.Tr[i];
             for (int c = 0; c < 3; ++c) {
@@ -163,6 +166,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         } else {
             double Fold[3], Jold[3], a2r[3], a3r[3];
             const double H = t - D.Tr[i];
+            lr_old = D.LR[i];
             for (int c = 0; c < 3; ++c) {
                 const int64_t q = 3 * i + c;
                 a1[c] = Fa[3 * p + c];
@@ -211,6 +215,10 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         int L = ac_level_rule(D.LI[i], crit, t_ticks, D.lmin, D.lmax);
         if (p >= 0) {
             if (D.LR[i] > L) D.LR[i] = L;  // regular step at least the new irregular step
+            if (D.LR[i] != lr_old) {
+                atomicSub(&D.lr_hist[lr_old], 1);
+                atomicAdd(&D.lr_hist[D.LR[i]], 1);
+            }
         } else if (L < D.LR[i]) {
             L = D.LR[i];  // irregular step at most the regular step
         }
@@ -231,6 +239,18 @@ __global__ void k_ac_lists(AcDev D, int64_t n_reg, const int32_t *reg_idx, const
         for (int64_t e = lane; e < len; e += 32) D.ell[(int64_t)i * D.cap + e] = csr[e0 + e];
         if (lane == 0) D.ell_cnt[i] = (int32_t)len;
     }
+}
+
+// The regular subset the classifier found must be the one the level histogram predicted.
+__global__ void k_ac_check_count(const unsigned *counter, int64_t expected, unsigned *status)
+{
+    if (*counter != (unsigned)expected) atomicOr(status, ST_DEVICE);
+}
+
+__global__ void k_ac_hist(AcDev D, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&D.lr_hist[D.LR[i]], 1);
 }
 
 __global__ void k_ac_get_steps(const AcDev D, int64_t n, double *dt, double *DT, double *T)
@@ -267,6 +287,9 @@ struct nb_ac {
            *Pa = nullptr, *Fn = nullptr, *Jn = nullptr, *Pn = nullptr;
     unsigned *counter = nullptr, *h_counter = nullptr;
     unsigned long long *pairs = nullptr;
+    int32_t *h_lr = nullptr;      // [64] host copy of the regular-level histogram (pinned)
+    unsigned *h_status = nullptr;  // the context's status word of the last block step (pinned)
+    bool overflow = false;         // some neighbour list was cut at nb_cap
     double stats[6] = {0, 0, 0, 0, 0, 0};
     char err[384] = {0};
 };
@@ -315,7 +338,9 @@ static bool ac_alloc(nb_ac *s, int64_t n, int cap)
         cudaMalloc(&s->Pa, n * 8) == cudaSuccess && cudaMalloc(&s->Fn, v3) == cudaSuccess &&
         cudaMalloc(&s->Jn, v3) == cudaSuccess && cudaMalloc(&s->Pn, n * 8) == cudaSuccess &&
         cudaMalloc(&s->counter, 4) == cudaSuccess && cudaMallocHost(&s->h_counter, 4) == cudaSuccess &&
-        cudaMalloc(&s->pairs, 8) == cudaSuccess;
+        cudaMalloc(&s->pairs, 8) == cudaSuccess && cudaMalloc(&D.lr_hist, 64 * 4) == cudaSuccess &&
+        cudaMallocHost(&s->h_lr, 64 * 4) == cudaSuccess && cudaMallocHost(&s->h_status, 4) == cudaSuccess &&
+        cudaMemset(D.lr_hist, 0, 64 * 4) == cudaSuccess && cudaMemset(s->pairs, 0, 8) == cudaSuccess;
     if (!ok) cudaGetLastError();
     return ok;
 }
@@ -335,6 +360,11 @@ static void ac_bind(nb_ac *s, const nb_ac_params *p, int lmin)
 }
 
 // Level of dt_max = 2^-lmin, or -1 if dt_max is not a power of 1/2 in range.
+// The scheduler must order its work after the integrator's kernels: it runs on the context's
+// stream, which for a context on the legacy default stream is named by its handle (a null
+// stream would give the scheduler a stream of its own).
+static void *sched_stream(cudaStream_t st) { return st ? (void *)st : (void *)cudaStreamLegacy; }
+
 static int params_lmin(const nb_ac_params *p)
 {
     if (!(p->dt_max > 0.0) || p->level_max > kAcTick || !(p->eta_irr > 0.0) || !(p->eta_reg > 0.0) ||
@@ -434,13 +464,20 @@ nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const
     k_ac_init<<<grid_of(n, 256, 152 * 16), 256, 0, st>>>(D, n, s->Fa, s->Ja, s->Fn, s->Jn, s->off, s->csr, p->eta_s,
                                                           s->want);
     ACK(cudaGetLastError(), "init launch");
+    ACK(cudaMemcpyAsync(s->h_lr, D.lr_hist, 64 * 4, cudaMemcpyDeviceToHost, st), "copy histogram");
     ANB(nb_sync(ctx), "initial forces");
-    nb_status ss = nb_sched_init(&s->sched, n, s->want, lmin, p->level_max, s->cs.device, (void *)st, 1);
+    nb_status ss = nb_sched_init(&s->sched, n, s->want, lmin, p->level_max, s->cs.device, sched_stream(st), 1);
     if (ss != NB_OK) return bail(afail(s, ss, "nb_sched_init"));
     *out = s;
     return NB_OK;
 }
 
+// One block step with a single host synchronisation (inside nb_sched_update): the size of the
+// regular subset follows from the histogram of regular levels read back with the previous
+// step (a particle takes a regular step exactly when its regular level is >= L*, the
+// coarsest level whose step divides the block time), so the regular force is launched
+// without waiting; the context's status word and the new histogram come back with the
+// scheduler's own read-back.
 nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_regular)
 {
     if (!s) return NB_ERR_ARG;
@@ -452,15 +489,18 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     const CtxState &cs = s->cs;
     cudaStream_t st = cs.stream;
     const int64_t t_ticks = (int64_t)std::ldexp(t, kAcTick);
+    int tz = 0;
+    while (tz < kAcTick && ((t_ticks >> tz) & 1) == 0) ++tz;
+    const int lstar = kAcTick - tz;
+    int64_t nr = 0;
+    for (int b = lstar; b < 64; ++b) nr += s->h_lr[b];
     const int cap = cs.cap;
     ACK(cudaMemsetAsync(s->counter, 0, 4, st), "memset");
     k_ac_classify<<<grid_of(na, 256, 152 * 16), 256, 0, st>>>(s->D, na, list, t_ticks, s->counter, s->reg_pos,
                                                                s->reg_idx, s->reg_rs2);
+    k_ac_check_count<<<1, 1, 0, st>>>(s->counter, nr, cs.status + SS_FLAGS);
     ACK(cudaGetLastError(), "classify launch");
-    ACK(cudaMemcpyAsync(s->h_counter, s->counter, 4, cudaMemcpyDeviceToHost, st), "copy count");
     ANB(nb_predict(s->ctx, t), "nb_predict");
-    ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-    const int64_t nr = *s->h_counter;
     if (nr > 0)
         ANB(nb_regular_force(s->ctx, nr, s->reg_idx, s->reg_rs2, 0, s->Fa, s->Ja, s->Pa, s->off, s->csr, nr * cap,
                              s->cnt_true, 1),
@@ -470,25 +510,37 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     if (nr > 0)
         launch_irregular(st, cs.precision, cs.num_sms, cs.rec, 1, cs.n, t, nr, s->reg_idx, s->off, s->csr, s->Fn,
                          s->Jn, s->Pn, nullptr, nullptr, nullptr, cs.status);
-    ACK(cudaMemsetAsync(s->pairs, 0, 8, st), "memset");
     k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks, s->reg_pos, s->Fo, s->Jo,
                                                               s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
                                                               s->pairs);
     if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);
     ACK(cudaGetLastError(), "corrector launch");
-    unsigned long long pairs = 0;
-    ACK(cudaMemcpyAsync(&pairs, s->pairs, 8, cudaMemcpyDeviceToHost, st), "copy pairs");
-    ANB(nb_sync(s->ctx), "block step");
-    ss = nb_sched_update(s->sched, s->want, nullptr, 1);
+    ACK(cudaMemcpyAsync(s->h_lr, s->D.lr_hist, 64 * 4, cudaMemcpyDeviceToHost, st), "copy histogram");
+    ACK(cudaMemcpyAsync(s->h_status, cs.status + SS_FLAGS, 4, cudaMemcpyDeviceToHost, st), "copy status");
+    ACK(cudaMemsetAsync(cs.status + SS_FLAGS, 0, 4, st), "clear status");
+    ss = nb_sched_update(s->sched, s->want, nullptr, 1);  // synchronises the stream
     if (ss != NB_OK) return afail(s, ss, "nb_sched_update: %s", nb_sched_last_error(s->sched));
+    const unsigned f = *s->h_status;
+    if (f & (ST_BAD_INDEX | ST_DUP_INDEX | ST_DEVICE | ST_TIMEOUT))
+        return afail(s, NB_ERR_DEVICE, "block step at t = %.17g: device status 0x%x", t, f);
+    if (f & (ST_NB_TRUNCATED | ST_CSR_FULL)) s->overflow = true;
     s->stats[0] += 1;
     s->stats[1] += (double)na;
     s->stats[2] += (double)nr;
-    s->stats[3] += (double)pairs;
     s->stats[4] += (double)nr * (double)(cs.n - 1);
     if (t_block) *t_block = t;
     if (n_active) *n_active = na;
     if (n_regular) *n_regular = nr;
+    return NB_OK;
+}
+
+// Counters of the run so far (the neighbour-pair count lives on the device).
+static nb_status ac_read_stats(nb_ac *s)
+{
+    unsigned long long pairs = 0;
+    ACK(cudaMemcpyAsync(&pairs, s->pairs, 8, cudaMemcpyDeviceToHost, s->cs.stream), "copy pairs");
+    ACK(cudaStreamSynchronize(s->cs.stream), "cudaStreamSynchronize");
+    s->stats[3] = (double)pairs;
     return NB_OK;
 }
 
@@ -510,7 +562,11 @@ nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats)
         if ((ss = nb_ac_step(s, nullptr, nullptr, nullptr)) != NB_OK) return ss;
         ++b;
     }
-    if (stats) memcpy(stats, s->stats, sizeof(s->stats));
+    if (stats) {
+        nb_status ss = ac_read_stats(s);
+        if (ss != NB_OK) return ss;
+        memcpy(stats, s->stats, sizeof(s->stats));
+    }
     return rc;
 }
 
@@ -565,6 +621,7 @@ nb_status nb_ac_save(nb_ac *s, void *buf, size_t bytes)
     h.params = s->p;
     nb_status ss = nb_sched_get(s->sched, nullptr, nullptr, &h.t_now, 0);
     if (ss != NB_OK) return afail(s, ss, "nb_sched_get");
+    if ((ss = ac_read_stats(s)) != NB_OK) return ss;
     memcpy(h.stats, s->stats, sizeof(h.stats));
     char *out = static_cast<char *>(buf);
     memcpy(out, &h, sizeof(h));
@@ -625,9 +682,16 @@ nb_status nb_ac_restore(nb_ac **out, nb_ctx *ctx, const void *buf, size_t bytes)
     }
     // LI follows x, v, a, jk (4 v3), tl, m (2 s1), Fr, Jr, D2, D3 (4 v3), rs2, Tr (2 s1), LR
     const int32_t *levels = (const int32_t *)(in + sizeof(h) + 8 * v3 + 4 * s1 + (size_t)n * 4);
-    nb_status ss = nb_sched_init(&s->sched, n, levels, lmin, h.params.level_max, s->cs.device, (void *)s->cs.stream, 0);
+    nb_status ss =
+        nb_sched_init(&s->sched, n, levels, lmin, h.params.level_max, s->cs.device, sched_stream(s->cs.stream), 0);
     if (ss == NB_OK) ss = nb_sched_set_time(s->sched, h.t_now);
     if (ss != NB_OK) return bail(afail(s, ss, "scheduler"));
+    const unsigned long long pairs = (unsigned long long)h.stats[3];
+    if (cudaMemcpyAsync(s->pairs, &pairs, 8, cudaMemcpyHostToDevice, s->cs.stream) != cudaSuccess)
+        return bail(NB_ERR_CUDA);
+    k_ac_hist<<<grid_of(n, 256, 152 * 16), 256, 0, s->cs.stream>>>(s->D, n);
+    if (cudaMemcpyAsync(s->h_lr, s->D.lr_hist, 64 * 4, cudaMemcpyDeviceToHost, s->cs.stream) != cudaSuccess)
+        return bail(NB_ERR_CUDA);
     if (cudaStreamSynchronize(s->cs.stream) != cudaSuccess) return bail(NB_ERR_CUDA);
     *out = s;
     return NB_OK;
@@ -640,10 +704,12 @@ nb_status nb_ac_free(nb_ac *s)
     if (s->sched) nb_sched_free(s->sched);
     void *p[] = {s->D.Fr, s->D.Jr, s->D.D2, s->D.D3, s->D.rs2, s->D.Tr, s->D.LR, s->D.LI, s->D.ell, s->D.ell_cnt,
                  s->reg_pos, s->reg_idx, s->want, s->cnt_true, s->csr, s->off, s->reg_rs2, s->Fo, s->Jo, s->Po,
-                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs};
+                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist};
     for (void *q : p)
         if (q) cudaFree(q);
     if (s->h_counter) cudaFreeHost(s->h_counter);
+    if (s->h_lr) cudaFreeHost(s->h_lr);
+    if (s->h_status) cudaFreeHost(s->h_status);
     delete s;
     return NB_OK;
 }

@@ -301,63 +301,96 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-template <int NP, bool MASK, int TJ>
+// r^2 of two rows against one j of the duplicated tile, in the rounding order of pair_mixed;
+// the neighbour pass recomputes it with this same function, so its decisions are those the
+// interaction loop saw.
+__device__ __forceinline__ float2 x2_r2(const float4 &a, const float4 &b, const float4 &c, const float4 &d,
+                                        const float2 (&h)[3], const float2 (&l)[3], float2 &dx, float2 &dy,
+                                        float2 &dz)
+{
+    dx = f2add(f2add(make_float2(a.x, a.y), h[0]), f2add(make_float2(c.x, c.y), l[0]));
+    dy = f2add(f2add(make_float2(a.z, a.w), h[1]), f2add(make_float2(c.z, c.w), l[1]));
+    dz = f2add(f2add(make_float2(b.x, b.y), h[2]), f2add(make_float2(d.x, d.y), l[2]));
+    return f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+}
+
+// The interaction loop only sets bit u of a 32-bit mask when j = jb + u lies inside r_s of
+// any of the thread's rows; the rare hits are recorded after each 32-j chunk, in ascending j,
+// so that the loop body has no branch and the compiler can interleave consecutive j.
+template <int NP>
+__device__ __forceinline__ void x2_record_hits(const float4 *__restrict__ sd, int64_t jb, unsigned hm, int64_t jend,
+                                            int L, const float2 (&nh)[NP][3], const float2 (&nl)[NP][3],
+                                            const float2 (&rs2f)[NP], const int32_t (&gi)[NP][2],
+                                            int32_t *slot0, int64_t sstride, int (&cnt)[NP][2])
+{
+    while (hm) {
+        const int u = __ffs(hm) - 1;
+        hm &= hm - 1;
+        const int64_t j = jb + u;
+        const int32_t j32 = (int32_t)j;
+        const float4 a = sd[5 * u], b = sd[5 * u + 1], c = sd[5 * u + 2], d = sd[5 * u + 3];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float2 dx, dy, dz;
+            const float2 r2 = x2_r2(a, b, c, d, nh[q], nl[q], dx, dy, dz);
+            if (r2.x < rs2f[q].x && j32 != gi[q][0] && j < jend) {
+                if (cnt[q][0] < L) slot0[(2 * q) * sstride + cnt[q][0]] = j32;
+                ++cnt[q][0];
+            }
+            if (r2.y < rs2f[q].y && j32 != gi[q][1] && j < jend) {
+                if (cnt[q][1] < L) slot0[(2 * q + 1) * sstride + cnt[q][1]] = j32;
+                ++cnt[q][1];
+            }
+        }
+    }
+}
+
+template <int NP, bool MASK, int TJ, int UJ>
 __device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int64_t jb, int64_t jend, int L,
                                               const float2 (&nh)[NP][3], const float2 (&nl)[NP][3],
                                               const float2 (&nv)[NP][3], const float2 (&rs2f)[NP],
-                                              const int64_t (&gi)[NP][2], int32_t *const (&slot)[NP][2],
+                                              const int32_t (&gi)[NP][2], int32_t *slot0, int64_t sstride,
                                               int (&cnt)[NP][2], float2 (&acc)[NP][7])
 {
+    static_assert(TJ % 32 == 0, "tiles are whole 32-j chunks");
     const float2 m3 = make_float2(-3.f, -3.f);
-#pragma unroll 2
-    for (int jj = 0; jj < TJ; ++jj) {
-        const float4 a = sd[5 * jj], b = sd[5 * jj + 1], c = sd[5 * jj + 2], d = sd[5 * jj + 3], e = sd[5 * jj + 4];
-        const float2 XH = make_float2(a.x, a.y), YH = make_float2(a.z, a.w), ZH = make_float2(b.x, b.y);
-        const float2 M = make_float2(b.z, b.w), XL = make_float2(c.x, c.y), YL = make_float2(c.z, c.w);
-        const float2 ZL = make_float2(d.x, d.y), VX = make_float2(d.z, d.w), VY = make_float2(e.x, e.y);
-        const float2 VZ = make_float2(e.z, e.w);
-        const int64_t j = jb + jj;
-        float2 r2[NP];
-        bool hit = false;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const float2 dx = f2add(f2add(XH, nh[q][0]), f2add(XL, nl[q][0]));
-            const float2 dy = f2add(f2add(YH, nh[q][1]), f2add(YL, nl[q][1]));
-            const float2 dz = f2add(f2add(ZH, nh[q][2]), f2add(ZL, nl[q][2]));
-            r2[q] = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-            float2 rinv = make_float2(rsqrtf(r2[q].x), rsqrtf(r2[q].y));
-            if (MASK) {
-                rinv.x = (j == gi[q][0]) ? 0.f : rinv.x;
-                rinv.y = (j == gi[q][1]) ? 0.f : rinv.y;
-            }
-            const float2 wx = f2add(VX, nv[q][0]), wy = f2add(VY, nv[q][1]), wz = f2add(VZ, nv[q][2]);
-            const float2 rw = f2fma(dz, wz, f2fma(dy, wy, f2mul(dx, wx)));
-            const float2 rinv2 = f2mul(rinv, rinv);
-            const float2 mr = f2mul(M, rinv);
-            const float2 mr3 = f2mul(mr, rinv2);
-            const float2 beta = f2mul(rw, f2mul(rinv2, m3));
-            acc[q][0] = f2fma(mr3, dx, acc[q][0]);
-            acc[q][1] = f2fma(mr3, dy, acc[q][1]);
-            acc[q][2] = f2fma(mr3, dz, acc[q][2]);
-            acc[q][3] = f2fma(mr3, f2fma(beta, dx, wx), acc[q][3]);
-            acc[q][4] = f2fma(mr3, f2fma(beta, dy, wy), acc[q][4]);
-            acc[q][5] = f2fma(mr3, f2fma(beta, dz, wz), acc[q][5]);
-            acc[q][6] = f2add(acc[q][6], mr);
-            hit |= (r2[q].x < rs2f[q].x) | (r2[q].y < rs2f[q].y);
-        }
-        if (hit) {  // rare: record in ascending j, the first L per segment
+    for (int jc = 0; jc < TJ; jc += 32) {
+        const float4 *sc = sd + 5 * jc;
+        unsigned hm = 0;
+#pragma unroll UJ
+        for (int u = 0; u < 32; ++u) {
+            const float4 a = sc[5 * u], b = sc[5 * u + 1], c = sc[5 * u + 2], d = sc[5 * u + 3], e = sc[5 * u + 4];
+            const float2 M = make_float2(b.z, b.w), VX = make_float2(d.z, d.w), VY = make_float2(e.x, e.y);
+            const float2 VZ = make_float2(e.z, e.w);
+            bool hit = false;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                if (r2[q].x < rs2f[q].x && j != gi[q][0] && j < jend) {
-                    if (cnt[q][0] < L) slot[q][0][cnt[q][0]] = (int32_t)j;
-                    ++cnt[q][0];
+                float2 dx, dy, dz;
+                const float2 r2 = x2_r2(a, b, c, d, nh[q], nl[q], dx, dy, dz);
+                float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                if (MASK) {
+                    const int32_t j = (int32_t)(jb + jc + u);
+                    rinv.x = (j == gi[q][0]) ? 0.f : rinv.x;
+                    rinv.y = (j == gi[q][1]) ? 0.f : rinv.y;
                 }
-                if (r2[q].y < rs2f[q].y && j != gi[q][1] && j < jend) {
-                    if (cnt[q][1] < L) slot[q][1][cnt[q][1]] = (int32_t)j;
-                    ++cnt[q][1];
-                }
+                const float2 wx = f2add(VX, nv[q][0]), wy = f2add(VY, nv[q][1]), wz = f2add(VZ, nv[q][2]);
+                const float2 rw = f2fma(dz, wz, f2fma(dy, wy, f2mul(dx, wx)));
+                const float2 rinv2 = f2mul(rinv, rinv);
+                const float2 mr = f2mul(M, rinv);
+                const float2 mr3 = f2mul(mr, rinv2);
+                const float2 beta = f2mul(rw, f2mul(rinv2, m3));
+                acc[q][0] = f2fma(mr3, dx, acc[q][0]);
+                acc[q][1] = f2fma(mr3, dy, acc[q][1]);
+                acc[q][2] = f2fma(mr3, dz, acc[q][2]);
+                acc[q][3] = f2fma(mr3, f2fma(beta, dx, wx), acc[q][3]);
+                acc[q][4] = f2fma(mr3, f2fma(beta, dy, wy), acc[q][4]);
+                acc[q][5] = f2fma(mr3, f2fma(beta, dz, wz), acc[q][5]);
+                acc[q][6] = f2add(acc[q][6], mr);
+                hit |= (r2.x < rs2f[q].x) | (r2.y < rs2f[q].y);
             }
+            hm |= (unsigned)hit << u;
         }
+        if (hm) x2_record_hits<NP>(sc, jb + jc, hm, jend, L, nh, nl, rs2f, gi, slot0, sstride, cnt);
     }
 }
 
@@ -373,6 +406,9 @@ template <int NI, int BLOCK, int TJ, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs A)
 {
     constexpr int NP = NI / 2;
+    // j per unrolled body: four for two rows a thread, two for four rows, one where four rows
+    // must fit in 128 registers (more would spill)
+    constexpr int UJ = NI >= 4 ? (MINB >= 4 ? 1 : 2) : 4;
     extern __shared__ __align__(16) float4 x2_smem[];
     float4 *raw = x2_smem;              // 3*TJ float4
     float4 *dup = x2_smem + 3 * TJ;     // 5*TJ float4
@@ -385,10 +421,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
     const float4 *rec = static_cast<const float4 *>(A.rec);
 
     // rows q*BLOCK + tid (q = 0..NI-1); pair p holds rows 2p and 2p+1
+    // the neighbour segment of row q starts at slot0 + q * sstride (rows past n_i never hit)
     float2 nh[NP][3], nl[NP][3], nv[NP][3], rs2f[NP];
-    int64_t gi[NP][2];
-    int32_t *slot[NP][2];
+    int32_t gi[NP][2];
     int cnt[NP][2];
+    int32_t *const slot0 = A.seg_slots + ((int64_t)s * A.n_i + kbase + tid) * A.L;
+    const int64_t sstride = (int64_t)BLOCK * A.L;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         float h[2][3], l[2][3], v[2][3], r[2];
@@ -403,9 +441,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
                     g = -1;
                 }
             }
-            gi[p][u] = g;
+            gi[p][u] = (int32_t)g;
             cnt[p][u] = 0;
-            slot[p][u] = A.seg_slots + ((int64_t)s * A.n_i + (k < A.n_i ? k : 0)) * A.L;
             if (g >= 0) {
                 const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
                 h[u][0] = -p0.x; h[u][1] = -p0.y; h[u][2] = -p0.z;
@@ -462,9 +499,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 #pragma unroll
             for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
         if (__any_sync(0xffffffffu, mine))
-            tile_mixed_x2<NP, true, TJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            tile_mixed_x2<NP, true, TJ, UJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot0, sstride, cnt, acc);
         else
-            tile_mixed_x2<NP, false, TJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+            tile_mixed_x2<NP, false, TJ, UJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot0, sstride, cnt, acc);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
@@ -501,6 +538,9 @@ template <int NI, int BLOCK, int TJ, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_batched(BatchArgs A)
 {
     constexpr int NP = NI / 2;
+    // j per unrolled body: four for two rows a thread, two for four rows, one where four rows
+    // must fit in 128 registers (more would spill)
+    constexpr int UJ = NI >= 4 ? (MINB >= 4 ? 1 : 2) : 4;
     extern __shared__ __align__(16) float4 x2_smem[];
     float4 *raw = x2_smem;
     float4 *dup = x2_smem + 3 * TJ;
@@ -519,9 +559,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_batched(BatchArgs A
         const float rs2c = A.want_nb ? __double2float_rn(A.rs2[W.cluster]) : -1.f;
 
         float2 nh[NP][3], nl[NP][3], nv[NP][3], rs2f[NP];
-        int64_t gi[NP][2];
-        int32_t *slot[NP][2];
+        int32_t gi[NP][2];
         int cnt[NP][2];
+        int32_t *const slot0 = A.seg_slots + ((int64_t)W.row0 + tid) * A.L;  // row q: + q * sstride
+        const int64_t sstride = (int64_t)BLOCK * A.L;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             float h[2][3], l[2][3], v[2][3], r[2];
@@ -537,9 +578,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_batched(BatchArgs A
                         g = -1;
                     }
                 }
-                gi[p][u] = g;
+                gi[p][u] = (int32_t)g;
                 cnt[p][u] = 0;
-                slot[p][u] = A.seg_slots + (rr < W.rows ? k : 0) * A.L;
                 if (g >= 0) {
                     const float4 p0 = A.rec[3 * g], p1 = A.rec[3 * g + 1], p2 = A.rec[3 * g + 2];
                     h[u][0] = -p0.x; h[u][1] = -p0.y; h[u][2] = -p0.z;
@@ -606,9 +646,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_batched(BatchArgs A
 #pragma unroll
                 for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
             if (__any_sync(0xffffffffu, mine))
-                tile_mixed_x2<NP, true, TJ>(dup, jb, j1, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+                tile_mixed_x2<NP, true, TJ, UJ>(dup, jb, j1, A.L, nh, nl, nv, rs2f, gi, slot0, sstride, cnt, acc);
             else
-                tile_mixed_x2<NP, false, TJ>(dup, jb, j1, A.L, nh, nl, nv, rs2f, gi, slot, cnt, acc);
+                tile_mixed_x2<NP, false, TJ, UJ>(dup, jb, j1, A.L, nh, nl, nv, rs2f, gi, slot0, sstride, cnt, acc);
 #pragma unroll
             for (int p = 0; p < NP; ++p)
 #pragma unroll

@@ -473,6 +473,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
         cp_async_commit();
     };
 
+    // FP32 sums of PT consecutive tiles, then promoted to the FP64 running sums: every two
+    // tiles, except for four rows at 3 CTAs per SM, where the longer FP32 chain was slower
+    constexpr int PT = (NI >= 4 && MINB < 4) ? 1 : 2;
+    float2 acc[NP][7];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
     // one raw buffer: tile t+1 lands in it while tile t is computed from dup
     if (t0 < t1) load_tile(t0);
     for (int64_t t = t0; t < t1; ++t) {
@@ -493,22 +501,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
         bool mine = false;
 #pragma unroll
         for (int p = 0; p < NP; ++p) mine |= (gi[p][0] >= jb && gi[p][0] < jb + TJ) | (gi[p][1] >= jb && gi[p][1] < jb + TJ);
-        float2 acc[NP][7];
-#pragma unroll
-        for (int p = 0; p < NP; ++p)
-#pragma unroll
-            for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
         if (__any_sync(0xffffffffu, mine))
             tile_mixed_x2<NP, true, TJ, UJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot0, sstride, cnt, acc);
         else
             tile_mixed_x2<NP, false, TJ, UJ>(dup, jb, A.j_hi, A.L, nh, nl, nv, rs2f, gi, slot0, sstride, cnt, acc);
+        if ((t - t0) % PT == PT - 1 || t + 1 == t1) {
 #pragma unroll
-        for (int p = 0; p < NP; ++p)
+            for (int p = 0; p < NP; ++p)
 #pragma unroll
-            for (int c = 0; c < 7; ++c) {
-                dacc[(c * NI + 2 * p) * BLOCK + tid] += (double)acc[p][c].x;
-                dacc[(c * NI + 2 * p + 1) * BLOCK + tid] += (double)acc[p][c].y;
-            }
+                for (int c = 0; c < 7; ++c) {
+                    dacc[(c * NI + 2 * p) * BLOCK + tid] += (double)acc[p][c].x;
+                    dacc[(c * NI + 2 * p + 1) * BLOCK + tid] += (double)acc[p][c].y;
+                    acc[p][c] = make_float2(0.f, 0.f);
+                }
+        }
     }
 #pragma unroll
     for (int q = 0; q < NI; ++q) {

@@ -112,6 +112,70 @@ __device__ __forceinline__ void irr_store(const IrrArgs &A, int64_t k, int lane,
     }
 }
 
+// (h, l) += (h2, l2) in double-float: TwoSum of the high parts (exact error term), the low
+// parts added to that error, renormalised by FastTwoSum. The error of the pair is about
+// 2^-44 of the sum, far below the FP32 lane sums it adds up.
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2)
+{
+    const float s = __fadd_rn(h, h2);
+    const float bp = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
+    const float t = __fadd_rn(e, __fadd_rn(l, l2));
+    h = __fadd_rn(s, t);
+    l = __fsub_rn(t, __fsub_rn(h, s));
+}
+
+// The seven FP32 lane sums f[0..6] of a row summed over the warp, transposed: at the xor-16,
+// -8 and -4 steps every lane keeps half of its components and sends the other half, so lane L
+// ends with component c = L >> 2 (bits 4, 3, 2 of L pick the halves) summed over eight lanes;
+// the xor-2 and xor-1 steps complete the 32-lane sum. Nine double-float adds and 14 shuffles
+// per row instead of 35 FP64 adds: GB300's FP64 pipe is 1/64 of its FP32 rate. Lane 4c
+// (c < 7) writes component c.
+__device__ __forceinline__ void warp_sum7_df(const float (&f)[7], int lane, float &h, float &l)
+{
+    const unsigned full = 0xffffffffu;
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    float v4[4], h2[2], l2[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float lo_c = f[k], hi_c = k + 4 < 7 ? f[k + 4] : 0.f;
+        const float send = b16 ? lo_c : hi_c;
+        v4[k] = b16 ? hi_c : lo_c;
+        float z = 0.f;
+        df_add(v4[k], z, __shfl_xor_sync(full, send, 16), 0.f);
+        if (k < 2) { h2[k] = v4[k]; l2[k] = z; }
+        else {  // pair component k with k - 2 for the xor-8 step
+            const float sh = b8 ? h2[k - 2] : v4[k], sl = b8 ? l2[k - 2] : z;
+            const float kh = b8 ? v4[k] : h2[k - 2], kl = b8 ? z : l2[k - 2];
+            h2[k - 2] = kh;
+            l2[k - 2] = kl;
+            df_add(h2[k - 2], l2[k - 2], __shfl_xor_sync(full, sh, 8), __shfl_xor_sync(full, sl, 8));
+        }
+    }
+    {
+        const float sh = b4 ? h2[0] : h2[1], sl = b4 ? l2[0] : l2[1];
+        h = b4 ? h2[1] : h2[0];
+        l = b4 ? l2[1] : l2[0];
+        df_add(h, l, __shfl_xor_sync(full, sh, 4), __shfl_xor_sync(full, sl, 4));
+    }
+    df_add(h, l, __shfl_xor_sync(full, h, 2), __shfl_xor_sync(full, l, 2));
+    df_add(h, l, __shfl_xor_sync(full, h, 1), __shfl_xor_sync(full, l, 1));
+}
+
+// Store of a row reduced by warp_sum7_df: lane 4c writes component c in FP64.
+__device__ __forceinline__ void irr_store_df(const IrrArgs &A, int64_t k, int lane, float h, float l, bool ok)
+{
+    if ((lane & 3) != 0 || lane >= 28) return;
+    const int c = lane >> 2;
+    const double v = ok ? __dadd_rn((double)h, (double)l) : 0.0;
+    double *out = c < 3 ? A.acc + 3 * k + c : c < 6 ? A.jerk + 3 * k + (c - 3) : A.pot + k;
+    *out = v;
+    if (A.acc_reg) {
+        double *reg = c < 3 ? A.acc_reg + 3 * k + c : c < 6 ? A.jerk_reg + 3 * k + (c - 3) : A.pot_reg + k;
+        *reg = __dsub_rn(*reg, v);
+    }
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_irregular_fp64(IrrArgs A)
 {
@@ -264,10 +328,9 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_mixed(IrrArgs A)
             for (int q = 0; q < 5; ++q) R[q] = S[5 * (int64_t)j + q];
             state_pair_mixed(R, A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
         }
-        double s[7];
-#pragma unroll
-        for (int c = 0; c < 7; ++c) s[c] = warp_sum((double)f[c]);
-        irr_store(A, k, lane, s, ok);
+        float h, l;
+        warp_sum7_df(f, lane, h, l);
+        irr_store_df(A, k, lane, h, l, ok);
     }
 }
 
@@ -344,10 +407,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_irregular_rec_mixed(IrrArgs A)
             if (ja >= 0 && ja != i) rec_pair_mixed(Ra, ih, il, iv, f);
             if (jb >= 0 && jb != i) rec_pair_mixed(Rb, ih, il, iv, f);
         }
-        double sd[7];
-#pragma unroll
-        for (int c = 0; c < 7; ++c) sd[c] = warp_sum((double)f[c]);
-        irr_store(A, k, lane, sd, ok);
+        float h, l;
+        warp_sum7_df(f, lane, h, l);
+        irr_store_df(A, k, lane, h, l, ok);
     }
 }
 

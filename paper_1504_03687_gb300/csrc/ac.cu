@@ -3,11 +3,16 @@
 // launches on the context stream:
 //   nb_sched_next (host)          -> block time t, active particles = list prefix
 //   k_ac_classify                 -> which active particles also take a regular step
-//   nb_predict(t)                 -> all particles predicted, j-records built
-//   nb_regular_force (regular)    -> all-j sums and the new lists of the regular subset
-//   irregular force, old lists    -> list sums of every active particle (predicted records)
-//   irregular force, new lists    -> list sums of the regular subset over its new lists
-//   k_ac_correct                  -> corrector, step criteria, regular bookkeeping, r_s
+//   with a regular subset:
+//     nb_predict(t)               -> all particles predicted, j-records built
+//     nb_regular_force (regular)  -> all-j sums and the new lists of the regular subset
+//     irregular force, old lists  -> list sums of every active particle (predicted records)
+//     irregular force, new lists  -> list sums of the regular subset over its new lists
+//   without one (most block steps):
+//     irregular force, old lists  -> list sums, i and its neighbours predicted on load from
+//                                    the state records (Sec. 3.3.3): no O(N) work
+//   k_ac_correct                  -> corrector, step criteria, regular bookkeeping, r_s; the
+//                                    state records of the corrected particles
 //   k_ac_lists                    -> the new lists replace the old ones
 //   nb_sched_update               -> the requested levels re-sort the active prefix
 // The corrector's FP64 arithmetic is written operation by operation in the order of the
@@ -29,7 +34,9 @@ constexpr int kAcTick = 48;  // the scheduler's time unit 2^-48
 
 struct AcDev {
     // context state
-    double *x, *v, *a, *jk, *tl, *m, *xp, *vp;
+    double *x, *v, *a, *jk, *tl, *m;
+    dvec4 *s64;   // state records of the predict-on-load irregular force (FP64 context) ...
+    float4 *s32;  // ... or mixed context; the other is null
     // integrator state
     double *Fr, *Jr, *D2, *D3, *rs2;
     double *Tr;
@@ -117,6 +124,7 @@ __global__ void k_ac_init(AcDev D, int64_t n, const double *Fa, const double *Ja
         D.LI[i] = LI;
         D.LR[i] = LR;
         atomicAdd(&D.lr_hist[LR], 1);
+        pack_state_one(i, D.x + 3 * i, D.v + 3 * i, Fa + 3 * i, Ja + 3 * i, 0.0, D.m[i], D.s64, D.s32);
         levels_out[i] = LI;
         const int64_t e0 = off[i], len = off[i + 1] - off[i];
         D.ell_cnt[i] = (int32_t)len;
@@ -196,16 +204,19 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
                 D.rs2[i] *= f;
             }
         }
-        // Hermite corrector on the total force
+        // Hermite corrector on the total force; the predicted state is recomputed here with
+        // the predictor's own function (bit-identical to the all-particle predictor)
         const double h = t - D.tl[i];
         double a2[3], a3[3], a2e[3];
         for (int c = 0; c < 3; ++c) {
             const int64_t q = 3 * i + c;
+            double xp, vp;
+            hermite_taylor(D.x[q], D.v[q], D.a[q], D.jk[q], h, xp, vp);
             const double da = D.a[q] - a1[c];
             a2[c] = (-6.0 * da - h * (4.0 * D.jk[q] + 2.0 * j1[c])) / (h * h);
             a3[c] = (12.0 * da + 6.0 * h * (D.jk[q] + j1[c])) / (h * h * h);
-            D.x[q] = D.xp[q] + h * h * h * h / 24.0 * a2[c] + h * h * h * h * h / 120.0 * a3[c];
-            D.v[q] = D.vp[q] + h * h * h / 6.0 * a2[c] + h * h * h * h / 24.0 * a3[c];
+            D.x[q] = xp + h * h * h * h / 24.0 * a2[c] + h * h * h * h * h / 120.0 * a3[c];
+            D.v[q] = vp + h * h * h / 6.0 * a2[c] + h * h * h * h / 24.0 * a3[c];
             D.a[q] = a1[c];
             D.jk[q] = j1[c];
             a2e[c] = a2[c] + h * a3[c];
@@ -224,6 +235,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         }
         D.LI[i] = L;
         want[k] = L;
+        pack_state_one(i, D.x + 3 * i, D.v + 3 * i, D.a + 3 * i, D.jk + 3 * i, t, D.m[i], D.s64, D.s32);
     }
 }
 
@@ -286,6 +298,7 @@ struct nb_ac {
     double *reg_rs2 = nullptr, *Fo = nullptr, *Jo = nullptr, *Po = nullptr, *Fa = nullptr, *Ja = nullptr,
            *Pa = nullptr, *Fn = nullptr, *Jn = nullptr, *Pn = nullptr;
     unsigned *counter = nullptr, *h_counter = nullptr;
+    void *srec = nullptr;  // state records (pack_state_one layout of the context's precision)
     unsigned long long *pairs = nullptr;
     int32_t *h_lr = nullptr;      // [64] host copy of the regular-level histogram (pinned)
     unsigned *h_status = nullptr;  // the context's status word of the last block step (pinned)
@@ -340,7 +353,8 @@ static bool ac_alloc(nb_ac *s, int64_t n, int cap)
         cudaMalloc(&s->counter, 4) == cudaSuccess && cudaMallocHost(&s->h_counter, 4) == cudaSuccess &&
         cudaMalloc(&s->pairs, 8) == cudaSuccess && cudaMalloc(&D.lr_hist, 64 * 4) == cudaSuccess &&
         cudaMallocHost(&s->h_lr, 64 * 4) == cudaSuccess && cudaMallocHost(&s->h_status, 4) == cudaSuccess &&
-        cudaMemset(D.lr_hist, 0, 64 * 4) == cudaSuccess && cudaMemset(s->pairs, 0, 8) == cudaSuccess;
+        cudaMemset(D.lr_hist, 0, 64 * 4) == cudaSuccess && cudaMemset(s->pairs, 0, 8) == cudaSuccess &&
+        cudaMalloc(&s->srec, state_record_bytes(s->cs.precision, n)) == cudaSuccess;
     if (!ok) cudaGetLastError();
     return ok;
 }
@@ -349,7 +363,8 @@ static void ac_bind(nb_ac *s, const nb_ac_params *p, int lmin)
 {
     AcDev &D = s->D;
     D.x = s->cs.x; D.v = s->cs.v; D.a = s->cs.a; D.jk = s->cs.jk; D.tl = s->cs.tl; D.m = s->cs.m;
-    D.xp = s->cs.xp; D.vp = s->cs.vp;
+    D.s64 = s->cs.precision == NB_FP64 ? static_cast<dvec4 *>(s->srec) : nullptr;
+    D.s32 = s->cs.precision == NB_FP64 ? nullptr : static_cast<float4 *>(s->srec);
     D.cap = s->cs.cap;
     D.lmin = lmin;
     D.lmax = p->level_max;
@@ -500,16 +515,19 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
                                                                s->reg_idx, s->reg_rs2);
     k_ac_check_count<<<1, 1, 0, st>>>(s->counter, nr, cs.status + SS_FLAGS);
     ACK(cudaGetLastError(), "classify launch");
-    ANB(nb_predict(s->ctx, t), "nb_predict");
-    if (nr > 0)
+    if (nr > 0) {
+        ANB(nb_predict(s->ctx, t), "nb_predict");
         ANB(nb_regular_force(s->ctx, nr, s->reg_idx, s->reg_rs2, 0, s->Fa, s->Ja, s->Pa, s->off, s->csr, nr * cap,
                              s->cnt_true, 1),
             "nb_regular_force");
-    launch_irregular(st, cs.precision, cs.num_sms, cs.rec, 1, cs.n, t, na, list, nullptr, s->D.ell, s->Fo, s->Jo,
-                     s->Po, nullptr, nullptr, nullptr, cs.status, s->D.ell_cnt, cap);
-    if (nr > 0)
+        launch_irregular(st, cs.precision, cs.num_sms, cs.rec, 1, cs.n, t, na, list, nullptr, s->D.ell, s->Fo, s->Jo,
+                         s->Po, nullptr, nullptr, nullptr, cs.status, s->D.ell_cnt, cap);
         launch_irregular(st, cs.precision, cs.num_sms, cs.rec, 1, cs.n, t, nr, s->reg_idx, s->off, s->csr, s->Fn,
                          s->Jn, s->Pn, nullptr, nullptr, nullptr, cs.status);
+    } else {  // no all-particle work: the active particles and their neighbours predicted on load
+        launch_irregular(st, cs.precision, cs.num_sms, s->srec, 0, cs.n, t, na, list, nullptr, s->D.ell, s->Fo,
+                         s->Jo, s->Po, nullptr, nullptr, nullptr, cs.status, s->D.ell_cnt, cap);
+    }
     k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks, s->reg_pos, s->Fo, s->Jo,
                                                               s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
                                                               s->pairs);
@@ -680,6 +698,7 @@ nb_status nb_ac_restore(nb_ac **out, nb_ctx *ctx, const void *buf, size_t bytes)
             return bail(NB_ERR_CUDA);
         o += f[q].bytes;
     }
+    launch_pack_state(s->cs.stream, s->cs.precision, n, s->D.x, s->D.v, s->D.a, s->D.jk, s->D.tl, s->D.m, s->srec);
     // LI follows x, v, a, jk (4 v3), tl, m (2 s1), Fr, Jr, D2, D3 (4 v3), rs2, Tr (2 s1), LR
     const int32_t *levels = (const int32_t *)(in + sizeof(h) + 8 * v3 + 4 * s1 + (size_t)n * 4);
     nb_status ss =
@@ -704,7 +723,7 @@ nb_status nb_ac_free(nb_ac *s)
     if (s->sched) nb_sched_free(s->sched);
     void *p[] = {s->D.Fr, s->D.Jr, s->D.D2, s->D.D3, s->D.rs2, s->D.Tr, s->D.LR, s->D.LI, s->D.ell, s->D.ell_cnt,
                  s->reg_pos, s->reg_idx, s->want, s->cnt_true, s->csr, s->off, s->reg_rs2, s->Fo, s->Jo, s->Po,
-                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist};
+                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist, s->srec};
     for (void *q : p)
         if (q) cudaFree(q);
     if (s->h_counter) cudaFreeHost(s->h_counter);

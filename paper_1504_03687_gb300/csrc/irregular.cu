@@ -19,44 +19,20 @@
 //    FP32; likewise w = (v_j - v_i) + (E_j - E_i), E = dt (a + dt jerk/2).  dt = t - t_last
 //    is formed in double-single from hi/lo halves of t and t_last, so that small steps at
 //    late times keep their digits.  Pair arithmetic in FP32, lane sums in FP32 (at most a
-//    few dozen terms), the warp reduction in FP64.
+//    few dozen terms), the warp reduction in double-float with one FP64 add per component.
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
 
 namespace nbgpu {
 
-// State records.
-//   FP64 : 4 dvec4  {x, y, z, t_last} {vx, vy, vz, m} {ax, ay, az, 0} {jx, jy, jz, 0}
-//   mixed: 5 float4 {xh, yh, zh, m} {xl, yl, zl, t_hi} {vx, vy, vz, t_lo} {ax, ay, az, 0}
-//                   {jx, jy, jz, 0}
+// State records: the layout is that of pack_state_one (nb_common.cuh).
 __global__ void k_pack_state(int64_t n, const double *__restrict__ x, const double *__restrict__ v,
                              const double *__restrict__ a, const double *__restrict__ jk,
                              const double *__restrict__ tl, const double *__restrict__ m, dvec4 *__restrict__ s64,
                              float4 *__restrict__ s32)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double *X = x + 3 * i, *V = v + 3 * i, *A = a + 3 * i, *J = jk + 3 * i;
-        if (s64) {
-            s64[4 * i] = make_dvec4(X[0], X[1], X[2], tl[i]);
-            s64[4 * i + 1] = make_dvec4(V[0], V[1], V[2], m[i]);
-            s64[4 * i + 2] = make_dvec4(A[0], A[1], A[2], 0.0);
-            s64[4 * i + 3] = make_dvec4(J[0], J[1], J[2], 0.0);
-        } else {
-            float h[3], l[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                h[c] = __double2float_rn(X[c]);
-                l[c] = __double2float_rn(X[c] - (double)h[c]);
-            }
-            const float th = __double2float_rn(tl[i]);
-            const float tlo = __double2float_rn(tl[i] - (double)th);
-            s32[5 * i] = make_float4(h[0], h[1], h[2], __double2float_rn(m[i]));
-            s32[5 * i + 1] = make_float4(l[0], l[1], l[2], th);
-            s32[5 * i + 2] = make_float4(__double2float_rn(V[0]), __double2float_rn(V[1]), __double2float_rn(V[2]), tlo);
-            s32[5 * i + 3] = make_float4(__double2float_rn(A[0]), __double2float_rn(A[1]), __double2float_rn(A[2]), 0.f);
-            s32[5 * i + 4] = make_float4(__double2float_rn(J[0]), __double2float_rn(J[1]), __double2float_rn(J[2]), 0.f);
-        }
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pack_state_one(i, x + 3 * i, v + 3 * i, a + 3 * i, jk + 3 * i, tl[i], m[i], s64, s32);
 }
 
 struct IrrArgs {

@@ -46,9 +46,6 @@ size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms,
 int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx, int64_t n_i,
                    const double *g_acc, const double *g_jerk, const double *g_pot, double *g_x, double *g_v,
                    double *g_m, void *scratch, unsigned *status, int num_sms);
-size_t state_record_bytes(int precision, int64_t n);
-void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
-                       const double *jk, const double *tl, const double *m, void *srec);
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this

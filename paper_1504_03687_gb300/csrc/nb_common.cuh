@@ -76,6 +76,37 @@ __device__ __forceinline__ void hermite_taylor(double x, double v, double a, dou
     vp = __fma_rn(dt, __fma_rn(h, j, a), v);
 }
 
+// ---- state records of the predict-on-load irregular force ---------------------------------
+//   FP64 : 4 dvec4  {x, y, z, t_last} {vx, vy, vz, m} {ax, ay, az, 0} {jx, jy, jz, 0}
+//   mixed: 5 float4 {xh, yh, zh, m} {xl, yl, zl, t_hi} {vx, vy, vz, t_lo} {ax, ay, az, 0}
+//                   {jx, jy, jz, 0}
+// (positions and t_last as hi/lo pairs of floats). Written for all particles by the packing
+// kernel, and for the particles it corrects by the integrator's corrector.
+__device__ __forceinline__ void pack_state_one(int64_t i, const double *X, const double *V, const double *A,
+                                               const double *J, double t_last, double m, dvec4 *s64, float4 *s32)
+{
+    if (s64) {
+        s64[4 * i] = make_dvec4(X[0], X[1], X[2], t_last);
+        s64[4 * i + 1] = make_dvec4(V[0], V[1], V[2], m);
+        s64[4 * i + 2] = make_dvec4(A[0], A[1], A[2], 0.0);
+        s64[4 * i + 3] = make_dvec4(J[0], J[1], J[2], 0.0);
+    } else {
+        float h[3], l[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            h[c] = __double2float_rn(X[c]);
+            l[c] = __double2float_rn(__dsub_rn(X[c], (double)h[c]));
+        }
+        const float th = __double2float_rn(t_last);
+        const float tlo = __double2float_rn(__dsub_rn(t_last, (double)th));
+        s32[5 * i] = make_float4(h[0], h[1], h[2], __double2float_rn(m));
+        s32[5 * i + 1] = make_float4(l[0], l[1], l[2], th);
+        s32[5 * i + 2] = make_float4(__double2float_rn(V[0]), __double2float_rn(V[1]), __double2float_rn(V[2]), tlo);
+        s32[5 * i + 3] = make_float4(__double2float_rn(A[0]), __double2float_rn(A[1]), __double2float_rn(A[2]), 0.f);
+        s32[5 * i + 4] = make_float4(__double2float_rn(J[0]), __double2float_rn(J[1]), __double2float_rn(J[2]), 0.f);
+    }
+}
+
 // ---- one FP64 pair --------------------------------------------------------------------------
 // p0 = {x_j, m_j}, p1 = {v_j, -} (predicted), xi, vi the predicted active particle:
 // acc[0..2] += m r/|r|^3 ; acc[3..5] += m (w - 3 (r.w) r/|r|^2)/|r|^3 ; acc[6] -= m/|r|

@@ -117,5 +117,9 @@ void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *s
                       double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
                       double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status,
                       const int32_t *ell_cnt = nullptr, int64_t ell_stride = 0);
+// State records of the predict-on-load form (pack_state_one layout) for particles 0..n-1.
+size_t state_record_bytes(int precision, int64_t n);
+void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,
+                       const double *jk, const double *tl, const double *m, void *srec);
 
 }  // namespace nbgpu

@@ -734,23 +734,33 @@ __global__ void k_adj_combine_i(const double *__restrict__ partA, int SA, int64_
 // ---------------------------------------------------------------- planning + launch
 constexpr int kAdjNI = 4, kAdjNJ = 4, kAdjBlock = 128, kAdjTJ = 128, kAdjTI = 64;
 
-static int splits_for(int64_t ctas_x, int64_t tiles, int64_t P)
-{
-    // enough CTAs for ~4 waves, each split keeping >= 2 streamed tiles
-    int64_t S = (4 * P + ctas_x - 1) / (ctas_x > 0 ? ctas_x : 1);
-    const int64_t smax = tiles / 2 > 1 ? tiles / 2 : 1;
-    if (S > smax) S = smax;
-    if (S < 1) S = 1;
-    return (int)S;
-}
-
 size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms, int64_t *rows_pad_out, int *SA,
                              int *SB);
 
 // The fused single pass does N x N pair work with ~96 FP32 operations, the two passes
 // 2 x N_i x N with ~56 and ~60: the fused pass wins for dense blocks.
-constexpr int kFusedBlock = 128, kFusedTJ = 64;
+constexpr int kFusedBlock = 128, kFusedTJ = 128;
 static bool use_fused(int precision, int64_t n, int64_t n_i) { return precision == 1 && 4 * n_i >= 3 * n; }
+
+// Splits of the streamed dimension for ctas_x CTAs along the other one, P resident CTAs:
+// the count with the least time in whole waves of the GPU, ceil(ctas_x S / P) / S, each
+// split charged 0.05 % for its partial sums and their combine, and each keeping >= 2
+// streamed tiles.
+static int splits_for(int64_t ctas_x, int64_t tiles, int64_t P)
+{
+    const int64_t smax = tiles / 2 > 1 ? tiles / 2 : 1;
+    if (ctas_x < 1) ctas_x = 1;
+    int64_t S = 1;
+    double best = 1e300;
+    for (int64_t q = 1; q <= smax && q <= 64; ++q) {
+        const double waves = (double)((ctas_x * q + P - 1) / P) / (double)q * (1.0 + 0.0005 * (double)q);
+        if (waves < best * (1.0 - 1e-9)) {
+            best = waves;
+            S = q;
+        }
+    }
+    return (int)S;
+}
 
 struct FusedGeom {
     int64_t n_pad, n_tiles, ctas;
@@ -763,12 +773,7 @@ static FusedGeom fused_geom(int64_t n, int num_sms)
     f.n_pad = ((n + 255) / 256) * 256;
     f.n_tiles = f.n_pad / kFusedTJ;
     f.ctas = (n + 2 * kFusedBlock - 1) / (2 * kFusedBlock);
-    int64_t P = (int64_t)(num_sms > 0 ? num_sms : 152) * 3;
-    int64_t S = (4 * P + f.ctas - 1) / (f.ctas > 0 ? f.ctas : 1);
-    const int64_t smax = f.n_tiles / 2 > 1 ? f.n_tiles / 2 : 1;
-    if (S > smax) S = smax;
-    if (S < 1) S = 1;
-    f.S = (int)S;
+    f.S = splits_for(f.ctas, f.n_tiles, (int64_t)(num_sms > 0 ? num_sms : 152) * 3);  // 3 CTAs per SM
     return f;
 }
 

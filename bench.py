@@ -124,7 +124,8 @@ class ClockSampler:
         reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
         pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+                "reasons": reasons, "samples": len(rows), "sm_mhz_min": min(sm) if sm else None,
+                "power_w_max": max(pw) if pw else None}
 
 
 def fp32_peak_tflops(num_sms):
@@ -307,6 +308,8 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        e2e_clocks = ClockSampler(local)
+        e2e_clocks.start()
         t0 = time.perf_counter()
         d2h = 0
         step_s = []
@@ -316,12 +319,13 @@ def main():
             step_s.append(time.perf_counter() - ts)  # host-mode calls return after their copies
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        e2e_clk = e2e_clocks.stop()
         el_t = torch.tensor([el], dtype=torch.float64, device=dev)
         if world > 1:
             torch.distributed.all_reduce(el_t, op=torch.distributed.ReduceOp.MAX)
         e2e = {"value": world * pairs_step * args.steps / float(el_t.item()) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "step_ms": [round(x * 1e3, 2) for x in step_s]}
+               "step_ms": [round(x * 1e3, 2) for x in step_s], "clocks": e2e_clk}
 
     # accuracy at the stated error: sampled rows of the full block vs the FP64 oracle,
     # and the GPU FP64 path on the 2^14 block (the >= 3x comparison)

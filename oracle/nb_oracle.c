@@ -17,7 +17,8 @@
  *    list of neighbours inside r_s (Sec. 2, Ahmad-Cohen scheme; Sec. 3.2.1,
  *    "Regular force and potential (GPU)"; Table 2 gives the O(N_i N) cost).
  *    The sums here run over ALL j != i: the split into inside/outside r_s is a
- *    subtraction by the consumer (reading recorded in the design doc).
+ *    subtraction by the consumer (the paper names the regular force as the part
+ *    from outside r_s; the all-j sum is what Newton's third law pins).
  *  - Its vector-Jacobian product (adjoint), obtained by differentiating the sums.
  *  - A fourth-order Hermite integrator with hierarchical power-of-two block
  *    steps (Sec. 2; the corrector and the Aarseth step criterion are the

@@ -407,3 +407,23 @@ def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
     tot = int(base.nb_off[-1])
     assert torch.equal(base.nb_idx[:tot], res.nb_idx[:tot])
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", list(range(10)))
+def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
+    """Dense neighbourhoods (r_s^2 x 9, hundreds of neighbours a row) with nb_cap 16: many hits
+    in every 32-j chunk of the packed kernels' interaction loop and lists cut at the cap inside a
+    chunk, for every variant; the kept entries are the smallest indices, as the oracle's."""
+    cl, rs2, idx, _ = p1k
+    big = 9 * rs2
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx, big, cap=16)
+    assert (ref[3] > 64).sum() > 100
+    ctx = make_ctx(cl.n, "mixed", cap=16)
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    ctx.set_plan_override(1, variant, 3)
+    res = ctx.regular_force(T(idx), big)
+    with pytest.warns(Warning):
+        ctx.sync()
+    check_mixed(res, ref)
+    check_lists_band(res, cl.x, idx, big, ref[3], ref[4], 16)
+    ctx.close()

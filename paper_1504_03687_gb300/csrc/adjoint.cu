@@ -16,7 +16,7 @@
 //            cotangents in shared memory) -> partial sums of dL/dr, dL/dw, dL/dm per j
 // A combine kernel adds the partials in a fixed order and scatters the i-side sums with
 // one atomic per (active i, component); for unique indices the result is deterministic.
-// For dense mixed-precision blocks (n_i >= 3n/4) one fused pass replaces the two: every
+// For dense blocks (n_i >= 3n/4), in either precision, one fused pass replaces the two: every
 // particle carries its (possibly zero) cotangents, and each pair evaluated once gives both
 // directions (i as the active row against j, and j as the active row against i).
 // Self pairs are skipped by r^2 == 0 (distinct particles never coincide).
@@ -601,6 +601,136 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const f
     }
 }
 
+// ---------------------------------------------------------------- fused single pass (FP64)
+// The same pair algebra as k_adj_fused_x2, in FP64 with one row per thread and the sums kept
+// in FP64 registers.  Records (four dvec4):
+//   {x,y,z,m} {vx,vy,vz,s} {ga0,ga1,ga2,gj0} {gj1,gj2,0,0}
+__global__ void k_build_crec64(int64_t n, int64_t n_pad, const dvec4 *__restrict__ rec, dvec4 *__restrict__ crec)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_pad; k += (int64_t)gridDim.x * blockDim.x) {
+        dvec4 a = make_dvec4(1e18, 1e18, 1e18, 0.0), b = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        if (k < n) {
+            a = rec[2 * k];
+            b = rec[2 * k + 1];
+        }
+        crec[4 * k] = a;
+        crec[4 * k + 1] = make_dvec4(b.x, b.y, b.z, 0.0);
+        crec[4 * k + 2] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        crec[4 * k + 3] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    }
+}
+
+__global__ void k_scatter_cotangents64(int64_t n, int64_t n_i, const int32_t *__restrict__ idx,
+                                       const double *__restrict__ g_acc, const double *__restrict__ g_jerk,
+                                       const double *__restrict__ g_pot, double *__restrict__ crec, unsigned *status)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_i; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[q];
+        if (i < 0 || i >= n) {
+            atomicOr(status, ST_BAD_INDEX);
+            continue;
+        }
+        double *r = crec + 16 * i;  // four dvec4 = 16 doubles
+        atomicAdd(r + 7, g_pot[q]);       // s
+        atomicAdd(r + 8, g_acc[3 * q]);   // ga
+        atomicAdd(r + 9, g_acc[3 * q + 1]);
+        atomicAdd(r + 10, g_acc[3 * q + 2]);
+        atomicAdd(r + 11, g_jerk[3 * q]);  // gj
+        atomicAdd(r + 12, g_jerk[3 * q + 1]);
+        atomicAdd(r + 13, g_jerk[3 * q + 2]);
+    }
+}
+
+template <int BLOCK, int TJ>
+__global__ void __launch_bounds__(BLOCK) k_adj_fused_f64(AdjArgs A, const dvec4 *__restrict__ crec)
+{
+    __shared__ dvec4 sj[2][4 * TJ];
+    const int tid = threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * BLOCK + tid;  // crec is padded past every row
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles_j * s) / A.S, t1 = (A.n_tiles_j * (s + 1)) / A.S;
+    const dvec4 a = crec[4 * k], b = crec[4 * k + 1], c = crec[4 * k + 2], d = crec[4 * k + 3];
+    const double xk[3] = {a.x, a.y, a.z}, vk[3] = {b.x, b.y, b.z}, ga[3] = {c.x, c.y, c.z}, gj[3] = {c.w, d.x, d.y};
+    const double mk = a.w, gs = b.w;
+    // k as receiver: its cotangents factor out of the j-sums (see k_adj_fused_x2)
+    double s0 = 0.0, s1 = 0.0, A1[3] = {0, 0, 0}, B1[3] = {0, 0, 0}, C1[3] = {0, 0, 0};
+    // m as receiver
+    double v2[3] = {0, 0, 0}, u2[3] = {0, 0, 0}, d2 = 0.0;
+    auto load_tile = [&](int buf, int64_t t) {
+        const dvec4 *src = crec + t * (4 * TJ);
+        for (int e = tid; e < 8 * TJ; e += BLOCK)
+            cp_async16(reinterpret_cast<char *>(&sj[buf][0]) + 16 * e, reinterpret_cast<const char *>(src) + 16 * e);
+        cp_async_commit();
+    };
+    if (t0 < t1) load_tile(0, t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        const int buf = (int)((t - t0) & 1);
+        if (t + 1 < t1) {
+            load_tile(buf ^ 1, t + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        for (int jj = 0; jj < TJ; ++jj) {
+            const dvec4 P0 = sj[buf][4 * jj], P1 = sj[buf][4 * jj + 1], P2 = sj[buf][4 * jj + 2],
+                        P3 = sj[buf][4 * jj + 3];
+            const double r[3] = {P0.x - xk[0], P0.y - xk[1], P0.z - xk[2]};
+            const double w[3] = {P1.x - vk[0], P1.y - vk[1], P1.z - vk[2]};
+            const double GAm[3] = {P2.x, P2.y, P2.z}, GJm[3] = {P2.w, P3.x, P3.y};
+            const double Mm = P0.w, Sm = P1.w;
+            const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            const double rinv = r2 > 0.0 ? rsqrt(r2) : 0.0;
+            const double rinv2 = rinv * rinv, rinv3 = rinv * rinv2;
+            const double q = r[0] * w[0] + r[1] * w[1] + r[2] * w[2];
+            const double b3 = -3.0 * rinv2;
+            const double gamma = b3 * q;
+            {  // k as receiver
+                const double ar = ga[0] * r[0] + ga[1] * r[1] + ga[2] * r[2];
+                const double jr = gj[0] * r[0] + gj[1] * r[1] + gj[2] * r[2];
+                const double jw = gj[0] * w[0] + gj[1] * w[1] + gj[2] * w[2];
+                const double beta = b3 * jr;
+                const double alpha = b3 * (ar + jw - 5.0 * q * jr * rinv2) + gs;
+                const double rm = rinv3 * Mm;
+                s0 += rm;
+                s1 += rm * gamma;
+                const double ra = rm * alpha, rb = rm * beta;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    A1[cc] += ra * r[cc];
+                    B1[cc] += rb * w[cc];
+                    C1[cc] += rb * r[cc];
+                }
+            }
+            {  // m as receiver
+                const double P = GAm[0] * r[0] + GAm[1] * r[1] + GAm[2] * r[2];
+                const double Q = GJm[0] * r[0] + GJm[1] * r[1] + GJm[2] * r[2];
+                const double R = GJm[0] * w[0] + GJm[1] * w[1] + GJm[2] * w[2];
+                const double PR = P + R;
+                const double b3Q = b3 * Q;
+                const double nalpha = b3 * (PR - 5.0 * q * Q * rinv2) - Sm;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    v2[cc] += rinv3 * (GAm[cc] + nalpha * r[cc] + b3Q * w[cc] + gamma * GJm[cc]);
+                    u2[cc] += rinv3 * (GJm[cc] + b3Q * r[cc]);
+                }
+                d2 -= rinv3 * (PR + gamma * Q) + Sm * rinv;
+            }
+        }
+        __syncthreads();
+    }
+    if (k < A.n) {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const double v1 = ga[cc] * s0 + gj[cc] * s1 + A1[cc] + B1[cc];
+            const double u1 = gj[cc] * s0 + C1[cc];
+            A.part[((int64_t)s * 7 + cc) * A.n + k] = mk * v2[cc] - v1;
+            A.part[((int64_t)s * 7 + 3 + cc) * A.n + k] = mk * u2[cc] - u1;
+        }
+        A.part[((int64_t)s * 7 + 6) * A.n + k] = d2;
+    }
+}
+
 // ---------------------------------------------------------------- FP64 passes
 template <int BLOCK, int TJ>
 __global__ void __launch_bounds__(BLOCK) k_adj_iside_f64(AdjArgs A)
@@ -737,10 +867,11 @@ constexpr int kAdjNI = 4, kAdjNJ = 4, kAdjBlock = 128, kAdjTJ = 128, kAdjTI = 64
 size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms, int64_t *rows_pad_out, int *SA,
                              int *SB);
 
-// The fused single pass does N x N pair work with ~96 FP32 operations, the two passes
-// 2 x N_i x N with ~56 and ~60: the fused pass wins for dense blocks.
-constexpr int kFusedBlock = 128, kFusedTJ = 128;
-static bool use_fused(int precision, int64_t n, int64_t n_i) { return precision == 1 && 4 * n_i >= 3 * n; }
+// The fused single pass does N x N pair work with ~96 FP32 operations (~81 in FP64), the two
+// passes 2 x N_i x N with ~56 and ~60 (~63 each in FP64): the fused pass wins for dense blocks.
+constexpr int kFusedBlock = 128, kFusedTJ = 128;     // mixed: one packed row pair a thread
+constexpr int kFused64Block = 128, kFused64TJ = 64;  // FP64: one row a thread
+static bool use_fused(int precision, int64_t n, int64_t n_i) { return 4 * n_i >= 3 * n; }
 
 // Splits of the streamed dimension for ctas_x CTAs along the other one, P resident CTAs:
 // the count with the least time in whole waves of the GPU, ceil(ctas_x S / P) / S, each
@@ -767,15 +898,25 @@ struct FusedGeom {
     int S;
 };
 
-static FusedGeom fused_geom(int64_t n, int num_sms)
+static FusedGeom fused_geom(int precision, int64_t n, int num_sms)
 {
     FusedGeom f{};
-    f.n_pad = ((n + 255) / 256) * 256;
-    f.n_tiles = f.n_pad / kFusedTJ;
-    f.ctas = (n + 2 * kFusedBlock - 1) / (2 * kFusedBlock);
-    f.S = splits_for(f.ctas, f.n_tiles, (int64_t)(num_sms > 0 ? num_sms : 152) * 3);  // 3 CTAs per SM
+    const int64_t sms = num_sms > 0 ? num_sms : 152;
+    f.n_pad = ((n + 255) / 256) * 256;  // a multiple of both tile depths and of the row blocks
+    if (precision == 1) {
+        f.n_tiles = f.n_pad / kFusedTJ;
+        f.ctas = (n + 2 * kFusedBlock - 1) / (2 * kFusedBlock);
+        f.S = splits_for(f.ctas, f.n_tiles, sms * 3);  // 3 CTAs per SM
+    } else {
+        f.n_tiles = f.n_pad / kFused64TJ;
+        f.ctas = (n + kFused64Block - 1) / kFused64Block;
+        f.S = splits_for(f.ctas, f.n_tiles, sms * 4);  // 4 CTAs per SM
+    }
     return f;
 }
+
+// Bytes of the fused pass's per-particle records.
+static size_t fused_rec_bytes(int precision, int64_t n_pad) { return (size_t)n_pad * (precision == 1 ? 80 : 128); }
 
 // Geometry shared by the scratch sizing and the launch.
 struct AdjGeom {
@@ -819,8 +960,8 @@ size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms,
     const size_t pa = (size_t)g.SA * 6 * (size_t)n_i * 8, pb = (size_t)g.SB * 7 * (size_t)n * 8;
     size_t need = irec + 256 + pa + 256 + pb;
     if (use_fused(precision, n, n_i)) {
-        const FusedGeom f = fused_geom(n, num_sms);
-        const size_t fb = (size_t)f.n_pad * 80 + 256 + (size_t)f.S * 7 * (size_t)n * 8;
+        const FusedGeom f = fused_geom(precision, n, num_sms);
+        const size_t fb = fused_rec_bytes(precision, f.n_pad) + 256 + (size_t)f.S * 7 * (size_t)n * 8;
         if (fb > need) need = fb;
     }
     return need;
@@ -831,18 +972,14 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
                    double *g_m, void *scratch, unsigned *status, int num_sms)
 {
     if (use_fused(precision, n, n_i)) {  // dense block: one fused pass over all pairs
-        const FusedGeom f = fused_geom(n, num_sms);
-        float4 *crec = static_cast<float4 *>(scratch);
+        const FusedGeom f = fused_geom(precision, n, num_sms);
         double *part = reinterpret_cast<double *>(static_cast<char *>(scratch) +
-                                                  (((size_t)f.n_pad * 80 + 255) & ~(size_t)255));
+                                                  ((fused_rec_bytes(precision, f.n_pad) + 255) & ~(size_t)255));
         int64_t gr = (f.n_pad + 255) / 256;
         if (gr > 152 * 8) gr = 152 * 8;
-        k_build_crec<<<(unsigned)gr, 256, 0, st>>>(n, f.n_pad, static_cast<const float4 *>(rec), crec);
         int64_t gq = (n_i + 255) / 256;
         if (gq > 152 * 8) gq = 152 * 8;
         if (gq < 1) gq = 1;
-        k_scatter_cotangents<<<(unsigned)gq, 256, 0, st>>>(n, n_i, idx, g_acc, g_jerk, g_pot,
-                                                           reinterpret_cast<float *>(crec), status);
         AdjArgs A{};
         A.n = n;
         A.n_i = n_i;
@@ -850,8 +987,21 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
         A.S = f.S;
         A.part = part;
         A.status = status;
-        k_adj_fused_x2<kFusedBlock, kFusedTJ, 3><<<dim3((unsigned)f.ctas, (unsigned)f.S), kFusedBlock,
-                                                   adj_fused_smem<kFusedBlock, kFusedTJ>(), st>>>(A, crec);
+        if (precision == 1) {
+            float4 *crec = static_cast<float4 *>(scratch);
+            k_build_crec<<<(unsigned)gr, 256, 0, st>>>(n, f.n_pad, static_cast<const float4 *>(rec), crec);
+            k_scatter_cotangents<<<(unsigned)gq, 256, 0, st>>>(n, n_i, idx, g_acc, g_jerk, g_pot,
+                                                               reinterpret_cast<float *>(crec), status);
+            k_adj_fused_x2<kFusedBlock, kFusedTJ, 3><<<dim3((unsigned)f.ctas, (unsigned)f.S), kFusedBlock,
+                                                       adj_fused_smem<kFusedBlock, kFusedTJ>(), st>>>(A, crec);
+        } else {
+            dvec4 *crec = static_cast<dvec4 *>(scratch);
+            k_build_crec64<<<(unsigned)gr, 256, 0, st>>>(n, f.n_pad, static_cast<const dvec4 *>(rec), crec);
+            k_scatter_cotangents64<<<(unsigned)gq, 256, 0, st>>>(n, n_i, idx, g_acc, g_jerk, g_pot,
+                                                                 reinterpret_cast<double *>(crec), status);
+            k_adj_fused_f64<kFused64Block, kFused64TJ>
+                <<<dim3((unsigned)f.ctas, (unsigned)f.S), kFused64Block, 0, st>>>(A, crec);
+        }
         int64_t gj = (n + 255) / 256;
         if (gj > 152 * 16) gj = 152 * 16;
         k_adj_combine_j<<<(unsigned)gj, 256, 0, st>>>(part, f.S, n, g_x, g_v, g_m);

@@ -211,11 +211,19 @@ def main():
     ap.add_argument("--variants", default="",
                     help="with --profile: comma list of kernel:variant:splits plans to time in turn "
                          "(e.g. 1:0:14,1:5:14); empty = the automatic plan")
+    ap.add_argument("--ac-king", type=float, default=None, metavar="T_END",
+                    help="only the Ahmad-Cohen integration of the million-body King cluster, from t = 0 to "
+                         "T_END (steps at most min(T_END, 1/64)); prints its JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile_case(args)
+    if args.ac_king is not None:
+        import torch
+        dev = torch.device("cuda", 0)
+        print(json.dumps(bench_ac_king_1m(dev, t_end=args.ac_king, dt_max=min(args.ac_king, 1.0 / 64))))
+        return
 
     import torch
     rank, world, local = dist_env()
@@ -734,11 +742,11 @@ def gpu_energy(dev, m, x, v):
     return 0.5 * float((m[:, None] * v * v).sum()) + W_
 
 
-def bench_ac_king_1m(dev, t_end=1.0 / 64):
+def bench_ac_king_1m(dev, t_end=1.0 / 64, dt_max=None):
     """The Ahmad-Cohen integrator on the million-body King W0 = 6 cluster (5 % binaries as
     centre-of-mass particles), mixed precision, r_s towards 50 neighbours (cap 256), from
-    t = 0 to t_end = dt_max; wall time, particle steps, energy error from the mixed all-pairs
-    potentials before and after.  Context: the paper's 1M runs took about 800 s of wall time
+    t = 0 to t_end (maximum step dt_max, by default t_end); wall time, particle steps, energy
+    error from the mixed all-pairs potentials before and after.  Context: the paper's 1M runs took about 800 s of wall time
     per N-body time unit on 16 nodes (32 K20X + 320 CPU cores)."""
     import torch
 
@@ -748,7 +756,8 @@ def bench_ac_king_1m(dev, t_end=1.0 / 64):
     rs2 = W.neighbour_radius2(cl.x, 50, seed=2)
     E0 = gpu_energy(dev, cl.m, cl.x, cl.v)
     ctx = Context(cl.n, precision="mixed", nb_cap=256, device=dev.index or 0)
-    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=t_end, nb_opt=50)
+    ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, eta_irr=0.02, eta_reg=0.03, eta_s=0.01,
+                      dt_max=t_end if dt_max is None else dt_max, nb_opt=50)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = ac.run(t_end, max_blocks=2000000)
@@ -762,6 +771,7 @@ def bench_ac_king_1m(dev, t_end=1.0 / 64):
                         f"mixed, t = 0 .. {t_end}", "wall_s": wall, "block_steps": st["blocks"],
             "irregular_steps": st["irregular_steps"], "regular_steps": st["regular_steps"],
             "particle_steps_per_s": st["irregular_steps"] / wall, "wall_s_per_nbody_time_unit": wall / t_end,
+            "dt_max": t_end if dt_max is None else dt_max,
             "energy_rel_error": (E1 - E0) / abs(E0), "all_synchronised": bool(np.all(g["t"] == t_end)),
             "context": "paper: about 800 s per N-body time unit for 1M on 16 nodes, 32 K20X + 320 CPU cores "
                        "(no binaries); this run is short and starts with small steps (eta_s), so the per-unit "

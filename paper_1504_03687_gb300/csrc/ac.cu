@@ -43,6 +43,9 @@ struct AcDev {
     int32_t *LR, *LI;
     int32_t *ell, *ell_cnt;
     int32_t *lr_hist;  // [64] particles per regular level (kept current by the corrector)
+    unsigned *tickets; // [2] CTAs done in the classify and corrector launches (last-CTA epilogues)
+    int32_t *io;       // device address of the pinned host words the corrector publishes:
+                       // [0, 64) the regular-level histogram, [64] the step's status flags
     int32_t cap, lmin, lmax;
     double eta_irr, eta_reg, dt_max;
     int32_t nb_opt;
@@ -135,7 +138,7 @@ __global__ void k_ac_init(AcDev D, int64_t n, const double *Fa, const double *Ja
 // Active row k: regular step too?  Compacts the regular subset (order of the subset is
 // irrelevant: every row's sums are independent of the others).
 __global__ void k_ac_classify(AcDev D, int64_t n_act, const int32_t *list, int64_t t_ticks, unsigned *counter,
-                              int32_t *reg_pos, int32_t *reg_idx, double *reg_rs2)
+                              int32_t *reg_pos, int32_t *reg_idx, double *reg_rs2, int64_t expected, unsigned *status)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = list[k];
@@ -149,12 +152,22 @@ __global__ void k_ac_classify(AcDev D, int64_t n_act, const int32_t *list, int64
         }
         reg_pos[k] = p;
     }
+    // the last CTA to finish checks the count against the host's prediction (a mismatch is a
+    // device error of the step) and leaves the counter at zero for the next step
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&D.tickets[0], 1u) == gridDim.x - 1) {
+        __threadfence();
+        if (atomicAdd(counter, 0u) != (unsigned)expected) atomicOr(status, ST_DEVICE);
+        atomicExch(counter, 0u);
+        atomicExch(&D.tickets[0], 0u);
+    }
 }
 
 __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double t, int64_t t_ticks,
                              const int32_t *reg_pos, const double *Fo, const double *Jo, const double *Fa,
                              const double *Ja, const double *Fn, const double *Jn, const int32_t *cnt_true,
-                             int32_t *want, unsigned long long *pairs)
+                             int32_t *want, unsigned long long *pairs, unsigned *status)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = list[k];
@@ -237,6 +250,20 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         want[k] = L;
         pack_state_one(i, D.x + 3 * i, D.v + 3 * i, D.a + 3 * i, D.jk + 3 * i, t, D.m[i], D.s64, D.s32);
     }
+    // the last CTA to finish publishes the final histogram and the step's status flags to the
+    // host words (read after the scheduler's synchronisation) and clears the flags; one word
+    // per thread (the launch has 128 threads a CTA)
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&D.tickets[1], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x < 64) D.io[threadIdx.x] = __ldcg(&D.lr_hist[threadIdx.x]);
+        if (threadIdx.x == 64) D.io[64] = (int32_t)atomicExch(status, 0u);
+        if (threadIdx.x == 65) atomicExch(&D.tickets[1], 0u);
+    }
 }
 
 // The regular subset's new lists (CSR) replace the old per-particle lists; one warp per row.
@@ -254,10 +281,6 @@ __global__ void k_ac_lists(AcDev D, int64_t n_reg, const int32_t *reg_idx, const
 }
 
 // The regular subset the classifier found must be the one the level histogram predicted.
-__global__ void k_ac_check_count(const unsigned *counter, int64_t expected, unsigned *status)
-{
-    if (*counter != (unsigned)expected) atomicOr(status, ST_DEVICE);
-}
 
 __global__ void k_ac_hist(AcDev D, int64_t n)
 {
@@ -300,8 +323,9 @@ struct nb_ac {
     unsigned *counter = nullptr, *h_counter = nullptr;
     void *srec = nullptr;  // state records (pack_state_one layout of the context's precision)
     unsigned long long *pairs = nullptr;
-    int32_t *h_lr = nullptr;      // [64] host copy of the regular-level histogram (pinned)
-    unsigned *h_status = nullptr;  // the context's status word of the last block step (pinned)
+    int32_t *h_io = nullptr;       // pinned, mapped: [0, 64) regular-level histogram, [64] status flags
+    int32_t *h_lr = nullptr;       // = h_io
+    unsigned *h_status = nullptr;  // = h_io + 64: the context's status flags of the last block step
     bool overflow = false;         // some neighbour list was cut at nb_cap
     double stats[6] = {0, 0, 0, 0, 0, 0};
     char err[384] = {0};
@@ -352,10 +376,15 @@ static bool ac_alloc(nb_ac *s, int64_t n, int cap)
         cudaMalloc(&s->Jn, v3) == cudaSuccess && cudaMalloc(&s->Pn, n * 8) == cudaSuccess &&
         cudaMalloc(&s->counter, 4) == cudaSuccess && cudaMallocHost(&s->h_counter, 4) == cudaSuccess &&
         cudaMalloc(&s->pairs, 8) == cudaSuccess && cudaMalloc(&D.lr_hist, 64 * 4) == cudaSuccess &&
-        cudaMallocHost(&s->h_lr, 64 * 4) == cudaSuccess && cudaMallocHost(&s->h_status, 4) == cudaSuccess &&
+        cudaMalloc(&D.tickets, 2 * 4) == cudaSuccess &&
+        cudaHostAlloc(&s->h_io, 80 * 4, cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer((void **)&D.io, s->h_io, 0) == cudaSuccess &&
         cudaMemset(D.lr_hist, 0, 64 * 4) == cudaSuccess && cudaMemset(s->pairs, 0, 8) == cudaSuccess &&
+        cudaMemset(D.tickets, 0, 2 * 4) == cudaSuccess && cudaMemset(s->counter, 0, 4) == cudaSuccess &&
         cudaMalloc(&s->srec, state_record_bytes(s->cs.precision, n)) == cudaSuccess;
     if (!ok) cudaGetLastError();
+    s->h_lr = s->h_io;
+    s->h_status = s->h_io ? reinterpret_cast<unsigned *>(s->h_io + 64) : nullptr;
     return ok;
 }
 
@@ -488,11 +517,14 @@ nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const
 }
 
 // One block step with a single host synchronisation (inside nb_sched_update): the size of the
-// regular subset follows from the histogram of regular levels read back with the previous
-// step (a particle takes a regular step exactly when its regular level is >= L*, the
-// coarsest level whose step divides the block time), so the regular force is launched
-// without waiting; the context's status word and the new histogram come back with the
-// scheduler's own read-back.
+// regular subset follows from the histogram of regular levels published by the previous step
+// (a particle takes a regular step exactly when its regular level is >= L*, the coarsest
+// level whose step divides the block time), so the regular force is launched without
+// waiting. The last CTA of the classify launch checks that size against the classified
+// count; the last CTA of the corrector writes the new histogram and the step's status flags
+// into mapped host words, which the scheduler's synchronisation makes visible. A step with no
+// regular particle is five launches (classify, irregular force, corrector, re-sort) and one
+// synchronisation.
 nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_regular)
 {
     if (!s) return NB_ERR_ARG;
@@ -510,10 +542,8 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     int64_t nr = 0;
     for (int b = lstar; b < 64; ++b) nr += s->h_lr[b];
     const int cap = cs.cap;
-    ACK(cudaMemsetAsync(s->counter, 0, 4, st), "memset");
     k_ac_classify<<<grid_of(na, 256, 152 * 16), 256, 0, st>>>(s->D, na, list, t_ticks, s->counter, s->reg_pos,
-                                                               s->reg_idx, s->reg_rs2);
-    k_ac_check_count<<<1, 1, 0, st>>>(s->counter, nr, cs.status + SS_FLAGS);
+                                                               s->reg_idx, s->reg_rs2, nr, cs.status + SS_FLAGS);
     ACK(cudaGetLastError(), "classify launch");
     if (nr > 0) {
         ANB(nb_predict(s->ctx, t), "nb_predict");
@@ -530,12 +560,9 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     }
     k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks, s->reg_pos, s->Fo, s->Jo,
                                                               s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
-                                                              s->pairs);
+                                                              s->pairs, cs.status + SS_FLAGS);
     if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);
     ACK(cudaGetLastError(), "corrector launch");
-    ACK(cudaMemcpyAsync(s->h_lr, s->D.lr_hist, 64 * 4, cudaMemcpyDeviceToHost, st), "copy histogram");
-    ACK(cudaMemcpyAsync(s->h_status, cs.status + SS_FLAGS, 4, cudaMemcpyDeviceToHost, st), "copy status");
-    ACK(cudaMemsetAsync(cs.status + SS_FLAGS, 0, 4, st), "clear status");
     ss = nb_sched_update(s->sched, s->want, nullptr, 1);  // synchronises the stream
     if (ss != NB_OK) return afail(s, ss, "nb_sched_update: %s", nb_sched_last_error(s->sched));
     const unsigned f = *s->h_status;
@@ -723,12 +750,11 @@ nb_status nb_ac_free(nb_ac *s)
     if (s->sched) nb_sched_free(s->sched);
     void *p[] = {s->D.Fr, s->D.Jr, s->D.D2, s->D.D3, s->D.rs2, s->D.Tr, s->D.LR, s->D.LI, s->D.ell, s->D.ell_cnt,
                  s->reg_pos, s->reg_idx, s->want, s->cnt_true, s->csr, s->off, s->reg_rs2, s->Fo, s->Jo, s->Po,
-                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist, s->srec};
+                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist, s->D.tickets, s->srec};
     for (void *q : p)
         if (q) cudaFree(q);
     if (s->h_counter) cudaFreeHost(s->h_counter);
-    if (s->h_lr) cudaFreeHost(s->h_lr);
-    if (s->h_status) cudaFreeHost(s->h_status);
+    if (s->h_io) cudaFreeHost(s->h_io);
     delete s;
     return NB_OK;
 }

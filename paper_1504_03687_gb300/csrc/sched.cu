@@ -214,6 +214,8 @@ struct nb_sched {
     int32_t *keep_part = nullptr, *keep_rank = nullptr, *bad = nullptr, *h_bad = nullptr;
     int8_t *keep_lev = nullptr;
     int32_t *cta_count = nullptr;
+    // level totals: pinned host memory mapped into the device, written by the sort kernels
+    // themselves (no copy to issue); totals is the device address of h_totals
     int64_t *totals = nullptr, *h_totals = nullptr;
     char err[256] = {0};
 };
@@ -264,9 +266,8 @@ static nb_status sched_sort(nb_sched *s, int64_t n_act, const int32_t *d_want, i
         k_sort_scatter<<<(int)g, 256, 0, s->stream>>>(A);
     }
     SCK(cudaGetLastError(), "sort launch");
-    SCK(cudaMemcpyAsync(s->h_totals, s->totals, kBins * sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream),
-        "copy level counts");
-    SCK(cudaMemcpyAsync(s->h_bad, s->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream), "copy flag");
+    // the flag can only be raised by stored levels out of range: the initial sort's
+    if (!d_want) SCK(cudaMemcpyAsync(s->h_bad, s->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream), "copy flag");
     SCK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
     return NB_OK;
 }
@@ -307,8 +308,8 @@ nb_status nb_sched_init(nb_sched **out, int64_t n, const int32_t *levels, int32_
         cudaMalloc(&s->keep_part, n * 4) != cudaSuccess ||
         cudaMalloc(&s->keep_rank, n * 4) != cudaSuccess || cudaMalloc(&s->keep_lev, n) != cudaSuccess ||
         cudaMalloc(&s->cta_count, chunks * kBins * 4) != cudaSuccess ||
-        cudaMalloc(&s->totals, kBins * sizeof(int64_t)) != cudaSuccess ||
-        cudaMallocHost(&s->h_totals, kBins * sizeof(int64_t)) != cudaSuccess) {
+        cudaHostAlloc(&s->h_totals, kBins * sizeof(int64_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&s->totals, s->h_totals, 0) != cudaSuccess) {
         cudaGetLastError();
         return bail(NB_ERR_OOM);
     }
@@ -338,7 +339,7 @@ nb_status nb_sched_free(nb_sched *s)
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     void *p[] = {s->list,      s->level,    s->want_stage, s->granted_stage, s->keep_part,
-                 s->keep_rank, s->keep_lev, s->cta_count,  s->totals,        s->bad};
+                 s->keep_rank, s->keep_lev, s->cta_count,  s->bad};
     for (void *q : p)
         if (q) cudaFree(q);
     if (s->h_totals) cudaFreeHost(s->h_totals);

@@ -563,6 +563,7 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
                                                               s->pairs, cs.status + SS_FLAGS);
     if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);
     ACK(cudaGetLastError(), "corrector launch");
+    ctx_state_changed(s->ctx);  // the corrector rewrote the context's state arrays
     ss = nb_sched_update(s->sched, s->want, nullptr, 1);  // synchronises the stream
     if (ss != NB_OK) return afail(s, ss, "nb_sched_update: %s", nb_sched_last_error(s->sched));
     const unsigned f = *s->h_status;

@@ -465,6 +465,13 @@ bool ctx_state(nb_ctx *c, CtxState *o)
                   c->precision, c->cap, c->num_sms, c->device, c->n, c->n_pad};
     return true;
 }
+
+// The state arrays were rewritten in place (by the integrator): what the context derived from
+// them (the state records of the irregular force) must be rebuilt on next use.
+void ctx_state_changed(nb_ctx *c)
+{
+    if (c) c->srec_valid = false;
+}
 }  // namespace nbgpu
 
 // ------------------------------------------------------------------------------ ABI

@@ -110,6 +110,7 @@ struct CtxState {
     int64_t n, n_pad;
 };
 bool ctx_state(::nb_ctx *c, CtxState *out);
+void ctx_state_changed(::nb_ctx *c);  // the state arrays were rewritten in place
 
 // Irregular force (irregular.cu).  Lists as CSR (off) or, with ell_stride > 0, per
 // particle: particle i's list is nb[i * ell_stride .. + ell_cnt[i]).

@@ -151,3 +151,37 @@ def test_hermite_run_to_t1_energy_drift(gpu_lib):
             assert e < 2 * e_ref + 1e-9, (e, e_ref)
         ac.close()
         ctx.close()
+
+
+def test_context_irregular_force_sees_the_integrated_state(gpu_lib):
+    """The integrator rewrites the context's state arrays in place: the context's own irregular
+    force (predict-on-load form, which caches per-particle state records) must use the state
+    after the steps, whether or not it was called before them. Two identical runs, one with a
+    call before the steps that fills the cache, give identical results after them (FP64)."""
+    from paper_1504_03687_gb300 import ACIntegrator
+    cl = W.plummer(2000, 107, masses="kroupa")
+    rs2 = W.neighbour_radius2(cl.x, 40, seed=107)
+    kw = dict(eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0.125, nb_opt=40)
+    idx = np.arange(0, 2000, 200, dtype=np.int32)  # 10 rows: 10 x 128 < N, the cached-record form
+
+    def csr(g):
+        cnt = g["nb_count"][idx]
+        off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+        flat = np.concatenate([g["nb_lists"][i, :c] for i, c in zip(idx, cnt)]).astype(np.int32)
+        return off, flat
+
+    out = []
+    for warm in (True, False):
+        ctx = make(cl.n, "fp64", 128)
+        ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
+        if warm:
+            ctx.irregular_force(0.0, idx, *csr(ac.get()))
+        t = 0.0
+        for _ in range(60):
+            t = ac.step()[0]
+        res = ctx.irregular_force(t, idx, *csr(ac.get()))
+        out.append(res)
+        ac.close()
+        ctx.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)

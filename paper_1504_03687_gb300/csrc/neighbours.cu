@@ -100,10 +100,12 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *wsum
     return before + x - v;
 }
 
-// Per row: true count = sum over segments; kept = min(count, cap); block-local scan.
+// Per row: true count = sum over segments; kept = min(count, cap); block-local scan. A launch
+// of one CTA (n_i <= SCAN_BLOCK) has the whole scan: it writes the total and checks the
+// capacity itself, and the block-sum passes are skipped.
 __global__ void k_seg_scan_local(const int32_t *__restrict__ seg_cnt, int64_t G, int64_t n_i, int cap,
                                  int64_t *__restrict__ off, int64_t *__restrict__ bsum,
-                                 int32_t *__restrict__ count_true, unsigned *status)
+                                 int32_t *__restrict__ count_true, unsigned *status, int64_t capacity)
 {
     __shared__ int64_t wsum[32];
     const int64_t k = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x;
@@ -118,7 +120,13 @@ __global__ void k_seg_scan_local(const int32_t *__restrict__ seg_cnt, int64_t G,
     int64_t total;
     const int64_t ex = block_exclusive_scan(kept, wsum, total);
     if (k < n_i) off[k] = ex;
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = total;
+        if (gridDim.x == 1) {
+            off[n_i] = total;
+            if (total > capacity) atomicOr(status, ST_CSR_FULL);
+        }
+    }
 }
 
 // Exclusive scan of the nb block sums in one CTA (chunks of SCAN_BLOCK with a carry);
@@ -252,10 +260,13 @@ int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap
         ++kernels;
     }
     k_seg_scan_local<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(many ? row_total : seg_cnt, many ? 1 : G, n_i, cap, off,
-                                                          scan_tmp, count_true, status);
-    k_scan_blocks<<<1, SCAN_BLOCK, 0, st>>>(scan_tmp, nb);
-    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(off, scan_tmp, n_i, nb, nb_capacity, status);
-    kernels += 3;
+                                                          scan_tmp, count_true, status, nb_capacity);
+    ++kernels;
+    if (nb > 1) {
+        k_scan_blocks<<<1, SCAN_BLOCK, 0, st>>>(scan_tmp, nb);
+        k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(off, scan_tmp, n_i, nb, nb_capacity, status);
+        kernels += 2;
+    }
     if (!nb_idx || L <= 0) return kernels;
     if (many) {
         k_seg_gather_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity);

@@ -13,6 +13,26 @@ namespace nbgpu {
 // replica of the state predicts bit-identically; against a term-by-term evaluation the
 // results agree to a few units in the last place.
 
+// Double-single split x = hi + lo for the mixed j-record.  hi is x with its 29 low mantissa
+// bits cleared, so x - hi is exact in FP64 and hi is exactly a float: its bits are assembled
+// with integer operations (exponent rebiased from 1023 to 127, top 23 mantissa bits) and only
+// lo takes an FP64 subtraction and one rounding to FP32 (|x - (hi + lo)| <= 2^-48 |x|).  On
+// GB300 the FP64 pipe, not HBM, bounds the predictor, and this split takes two FP64
+// operations a coordinate instead of four.  Zero and values outside the normal float range
+// take the conversion itself.
+__device__ __forceinline__ void split_ds(double x, float &hi, float &lo)
+{
+    const long long b = __double_as_longlong(x);
+    const double xh = __longlong_as_double(b & ~0x1FFFFFFFLL);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e >= 897 && e <= 1150)
+        hi = __uint_as_float((unsigned)((b >> 32) & 0x80000000LL) | ((unsigned)(e - 896) << 23) |
+                             (unsigned)((b >> 29) & 0x7FFFFF));
+    else
+        hi = __double2float_rn(xh);
+    lo = __double2float_rn(__dsub_rn(x, xh));
+}
+
 __device__ __forceinline__ void write_records(int64_t i, double x, double y, double z, double vx,
                                               double vy, double vz, double m, dvec4 *rec64,
                                               float4 *rec32)
@@ -22,10 +42,10 @@ __device__ __forceinline__ void write_records(int64_t i, double x, double y, dou
         rec64[2 * i + 1] = make_dvec4(vx, vy, vz, 0.0);
     }
     if (rec32) {
-        const float xh = __double2float_rn(x), yh = __double2float_rn(y), zh = __double2float_rn(z);
-        const float xl = __double2float_rn(x - (double)xh);
-        const float yl = __double2float_rn(y - (double)yh);
-        const float zl = __double2float_rn(z - (double)zh);
+        float xh, yh, zh, xl, yl, zl;
+        split_ds(x, xh, xl);
+        split_ds(y, yh, yl);
+        split_ds(z, zh, zl);
         rec32[3 * i] = make_float4(xh, yh, zh, __double2float_rn(m));
         rec32[3 * i + 1] = make_float4(xl, yl, zl, 0.f);
         rec32[3 * i + 2] = make_float4(__double2float_rn(vx), __double2float_rn(vy),

@@ -337,6 +337,9 @@ def main():
 
     # accuracy at the stated error: sampled rows of the full block vs the FP64 oracle,
     # and the GPU FP64 path on the 2^14 block (the >= 3x comparison)
+    # with more than one rank only the step itself (and its accuracy) is measured: the other
+    # sections are single-GPU measurements and would hold every rank's GPU meanwhile
+    solo = world == 1
     extra = {}
     if rank == 0:
         import oracle
@@ -355,6 +358,7 @@ def main():
                     for q, e in (("acc", ea), ("jerk", ej), ("pot", ep))}
         extra["error_vs_oracle_mixed"] = errs(full.acc[sel].cpu().numpy(), full.jerk[sel].cpu().numpy(),
                                               full.pot[sel].cpu().numpy())
+    if rank == 0 and solo:
         ctx64 = Context(n, precision="fp64", nb_cap=NB_CAP, device=local)
         ctx64.set_particles(*state)
         ctx64.predict(0.125)
@@ -389,14 +393,14 @@ def main():
             extra["scheduler"] = bench_scheduler(dev, cl)
         ctx64.close()
 
-    if rank == 0 and not args.no_ensemble:
+    if rank == 0 and solo and not args.no_ensemble:
         extra["ensemble"] = bench_ensemble(dev)
-    if rank == 0 and not args.no_adjoint:
+    if rank == 0 and solo and not args.no_adjoint:
         extra["adjoint"] = bench_adjoint(dev)
-    if rank == 0 and not args.no_integrator:
+    if rank == 0 and solo and not args.no_integrator:
         extra["ac_integrator"] = bench_ac(dev)
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and solo and not args.no_cpu:
         import oracle
         import types
         xp_np, vp_np = oracle.predict(0.125, cl.x, cl.v, a0, j0, tl)

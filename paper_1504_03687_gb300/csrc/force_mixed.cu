@@ -4,7 +4,8 @@
 // Precision scheme: positions arrive as FP64 split into hi/lo floats; the coordinate
 // difference is formed in double-single ((hi - hi) + (lo - lo)), every other pairwise
 // operation runs in FP32 on the CUDA cores (one MUFU rsqrt per pair), per-i sums are
-// accumulated in FP32 over one j-tile and promoted to FP64 at the end of every tile.
+// accumulated in FP32 over one j-tile, or two in the packed variants other than the
+// four-row one at 3 CTAs per SM (128 to 512 j), and promoted to FP64 after it.
 // Not a dense contraction, so no tensor cores.
 //
 // Kernels:

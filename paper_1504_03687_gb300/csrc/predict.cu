@@ -2,8 +2,10 @@
 // j-records the force kernels stream (paper Sec. 3.3.3; the predictor is the Taylor
 // series to the jerk term of the fourth-order Hermite scheme, Sec. 2).
 //
-// HBM-bound: 104 B read (x, v, a, jerk: 4 x 24 B; t_last, m: 16 B) and 48 B (predicted
-// x_p, v_p) + 64 B or 48 B (j-record) written per particle.
+// 112 B read (x, v, a, jerk: 4 x 24 B; t_last, m: 16 B) and 48 B (predicted x_p, v_p) +
+// 64 B or 48 B (j-record) written per particle.  On GB300 the FP64 pipe (1/64 of the FP32
+// rate), not HBM, bounds the kernel: 18 FP64 operations of Taylor terms and, for the mixed
+// record, 10 more for the hi/lo split and the conversions.
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
 

@@ -39,8 +39,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // ---- the neighbour-test distances ------------------------------------------------------
 // Both are written with explicit round-to-nearest intrinsics so that every kernel that
-// decides "j is a neighbour of i" (the force kernels and the ordered recompute of
-// over-full lists) obtains bit-identical r^2 values.
+// decides "j is a neighbour of i" (the scalar and packed force kernels, and the packed
+// kernels' replay of a chunk's hits) obtains bit-identical r^2 values.
 
 // Mixed precision: double-single coordinate difference (hi - hi) + (lo - lo).  The hi
 // difference is exact when the particles are close (Sterbenz), so close pairs keep the

@@ -11,7 +11,8 @@ namespace nbgpu {
 //  FP64 : 2 dvec4 per particle  {x, y, z, m}, {vx, vy, vz, 0}                   (64 B)
 //  mixed: 3 float4 per particle {x_hi, y_hi, z_hi, m}, {x_lo, y_lo, z_lo, 0},
 //                               {vx, vy, vz, 0}                                 (48 B)
-// x_hi = fl32(x), x_lo = fl32(x - x_hi).  Records n .. n_pad-1 are padding: mass 0,
+// x_hi = x with its 29 low mantissa bits cleared (a float), x_lo = fl32(x - x_hi), so
+// |x - (x_hi + x_lo)| <= 2^-48 |x|.  Records n .. n_pad-1 are padding: mass 0,
 // position 1e18, so whole tiles can be read without a bounds check.
 //
 // Neighbour capture.  The j-range is cut into G ordered segments; for every (segment g,

@@ -320,7 +320,7 @@ struct nb_ac {
     int64_t *off = nullptr;
     double *reg_rs2 = nullptr, *Fo = nullptr, *Jo = nullptr, *Po = nullptr, *Fa = nullptr, *Ja = nullptr,
            *Pa = nullptr, *Fn = nullptr, *Jn = nullptr, *Pn = nullptr;
-    unsigned *counter = nullptr, *h_counter = nullptr;
+    unsigned *counter = nullptr;  // regular rows classified so far in this step (reset by the last CTA)
     void *srec = nullptr;  // state records (pack_state_one layout of the context's precision)
     unsigned long long *pairs = nullptr;
     int32_t *h_io = nullptr;       // pinned, mapped: [0, 64) regular-level histogram, [64] status flags
@@ -374,7 +374,7 @@ static bool ac_alloc(nb_ac *s, int64_t n, int cap)
         cudaMalloc(&s->Fa, v3) == cudaSuccess && cudaMalloc(&s->Ja, v3) == cudaSuccess &&
         cudaMalloc(&s->Pa, n * 8) == cudaSuccess && cudaMalloc(&s->Fn, v3) == cudaSuccess &&
         cudaMalloc(&s->Jn, v3) == cudaSuccess && cudaMalloc(&s->Pn, n * 8) == cudaSuccess &&
-        cudaMalloc(&s->counter, 4) == cudaSuccess && cudaMallocHost(&s->h_counter, 4) == cudaSuccess &&
+        cudaMalloc(&s->counter, 4) == cudaSuccess &&
         cudaMalloc(&s->pairs, 8) == cudaSuccess && cudaMalloc(&D.lr_hist, 64 * 4) == cudaSuccess &&
         cudaMalloc(&D.tickets, 2 * 4) == cudaSuccess &&
         cudaHostAlloc(&s->h_io, 80 * 4, cudaHostAllocMapped) == cudaSuccess &&
@@ -754,7 +754,6 @@ nb_status nb_ac_free(nb_ac *s)
                  s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist, s->D.tickets, s->srec};
     for (void *q : p)
         if (q) cudaFree(q);
-    if (s->h_counter) cudaFreeHost(s->h_counter);
     if (s->h_io) cudaFreeHost(s->h_io);
     delete s;
     return NB_OK;

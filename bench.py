@@ -503,9 +503,10 @@ def run_profile_case(args):
 
 def bench_small_blocks(ctx, n, order, rs2_dev, dev, sizes=(1, 16, 128, 1024), reps=20):
     """Small active blocks of the same 2^20 cluster: the force call is then a pass over the j-records
-    (48 B per particle, mixed) rather than arithmetic.  L2 flushed before every call; median of
-    `reps` calls of the force kernel (library CUDA events) and of the whole step (predict + force
-    + reduce + neighbours).  Achieved GB/s counts the record bytes once per call."""
+    (48 B per particle, mixed) rather than arithmetic.  L2 flushed before every step (the step's
+    predictor then writes the records its force call reads); median of `reps` calls of the force
+    kernel (library CUDA events) and of the whole step (predict + force + reduce + neighbours).
+    Achieved GB/s counts the record bytes once per call."""
     import torch
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     peak = None
@@ -515,7 +516,8 @@ def bench_small_blocks(ctx, n, order, rs2_dev, dev, sizes=(1, 16, 128, 1024), re
     except Exception:
         pass
     rec_bytes = ((n + 255) // 256 * 256) * 48
-    res = {"record_bytes": rec_bytes, "hbm_peak_gbs": peak, "l2": "flushed (512 MB write) before every call",
+    res = {"record_bytes": rec_bytes, "hbm_peak_gbs": peak,
+           "l2": "flushed (512 MB write) before every step; the step's predictor writes the records",
            "blocks": {}}
     for b in sizes:
         idx = torch.as_tensor(order[:b], device=dev)

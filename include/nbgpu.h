@@ -32,6 +32,7 @@
 #ifndef NBGPU_H
 #define NBGPU_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

@@ -140,6 +140,19 @@ def fp32_peak_tflops(num_sms):
     return num_sms * 128 * 2 * mhz * 1e6 / 1e12, src
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine architecture."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
 def oracle_rate(cl, rs2, rows, threads=None):
     """Oracle pairs/s on `rows` active particles against all j (host cores)."""
     import oracle
@@ -179,7 +192,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": cl.n, "sample": sample_desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc,
+                         "cpu": host_cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -409,7 +423,7 @@ def main():
         rows = int(max(32, min(BLOCKS[-1], 12.0 * rate / n)))  # ~12 s of oracle work
         rate, dt = oracle_rate(pred, rs2, order[:rows])
         cores = oracle.num_threads()
-        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu_model(),
                "sample": f"{rows} active rows (head of the sorted step list) x all {n} j, FP64 direct sum "
                          f"with neighbour lists, {dt:.1f} s"}
         rate1, dt1 = oracle_rate(pred, rs2, order[:16], threads=1)  # the same oracle on one core

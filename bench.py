@@ -225,6 +225,9 @@ def main():
     ap.add_argument("--variants", default="",
                     help="with --profile: comma list of kernel:variant:splits plans to time in turn "
                          "(e.g. 1:0:14,1:5:14); empty = the automatic plan")
+    ap.add_argument("--ac-plummer", action="store_true",
+                    help="only the mixed Ahmad-Cohen integration of the 65536-body Plummer sphere to t = 1/64 "
+                         "(the ac_integrator.mixed run); prints its JSON line")
     ap.add_argument("--ac-king", type=float, default=None, metavar="T_END",
                     help="only the Ahmad-Cohen integration of the million-body King cluster, from t = 0 to "
                          "T_END (steps at most min(T_END, 1/64)); prints its JSON line")
@@ -233,6 +236,10 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile_case(args)
+    if args.ac_plummer:
+        import torch
+        print(json.dumps(bench_ac(torch.device("cuda", 0), precisions=("mixed",), reference=False)))
+        return
     if args.ac_king is not None:
         import torch
         dev = torch.device("cuda", 0)
@@ -671,7 +678,7 @@ def bench_scheduler(dev, cl, steps=512, parity_steps=16):
             "parity_with_reference_first_steps": parity, "parity_steps": parity_steps}
 
 
-def bench_ac(dev, n=65536, t_end=1.0 / 64):
+def bench_ac(dev, n=65536, t_end=1.0 / 64, precisions=("mixed", "fp64"), reference=True):
     """Ahmad-Cohen block-step integration on the device (nb_ac_*): Plummer N = 65536 with
     Kroupa masses, r_s adapted towards 50 neighbours (cap 256), eta_irr 0.02, eta_reg 0.03,
     from t = 0 to t_end, in a mixed and an FP64 context; wall time on the host clock, particle
@@ -688,7 +695,7 @@ def bench_ac(dev, n=65536, t_end=1.0 / 64):
     E0 = sum(oracle.energy(cl.m, cl.x, cl.v))
     res = {"workload": f"Plummer N={n} Kroupa, r_s towards 50 neighbours (cap 256), eta_irr 0.02, eta_reg 0.03, "
                        f"t = 0 .. {t_end} (= dt_max: every particle ends at t_end)"}
-    for prec in ("mixed", "fp64"):
+    for prec in precisions:
         ctx = Context(n, precision=prec, nb_cap=256, device=dev.index or 0)
         ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
         torch.cuda.synchronize()
@@ -704,6 +711,8 @@ def bench_ac(dev, n=65536, t_end=1.0 / 64):
                      "all_synchronised": bool(np.all(g["t"] == t_end)), "median_neighbours": float(np.median(g["nb_count"]))}
         ac.close()
         ctx.close()
+    if not reference:
+        return res
     t0 = time.perf_counter()
     ox, ov, _, info = oracle.ac_run(cl.m, cl.x, cl.v, rs2, t_end, cap=256, **kw)
     wall = time.perf_counter() - t0

@@ -251,8 +251,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         pack_state_one(i, D.x + 3 * i, D.v + 3 * i, D.a + 3 * i, D.jk + 3 * i, t, D.m[i], D.s64, D.s32);
     }
     // the last CTA to finish publishes the final histogram and the step's status flags to the
-    // host words (read after the scheduler's synchronisation) and clears the flags; one word
-    // per thread (the launch has 128 threads a CTA)
+    // host words (read after the scheduler's synchronisation) and clears the flags
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -260,9 +259,11 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
     __syncthreads();
     if (last) {
         __threadfence();
-        if (threadIdx.x < 64) D.io[threadIdx.x] = __ldcg(&D.lr_hist[threadIdx.x]);
-        if (threadIdx.x == 64) D.io[64] = (int32_t)atomicExch(status, 0u);
-        if (threadIdx.x == 65) atomicExch(&D.tickets[1], 0u);
+        for (int b = threadIdx.x; b < 64; b += blockDim.x) D.io[b] = __ldcg(&D.lr_hist[b]);
+        if (threadIdx.x == 0) {
+            D.io[64] = (int32_t)atomicExch(status, 0u);
+            atomicExch(&D.tickets[1], 0u);
+        }
     }
 }
 

@@ -2,7 +2,8 @@
 // is stated with the declarations in nbgpu.h).  One block step is a fixed sequence of
 // launches on the context stream:
 //   nb_sched_next (host)          -> block time t, active particles = list prefix
-//   k_ac_classify                 -> which active particles also take a regular step
+//   k_ac_classify                 -> which active particles also take a regular step (only
+//                                    when the regular-level histogram predicts some)
 //   with a regular subset:
 //     nb_predict(t)               -> all particles predicted, j-records built
 //     nb_regular_force (regular)  -> all-j sums and the new lists of the regular subset
@@ -171,7 +172,14 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = list[k];
-        const int32_t p = reg_pos[k];
+        // reg_pos == null: the host predicted no regular particle in this step and skipped the
+        // classify launch; a particle that is due for a regular step is then a device error
+        int32_t p = -1;
+        if (reg_pos) {
+            p = reg_pos[k];
+        } else if ((t_ticks & (((int64_t)1 << (kAcTick - D.LR[i])) - 1)) == 0) {
+            atomicOr(status, ST_DEVICE);
+        }
         atomicAdd(pairs, (unsigned long long)D.ell_cnt[i]);
         double a1[3], j1[3];
         int lr_old = -1;
@@ -524,8 +532,8 @@ nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const
 // waiting. The last CTA of the classify launch checks that size against the classified
 // count; the last CTA of the corrector writes the new histogram and the step's status flags
 // into mapped host words, which the scheduler's synchronisation makes visible. A step with no
-// regular particle is five launches (classify, irregular force, corrector, re-sort) and one
-// synchronisation.
+// regular particle is three launches (irregular force, corrector, re-sort: the corrector
+// then checks that no particle was due for a regular step) and one synchronisation.
 nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_regular)
 {
     if (!s) return NB_ERR_ARG;
@@ -543,9 +551,11 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     int64_t nr = 0;
     for (int b = lstar; b < 64; ++b) nr += s->h_lr[b];
     const int cap = cs.cap;
-    k_ac_classify<<<grid_of(na, 256, 152 * 16), 256, 0, st>>>(s->D, na, list, t_ticks, s->counter, s->reg_pos,
-                                                               s->reg_idx, s->reg_rs2, nr, cs.status + SS_FLAGS);
-    ACK(cudaGetLastError(), "classify launch");
+    if (nr > 0) {  // with no regular particle predicted the corrector makes the check itself
+        k_ac_classify<<<grid_of(na, 256, 152 * 16), 256, 0, st>>>(s->D, na, list, t_ticks, s->counter, s->reg_pos,
+                                                                   s->reg_idx, s->reg_rs2, nr, cs.status + SS_FLAGS);
+        ACK(cudaGetLastError(), "classify launch");
+    }
     if (nr > 0) {
         ANB(nb_predict(s->ctx, t), "nb_predict");
         ANB(nb_regular_force(s->ctx, nr, s->reg_idx, s->reg_rs2, 0, s->Fa, s->Ja, s->Pa, s->off, s->csr, nr * cap,
@@ -559,7 +569,8 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
         launch_irregular(st, cs.precision, cs.num_sms, s->srec, 0, cs.n, t, na, list, nullptr, s->D.ell, s->Fo,
                          s->Jo, s->Po, nullptr, nullptr, nullptr, cs.status, s->D.ell_cnt, cap);
     }
-    k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks, s->reg_pos, s->Fo, s->Jo,
+    k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks,
+                                                              nr > 0 ? s->reg_pos : nullptr, s->Fo, s->Jo,
                                                               s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
                                                               s->pairs, cs.status + SS_FLAGS);
     if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);

@@ -427,3 +427,22 @@ def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
     check_mixed(res, ref)
     check_lists_band(res, cl.x, idx, big, ref[3], ref[4], 16)
     ctx.close()
+
+
+def test_mixed_far_from_the_origin(gpu_lib):
+    """The cluster translated by (1e4, -2e4, 3e3) length units (a star cluster far from the
+    coordinate origin): forces do not change, but single-precision coordinates would lose about
+    four digits of every separation there. The double-single differences keep the mixed path
+    within its bars against the oracle of the shifted state, with the same neighbour lists."""
+    cl = W.plummer(4096, 77, masses="kroupa")
+    rs2 = float(W.neighbour_radius2(cl.x, 50, seed=77))
+    x = cl.x + np.array([1.0e4, -2.0e4, 3.0e3])
+    idx = np.arange(0, 4096, 3, dtype=np.int32)
+    ref = oracle.regular_force(x, cl.v, cl.m, idx, rs2, cap=512)
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(T(x), T(cl.v), T(cl.m))
+    res = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    check_mixed(res, ref)
+    check_lists_band(res, x, idx, rs2, ref[3], ref[4], 512)
+    ctx.close()

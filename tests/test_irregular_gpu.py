@@ -194,3 +194,34 @@ def test_fp64_forms_agree_bit_for_bit(gpu_lib, setup):
                 e = d / sref
                 assert np.median(e) <= 2e-6 and e.max() <= 1e-4
         ctx.close()
+
+
+@pytest.mark.parametrize("n_i", [64, 4096])
+def test_mixed_late_time_far_from_the_origin(gpu_lib, n_i):
+    """Mixed irregular force of a cluster translated by (1e4, -2e4, 3e3) at block time
+    t = 4096 + 37/2^14 with steps of 2^-12 .. 2^-16: both the base differences of the positions
+    and t - t_last (formed from hi/lo halves of both times) would lose most of their digits in
+    single precision; in double-single the rows stay within the mixed bars. Both forms: the
+    neighbour-only one (64 rows) and predict-all (4096 rows: 4096 x 8 >= N)."""
+    from paper_1504_03687_gb300 import Context
+    n = 6000
+    cl = W.plummer(n, 91, masses="kroupa")
+    x = cl.x + np.array([1.0e4, -2.0e4, 3.0e3])
+    rng = np.random.default_rng(91)
+    t = 4096.0 + 37.0 / 2 ** 14
+    dt = 2.0 ** -rng.integers(12, 17, n)
+    tl = t - dt * rng.integers(0, 2, n)
+    a0 = rng.standard_normal((n, 3))
+    j0 = 10.0 * rng.standard_normal((n, 3))
+    xp, vp = oracle.predict(t, x, cl.v, a0, j0, tl)
+    rs2 = float(W.neighbour_radius2(xp, 50, seed=91))
+    idx = np.sort(rng.choice(n, n_i, replace=False)).astype(np.int32)
+    _, _, _, cnt, lists = oracle.regular_force(xp, vp, cl.m, idx, rs2, cap=256)
+    off, flat = csr(lists)
+    ref = oracle.irregular_force(t, x, cl.v, a0, j0, tl, cl.m, idx, off, flat)
+    ctx = Context(n, precision="mixed", nb_cap=256)
+    ctx.set_particles(*[T(q) for q in (x, cl.v, a0, j0, cl.m, tl)])
+    got = ctx.irregular_force(t, T(idx), T(off), T(flat) if flat.size else T(np.zeros(1, np.int32)))
+    ctx.sync()
+    check("mixed", got, ref, list_term_sums(xp, vp, cl.m, idx, lists), cnt > 0)
+    ctx.close()

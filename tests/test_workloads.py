@@ -93,3 +93,34 @@ def test_ensemble_layout():
         act = e.idx[e.active_off[c]:e.active_off[c + 1]]
         assert act.min() >= lo and act.max() < hi
         assert 256 <= hi - lo <= 32768
+
+
+def _ks(sample, cdf):
+    s = np.sort(sample)
+    n = s.size
+    f = cdf(s)
+    return max(np.max(np.arange(1, n + 1) / n - f), np.max(f - np.arange(n) / n))
+
+
+def test_plummer_sampler_follows_its_distribution_function():
+    """Raw Plummer samples (before the centre-of-mass shift): radii against the truncated
+    cumulative mass M(r)/x_max (Kolmogorov-Smirnov at the 99.9 % level), every speed below the
+    local escape speed, q = v/v_esc against the normalised isotropic distribution
+    q^2 (1 - q^2)^(7/2), and isotropic directions of positions and velocities."""
+    n, a, x_max = 200000, W.PLUMMER_A_NBODY, 0.999
+    pos, vel = W.plummer_positions_velocities(n, np.random.default_rng(12), a=a, x_max=x_max)
+    r = np.sqrt((pos ** 2).sum(1))
+    crit = 1.95 / math.sqrt(n)
+    assert _ks(r, lambda s: W.plummer_enclosed_mass(s, a) / x_max) < crit
+    v = np.sqrt((vel ** 2).sum(1))
+    v_esc = math.sqrt(2.0) * (1.0 + r * r / (a * a)) ** (-0.25) / math.sqrt(a)
+    q = v / v_esc
+    assert q.max() < 1.0 and q.min() >= 0.0
+    grid = np.linspace(0.0, 1.0, 20001)
+    dens = grid ** 2 * (1.0 - grid ** 2) ** 3.5
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(grid))])
+    cum /= cum[-1]
+    assert _ks(q, lambda s: np.interp(s, grid, cum)) < crit
+    for u in (pos / r[:, None], vel / v[:, None]):
+        assert np.abs(u.mean(0)).max() < 5.0 / math.sqrt(n)
+        assert np.abs((u ** 2).mean(0) - 1.0 / 3.0).max() < 5.0 / math.sqrt(n)

@@ -1,4 +1,4 @@
-"""Multi-rank host logic on CPU (gloo, world size 2): the copy-algorithm row sharding and the
+"""Multi-rank host logic on CPU (gloo, world sizes 2 and 3): the copy-algorithm row sharding and the
 result exchange reproduce the single-rank result exactly.  Each rank computes its share of
 the active rows with the FP64 oracle (the GPU path is exercised on one GPU elsewhere)."""
 import os
@@ -53,11 +53,12 @@ def _worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_copy_algorithm_exchange_matches_single_rank():
+@pytest.mark.parametrize("world", [2, 3])
+def test_copy_algorithm_exchange_matches_single_rank(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for pr in procs:
         pr.start()
     got = q.get(timeout=120)
@@ -144,11 +145,12 @@ def _source_worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_source_sharded_exchange_matches_single_rank():
+@pytest.mark.parametrize("world", [2, 3])  # 3 ranks: source shards of 256, 256 and 512 particles
+def test_source_sharded_exchange_matches_single_rank(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_source_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_source_worker, args=(r, world, port, q)) for r in range(world)]
     for pr in procs:
         pr.start()
     got = q.get(timeout=120)

@@ -357,7 +357,9 @@ const char *nb_sched_last_error(const nb_sched *s);
  * target neighbour number, App. A).  The paper prints no formulas; the scheme, step for
  * step:
  *  - block step: the scheduler above selects the particles whose irregular step ends at
- *    the new block time t; all particles are predicted to t (nb_predict);
+ *    the new block time t; when some of them also end a regular step, all particles are
+ *    predicted to t (nb_predict), otherwise only the active particles and their neighbours,
+ *    on load (the neighbour-only prediction of Sec. 3.3.3);
  *  - every active particle gets the irregular force over its current list; one whose
  *    regular step also ends at t gets the all-j sums (nb_regular_force, which also yields
  *    its new list) and the irregular force over the new list;
@@ -387,7 +389,8 @@ typedef struct nb_ac nb_ac;
 
 /* Start an integration of n particles (masses m, positions x, velocities v (n,3) at t = 0,
  * squared neighbour radii rs2 (n); host or device pointers) on the context ctx (n <= its
- * n_max; the context's particle state is taken over and evolved by the integrator). */
+ * n_max; the context's particle state is taken over and evolved in place by the integrator:
+ * load no other state into the context while the integrator lives). */
 nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v,
                      const double *rs2, const nb_ac_params *params, int32_t on_device);
 

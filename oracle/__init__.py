@@ -239,11 +239,14 @@ def ac_run(m, x, v, rs2, t_end, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0
            cap=256, max_blocks=0):
     """Ahmad-Cohen Hermite block-step run (see orc_ac_run).  Returns (x, v, rs2, info) with
     info = dict(t, dt, DT, T, nb_count, nb_lists, blocks, irregular_steps, regular_steps,
-    neighbour_pairs, all_pairs, rc)."""
+    neighbour_pairs, all_pairs, rc, acc, jerk, xp, vp): acc and jerk are the total force and its
+    derivative each particle holds after its last step, xp and vp the predicted state of the
+    last block step (the state those were evaluated on when the end time synchronises all)."""
     lib = _load()
     if not hasattr(lib, "_ac"):
         P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-        lib.orc_ac_run.argtypes = [i64, P, P, P, P, dbl, dbl, dbl, dbl, dbl, i32, i32, i64, P, P, P, P, P, P, P]
+        lib.orc_ac_run.argtypes = [i64, P, P, P, P, dbl, dbl, dbl, dbl, dbl, i32, i32, i64, P, P, P, P, P, P, P,
+                                   P, P, P, P]
         lib.orc_ac_run.restype = ctypes.c_int
         lib._ac = True
     m = _c(m, np.float64)
@@ -254,12 +257,13 @@ def ac_run(m, x, v, rs2, t_end, eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=0
     t, dt, DT, T = (np.zeros(n) for _ in range(4))
     nbc = np.zeros(n, np.int32)
     nbl = np.zeros((n, cap), np.int32)
+    acc, jerk, xp, vp = (np.zeros((n, 3)) for _ in range(4))
     rc = lib.orc_ac_run(n, _p(m), _p(x), _p(v), _p(rs2), float(t_end), float(eta_irr), float(eta_reg), float(eta_s),
                         float(dt_max), int(nb_opt), int(cap), int(max_blocks), _p(stats), _p(t), _p(dt), _p(DT),
-                        _p(T), _p(nbc), _p(nbl))
+                        _p(T), _p(nbc), _p(nbl), _p(acc), _p(jerk), _p(xp), _p(vp))
     info = dict(t=t, dt=dt, DT=DT, T=T, nb_count=nbc, nb_lists=[nbl[i, :nbc[i]].copy() for i in range(n)],
                 blocks=int(stats[0]), irregular_steps=int(stats[1]), regular_steps=int(stats[2]),
-                neighbour_pairs=stats[3], all_pairs=stats[4], rc=rc)
+                neighbour_pairs=stats[3], all_pairs=stats[4], rc=rc, acc=acc, jerk=jerk, xp=xp, vp=vp)
     return x, v, rs2, info
 
 

@@ -541,7 +541,10 @@ int orc_irregular_force(int64_t n, const double *x, const double *v, const doubl
  * With r_s covering every particle and nb_opt <= 0 the regular force is exactly zero and
  * this reduces to hermite_core.
  * rs2 (n) is used and updated in place.  Optional outputs (n entries, or n*cap for the
- * lists): t_i, dt_i, DT_i, T_i, list lengths and lists.  stats (6 doubles): block steps,
+ * lists): t_i, dt_i, DT_i, T_i, list lengths and lists; (n,3) each: the total acceleration and
+ * jerk each particle holds after its last step (a1, j1 of that step), and the predicted state of
+ * the last block step (the state those forces were evaluated on, for the particles of that
+ * block; a synchronised end time makes it every particle).  stats (6 doubles): block steps,
  * irregular particle steps, regular particle steps, neighbour pair evaluations, all-j pair
  * evaluations, 0.  Returns 0, or -2 when max_blocks was reached. */
 static void ac_list_sum(int64_t i, const int32_t *list, int32_t cnt, const double *xp, const double *vp,
@@ -598,7 +601,7 @@ static double ac_criterion(double eta, const double *a, const double *j, const d
 int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, double t_end, double eta_irr,
                double eta_reg, double eta_s, double dt_max, int32_t nb_opt, int32_t cap, int64_t max_blocks,
                double *stats, double *t_out, double *dt_out, double *DT_out, double *T_out, int32_t *nbc_out,
-               int32_t *nbl_out)
+               int32_t *nbl_out, double *a_out, double *j_out, double *xp_out, double *vp_out)
 {
     double *a = malloc(3 * n * sizeof(double)), *jk = malloc(3 * n * sizeof(double));
     double *xp = malloc(3 * n * sizeof(double)), *vp = malloc(3 * n * sizeof(double));
@@ -738,6 +741,10 @@ int orc_ac_run(int64_t n, const double *m, double *x, double *v, double *rs2, do
         if (nbc_out) nbc_out[i] = nbc[i];
     }
     if (nbl_out) memcpy(nbl_out, nbl, (size_t)n * cap * sizeof(int32_t));
+    if (a_out) memcpy(a_out, a, 3 * (size_t)n * sizeof(double));
+    if (j_out) memcpy(j_out, jk, 3 * (size_t)n * sizeof(double));
+    if (xp_out) memcpy(xp_out, xp, 3 * (size_t)n * sizeof(double));
+    if (vp_out) memcpy(vp_out, vp, 3 * (size_t)n * sizeof(double));
     free(a); free(jk); free(xp); free(vp); free(t); free(dt); free(T); free(DT); free(Fr); free(Jr);
     free(D2); free(D3); free(a1); free(j1); free(pot); free(nbl); free(nbc); free(act); free(newl); free(regk);
     return rc;

@@ -538,3 +538,56 @@ def test_ac_energy_conservation_and_regular_step_convergence():
             assert info["regular_steps"] < 0.25 * info["irregular_steps"]
             assert 40 <= np.median(info["nb_count"]) <= 62
     assert errs[0] < 1e-5 and errs[1] < errs[0] / 4, errs
+
+
+def _two_circular_binaries(d=1.0, a=0.1):
+    """Two equal-mass circular binaries (total mass 1/2 each, separation a) on a circular
+    mutual orbit of separation d, with inclined orbital planes: each member's only neighbour
+    is its partner, and the regular force on it (from the other binary) is smooth in time."""
+    def rot(axis, ang):
+        u = np.asarray(axis, float) / np.linalg.norm(axis)
+        K = np.array([[0, -u[2], u[1]], [u[2], 0, -u[0]], [-u[1], u[0], 0]])
+        return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+    def binary(R):
+        w = np.sqrt(0.5 / a)
+        return (np.array([[a / 2, 0, 0], [-a / 2, 0, 0]]) @ R.T,
+                np.array([[0, w / 2, 0], [0, -w / 2, 0]]) @ R.T)
+    xa, va = binary(rot([1, 0.3, 0.2], 0.4))
+    xb, vb = binary(rot([0.2, 1, 0.5], 1.1))
+    w = np.sqrt(1.0 / d)
+    x = np.concatenate([xa + [d / 2, 0, 0], xb - [d / 2, 0, 0]])
+    v = np.concatenate([va + [0, w / 2, 0], vb - [0, w / 2, 0]])
+    return np.full(4, 0.25), x, v
+
+
+def test_ac_regular_force_extrapolation_order():
+    """Between regular steps the integrator extrapolates the regular force to third order in
+    tau = t - T_i from its value, derivative and the second and third derivatives of the last
+    Hermite interpolation (the Ahmad-Cohen scheme, Sec. 2).  Its error is therefore O(DT^4) in
+    the force and O(DT^3) in the jerk when tau is a fixed fraction of the regular step DT.
+    Measured directly: the regular step is forced to DT = 2^-k (dt_max, infinite eta_reg),
+    the irregular steps are much smaller, and the run ends at t = 1/2 + DT/2, half a regular
+    step after the last regular time 1/2; the total force and jerk the integrator holds there
+    are compared with the all-j sums over the very predicted state they were evaluated on (the
+    list part is exact, so the difference is the extrapolation error alone).  Halving DT must
+    cut the force error 16-fold and the jerk error 8-fold: a dropped or mis-scaled third-
+    derivative term leaves 8 and 4, a wrong second-derivative term 4 and 2."""
+    m, x, v = _two_circular_binaries()
+    idx = np.arange(4, dtype=np.int32)
+    eF, eJ = [], []
+    for k in range(6, 10):
+        H = 2.0 ** -k
+        _, _, _, info = oracle.ac_run(m, x, v, 0.3 ** 2, 0.5 + H / 2, eta_irr=2.5e-4, eta_reg=1e30, eta_s=1e-3,
+                                      dt_max=H, cap=8, nb_opt=0)
+        assert info["rc"] == 0 and list(info["nb_count"]) == [1, 1, 1, 1]
+        assert np.all(info["t"] == 0.5 + H / 2) and np.all(info["T"] == 0.5) and np.all(info["DT"] == H)
+        assert np.all(info["dt"] <= H / 4)
+        a, j, _, _, _ = oracle.regular_force(info["xp"], info["vp"], m, idx, 0.3 ** 2, cap=8)
+        eF.append(np.abs(info["acc"] - a).max() / np.abs(a).max())
+        eJ.append(np.abs(info["jerk"] - j).max() / np.abs(j).max())
+    rF = [eF[q] / eF[q + 1] for q in range(3)]
+    rJ = [eJ[q] / eJ[q + 1] for q in range(3)]
+    assert all(13.0 < r < 20.0 for r in rF), (eF, rF)
+    assert all(6.5 < r < 10.0 for r in rJ), (eJ, rJ)
+    assert 1e-9 < eF[0] < 1e-5 and 1e-8 < eJ[0] < 1e-4, (eF, eJ)

@@ -447,7 +447,8 @@ def main():
                        "nb_cap": NB_CAP, "rs2": rs2, "precision": "mixed (ds-f32 differences, f32 pairwise, "
                        "f64 predictor and per-tile sums)", "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"{world} independent clusters, one per GPU",
-                       "launch_plans": "autotuned table" if tuned else "automatic planner"},
+                       "launch_plans": "autotuned table" if tuned else "automatic planner",
+                       "accuracy": accuracy_summary(extra)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": force_traffic_per_launch(),
                          "traffic_per_block": (dict(zip(map(str, BLOCKS), FORCE_TRAFFIC["bytes_per_launch"]))
@@ -465,6 +466,23 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def accuracy_summary(extra):
+    """The stated-error and FP64-comparison figures in compact form ([median, max] relative error
+    per particle against the FP64 oracle; mixed over FP64 force-kernel rate on the same block),
+    kept inside the contract line's config."""
+    out = {}
+    for key, name in (("error_vs_oracle_mixed", "mixed_vs_oracle_64_rows_of_2^20_block"),
+                      ("error_vs_oracle_fp64", "fp64_vs_oracle_32_rows_of_2^14_block")):
+        if key in extra:
+            out[name] = {q: [float(f"{v['median']:.3g}"), float(f"{v['max']:.3g}")] for q, v in extra[key].items()}
+    if "fp64_path" in extra:
+        f = extra["fp64_path"]
+        out["fp64_Ginteractions_s_2^14_block"] = round(f["force_kernel_Ginteractions_s"], 2)
+        out["mixed_Ginteractions_s_2^14_block"] = round(f["mixed_force_kernel_Ginteractions_s_same_block"], 1)
+        out["mixed_over_fp64"] = round(f["mixed_over_fp64"], 1)
+    return out
 
 
 def run_profile_case(args):

@@ -148,7 +148,11 @@ nb_status nb_set_source_range(nb_ctx *ctx, int64_t j_lo, int64_t j_hi);
  * obtained by differentiating the sums above).  For
  *   L = sum_k g_acc[k].acc_k + g_jerk[k].jerk_k + g_pot[k] pot_k
  * it writes g_x = dL/dx_p, g_v = dL/dv_p (n,3) and g_m = dL/dm (n), overwriting them.
- * Uses the state of the last nb_predict / nb_set_predicted. */
+ * Uses the state of the last nb_predict / nb_set_predicted.  idx: (n_i) int32, unique, each
+ * in [0, n); g_acc, g_jerk (n_i,3) and g_pot (n_i) are the cotangents of row k = idx[k].  An
+ * index outside [0, n) or named twice makes the call fail with NB_ERR_ARG (returned by this
+ * call when on_device = 0, by the next nb_sync when on_device = 1), its outputs unspecified;
+ * with unique indices every sum has a fixed order and runs are bitwise reproducible. */
 nb_status nb_regular_force_backward(nb_ctx *ctx, int64_t n_i, const int32_t *idx,
                                     const double *g_acc, const double *g_jerk,
                                     const double *g_pot, double *g_x, double *g_v, double *g_m,
@@ -281,7 +285,10 @@ nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_pe
  * library (every GPU that loads the library holds it until the process exits).  n_i above
  * 65536 is rejected with NB_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array: calls that overlap on the GPU (on
+ * any stream capture.  A lookup that fails returns NB_ERR_CUDA and is tried again by the
+ * next call; once it has succeeded the address is kept.  A CUDA error already pending on
+ * the calling thread (left by earlier, unrelated work) makes the call return NB_ERR_CUDA
+ * without running anything and without clearing that error.  All calls share the one array: calls that overlap on the GPU (on
  * different streams, or from different host threads without ordering) race and corrupt
  * each other's results.  Every scratch element a call reads is written earlier in the same
  * call, so no clearing is needed between calls. */

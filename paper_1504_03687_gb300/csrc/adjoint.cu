@@ -403,6 +403,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_jside_x2(AdjArgs A)
 // R = gj_m.w and E = P + R - 5 q Q / |r|^2 the reversed pair reads
 //   V = ga_m - (s_m + 3 E / |r|^2) r - 3 Q w / |r|^2 + gamma gj_m,  U = gj_m - 3 Q r / |r|^2,
 //   D = -|r|^-3 (P + R + gamma Q) - s_m / |r|,  gamma = -3 q / |r|^2.
+// Every active index must appear once: each row's cotangents are written into its particle's
+// record, and the i-side sums are added into g_x, g_v of that particle.  claim (n words) is
+// zero on entry; a second claim of the same particle flags ST_DUP_INDEX (the call then fails
+// with NB_ERR_ARG and its outputs are unspecified).
+__global__ void k_check_unique(int64_t n, int64_t n_i, const int32_t *__restrict__ idx, unsigned *__restrict__ claim,
+                               unsigned *status)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_i; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[q];
+        if (i < 0 || i >= n) continue;  // reported by the kernels that use the row
+        if (atomicExch(claim + i, 1u) != 0u) atomicOr(status, ST_DUP_INDEX);
+    }
+}
+
 __global__ void k_build_crec(int64_t n, int64_t n_pad, const float4 *__restrict__ rec, float4 *__restrict__ crec)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_pad; k += (int64_t)gridDim.x * blockDim.x) {
@@ -430,14 +444,15 @@ __global__ void k_scatter_cotangents(int64_t n, int64_t n_i, const int32_t *__re
             atomicOr(status, ST_BAD_INDEX);
             continue;
         }
+        // idx is checked for duplicates first (k_check_unique), so one row writes each record
         float *r = crec + 20 * i;  // five float4 = 20 floats
-        atomicAdd(r + 7, (float)g_pot[q]);         // s
-        atomicAdd(r + 11, (float)g_jerk[3 * q]);   // gj0
-        atomicAdd(r + 12, (float)g_acc[3 * q]);    // ga0
-        atomicAdd(r + 13, (float)g_acc[3 * q + 1]);
-        atomicAdd(r + 14, (float)g_acc[3 * q + 2]);
-        atomicAdd(r + 15, (float)g_jerk[3 * q + 1]);  // gj1
-        atomicAdd(r + 16, (float)g_jerk[3 * q + 2]);  // gj2
+        r[7] = (float)g_pot[q];         // s
+        r[11] = (float)g_jerk[3 * q];   // gj0
+        r[12] = (float)g_acc[3 * q];    // ga0
+        r[13] = (float)g_acc[3 * q + 1];
+        r[14] = (float)g_acc[3 * q + 2];
+        r[15] = (float)g_jerk[3 * q + 1];  // gj1
+        r[16] = (float)g_jerk[3 * q + 2];  // gj2
     }
 }
 
@@ -630,14 +645,14 @@ __global__ void k_scatter_cotangents64(int64_t n, int64_t n_i, const int32_t *__
             atomicOr(status, ST_BAD_INDEX);
             continue;
         }
-        double *r = crec + 16 * i;  // four dvec4 = 16 doubles
-        atomicAdd(r + 7, g_pot[q]);       // s
-        atomicAdd(r + 8, g_acc[3 * q]);   // ga
-        atomicAdd(r + 9, g_acc[3 * q + 1]);
-        atomicAdd(r + 10, g_acc[3 * q + 2]);
-        atomicAdd(r + 11, g_jerk[3 * q]);  // gj
-        atomicAdd(r + 12, g_jerk[3 * q + 1]);
-        atomicAdd(r + 13, g_jerk[3 * q + 2]);
+        double *r = crec + 16 * i;  // four dvec4 = 16 doubles; one row writes each record
+        r[7] = g_pot[q];       // s
+        r[8] = g_acc[3 * q];   // ga
+        r[9] = g_acc[3 * q + 1];
+        r[10] = g_acc[3 * q + 2];
+        r[11] = g_jerk[3 * q];  // gj
+        r[12] = g_jerk[3 * q + 1];
+        r[13] = g_jerk[3 * q + 2];
     }
 }
 
@@ -949,6 +964,14 @@ static AdjGeom adj_geom(int precision, int64_t n, int64_t n_i, int num_sms)
     return g;
 }
 
+// Bytes of the pass scratch (records and partial sums); the duplicate check's n claim words
+// follow at the next 256-byte boundary.
+static size_t adjoint_core_bytes(int precision, int64_t n, int64_t n_i, int num_sms);
+static size_t claim_offset(int precision, int64_t n, int64_t n_i, int num_sms)
+{
+    return (adjoint_core_bytes(precision, n, n_i, num_sms) + 255) & ~(size_t)255;
+}
+
 size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms, int64_t *rows_pad_out, int *SA,
                              int *SB)
 {
@@ -956,6 +979,12 @@ size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms,
     *rows_pad_out = g.rows_pad;
     *SA = g.SA;
     *SB = g.SB;
+    return claim_offset(precision, n, n_i, num_sms) + (size_t)n * sizeof(unsigned);
+}
+
+static size_t adjoint_core_bytes(int precision, int64_t n, int64_t n_i, int num_sms)
+{
+    const AdjGeom g = adj_geom(precision, n, n_i, num_sms);
     const size_t irec = (size_t)g.rows_pad * (precision == 1 ? 64 : 128);
     const size_t pa = (size_t)g.SA * 6 * (size_t)n_i * 8, pb = (size_t)g.SB * 7 * (size_t)n * 8;
     size_t need = irec + 256 + pa + 256 + pb;
@@ -971,6 +1000,15 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
                    const double *g_acc, const double *g_jerk, const double *g_pot, double *g_x, double *g_v,
                    double *g_m, void *scratch, unsigned *status, int num_sms)
 {
+    {
+        unsigned *claim = reinterpret_cast<unsigned *>(static_cast<char *>(scratch) +
+                                                       claim_offset(precision, n, n_i, num_sms));
+        cudaMemsetAsync(claim, 0, (size_t)n * sizeof(unsigned), st);
+        int64_t gq = (n_i + 255) / 256;
+        if (gq > 152 * 8) gq = 152 * 8;
+        if (gq < 1) gq = 1;
+        k_check_unique<<<(unsigned)gq, 256, 0, st>>>(n, n_i, idx, claim, status);
+    }
     if (use_fused(precision, n, n_i)) {  // dense block: one fused pass over all pairs
         const FusedGeom f = fused_geom(precision, n, num_sms);
         double *part = reinterpret_cast<double *>(static_cast<char *>(scratch) +
@@ -1005,7 +1043,7 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
         int64_t gj = (n + 255) / 256;
         if (gj > 152 * 16) gj = 152 * 16;
         k_adj_combine_j<<<(unsigned)gj, 256, 0, st>>>(part, f.S, n, g_x, g_v, g_m);
-        return 4;
+        return 5;
     }
     const AdjGeom g = adj_geom(precision, n, n_i, num_sms);
     char *p = static_cast<char *>(scratch);
@@ -1025,7 +1063,7 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
     A.g_jerk = g_jerk;
     A.g_pot = g_pot;
     A.status = status;
-    int kernels = 0;
+    int kernels = 1;  // k_check_unique
     {
         int64_t gr = (g.rows_pad + 255) / 256;
         if (gr > 152 * 8) gr = 152 * 8;

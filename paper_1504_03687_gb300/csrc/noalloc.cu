@@ -13,6 +13,11 @@
 // n sources for a batch of up to IB active rows; every warp walks 32 consecutive sources
 // per step) reading the caller's FP64 arrays directly, followed by the fixed-order
 // reduction of the partial sums.  Neighbour lists are not produced here.
+// Layout: the caller's arrays are interleaved row-major (n,3) positions and velocities and
+// (n) masses, read as they are (no repacking, which would need scratch): lane j loads the
+// three components of particle j at a 24-byte stride, so a warp's loads of one component
+// touch 768 contiguous bytes shared by the three component loads (about 3x the sectors of
+// a component-major layout per instruction; the kernel is FP64-pipe bound, not load bound).
 #include <mutex>
 
 #include "nbgpu.h"
@@ -28,14 +33,14 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[kNoallocDoubles];
 
-// Device address of g_noalloc_partials, looked up once per device with that device current.
+// Device address of g_noalloc_partials per device, looked up with that device current and
+// kept once the lookup has succeeded (a failed lookup is retried by the next call).
 static double *g_scratch_ptr[kNoallocMaxDevices];
-static cudaError_t g_scratch_err[kNoallocMaxDevices];
-static std::once_flag g_scratch_once[kNoallocMaxDevices];
+static std::mutex g_scratch_mutex;
 
 template <int IB, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-    k_force_fp64_soa_jstream(int64_t n, const double *__restrict__ xp, const double *__restrict__ vp,
+    k_force_fp64_aos_jstream(int64_t n, const double *__restrict__ xp, const double *__restrict__ vp,
                              const double *__restrict__ m, const int32_t *__restrict__ idx, int64_t n_i, int S,
                              double *__restrict__ part)
 {
@@ -141,23 +146,36 @@ extern "C" nb_status nb_regular_force_noalloc(int64_t n, const double *xp, const
         set_msg(err, err_len, "nb_regular_force_noalloc: null array");
         return NB_ERR_ARG;
     }
+    // an error left pending by earlier work on this thread is reported as such and left in
+    // place for its owner (cudaGetLastError below must only see this call's launches)
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        set_msg(err, err_len, "nb_regular_force_noalloc: a CUDA error was pending before the call (nothing run)");
+        return NB_ERR_CUDA;
+    }
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
         set_msg(err, err_len, "nb_regular_force_noalloc: no usable current CUDA device");
         return NB_ERR_CUDA;
     }
-    // one-time set-up on this device (the device is current): the scratch array's address
-    std::call_once(g_scratch_once[dev], [dev]() {
-        void *p = nullptr;
-        g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        g_scratch_ptr[dev] = g_scratch_err[dev] == cudaSuccess ? static_cast<double *>(p) : nullptr;
-    });
-    if (g_scratch_err[dev] != cudaSuccess || !g_scratch_ptr[dev]) {
-        set_msg(err, err_len, "nb_regular_force_noalloc: cudaGetSymbolAddress of the scratch array failed");
-        return NB_ERR_CUDA;
+    // set-up on this device (the device is current): the scratch array's address, looked up
+    // by the first call that succeeds in doing so and kept from then on
+    double *part = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();  // clear the lookup's own error; the next call retries
+                set_msg(err, err_len, "nb_regular_force_noalloc: cudaGetSymbolAddress of the scratch array failed");
+                return NB_ERR_CUDA;
+            }
+            g_scratch_ptr[dev] = static_cast<double *>(p);
+        }
+        part = g_scratch_ptr[dev];
     }
-    double *part = g_scratch_ptr[dev];
     int sms = 152;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
     constexpr int IB = 4, BLOCK = 256;
@@ -171,7 +189,7 @@ extern "C" nb_status nb_regular_force_noalloc(int64_t n, const double *xp, const
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // every partial slot the reduction reads is written by this launch: nothing in the
     // shared scratch has to start at zero
-    k_force_fp64_soa_jstream<IB, BLOCK><<<dim3((unsigned)batches, (unsigned)S), BLOCK, 0, st>>>(
+    k_force_fp64_aos_jstream<IB, BLOCK><<<dim3((unsigned)batches, (unsigned)S), BLOCK, 0, st>>>(
         n, xp, vp, m, idx, n_i, (int)S, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

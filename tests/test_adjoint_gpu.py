@@ -42,6 +42,33 @@ def gpu_vjp(ctx, cl, idx, ga, gj, gp):
     return gx.cpu().numpy(), gv.cpu().numpy(), gm.cpu().numpy()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,n_i", [(1000, 900), (1000, 137)])  # the fused pass and the two passes
+def test_backward_rejects_duplicate_indices_and_is_reproducible(gpu_lib, prec, n, n_i):
+    """Each active row writes its cotangents into its particle's record, so an index named
+    twice is an argument error (reported, never summed in a racing order); with unique
+    indices two calls give bit-identical gradients."""
+    from paper_1504_03687_gb300 import api
+    cl = W.plummer(n, 60, masses="kroupa")
+    rng = np.random.default_rng(n_i)
+    idx = rng.permutation(n)[:n_i].astype(np.int32)
+    ga, gj, gp = rng.standard_normal((n_i, 3)), rng.standard_normal((n_i, 3)), rng.standard_normal(n_i)
+    ctx = make_ctx(n, prec)
+    a = gpu_vjp(ctx, cl, idx, ga, gj, gp)
+    b = gpu_vjp(ctx, cl, idx, ga, gj, gp)
+    for q in range(3):
+        assert np.array_equal(a[q], b[q])
+    dup = idx.copy()
+    dup[n_i // 2] = dup[1]
+    with pytest.raises(api.NBError, match="more than once"):
+        gpu_vjp(ctx, cl, dup, ga, gj, gp)
+    # the context stays usable and the next call is correct again
+    c = gpu_vjp(ctx, cl, idx, ga, gj, gp)
+    for q in range(3):
+        assert np.array_equal(a[q], c[q])
+    ctx.close()
+
+
 @pytest.mark.parametrize("n,n_i", [(512, 512), (1000, 137), (3000, 1), (3000, 33), (4099, 2050), (2048, 1800),
                                    (3001, 3001)])
 def test_backward_matches_oracle_vjp(gpu_lib, n, n_i):

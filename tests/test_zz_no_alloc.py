@@ -2,11 +2,14 @@
 allocate device memory while they integrate (a host code whose own memory manager owns
 the device, or a step loop that must not reach cudaMalloc/cudaFree).
 
-It is called here through the C ABI (ctypes) and compared with the context-based
-nb_regular_force (FP64) on the same inputs, with the FP64 parity bar of the other GPU
-tests (1e-12 relative per row).  Two calls in a row on different inputs check that the
-shared scratch array carries nothing stale from one call into the next.  This file is
-named so that pytest collects it last.
+It is called here through the C ABI (ctypes) and compared with the FP64 oracle directly and
+with the context-based nb_regular_force (FP64) on the same inputs, with the FP64 parity bar
+of the other GPU tests (1e-12 relative per row).  Two calls in a row on different inputs
+check that the shared scratch array carries nothing stale from one call into the next.  The
+cases reach every launch shape the entry point has: a few splits (small n), many splits
+over a handful of rows (the wide reduction), one split at the 65536-row limit (the scratch
+bound), and rows whose index is outside [0, n) (zeros).  This file is named so that pytest
+collects it last.
 """
 import ctypes
 
@@ -55,6 +58,12 @@ def assert_rows_close(got, ref, tol=1e-12):
     assert np.all(d <= tol * np.maximum(s, 1e-3 * s.max())), float((d / s).max())
 
 
+def oracle_rows(cl, idx):
+    import oracle
+    a, j, p, _, _ = oracle.regular_force(cl.x, cl.v, cl.m, idx, 0.0, cap=1, lists=False)
+    return a, j, p
+
+
 def test_noalloc_matches_regular_force_on_two_calls_in_a_row():
     from paper_1504_03687_gb300 import api
     lib = api.load_library()
@@ -67,8 +76,47 @@ def test_noalloc_matches_regular_force_on_two_calls_in_a_row():
     torch.cuda.synchronize()
     for (c, i), got in zip(cases, outs):
         ref = with_context(c, i)
-        for g, r in zip(got, ref):
+        orc = oracle_rows(c, i)
+        for g, r, o in zip(got, ref, orc):
             assert_rows_close(g.cpu().numpy(), r)
+            assert_rows_close(g.cpu().numpy(), o)
+
+
+def test_noalloc_many_splits_and_the_row_limit():
+    """n = 65536: 8 rows (64 source splits, the wide fixed-order reduction) and then all
+    65536 rows (the 4 MiB scratch allows one split), back to back; against the context path
+    on every row and the oracle on sampled rows."""
+    from paper_1504_03687_gb300 import api
+    lib = api.load_library()
+    cl = W.plummer(65536, 73, masses="kroupa")
+    few = np.random.default_rng(3).permutation(cl.n)[:8].astype(np.int32)
+    full = np.random.default_rng(4).permutation(cl.n).astype(np.int32)
+    xd, vd, md = T(cl.x), T(cl.v), T(cl.m)
+    out_few = noalloc(lib, xd, vd, md, T(few))
+    out_full = noalloc(lib, xd, vd, md, T(full))
+    torch.cuda.synchronize()
+    sel = np.sort(np.random.default_rng(5).choice(cl.n, 48, replace=False))
+    for rows, got, sub in ((few, out_few, np.arange(8)), (full, out_full, sel)):
+        ref = with_context(cl, rows)
+        orc = oracle_rows(cl, rows[sub])
+        for g, r, o in zip(got, ref, orc):
+            g = g.cpu().numpy()
+            assert_rows_close(g, r)
+            assert_rows_close(g[sub], o)
+
+
+def test_noalloc_out_of_range_rows_are_zero():
+    from paper_1504_03687_gb300 import api
+    lib = api.load_library()
+    cl = W.plummer(2000, 74)
+    idx = np.array([5, -1, 17, 2000, 1999, 0], np.int32)
+    got = [g.cpu().numpy() for g in noalloc(lib, T(cl.x), T(cl.v), T(cl.m), T(idx))]
+    torch.cuda.synchronize()
+    ok = np.array([0, 2, 4, 5])
+    orc = oracle_rows(cl, idx[ok])
+    for g, o in zip(got, orc):
+        assert not np.any(g[[1, 3]])
+        assert_rows_close(g[ok], o)
 
 
 def test_noalloc_rejects_blocks_beyond_its_scratch():

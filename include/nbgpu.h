@@ -210,9 +210,10 @@ nb_status nb_irregular_force(nb_ctx *ctx, double t, int64_t n_i, const int32_t *
  * stream and returns, per phase, the summed device time in ms and the number of kernels
  * launched since the previous nb_get_timings (launch counts are kept even with timing
  * off), then resets both.  Phases: 0 predict, 1 force, 2 partial reduction,
- * 3 neighbour CSR, 4 backward, 5 irregular force.  ms and launches have NB_PHASES
+ * 3 neighbour CSR, 4 backward, 5 irregular force, 6 row order (the spatial order of the
+ * active rows that the anchored force kernel takes).  ms and launches have NB_PHASES
  * entries each. */
-#define NB_PHASES 6
+#define NB_PHASES 7
 nb_status nb_set_timing(nb_ctx *ctx, int32_t enable);
 nb_status nb_get_timings(nb_ctx *ctx, double *ms, int64_t *launches);
 
@@ -239,6 +240,18 @@ nb_status nb_inject_fault(nb_ctx *ctx, int32_t kind, int32_t after);
 /* One-line description of the last error on this context (never NULL). */
 const char *nb_last_error(const nb_ctx *ctx);
 
+/* Spatial order of an active block's rows: the permutation that the anchored mixed force
+ * kernel (plan variants 10-12) takes before it runs, and that a caller may use to lay out its
+ * own blocks (no counterpart in the paper; a locality device of this GPU design).  The rows
+ * idx (n_i, device int32) are ordered along the Morton (Z) curve of their predicted positions,
+ * quantised to 8 bits per coordinate over the block's bounding box (the hi parts of the mixed
+ * j-records of the last nb_predict / nb_set_predicted); ties keep row order (a stable sort), so
+ * the order is deterministic.  Writes perm (n_i, device int32): perm[r] is the row taken r-th.
+ * Rows whose index is outside [0, n) come last.  Asynchronous on the context stream.
+ * NB_ERR_STATE for an FP64 context or before a prediction; NB_ERR_ARG for n_i < 0 or null
+ * arrays (n_i = 0 does nothing). */
+nb_status nb_row_order(nb_ctx *ctx, int64_t n_i, const int32_t *idx, int32_t *perm);
+
 /* Describe the launch plan nb_regular_force would use (host-only, no GPU work):
  * out[0] = kernel id (0 = FP64 tiled, 1 = mixed tiled, 2 = mixed j-streamed,
  * 3 = FP64 j-streamed), out[1] = i-particles per CTA, out[2] = j-splits, out[3] = CTAs,
@@ -260,7 +273,7 @@ nb_status nb_set_plan_table(nb_ctx *ctx, int32_t n_entries, const int64_t *ni_ma
                             const int32_t *kernel, const int32_t *variant, const int32_t *splits);
 
 /* The automatic plan for a given device shape, without a context or a GPU (host-only):
- * num_sms SMs, ctas_per_sm[0..10] resident CTAs of the ten mixed tiled variants and the
+ * num_sms SMs, ctas_per_sm[0..13] resident CTAs of the thirteen mixed tiled variants and the
  * FP64 tiled kernel (NULL = 1 each), and the context's nb_cap. */
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
                       int64_t n_i, int32_t nb_cap, int64_t *out);

@@ -28,7 +28,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
 EXTRA = {"force_mixed.cu": ["-ftz=true"], "adjoint.cu": ["-ftz=true"], "irregular.cu": ["-ftz=true"],
          "ac.cu": ["-fmad=false"]}
 SOURCES = ["nb_api.cu", "predict.cu", "force_mixed.cu", "force_fp64.cu", "neighbours.cu", "adjoint.cu",
-           "noalloc.cu", "irregular.cu", "sched.cu", "ac.cu"]
+           "noalloc.cu", "irregular.cu", "sched.cu", "ac.cu", "roworder.cu"]
 
 
 def _nvcc() -> str:

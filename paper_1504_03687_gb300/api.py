@@ -32,7 +32,8 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force", "nb_sched_init", "nb_sched_free",
            "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error",
            "nb_sched_peek", "nb_ac_init", "nb_ac_step", "nb_ac_run", "nb_ac_get", "nb_ac_free", "nb_ac_last_error",
-           "nb_inject_fault", "nb_sched_set_time", "nb_ac_snapshot_bytes", "nb_ac_save", "nb_ac_restore")
+           "nb_inject_fault", "nb_sched_set_time", "nb_ac_snapshot_bytes", "nb_ac_save", "nb_ac_restore",
+           "nb_row_order")
 NB_FAULT_ALLOC, NB_FAULT_SYNC, NB_FAULT_STATUS = 1, 2, 3
 NB_SOURCE_ALIGN = 256
 
@@ -86,6 +87,7 @@ def load_library(build_if_needed: bool = True):
         "nb_sync": (st, [P]),
         "nb_last_error": (ctypes.c_char_p, [P]),
         "nb_plan": (st, [P, i64, i64, P]),
+        "nb_row_order": (st, [P, i64, P, P]),
         "nb_plan_for": (st, [i32, i32, P, i64, i64, i32, P]),
         "nb_set_plan_override": (st, [P, i32, i32, i32]),
         "nb_batch_plan": (st, [P, i64, P, P, i32]),
@@ -128,7 +130,7 @@ def plan_for(precision: str, num_sms: int, ctas_per_sm, n: int, n_i: int, nb_cap
     """Host-only launch plan (no GPU needed)."""
     lib = load_library()
     out = (ctypes.c_int64 * 6)()
-    occ = (ctypes.c_int32 * 11)(*ctas_per_sm) if ctas_per_sm is not None else None
+    occ = (ctypes.c_int32 * 14)(*ctas_per_sm) if ctas_per_sm is not None else None
     s = lib.nb_plan_for(PRECISIONS[precision], num_sms, ctypes.cast(occ, ctypes.c_void_p) if occ else None,
                         n, n_i, nb_cap, ctypes.cast(out, ctypes.c_void_p))
     if s != NB_OK:
@@ -359,7 +361,7 @@ class Context:
     def set_timing(self, enable: bool = True):
         self._check(self.lib.nb_set_timing(self.h, 1 if enable else 0), "nb_set_timing")
 
-    PHASES = ("predict", "force", "reduce", "neighbours", "backward", "irregular")
+    PHASES = ("predict", "force", "reduce", "neighbours", "backward", "irregular", "order")
 
     def timings(self) -> dict:
         """{phase: (device ms, kernel launches)} since the last call; synchronises."""
@@ -371,6 +373,14 @@ class Context:
 
     def sync(self, allow_overflow: bool = True) -> int:
         return self._check(self.lib.nb_sync(self.h), "nb_sync", allow_overflow)
+
+    def row_order(self, idx):
+        """nb_row_order: the spatial (Morton) order of the rows idx (device int32 tensor) that
+        the anchored force kernel takes; returns the permutation as a device int32 tensor."""
+        import torch
+        perm = torch.empty_like(idx)
+        self._check(self.lib.nb_row_order(self.h, int(idx.shape[0]), idx.data_ptr(), perm.data_ptr()), "nb_row_order")
+        return perm
 
     def plan(self, n: int, n_i: int) -> dict:
         out = (ctypes.c_int64 * 6)()

@@ -532,6 +532,288 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 }
 
 // ------------------------------------------------------------------------------------------
+// Anchored packed kernel.  The rows of a CTA are taken in the order A.perm (Morton order of
+// their positions, so a CTA's rows lie close together) and every position is measured from
+// one anchor B per CTA, the predicted position of the CTA's middle row: e_i = ds(x_i - B) once
+// per row and f_j = ds(x_j - B) once per j and CTA (in the tile expansion), both rounded to
+// FP32, with ds the double-single difference of the other kernels.  The pair separation is
+// then the single FP32 subtraction f_j - e_i: 3 lane-operations per pair where the
+// double-single difference takes 9 (27 instead of 33 FP32 lane-operations a pair), at an
+// error of at most about 4u |x_i - B| + 3u |r| (u = 2^-24) in the separation.  Pairs for which
+// that is not small against |r| — |r| below r_c,i = |x_i - B| / 16, where the bound is 67u |r| —
+// are masked out of the interaction loop (their inverse distance set to 0) and added by the
+// chunk replay with the double-single separation, exactly as the other kernels compute them.
+// The replay also decides the neighbours, from the double-single r^2 of the other kernels, so
+// the lists are bit-identical to theirs.  The loop's hit mask marks j that is either masked
+// (anchored r^2 < r_c,i^2) or possibly a neighbour (anchored r^2 < max(r_s^2, r_c,i^2) (1 +
+// 2^-10), a margin far above the anchored r^2 error at those distances).  The self pair has
+// separation exactly 0 (e_i and f_i are the same computation) and is masked like any pair.
+// Correct for any row order; the order only decides how many pairs are masked.
+//
+// Duplicated tile layout, five float4 per j:
+//   {fx,fx,fy,fy} {fz,fz,m,m} {vx,vx,vy,vy} {vz,vz,xh,yh} {zh,xl,yl,zl}
+// (the loop reads the first four; the replay also reads the absolute hi/lo position).
+// Per-row data the replay needs live in shared memory: index, output row, neighbour count,
+// r_s^2 (float) and the row's hi/lo position.
+enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_XH = 4, AR_XL = 7, AR_WORDS = 10 };
+
+template <int NI, int BLOCK, int TJ>
+constexpr int anchored_smem_bytes()
+{
+    return 3 * TJ * 16 + 5 * TJ * 16 + 7 * NI * BLOCK * 8 + AR_WORDS * NI * BLOCK * 4;
+}
+
+template <int NP, int BLOCK, int TJ, int UJ>
+__device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ sd, int64_t jb, const ForceArgs &A,
+                                                    int s, const float2 (&ne)[NP][3], const float2 (&nv)[NP][3],
+                                                    const float2 (&tm)[NP], const float2 (&th)[NP],
+                                                    int32_t *__restrict__ srow, float2 (&acc)[NP][7])
+{
+    static_assert(TJ % 32 == 0, "tiles are whole 32-j chunks");
+    constexpr int NR = 2 * NP;  // rows a thread
+    const float2 m3 = make_float2(-3.f, -3.f);
+    const int tid = threadIdx.x;
+    for (int jc = 0; jc < TJ; jc += 32) {
+        const float4 *sc = sd + 5 * jc;
+        unsigned hm = 0;
+#pragma unroll UJ
+        for (int u = 0; u < 32; ++u) {
+            const float4 a = sc[5 * u], b = sc[5 * u + 1], c = sc[5 * u + 2], d = sc[5 * u + 3];
+            const float2 M = make_float2(b.z, b.w), VX = make_float2(c.x, c.y), VY = make_float2(c.z, c.w);
+            const float2 VZ = make_float2(d.x, d.y);
+            bool hit = false;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 dx = f2add(make_float2(a.x, a.y), ne[q][0]);
+                const float2 dy = f2add(make_float2(a.z, a.w), ne[q][1]);
+                const float2 dz = f2add(make_float2(b.x, b.y), ne[q][2]);
+                const float2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+                float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                rinv.x = r2.x < tm[q].x ? 0.f : rinv.x;
+                rinv.y = r2.y < tm[q].y ? 0.f : rinv.y;
+                const float2 wx = f2add(VX, nv[q][0]), wy = f2add(VY, nv[q][1]), wz = f2add(VZ, nv[q][2]);
+                const float2 rw = f2fma(dz, wz, f2fma(dy, wy, f2mul(dx, wx)));
+                const float2 rinv2 = f2mul(rinv, rinv);
+                const float2 mr = f2mul(M, rinv);
+                const float2 mr3 = f2mul(mr, rinv2);
+                const float2 beta = f2mul(rw, f2mul(rinv2, m3));
+                acc[q][0] = f2fma(mr3, dx, acc[q][0]);
+                acc[q][1] = f2fma(mr3, dy, acc[q][1]);
+                acc[q][2] = f2fma(mr3, dz, acc[q][2]);
+                acc[q][3] = f2fma(mr3, f2fma(beta, dx, wx), acc[q][3]);
+                acc[q][4] = f2fma(mr3, f2fma(beta, dy, wy), acc[q][4]);
+                acc[q][5] = f2fma(mr3, f2fma(beta, dz, wz), acc[q][5]);
+                acc[q][6] = f2add(acc[q][6], mr);
+                hit |= (r2.x < th[q].x) | (r2.y < th[q].y);
+            }
+            hm |= (unsigned)hit << u;
+        }
+        // replay of the chunk's rare hits, in ascending j
+        while (hm) {
+            const int u = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int64_t j = jb + jc + u;
+            const int32_t j32 = (int32_t)j;
+            const float4 a = sc[5 * u], b = sc[5 * u + 1], c = sc[5 * u + 2], d = sc[5 * u + 3], e = sc[5 * u + 4];
+            const float jh[3] = {d.z, d.w, e.x}, jl[3] = {e.y, e.z, e.w}, jv[3] = {c.x, c.z, d.x};
+            const float jm = b.z;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 dx = f2add(make_float2(a.x, a.y), ne[q][0]);
+                const float2 dy = f2add(make_float2(a.z, a.w), ne[q][1]);
+                const float2 dz = f2add(make_float2(b.x, b.y), ne[q][2]);
+                const float2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float r2a = h ? r2.y : r2.x;
+                    if (!(r2a < (h ? th[q].y : th[q].x))) continue;
+                    const int slot = (2 * q + h) * BLOCK + tid;
+                    const int32_t gi = srow[AR_GI * NR * BLOCK + slot];
+                    if (j32 == gi) continue;
+                    const float *xr = reinterpret_cast<const float *>(srow);
+                    float r[3];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+                        r[cc] = ds_diff(jh[cc], jl[cc], xr[(AR_XH + cc) * NR * BLOCK + slot],
+                                        xr[(AR_XL + cc) * NR * BLOCK + slot]);
+                    const float r2p = r2_f32(r[0], r[1], r[2]);
+                    if (r2p < xr[AR_RS2 * NR * BLOCK + slot] && j < A.j_hi) {
+                        int32_t *cp = srow + AR_CNT * NR * BLOCK + slot;
+                        const int cnt = *cp;
+                        if (cnt < A.L)
+                            A.seg_slots[((int64_t)s * A.n_i + srow[AR_K * NR * BLOCK + slot]) * A.L + cnt] = j32;
+                        *cp = cnt + 1;
+                    }
+                    if (r2a < (h ? tm[q].y : tm[q].x)) {  // masked: add the pair in double-single form
+                        const float rinv = rsqrtf(r2p);
+                        const float w0 = jv[0] + (h ? nv[q][0].y : nv[q][0].x);
+                        const float w1 = jv[1] + (h ? nv[q][1].y : nv[q][1].x);
+                        const float w2 = jv[2] + (h ? nv[q][2].y : nv[q][2].x);
+                        const float rw = r[0] * w0 + r[1] * w1 + r[2] * w2;
+                        const float rinv2 = rinv * rinv;
+                        const float mr = jm * rinv;
+                        const float mr3 = mr * rinv2;
+                        const float beta = rw * (rinv2 * -3.f);
+                        const float t[7] = {mr3 * r[0], mr3 * r[1], mr3 * r[2], mr3 * (w0 + beta * r[0]),
+                                            mr3 * (w1 + beta * r[1]), mr3 * (w2 + beta * r[2]), mr};
+#pragma unroll
+                        for (int cc = 0; cc < 7; ++cc) {
+                            if (h) acc[q][cc].y += t[cc];
+                            else acc[q][cc].x += t[cc];
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_anchored_x2(ForceArgs A)
+{
+    constexpr int NP = NI / 2;
+    constexpr int UJ = NI >= 4 ? (MINB >= 4 ? 1 : 2) : 4;
+    constexpr int PT = TJ >= 256 ? 1 : 256 / TJ;  // FP32 sums over 256 j, then promoted to FP64
+    extern __shared__ __align__(16) float4 an_smem[];
+    float4 *raw = an_smem;                                           // 3*TJ float4
+    float4 *dup = an_smem + 3 * TJ;                                  // 5*TJ float4
+    double *dacc = reinterpret_cast<double *>(an_smem + 8 * TJ);     // [7][NI][BLOCK]
+    int32_t *srow = reinterpret_cast<int32_t *>(dacc + 7 * NI * BLOCK);  // [AR_WORDS][NI*BLOCK]
+    float *srowf = reinterpret_cast<float *>(srow);
+    __shared__ float s_anchor[6];  // B as hi (x, y, z) and lo (x, y, z)
+    const int tid = threadIdx.x;
+    const int64_t kbase = (int64_t)blockIdx.x * (BLOCK * NI);
+    const int s = blockIdx.y;
+    const int64_t tb = A.j_lo / TJ;
+    const int64_t t0 = tb + (A.n_tiles * s) / A.S, t1 = tb + (A.n_tiles * (s + 1)) / A.S;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+
+    if (tid == 0) {
+        const int64_t rows = A.n_i - kbase < NI * BLOCK ? A.n_i - kbase : NI * BLOCK;
+        const int64_t ra = kbase + rows / 2;
+        const int64_t ka = A.perm ? A.perm[ra] : ra;
+        const int64_t ga = (ka >= 0 && ka < A.n_i) ? A.idx[ka] : -1;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+        if (ga >= 0 && ga < A.n) {
+            h = rec[3 * ga];
+            l = rec[3 * ga + 1];
+        }
+        s_anchor[0] = h.x; s_anchor[1] = h.y; s_anchor[2] = h.z;
+        s_anchor[3] = l.x; s_anchor[4] = l.y; s_anchor[5] = l.z;
+    }
+    __syncthreads();
+    const float Bh[3] = {s_anchor[0], s_anchor[1], s_anchor[2]}, Bl[3] = {s_anchor[3], s_anchor[4], s_anchor[5]};
+
+    float2 ne[NP][3], nv[NP][3], tm[NP], th[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float e[2][3], v[2][3], tmask[2], thit[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int slot = (2 * p + u) * BLOCK + tid;
+            const int64_t r = kbase + slot;
+            int64_t k = -1, g = -1;
+            if (r < A.n_i) {
+                k = A.perm ? A.perm[r] : r;
+                g = A.idx[k];
+                if (g < 0 || g >= A.n) {
+                    if (s == 0) atomicOr(A.status, ST_BAD_INDEX);
+                    g = -1;
+                }
+            }
+            float h3[3] = {0.f, 0.f, 0.f}, l3[3] = {0.f, 0.f, 0.f}, rs2f = -1.f;
+            v[u][0] = v[u][1] = v[u][2] = 0.f;
+            if (g >= 0) {
+                const float4 p0 = rec[3 * g], p1 = rec[3 * g + 1], p2 = rec[3 * g + 2];
+                h3[0] = p0.x; h3[1] = p0.y; h3[2] = p0.z;
+                l3[0] = p1.x; l3[1] = p1.y; l3[2] = p1.z;
+                v[u][0] = -p2.x; v[u][1] = -p2.y; v[u][2] = -p2.z;
+                if (A.want_nb) rs2f = __double2float_rn(A.rs2[A.rs2_scalar ? 0 : k]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) e[u][c] = -ds_diff(h3[c], l3[c], Bh[c], Bl[c]);
+            const float ee = r2_f32(e[u][0], e[u][1], e[u][2]);
+            const float rc2 = fmaxf(ee * (1.f / 256.f), 1.17549435e-38f);
+            tmask[u] = g >= 0 ? rc2 : -1.f;
+            thit[u] = g >= 0 ? fmaxf(rs2f, rc2) * (1.f + 1.f / 1024.f) : -1.f;
+            srow[AR_GI * NI * BLOCK + slot] = (int32_t)g;
+            srow[AR_K * NI * BLOCK + slot] = (int32_t)k;
+            srow[AR_CNT * NI * BLOCK + slot] = 0;
+            srowf[AR_RS2 * NI * BLOCK + slot] = rs2f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                srowf[(AR_XH + c) * NI * BLOCK + slot] = h3[c];
+                srowf[(AR_XL + c) * NI * BLOCK + slot] = l3[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ne[p][c] = make_float2(e[0][c], e[1][c]);
+            nv[p][c] = make_float2(v[0][c], v[1][c]);
+        }
+        tm[p] = make_float2(tmask[0], tmask[1]);
+        th[p] = make_float2(thit[0], thit[1]);
+    }
+#pragma unroll
+    for (int e = 0; e < 7 * NI; ++e) dacc[e * BLOCK + tid] = 0.0;
+
+    auto load_tile = [&](int64_t t) {
+        const float4 *src = rec + t * (3 * TJ);
+#pragma unroll
+        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
+        cp_async_commit();
+    };
+    float2 acc[NP][7];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[p][c] = make_float2(0.f, 0.f);
+    if (t0 < t1) load_tile(t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        cp_async_wait<0>();
+        __syncthreads();  // raw holds tile t; every thread is done with the previous dup
+#pragma unroll
+        for (int jj = tid; jj < TJ; jj += BLOCK) {
+            const float4 p0 = raw[3 * jj], p1 = raw[3 * jj + 1], p2 = raw[3 * jj + 2];
+            const float fx = ds_diff(p0.x, p1.x, Bh[0], Bl[0]);
+            const float fy = ds_diff(p0.y, p1.y, Bh[1], Bl[1]);
+            const float fz = ds_diff(p0.z, p1.z, Bh[2], Bl[2]);
+            dup[5 * jj] = make_float4(fx, fx, fy, fy);
+            dup[5 * jj + 1] = make_float4(fz, fz, p0.w, p0.w);
+            dup[5 * jj + 2] = make_float4(p2.x, p2.x, p2.y, p2.y);
+            dup[5 * jj + 3] = make_float4(p2.z, p2.z, p0.x, p0.y);
+            dup[5 * jj + 4] = make_float4(p0.z, p1.x, p1.y, p1.z);
+        }
+        __syncthreads();  // dup complete; raw is free again
+        if (t + 1 < t1) load_tile(t + 1);
+        tile_mixed_anchored<NP, BLOCK, TJ, UJ>(dup, t * TJ, A, s, ne, nv, tm, th, srow, acc);
+        if ((t - t0) % PT == PT - 1 || t + 1 == t1) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    dacc[(c * NI + 2 * p) * BLOCK + tid] += (double)acc[p][c].x;
+                    dacc[(c * NI + 2 * p + 1) * BLOCK + tid] += (double)acc[p][c].y;
+                    acc[p][c] = make_float2(0.f, 0.f);
+                }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int slot = q * BLOCK + tid;
+        const int64_t k = srow[AR_K * NI * BLOCK + slot];
+        if (k >= 0) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const double v = dacc[(c * NI + q) * BLOCK + tid];
+                A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -v : v;
+            }
+            if (A.want_nb) A.seg_cnt[(int64_t)s * A.n_i + k] = srow[AR_CNT * NI * BLOCK + slot];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Batched ensemble kernel: many independent clusters in one persistent launch.  The particle
 // arrays of all clusters are concatenated; cluster c owns the j-range
 // [cluster_off[c], cluster_off[c+1]) and the active rows it lists.  Work items (cluster, up to
@@ -734,37 +1016,44 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
 }
 
 // ------------------------------------------------------------------------------------------
-// Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM).  The plan's
+// Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM, kind).  The plan's
 // `variant` indexes this list; ids 0-3 are the scalar kernel, 4-9 the packed-FP32x2 one
-// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows).
-// Last column: 1 = packed kernel (dynamic shared memory, x2_smem_bytes).
-#define NB_MIXED_TILED_VARIANTS(X)                    \
-    X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)      \
-    X(1, k_force_mixed_tiled, 2, 128, 256, 4, 0)      \
-    X(2, k_force_mixed_tiled, 1, 128, 256, 4, 0)      \
-    X(3, k_force_mixed_tiled, 4, 256, 256, 1, 0)      \
-    X(4, k_force_mixed_tiled_x2, 4, 128, 256, 3, 1)   \
-    X(5, k_force_mixed_tiled_x2, 2, 128, 256, 4, 1)   \
-    X(6, k_force_mixed_tiled_x2, 4, 128, 128, 4, 1)   \
-    X(7, k_force_mixed_tiled_x2, 2, 256, 256, 2, 1)   \
-    X(8, k_force_mixed_tiled_x2, 2, 64, 128, 8, 1)    \
-    X(9, k_force_mixed_tiled_x2, 2, 32, 128, 12, 1)
+// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-12 the
+// anchored packed kernel (rows in spatial order, anchor-relative separations).
+// Last column: 0 = scalar (static shared memory), 1 = packed (x2_smem_bytes), 2 = anchored
+// (anchored_smem_bytes; needs the row order A.perm).
+#define NB_MIXED_TILED_VARIANTS(X)                       \
+    X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)         \
+    X(1, k_force_mixed_tiled, 2, 128, 256, 4, 0)         \
+    X(2, k_force_mixed_tiled, 1, 128, 256, 4, 0)         \
+    X(3, k_force_mixed_tiled, 4, 256, 256, 1, 0)         \
+    X(4, k_force_mixed_tiled_x2, 4, 128, 256, 3, 1)      \
+    X(5, k_force_mixed_tiled_x2, 2, 128, 256, 4, 1)      \
+    X(6, k_force_mixed_tiled_x2, 4, 128, 128, 4, 1)      \
+    X(7, k_force_mixed_tiled_x2, 2, 256, 256, 2, 1)      \
+    X(8, k_force_mixed_tiled_x2, 2, 64, 128, 8, 1)       \
+    X(9, k_force_mixed_tiled_x2, 2, 32, 128, 12, 1)      \
+    X(10, k_force_mixed_anchored_x2, 4, 128, 128, 3, 2)  \
+    X(11, k_force_mixed_anchored_x2, 2, 128, 128, 4, 2)  \
+    X(12, k_force_mixed_anchored_x2, 4, 128, 256, 2, 2)
 
 struct TiledVariant {
-    int ni, block, tj, smem;
+    int ni, block, tj, smem, kind;
 };
-#define NB_TV_ROW(id, K, NI, B, TJ, MB, X2) {NI, B, TJ, X2 ? x2_smem_bytes<NI, B, TJ>() : 0},
+#define NB_TV_ROW(id, K, NI, B, TJ, MB, KIND) \
+    {NI, B, TJ, KIND == 1 ? x2_smem_bytes<NI, B, TJ>() : (KIND == 2 ? anchored_smem_bytes<NI, B, TJ>() : 0), KIND},
 static const TiledVariant kTiled[] = {NB_MIXED_TILED_VARIANTS(NB_TV_ROW)};
 #undef NB_TV_ROW
 
 int mixed_tiled_dyn_smem(int v) { return kTiled[v].smem; }
+int mixed_tiled_anchored(int v) { return v >= 0 && v < (int)(sizeof(kTiled) / sizeof(kTiled[0])) && kTiled[v].kind == 2; }
 
 // Raise the dynamic shared-memory limit of the packed kernels (needed above 48 KB); called
 // once per context before occupancy queries and launches.
 void mixed_tiled_configure()
 {
-#define NB_TV_CFG(id, K, NI, B, TJ, MB, X2)                                                          \
-    if (X2)                                                                                          \
+#define NB_TV_CFG(id, K, NI, B, TJ, MB, KIND)                                                        \
+    if (KIND)                                                                                        \
         cudaFuncSetAttribute((const void *)K<NI, B, TJ, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              kTiled[id].smem);
     NB_MIXED_TILED_VARIANTS(NB_TV_CFG)
@@ -777,7 +1066,7 @@ int mixed_tiled_variants() { return (int)(sizeof(kTiled) / sizeof(kTiled[0])); }
 void *mixed_tiled_fn(int v)
 {
     switch (v) {
-#define NB_TV_FN(id, K, NI, B, TJ, MB, X2) \
+#define NB_TV_FN(id, K, NI, B, TJ, MB, KIND) \
     case id: return (void *)K<NI, B, TJ, MB>;
         NB_MIXED_TILED_VARIANTS(NB_TV_FN)
 #undef NB_TV_FN
@@ -796,7 +1085,7 @@ void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x
     dim3 grid((unsigned)ctas_x, (unsigned)S);
     if (kernel == 1) {
         switch (variant) {
-#define NB_TV_LAUNCH(id, K, NI, B, TJ, MB, X2) \
+#define NB_TV_LAUNCH(id, K, NI, B, TJ, MB, KIND) \
     case id: K<NI, B, TJ, MB><<<grid, B, kTiled[id].smem, st>>>(a); break;
             NB_MIXED_TILED_VARIANTS(NB_TV_LAUNCH)
 #undef NB_TV_LAUNCH

@@ -32,6 +32,7 @@ int mixed_tiled_tj(int v);
 int mixed_jstream_ib(int v);
 int jstream_warps();
 int mixed_tiled_dyn_smem(int v);
+int mixed_tiled_anchored(int v);
 void mixed_tiled_configure();
 int mixed_batched_rows_per_item(int v);
 int mixed_batched_variants();
@@ -49,9 +50,9 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
-static constexpr int kMixedTiledVariants = 10;  // entries of the mixed tiled variant table
-static constexpr int kOccFp64 = 10;             // occupancy slot of the FP64 tiled kernel
-static constexpr int kOccSlots = 11;
+static constexpr int kMixedTiledVariants = 13;  // entries of the mixed tiled variant table
+static constexpr int kOccFp64 = 13;             // occupancy slot of the FP64 tiled kernel
+static constexpr int kOccSlots = 14;
 static constexpr int kMaxCap = 8192;
 // Irregular force: predict all particles once when N_i * factor >= N.  Measured on this GPU
 // (King cluster, N = 2^20, r_s for a median of 80 neighbours): in FP64 the per-pair prediction
@@ -92,6 +93,7 @@ struct nb_ctx {
     // batched ensemble plan (nb_batch_plan)
     void *b_items = nullptr; size_t b_items_cap = 0;
     int64_t *b_cluster_off = nullptr; size_t b_cluster_off_cap = 0;
+    void *ro = nullptr; size_t ro_cap = 0;  // row order of the anchored force kernel
     int64_t b_clusters = 0, b_rows = 0, b_items_n = 0, b_n = 0;
     int b_variant = -1, b_ctas = 0, b_L = 0;
     char err[512] = {0};
@@ -109,7 +111,8 @@ struct nb_ctx {
     int fault_kind = 0, fault_after = 0;
 };
 
-enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_IRREGULAR = 5, PH_COUNT = 6 };
+enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_IRREGULAR = 5, PH_ORDER = 6,
+       PH_COUNT = 7 };
 
 static cudaEvent_t ev_take(nb_ctx *c)
 {
@@ -302,8 +305,10 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
         // relative per-pair speed of the tiled variants (scalar NI=4/2/1, NI=4 x 256 threads,
         // packed FP32x2 NI=4/2, NI=4 with 128-j tiles, NI=2 x 256 threads), measured on a
         // GB300 at N = 2^20, N_i = 2^17 (King W0 = 6); the two small-tile packed variants
-        // (NI=2 x 64 and x 32 threads) estimated from their occupancy
-        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91, 0.85, 0.75};
+        // (NI=2 x 64 and x 32 threads) estimated from their occupancy, the three anchored
+        // variants from their FP32 operation count (27 instead of 33 lane-operations a pair)
+        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0,
+                                                           0.91, 0.85, 0.75, 1.2, 1.1, 1.15};
         double best = -1.0;
         for (int v = 0; v < kMixedTiledVariants; ++v) {
             if (only_variant >= 0 && v != only_variant) continue;
@@ -385,6 +390,7 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
 void query_occupancy(int *occ)
 {
     mixed_tiled_configure();
+    roworder_configure();
     for (int v = 0; v < kMixedTiledVariants; ++v) {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mixed_tiled_fn(v), mixed_tiled_block(v),
@@ -542,7 +548,7 @@ nb_status nb_free(nb_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->x, c->v, c->a, c->jk, c->m, c->tl, c->xp, c->vp, c->rec, c->status,
                     c->part, c->seg_slots, c->seg_cnt, c->row_total, c->scan, c->stage, c->adj, c->b_items,
-                    c->b_cluster_off, c->srec, c->prec};
+                    c->b_cluster_off, c->srec, c->prec, c->ro};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -678,6 +684,25 @@ nb_status nb_set_plan_table(nb_ctx *c, int32_t n_entries, const int64_t *ni_max,
         t.push_back({ni_max[q], kernel[q], variant[q], splits[q]});
     }
     c->table.swap(t);
+    return NB_OK;
+}
+
+nb_status nb_row_order(nb_ctx *c, int64_t n_i, const int32_t *idx, int32_t *perm)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (c->precision != NB_MIXED) return fail(c, NB_ERR_STATE, "nb_row_order reads the mixed j-records: mixed context only");
+    if (!c->have_pred) return fail(c, NB_ERR_STATE, "nb_row_order before nb_predict / nb_set_predicted");
+    if (n_i < 0 || n_i > (int64_t)INT32_MAX) return fail(c, NB_ERR_ARG, "n_i=%lld out of range", (long long)n_i);
+    if (n_i == 0) return NB_OK;
+    if (!idx || !perm) return fail(c, NB_ERR_ARG, "null array");
+    if ((s = grow(c, &c->ro, &c->ro_cap, roworder_scratch_bytes(n_i), "row order")) != NB_OK) return s;
+    cudaEvent_t t0 = span_begin(c);
+    const int32_t *out = nullptr;
+    const int kernels = launch_row_order(c->stream, c->rec, idx, c->n, n_i, c->ro, &out);
+    CK_LAUNCH("row order launch");
+    CK(cudaMemcpyAsync(perm, out, (size_t)n_i * 4, cudaMemcpyDeviceToDevice, c->stream), "copy order");
+    span_end(c, PH_ORDER, t0, kernels);
     return NB_OK;
 }
 
@@ -825,6 +850,13 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
         if ((s = grow(c, (void **)&c->scan, &c->scan_cap, scan_elems * 8, "scan scratch")) != NB_OK) return s;
     }
     ForceArgs fa{};
+    if (p.kernel == 1 && mixed_tiled_anchored(p.variant)) {  // spatial order of the rows first
+        if ((s = grow(c, &c->ro, &c->ro_cap, roworder_scratch_bytes(n_i), "row order")) != NB_OK) return s;
+        cudaEvent_t t0 = span_begin(c);
+        const int kernels = launch_row_order(c->stream, c->rec, d_idx, n, n_i, c->ro, &fa.perm);
+        CK_LAUNCH("row order launch");
+        span_end(c, PH_ORDER, t0, kernels);
+    }
     fa.rec = c->rec;
     fa.n = n;
     fa.j_lo = j_lo;

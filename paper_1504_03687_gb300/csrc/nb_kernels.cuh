@@ -30,6 +30,7 @@ struct ForceArgs {
     int64_t n_tiles;        // j-tiles of the launch's tile size covering the source range
     const int32_t *idx;     // active indices
     int64_t n_i;
+    const int32_t *perm;    // anchored kernel: row order (the r-th row is row perm[r]); null = identity
     const double *rs2;      // (n_i) or scalar
     int32_t rs2_scalar;
     int32_t want_nb;        // 0: skip neighbour capture
@@ -86,6 +87,13 @@ void launch_pack_predicted(cudaStream_t st, int64_t n, int64_t n_pad, const doub
                            const double *vp, const double *m, void *rec64, void *rec32);
 
 void launch_force(cudaStream_t st, const Plan &p, ForceArgs a);
+
+// Spatial (Morton) order of an active block's rows for the anchored force kernel
+// (roworder.cu): writes a permutation of [0, n_i) into scratch and returns the launches.
+size_t roworder_scratch_bytes(int64_t n_i);
+void roworder_configure();
+int launch_row_order(cudaStream_t st, const void *rec, const int32_t *idx, int64_t n, int64_t n_i, void *scratch,
+                     const int32_t **perm_out);
 
 void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc,
                    double *jerk, double *pot);

@@ -23,7 +23,7 @@ import numpy as np
 TABLE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_plans.json")
 
 # candidate plans: (kernel, variant, splits); splits 0 = the planner's split count
-MIXED_CANDIDATES = [(1, v, 0) for v in range(10)] + [(2, v, 0) for v in range(3)]
+MIXED_CANDIDATES = [(1, v, 0) for v in range(13)] + [(2, v, 0) for v in range(3)]
 FP64_CANDIDATES = [(0, 0, 0), (3, 0, 0), (3, 1, 0)]
 
 
@@ -45,7 +45,8 @@ def _time_plan(ctx, idx, rs2, plan, reps):
     ctx.set_timing(False)
     ctx.sync()
     ctx.set_plan_override(-1)
-    return (ph["force"][0] + ph["reduce"][0] + ph["neighbours"][0]) / reps
+    # the anchored variants pay for their row order too
+    return (ph["order"][0] + ph["force"][0] + ph["reduce"][0] + ph["neighbours"][0]) / reps
 
 
 def tune_force(ctx, order, rs2, buckets=None, reps=2, candidates=None, log=print):

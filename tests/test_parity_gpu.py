@@ -402,7 +402,7 @@ def test_million_body_sampled_rows(gpu_lib, king1m):
 
 
 # ------------------------------------------------------------------ every tiled kernel variant
-@pytest.mark.parametrize("variant", list(range(10)))
+@pytest.mark.parametrize("variant", list(range(13)))
 def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
     """Every variant of the mixed tiled kernel (scalar and packed FP32x2, forced through the plan
     override) meets the mixed bar against the oracle and gives the same neighbour lists."""
@@ -426,7 +426,7 @@ def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", list(range(10)))
+@pytest.mark.parametrize("variant", list(range(13)))
 def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
     """Dense neighbourhoods (r_s^2 x 9, hundreds of neighbours a row) with nb_cap 16: many hits
     in every 32-j chunk of the packed kernels' interaction loop and lists cut at the cap inside a
@@ -449,8 +449,9 @@ def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
 def test_mixed_far_from_the_origin(gpu_lib):
     """The cluster translated by (1e4, -2e4, 3e3) length units (a star cluster far from the
     coordinate origin): forces do not change, but single-precision coordinates would lose about
-    four digits of every separation there. The double-single differences keep the mixed path
-    within its bars against the oracle of the shifted state, with the same neighbour lists."""
+    four digits of every separation there. The double-single differences (and the anchored
+    kernel's separations from an anchor among the rows) keep the mixed path within its bars
+    against the oracle of the shifted state, with the same neighbour lists."""
     cl = W.plummer(4096, 77, masses="kroupa")
     rs2 = float(W.neighbour_radius2(cl.x, 50, seed=77))
     x = cl.x + np.array([1.0e4, -2.0e4, 3.0e3])
@@ -458,8 +459,11 @@ def test_mixed_far_from_the_origin(gpu_lib):
     ref = oracle.regular_force(x, cl.v, cl.m, idx, rs2, cap=512)
     ctx = make_ctx(cl.n, "mixed")
     ctx.set_predicted(T(x), T(cl.v), T(cl.m))
-    res = ctx.regular_force(T(idx), rs2)
-    ctx.sync()
-    check_mixed(res, ref)
-    check_lists_band(res, x, idx, rs2, ref[3], ref[4], 512)
+    for variant in (None, 4, 10):  # the automatic plan, the packed and the anchored kernel
+        if variant is not None:
+            ctx.set_plan_override(1, variant, 0)
+        res = ctx.regular_force(T(idx), rs2)
+        ctx.sync()
+        check_mixed(res, ref)
+        check_lists_band(res, x, idx, rs2, ref[3], ref[4], 512)
     ctx.close()

@@ -1018,8 +1018,9 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
 // ------------------------------------------------------------------------------------------
 // Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM, kind).  The plan's
 // `variant` indexes this list; ids 0-3 are the scalar kernel, 4-9 the packed-FP32x2 one
-// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-12 the
-// anchored packed kernel (rows in spatial order, anchor-relative separations).
+// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-14 the
+// anchored packed kernel (rows in spatial order, anchor-relative separations; 13 and 14 with
+// row tiles of 128 and 64).
 // Last column: 0 = scalar (static shared memory), 1 = packed (x2_smem_bytes), 2 = anchored
 // (anchored_smem_bytes; needs the row order A.perm).
 #define NB_MIXED_TILED_VARIANTS(X)                       \
@@ -1035,7 +1036,9 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
     X(9, k_force_mixed_tiled_x2, 2, 32, 128, 12, 1)      \
     X(10, k_force_mixed_anchored_x2, 4, 128, 128, 3, 2)  \
     X(11, k_force_mixed_anchored_x2, 2, 128, 128, 4, 2)  \
-    X(12, k_force_mixed_anchored_x2, 4, 128, 256, 2, 2)
+    X(12, k_force_mixed_anchored_x2, 4, 128, 256, 2, 2)  \
+    X(13, k_force_mixed_anchored_x2, 2, 64, 64, 8, 2)    \
+    X(14, k_force_mixed_anchored_x2, 2, 32, 64, 12, 2)
 
 struct TiledVariant {
     int ni, block, tj, smem, kind;

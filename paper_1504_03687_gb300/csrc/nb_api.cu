@@ -50,9 +50,9 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
-static constexpr int kMixedTiledVariants = 13;  // entries of the mixed tiled variant table
-static constexpr int kOccFp64 = 13;             // occupancy slot of the FP64 tiled kernel
-static constexpr int kOccSlots = 14;
+static constexpr int kMixedTiledVariants = 15;  // entries of the mixed tiled variant table
+static constexpr int kOccFp64 = 15;             // occupancy slot of the FP64 tiled kernel
+static constexpr int kOccSlots = 16;
 static constexpr int kMaxCap = 8192;
 // Irregular force: predict all particles once when N_i * factor >= N.  Measured on this GPU
 // (King cluster, N = 2^20, r_s for a median of 80 neighbours): in FP64 the per-pair prediction
@@ -305,10 +305,10 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
         // relative per-pair speed of the tiled variants (scalar NI=4/2/1, NI=4 x 256 threads,
         // packed FP32x2 NI=4/2, NI=4 with 128-j tiles, NI=2 x 256 threads), measured on a
         // GB300 at N = 2^20, N_i = 2^17 (King W0 = 6); the two small-tile packed variants
-        // (NI=2 x 64 and x 32 threads) estimated from their occupancy, the three anchored
-        // variants from their FP32 operation count (27 instead of 33 lane-operations a pair)
-        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0,
-                                                           0.91, 0.85, 0.75, 1.2, 1.1, 1.15};
+        // (NI=2 x 64 and x 32 threads) estimated from their occupancy; the anchored variants
+        // measured the same way (10-12) or estimated (13, 14: the small-tile packed ones x 1.1)
+        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91,
+                                                           0.85, 0.75, 1.12, 1.08, 1.04, 0.94, 0.82};
         double best = -1.0;
         for (int v = 0; v < kMixedTiledVariants; ++v) {
             if (only_variant >= 0 && v != only_variant) continue;

@@ -130,9 +130,11 @@ __device__ void ro_box_rows(const RoRows &R, int64_t r0, int64_t r1, int64_t str
 
 // Ranks of the rows of one CTA chunk by digit, in row order (stable).  d_of(it) gives the
 // digit of round it's row (kRoBins for a row past the end); rank(it, r) receives its rank
-// among the chunk's rows with the same digit.  On return s_run holds the chunk's digit counts.
+// among the chunk's rows with the same digit.  Only the first `rounds` rounds hold rows (the
+// same count for the whole CTA).  On return s_run holds the chunk's digit counts.
 template <typename DigitOf, typename Rank>
-__device__ __forceinline__ void ro_rank_chunk(DigitOf d_of, Rank rank, int32_t (*s_wcnt)[kRoBins], int32_t *s_run)
+__device__ __forceinline__ void ro_rank_chunk(DigitOf d_of, Rank rank, int rounds, int32_t (*s_wcnt)[kRoBins],
+                                              int32_t *s_run)
 {
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     s_run[tid] = 0;
@@ -141,6 +143,7 @@ __device__ __forceinline__ void ro_rank_chunk(DigitOf d_of, Rank rank, int32_t (
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kRoItems; ++it) {
+        if (it >= rounds) break;
         const int d = d_of(it);
         const bool valid = d < kRoBins;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -200,6 +203,7 @@ __global__ void __launch_bounds__(kRoThreads) k_ro_single(RoRows R, int32_t *__r
     __syncthreads();
     float lo[3], inv[3];
     ro_frame(s_box, lo, inv);
+#pragma unroll
     for (int it = 0; it < kRoItems; ++it) {
         const int64_t e = (int64_t)it * kRoThreads + tid;
         if (e < n_i) ro_buf[e] = ((unsigned long long)ro_key(R, e, lo, inv) << 32) | (unsigned long long)e;
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(kRoThreads) k_ro_single(RoRows R, int32_t *__r
                 const int64_t e = (int64_t)it * kRoThreads + tid;
                 return e < n_i ? (int)((in[e] >> shift) & 0xffu) : kRoBins;
             },
-            [&](int it, int r) { rk[it] = r; }, s_wcnt, s_run);
+            [&](int it, int r) { rk[it] = r; }, (int)((n_i + kRoThreads - 1) / kRoThreads), s_wcnt, s_run);
         ro_scan_bins(s_run, s_warp);
 #pragma unroll
         for (int it = 0; it < kRoItems; ++it) {
@@ -264,10 +268,13 @@ __global__ void __launch_bounds__(kRoThreads) k_ro_rank(RoPass P, RoRows R, cons
     const int64_t c0 = (int64_t)blockIdx.x * kRoChunk;
     float lo[3] = {0.f, 0.f, 0.f}, inv[3] = {0.f, 0.f, 0.f};
     if (FIRST) ro_frame(box, lo, inv);
-    ro_rank_chunk(
-        [&](int it) {
-            const int64_t e = c0 + (int64_t)it * kRoThreads + tid;
-            if (e >= P.n_i) return kRoBins;
+    // every round's digit first, so that the loads of all rounds are in flight together
+    int dig[kRoItems];
+#pragma unroll
+    for (int it = 0; it < kRoItems; ++it) {
+        const int64_t e = c0 + (int64_t)it * kRoThreads + tid;
+        dig[it] = kRoBins;
+        if (e < P.n_i) {
             uint32_t key;
             if (FIRST) {
                 key = ro_key(R, e, lo, inv);
@@ -275,9 +282,13 @@ __global__ void __launch_bounds__(kRoThreads) k_ro_rank(RoPass P, RoRows R, cons
             } else {
                 key = P.key_in[e];
             }
-            return (int)((key >> P.shift) & 0xffu);
-        },
-        [&](int it, int r) { P.rank[c0 + (int64_t)it * kRoThreads + tid] = r; }, s_wcnt, s_run);
+            dig[it] = (int)((key >> P.shift) & 0xffu);
+        }
+    }
+    const int64_t left = P.n_i - c0;
+    const int rounds = left >= kRoChunk ? kRoItems : (int)((left + kRoThreads - 1) / kRoThreads);
+    ro_rank_chunk([&](int it) { return dig[it]; },
+                  [&](int it, int r) { P.rank[c0 + (int64_t)it * kRoThreads + tid] = r; }, rounds, s_wcnt, s_run);
     P.hist[(int64_t)tid * P.ctas + blockIdx.x] = s_run[tid];
 }
 

@@ -18,7 +18,9 @@
 // one atomic per (active i, component); for unique indices the result is deterministic.
 // For dense blocks (n_i >= 3n/4), in either precision, one fused pass replaces the two: every
 // particle carries its (possibly zero) cotangents, and each pair evaluated once gives both
-// directions (i as the active row against j, and j as the active row against i).
+// directions (i as the active row against j, and j as the active row against i).  In mixed
+// precision the fused pass takes the particles in spatial order and measures separations from
+// one anchor per CTA (k_adj_fused_anchored_x2), with close pairs replayed in double-single form.
 // Self pairs are skipped by r^2 == 0 (distinct particles never coincide).
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
@@ -456,143 +458,20 @@ __global__ void k_scatter_cotangents(int64_t n, int64_t n_i, const int32_t *__re
     }
 }
 
-template <int BLOCK, int TJ>
-constexpr int adj_fused_smem()
-{
-    return 5 * TJ * 16 + 9 * TJ * 16 + 7 * 2 * BLOCK * 8;
-}
-
-// One packed row pair per thread (rows tid and BLOCK + tid of the CTA), j-tiles of crec.
-template <int BLOCK, int TJ, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const float4 *__restrict__ crec)
-{
-    extern __shared__ __align__(16) float4 adj_smem[];
-    float4 *raw = adj_smem;                 // 5*TJ
-    float4 *dup = adj_smem + 5 * TJ;        // 9*TJ
-    double *dacc = reinterpret_cast<double *>(adj_smem + 14 * TJ);  // [7][2][BLOCK]
-    const int tid = threadIdx.x;
-    const int64_t kbase = (int64_t)blockIdx.x * (2 * BLOCK);
-    const int s = blockIdx.y;
-    const int64_t t0 = (A.n_tiles_j * s) / A.S, t1 = (A.n_tiles_j * (s + 1)) / A.S;
-    float2 nh[3], nl[3], nv[3], ga[3], gj[3], gs, mk;
+// FP32 sums of one row pair over a j-tile in the fused pass, and their promotion to the FP64
+// running sums dacc[c][2][BLOCK] (c: g_x 0-2, g_v 3-5, g_m 6).
+struct AdjTileSums {
+    float2 s0, s1, A1[3], B1[3], C1[3], v2[3], u2[3], d2;
+    __device__ __forceinline__ void zero()
     {
-        float4 a[2], b[2], c[2], d[2], e[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {  // crec is padded to the tile multiple
-            const int64_t k = kbase + u * BLOCK + tid;
-            a[u] = crec[5 * k]; b[u] = crec[5 * k + 1]; c[u] = crec[5 * k + 2];
-            d[u] = crec[5 * k + 3]; e[u] = crec[5 * k + 4];
-        }
-        nh[0] = make_float2(-a[0].x, -a[1].x); nh[1] = make_float2(-a[0].y, -a[1].y);
-        nh[2] = make_float2(-a[0].z, -a[1].z); mk = make_float2(a[0].w, a[1].w);
-        nl[0] = make_float2(-b[0].x, -b[1].x); nl[1] = make_float2(-b[0].y, -b[1].y);
-        nl[2] = make_float2(-b[0].z, -b[1].z); gs = make_float2(b[0].w, b[1].w);
-        nv[0] = make_float2(-c[0].x, -c[1].x); nv[1] = make_float2(-c[0].y, -c[1].y);
-        nv[2] = make_float2(-c[0].z, -c[1].z); gj[0] = make_float2(c[0].w, c[1].w);
-        ga[0] = make_float2(d[0].x, d[1].x); ga[1] = make_float2(d[0].y, d[1].y);
-        ga[2] = make_float2(d[0].z, d[1].z); gj[1] = make_float2(d[0].w, d[1].w);
-        gj[2] = make_float2(e[0].x, e[1].x);
-    }
-#pragma unroll
-    for (int e = 0; e < 14; ++e) dacc[e * BLOCK + tid] = 0.0;
-    const float2 m3 = make_float2(-3.f, -3.f), m5 = make_float2(-5.f, -5.f);
-    auto load_tile = [&](int64_t t) {
-        const float4 *src = crec + t * (5 * TJ);
-#pragma unroll
-        for (int e = tid; e < 5 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
-        cp_async_commit();
-    };
-    if (t0 < t1) load_tile(t0);
-    for (int64_t t = t0; t < t1; ++t) {
-        cp_async_wait<0>();
-        __syncthreads();
-#pragma unroll
-        for (int jj = tid; jj < TJ; jj += BLOCK) {
-            const float4 a = raw[5 * jj], b = raw[5 * jj + 1], c = raw[5 * jj + 2], d = raw[5 * jj + 3],
-                         e = raw[5 * jj + 4];
-            dup[9 * jj] = make_float4(a.x, a.x, a.y, a.y);
-            dup[9 * jj + 1] = make_float4(a.z, a.z, a.w, a.w);
-            dup[9 * jj + 2] = make_float4(b.x, b.x, b.y, b.y);
-            dup[9 * jj + 3] = make_float4(b.z, b.z, b.w, b.w);
-            dup[9 * jj + 4] = make_float4(c.x, c.x, c.y, c.y);
-            dup[9 * jj + 5] = make_float4(c.z, c.z, c.w, c.w);
-            dup[9 * jj + 6] = make_float4(d.x, d.x, d.y, d.y);
-            dup[9 * jj + 7] = make_float4(d.z, d.z, d.w, d.w);
-            dup[9 * jj + 8] = make_float4(e.x, e.x, 0.f, 0.f);
-        }
-        __syncthreads();
-        if (t + 1 < t1) load_tile(t + 1);
-        // k as receiver: its cotangents are constant over the tile, so the sums of
-        //   V = ga + alpha r + beta w + gamma gj   and   U = gj + beta r   (times m_m |r|^-3)
-        // are kept as sum(m|r|^-3) ga + sum(m|r|^-3 gamma) gj + sum(m|r|^-3 alpha r)
-        // + sum(m|r|^-3 beta w), and sum(m|r|^-3) gj + sum(m|r|^-3 beta r).
-        float2 s0 = make_float2(0.f, 0.f), s1 = s0, A1[3], B1[3], C1[3], v2[3], u2[3], d2 = s0;
+        s0 = s1 = d2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) A1[c] = B1[c] = C1[c] = v2[c] = u2[c] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int jj = 0; jj < TJ; ++jj) {
-            const float4 q0 = dup[9 * jj], q1 = dup[9 * jj + 1], q2 = dup[9 * jj + 2], q3 = dup[9 * jj + 3],
-                         q4 = dup[9 * jj + 4], q5 = dup[9 * jj + 5], q6 = dup[9 * jj + 6], q7 = dup[9 * jj + 7],
-                         q8 = dup[9 * jj + 8];
-            const float2 XH[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
-            const float2 M = make_float2(q1.z, q1.w);
-            const float2 XL[3] = {make_float2(q2.x, q2.y), make_float2(q2.z, q2.w), make_float2(q3.x, q3.y)};
-            const float2 Sm = make_float2(q3.z, q3.w);
-            const float2 V[3] = {make_float2(q4.x, q4.y), make_float2(q4.z, q4.w), make_float2(q5.x, q5.y)};
-            const float2 GJm[3] = {make_float2(q5.z, q5.w), make_float2(q7.z, q7.w), make_float2(q8.x, q8.y)};
-            const float2 GAm[3] = {make_float2(q6.x, q6.y), make_float2(q6.z, q6.w), make_float2(q7.x, q7.y)};
-            float2 r[3], w[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                r[k] = a2add(a2add(XH[k], nh[k]), a2add(XL[k], nl[k]));
-                w[k] = a2add(V[k], nv[k]);
-            }
-            const float2 r2 = a2fma(r[2], r[2], a2fma(r[1], r[1], a2mul(r[0], r[0])));
-            const float2 rinv = rsqrt_nz(r2);
-            const float2 rinv2 = a2mul(rinv, rinv);
-            const float2 rinv3 = a2mul(rinv, rinv2);
-            const float2 q = a2fma(r[2], w[2], a2fma(r[1], w[1], a2mul(r[0], w[0])));
-            const float2 b3 = a2mul(rinv2, m3);
-            const float2 gamma = a2mul(b3, q);
-            // k as receiver (cotangents of k), source mass m_m
-            {
-                const float2 ar = a2fma(ga[2], r[2], a2fma(ga[1], r[1], a2mul(ga[0], r[0])));
-                const float2 jr = a2fma(gj[2], r[2], a2fma(gj[1], r[1], a2mul(gj[0], r[0])));
-                const float2 jw = a2fma(gj[2], w[2], a2fma(gj[1], w[1], a2mul(gj[0], w[0])));
-                const float2 tt = a2add(ar, jw);
-                const float2 beta = a2mul(b3, jr);
-                const float2 alpha = a2fma(b3, a2fma(m5, a2mul(a2mul(q, jr), rinv2), tt), gs);
-                const float2 rinv3m = a2mul(rinv3, M);
-                s0 = a2add(s0, rinv3m);
-                s1 = a2fma(rinv3m, gamma, s1);
-                const float2 ra = a2mul(rinv3m, alpha), rb = a2mul(rinv3m, beta);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    A1[c] = a2fma(ra, r[c], A1[c]);
-                    B1[c] = a2fma(rb, w[c], B1[c]);
-                    C1[c] = a2fma(rb, r[c], C1[c]);
-                }
-            }
-            // m as receiver (cotangents of m), source k (mass m_k applied per tile)
-            {
-                const float2 P = a2fma(GAm[2], r[2], a2fma(GAm[1], r[1], a2mul(GAm[0], r[0])));
-                const float2 Q = a2fma(GJm[2], r[2], a2fma(GJm[1], r[1], a2mul(GJm[0], r[0])));
-                const float2 R = a2fma(GJm[2], w[2], a2fma(GJm[1], w[1], a2mul(GJm[0], w[0])));
-                const float2 PR = a2add(P, R);
-                const float2 b3Q = a2mul(b3, Q);
-                const float2 E = a2fma(m5, a2mul(a2mul(q, Q), rinv2), PR);
-                // alpha' = s_m - b3 E, applied as -alpha' r
-                const float2 nalpha = a2fma(b3, E, make_float2(-Sm.x, -Sm.y));
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 in = a2fma(gamma, GJm[c], a2fma(b3Q, w[c], a2fma(nalpha, r[c], GAm[c])));
-                    v2[c] = a2fma(rinv3, in, v2[c]);
-                    u2[c] = a2fma(rinv3, a2fma(b3Q, r[c], GJm[c]), u2[c]);
-                }
-                const float2 nd = a2fma(rinv3, a2fma(gamma, Q, PR), a2mul(Sm, rinv));
-                d2 = a2add(d2, make_float2(-nd.x, -nd.y));
-            }
-        }
+    }
+    template <int BLOCK>
+    __device__ __forceinline__ void promote(const float2 (&ga)[3], const float2 (&gj)[3], float2 mk, double *dacc,
+                                            int tid) const
+    {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float2 v1 = a2add(a2fma(ga[c], s0, a2mul(gj[c], s1)), a2add(A1[c], B1[c]));
@@ -607,9 +486,234 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const f
         dacc[12 * BLOCK + tid] += (double)d2.x;
         dacc[13 * BLOCK + tid] += (double)d2.y;
     }
+};
+
+// One pair (row pair k against source m) of the fused pass: separation r = x_m - x_k, w =
+// v_m - v_k, rinv = 1/|r| (0 zeroes every term: the self pair, or a pair handled elsewhere);
+// m's mass M, its cotangents Sm, GAm, GJm; k's cotangents ga, gj, gs.
+__device__ __forceinline__ void adj_fused_pair(const float2 (&r)[3], const float2 (&w)[3], float2 rinv, float2 M,
+                                               float2 Sm, const float2 (&GAm)[3], const float2 (&GJm)[3],
+                                               const float2 (&ga)[3], const float2 (&gj)[3], float2 gs,
+                                               AdjTileSums &S)
+{
+    const float2 m3 = make_float2(-3.f, -3.f), m5 = make_float2(-5.f, -5.f);
+    const float2 rinv2 = a2mul(rinv, rinv);
+    const float2 rinv3 = a2mul(rinv, rinv2);
+    const float2 q = a2fma(r[2], w[2], a2fma(r[1], w[1], a2mul(r[0], w[0])));
+    const float2 b3 = a2mul(rinv2, m3);
+    const float2 gamma = a2mul(b3, q);
+    // k as receiver (cotangents of k), source mass m_m
+    {
+        const float2 ar = a2fma(ga[2], r[2], a2fma(ga[1], r[1], a2mul(ga[0], r[0])));
+        const float2 jr = a2fma(gj[2], r[2], a2fma(gj[1], r[1], a2mul(gj[0], r[0])));
+        const float2 jw = a2fma(gj[2], w[2], a2fma(gj[1], w[1], a2mul(gj[0], w[0])));
+        const float2 tt = a2add(ar, jw);
+        const float2 beta = a2mul(b3, jr);
+        const float2 alpha = a2fma(b3, a2fma(m5, a2mul(a2mul(q, jr), rinv2), tt), gs);
+        const float2 rinv3m = a2mul(rinv3, M);
+        S.s0 = a2add(S.s0, rinv3m);
+        S.s1 = a2fma(rinv3m, gamma, S.s1);
+        const float2 ra = a2mul(rinv3m, alpha), rb = a2mul(rinv3m, beta);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            S.A1[c] = a2fma(ra, r[c], S.A1[c]);
+            S.B1[c] = a2fma(rb, w[c], S.B1[c]);
+            S.C1[c] = a2fma(rb, r[c], S.C1[c]);
+        }
+    }
+    // m as receiver (cotangents of m), source k (mass m_k applied per tile)
+    {
+        const float2 P = a2fma(GAm[2], r[2], a2fma(GAm[1], r[1], a2mul(GAm[0], r[0])));
+        const float2 Q = a2fma(GJm[2], r[2], a2fma(GJm[1], r[1], a2mul(GJm[0], r[0])));
+        const float2 R = a2fma(GJm[2], w[2], a2fma(GJm[1], w[1], a2mul(GJm[0], w[0])));
+        const float2 PR = a2add(P, R);
+        const float2 b3Q = a2mul(b3, Q);
+        const float2 E = a2fma(m5, a2mul(a2mul(q, Q), rinv2), PR);
+        // alpha' = s_m - b3 E, applied as -alpha' r
+        const float2 nalpha = a2fma(b3, E, make_float2(-Sm.x, -Sm.y));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 in = a2fma(gamma, GJm[c], a2fma(b3Q, w[c], a2fma(nalpha, r[c], GAm[c])));
+            S.v2[c] = a2fma(rinv3, in, S.v2[c]);
+            S.u2[c] = a2fma(rinv3, a2fma(b3Q, r[c], GJm[c]), S.u2[c]);
+        }
+        const float2 nd = a2fma(rinv3, a2fma(gamma, Q, PR), a2mul(Sm, rinv));
+        S.d2 = a2add(S.d2, make_float2(-nd.x, -nd.y));
+    }
+}
+
+// ---------------------------------------------------------------- anchored fused pass (mixed)
+// The fused pass with the anchored separations of the forward's anchored kernel: the rows (all
+// particles) are taken in the spatial order perm (Morton order, so a CTA's rows lie close
+// together), every position is measured from one anchor B per CTA (the predicted position of
+// its middle row), e_k = ds(x_k - B) once per row and f_m = ds(x_m - B) once per source and CTA,
+// rounded to FP32, and the separation is the single subtraction f_m - e_k (3 FP32 lane-operations
+// a pair where the double-single difference takes 9).  Its error is at most about
+// 4u |x_k - B| + 3u |r| (u = 2^-24); pairs with |r| below |x_k - B| / 16, where that is not small
+// against |r|, and the self pair (separation exactly zero), are masked out of the loop (inverse
+// distance 0 zeroes every term) and replayed after each 32-source chunk with the double-single
+// separation ((hi - hi) + (lo - lo), as in the forward kernels), so every pair is computed to
+// the double-single accuracy or better.
+// Duplicated tile, nine float4 per source:
+//   {fx,fx,fy,fy} {fz,fz,m,m} {vx,vx,vy,vy} {vz,vz,s,s} {ga0,ga0,ga1,ga1} {ga2,ga2,gj0,gj0}
+//   {gj1,gj1,gj2,gj2} {xh,yh,zh,xl} {yl,zl,0,0}
+// (the loop reads the first seven; the replay also reads the absolute hi/lo position).  The
+// rows' own hi/lo positions are kept in shared memory for the replay.
+template <int BLOCK, int TJ>
+constexpr int adj_anchored_smem()
+{
+    return 5 * TJ * 16 + 9 * TJ * 16 + 7 * 2 * BLOCK * 8 + 6 * 2 * BLOCK * 4;
+}
+
+template <int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+    k_adj_fused_anchored_x2(AdjArgs A, const float4 *__restrict__ crec, const int32_t *__restrict__ perm)
+{
+    extern __shared__ __align__(16) float4 adj_smem[];
+    float4 *raw = adj_smem;                 // 5*TJ
+    float4 *dup = adj_smem + 5 * TJ;        // 9*TJ
+    double *dacc = reinterpret_cast<double *>(adj_smem + 14 * TJ);  // [7][2][BLOCK]
+    float *spos = reinterpret_cast<float *>(dacc + 14 * BLOCK);     // [6][2][BLOCK]: hi xyz, lo xyz
+    __shared__ float s_anchor[6];
+    const int tid = threadIdx.x;
+    const int64_t kbase = (int64_t)blockIdx.x * (2 * BLOCK);
+    const int s = blockIdx.y;
+    const int64_t t0 = (A.n_tiles_j * s) / A.S, t1 = (A.n_tiles_j * (s + 1)) / A.S;
+    if (tid == 0) {  // anchor: the middle row of the CTA's valid rows
+        const int64_t rows = A.n - kbase < 2 * BLOCK ? A.n - kbase : 2 * BLOCK;
+        const int64_t ka = perm[kbase + (rows > 0 ? rows / 2 : 0)];
+        const float4 h = crec[5 * ka], l = crec[5 * ka + 1];
+        s_anchor[0] = h.x; s_anchor[1] = h.y; s_anchor[2] = h.z;
+        s_anchor[3] = l.x; s_anchor[4] = l.y; s_anchor[5] = l.z;
+    }
+    __syncthreads();
+    const float Bh[3] = {s_anchor[0], s_anchor[1], s_anchor[2]}, Bl[3] = {s_anchor[3], s_anchor[4], s_anchor[5]};
+    float2 ne[3], nv[3], ga[3], gj[3], gs, mk, tm;
+    int64_t krow[2];
+    {
+        float4 a[2], b[2], c[2], d[2], e[2];
+        float tmu[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {  // crec is padded to the tile multiple; rows past n are padding
+            const int64_t r = kbase + u * BLOCK + tid;
+            const int64_t k = r < A.n ? perm[r] : r;
+            krow[u] = k;
+            a[u] = crec[5 * k]; b[u] = crec[5 * k + 1]; c[u] = crec[5 * k + 2];
+            d[u] = crec[5 * k + 3]; e[u] = crec[5 * k + 4];
+            const float ex = ds_diff(a[u].x, b[u].x, Bh[0], Bl[0]);
+            const float ey = ds_diff(a[u].y, b[u].y, Bh[1], Bl[1]);
+            const float ez = ds_diff(a[u].z, b[u].z, Bh[2], Bl[2]);
+            const int slot = u * BLOCK + tid;
+            spos[0 * 2 * BLOCK + slot] = a[u].x; spos[1 * 2 * BLOCK + slot] = a[u].y; spos[2 * 2 * BLOCK + slot] = a[u].z;
+            spos[3 * 2 * BLOCK + slot] = b[u].x; spos[4 * 2 * BLOCK + slot] = b[u].y; spos[5 * 2 * BLOCK + slot] = b[u].z;
+            if (u == 0) { ne[0].x = -ex; ne[1].x = -ey; ne[2].x = -ez; }
+            else { ne[0].y = -ex; ne[1].y = -ey; ne[2].y = -ez; }
+            tmu[u] = r < A.n ? fmaxf(r2_f32(ex, ey, ez) * (1.f / 256.f), 1.17549435e-38f) : -1.f;
+        }
+        mk = make_float2(a[0].w, a[1].w);
+        gs = make_float2(b[0].w, b[1].w);
+        nv[0] = make_float2(-c[0].x, -c[1].x); nv[1] = make_float2(-c[0].y, -c[1].y);
+        nv[2] = make_float2(-c[0].z, -c[1].z); gj[0] = make_float2(c[0].w, c[1].w);
+        ga[0] = make_float2(d[0].x, d[1].x); ga[1] = make_float2(d[0].y, d[1].y);
+        ga[2] = make_float2(d[0].z, d[1].z); gj[1] = make_float2(d[0].w, d[1].w);
+        gj[2] = make_float2(e[0].x, e[1].x);
+        tm = make_float2(tmu[0], tmu[1]);
+    }
+#pragma unroll
+    for (int e = 0; e < 14; ++e) dacc[e * BLOCK + tid] = 0.0;
+    auto load_tile = [&](int64_t t) {
+        const float4 *src = crec + t * (5 * TJ);
+#pragma unroll
+        for (int e = tid; e < 5 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
+        cp_async_commit();
+    };
+    if (t0 < t1) load_tile(t0);
+    for (int64_t t = t0; t < t1; ++t) {
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll
+        for (int jj = tid; jj < TJ; jj += BLOCK) {
+            const float4 a = raw[5 * jj], b = raw[5 * jj + 1], c = raw[5 * jj + 2], d = raw[5 * jj + 3],
+                         e = raw[5 * jj + 4];
+            const float fx = ds_diff(a.x, b.x, Bh[0], Bl[0]);
+            const float fy = ds_diff(a.y, b.y, Bh[1], Bl[1]);
+            const float fz = ds_diff(a.z, b.z, Bh[2], Bl[2]);
+            dup[9 * jj] = make_float4(fx, fx, fy, fy);
+            dup[9 * jj + 1] = make_float4(fz, fz, a.w, a.w);
+            dup[9 * jj + 2] = make_float4(c.x, c.x, c.y, c.y);
+            dup[9 * jj + 3] = make_float4(c.z, c.z, b.w, b.w);
+            dup[9 * jj + 4] = make_float4(d.x, d.x, d.y, d.y);
+            dup[9 * jj + 5] = make_float4(d.z, d.z, c.w, c.w);
+            dup[9 * jj + 6] = make_float4(d.w, d.w, e.x, e.x);
+            dup[9 * jj + 7] = make_float4(a.x, a.y, a.z, b.x);
+            dup[9 * jj + 8] = make_float4(b.y, b.z, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (t + 1 < t1) load_tile(t + 1);
+        AdjTileSums S;
+        S.zero();
+        for (int jc = 0; jc < TJ; jc += 32) {
+            const float4 *sc = dup + 9 * jc;
+            unsigned hm0 = 0, hm1 = 0;
+#pragma unroll 2
+            for (int u = 0; u < 32; ++u) {
+                const float4 q0 = sc[9 * u], q1 = sc[9 * u + 1], q2 = sc[9 * u + 2], q3 = sc[9 * u + 3],
+                             q4 = sc[9 * u + 4], q5 = sc[9 * u + 5], q6 = sc[9 * u + 6];
+                const float2 M = make_float2(q1.z, q1.w), Sm = make_float2(q3.z, q3.w);
+                const float2 GAm[3] = {make_float2(q4.x, q4.y), make_float2(q4.z, q4.w), make_float2(q5.x, q5.y)};
+                const float2 GJm[3] = {make_float2(q5.z, q5.w), make_float2(q6.x, q6.y), make_float2(q6.z, q6.w)};
+                float2 r[3], w[3];
+                r[0] = a2add(make_float2(q0.x, q0.y), ne[0]);
+                r[1] = a2add(make_float2(q0.z, q0.w), ne[1]);
+                r[2] = a2add(make_float2(q1.x, q1.y), ne[2]);
+                w[0] = a2add(make_float2(q2.x, q2.y), nv[0]);
+                w[1] = a2add(make_float2(q2.z, q2.w), nv[1]);
+                w[2] = a2add(make_float2(q3.x, q3.y), nv[2]);
+                const float2 r2 = a2fma(r[2], r[2], a2fma(r[1], r[1], a2mul(r[0], r[0])));
+                const bool m0 = r2.x < tm.x, m1 = r2.y < tm.y;
+                hm0 |= (unsigned)m0 << u;
+                hm1 |= (unsigned)m1 << u;
+                float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                rinv.x = m0 ? 0.f : rinv.x;
+                rinv.y = m1 ? 0.f : rinv.y;
+                adj_fused_pair(r, w, rinv, M, Sm, GAm, GJm, ga, gj, gs, S);
+            }
+            // masked pairs: the double-single separation, one row of the pair at a time
+            unsigned hm = hm0 | hm1;
+            while (hm) {
+                const int u = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const float4 q0 = sc[9 * u + 1], q2 = sc[9 * u + 2], q3 = sc[9 * u + 3], q4 = sc[9 * u + 4],
+                             q5 = sc[9 * u + 5], q6 = sc[9 * u + 6], q7 = sc[9 * u + 7], q8 = sc[9 * u + 8];
+                const float2 M = make_float2(q0.z, q0.w), Sm = make_float2(q3.z, q3.w);
+                const float2 GAm[3] = {make_float2(q4.x, q4.y), make_float2(q4.z, q4.w), make_float2(q5.x, q5.y)};
+                const float2 GJm[3] = {make_float2(q5.z, q5.w), make_float2(q6.x, q6.y), make_float2(q6.z, q6.w)};
+                const float jh[3] = {q7.x, q7.y, q7.z}, jl[3] = {q7.w, q8.x, q8.y};
+                float2 w[3];
+                w[0] = a2add(make_float2(q2.x, q2.y), nv[0]);
+                w[1] = a2add(make_float2(q2.z, q2.w), nv[1]);
+                w[2] = a2add(make_float2(q3.x, q3.y), nv[2]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!(((h ? hm1 : hm0) >> u) & 1u)) continue;
+                    const int slot = h * BLOCK + tid;
+                    float2 r[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float d = ds_diff(jh[c], jl[c], spos[c * 2 * BLOCK + slot], spos[(3 + c) * 2 * BLOCK + slot]);
+                        r[c] = make_float2(d, d);
+                    }
+                    const float r2 = r2_f32(r[0].x, r[1].x, r[2].x);
+                    const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;  // the self pair has r = 0
+                    adj_fused_pair(r, w, h ? make_float2(0.f, ri) : make_float2(ri, 0.f), M, Sm, GAm, GJm, ga, gj, gs, S);
+                }
+            }
+        }
+        S.promote<BLOCK>(ga, gj, mk, dacc, tid);
+    }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-        const int64_t k = kbase + u * BLOCK + tid;
+        const int64_t k = krow[u];
         if (k < A.n)
 #pragma unroll
             for (int c = 0; c < 7; ++c) A.part[((int64_t)s * 7 + c) * A.n + k] = dacc[(c * 2 + u) * BLOCK + tid];
@@ -617,7 +721,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_adj_fused_x2(AdjArgs A, const f
 }
 
 // ---------------------------------------------------------------- fused single pass (FP64)
-// The same pair algebra as k_adj_fused_x2, in FP64 with one row per thread and the sums kept
+// The same pair algebra as the mixed fused pass (adj_fused_pair), in FP64 with one row per thread and the sums kept
 // in FP64 registers.  Records (four dvec4):
 //   {x,y,z,m} {vx,vy,vz,s} {ga0,ga1,ga2,gj0} {gj1,gj2,0,0}
 __global__ void k_build_crec64(int64_t n, int64_t n_pad, const dvec4 *__restrict__ rec, dvec4 *__restrict__ crec)
@@ -667,7 +771,7 @@ __global__ void __launch_bounds__(BLOCK) k_adj_fused_f64(AdjArgs A, const dvec4 
     const dvec4 a = crec[4 * k], b = crec[4 * k + 1], c = crec[4 * k + 2], d = crec[4 * k + 3];
     const double xk[3] = {a.x, a.y, a.z}, vk[3] = {b.x, b.y, b.z}, ga[3] = {c.x, c.y, c.z}, gj[3] = {c.w, d.x, d.y};
     const double mk = a.w, gs = b.w;
-    // k as receiver: its cotangents factor out of the j-sums (see k_adj_fused_x2)
+    // k as receiver: its cotangents factor out of the j-sums (see AdjTileSums)
     double s0 = 0.0, s1 = 0.0, A1[3] = {0, 0, 0}, B1[3] = {0, 0, 0}, C1[3] = {0, 0, 0};
     // m as receiver
     double v2[3] = {0, 0, 0}, u2[3] = {0, 0, 0}, d2 = 0.0;
@@ -990,10 +1094,19 @@ static size_t adjoint_core_bytes(int precision, int64_t n, int64_t n_i, int num_
     size_t need = irec + 256 + pa + 256 + pb;
     if (use_fused(precision, n, n_i)) {
         const FusedGeom f = fused_geom(precision, n, num_sms);
-        const size_t fb = fused_rec_bytes(precision, f.n_pad) + 256 + (size_t)f.S * 7 * (size_t)n * 8;
+        size_t fb = fused_rec_bytes(precision, f.n_pad) + 256 + (size_t)f.S * 7 * (size_t)n * 8;
+        if (precision == 1) fb = ((fb + 255) & ~(size_t)255) + roworder_scratch_bytes(n);  // row order
         if (fb > need) need = fb;
     }
     return need;
+}
+
+// Dynamic shared-memory limit of the anchored fused pass (just above the 48 KB default).
+void adjoint_configure()
+{
+    cudaFuncSetAttribute((const void *)k_adj_fused_anchored_x2<kFusedBlock, kFusedTJ, 3>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, adj_anchored_smem<kFusedBlock, kFusedTJ>());
+    cudaGetLastError();
 }
 
 int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx, int64_t n_i,
@@ -1025,13 +1138,20 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
         A.S = f.S;
         A.part = part;
         A.status = status;
+        int order_kernels = 0;
         if (precision == 1) {
             float4 *crec = static_cast<float4 *>(scratch);
             k_build_crec<<<(unsigned)gr, 256, 0, st>>>(n, f.n_pad, static_cast<const float4 *>(rec), crec);
             k_scatter_cotangents<<<(unsigned)gq, 256, 0, st>>>(n, n_i, idx, g_acc, g_jerk, g_pot,
                                                                reinterpret_cast<float *>(crec), status);
-            k_adj_fused_x2<kFusedBlock, kFusedTJ, 3><<<dim3((unsigned)f.ctas, (unsigned)f.S), kFusedBlock,
-                                                       adj_fused_smem<kFusedBlock, kFusedTJ>(), st>>>(A, crec);
+            // every particle is a row: spatial order of all of them, then the anchored pass
+            const size_t fb = fused_rec_bytes(precision, f.n_pad) + 256 + (size_t)f.S * 7 * (size_t)n * 8;
+            void *ro = static_cast<char *>(scratch) + ((fb + 255) & ~(size_t)255);
+            const int32_t *perm = nullptr;
+            order_kernels = launch_row_order(st, rec, nullptr, n, n, ro, &perm);
+            k_adj_fused_anchored_x2<kFusedBlock, kFusedTJ, 3>
+                <<<dim3((unsigned)f.ctas, (unsigned)f.S), kFusedBlock, adj_anchored_smem<kFusedBlock, kFusedTJ>(),
+                   st>>>(A, crec, perm);
         } else {
             dvec4 *crec = static_cast<dvec4 *>(scratch);
             k_build_crec64<<<(unsigned)gr, 256, 0, st>>>(n, f.n_pad, static_cast<const dvec4 *>(rec), crec);
@@ -1043,7 +1163,7 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
         int64_t gj = (n + 255) / 256;
         if (gj > 152 * 16) gj = 152 * 16;
         k_adj_combine_j<<<(unsigned)gj, 256, 0, st>>>(part, f.S, n, g_x, g_v, g_m);
-        return 5;
+        return 5 + order_kernels;
     }
     const AdjGeom g = adj_geom(precision, n, n_i, num_sms);
     char *p = static_cast<char *>(scratch);

@@ -42,6 +42,7 @@ void *fp64_tiled_fn();
 int fp64_jstream_ib(int v);
 void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
 void launch_force_fp64(cudaStream_t st, int kernel, int variant, int64_t ctas_x, int S, ForceArgs a);
+void adjoint_configure();
 size_t adjoint_scratch_bytes(int precision, int64_t n, int64_t n_i, int num_sms, int64_t *rows_pad_out, int *SA,
                              int *SB);
 int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, const int32_t *idx, int64_t n_i,
@@ -391,6 +392,7 @@ void query_occupancy(int *occ)
 {
     mixed_tiled_configure();
     roworder_configure();
+    adjoint_configure();
     for (int v = 0; v < kMixedTiledVariants; ++v) {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mixed_tiled_fn(v), mixed_tiled_block(v),

@@ -55,8 +55,9 @@ __device__ __forceinline__ uint32_t ro_spread(uint32_t a)
 
 struct RoRows {
     const float4 *rec;   // mixed j-records (x_hi in the first float4 of each particle)
-    const int32_t *idx;  // active indices
+    const int32_t *idx;  // active indices; null: row r is particle r (n_i = n)
     int64_t n, n_i;
+    __device__ __forceinline__ int64_t particle(int64_t r) const { return idx ? (int64_t)idx[r] : r; }
 };
 
 // The bounding box is kept as ordered unsigned images, the minimum complemented, so that both
@@ -75,7 +76,7 @@ __device__ __forceinline__ void ro_frame(const unsigned *box, float (&lo)[3], fl
 
 __device__ __forceinline__ uint32_t ro_key(const RoRows &R, int64_t r, const float (&lo)[3], const float (&inv)[3])
 {
-    const int64_t g = R.idx[r];
+    const int64_t g = R.particle(r);
     if (g < 0 || g >= R.n) return kRoBadKey;
     const float4 p = R.rec[3 * g];
     const float x[3] = {p.x, p.y, p.z};
@@ -108,7 +109,7 @@ __device__ void ro_box_rows(const RoRows &R, int64_t r0, int64_t r1, int64_t str
 {
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t r = r0; r < r1; r += stride) {
-        const int64_t g = R.idx[r];
+        const int64_t g = R.particle(r);
         if (g < 0 || g >= R.n) continue;
         const float4 p = R.rec[3 * g];
         mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);

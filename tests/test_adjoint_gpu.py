@@ -42,6 +42,35 @@ def gpu_vjp(ctx, cl, idx, ga, gj, gp):
     return gx.cpu().numpy(), gv.cpu().numpy(), gm.cpu().numpy()
 
 
+def test_mixed_fused_backward_with_close_pairs(gpu_lib):
+    """Dense block (the fused pass, anchored separations) on a Plummer sphere with a tight pair
+    planted next to every 40th particle, 1e-6 to 1e-3 apart, the cluster far from the origin:
+    the pairs too close for the anchored separation are masked and replayed in double-single
+    form, so the mixed bars against the oracle VJP hold."""
+    cl = W.plummer(4000, 79, masses="kroupa")
+    rng = np.random.default_rng(79)
+    near = np.arange(0, 4000, 40)
+    d = rng.standard_normal((near.size, 3))
+    d *= (10.0 ** rng.uniform(-6, -3, near.size) / np.linalg.norm(d, axis=1))[:, None]
+
+    class C:
+        pass
+    c = C()
+    c.x = np.concatenate([cl.x, cl.x[near] + d]) + np.array([300.0, -200.0, 50.0])
+    c.v = np.concatenate([cl.v, cl.v[near] + 0.1 * rng.standard_normal((near.size, 3))])
+    c.m = np.concatenate([cl.m, cl.m[near]])
+    n = c.x.shape[0]
+    idx = rng.permutation(n).astype(np.int32)
+    ga, gj, gp = rng.standard_normal((n, 3)), rng.standard_normal((n, 3)), rng.standard_normal(n)
+    ref = oracle.regular_force_vjp(c.x, c.v, c.m, idx, ga, gj, gp)
+    ctx = make_ctx(n, "mixed")
+    got = gpu_vjp(ctx, c, idx, ga, gj, gp)
+    ctx.close()
+    for q in range(3):
+        e = row_err(got[q], ref[q])
+        assert np.median(e) <= 2e-5 and e.max() <= 1e-3, (q, float(np.median(e)), float(e.max()))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("n,n_i", [(1000, 900), (1000, 137)])  # the fused pass and the two passes
 def test_backward_rejects_duplicate_indices_and_is_reproducible(gpu_lib, prec, n, n_i):

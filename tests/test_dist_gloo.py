@@ -220,3 +220,58 @@ def test_rank_leaving_between_steps_is_detected_by_heartbeat():
     lost = [m for m in msgs if m[0] == "lost"]
     assert len(lost) == 1 and lost[0][1] == 0 and lost[0][2] == 1
     assert not any(m[0] == "step" and m[2] >= 1 for m in msgs)
+
+def _bench_worker(rank, world, port, out):
+    """The benchmark's copy-algorithm step on gloo ranks, the oracle standing in for the
+    device call: every rank computes its share of the rows of three blocks and the results
+    are all-gathered."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        blocks, force = _bench_problem()
+        res = bench.copy_algorithm_step(blocks, [force] * len(blocks), world, rank)
+        if rank == 0:
+            out.put([[t.numpy() for t in r] for r in res])
+    finally:
+        dist.destroy_process_group()
+
+
+def _bench_problem():
+    cl, rs2 = W.plummer_1k_equal()
+    order = W.sorted_step_list(W.block_steps(cl, seed=0)).astype(np.int32)
+    blocks = [order[:b] for b in (1, 37, 300)]
+
+    def force(rows):
+        a, j, p, cnt, lists = oracle.regular_force(cl.x, cl.v, cl.m, np.asarray(rows), rs2, cap=64)
+        off = np.zeros(len(rows) + 1, np.int64)
+        off[1:] = np.cumsum([len(l) for l in lists])
+        flat = np.concatenate(lists).astype(np.int32) if len(lists) else np.zeros(0, np.int32)
+        return tuple(torch.from_numpy(np.ascontiguousarray(t)) for t in (a, j, p, off, flat))
+    return blocks, force
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_bench_copy_algorithm_step_matches_one_rank(world):
+    """bench.py's timed step under torchrun (row-sharded copy algorithm, all-gather of the row
+    results) gives every block exactly as one rank computing all rows does."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = q.get(timeout=120)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    blocks, force = _bench_problem()
+    one = bench.copy_algorithm_step(blocks, [force] * len(blocks), 1, 0)
+    assert len(got) == len(one) == 3
+    for g, o in zip(got, one):
+        for a, b in zip(g, o):
+            np.testing.assert_array_equal(a, b.numpy())

@@ -209,9 +209,10 @@ nb_status nb_irregular_force(nb_ctx *ctx, double t, int64_t n_i, const int32_t *
  * bracketed by CUDA events on the context stream.  nb_get_timings synchronises the
  * stream and returns, per phase, the summed device time in ms and the number of kernels
  * launched since the previous nb_get_timings (launch counts are kept even with timing
- * off), then resets both.  Phases: 0 predict, 1 force, 2 partial reduction,
- * 3 neighbour CSR, 4 backward, 5 irregular force, 6 row order (the spatial order of the
- * active rows that the anchored force kernel takes).  ms and launches have NB_PHASES
+ * off), then resets both.  Phases: 0 predict (and the array predictor and corrector),
+ * 1 force, 2 partial reduction, 3 neighbour CSR, 4 backward (and the predictor's and the
+ * corrector's VJPs), 5 irregular force, 6 row order (the spatial order of the active rows
+ * that the anchored force kernel takes).  ms and launches have NB_PHASES
  * entries each. */
 #define NB_PHASES 7
 nb_status nb_set_timing(nb_ctx *ctx, int32_t enable);
@@ -239,6 +240,45 @@ nb_status nb_inject_fault(nb_ctx *ctx, int32_t kind, int32_t after);
 
 /* One-line description of the last error on this context (never NULL). */
 const char *nb_last_error(const nb_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * The Hermite predictor and corrector over caller arrays, and their vector-Jacobian
+ * products: the O(N) steps of a block-step integration that a differentiable chain of block
+ * steps (predictor -> nb_regular_force -> corrector) runs between force calls, and runs
+ * backwards for its gradient (Sec. 2: the fourth-order Hermite scheme after Makino 1991;
+ * Sec. 3.3.3: prediction).  All arrays are device arrays, (n,3) row-major for vectors and (n)
+ * for t_last; the calls are asynchronous on the context stream and read no context state.
+ * Outputs are overwritten (and must not alias inputs).  NB_ERR_ARG for n < 0 or a null array
+ * (n = 0 does nothing).  t and t_last are not differentiated.
+ * --------------------------------------------------------------------------------------- */
+
+/* Predict to time t: dt_k = t - t_last[k], xp = x + dt (v + dt/2 (a + dt/3 jerk)),
+ * vp = v + dt (a + dt/2 jerk), in the same operation order as nb_predict (bit-identical). */
+nb_status nb_hermite_predict(nb_ctx *ctx, int64_t n, double t, const double *x, const double *v,
+                             const double *a, const double *jerk, const double *t_last, double *xp,
+                             double *vp);
+
+/* VJP of nb_hermite_predict: g_x = g_xp, g_v = dt g_xp + g_vp, g_a = dt^2/2 g_xp + dt g_vp,
+ * g_jerk = dt^3/6 g_xp + dt^2/2 g_vp. */
+nb_status nb_hermite_predict_backward(nb_ctx *ctx, int64_t n, double t, const double *t_last,
+                                      const double *g_xp, const double *g_vp, double *g_x, double *g_v,
+                                      double *g_a, double *g_jerk);
+
+/* Fourth-order Hermite corrector of n rows stepping from t_last[k] to t (h = t - t_last[k] > 0):
+ * a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2, a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3,
+ * x1 = xp + h^4/24 a2 + h^5/120 a3, v1 = vp + h^3/6 a2 + h^4/24 a3, with xp, vp the predicted
+ * state, a0, j0 the force and jerk at t_last and a1, j1 at t (the operation order of that
+ * definition, without FMA contraction: the same arithmetic as the device integrator). */
+nb_status nb_hermite_correct(nb_ctx *ctx, int64_t n, double t, const double *t_last, const double *xp,
+                             const double *vp, const double *a0, const double *j0, const double *a1,
+                             const double *j1, double *x1, double *v1);
+
+/* VJP of nb_hermite_correct (the corrector is linear in its inputs): g_xp = g_x1, g_vp = g_v1,
+ * g_a0 = -3h^2/20 g_x1 - h/2 g_v1, g_j0 = -7h^3/60 g_x1 - 5h^2/12 g_v1, g_a1 = -g_a0,
+ * g_j1 = -h^3/30 g_x1 - h^2/12 g_v1. */
+nb_status nb_hermite_correct_backward(nb_ctx *ctx, int64_t n, double t, const double *t_last,
+                                      const double *g_x1, const double *g_v1, double *g_xp, double *g_vp,
+                                      double *g_a0, double *g_j0, double *g_a1, double *g_j1);
 
 /* Spatial order of an active block's rows: the permutation that the anchored mixed force
  * kernel (plan variants 10-14) takes before it runs, and that a caller may use to lay out its

@@ -33,9 +33,15 @@ EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particle
            "nb_sched_next", "nb_sched_update", "nb_sched_get", "nb_sched_counts", "nb_sched_last_error",
            "nb_sched_peek", "nb_ac_init", "nb_ac_step", "nb_ac_run", "nb_ac_get", "nb_ac_free", "nb_ac_last_error",
            "nb_inject_fault", "nb_sched_set_time", "nb_ac_snapshot_bytes", "nb_ac_save", "nb_ac_restore",
-           "nb_row_order")
+           "nb_row_order", "nb_hermite_predict", "nb_hermite_predict_backward", "nb_hermite_correct",
+           "nb_hermite_correct_backward")
 NB_FAULT_ALLOC, NB_FAULT_SYNC, NB_FAULT_STATUS = 1, 2, 3
 NB_SOURCE_ALIGN = 256
+
+
+def _torch():
+    import torch
+    return torch
 
 
 class NBError(RuntimeError):
@@ -88,6 +94,10 @@ def load_library(build_if_needed: bool = True):
         "nb_last_error": (ctypes.c_char_p, [P]),
         "nb_plan": (st, [P, i64, i64, P]),
         "nb_row_order": (st, [P, i64, P, P]),
+        "nb_hermite_predict": (st, [P, i64, dbl, P, P, P, P, P, P, P]),
+        "nb_hermite_predict_backward": (st, [P, i64, dbl, P, P, P, P, P, P, P]),
+        "nb_hermite_correct": (st, [P, i64, dbl, P, P, P, P, P, P, P, P, P]),
+        "nb_hermite_correct_backward": (st, [P, i64, dbl, P, P, P, P, P, P, P, P, P]),
         "nb_plan_for": (st, [i32, i32, P, i64, i64, i32, P]),
         "nb_set_plan_override": (st, [P, i32, i32, i32]),
         "nb_batch_plan": (st, [P, i64, P, P, i32]),
@@ -373,6 +383,49 @@ class Context:
 
     def sync(self, allow_overflow: bool = True) -> int:
         return self._check(self.lib.nb_sync(self.h), "nb_sync", allow_overflow)
+
+    # ---- Hermite predictor / corrector over device arrays, and their VJPs ----------------
+    @staticmethod
+    def _dev64(*ts):
+        for t in ts:
+            if not (t.is_cuda and t.dtype == _torch().float64 and t.is_contiguous()):
+                raise ValueError("Hermite arrays must be contiguous float64 device tensors")
+
+    def hermite_predict(self, t: float, x, v, a, jerk, t_last):
+        """nb_hermite_predict: (xp, vp) at time t of the (n,3) states, t_last (n)."""
+        self._dev64(x, v, a, jerk, t_last)
+        xp, vp = _torch().empty_like(x), _torch().empty_like(v)
+        self._check(self.lib.nb_hermite_predict(self.h, x.shape[0], float(t), x.data_ptr(), v.data_ptr(), a.data_ptr(),
+                                                jerk.data_ptr(), t_last.data_ptr(), xp.data_ptr(), vp.data_ptr()),
+                    "nb_hermite_predict")
+        return xp, vp
+
+    def hermite_predict_backward(self, t: float, t_last, g_xp, g_vp):
+        """nb_hermite_predict_backward: (g_x, g_v, g_a, g_jerk)."""
+        self._dev64(t_last, g_xp, g_vp)
+        out = [_torch().empty_like(g_xp) for _ in range(4)]
+        self._check(self.lib.nb_hermite_predict_backward(self.h, g_xp.shape[0], float(t), t_last.data_ptr(),
+                                                         g_xp.data_ptr(), g_vp.data_ptr(),
+                                                         *[o.data_ptr() for o in out]), "nb_hermite_predict_backward")
+        return tuple(out)
+
+    def hermite_correct(self, t: float, t_last, xp, vp, a0, j0, a1, j1):
+        """nb_hermite_correct: (x1, v1) of rows stepping from t_last (n) to t."""
+        self._dev64(t_last, xp, vp, a0, j0, a1, j1)
+        x1, v1 = _torch().empty_like(xp), _torch().empty_like(vp)
+        self._check(self.lib.nb_hermite_correct(self.h, xp.shape[0], float(t), t_last.data_ptr(), xp.data_ptr(),
+                                                vp.data_ptr(), a0.data_ptr(), j0.data_ptr(), a1.data_ptr(),
+                                                j1.data_ptr(), x1.data_ptr(), v1.data_ptr()), "nb_hermite_correct")
+        return x1, v1
+
+    def hermite_correct_backward(self, t: float, t_last, g_x1, g_v1):
+        """nb_hermite_correct_backward: (g_xp, g_vp, g_a0, g_j0, g_a1, g_j1)."""
+        self._dev64(t_last, g_x1, g_v1)
+        out = [_torch().empty_like(g_x1) for _ in range(6)]
+        self._check(self.lib.nb_hermite_correct_backward(self.h, g_x1.shape[0], float(t), t_last.data_ptr(),
+                                                         g_x1.data_ptr(), g_v1.data_ptr(),
+                                                         *[o.data_ptr() for o in out]), "nb_hermite_correct_backward")
+        return tuple(out)
 
     def row_order(self, idx):
         """nb_row_order: the spatial (Morton) order of the rows idx (device int32 tensor) that

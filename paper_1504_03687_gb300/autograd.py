@@ -1,14 +1,18 @@
-"""torch.autograd binding of the regular-force step and its hand-written adjoint.
+"""torch.autograd binding of the regular-force step, the Hermite predictor and corrector, and
+their hand-written adjoints.
 
 RegularForce.apply(xp, vp, m, idx, rs2, ctx) -> (acc, jerk, pot): the forward runs
 nb_set_predicted + nb_regular_force (no neighbour lists); the backward runs
 nb_set_predicted on the saved state + nb_regular_force_backward, the CUDA VJP
 kernels.  Gradients flow to xp, vp and m (all particles).
 
-hermite_chain(...) composes the fourth-order Hermite predictor/corrector (plain
-torch FP64 tensor ops, O(N) per step) with RegularForce over K block steps of a
-frozen schedule, with torch.utils.checkpoint segments, to differentiate a final-
-state observable with respect to the initial conditions.
+Predict / Correct: nb_hermite_predict and nb_hermite_correct forward, their VJP kernels
+(nb_hermite_predict_backward, nb_hermite_correct_backward) backward.
+
+hermite_chain(...) composes them with RegularForce over K block steps of a frozen schedule,
+with torch.utils.checkpoint segments, to differentiate a final-state observable with respect
+to the initial conditions.  This module only marshals tensors between library calls (row
+gathers and scatters of the active set); every arithmetic step runs in the library.
 """
 from __future__ import annotations
 
@@ -43,37 +47,55 @@ def regular_force(xp, vp, m, idx, nbctx, rs2=0.0):
 
 
 # ------------------------------------------------------------------------------------------
-def predict(x, v, a, j, dt):
-    """Hermite predictor to the block time (Taylor series to the jerk term)."""
-    dt = dt[:, None]
-    xp = x + v * dt + a * dt * dt / 2 + j * dt * dt * dt / 6
-    vp = v + a * dt + j * dt * dt / 2
-    return xp, vp
+def _or_zeros(g, like):
+    return g.contiguous() if g is not None else like.new_zeros(like.shape)
 
 
-def correct(xp, vp, a0, j0, a1, j1, h):
-    """Fourth-order Hermite corrector for a step of length h (per row)."""
-    h = h[:, None]
-    da = a0 - a1
-    a2 = (-6 * da - h * (4 * j0 + 2 * j1)) / (h * h)
-    a3 = (12 * da + 6 * h * (j0 + j1)) / (h * h * h)
-    x1 = xp + h ** 4 / 24 * a2 + h ** 5 / 120 * a3
-    v1 = vp + h ** 3 / 6 * a2 + h ** 4 / 24 * a3
-    return x1, v1
+class Predict(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, v, a, j, t_last, t, nbctx):
+        xp, vp = nbctx.hermite_predict(t, x.detach().contiguous(), v.detach().contiguous(), a.detach().contiguous(),
+                                       j.detach().contiguous(), t_last.contiguous())
+        ctx.save_for_backward(t_last)
+        ctx.t, ctx.nbctx = t, nbctx
+        return xp, vp
+
+    @staticmethod
+    def backward(ctx, g_xp, g_vp):
+        (t_last,) = ctx.saved_tensors
+        like = t_last.new_zeros((t_last.shape[0], 3))
+        gx, gv, ga, gj = ctx.nbctx.hermite_predict_backward(ctx.t, t_last, _or_zeros(g_xp, like), _or_zeros(g_vp, like))
+        return gx, gv, ga, gj, None, None, None
+
+
+class Correct(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xp, vp, a0, j0, a1, j1, t_last, t, nbctx):
+        d = lambda q: q.detach().contiguous()
+        x1, v1 = nbctx.hermite_correct(t, t_last.contiguous(), d(xp), d(vp), d(a0), d(j0), d(a1), d(j1))
+        ctx.save_for_backward(t_last)
+        ctx.t, ctx.nbctx = t, nbctx
+        return x1, v1
+
+    @staticmethod
+    def backward(ctx, g_x1, g_v1):
+        (t_last,) = ctx.saved_tensors
+        like = t_last.new_zeros((t_last.shape[0], 3))
+        grads = ctx.nbctx.hermite_correct_backward(ctx.t, t_last, _or_zeros(g_x1, like), _or_zeros(g_v1, like))
+        return (*grads, None, None, None)
 
 
 def block_step(state, m, active, t_next, nbctx):
     """One block step of a frozen schedule: predict all, force on the active set, correct it.
 
     state = (x, v, a, j, t_last); t_last (FP64, not differentiated) gives each active
-    particle's step h = t_next - t_last.
+    particle's step t_next - t_last.
     """
     x, v, a, j, t_last = state
-    xp, vp = predict(x, v, a, j, t_next - t_last)
+    xp, vp = Predict.apply(x, v, a, j, t_last, float(t_next), nbctx)
     a1, j1, _ = regular_force(xp, vp, m, active, nbctx)
     act = active.long()
-    h = t_next - t_last[act]
-    x1, v1 = correct(xp[act], vp[act], a[act], j[act], a1, j1, h)
+    x1, v1 = Correct.apply(xp[act], vp[act], a[act], j[act], a1, j1, t_last[act].contiguous(), float(t_next), nbctx)
     x = x.index_copy(0, act, x1)
     v = v.index_copy(0, act, v1)
     a = a.index_copy(0, act, a1)

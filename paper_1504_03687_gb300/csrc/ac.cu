@@ -233,11 +233,10 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
             const int64_t q = 3 * i + c;
             double xp, vp;
             hermite_taylor(D.x[q], D.v[q], D.a[q], D.jk[q], h, xp, vp);
-            const double da = D.a[q] - a1[c];
-            a2[c] = (-6.0 * da - h * (4.0 * D.jk[q] + 2.0 * j1[c])) / (h * h);
-            a3[c] = (12.0 * da + 6.0 * h * (D.jk[q] + j1[c])) / (h * h * h);
-            D.x[q] = xp + h * h * h * h / 24.0 * a2[c] + h * h * h * h * h / 120.0 * a3[c];
-            D.v[q] = vp + h * h * h / 6.0 * a2[c] + h * h * h * h / 24.0 * a3[c];
+            double x1, v1;
+            hermite_correct(xp, vp, D.a[q], D.jk[q], a1[c], j1[c], h, x1, v1, a2[c], a3[c]);
+            D.x[q] = x1;
+            D.v[q] = v1;
             D.a[q] = a1[c];
             D.jk[q] = j1[c];
             a2e[c] = a2[c] + h * a3[c];

@@ -18,6 +18,8 @@
 #include <new>
 #include <vector>
 
+#include <initializer_list>
+
 #include "nbgpu.h"
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
@@ -686,6 +688,67 @@ nb_status nb_set_plan_table(nb_ctx *c, int32_t n_entries, const int64_t *ni_max,
         t.push_back({ni_max[q], kernel[q], variant[q], splits[q]});
     }
     c->table.swap(t);
+    return NB_OK;
+}
+
+// ---- Hermite predictor / corrector over caller arrays (differentiable integration) -------
+static nb_status hermite_args(nb_ctx *c, int64_t n, std::initializer_list<const void *> arrays)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (n < 0) return fail(c, NB_ERR_ARG, "n=%lld out of range", (long long)n);
+    for (const void *p : arrays)
+        if (n > 0 && !p) return fail(c, NB_ERR_ARG, "null array");
+    return NB_OK;
+}
+
+nb_status nb_hermite_predict(nb_ctx *c, int64_t n, double t, const double *x, const double *v, const double *a,
+                             const double *jerk, const double *t_last, double *xp, double *vp)
+{
+    nb_status s = hermite_args(c, n, {x, v, a, jerk, t_last, xp, vp});
+    if (s != NB_OK || n == 0) return s;
+    cudaEvent_t t0 = span_begin(c);
+    launch_hermite_predict(c->stream, n, t, x, v, a, jerk, t_last, xp, vp);
+    CK_LAUNCH("k_hermite_predict launch");
+    span_end(c, PH_PREDICT, t0, 1);
+    return NB_OK;
+}
+
+nb_status nb_hermite_predict_backward(nb_ctx *c, int64_t n, double t, const double *t_last, const double *g_xp,
+                                      const double *g_vp, double *g_x, double *g_v, double *g_a, double *g_jerk)
+{
+    nb_status s = hermite_args(c, n, {t_last, g_xp, g_vp, g_x, g_v, g_a, g_jerk});
+    if (s != NB_OK || n == 0) return s;
+    cudaEvent_t t0 = span_begin(c);
+    launch_hermite_predict_vjp(c->stream, n, t, t_last, g_xp, g_vp, g_x, g_v, g_a, g_jerk);
+    CK_LAUNCH("k_hermite_predict_vjp launch");
+    span_end(c, PH_BACKWARD, t0, 1);
+    return NB_OK;
+}
+
+nb_status nb_hermite_correct(nb_ctx *c, int64_t n, double t, const double *t_last, const double *xp,
+                             const double *vp, const double *a0, const double *j0, const double *a1,
+                             const double *j1, double *x1, double *v1)
+{
+    nb_status s = hermite_args(c, n, {t_last, xp, vp, a0, j0, a1, j1, x1, v1});
+    if (s != NB_OK || n == 0) return s;
+    cudaEvent_t t0 = span_begin(c);
+    launch_hermite_correct(c->stream, n, t, t_last, xp, vp, a0, j0, a1, j1, x1, v1);
+    CK_LAUNCH("k_hermite_correct launch");
+    span_end(c, PH_PREDICT, t0, 1);
+    return NB_OK;
+}
+
+nb_status nb_hermite_correct_backward(nb_ctx *c, int64_t n, double t, const double *t_last, const double *g_x1,
+                                      const double *g_v1, double *g_xp, double *g_vp, double *g_a0, double *g_j0,
+                                      double *g_a1, double *g_j1)
+{
+    nb_status s = hermite_args(c, n, {t_last, g_x1, g_v1, g_xp, g_vp, g_a0, g_j0, g_a1, g_j1});
+    if (s != NB_OK || n == 0) return s;
+    cudaEvent_t t0 = span_begin(c);
+    launch_hermite_correct_vjp(c->stream, n, t, t_last, g_x1, g_v1, g_xp, g_vp, g_a0, g_j0, g_a1, g_j1);
+    CK_LAUNCH("k_hermite_correct_vjp launch");
+    span_end(c, PH_BACKWARD, t0, 1);
     return NB_OK;
 }
 

@@ -76,6 +76,24 @@ __device__ __forceinline__ void hermite_taylor(double x, double v, double a, dou
     vp = __fma_rn(dt, __fma_rn(h, j, a), v);
 }
 
+// ---- the Hermite corrector -----------------------------------------------------------------
+// Fourth-order Hermite corrector of one component over a step h (Sec. 2, after Makino 1991):
+// from the predicted xp, vp and the force and jerk a0, j0 at the start of the step and a1, j1
+// at its end, the second and third derivatives of the force at the start,
+//   a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2,   a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3,
+// and the corrected x1 = xp + h^4/24 a2 + h^5/120 a3, v1 = vp + h^3/6 a2 + h^4/24 a3.  Written
+// operation by operation in the order of that definition; the units that call it are compiled
+// without FMA contraction, so an FP64 run follows the plain definition to rounding.
+__device__ __forceinline__ void hermite_correct(double xp, double vp, double a0, double j0, double a1, double j1,
+                                                double h, double &x1, double &v1, double &a2, double &a3)
+{
+    const double da = a0 - a1;
+    a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) / (h * h);
+    a3 = (12.0 * da + 6.0 * h * (j0 + j1)) / (h * h * h);
+    x1 = xp + h * h * h * h / 24.0 * a2 + h * h * h * h * h / 120.0 * a3;
+    v1 = vp + h * h * h / 6.0 * a2 + h * h * h * h / 24.0 * a3;
+}
+
 // ---- state records of the predict-on-load irregular force ---------------------------------
 //   FP64 : 4 dvec4  {x, y, z, t_last} {vx, vy, vz, m} {ax, ay, az, 0} {jx, jy, jz, 0}
 //   mixed: 5 float4 {xh, yh, zh, m} {xl, yl, zl, t_hi} {vx, vy, vz, t_lo} {ax, ay, az, 0}

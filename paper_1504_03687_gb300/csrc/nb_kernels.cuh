@@ -121,6 +121,18 @@ struct CtxState {
 bool ctx_state(::nb_ctx *c, CtxState *out);
 void ctx_state_changed(::nb_ctx *c);  // the state arrays were rewritten in place
 
+// Hermite predictor and corrector over caller arrays, and their VJPs (hermite.cu).
+void launch_hermite_predict(cudaStream_t st, int64_t n, double t, const double *x, const double *v, const double *a,
+                            const double *j, const double *tl, double *xp, double *vp);
+void launch_hermite_predict_vjp(cudaStream_t st, int64_t n, double t, const double *tl, const double *gxp,
+                                const double *gvp, double *gx, double *gv, double *ga, double *gj);
+void launch_hermite_correct(cudaStream_t st, int64_t n, double t, const double *tl, const double *xp, const double *vp,
+                            const double *a0, const double *j0, const double *a1, const double *j1, double *x1,
+                            double *v1);
+void launch_hermite_correct_vjp(cudaStream_t st, int64_t n, double t, const double *tl, const double *gx1,
+                                const double *gv1, double *gxp, double *gvp, double *ga0, double *gj0, double *ga1,
+                                double *gj1);
+
 // Irregular force (irregular.cu).  Lists as CSR (off) or, with ell_stride > 0, per
 // particle: particle i's list is nb[i * ell_stride .. + ell_cnt[i]).
 void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,

@@ -8,8 +8,8 @@ concatenated indices and re-offset.
 
 Source sharding (the GPUs of one node, Sec. 3.4): every rank sums over its own contiguous
 share of the source particles (nb_set_source_range) for all active rows; the partial sums
-are added in rank order, the neighbour lists concatenated in rank order (which keeps them
-in ascending j) and cut at nb_cap, and the true counts added.
+and the true counts are added by the backend's all-reduce, the neighbour lists concatenated
+in rank order (which keeps them in ascending j) and cut at nb_cap.
 
 Any torch.distributed backend works (NCCL between GPUs, gloo on the host).
 """
@@ -85,71 +85,62 @@ def shard_sources(n: int, world: int, rank: int, align: int = SOURCE_ALIGN) -> t
     return cut(rank), cut(rank + 1)
 
 
-def combine_source_shards(parts, nb_cap: int):
-    """Merge per-source-range results into the full-set result.
-
-    parts: [(acc, jerk, pot, nb_off, nb_idx, nb_count), ...] in ascending range order, all
-    torch tensors on one device, for the same active rows; nb_off / nb_idx / nb_count may be
-    None throughout.  Each part's lists must be complete up to nb_cap (no CSR overflow).
-    Returns (acc, jerk, pot, nb_off, nb_idx, nb_count): sums added in part order, lists
-    concatenated in part order and cut at nb_cap, counts added."""
-    acc, jerk, pot = (p.clone() for p in parts[0][:3])
-    for p in parts[1:]:
-        acc += p[0]
-        jerk += p[1]
-        pot += p[2]
-    if parts[0][3] is None:
-        return acc, jerk, pot, None, None, None
-    dev = acc.device
-    n_i = acc.shape[0]
-    kept = [(p[3][1:] - p[3][:-1]).to(torch.int64) for p in parts]
+def merge_source_lists(offs, idxs, nb_cap: int):
+    """Neighbour lists of the source shards, merged: every row's lists concatenated in shard
+    order (which keeps them in ascending j, the shards being ascending source ranges) and cut
+    at nb_cap.  offs[r] (n_i + 1) int64 and idxs[r] are shard r's CSR lists, all on one
+    device, each complete up to nb_cap (no CSR overflow).  Returns (nb_off, nb_idx)."""
+    dev = offs[0].device
+    n_i = offs[0].shape[0] - 1
+    kept = [(o[1:] - o[:-1]).to(torch.int64) for o in offs]
     total = torch.stack(kept).sum(0) if kept else torch.zeros(n_i, dtype=torch.int64, device=dev)
     merged = torch.clamp(total, max=nb_cap)
     off = torch.zeros(n_i + 1, dtype=torch.int64, device=dev)
     off[1:] = torch.cumsum(merged, 0)
     out = torch.empty(max(int(off[-1].item()), 1), dtype=torch.int32, device=dev)
-    before = torch.zeros(n_i, dtype=torch.int64, device=dev)  # entries of earlier parts per row
+    before = torch.zeros(n_i, dtype=torch.int64, device=dev)  # entries of earlier shards per row
     rows_all = torch.arange(n_i, device=dev)
-    for p, k in zip(parts, kept):
-        used = int(p[3][-1].item())
+    for o, ix, k in zip(offs, idxs, kept):
+        used = int(o[-1].item())
         if used:
             row = torch.repeat_interleave(rows_all, k)
-            local = torch.arange(used, device=dev) - p[3][:-1][row]
+            local = torch.arange(used, device=dev) - o[:-1][row]
             dest = before[row] + local
             keep = dest < nb_cap
-            out[(off[:-1][row] + dest)[keep]] = p[4][:used][keep]
+            out[(off[:-1][row] + dest)[keep]] = ix[:used][keep]
         before += k
-    count = parts[0][5].clone()
-    for p in parts[1:]:
-        count += p[5]
-    return acc, jerk, pot, off, out, count
+    return off, out
 
 
 def reduce_sources(acc, jerk, pot, nb_off=None, nb_idx=None, nb_count=None, nb_cap: int = 512, group=None):
-    """Source-sharded exchange: gather every rank's partial result for the same active rows
-    and merge them in rank order (combine_source_shards) on every rank, so that the sums
-    are added in a fixed order whatever the backend."""
+    """Source-sharded exchange on every rank: the partial sums and the true neighbour counts
+    are reduced by the backend (an all-reduce sum: NCCL between GPUs, gloo on the host; the
+    order of its additions is the backend's, fixed for a given backend and rank count), and
+    the neighbour lists are gathered and merged in rank order (merge_source_lists).  Returns
+    (acc, jerk, pot, nb_off, nb_idx, nb_count) of the full source set."""
     import torch.distributed as dist
     world = dist.get_world_size(group)
+    acc, jerk, pot = acc.clone(), jerk.clone(), pot.clone()
+    for t in (acc, jerk, pot):
+        dist.all_reduce(t, group=group)
+    if nb_off is None:
+        return acc, jerk, pot, None, None, None
+    count = nb_count.clone()
+    dist.all_reduce(count, group=group)
 
     def gather_same(t):
         bufs = [torch.empty_like(t) for _ in range(world)]
         dist.all_gather(bufs, t.contiguous(), group=group)
         return bufs
 
-    accs, jerks, pots = gather_same(acc), gather_same(jerk), gather_same(pot)
-    if nb_off is None:
-        parts = [(a, j, p, None, None, None) for a, j, p in zip(accs, jerks, pots)]
-        return combine_source_shards(parts, nb_cap)
-    offs, counts = gather_same(nb_off), gather_same(nb_count)
+    offs = gather_same(nb_off)
     used = int(nb_off[-1].item())
     lens = gather_same(torch.tensor([used], dtype=torch.int64, device=acc.device))
     lmax = max(int(q.item()) for q in lens)
     padded = torch.zeros(max(lmax, 1), dtype=nb_idx.dtype, device=nb_idx.device)
     padded[:used] = nb_idx[:used]
-    idxs = gather_same(padded)
-    parts = list(zip(accs, jerks, pots, offs, idxs, counts))
-    return combine_source_shards(parts, nb_cap)
+    off, idx = merge_source_lists(offs, gather_same(padded), nb_cap)
+    return acc, jerk, pot, off, idx, count
 
 
 class PeerLost(RuntimeError):

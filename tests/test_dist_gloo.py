@@ -115,16 +115,25 @@ def _check_against_full(got, cl, idx, rs2, cap):
     np.testing.assert_array_equal(got[5].numpy(), cnt)
 
 
-def test_combine_source_shards_matches_full_set():
+def combine_shards(parts, cap):
+    """Single-process stand-in for the exchange: the shards' sums and counts added in shard
+    order (what the all-reduce computes), their lists merged by the library's merge."""
+    from paper_1504_03687_gb300.dist import merge_source_lists
+    acc, jerk, pot, count = (sum(p[q] for p in parts) for q in (0, 1, 2, 5))
+    off, idx = merge_source_lists([p[3] for p in parts], [p[4] for p in parts], cap)
+    return acc, jerk, pot, off, idx, count
+
+
+def test_merged_source_shards_match_full_set():
     """Three unequal source ranges, cap 16 (most lists are cut, some inside the first
     range, some across ranges): sums up to reassociation, lists and counts exact."""
-    from paper_1504_03687_gb300.dist import combine_source_shards, shard_sources
+    from paper_1504_03687_gb300.dist import shard_sources
     cl, rs2 = W.plummer_1k_equal()
     _range_result.rs2 = rs2
     idx = W.active_block(W.block_steps(cl, seed=0), 301)
     cap = 16
     parts = [_range_result(cl, idx, *shard_sources(cl.n, 3, r), cap) for r in range(3)]
-    _check_against_full(combine_source_shards(parts, cap), cl, idx, rs2, cap)
+    _check_against_full(combine_shards(parts, cap), cl, idx, rs2, cap)
 
 
 def _source_worker(rank, world, port, out):

@@ -557,13 +557,32 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 // r_s^2 (float) and the row's hi/lo position.
 enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_XH = 4, AR_XL = 7, AR_WORDS = 10 };
 
-template <int NI, int BLOCK, int TJ>
+// STAGE: every row's neighbour hits are gathered in shared memory, kStageHits at a time, and
+// written out as whole 32-byte sectors (instead of one 4-byte store a hit, which leaves
+// partly written sectors that the memory system completes with extra DRAM reads and writes).
+constexpr int kStageHits = 8;
+
+template <int NI, int BLOCK, int TJ, bool STAGE = false>
 constexpr int anchored_smem_bytes()
 {
-    return 3 * TJ * 16 + 5 * TJ * 16 + 7 * NI * BLOCK * 8 + AR_WORDS * NI * BLOCK * 4;
+    return 3 * TJ * 16 + 5 * TJ * 16 + 7 * NI * BLOCK * 8 + (AR_WORDS + (STAGE ? kStageHits : 0)) * NI * BLOCK * 4;
 }
 
-template <int NP, int BLOCK, int TJ, int UJ>
+// Writes the staged hits first .. last (inclusive, same group of kStageHits) of one row to its
+// neighbour segment: a whole aligned group as two 16-byte stores, a partial one entry by entry.
+__device__ __forceinline__ void flush_staged(int32_t *seg, const int32_t *sbuf, int stride, int first, int last,
+                                             bool aligned)
+{
+    if (aligned && last - first == kStageHits - 1) {
+        int4 *dst = reinterpret_cast<int4 *>(seg + first);
+        dst[0] = make_int4(sbuf[0], sbuf[stride], sbuf[2 * stride], sbuf[3 * stride]);
+        dst[1] = make_int4(sbuf[4 * stride], sbuf[5 * stride], sbuf[6 * stride], sbuf[7 * stride]);
+    } else {
+        for (int q = first; q <= last; ++q) seg[q] = sbuf[(q & (kStageHits - 1)) * stride];
+    }
+}
+
+template <int NP, int BLOCK, int TJ, int UJ, bool STAGE>
 __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ sd, int64_t jb, const ForceArgs &A,
                                                     int s, const float2 (&ne)[NP][3], const float2 (&nv)[NP][3],
                                                     const float2 (&tm)[NP], const float2 (&th)[NP],
@@ -640,8 +659,18 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
                     if (r2p < xr[AR_RS2 * NR * BLOCK + slot] && j < A.j_hi) {
                         int32_t *cp = srow + AR_CNT * NR * BLOCK + slot;
                         const int cnt = *cp;
-                        if (cnt < A.L)
-                            A.seg_slots[((int64_t)s * A.n_i + srow[AR_K * NR * BLOCK + slot]) * A.L + cnt] = j32;
+                        if (cnt < A.L) {
+                            int32_t *seg = A.seg_slots + ((int64_t)s * A.n_i + srow[AR_K * NR * BLOCK + slot]) * A.L;
+                            if (STAGE) {
+                                int32_t *sbuf = srow + AR_WORDS * NR * BLOCK + slot;
+                                sbuf[(cnt & (kStageHits - 1)) * NR * BLOCK] = j32;
+                                if ((cnt & (kStageHits - 1)) == kStageHits - 1 || cnt == A.L - 1)
+                                    flush_staged(seg, sbuf, NR * BLOCK, cnt & ~(kStageHits - 1), cnt,
+                                                 (A.L & (kStageHits - 1)) == 0);
+                            } else {
+                                seg[cnt] = j32;
+                            }
+                        }
                         *cp = cnt + 1;
                     }
                     if (r2a < (h ? tm[q].y : tm[q].x)) {  // masked: add the pair in double-single form
@@ -668,8 +697,8 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
     }
 }
 
-template <int NI, int BLOCK, int TJ, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_anchored_x2(ForceArgs A)
+template <int NI, int BLOCK, int TJ, int MINB, bool STAGE>
+__device__ __forceinline__ void anchored_body(const ForceArgs &A)
 {
     constexpr int NP = NI / 2;
     constexpr int UJ = NI >= 4 ? (MINB >= 4 ? 1 : 2) : 4;
@@ -786,7 +815,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_anchored_x2(ForceAr
         }
         __syncthreads();  // dup complete; raw is free again
         if (t + 1 < t1) load_tile(t + 1);
-        tile_mixed_anchored<NP, BLOCK, TJ, UJ>(dup, t * TJ, A, s, ne, nv, tm, th, srow, acc);
+        tile_mixed_anchored<NP, BLOCK, TJ, UJ, STAGE>(dup, t * TJ, A, s, ne, nv, tm, th, srow, acc);
         if ((t - t0) % PT == PT - 1 || t + 1 == t1) {
 #pragma unroll
             for (int p = 0; p < NP; ++p)
@@ -808,9 +837,29 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_anchored_x2(ForceAr
                 const double v = dacc[(c * NI + q) * BLOCK + tid];
                 A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -v : v;
             }
-            if (A.want_nb) A.seg_cnt[(int64_t)s * A.n_i + k] = srow[AR_CNT * NI * BLOCK + slot];
+            if (A.want_nb) {
+                const int cnt = srow[AR_CNT * NI * BLOCK + slot];
+                A.seg_cnt[(int64_t)s * A.n_i + k] = cnt;
+                const int c = cnt < A.L ? cnt : A.L;  // staged hits not yet written (a last, partial group)
+                if (STAGE && c < A.L && (c & (kStageHits - 1)) != 0)
+                    flush_staged(A.seg_slots + ((int64_t)s * A.n_i + k) * A.L, srow + AR_WORDS * NI * BLOCK + slot,
+                                 NI * BLOCK, c & ~(kStageHits - 1), c - 1, false);
+            }
         }
     }
+}
+
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_anchored_x2(ForceArgs A)
+{
+    anchored_body<NI, BLOCK, TJ, MINB, false>(A);
+}
+
+// The anchored kernel with the neighbour hits staged in shared memory (whole-sector writes).
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_staged_x2(ForceArgs A)
+{
+    anchored_body<NI, BLOCK, TJ, MINB, true>(A);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1018,11 +1067,12 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
 // ------------------------------------------------------------------------------------------
 // Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM, kind).  The plan's
 // `variant` indexes this list; ids 0-3 are the scalar kernel, 4-9 the packed-FP32x2 one
-// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-14 the
+// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-16 the
 // anchored packed kernel (rows in spatial order, anchor-relative separations; 13 and 14 with
-// row tiles of 128 and 64).
+// row tiles of 128 and 64; 15 and 16 staging the neighbour hits).
 // Last column: 0 = scalar (static shared memory), 1 = packed (x2_smem_bytes), 2 = anchored
-// (anchored_smem_bytes; needs the row order A.perm).
+// (anchored_smem_bytes; needs the row order A.perm), 3 = anchored with the neighbour hits staged
+// in shared memory and written as whole sectors (15, 16).
 #define NB_MIXED_TILED_VARIANTS(X)                       \
     X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)         \
     X(1, k_force_mixed_tiled, 2, 128, 256, 4, 0)         \
@@ -1038,18 +1088,23 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
     X(11, k_force_mixed_anchored_x2, 2, 128, 128, 4, 2)  \
     X(12, k_force_mixed_anchored_x2, 4, 128, 256, 2, 2)  \
     X(13, k_force_mixed_anchored_x2, 2, 64, 64, 8, 2)    \
-    X(14, k_force_mixed_anchored_x2, 2, 32, 64, 12, 2)
+    X(14, k_force_mixed_anchored_x2, 2, 32, 64, 12, 2)   \
+    X(15, k_force_mixed_staged_x2, 4, 128, 64, 3, 3)     \
+    X(16, k_force_mixed_staged_x2, 2, 128, 128, 4, 3)
 
 struct TiledVariant {
     int ni, block, tj, smem, kind;
 };
-#define NB_TV_ROW(id, K, NI, B, TJ, MB, KIND) \
-    {NI, B, TJ, KIND == 1 ? x2_smem_bytes<NI, B, TJ>() : (KIND == 2 ? anchored_smem_bytes<NI, B, TJ>() : 0), KIND},
+#define NB_TV_ROW(id, K, NI, B, TJ, MB, KIND)                                                         \
+    {NI, B, TJ,                                                                                      \
+     KIND == 1 ? x2_smem_bytes<NI, B, TJ>()                                                          \
+               : (KIND >= 2 ? anchored_smem_bytes<NI, B, TJ, KIND == 3>() : 0),                      \
+     KIND},
 static const TiledVariant kTiled[] = {NB_MIXED_TILED_VARIANTS(NB_TV_ROW)};
 #undef NB_TV_ROW
 
 int mixed_tiled_dyn_smem(int v) { return kTiled[v].smem; }
-int mixed_tiled_anchored(int v) { return v >= 0 && v < (int)(sizeof(kTiled) / sizeof(kTiled[0])) && kTiled[v].kind == 2; }
+int mixed_tiled_anchored(int v) { return v >= 0 && v < (int)(sizeof(kTiled) / sizeof(kTiled[0])) && kTiled[v].kind >= 2; }
 
 // Raise the dynamic shared-memory limit of the packed kernels (needed above 48 KB); called
 // once per context before occupancy queries and launches.

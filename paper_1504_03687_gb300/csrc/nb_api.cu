@@ -53,20 +53,21 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
-static constexpr int kMixedTiledVariants = 15;  // entries of the mixed tiled variant table
-static constexpr int kOccFp64 = 15;             // occupancy slot of the FP64 tiled kernel
-static constexpr int kOccSlots = 16;
-static constexpr int kMaxCap = 8192;
+static constexpr int kMixedTiledVariants = 17;  // entries of the mixed tiled variant table
+static constexpr int kOccFp64 = 17;             // occupancy slot of the FP64 tiled kernel
+static constexpr int kOccSlots = 18;
+static_assert(kOccSlots == kMixedTiledVariants + 1, "one occupancy slot per mixed tiled variant, then the FP64 kernel");
+static constexpr int kMaxCap = 8192;   // largest nb_cap (sort buffers live in shared memory)
 // Irregular force: predict all particles once when N_i * factor >= N.  Measured on this GPU
 // (King cluster, N = 2^20, r_s for a median of 80 neighbours): in FP64 the per-pair prediction
 // (25 FP64 operations) makes predict-all pay already at N/128 active rows; in mixed precision
 // the 80-byte state gathers only lose to one full predictor pass above about N/8.
 static constexpr int64_t kIrrAllFactorFp64 = 128;
-static constexpr int64_t kIrrAllFactorMixed = 8;   // largest nb_cap (sort buffers live in shared memory)
+static constexpr int64_t kIrrAllFactorMixed = 8;
 
 struct nb_ctx {
     int device = 0, precision = 0, cap = 0, num_sms = 0;
-    int occ[16] = {0};
+    int occ[kOccSlots] = {0};  // resident CTAs per SM of every planned kernel variant
     int force_kernel = -1, force_variant = 0, force_splits = 0;  // plan override (-1: none)
     struct TableEntry {
         int64_t ni_max;
@@ -108,7 +109,7 @@ struct nb_ctx {
     };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> evpool;
-    int64_t launches[8] = {0};
+    int64_t launches[NB_PHASES] = {0};  // kernels launched per phase since nb_get_timings
     // test hook (nb_inject_fault / NB_FAULT): the operation of kind fault_kind that comes
     // after fault_after more of its kind reports the failure the CUDA runtime would
     int fault_kind = 0, fault_after = 0;
@@ -116,6 +117,7 @@ struct nb_ctx {
 
 enum { PH_PREDICT = 0, PH_FORCE = 1, PH_REDUCE = 2, PH_NEIGHBOURS = 3, PH_BACKWARD = 4, PH_IRREGULAR = 5, PH_ORDER = 6,
        PH_COUNT = 7 };
+static_assert(PH_COUNT == NB_PHASES, "one timing phase per NB_PHASES entry");
 
 static cudaEvent_t ev_take(nb_ctx *c)
 {
@@ -309,9 +311,10 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
         // packed FP32x2 NI=4/2, NI=4 with 128-j tiles, NI=2 x 256 threads), measured on a
         // GB300 at N = 2^20, N_i = 2^17 (King W0 = 6); the two small-tile packed variants
         // (NI=2 x 64 and x 32 threads) estimated from their occupancy; the anchored variants
-        // measured the same way (10-12) or estimated (13, 14: the small-tile packed ones x 1.1)
-        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91,
-                                                           0.85, 0.75, 1.12, 1.08, 1.04, 0.94, 0.82};
+        // measured the same way (10-12) or estimated (13, 14: the small-tile packed ones x 1.1;
+        // 15, 16: the staged-hit forms of 10 and 11)
+        static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91, 0.85,
+                                                           0.75, 1.12, 1.08, 1.04, 0.94, 0.82, 1.10, 1.06};
         double best = -1.0;
         for (int v = 0; v < kMixedTiledVariants; ++v) {
             if (only_variant >= 0 && v != only_variant) continue;
@@ -788,8 +791,8 @@ nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_pe
                       int32_t nb_cap, int64_t *out)
 {
     if (!out || n < 1 || n_i < 0 || nb_cap < 1 || (precision != NB_FP64 && precision != NB_MIXED)) return NB_ERR_ARG;
-    int occ[16];
-    for (int q = 0; q < 16; ++q) occ[q] = 1;
+    int occ[kOccSlots];
+    for (int q = 0; q < kOccSlots; ++q) occ[q] = 1;
     if (ctas_per_sm)
         for (int q = 0; q < kOccSlots; ++q) occ[q] = ctas_per_sm[q];
     Plan p = plan_force(precision, num_sms, occ, n, n_i, nb_cap);

@@ -557,32 +557,35 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 // r_s^2 (float) and the row's hi/lo position.
 enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_XH = 4, AR_XL = 7, AR_WORDS = 10 };
 
-// STAGE: every row's neighbour hits are gathered in shared memory, kStageHits at a time, and
-// written out as whole 32-byte sectors (instead of one 4-byte store a hit, which leaves
-// partly written sectors that the memory system completes with extra DRAM reads and writes).
-constexpr int kStageHits = 8;
-
-template <int NI, int BLOCK, int TJ, bool STAGE = false>
+// HITS > 0: every row's neighbour hits are gathered in shared memory, HITS at a time (8: one
+// 32-byte sector, 16: two), and written out as whole aligned groups instead of one 4-byte store
+// a hit, which leaves partly written sectors that the memory system completes with extra DRAM
+// reads and writes.
+template <int NI, int BLOCK, int TJ, int HITS = 0>
 constexpr int anchored_smem_bytes()
 {
-    return 3 * TJ * 16 + 5 * TJ * 16 + 7 * NI * BLOCK * 8 + (AR_WORDS + (STAGE ? kStageHits : 0)) * NI * BLOCK * 4;
+    return 3 * TJ * 16 + 5 * TJ * 16 + 7 * NI * BLOCK * 8 + (AR_WORDS + HITS) * NI * BLOCK * 4;
 }
 
-// Writes the staged hits first .. last (inclusive, same group of kStageHits) of one row to its
-// neighbour segment: a whole aligned group as two 16-byte stores, a partial one entry by entry.
+// Writes the staged hits first .. last (inclusive, one group of HITS) of one row to its
+// neighbour segment: a whole aligned group as 16-byte stores, a partial one entry by entry.
+template <int HITS>
 __device__ __forceinline__ void flush_staged(int32_t *seg, const int32_t *sbuf, int stride, int first, int last,
                                              bool aligned)
 {
-    if (aligned && last - first == kStageHits - 1) {
+    // streaming (evict-first) stores: the lists are read once, by the CSR gather
+    if (aligned && last - first == HITS - 1) {
         int4 *dst = reinterpret_cast<int4 *>(seg + first);
-        dst[0] = make_int4(sbuf[0], sbuf[stride], sbuf[2 * stride], sbuf[3 * stride]);
-        dst[1] = make_int4(sbuf[4 * stride], sbuf[5 * stride], sbuf[6 * stride], sbuf[7 * stride]);
+#pragma unroll
+        for (int q = 0; q < HITS / 4; ++q)
+            __stcs(dst + q, make_int4(sbuf[(4 * q) * stride], sbuf[(4 * q + 1) * stride], sbuf[(4 * q + 2) * stride],
+                                      sbuf[(4 * q + 3) * stride]));
     } else {
-        for (int q = first; q <= last; ++q) seg[q] = sbuf[(q & (kStageHits - 1)) * stride];
+        for (int q = first; q <= last; ++q) __stcs(seg + q, sbuf[(q & (HITS - 1)) * stride]);
     }
 }
 
-template <int NP, int BLOCK, int TJ, int UJ, bool STAGE>
+template <int NP, int BLOCK, int TJ, int UJ, int HITS>
 __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ sd, int64_t jb, const ForceArgs &A,
                                                     int s, const float2 (&ne)[NP][3], const float2 (&nv)[NP][3],
                                                     const float2 (&tm)[NP], const float2 (&th)[NP],
@@ -661,14 +664,14 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
                         const int cnt = *cp;
                         if (cnt < A.L) {
                             int32_t *seg = A.seg_slots + ((int64_t)s * A.n_i + srow[AR_K * NR * BLOCK + slot]) * A.L;
-                            if (STAGE) {
+                            if (HITS > 0) {
                                 int32_t *sbuf = srow + AR_WORDS * NR * BLOCK + slot;
-                                sbuf[(cnt & (kStageHits - 1)) * NR * BLOCK] = j32;
-                                if ((cnt & (kStageHits - 1)) == kStageHits - 1 || cnt == A.L - 1)
-                                    flush_staged(seg, sbuf, NR * BLOCK, cnt & ~(kStageHits - 1), cnt,
-                                                 (A.L & (kStageHits - 1)) == 0);
+                                sbuf[(cnt & (HITS - 1)) * NR * BLOCK] = j32;
+                                if ((cnt & (HITS - 1)) == HITS - 1 || cnt == A.L - 1)
+                                    flush_staged<HITS>(seg, sbuf, NR * BLOCK, cnt & ~(HITS - 1), cnt,
+                                                       (A.L & (HITS - 1)) == 0);
                             } else {
-                                seg[cnt] = j32;
+                                __stcs(seg + cnt, j32);
                             }
                         }
                         *cp = cnt + 1;
@@ -697,7 +700,7 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
     }
 }
 
-template <int NI, int BLOCK, int TJ, int MINB, bool STAGE>
+template <int NI, int BLOCK, int TJ, int MINB, int HITS>
 __device__ __forceinline__ void anchored_body(const ForceArgs &A)
 {
     constexpr int NP = NI / 2;
@@ -786,10 +789,11 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
 #pragma unroll
     for (int e = 0; e < 7 * NI; ++e) dacc[e * BLOCK + tid] = 0.0;
 
+    const uint64_t keep = l2_keep_policy();  // the j-records stay in L2 past the list stores
     auto load_tile = [&](int64_t t) {
         const float4 *src = rec + t * (3 * TJ);
 #pragma unroll
-        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16(&raw[e], src + e);
+        for (int e = tid; e < 3 * TJ; e += BLOCK) cp_async16_keep(&raw[e], src + e, keep);
         cp_async_commit();
     };
     float2 acc[NP][7];
@@ -815,7 +819,7 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
         }
         __syncthreads();  // dup complete; raw is free again
         if (t + 1 < t1) load_tile(t + 1);
-        tile_mixed_anchored<NP, BLOCK, TJ, UJ, STAGE>(dup, t * TJ, A, s, ne, nv, tm, th, srow, acc);
+        tile_mixed_anchored<NP, BLOCK, TJ, UJ, HITS>(dup, t * TJ, A, s, ne, nv, tm, th, srow, acc);
         if ((t - t0) % PT == PT - 1 || t + 1 == t1) {
 #pragma unroll
             for (int p = 0; p < NP; ++p)
@@ -835,15 +839,15 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
                 const double v = dacc[(c * NI + q) * BLOCK + tid];
-                A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -v : v;
+                __stcs(A.part + ((int64_t)s * 7 + c) * A.n_i + k, (c == 6) ? -v : v);
             }
             if (A.want_nb) {
                 const int cnt = srow[AR_CNT * NI * BLOCK + slot];
                 A.seg_cnt[(int64_t)s * A.n_i + k] = cnt;
                 const int c = cnt < A.L ? cnt : A.L;  // staged hits not yet written (a last, partial group)
-                if (STAGE && c < A.L && (c & (kStageHits - 1)) != 0)
-                    flush_staged(A.seg_slots + ((int64_t)s * A.n_i + k) * A.L, srow + AR_WORDS * NI * BLOCK + slot,
-                                 NI * BLOCK, c & ~(kStageHits - 1), c - 1, false);
+                if (HITS > 0 && c < A.L && (c & (HITS - 1)) != 0)
+                    flush_staged<HITS>(A.seg_slots + ((int64_t)s * A.n_i + k) * A.L,
+                                       srow + AR_WORDS * NI * BLOCK + slot, NI * BLOCK, c & ~(HITS - 1), c - 1, false);
             }
         }
     }
@@ -852,14 +856,15 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
 template <int NI, int BLOCK, int TJ, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_anchored_x2(ForceArgs A)
 {
-    anchored_body<NI, BLOCK, TJ, MINB, false>(A);
+    anchored_body<NI, BLOCK, TJ, MINB, 0>(A);
 }
 
-// The anchored kernel with the neighbour hits staged in shared memory (whole-sector writes).
+// The anchored kernel with the neighbour hits staged in shared memory and written in whole
+// 32-byte sectors (8 hits), or in pairs of sectors (16 hits: the two-row variant).
 template <int NI, int BLOCK, int TJ, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_staged_x2(ForceArgs A)
 {
-    anchored_body<NI, BLOCK, TJ, MINB, true>(A);
+    anchored_body<NI, BLOCK, TJ, MINB, NI >= 4 ? 8 : 16>(A);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1090,7 +1095,7 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
     X(13, k_force_mixed_anchored_x2, 2, 64, 64, 8, 2)    \
     X(14, k_force_mixed_anchored_x2, 2, 32, 64, 12, 2)   \
     X(15, k_force_mixed_staged_x2, 4, 128, 64, 3, 3)     \
-    X(16, k_force_mixed_staged_x2, 2, 128, 128, 4, 3)
+    X(16, k_force_mixed_staged_x2, 2, 128, 64, 4, 3)
 
 struct TiledVariant {
     int ni, block, tj, smem, kind;
@@ -1098,7 +1103,7 @@ struct TiledVariant {
 #define NB_TV_ROW(id, K, NI, B, TJ, MB, KIND)                                                         \
     {NI, B, TJ,                                                                                      \
      KIND == 1 ? x2_smem_bytes<NI, B, TJ>()                                                          \
-               : (KIND >= 2 ? anchored_smem_bytes<NI, B, TJ, KIND == 3>() : 0),                      \
+               : (KIND >= 2 ? anchored_smem_bytes<NI, B, TJ, KIND == 3 ? (NI >= 4 ? 8 : 16) : 0>() : 0), \
      KIND},
 static const TiledVariant kTiled[] = {NB_MIXED_TILED_VARIANTS(NB_TV_ROW)};
 #undef NB_TV_ROW

@@ -37,6 +37,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// L2 policy that keeps a line past streaming traffic (evict_last), and a cp.async carrying it:
+// for data every CTA re-reads (the j-records) while a kernel streams its outputs through L2.
+__device__ __forceinline__ uint64_t l2_keep_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void cp_async16_keep(void *smem, const void *gmem, uint64_t policy)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "l"(policy)
+                 : "memory");
+}
+
 // ---- the neighbour-test distances ------------------------------------------------------
 // Both are written with explicit round-to-nearest intrinsics so that every kernel that
 // decides "j is a neighbour of i" (the scalar and packed force kernels, and the packed

@@ -41,7 +41,7 @@ NB_CAP = 512
 # force-kernel sources whose SHA-256 is recorded with them.
 FORCE_TRAFFIC = {"sources_sha256": "384064c57e33dcaef0fe885dbaeda7197b564711176fbd676235b7d3b46dc1e1",
                  "bytes_per_launch": [59108864, 124853760, 1003102464, 2345910272]}
-FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh")
+FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh", "roworder.cu")
 
 
 def force_sources_sha256() -> str:

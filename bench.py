@@ -39,8 +39,8 @@ NB_CAP = 512
 # one ncu capture of `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu --no-ensemble
 # --no-adjoint` (metrics dram__bytes_read.sum, dram__bytes_write.sum), valid only for the
 # force-kernel sources whose SHA-256 is recorded with them.
-FORCE_TRAFFIC = {"sources_sha256": "384064c57e33dcaef0fe885dbaeda7197b564711176fbd676235b7d3b46dc1e1",
-                 "bytes_per_launch": [59108864, 124853760, 1003102464, 2345910272]}
+FORCE_TRAFFIC = {"sources_sha256": "bbd7f6e973dcee1abf08528ebdacb8ec3facaf31f82f4846bd9b33ad60453125",
+                 "bytes_per_launch": [64852224, 141047296, 1287248640, 3185677312]}
 FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh", "roworder.cu")
 
 

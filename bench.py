@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--ni", type=int, default=2048)
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--backward", action="store_true", help="with --profile: also run the adjoint")
+    ap.add_argument("--no-lists", action="store_true",
+                    help="with --profile: the force call without neighbour capture (sums only)")
     ap.add_argument("--irregular", action="store_true",
                     help="with --profile: also run the irregular force over the lists just returned")
     ap.add_argument("--model", default="king", choices=["king", "plummer"],
@@ -582,7 +584,8 @@ def run_profile_case(args):
         for it in range(2):
             ctx.set_timing(it == 1)
             ctx.predict(0.125)
-            out = ctx.regular_force(idx, rs2_dev, nb_capacity=args.ni * NB_PER_ROW)
+            out = ctx.regular_force(idx, rs2_dev, neighbours=not args.no_lists,
+                                    nb_capacity=0 if args.no_lists else args.ni * NB_PER_ROW)
             if args.backward:
                 ctx.regular_force_backward(idx, *g)
             if args.irregular:
@@ -593,17 +596,18 @@ def run_profile_case(args):
         res = {"case": f"{args.model} n={cl.n} n_i={args.ni} {args.prec}", "plan": ctx.plan(cl.n, args.ni),
                "phase_ms": {k: v[0] for k, v in ph.items()}, "launches": {k: v[1] for k, v in ph.items()},
                "force_Ginteractions_s": pairs / (ph["force"][0] * 1e-3) / 1e9 if ph["force"][0] > 0 else None,
-               "nb_total": int(out.nb_off[-1].item())}
+               "nb_total": 0 if args.no_lists else int(out.nb_off[-1].item())}
         if args.irregular and ph["irregular"][0] > 0:
             res["irregular_Gpairs_s"] = res["nb_total"] / (ph["irregular"][0] * 1e-3) / 1e9
         if args.backward and ph["force"][0] > 0:
             fwd = ph["force"][0] + ph["reduce"][0] + ph["neighbours"][0]
             res["backward_over_forward"] = ph["backward"][0] / fwd
         if ref is None:
-            ref = (out.acc.clone(), out.nb_off.clone())
+            ref = (out.acc.clone(), None if args.no_lists else out.nb_off.clone())
         else:  # every plan must give the same answer (to FP32 rounding of the partial sums)
             res["max_rel_acc_diff_vs_first"] = float(((out.acc - ref[0]).norm(dim=1) / ref[0].norm(dim=1)).max())
-            res["same_neighbour_offsets"] = bool(torch.equal(out.nb_off, ref[1]))
+            if not args.no_lists:
+                res["same_neighbour_offsets"] = bool(torch.equal(out.nb_off, ref[1]))
         print(json.dumps(res))
 
 

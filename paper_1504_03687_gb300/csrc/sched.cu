@@ -63,8 +63,17 @@ __device__ void rank_chunk(const SortArgs &A, int64_t c0, int32_t (&part)[kSortI
     for (int b = tid; b < kBins; b += kSortThreads) s_cnt[b] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
+    // rounds past the end of the prefix hold no entry (the same count for the whole CTA)
+    const int64_t left = A.n_act - c0;
+    const int rounds = left >= kChunk ? kSortItems : (int)((left + kSortThreads - 1) / kSortThreads);
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
+        if (r >= rounds) {
+            part[r] = -1;
+            lev[r] = 0;
+            rank[r] = 0;
+            continue;
+        }
         const int64_t e = c0 + (int64_t)r * kSortThreads + tid;
         const bool in = e < A.n_act;
         int32_t p = -1, L = 0;

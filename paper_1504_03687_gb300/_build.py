@@ -25,9 +25,11 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE
           "--expt-relaxed-constexpr"]
 # per-file extra flags: the mixed kernels flush FP32 denormals (no distinct particles are
 # 1e-19 apart) so that rsqrtf is a single hardware instruction; the integrator and the array
-# corrector keep the plain definition's FP64 operation order (no FMA contraction)
-EXTRA = {"force_mixed.cu": ["-ftz=true"], "adjoint.cu": ["-ftz=true"], "irregular.cu": ["-ftz=true"],
-         "ac.cu": ["-fmad=false"], "hermite.cu": ["-fmad=false"]}
+# corrector keep the plain definition's FP64 operation order (no FMA contraction), and the
+# irregular force shares its per-row code with the integrator's fused step, so it is compiled
+# with the same flags (the two give the same bits for a row)
+EXTRA = {"force_mixed.cu": ["-ftz=true"], "adjoint.cu": ["-ftz=true"], "irregular.cu": ["-ftz=true", "-fmad=false"],
+         "ac.cu": ["-ftz=true", "-fmad=false"], "hermite.cu": ["-fmad=false"]}
 SOURCES = ["nb_api.cu", "predict.cu", "force_mixed.cu", "force_fp64.cu", "neighbours.cu", "adjoint.cu",
            "noalloc.cu", "irregular.cu", "sched.cu", "ac.cu", "roworder.cu",
            "hermite.cu"]

@@ -27,6 +27,7 @@
 
 #include "nbgpu.h"
 #include "nb_common.cuh"
+#include "nb_irregular.cuh"
 #include "nb_kernels.cuh"
 
 namespace nbgpu {
@@ -136,142 +137,426 @@ __global__ void k_ac_init(AcDev D, int64_t n, const double *Fa, const double *Ja
     }
 }
 
-// Active row k: regular step too?  Compacts the regular subset (order of the subset is
-// irrelevant: every row's sums are independent of the others).
-__global__ void k_ac_classify(AcDev D, int64_t n_act, const int32_t *list, int64_t t_ticks, unsigned *counter,
-                              int32_t *reg_pos, int32_t *reg_idx, double *reg_rs2, int64_t expected, unsigned *status)
+// Active row k: regular step too?  The regular subset is compacted in list order (the order
+// is deterministic, so the regular force, whose anchored kernel groups rows into CTAs by their
+// order, gives the same bits every run): CTA b owns the list chunk [b kClassifyChunk,
+// (b + 1) kClassifyChunk); the count pass writes the chunk's regular rows, the place pass turns
+// the counts before b into the chunk's base and ranks its rows in order.
+constexpr int kClassifyBlock = 256, kClassifyChunk = 1024;
+
+__device__ __forceinline__ bool ac_regular_row(const AcDev &D, const int32_t *list, int64_t k, int64_t t_ticks)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = list[k];
-        const int LR = D.LR[i];
-        const bool reg = (t_ticks & (((int64_t)1 << (kAcTick - LR)) - 1)) == 0;
-        int32_t p = -1;
-        if (reg) {
-            p = (int32_t)atomicAdd(counter, 1u);
-            reg_idx[p] = i;
-            reg_rs2[p] = D.rs2[i];
-        }
-        reg_pos[k] = p;
-    }
-    // the last CTA to finish checks the count against the host's prediction (a mismatch is a
-    // device error of the step) and leaves the counter at zero for the next step
-    __threadfence();
+    const int LR = D.LR[list[k]];
+    return (t_ticks & (((int64_t)1 << (kAcTick - LR)) - 1)) == 0;
+}
+
+__global__ void __launch_bounds__(kClassifyBlock) k_ac_classify_count(AcDev D, int64_t n_act, const int32_t *list,
+                                                                    int64_t t_ticks, int32_t *cta_count)
+{
+    __shared__ int32_t s_warp[kClassifyBlock / 32];
+    const int64_t c0 = (int64_t)blockIdx.x * kClassifyChunk;
+    int cnt = 0;
+    for (int64_t k = c0 + threadIdx.x; k < n_act && k < c0 + kClassifyChunk; k += kClassifyBlock)
+        cnt += ac_regular_row(D, list, k, t_ticks);
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = cnt;
     __syncthreads();
-    if (threadIdx.x == 0 && atomicAdd(&D.tickets[0], 1u) == gridDim.x - 1) {
-        __threadfence();
-        if (atomicAdd(counter, 0u) != (unsigned)expected) atomicOr(status, ST_DEVICE);
-        atomicExch(counter, 0u);
-        atomicExch(&D.tickets[0], 0u);
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < kClassifyBlock / 32; ++w) tot += s_warp[w];
+        cta_count[blockIdx.x] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kClassifyBlock)
+    k_ac_classify_place(AcDev D, int64_t n_act, const int32_t *list, int64_t t_ticks, const int32_t *cta_count,
+                        int32_t *reg_pos, int32_t *reg_idx, double *reg_rs2, int64_t expected, unsigned *status)
+{
+    __shared__ int32_t s_warp[kClassifyBlock / 32];
+    __shared__ int64_t s_part[kClassifyBlock / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // the regular rows of the chunks before this one (CTA 0: of all chunks, for the check)
+    const int nb = blockIdx.x == 0 ? (int)gridDim.x : (int)blockIdx.x;
+    int64_t part = 0;
+    for (int b = tid; b < nb; b += kClassifyBlock) part += cta_count[b];
+    part = warp_sum(part);
+    if (lane == 0) s_part[w] = part;
+    __syncthreads();
+    int64_t tot = 0;
+    for (int q = 0; q < kClassifyBlock / 32; ++q) tot += s_part[q];
+    // the host's prediction must be the classified count (else a device error of the step)
+    if (blockIdx.x == 0 && tid == 0 && tot != expected) atomicOr(status, ST_DEVICE);
+    int64_t run = blockIdx.x == 0 ? 0 : tot;
+    const int64_t c0 = (int64_t)blockIdx.x * kClassifyChunk;
+    for (int64_t r0 = c0; r0 < c0 + kClassifyChunk && r0 < n_act; r0 += kClassifyBlock) {
+        const int64_t k = r0 + tid;
+        const bool reg = k < n_act && ac_regular_row(D, list, k, t_ticks);
+        const unsigned m = __ballot_sync(0xffffffffu, reg);
+        if (lane == 0) s_warp[w] = __popc(m);
+        __syncthreads();
+        int64_t before = run;
+        int round_total = 0;
+        for (int q = 0; q < kClassifyBlock / 32; ++q) {
+            if (q < w) before += s_warp[q];
+            round_total += s_warp[q];
+        }
+        if (k < n_act) {
+            int32_t p = -1;
+            if (reg) {
+                p = (int32_t)(before + __popc(m & ((1u << lane) - 1u)));
+                const int32_t i = list[k];
+                reg_idx[p] = i;
+                reg_rs2[p] = D.rs2[i];
+            }
+            reg_pos[k] = p;
+        }
+        run += round_total;
+        __syncthreads();  // s_warp is rewritten in the next round
     }
 }
 
 __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double t, int64_t t_ticks,
                              const int32_t *reg_pos, const double *Fo, const double *Jo, const double *Fa,
                              const double *Ja, const double *Fn, const double *Jn, const int32_t *cnt_true,
-                             int32_t *want, unsigned long long *pairs, unsigned *status)
+                             int32_t *want, unsigned long long *pairs, unsigned *status, const StepParams *dyn)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += (int64_t)gridDim.x * blockDim.x) {
+    if (dyn) {  // a device-driven step: its prefix and block time (nothing to do when halted)
+        if (dyn->halt) return;
+        n_act = dyn->n_act;
+        t = dyn->t;
+        t_ticks = dyn->t_ticks;
+    }
+    // CTAs past the rows have nothing to do and take no part in the last-CTA epilogue
+    const int64_t per = (int64_t)gridDim.x * blockDim.x;
+    const int64_t used = n_act <= 0 ? 1 : (n_act < per ? (n_act + blockDim.x - 1) / blockDim.x : gridDim.x);
+    if (blockIdx.x >= used) return;
+    unsigned long long my_pairs = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_act; k += per) {
+        // every input is loaded before the first store: the state arrays are separate
+        // allocations, but the compiler cannot know it and would otherwise order each load
+        // behind the stores before it, a chain of dependent memory round trips per row
         const int32_t i = list[k];
         // reg_pos == null: the host predicted no regular particle in this step and skipped the
         // classify launch; a particle that is due for a regular step is then a device error
-        int32_t p = -1;
-        if (reg_pos) {
-            p = reg_pos[k];
-        } else if ((t_ticks & (((int64_t)1 << (kAcTick - D.LR[i])) - 1)) == 0) {
-            atomicOr(status, ST_DEVICE);
+        const int32_t p = reg_pos ? reg_pos[k] : -1;
+        const int LR0 = D.LR[i], LI0 = D.LI[i];
+        const double Tr = D.Tr[i], tl = D.tl[i], mi = D.m[i];
+        double x0[3], v0[3], a0[3], j0[3], Fr[3], Jr[3], D2[3], D3[3], fo[3], jo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t q = 3 * i + c;
+            x0[c] = D.x[q];
+            v0[c] = D.v[q];
+            a0[c] = D.a[q];
+            j0[c] = D.jk[q];
+            Fr[c] = D.Fr[q];
+            Jr[c] = D.Jr[q];
+            D2[c] = D.D2[q];
+            D3[c] = D.D3[q];
+            fo[c] = Fo[3 * k + c];
+            jo[c] = Jo[3 * k + c];
         }
-        atomicAdd(pairs, (unsigned long long)D.ell_cnt[i]);
+        my_pairs += (unsigned long long)D.ell_cnt[i];
+        if (!reg_pos && (t_ticks & (((int64_t)1 << (kAcTick - LR0)) - 1)) == 0) atomicOr(status, ST_DEVICE);
         double a1[3], j1[3];
-        int lr_old = -1;
+        int LR = LR0;
         if (p < 0) {
-            const double tau = t - D.Tr[i];
+            const double tau = t - Tr;
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const int64_t q = 3 * i + c;
-                const double Fx = D.Fr[q] + D.Jr[q] * tau + D.D2[q] * tau * tau / 2.0 + D.D3[q] * tau * tau * tau / 6.0;
-                const double Jx = D.Jr[q] + D.D2[q] * tau + D.D3[q] * tau * tau / 2.0;
-                a1[c] = Fo[3 * k + c] + Fx;
-                j1[c] = Jo[3 * k + c] + Jx;
+                const double Fx = Fr[c] + Jr[c] * tau + D2[c] * tau * tau / 2.0 + D3[c] * tau * tau * tau / 6.0;
+                const double Jx = Jr[c] + D2[c] * tau + D3[c] * tau * tau / 2.0;
+                a1[c] = fo[c] + Fx;
+                j1[c] = jo[c] + Jx;
             }
         } else {
-            double Fold[3], Jold[3], a2r[3], a3r[3];
-            const double H = t - D.Tr[i];
-            lr_old = D.LR[i];
+            double Fold[3], Jold[3], a2r[3], a3r[3], fn[3], jn[3];
+            const double H = t - Tr;
+            const int32_t ct = cnt_true[p];
+            const double rs2 = D.rs2[i];
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const int64_t q = 3 * i + c;
                 a1[c] = Fa[3 * p + c];
                 j1[c] = Ja[3 * p + c];
-                Fold[c] = a1[c] - Fo[3 * k + c];
-                Jold[c] = j1[c] - Jo[3 * k + c];
-                const double df = D.Fr[q] - Fold[c];
-                const double a2 = (-6.0 * df - H * (4.0 * D.Jr[q] + 2.0 * Jold[c])) / (H * H);
-                const double a3 = (12.0 * df + 6.0 * H * (D.Jr[q] + Jold[c])) / (H * H * H);
+                fn[c] = Fn[3 * p + c];
+                jn[c] = Jn[3 * p + c];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Fold[c] = a1[c] - fo[c];
+                Jold[c] = j1[c] - jo[c];
+                const double df = Fr[c] - Fold[c];
+                const double a2 = (-6.0 * df - H * (4.0 * Jr[c] + 2.0 * Jold[c])) / (H * H);
+                const double a3 = (12.0 * df + 6.0 * H * (Jr[c] + Jold[c])) / (H * H * H);
                 a2r[c] = a2 + H * a3;
                 a3r[c] = a3;
             }
             const double critR = ac_crit(D.eta_reg, Fold, Jold, a2r, a3r);
-            D.LR[i] = ac_level_rule(D.LR[i], critR, t_ticks, D.lmin, D.lmax);
+            LR = ac_level_rule(LR0, critR, t_ticks, D.lmin, D.lmax);
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int64_t q = 3 * i + c;
-                D.Fr[q] = a1[c] - Fn[3 * p + c];
-                D.Jr[q] = j1[c] - Jn[3 * p + c];
+                D.Fr[q] = a1[c] - fn[c];
+                D.Jr[q] = j1[c] - jn[c];
                 D.D2[q] = a2r[c];
                 D.D3[q] = a3r[c];
             }
             D.Tr[i] = t;
             if (D.nb_opt > 0) {
-                const int32_t ct = cnt_true[p];
                 double f = pow((double)D.nb_opt / (double)(ct > 0 ? ct : 1), 2.0 / 3.0);
                 f = f < 0.5 ? 0.5 : (f > 2.0 ? 2.0 : f);
-                D.rs2[i] *= f;
+                D.rs2[i] = rs2 * f;
             }
         }
         // Hermite corrector on the total force; the predicted state is recomputed here with
         // the predictor's own function (bit-identical to the all-particle predictor)
-        const double h = t - D.tl[i];
-        double a2[3], a3[3], a2e[3];
+        const double h = t - tl;
+        double a2[3], a3[3], a2e[3], x1[3], v1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double xp, vp;
+            hermite_taylor(x0[c], v0[c], a0[c], j0[c], h, xp, vp);
+            hermite_correct(xp, vp, a0[c], j0[c], a1[c], j1[c], h, x1[c], v1[c], a2[c], a3[c]);
+            a2e[c] = a2[c] + h * a3[c];
+        }
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int64_t q = 3 * i + c;
-            double xp, vp;
-            hermite_taylor(D.x[q], D.v[q], D.a[q], D.jk[q], h, xp, vp);
-            double x1, v1;
-            hermite_correct(xp, vp, D.a[q], D.jk[q], a1[c], j1[c], h, x1, v1, a2[c], a3[c]);
-            D.x[q] = x1;
-            D.v[q] = v1;
+            D.x[q] = x1[c];
+            D.v[q] = v1[c];
             D.a[q] = a1[c];
             D.jk[q] = j1[c];
-            a2e[c] = a2[c] + h * a3[c];
         }
         D.tl[i] = t;
         const double crit = ac_crit(D.eta_irr, a1, j1, a2e, a3);
-        int L = ac_level_rule(D.LI[i], crit, t_ticks, D.lmin, D.lmax);
+        int L = ac_level_rule(LI0, crit, t_ticks, D.lmin, D.lmax);
         if (p >= 0) {
-            if (D.LR[i] > L) D.LR[i] = L;  // regular step at least the new irregular step
-            if (D.LR[i] != lr_old) {
-                atomicSub(&D.lr_hist[lr_old], 1);
-                atomicAdd(&D.lr_hist[D.LR[i]], 1);
+            if (LR > L) LR = L;  // regular step at least the new irregular step
+            D.LR[i] = LR;
+            if (LR != LR0) {
+                atomicSub(&D.lr_hist[LR0], 1);
+                atomicAdd(&D.lr_hist[LR], 1);
             }
-        } else if (L < D.LR[i]) {
-            L = D.LR[i];  // irregular step at most the regular step
+        } else if (L < LR) {
+            L = LR;  // irregular step at most the regular step
         }
         D.LI[i] = L;
         want[k] = L;
-        pack_state_one(i, D.x + 3 * i, D.v + 3 * i, D.a + 3 * i, D.jk + 3 * i, t, D.m[i], D.s64, D.s32);
+        pack_state_one(i, x1, v1, a1, j1, t, mi, D.s64, D.s32);
     }
+    // one atomic per warp for the neighbour-pair count (a row's count is at most nb_cap)
+    const unsigned wp = __reduce_add_sync(0xffffffffu, (unsigned)my_pairs);
+    if ((threadIdx.x & 31) == 0 && wp) atomicAdd(pairs, (unsigned long long)wp);
+    if (dyn) return;  // a batch of device-driven steps publishes once, after its last step
     // the last CTA to finish publishes the final histogram and the step's status flags to the
-    // host words (read after the scheduler's synchronisation) and clears the flags
+    // host words (read after the scheduler's synchronisation; the flags are OR-ed in, so a batch
+    // of device-driven steps reports every step's) and clears the device flags
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&D.tickets[1], 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(&D.tickets[1], 1u) == (unsigned)used - 1;
     __syncthreads();
     if (last) {
         __threadfence();
         for (int b = threadIdx.x; b < 64; b += blockDim.x) D.io[b] = __ldcg(&D.lr_hist[b]);
         if (threadIdx.x == 0) {
-            D.io[64] = (int32_t)atomicExch(status, 0u);
+            D.io[64] |= (int32_t)atomicExch(status, 0u);  // the host clears it after reading
             atomicExch(&D.tickets[1], 0u);
         }
     }
+}
+
+// A device-driven block step without a regular subset, fused: for every row of the step's
+// prefix one warp computes the irregular force (the irregular force kernels' own per-row code:
+// the lanes stride over the row's list, neighbours predicted on load from the state records,
+// the same fixed-order warp reduction) and then the corrector of k_ac_correct's irregular
+// branch, lane c taking component c and every lane the shared step rule (the FP64 pipe runs a
+// warp instruction in the same time with one lane active or 32, so the per-row chain is the
+// one component's, not three).  The corrected state records go to rec_new[k] (list position),
+// not to the records the other rows are reading: the scheduler's re-sort, the next kernel,
+// copies them in.  Rows are spread over the CTAs first (row k: CTA k mod G), so a short
+// prefix has one busy warp per SM sub-partition.  The arithmetic is k_irregular_* followed by
+// k_ac_correct, operation for operation, so the state after the step is the same bits.
+constexpr int kStepWarps = 4;
+constexpr int64_t kDevicePrefix = 16384;  // the longest prefix a device-driven step takes
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, int64_t n, const int32_t *list,
+                                                                     uint4 *rec_new, int32_t *want,
+                                                                     unsigned long long *pairs, unsigned *status,
+                                                                     const StepParams *dyn)
+{
+    pdl_trigger();
+    pdl_wait();
+    if (dyn->halt) return;
+    IrrArgs A{};
+    A.srec = MIXED ? (const void *)D.s32 : (const void *)D.s64;
+    A.n = n;
+    A.n_i = dyn->n_act;
+    A.idx = list;
+    A.nb = D.ell;
+    A.t = dyn->t;
+    A.t_hi = dyn->t_hi;
+    A.t_lo = dyn->t_lo;
+    A.status = status;
+    A.ell_cnt = D.ell_cnt;
+    A.ell_stride = D.cap;
+    const int64_t t_ticks = dyn->t_ticks;
+    const double t = A.t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = lane < 3 ? lane : 0;  // the component lanes 0-2 correct (the others shadow 0)
+    unsigned my_pairs = 0;
+    for (int64_t k = blockIdx.x + (int64_t)gridDim.x * w; k < A.n_i; k += (int64_t)gridDim.x * kStepWarps) {
+        int64_t i, e0, e1;
+        const bool ok = irr_row(A, k, lane, i, e0, e1);
+        // the corrector's inputs do not depend on the force: requested before the list pass
+        const int64_t ii = ok ? i : 0, q = 3 * ii + c;
+        const int LR0 = D.LR[ii], LI0 = D.LI[ii];
+        const double Tr = D.Tr[ii], tl = D.tl[ii], mi = D.m[ii];
+        const double x0 = D.x[q], v0 = D.v[q], a0 = D.a[q], j0 = D.jk[q];
+        const double Fr = D.Fr[q], Jr = D.Jr[q], D2 = D.D2[q], D3 = D.D3[q];
+        double fo, jo;  // the irregular force and jerk, component c
+        if constexpr (MIXED) {
+            const float4 *S = static_cast<const float4 *>(A.srec);
+            float ih[3] = {0, 0, 0}, il[3] = {0, 0, 0}, iv[3] = {0, 0, 0}, iD[3] = {0, 0, 0}, iE[3] = {0, 0, 0};
+            if (ok) {
+                const float4 P = S[5 * i], L = S[5 * i + 1], V = S[5 * i + 2], Ac = S[5 * i + 3], J = S[5 * i + 4];
+                const float dt = __fadd_rn(__fsub_rn(A.t_hi, L.w), __fsub_rn(A.t_lo, V.w));
+                ih[0] = P.x; ih[1] = P.y; ih[2] = P.z;
+                il[0] = L.x; il[1] = L.y; il[2] = L.z;
+                iv[0] = V.x; iv[1] = V.y; iv[2] = V.z;
+                incr_f32(V.x, Ac.x, J.x, dt, iD[0], iE[0]);
+                incr_f32(V.y, Ac.y, J.y, dt, iD[1], iE[1]);
+                incr_f32(V.z, Ac.z, J.z, dt, iD[2], iE[2]);
+            }
+            float f[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
+                const int32_t j = irr_neighbour(A, e, e1);
+                if (j < 0 || j == i) continue;
+                float4 R[5];
+#pragma unroll
+                for (int u = 0; u < 5; ++u) R[u] = S[5 * (int64_t)j + u];
+                state_pair_mixed(R, A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
+            }
+            float h, l;
+            warp_sum7_df(f, lane, h, l);
+            const double v = ok ? __dadd_rn((double)h, (double)l) : 0.0;  // lane 4 c': component c'
+            fo = __shfl_sync(0xffffffffu, v, 4 * c);
+            jo = __shfl_sync(0xffffffffu, v, 4 * (c + 3));
+        } else {
+            const dvec4 *S = static_cast<const dvec4 *>(A.srec);
+            double own = 0.0;
+            if (ok && lane < 6) {
+                const int cc = lane < 3 ? lane : lane - 3;
+                const dvec4 P = S[4 * i], V = S[4 * i + 1], Ac = S[4 * i + 2], J = S[4 * i + 3];
+                auto pick = [cc](const dvec4 &u) { return cc == 0 ? u.x : (cc == 1 ? u.y : u.z); };
+                double xp, vp;
+                hermite_taylor(pick(P), pick(V), pick(Ac), pick(J), __dsub_rn(A.t, P.w), xp, vp);
+                own = lane < 3 ? xp : vp;
+            }
+            double xi[3], vi[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                xi[u] = __shfl_sync(0xffffffffu, own, u);
+                vi[u] = __shfl_sync(0xffffffffu, own, 3 + u);
+            }
+            double sum[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
+                const int64_t j = A.nb[e];
+                if (j < 0 || j >= A.n) {
+                    atomicOr(A.status, ST_BAD_INDEX);
+                    continue;
+                }
+                if (j == i) continue;
+                const dvec4 P = S[4 * j], V = S[4 * j + 1], Ac = S[4 * j + 2], J = S[4 * j + 3];
+                const double dt = __dsub_rn(A.t, P.w);
+                double x0j, x1j, x2j, v0j, v1j, v2j;
+                hermite_taylor(P.x, V.x, Ac.x, J.x, dt, x0j, v0j);
+                hermite_taylor(P.y, V.y, Ac.y, J.y, dt, x1j, v1j);
+                hermite_taylor(P.z, V.z, Ac.z, J.z, dt, x2j, v2j);
+                pair_f64(make_dvec4(x0j, x1j, x2j, V.w), make_dvec4(v0j, v1j, v2j, 0.0), xi, vi, false, sum);
+            }
+#pragma unroll
+            for (int u = 0; u < 7; ++u) sum[u] = warp_sum(sum[u]);
+            fo = jo = 0.0;
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+                if (c == u) {
+                    fo = sum[u];
+                    jo = sum[3 + u];
+                }
+            if (!ok) fo = jo = 0.0;
+        }
+        if (!ok) continue;  // (warp-uniform) the status bit is set; the row is left as it was
+        // k_ac_correct's irregular branch, component c: the extrapolated regular force ...
+        const double tau = t - Tr;
+        const double Fx = Fr + Jr * tau + D2 * tau * tau / 2.0 + D3 * tau * tau * tau / 6.0;
+        const double Jx = Jr + D2 * tau + D3 * tau * tau / 2.0;
+        const double a1 = fo + Fx, j1 = jo + Jx;
+        // ... and the Hermite corrector on the total force
+        const double h = t - tl;
+        double xp, vp, x1, v1, a2, a3;
+        hermite_taylor(x0, v0, a0, j0, h, xp, vp);
+        hermite_correct(xp, vp, a0, j0, a1, j1, h, x1, v1, a2, a3);
+        const double a2e = a2 + h * a3;
+        double A1[3], J1[3], A2E[3], A3[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            A1[u] = __shfl_sync(0xffffffffu, a1, u);
+            J1[u] = __shfl_sync(0xffffffffu, j1, u);
+            A2E[u] = __shfl_sync(0xffffffffu, a2e, u);
+            A3[u] = __shfl_sync(0xffffffffu, a3, u);
+        }
+        const double crit = ac_crit(D.eta_irr, A1, J1, A2E, A3);
+        int L = ac_level_rule(LI0, crit, t_ticks, D.lmin, D.lmax);
+        if (L < LR0) L = LR0;  // irregular step at most the regular step
+        if (lane < 3) {
+            D.x[q] = x1;
+            D.v[q] = v1;
+            D.a[q] = a1;
+            D.jk[q] = j1;
+        }
+        // the new state record (pack_state_one's layout and conversions), lane c its component
+        if constexpr (MIXED) {
+            float *R = reinterpret_cast<float *>(rec_new + 5 * k);
+            if (lane < 3) {
+                const float hx = __double2float_rn(x1);
+                R[c] = hx;
+                R[4 + c] = __double2float_rn(__dsub_rn(x1, (double)hx));
+                R[8 + c] = __double2float_rn(v1);
+                R[12 + c] = __double2float_rn(a1);
+                R[16 + c] = __double2float_rn(j1);
+            } else if (lane == 3) {
+                const float th = __double2float_rn(t);
+                R[3] = __double2float_rn(mi);
+                R[7] = th;
+                R[11] = __double2float_rn(__dsub_rn(t, (double)th));
+                R[15] = 0.f;
+                R[19] = 0.f;
+            }
+        } else {
+            double *R = reinterpret_cast<double *>(rec_new + 8 * k);
+            if (lane < 3) {
+                R[c] = x1;
+                R[4 + c] = v1;
+                R[8 + c] = a1;
+                R[12 + c] = j1;
+            } else if (lane == 3) {
+                R[3] = t;
+                R[7] = mi;
+                R[11] = 0.0;
+                R[15] = 0.0;
+            }
+        }
+        if (lane == 0) {
+            if ((t_ticks & (((int64_t)1 << (kAcTick - LR0)) - 1)) == 0) atomicOr(status, ST_DEVICE);
+            D.tl[i] = t;
+            D.LI[i] = L;
+            want[k] = L;
+            my_pairs += (unsigned)D.ell_cnt[i];
+        }
+    }
+    if (lane == 0 && my_pairs) atomicAdd(pairs, (unsigned long long)my_pairs);
 }
 
 // The regular subset's new lists (CSR) replace the old per-particle lists; one warp per row.
@@ -305,6 +590,71 @@ __global__ void k_ac_get_steps(const AcDev D, int64_t n, double *dt, double *DT,
     }
 }
 
+// The first kernel of a device-driven block step (one thread): the next block time and the
+// active prefix from the scheduler's device counts, as nb_sched_next finds them on the host.
+// The step halts, and with it every step queued after it, when that time passes t_end, when
+// the regular-level histogram says some particle takes a regular step there (the host path
+// runs those), when the prefix is longer than one device re-sort takes, or when the batch's
+// budget dstep[0] is spent; otherwise it counts the step (dstep[1]) and its rows (dstep[2]).
+__global__ void __launch_bounds__(32) k_ac_begin(StepParams *P, SchedDevice S, const int32_t *lr_hist, double t_end,
+                                                  int64_t *dstep)
+{
+    // one warp: lane l holds the levels l and l + 32
+    pdl_trigger();
+    pdl_wait();
+    if (P->halt) return;
+    const int lane = threadIdx.x;
+    const int64_t c_lo = S.count[lane], c_hi = S.count[lane + 32];
+    const int32_t r_lo = lr_hist[lane], r_hi = lr_hist[lane + 32];
+    if (dstep[0] <= 0) {
+        if (lane == 0) P->halt = STEP_BUDGET;
+        return;
+    }
+    const unsigned m_hi = __ballot_sync(0xffffffffu, c_hi != 0), m_lo = __ballot_sync(0xffffffffu, c_lo != 0);
+    const int lmax = m_hi ? 63 - __clz(m_hi) : (m_lo ? 31 - __clz(m_lo) : -1);
+    if (lmax < 0) {
+        if (lane == 0) P->halt = STEP_END;
+        return;
+    }
+    const int64_t T_new = *S.T + ((int64_t)1 << (kAcTick - lmax));
+    const double t = ldexp((double)T_new, -kAcTick);
+    if (t > t_end) {
+        if (lane == 0) P->halt = STEP_END;
+        return;
+    }
+    int lstar = kAcTick - (__ffsll(T_new) - 1);
+    if (lstar < 0) lstar = 0;
+    int64_t na = (lane >= lstar ? c_lo : 0) + (lane + 32 >= lstar ? c_hi : 0);
+    int64_t nr = (lane >= lstar ? r_lo : 0) + (lane + 32 >= lstar ? r_hi : 0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_xor_sync(0xffffffffu, na, o);
+        nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    }
+    if (lane != 0) return;
+    if (nr > 0 || na > S.max_prefix) {
+        P->halt = nr > 0 ? STEP_REGULAR : STEP_LONG;
+        return;
+    }
+    P->t = t;
+    P->t_ticks = T_new;
+    P->n_act = na;
+    P->lstar = lstar;
+    P->t_hi = (float)t;
+    P->t_lo = (float)(t - (double)P->t_hi);
+    dstep[0] -= 1;
+    dstep[1] += 1;
+    dstep[2] += na;
+}
+
+// The host words after a batch of device-driven steps: the regular-level histogram and the
+// status flags the batch's steps raised (cleared on the device; the host clears its copy).
+__global__ void k_ac_publish(AcDev D, unsigned *status)
+{
+    D.io[threadIdx.x] = __ldcg(&D.lr_hist[threadIdx.x]);
+    if (threadIdx.x == 0) D.io[64] |= (int32_t)atomicExch(status, 0u);
+}
+
 static int grid_of(int64_t n, int block, int cap_ctas)
 {
     int64_t g = (n + block - 1) / block;
@@ -328,12 +678,16 @@ struct nb_ac {
     int64_t *off = nullptr;
     double *reg_rs2 = nullptr, *Fo = nullptr, *Jo = nullptr, *Po = nullptr, *Fa = nullptr, *Ja = nullptr,
            *Pa = nullptr, *Fn = nullptr, *Jn = nullptr, *Pn = nullptr;
-    unsigned *counter = nullptr;  // regular rows classified so far in this step (reset by the last CTA)
+    int32_t *cta_count = nullptr;  // regular rows per list chunk of the classify passes
     void *srec = nullptr;  // state records (pack_state_one layout of the context's precision)
     unsigned long long *pairs = nullptr;
     int32_t *h_io = nullptr;       // pinned, mapped: [0, 64) regular-level histogram, [64] status flags
     int32_t *h_lr = nullptr;       // = h_io
-    unsigned *h_status = nullptr;  // = h_io + 64: the context's status flags of the last block step
+    unsigned *h_status = nullptr;  // = h_io + 64: the context's status flags since the host last read them
+    StepParams *P = nullptr;       // device-driven steps: the current step's parameters
+    int64_t *dstep = nullptr;      // device-driven steps: [0] budget left, [1] steps done, [2] active rows
+    uint4 *rec_new = nullptr;      // device-driven steps: the corrected records of a step's prefix
+    int64_t rec_rows = 0;          // ... for up to this many rows
     bool overflow = false;         // some neighbour list was cut at nb_cap
     double stats[6] = {0, 0, 0, 0, 0, 0};
     char err[384] = {0};
@@ -382,15 +736,21 @@ static bool ac_alloc(nb_ac *s, int64_t n, int cap)
         cudaMalloc(&s->Fa, v3) == cudaSuccess && cudaMalloc(&s->Ja, v3) == cudaSuccess &&
         cudaMalloc(&s->Pa, n * 8) == cudaSuccess && cudaMalloc(&s->Fn, v3) == cudaSuccess &&
         cudaMalloc(&s->Jn, v3) == cudaSuccess && cudaMalloc(&s->Pn, n * 8) == cudaSuccess &&
-        cudaMalloc(&s->counter, 4) == cudaSuccess &&
+        cudaMalloc(&s->cta_count, ((n + kClassifyChunk - 1) / kClassifyChunk + 1) * 4) == cudaSuccess &&
         cudaMalloc(&s->pairs, 8) == cudaSuccess && cudaMalloc(&D.lr_hist, 64 * 4) == cudaSuccess &&
         cudaMalloc(&D.tickets, 2 * 4) == cudaSuccess &&
         cudaHostAlloc(&s->h_io, 80 * 4, cudaHostAllocMapped) == cudaSuccess &&
         cudaHostGetDevicePointer((void **)&D.io, s->h_io, 0) == cudaSuccess &&
         cudaMemset(D.lr_hist, 0, 64 * 4) == cudaSuccess && cudaMemset(s->pairs, 0, 8) == cudaSuccess &&
-        cudaMemset(D.tickets, 0, 2 * 4) == cudaSuccess && cudaMemset(s->counter, 0, 4) == cudaSuccess &&
-        cudaMalloc(&s->srec, state_record_bytes(s->cs.precision, n)) == cudaSuccess;
+        cudaMemset(D.tickets, 0, 2 * 4) == cudaSuccess &&
+        cudaMalloc(&s->srec, state_record_bytes(s->cs.precision, n)) == cudaSuccess &&
+        cudaMalloc(&s->P, sizeof(StepParams)) == cudaSuccess && cudaMalloc(&s->dstep, 3 * sizeof(int64_t)) == cudaSuccess &&
+        cudaMemset(s->P, 0, sizeof(StepParams)) == cudaSuccess &&
+        cudaMalloc(&s->rec_new, state_record_bytes(s->cs.precision, n < kDevicePrefix ? n : kDevicePrefix)) ==
+            cudaSuccess;
+    s->rec_rows = n < kDevicePrefix ? n : kDevicePrefix;
     if (!ok) cudaGetLastError();
+    if (s->h_io) memset(s->h_io, 0, 80 * 4);
     s->h_lr = s->h_io;
     s->h_status = s->h_io ? reinterpret_cast<unsigned *>(s->h_io + 64) : nullptr;
     return ok;
@@ -551,8 +911,10 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     for (int b = lstar; b < 64; ++b) nr += s->h_lr[b];
     const int cap = cs.cap;
     if (nr > 0) {  // with no regular particle predicted the corrector makes the check itself
-        k_ac_classify<<<grid_of(na, 256, 152 * 16), 256, 0, st>>>(s->D, na, list, t_ticks, s->counter, s->reg_pos,
-                                                                   s->reg_idx, s->reg_rs2, nr, cs.status + SS_FLAGS);
+        const int cg = (int)((na + kClassifyChunk - 1) / kClassifyChunk);
+        k_ac_classify_count<<<cg, kClassifyBlock, 0, st>>>(s->D, na, list, t_ticks, s->cta_count);
+        k_ac_classify_place<<<cg, kClassifyBlock, 0, st>>>(s->D, na, list, t_ticks, s->cta_count, s->reg_pos,
+                                                           s->reg_idx, s->reg_rs2, nr, cs.status + SS_FLAGS);
         ACK(cudaGetLastError(), "classify launch");
     }
     if (nr > 0) {
@@ -571,13 +933,14 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks,
                                                               nr > 0 ? s->reg_pos : nullptr, s->Fo, s->Jo,
                                                               s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
-                                                              s->pairs, cs.status + SS_FLAGS);
+                                                              s->pairs, cs.status + SS_FLAGS, nullptr);
     if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);
     ACK(cudaGetLastError(), "corrector launch");
     ctx_state_changed(s->ctx);  // the corrector rewrote the context's state arrays
     ss = nb_sched_update(s->sched, s->want, nullptr, 1);  // synchronises the stream
     if (ss != NB_OK) return afail(s, ss, "nb_sched_update: %s", nb_sched_last_error(s->sched));
     const unsigned f = *s->h_status;
+    *s->h_status = 0;
     if (f & (ST_BAD_INDEX | ST_DUP_INDEX | ST_DEVICE | ST_TIMEOUT))
         return afail(s, NB_ERR_DEVICE, "block step at t = %.17g: device status 0x%x", t, f);
     if (f & (ST_NB_TRUNCATED | ST_CSR_FULL)) s->overflow = true;
@@ -601,9 +964,97 @@ static nb_status ac_read_stats(nb_ac *s)
     return NB_OK;
 }
 
+// Whether the block step at time t has a regular subset, from the regular-level histogram
+// the last corrector published (the test nb_ac_step makes before it launches).
+static bool ac_regular_due(const nb_ac *s, double t)
+{
+    const int64_t t_ticks = (int64_t)std::ldexp(t, kAcTick);
+    int tz = 0;
+    while (tz < kAcTick && ((t_ticks >> tz) & 1) == 0) ++tz;
+    int64_t nr = 0;
+    for (int b = kAcTick - tz; b < 64; ++b) nr += s->h_lr[b];
+    return nr > 0;
+}
+
+// Up to K block steps without a regular subset, driven by the device: per step the begin
+// kernel, the irregular force (predict on load), the corrector and the scheduler's re-sort,
+// all reading the step's parameters from device memory, so the host enqueues the whole batch
+// and synchronises once.  The first step that needs the host (a regular subset, a prefix too
+// long for one re-sort CTA) or the end time halts the rest.  *done: the steps taken.
+static nb_status ac_device_steps(nb_ac *s, double t_end, int64_t K, int64_t *done)
+{
+    *done = 0;
+    SchedDevice S;
+    if (!sched_device(s->sched, &S)) return afail(s, NB_ERR_OOM, "device scheduler state");
+    if (S.max_prefix > s->rec_rows) S.max_prefix = s->rec_rows;  // longer prefixes: the host path
+    if (!sched_push(s->sched)) return afail(s, NB_ERR_CUDA, "scheduler state to the device");
+    const CtxState &cs = s->cs;
+    cudaStream_t st = cs.stream;
+    int64_t h[3] = {K, 0, 0};
+    int32_t halt = 0;
+    ACK(cudaMemsetAsync(&s->P->halt, 0, sizeof(int32_t), st), "clear halt");
+    ACK(cudaMemcpyAsync(s->dstep, h, sizeof(h), cudaMemcpyHostToDevice, st), "step budget");
+    // per step: begin, the fused irregular force and corrector, the re-sort (which copies the
+    // corrected records in); each a programmatic dependent of the one before, except the first
+    const int rb = (int)state_record_bytes(cs.precision, 1);
+    auto step_kernel = cs.precision == 0 ? k_ac_irregular_step<false> : k_ac_irregular_step<true>;
+    const dim3 sgrid(2 * cs.num_sms), sblock(kStepWarps * 32);
+    for (int64_t k = 0; k < K; ++k) {
+        ACK(launch_pdl(k > 0, k_ac_begin, dim3(1), dim3(32), st, s->P, S, (const int32_t *)s->D.lr_hist, t_end,
+                       s->dstep),
+            "begin launch");
+        ACK(launch_pdl(true, step_kernel, sgrid, sblock, st, s->D, cs.n, (const int32_t *)S.list, s->rec_new,
+                       s->want, s->pairs, cs.status + SS_FLAGS, (const StepParams *)s->P),
+            "block-step launch");
+        if (!sched_device_sort(s->sched, s->want, s->P, s->rec_new, s->srec, rb, true))
+            return afail(s, NB_ERR_CUDA, "device re-sort launch");
+    }
+    k_ac_publish<<<1, 64, 0, st>>>(s->D, cs.status + SS_FLAGS);
+    ACK(cudaGetLastError(), "device step launches");
+    ACK(cudaMemcpyAsync(h, s->dstep, sizeof(h), cudaMemcpyDeviceToHost, st), "step counters");
+    ACK(cudaMemcpyAsync(&halt, &s->P->halt, sizeof(halt), cudaMemcpyDeviceToHost, st), "halt flag");
+    if (!sched_pull(s->sched)) return afail(s, NB_ERR_CUDA, "scheduler state from the device");  // synchronises
+    if (h[1] > 0) ctx_state_changed(s->ctx);  // the correctors rewrote the context's state arrays
+    const unsigned f = *s->h_status;
+    *s->h_status = 0;
+    if (f & (ST_BAD_INDEX | ST_DUP_INDEX | ST_DEVICE | ST_TIMEOUT))
+        return afail(s, NB_ERR_DEVICE, "device-driven block steps: device status 0x%x", f);
+    if (f & (ST_NB_TRUNCATED | ST_CSR_FULL)) s->overflow = true;
+    *done = h[1];
+    s->stats[0] += (double)h[1];
+    s->stats[1] += (double)h[2];
+    return NB_OK;
+}
+
+// The number of block steps from the next one (at tn) up to, not including, the next step
+// with a regular subset or the first step past t_end, if the levels stay as they are: the
+// block time advances by the finest irregular step present, and the next regular subset falls
+// on the first multiple of the finest regular step present (the published histogram).
+static int64_t ac_run_length(nb_ac *s, double tn, double t_end)
+{
+    int64_t counts[64];
+    if (nb_sched_counts(s->sched, counts) != NB_OK) return 1;
+    int li = -1, lr = -1;
+    for (int b = 63; b >= 0; --b)
+        if (li < 0 && counts[b]) li = b;
+    for (int b = 63; b >= 0; --b)
+        if (lr < 0 && s->h_lr[b]) lr = b;
+    if (li < 0) return 1;
+    const double dt = std::ldexp(1.0, -li);
+    double t_stop = t_end + dt;  // the first block time past t_end
+    if (lr >= 0) {
+        const double DT = std::ldexp(1.0, -lr);
+        const double t_reg = std::ceil(tn / DT) * DT;  // the next regular time (tn is not one)
+        if (t_reg < t_stop) t_stop = t_reg;
+    }
+    const double k = (t_stop - tn) / dt;
+    return k < 1.0 ? 1 : (k > 1e6 ? 1000000 : (int64_t)k);
+}
+
 nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats)
 {
     if (!s) return NB_ERR_ARG;
+    constexpr int64_t kMaxBatch = 128;
     int64_t b = 0;
     nb_status rc = NB_OK;
     for (;;) {
@@ -616,8 +1067,20 @@ nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats)
             afail(s, rc, "max_blocks reached");
             break;
         }
-        if ((ss = nb_ac_step(s, nullptr, nullptr, nullptr)) != NB_OK) return ss;
-        ++b;
+        int64_t done = 0;
+        if (!ac_regular_due(s, tn)) {  // a run of steps without regular subsets: the device drives them
+            // as many steps as the run should hold (a finer level ends the batch early, through its
+            // budget; a coarser one halts it at the regular step, the rest of the batch no-ops)
+            int64_t k = ac_run_length(s, tn, t_end);
+            if (k > kMaxBatch) k = kMaxBatch;
+            if (max_blocks > 0 && max_blocks - b < k) k = max_blocks - b;
+            if ((ss = ac_device_steps(s, t_end, k, &done)) != NB_OK) return ss;
+            b += done;
+        }
+        if (done == 0) {  // a regular subset is due (or the device took no step): the host path
+            if ((ss = nb_ac_step(s, nullptr, nullptr, nullptr)) != NB_OK) return ss;
+            ++b;
+        }
     }
     if (stats) {
         nb_status ss = ac_read_stats(s);
@@ -762,7 +1225,8 @@ nb_status nb_ac_free(nb_ac *s)
     if (s->sched) nb_sched_free(s->sched);
     void *p[] = {s->D.Fr, s->D.Jr, s->D.D2, s->D.D3, s->D.rs2, s->D.Tr, s->D.LR, s->D.LI, s->D.ell, s->D.ell_cnt,
                  s->reg_pos, s->reg_idx, s->want, s->cnt_true, s->csr, s->off, s->reg_rs2, s->Fo, s->Jo, s->Po,
-                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->counter, s->pairs, s->D.lr_hist, s->D.tickets, s->srec};
+                 s->Fa, s->Ja, s->Pa, s->Fn, s->Jn, s->Pn, s->cta_count, s->pairs, s->D.lr_hist, s->D.tickets, s->srec,
+                 s->P, s->dstep, s->rec_new};
     for (void *q : p)
         if (q) cudaFree(q);
     if (s->h_io) cudaFreeHost(s->h_io);

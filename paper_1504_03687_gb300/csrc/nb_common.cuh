@@ -27,6 +27,33 @@ enum { SS_FLAGS = 0, SS_OVERFLOW_COUNT = 1, SS_QUEUE = 2, SS_WORDS = 8 };
 
 constexpr float kPadPos = 1.0e18f;    // far-away position of the padding j-records (mass 0)
 
+// ---- programmatic dependent launch ------------------------------------------------------
+// A chain of short dependent kernels (the device-driven block steps) launches each kernel
+// with programmatic stream serialisation: its CTAs are scheduled while the kernel before it
+// still runs, and wait in pdl_wait() (griddepcontrol.wait: until the grids it depends on have
+// completed and their writes are visible) before they touch anything those grids wrote.
+// pdl_trigger() lets the next kernel's launch begin.  In a kernel launched the ordinary way
+// both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---- cp.async (LDGSTS) staging of j-tiles into shared memory ---------------------------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {

@@ -4,8 +4,43 @@
 #include <cuda_runtime.h>
 
 struct nb_ctx;
+struct nb_sched;
 
 namespace nbgpu {
+
+// ---- device-driven block steps ------------------------------------------------------------
+// The parameters of one block step held in device memory, so that a batch of block steps can
+// be enqueued with no host work in between: the step's begin kernel (ac.cu) writes them from
+// the scheduler's device state, and every later kernel of the step reads them.  A nonzero
+// halt turns every kernel of the step, and of every step queued after it, into a no-op.
+struct StepParams {
+    double t;          // block time
+    int64_t t_ticks;   // block time in ticks of 2^-48
+    int64_t n_act;     // active particles: the list prefix [0, n_act)
+    float t_hi, t_lo;  // the block time as a double-single pair
+    int32_t lstar;     // coarsest active level
+    int32_t halt;      // 0 run; 1 end time passed; 2 a regular step is due; 3 prefix too long; 4 batch done
+};
+enum { STEP_RUN = 0, STEP_END = 1, STEP_REGULAR = 2, STEP_LONG = 3, STEP_BUDGET = 4 };
+
+// The scheduler's state on the device for device-driven steps (sched.cu): the list, device
+// copies of the per-level counts and of the current time, and the longest prefix one device
+// re-sort takes (one CTA).
+struct SchedDevice {
+    int32_t *list;
+    int64_t *count;  // [64]
+    int64_t *T;
+    int64_t max_prefix;
+};
+bool sched_device(::nb_sched *s, SchedDevice *out);  // allocates the device copies on first use
+bool sched_push(::nb_sched *s);                      // host counts and time -> device (stream-ordered)
+bool sched_pull(::nb_sched *s);                      // device -> host (synchronises the stream)
+// Enqueue the re-sort of the prefix of a device-driven step (its size and level from P) by
+// the requested levels `want`; it also advances the device counts and time.  With rec_new,
+// the prefix's records (rec_bytes each, a multiple of 16, in list order) are first copied to
+// rec[particle].  pdl: launched as a programmatic dependent of the kernel before it.
+bool sched_device_sort(::nb_sched *s, const int32_t *want, const StepParams *P, const void *rec_new = nullptr,
+                       void *rec = nullptr, int rec_bytes = 0, bool pdl = false);
 
 // Predicted j-records.
 //  FP64 : 2 dvec4 per particle  {x, y, z, m}, {vx, vy, vz, 0}                   (64 B)
@@ -138,7 +173,7 @@ void launch_hermite_correct_vjp(cudaStream_t st, int64_t n, double t, const doub
 void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
                       double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
                       double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status,
-                      const int32_t *ell_cnt = nullptr, int64_t ell_stride = 0);
+                      const int32_t *ell_cnt = nullptr, int64_t ell_stride = 0, const StepParams *dyn = nullptr);
 // State records of the predict-on-load form (pack_state_one layout) for particles 0..n-1.
 size_t state_record_bytes(int precision, int64_t n);
 void launch_pack_state(cudaStream_t st, int precision, int64_t n, const double *x, const double *v, const double *a,

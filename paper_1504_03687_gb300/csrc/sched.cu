@@ -27,6 +27,7 @@
 
 #include "nbgpu.h"
 #include "nb_common.cuh"
+#include "nb_kernels.cuh"
 
 namespace nbgpu {
 
@@ -50,6 +51,12 @@ struct SortArgs {
     int32_t *cta_count;     // [ctas][kBins]
     int64_t *totals;        // [kBins] entries per new level (written by the scan)
     int32_t *bad;           // set when a stored level is outside [0, kBins) (initial sort)
+    const StepParams *dyn;  // device-driven step: n_act and lstar from here (nothing when halted)
+    int64_t *dev_count;     // device-driven step: the device counts of levels >= lstar are set
+    int64_t *dev_T;         // ... and the device time advanced to the step's block time
+    const uint4 *rec_new;   // optional (single CTA): records of the prefix in list order, copied ...
+    uint4 *rec;             // ... to rec[particle] before the re-sort; rec_u4 16-byte words each
+    int32_t rec_u4;
 };
 
 // One CTA: read its chunk of the prefix, apply the block rule, and rank every entry within
@@ -79,6 +86,8 @@ __device__ void rank_chunk(const SortArgs &A, int64_t c0, int32_t (&part)[kSortI
         int32_t p = -1, L = 0;
         if (in) {
             p = A.list[e];
+            if (A.rec)
+                for (int u = 0; u < A.rec_u4; ++u) A.rec[(int64_t)p * A.rec_u4 + u] = A.rec_new[e * A.rec_u4 + u];
             L = A.level[p];
             if (L < 0 || L >= kBins) {  // only possible for levels handed to the initial sort
                 atomicOr(A.bad, 1);
@@ -124,6 +133,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_single(SortArgs A)
     __shared__ int32_t s_cnt[kBins];
     __shared__ int32_t s_base[kBins];
     __shared__ int32_t s_warp[kSortWarps][kBins];
+    pdl_trigger();
+    pdl_wait();
+    if (A.dyn) {  // a device-driven step: its prefix and coarsest level
+        if (A.dyn->halt) return;
+        A.n_act = A.dyn->n_act;
+        A.lstar = A.dyn->lstar;
+    }
     int32_t part[kSortItems], lev[kSortItems], rank[kSortItems];
     rank_chunk(A, 0, part, lev, rank, s_cnt, s_warp);
     if (threadIdx.x == 0) {
@@ -133,7 +149,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_single(SortArgs A)
             acc += s_cnt[b];
         }
     }
-    if (threadIdx.x < kBins) A.totals[threadIdx.x] = s_cnt[threadIdx.x];
+    if (A.totals && threadIdx.x < kBins) A.totals[threadIdx.x] = s_cnt[threadIdx.x];
+    if (A.dyn) {  // the scheduler's device state moves on to the step's block time
+        if (threadIdx.x < kBins && threadIdx.x >= A.lstar) A.dev_count[threadIdx.x] = s_cnt[threadIdx.x];
+        if (threadIdx.x == 0) *A.dev_T = A.dyn->t_ticks;
+    }
     __syncthreads();  // every entry is in registers: the in-place scatter is safe
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
@@ -226,6 +246,8 @@ struct nb_sched {
     // level totals: pinned host memory mapped into the device, written by the sort kernels
     // themselves (no copy to issue); totals is the device address of h_totals
     int64_t *totals = nullptr, *h_totals = nullptr;
+    // device copies of count and T for device-driven block steps (allocated on first use)
+    int64_t *d_count = nullptr, *d_T = nullptr;
     char err[256] = {0};
 };
 
@@ -264,6 +286,12 @@ static nb_status sched_sort(nb_sched *s, int64_t n_act, const int32_t *d_want, i
     A.cta_count = s->cta_count;
     A.totals = s->totals;
     A.bad = s->bad;
+    A.dyn = nullptr;
+    A.dev_count = nullptr;
+    A.dev_T = nullptr;
+    A.rec_new = nullptr;
+    A.rec = nullptr;
+    A.rec_u4 = 0;
     if (n_act <= kChunk) {
         k_sort_single<<<1, kSortThreads, 0, s->stream>>>(A);
     } else {
@@ -280,6 +308,71 @@ static nb_status sched_sort(nb_sched *s, int64_t n_act, const int32_t *d_want, i
     SCK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
     return NB_OK;
 }
+
+// ---- device-driven block steps (the integrator's batched loop) ---------------------------
+namespace nbgpu {
+
+bool sched_device(nb_sched *s, SchedDevice *out)
+{
+    if (!s || s->pending) return false;
+    if (!s->d_count) {
+        if (cudaMalloc(&s->d_count, kBins * sizeof(int64_t)) != cudaSuccess ||
+            cudaMalloc(&s->d_T, sizeof(int64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    out->list = s->list;
+    out->count = s->d_count;
+    out->T = s->d_T;
+    out->max_prefix = kChunk;
+    return true;
+}
+
+bool sched_push(nb_sched *s)
+{
+    // pageable sources: the copies have taken the host words when the calls return
+    return cudaMemcpyAsync(s->d_count, s->count, kBins * sizeof(int64_t), cudaMemcpyHostToDevice, s->stream) ==
+               cudaSuccess &&
+           cudaMemcpyAsync(s->d_T, &s->T, sizeof(int64_t), cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
+}
+
+bool sched_pull(nb_sched *s)
+{
+    return cudaMemcpyAsync(s->count, s->d_count, kBins * sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream) ==
+               cudaSuccess &&
+           cudaMemcpyAsync(&s->T, s->d_T, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream) == cudaSuccess &&
+           cudaStreamSynchronize(s->stream) == cudaSuccess;
+}
+
+bool sched_device_sort(nb_sched *s, const int32_t *want, const StepParams *P, const void *rec_new, void *rec,
+                       int rec_bytes, bool pdl)
+{
+    SortArgs A;
+    A.list = s->list;
+    A.level = s->level;
+    A.want = want;
+    A.granted = nullptr;
+    A.n_act = 0;   // from P
+    A.lstar = 0;   // from P
+    A.lmin = s->lmin;
+    A.lmax = s->lmax;
+    A.keep_part = s->keep_part;
+    A.keep_rank = s->keep_rank;
+    A.keep_lev = s->keep_lev;
+    A.cta_count = s->cta_count;
+    A.totals = nullptr;  // the host reads the device counts after the batch instead
+    A.bad = s->bad;
+    A.dyn = P;
+    A.dev_count = s->d_count;
+    A.dev_T = s->d_T;
+    A.rec_new = static_cast<const uint4 *>(rec_new);
+    A.rec = static_cast<uint4 *>(rec);
+    A.rec_u4 = rec_bytes / 16;
+    return launch_pdl(pdl, k_sort_single, dim3(1), dim3(kSortThreads), s->stream, A) == cudaSuccess;
+}
+
+}  // namespace nbgpu
 
 extern "C" {
 
@@ -348,7 +441,7 @@ nb_status nb_sched_free(nb_sched *s)
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     void *p[] = {s->list,      s->level,    s->want_stage, s->granted_stage, s->keep_part,
-                 s->keep_rank, s->keep_lev, s->cta_count,  s->bad};
+                 s->keep_rank, s->keep_lev, s->cta_count,  s->bad,           s->d_count, s->d_T};
     for (void *q : p)
         if (q) cudaFree(q);
     if (s->h_totals) cudaFreeHost(s->h_totals);

@@ -49,6 +49,40 @@ def test_ac_fp64_follows_the_reference_step_for_step(gpu_lib):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ac_device_driven_run_equals_step_by_step(gpu_lib, prec):
+    """nb_ac_run drives the block steps without a regular subset from the device, in batches
+    the host enqueues without synchronising in between; stepping one block at a time through
+    nb_ac_step (the host path) for the same number of block steps gives bit-identical
+    positions, velocities, times, steps, lists and counters."""
+    from paper_1504_03687_gb300 import ACIntegrator
+    cl = W.plummer(4096, 105, masses="kroupa")
+    rs2 = W.neighbour_radius2(cl.x, 50, seed=105)
+    kw = dict(eta_irr=0.02, eta_reg=0.03, eta_s=0.01, dt_max=1.0 / 16, nb_opt=50)
+    ctx = make(cl.n, prec, 128)
+    a = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
+    sa = a.run(1.0 / 16, max_blocks=1000000)
+    ga = a.get()
+    a.close()
+    assert sa["blocks"] > 100 and sa["regular_steps"] > 0
+    b = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
+    n_act = n_reg = 0
+    for _ in range(sa["blocks"]):
+        _, na, nr = b.step()
+        n_act += na
+        n_reg += nr
+    gb = b.get()
+    b.close()
+    ctx.close()
+    assert n_act == sa["irregular_steps"] and n_reg == sa["regular_steps"]
+    for k in ("x", "v", "t", "dt", "DT", "T", "rs2", "nb_count"):
+        np.testing.assert_array_equal(ga[k], gb[k], err_msg=k)
+    for i in range(cl.n):
+        c = ga["nb_count"][i]
+        np.testing.assert_array_equal(ga["nb_lists"][i, :c], gb["nb_lists"][i, :c])
+    assert np.all(ga["t"] == 1.0 / 16)
+
+
 def test_ac_every_particle_a_neighbour_is_plain_hermite(gpu_lib):
     """r_s covering the system, fixed: the device AC run is the plain block-step Hermite run
     (the reference's reduction, pinned against the Kepler orbit), to rounding."""

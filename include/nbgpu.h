@@ -459,8 +459,13 @@ nb_status nb_ac_init(nb_ac **out, nb_ctx *ctx, int64_t n, const double *m, const
 nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_regular);
 
 /* Block steps until the next one would pass t_end, or max_blocks steps (0: no limit;
- * NB_ERR_STATE when reached).  stats (6 doubles, optional): block steps, irregular particle
- * steps, regular particle steps, neighbour-list pair terms, all-j pair terms, 0. */
+ * NB_ERR_STATE when reached).  Runs of block steps without a regular subset are driven from
+ * the device: one kernel per step (irregular force, corrector, re-sort of the time-step list
+ * and the next step's selection), enqueued in batches with one host synchronisation per
+ * batch; a step with a regular subset, or with more than 4096 active particles, is taken by
+ * the host path of nb_ac_step.  Both give the same bits.  stats (6 doubles, optional): block
+ * steps, irregular particle steps, regular particle steps, neighbour-list pair terms, all-j
+ * pair terms, block steps driven from the device. */
 nb_status nb_ac_run(nb_ac *s, double t_end, int64_t max_blocks, double *stats);
 
 /* Copy out (each may be NULL; n entries, x and v (n,3), lists n x nb_cap): positions and

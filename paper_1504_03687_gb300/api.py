@@ -640,7 +640,7 @@ class ACIntegrator:
         self._check(self.lib.nb_ac_run(self.h, float(t_end), int(max_blocks), st.ctypes.data), "nb_ac_run",
                     allow=(NB_ERR_STATE,) if max_blocks else ())
         return dict(blocks=int(st[0]), irregular_steps=int(st[1]), regular_steps=int(st[2]),
-                    neighbour_pairs=st[3], all_pairs=st[4])
+                    neighbour_pairs=st[3], all_pairs=st[4], device_blocks=int(st[5]))
 
     def get(self) -> dict:
         n, cap = self.n, self.cap

@@ -29,6 +29,7 @@
 #include "nb_common.cuh"
 #include "nb_irregular.cuh"
 #include "nb_kernels.cuh"
+#include "nb_sched.cuh"
 
 namespace nbgpu {
 
@@ -45,7 +46,7 @@ struct AcDev {
     int32_t *LR, *LI;
     int32_t *ell, *ell_cnt;
     int32_t *lr_hist;  // [64] particles per regular level (kept current by the corrector)
-    unsigned *tickets; // [2] CTAs done in the classify and corrector launches (last-CTA epilogues)
+    unsigned *tickets; // [2] CTAs done in the fused block-step and corrector launches (last-CTA epilogues)
     int32_t *io;       // device address of the pinned host words the corrector publishes:
                        // [0, 64) the regular-level histogram, [64] the step's status flags
     int32_t cap, lmin, lmax;
@@ -69,7 +70,7 @@ __device__ double ac_crit(double eta, const double *a, const double *j, const do
 // crit >= 2 h, 2 h <= dt_max and the time t (ticks of 2^-48) is a multiple of 2 h.
 __device__ int ac_level_rule(int L, double crit, int64_t t_ticks, int lmin, int lmax)
 {
-    const double h = ldexp(1.0, -L);
+    const double h = pow2i(-L);
     if (crit < h) {
         int Ln = L;
         double hn = h;
@@ -80,6 +81,44 @@ __device__ int ac_level_rule(int L, double crit, int64_t t_ticks, int lmin, int 
         return Ln;
     }
     if (crit >= 2.0 * h && L - 1 >= lmin && (t_ticks & (((int64_t)1 << (kAcTick - (L - 1))) - 1)) == 0)
+        return L - 1;
+    return L;
+}
+
+// The step rule's level for the criterion of ac_crit, decided on an FP32 estimate where that
+// is provably the FP64 decision; -1 where it is not (the caller then evaluates ac_crit).  A, J,
+// A2, A3 are FP32 sums of squares of the FP32-rounded components of a, jerk, a2 and a3, so
+//   crit^2 = eta (sqrt(A A2) + J) / (sqrt(J A3) + A2)
+// is the square of ac_crit's value, computed to a relative error below 18 * 2^-24 < 2^-19 (as
+// long as every quantity is a normal FP32 number; ac_crit's own rounding is far smaller).  The
+// rule compares crit only with powers of two, so where the estimate of crit^2 is at least
+// 2^-14 (relative) from every power of two, the FP64 criterion lies on the same side of each
+// of them and the rule on the estimate gives the same level.  Only a row whose crit^2 falls
+// within that margin of a power of two (about one in 8000) takes the FP64 criterion.
+__device__ __forceinline__ int ac_level_rule_est(int L, float A, float J, float A2, float A3, float eta,
+                                                 int64_t t_ticks, int lmin, int lmax)
+{
+    const float AA2 = __fmul_rn(A, A2), JA3 = __fmul_rn(J, A3);
+    const float num = __fadd_rn(__fsqrt_rn(AA2), J), den = __fadd_rn(__fsqrt_rn(JA3), A2);
+    const float c2 = __fdiv_rn(__fmul_rn(eta, num), den);
+    auto normal = [](float x) { return x >= 1.17549435e-38f && x <= 3.40282347e38f; };  // false for NaN
+    if (!(normal(A) && normal(J) && normal(A2) && normal(A3) && normal(AA2) && normal(JA3) && normal(num) &&
+          normal(den) && normal(c2)))
+        return -1;
+    const unsigned m = __float_as_uint(c2) & 0x7FFFFFu;
+    if (m < (1u << 9) || m > 0x7FFFFFu - (1u << 9)) return -1;  // within 2^-14 of a power of two
+    const float crit = __fsqrt_rn(c2);
+    const float h = __uint_as_float((unsigned)(127 - L) << 23);  // 2^-L, exactly
+    if (crit < h) {
+        int Ln = L;
+        float hn = h;
+        while (hn > crit && Ln < lmax) {
+            hn *= 0.5f;
+            ++Ln;
+        }
+        return Ln;
+    }
+    if (crit >= 2.0f * h && L - 1 >= lmin && (t_ticks & (((int64_t)1 << (kAcTick - (L - 1))) - 1)) == 0)
         return L - 1;
     return L;
 }
@@ -271,7 +310,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
             }
         } else {
             double Fold[3], Jold[3], a2r[3], a3r[3], fn[3], jn[3];
-            const double H = t - Tr;
+            const double H = t - Tr, iH = 1.0 / H;  // H is the regular step, a power of two
             const int32_t ct = cnt_true[p];
             const double rs2 = D.rs2[i];
 #pragma unroll
@@ -286,8 +325,9 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
                 Fold[c] = a1[c] - fo[c];
                 Jold[c] = j1[c] - jo[c];
                 const double df = Fr[c] - Fold[c];
-                const double a2 = (-6.0 * df - H * (4.0 * Jr[c] + 2.0 * Jold[c])) / (H * H);
-                const double a3 = (12.0 * df + 6.0 * H * (Jr[c] + Jold[c])) / (H * H * H);
+                // the definition's divisions by H^2 and H^3, as exact scalings
+                const double a2 = (-6.0 * df - H * (4.0 * Jr[c] + 2.0 * Jold[c])) * (iH * iH);
+                const double a3 = (12.0 * df + 6.0 * H * (Jr[c] + Jold[c])) * (iH * iH * iH);
                 a2r[c] = a2 + H * a3;
                 a3r[c] = a3;
             }
@@ -310,13 +350,13 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
         }
         // Hermite corrector on the total force; the predicted state is recomputed here with
         // the predictor's own function (bit-identical to the all-particle predictor)
-        const double h = t - tl;
+        const double h = t - tl, ih = 1.0 / h;  // h is the irregular step, a power of two
         double a2[3], a3[3], a2e[3], x1[3], v1[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double xp, vp;
             hermite_taylor(x0[c], v0[c], a0[c], j0[c], h, xp, vp);
-            hermite_correct(xp, vp, a0[c], j0[c], a1[c], j1[c], h, x1[c], v1[c], a2[c], a3[c]);
+            hermite_correct_pow2(xp, vp, a0[c], j0[c], a1[c], j1[c], h, ih, x1[c], v1[c], a2[c], a3[c]);
             a2e[c] = a2[c] + h * a3[c];
         }
 #pragma unroll
@@ -366,28 +406,47 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
     }
 }
 
-// A device-driven block step without a regular subset, fused: for every row of the step's
-// prefix one warp computes the irregular force (the irregular force kernels' own per-row code:
-// the lanes stride over the row's list, neighbours predicted on load from the state records,
-// the same fixed-order warp reduction) and then the corrector of k_ac_correct's irregular
-// branch, lane c taking component c and every lane the shared step rule (the FP64 pipe runs a
-// warp instruction in the same time with one lane active or 32, so the per-row chain is the
-// one component's, not three).  The corrected state records go to rec_new[k] (list position),
-// not to the records the other rows are reading: the scheduler's re-sort, the next kernel,
-// copies them in.  Rows are spread over the CTAs first (row k: CTA k mod G), so a short
-// prefix has one busy warp per SM sub-partition.  The arithmetic is k_irregular_* followed by
-// k_ac_correct, operation for operation, so the state after the step is the same bits.
-constexpr int kStepWarps = 4;
-constexpr int64_t kDevicePrefix = 16384;  // the longest prefix a device-driven step takes
+// A device-driven block step without a regular subset, in one kernel.  For every row of the
+// step's prefix one warp computes the irregular force (the irregular force kernels' own
+// per-row code: the lanes stride over the row's list, neighbours predicted on load from the
+// state records, the same fixed-order warp reduction) and then the corrector of k_ac_correct's
+// irregular branch, lane c < 3 taking component c (GB300's FP64 pipe takes about as long for a
+// warp instruction with three lanes active as with 32, so three component chains in one
+// instruction stream cost one).  The step rule is decided on an FP32 estimate of the criterion
+// where that provably gives the FP64 decision (ac_level_rule_est), else on ac_crit.  The
+// corrected state records go to rec_new[k] (list position), not to the records other rows are
+// reading.  Rows go four to a CTA, one to each SM sub-partition, so a short prefix occupies
+// few CTAs (few tickets) and no sub-partition runs two rows.  The last CTA to finish (a ticket, no
+// waiting) then re-sorts the prefix by the new levels with sort_prefix_cta, copying the new
+// records in on the way, and begins the next step.  The arithmetic is k_irregular_* followed
+// by k_ac_correct, operation for operation, and the re-sort is the scheduler's, so the state
+// after the step is the same bits as the host path's.
+constexpr int kStepWarps = 8;
+constexpr int kStepThreads = kStepWarps * 32;
+constexpr int kStepSortItems = 16;
+constexpr int64_t kDevicePrefix = (int64_t)kStepThreads * kStepSortItems;  // the longest prefix (4096)
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, int64_t n, const int32_t *list,
-                                                                     uint4 *rec_new, int32_t *want,
-                                                                     unsigned long long *pairs, unsigned *status,
-                                                                     const StepParams *dyn)
+__global__ void __launch_bounds__(kStepThreads) k_ac_irregular_step(AcDev D, int64_t n, uint4 *rec_new,
+                                                                    unsigned long long *pairs, unsigned *status,
+                                                                    SortArgs SA)
 {
+    __shared__ int32_t s_cnt[kBins];
+    __shared__ int32_t s_base[kBins];
+    __shared__ int32_t s_warp[kStepWarps][kBins];
+    __shared__ bool s_last;
     pdl_trigger();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // rows in rounds of 8 G: the first 4 G go four to a CTA, one to each of its warps 0-3 (one
+    // per SM sub-partition), the next 4 G likewise to warps 4-7
+    const int64_t k_first = 4 * (int64_t)blockIdx.x + (w & 3) + (int64_t)(w >> 2) * 4 * gridDim.x;
+    const int64_t k_step = (int64_t)gridDim.x * kStepWarps;
+    const StepParams *dyn = SA.dyn;
+    const int32_t *list = SA.list;
+    int32_t *want = const_cast<int32_t *>(SA.want);
     pdl_wait();
+    // the first row's particle is requested with the step's parameters (the list holds n entries)
+    const int32_t i_first = k_first < n ? list[k_first] : 0;
     if (dyn->halt) return;
     IrrArgs A{};
     A.srec = MIXED ? (const void *)D.s32 : (const void *)D.s64;
@@ -403,12 +462,18 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, 
     A.ell_stride = D.cap;
     const int64_t t_ticks = dyn->t_ticks;
     const double t = A.t;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // CTAs past the rows have nothing to do and take no part in the ticket
+    const int64_t used = A.n_i <= 0 ? 1 : ((A.n_i + 3) / 4 < gridDim.x ? (A.n_i + 3) / 4 : gridDim.x);
+    if (blockIdx.x >= used) return;
     const int c = lane < 3 ? lane : 0;  // the component lanes 0-2 correct (the others shadow 0)
+    const float eta_f = (float)D.eta_irr;
     unsigned my_pairs = 0;
-    for (int64_t k = blockIdx.x + (int64_t)gridDim.x * w; k < A.n_i; k += (int64_t)gridDim.x * kStepWarps) {
-        int64_t i, e0, e1;
-        const bool ok = irr_row(A, k, lane, i, e0, e1);
+    for (int64_t k = k_first; k < A.n_i; k += k_step) {
+        // row k's particle and list range (irr_row's checks)
+        const int64_t i = k == k_first ? i_first : list[k];
+        const bool ok = i >= 0 && i < n;
+        const int64_t e0 = ok ? i * A.ell_stride : 0, e1 = ok ? e0 + D.ell_cnt[i] : 0;
+        if (!ok && lane == 0) atomicOr(status, ST_BAD_INDEX);
         // the corrector's inputs do not depend on the force: requested before the list pass
         const int64_t ii = ok ? i : 0, q = 3 * ii + c;
         const int LR0 = D.LR[ii], LI0 = D.LI[ii];
@@ -416,11 +481,38 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, 
         const double x0 = D.x[q], v0 = D.v[q], a0 = D.a[q], j0 = D.jk[q];
         const double Fr = D.Fr[q], Jr = D.Jr[q], D2 = D.D2[q], D3 = D.D3[q];
         double fo, jo;  // the irregular force and jerk, component c
+        // the corrector's steps that do not need the force, in lanes 0-2 (FP64), are placed
+        // where the force pass waits for its first gathers: the extrapolated regular force and
+        // jerk at t and the predicted position and velocity
+        double Fx = 0.0, Jx = 0.0, xp = 0.0, vp = 0.0;
+        const double h = t - tl;  // the irregular step, a power of two
+        auto prework = [&]() {
+            if (lane < 3) {
+                const double tau = t - Tr;
+                Fx = Fr + Jr * tau + D2 * tau * tau / 2.0 + D3 * tau * tau * tau / 6.0;
+                Jx = Jr + D2 * tau + D3 * tau * tau / 2.0;
+                hermite_taylor(x0, v0, a0, j0, h, xp, vp);
+            }
+        };
         if constexpr (MIXED) {
             const float4 *S = static_cast<const float4 *>(A.srec);
             float ih[3] = {0, 0, 0}, il[3] = {0, 0, 0}, iv[3] = {0, 0, 0}, iD[3] = {0, 0, 0}, iE[3] = {0, 0, 0};
+            float4 Pi[5];
+            if (ok)
+#pragma unroll
+                for (int u = 0; u < 5; ++u) Pi[u] = S[5 * i + u];
+            // the lane's first list entry and its record are requested before the FP64 work,
+            // and each round's successor while the round is summed (the per-lane order of the
+            // terms is the irregular force kernel's)
+            int64_t e = e0 + lane;
+            int32_t jn = irr_neighbour(A, e, e1);
+            float4 Rn[5];
+            if (jn >= 0)
+#pragma unroll
+                for (int u = 0; u < 5; ++u) Rn[u] = S[5 * (int64_t)jn + u];
+            prework();
             if (ok) {
-                const float4 P = S[5 * i], L = S[5 * i + 1], V = S[5 * i + 2], Ac = S[5 * i + 3], J = S[5 * i + 4];
+                const float4 P = Pi[0], L = Pi[1], V = Pi[2], Ac = Pi[3], J = Pi[4];
                 const float dt = __fadd_rn(__fsub_rn(A.t_hi, L.w), __fsub_rn(A.t_lo, V.w));
                 ih[0] = P.x; ih[1] = P.y; ih[2] = P.z;
                 il[0] = L.x; il[1] = L.y; il[2] = L.z;
@@ -430,13 +522,17 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, 
                 incr_f32(V.z, Ac.z, J.z, dt, iD[2], iE[2]);
             }
             float f[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (int64_t e = e0 + lane; e < e1; e += 32) {
-                const int32_t j = irr_neighbour(A, e, e1);
-                if (j < 0 || j == i) continue;
+            while (e < e1) {
+                const int32_t j = jn;
                 float4 R[5];
 #pragma unroll
-                for (int u = 0; u < 5; ++u) R[u] = S[5 * (int64_t)j + u];
-                state_pair_mixed(R, A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
+                for (int u = 0; u < 5; ++u) R[u] = Rn[u];
+                e += 32;
+                jn = irr_neighbour(A, e, e1);
+                if (jn >= 0)
+#pragma unroll
+                    for (int u = 0; u < 5; ++u) Rn[u] = S[5 * (int64_t)jn + u];
+                if (j >= 0 && j != i) state_pair_mixed(R, A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
             }
             float h, l;
             warp_sum7_df(f, lane, h, l);
@@ -445,6 +541,7 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, 
             jo = __shfl_sync(0xffffffffu, v, 4 * (c + 3));
         } else {
             const dvec4 *S = static_cast<const dvec4 *>(A.srec);
+            prework();
             double own = 0.0;
             if (ok && lane < 6) {
                 const int cc = lane < 3 ? lane : lane - 3;
@@ -488,27 +585,38 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, 
             if (!ok) fo = jo = 0.0;
         }
         if (!ok) continue;  // (warp-uniform) the status bit is set; the row is left as it was
-        // k_ac_correct's irregular branch, component c: the extrapolated regular force ...
-        const double tau = t - Tr;
-        const double Fx = Fr + Jr * tau + D2 * tau * tau / 2.0 + D3 * tau * tau * tau / 6.0;
-        const double Jx = Jr + D2 * tau + D3 * tau * tau / 2.0;
-        const double a1 = fo + Fx, j1 = jo + Jx;
-        // ... and the Hermite corrector on the total force
-        const double h = t - tl;
-        double xp, vp, x1, v1, a2, a3;
-        hermite_taylor(x0, v0, a0, j0, h, xp, vp);
-        hermite_correct(xp, vp, a0, j0, a1, j1, h, x1, v1, a2, a3);
-        const double a2e = a2 + h * a3;
-        double A1[3], J1[3], A2E[3], A3[3];
+        // k_ac_correct's irregular branch, lane c < 3 component c: the extrapolated regular
+        // force, then the Hermite corrector on the total force
+        double x1 = 0.0, v1 = 0.0, a1 = 0.0, j1 = 0.0, a2e = 0.0, a3 = 0.0;
+        float sq[4] = {0.f, 0.f, 0.f, 0.f};  // FP32 squares of a1, j1, a2e, a3 for the estimate
+        if (lane < 3) {
+            a1 = fo + Fx;
+            j1 = jo + Jx;
+            double a2;
+            hermite_correct_pow2(xp, vp, a0, j0, a1, j1, h, recip_pow2(h), x1, v1, a2, a3);
+            a2e = a2 + h * a3;
+            const float q4[4] = {__double2float_rn(a1), __double2float_rn(j1), __double2float_rn(a2e),
+                                 __double2float_rn(a3)};
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            A1[u] = __shfl_sync(0xffffffffu, a1, u);
-            J1[u] = __shfl_sync(0xffffffffu, j1, u);
-            A2E[u] = __shfl_sync(0xffffffffu, a2e, u);
-            A3[u] = __shfl_sync(0xffffffffu, a3, u);
+            for (int u = 0; u < 4; ++u) sq[u] = __fmul_rn(q4[u], q4[u]);
         }
-        const double crit = ac_crit(D.eta_irr, A1, J1, A2E, A3);
-        int L = ac_level_rule(LI0, crit, t_ticks, D.lmin, D.lmax);
+        float tot[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            tot[u] = __fadd_rn(__fadd_rn(sq[u], __shfl_sync(0xffffffffu, sq[u], 1)), __shfl_sync(0xffffffffu, sq[u], 2));
+        int L = ac_level_rule_est(LI0, tot[0], tot[1], tot[2], tot[3], eta_f, t_ticks, D.lmin, D.lmax);
+        L = __shfl_sync(0xffffffffu, L, 0);
+        if (L < 0) {  // within the estimate's margin of a power of two: the FP64 criterion
+            double A1[3], J1[3], A2E[3], A3[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                A1[u] = __shfl_sync(0xffffffffu, a1, u);
+                J1[u] = __shfl_sync(0xffffffffu, j1, u);
+                A2E[u] = __shfl_sync(0xffffffffu, a2e, u);
+                A3[u] = __shfl_sync(0xffffffffu, a3, u);
+            }
+            L = ac_level_rule(LI0, ac_crit(D.eta_irr, A1, J1, A2E, A3), t_ticks, D.lmin, D.lmax);
+        }
         if (L < LR0) L = LR0;  // irregular step at most the regular step
         if (lane < 3) {
             D.x[q] = x1;
@@ -557,6 +665,18 @@ __global__ void __launch_bounds__(kStepWarps * 32) k_ac_irregular_step(AcDev D, 
         }
     }
     if (lane == 0 && my_pairs) atomicAdd(pairs, (unsigned long long)my_pairs);
+    // the last CTA to finish re-sorts the prefix (every other CTA's writes are visible to it:
+    // each fenced them before taking its ticket) and begins the next step
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&D.tickets[0], 1u) == (unsigned)used - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) D.tickets[0] = 0u;  // the next step's kernel starts after this one ends
+    SA.n_act = A.n_i;
+    SA.lstar = dyn->lstar;
+    sort_prefix_cta<kStepThreads, kStepSortItems, true>(SA, s_cnt, s_base, s_warp);
 }
 
 // The regular subset's new lists (CSR) replace the old per-particle lists; one warp per row.
@@ -596,55 +716,14 @@ __global__ void k_ac_get_steps(const AcDev D, int64_t n, double *dt, double *DT,
 // the regular-level histogram says some particle takes a regular step there (the host path
 // runs those), when the prefix is longer than one device re-sort takes, or when the batch's
 // budget dstep[0] is spent; otherwise it counts the step (dstep[1]) and its rows (dstep[2]).
-__global__ void __launch_bounds__(32) k_ac_begin(StepParams *P, SchedDevice S, const int32_t *lr_hist, double t_end,
-                                                  int64_t *dstep)
+__global__ void __launch_bounds__(32) k_ac_begin(StepBegin B, SchedDevice S)
 {
     // one warp: lane l holds the levels l and l + 32
     pdl_trigger();
     pdl_wait();
-    if (P->halt) return;
-    const int lane = threadIdx.x;
-    const int64_t c_lo = S.count[lane], c_hi = S.count[lane + 32];
-    const int32_t r_lo = lr_hist[lane], r_hi = lr_hist[lane + 32];
-    if (dstep[0] <= 0) {
-        if (lane == 0) P->halt = STEP_BUDGET;
-        return;
-    }
-    const unsigned m_hi = __ballot_sync(0xffffffffu, c_hi != 0), m_lo = __ballot_sync(0xffffffffu, c_lo != 0);
-    const int lmax = m_hi ? 63 - __clz(m_hi) : (m_lo ? 31 - __clz(m_lo) : -1);
-    if (lmax < 0) {
-        if (lane == 0) P->halt = STEP_END;
-        return;
-    }
-    const int64_t T_new = *S.T + ((int64_t)1 << (kAcTick - lmax));
-    const double t = ldexp((double)T_new, -kAcTick);
-    if (t > t_end) {
-        if (lane == 0) P->halt = STEP_END;
-        return;
-    }
-    int lstar = kAcTick - (__ffsll(T_new) - 1);
-    if (lstar < 0) lstar = 0;
-    int64_t na = (lane >= lstar ? c_lo : 0) + (lane + 32 >= lstar ? c_hi : 0);
-    int64_t nr = (lane >= lstar ? r_lo : 0) + (lane + 32 >= lstar ? r_hi : 0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        na += __shfl_xor_sync(0xffffffffu, na, o);
-        nr += __shfl_xor_sync(0xffffffffu, nr, o);
-    }
-    if (lane != 0) return;
-    if (nr > 0 || na > S.max_prefix) {
-        P->halt = nr > 0 ? STEP_REGULAR : STEP_LONG;
-        return;
-    }
-    P->t = t;
-    P->t_ticks = T_new;
-    P->n_act = na;
-    P->lstar = lstar;
-    P->t_hi = (float)t;
-    P->t_lo = (float)(t - (double)P->t_hi);
-    dstep[0] -= 1;
-    dstep[1] += 1;
-    dstep[2] += na;
+    if (B.P->halt) return;
+    step_begin(B, S.count[threadIdx.x], S.count[threadIdx.x + 32], *S.T, threadIdx.x,
+               step_begin_inputs(B, threadIdx.x));
 }
 
 // The host words after a batch of device-driven steps: the regular-level histogram and the
@@ -994,21 +1073,18 @@ static nb_status ac_device_steps(nb_ac *s, double t_end, int64_t K, int64_t *don
     int32_t halt = 0;
     ACK(cudaMemsetAsync(&s->P->halt, 0, sizeof(int32_t), st), "clear halt");
     ACK(cudaMemcpyAsync(s->dstep, h, sizeof(h), cudaMemcpyHostToDevice, st), "step budget");
-    // per step: begin, the fused irregular force and corrector, the re-sort (which copies the
-    // corrected records in); each a programmatic dependent of the one before, except the first
+    // the first step's begin, then one kernel per step: the fused irregular force, corrector
+    // and re-sort, which ends with the next step's begin; each a programmatic dependent of the
+    // kernel before it
     const int rb = (int)state_record_bytes(cs.precision, 1);
     auto step_kernel = cs.precision == 0 ? k_ac_irregular_step<false> : k_ac_irregular_step<true>;
-    const dim3 sgrid(2 * cs.num_sms), sblock(kStepWarps * 32);
-    for (int64_t k = 0; k < K; ++k) {
-        ACK(launch_pdl(k > 0, k_ac_begin, dim3(1), dim3(32), st, s->P, S, (const int32_t *)s->D.lr_hist, t_end,
-                       s->dstep),
-            "begin launch");
-        ACK(launch_pdl(true, step_kernel, sgrid, sblock, st, s->D, cs.n, (const int32_t *)S.list, s->rec_new,
-                       s->want, s->pairs, cs.status + SS_FLAGS, (const StepParams *)s->P),
+    StepBegin B{s->P, s->D.lr_hist, t_end, s->dstep, S.max_prefix};
+    const SortArgs SA = sched_device_sort_args(s->sched, s->want, s->P, s->rec_new, s->srec, rb, &B);
+    k_ac_begin<<<1, 32, 0, st>>>(B, S);
+    for (int64_t k = 0; k < K; ++k)
+        ACK(launch_pdl(true, step_kernel, dim3(cs.num_sms), dim3(kStepThreads), st, s->D, cs.n, s->rec_new, s->pairs,
+                       cs.status + SS_FLAGS, SA),
             "block-step launch");
-        if (!sched_device_sort(s->sched, s->want, s->P, s->rec_new, s->srec, rb, true))
-            return afail(s, NB_ERR_CUDA, "device re-sort launch");
-    }
     k_ac_publish<<<1, 64, 0, st>>>(s->D, cs.status + SS_FLAGS);
     ACK(cudaGetLastError(), "device step launches");
     ACK(cudaMemcpyAsync(h, s->dstep, sizeof(h), cudaMemcpyDeviceToHost, st), "step counters");
@@ -1023,6 +1099,7 @@ static nb_status ac_device_steps(nb_ac *s, double t_end, int64_t K, int64_t *don
     *done = h[1];
     s->stats[0] += (double)h[1];
     s->stats[1] += (double)h[2];
+    s->stats[5] += (double)h[1];
     return NB_OK;
 }
 

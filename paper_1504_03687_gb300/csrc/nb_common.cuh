@@ -136,6 +136,36 @@ __device__ __forceinline__ void hermite_correct(double xp, double vp, double a0,
     v1 = vp + h * h * h / 6.0 * a2 + h * h * h * h / 24.0 * a3;
 }
 
+// The same corrector for a step h that is a power of two (every block step of the integrator),
+// given ih = 1/h (exact): the divisions by h^2 and h^3 become products with ih^2 and ih^3, and
+// h^4/24, h^5/120, h^3/6 products with the rounded constants.  Scaling by a power of two
+// commutes with rounding, so every result is bit-identical to hermite_correct's, with no FP64
+// division (a few dozen instructions on GB300's narrow FP64 pipe).
+__device__ __forceinline__ void hermite_correct_pow2(double xp, double vp, double a0, double j0, double a1, double j1,
+                                                     double h, double ih, double &x1, double &v1, double &a2,
+                                                     double &a3)
+{
+    const double da = a0 - a1;
+    a2 = (-6.0 * da - h * (4.0 * j0 + 2.0 * j1)) * (ih * ih);
+    a3 = (12.0 * da + 6.0 * h * (j0 + j1)) * (ih * ih * ih);
+    x1 = xp + h * h * h * h * (1.0 / 24.0) * a2 + h * h * h * h * h * (1.0 / 120.0) * a3;
+    v1 = vp + h * h * h * (1.0 / 6.0) * a2 + h * h * h * h * (1.0 / 24.0) * a3;
+}
+
+// 2^e, exactly, for e in [-1022, 1023].
+__device__ __forceinline__ double pow2i(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// 1/h: for h a positive normal power of two (with a normal reciprocal) the exact reciprocal
+// from the exponent bits, which is what the division gives; the division otherwise.
+__device__ __forceinline__ double recip_pow2(double h)
+{
+    const long long b = __double_as_longlong(h);
+    const long long ex = b >> 52;  // sign 0 and biased exponent
+    if ((b & 0x000FFFFFFFFFFFFFLL) == 0 && ex >= 1 && ex <= 2045)
+        return __longlong_as_double(0x7FE0000000000000LL - b);
+    return 1.0 / h;
+}
+
 // ---- state records of the predict-on-load irregular force ---------------------------------
 //   FP64 : 4 dvec4  {x, y, z, t_last} {vx, vy, vz, m} {ax, ay, az, 0} {jx, jy, jz, 0}
 //   mixed: 5 float4 {xh, yh, zh, m} {xl, yl, zl, t_hi} {vx, vy, vz, t_lo} {ax, ay, az, 0}

@@ -28,104 +28,9 @@
 #include "nbgpu.h"
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
+#include "nb_sched.cuh"
 
 namespace nbgpu {
-
-constexpr int kTick = 48;        // time unit 2^-48
-constexpr int kBins = 64;        // level bins
-constexpr int kSortThreads = 1024;
-constexpr int kSortItems = 16;   // rounds of 32 entries per warp
-constexpr int kChunk = kSortThreads * kSortItems;  // entries per CTA (16384)
-constexpr int kSortWarps = kSortThreads / 32;
-
-struct SortArgs {
-    int32_t *list;          // the list; the prefix [0, n_act) is re-sorted
-    int32_t *level;         // (n) level of every particle
-    const int32_t *want;    // (n_act) requested levels in list order, or null (initial sort)
-    int32_t *granted;       // (n_act) optional: the granted levels in list order
-    int64_t n_act;
-    int32_t lstar, lmin, lmax;
-    int32_t *keep_part;     // multi-CTA: particle of every entry
-    int32_t *keep_rank;     // multi-CTA: rank of every entry within its CTA and level
-    int8_t *keep_lev;       // multi-CTA: new level of every entry
-    int32_t *cta_count;     // [ctas][kBins]
-    int64_t *totals;        // [kBins] entries per new level (written by the scan)
-    int32_t *bad;           // set when a stored level is outside [0, kBins) (initial sort)
-    const StepParams *dyn;  // device-driven step: n_act and lstar from here (nothing when halted)
-    int64_t *dev_count;     // device-driven step: the device counts of levels >= lstar are set
-    int64_t *dev_T;         // ... and the device time advanced to the step's block time
-    const uint4 *rec_new;   // optional (single CTA): records of the prefix in list order, copied ...
-    uint4 *rec;             // ... to rec[particle] before the re-sort; rec_u4 16-byte words each
-    int32_t rec_u4;
-};
-
-// One CTA: read its chunk of the prefix, apply the block rule, and rank every entry within
-// (CTA, new level) in list order.  Entry e of the chunk is handled in round e / 1024 by
-// warp (e % 1024) / 32, lane e % 32; the rank counts earlier rounds of all warps, then earlier
-// warps of the same round, then earlier lanes.  Returns the CTA's per-level counts in s_cnt.
-__device__ void rank_chunk(const SortArgs &A, int64_t c0, int32_t (&part)[kSortItems], int32_t (&lev)[kSortItems],
-                           int32_t (&rank)[kSortItems], int32_t *s_cnt, int32_t (*s_warp)[kBins])
-{
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int b = tid; b < kBins; b += kSortThreads) s_cnt[b] = 0;
-    __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    // rounds past the end of the prefix hold no entry (the same count for the whole CTA)
-    const int64_t left = A.n_act - c0;
-    const int rounds = left >= kChunk ? kSortItems : (int)((left + kSortThreads - 1) / kSortThreads);
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        if (r >= rounds) {
-            part[r] = -1;
-            lev[r] = 0;
-            rank[r] = 0;
-            continue;
-        }
-        const int64_t e = c0 + (int64_t)r * kSortThreads + tid;
-        const bool in = e < A.n_act;
-        int32_t p = -1, L = 0;
-        if (in) {
-            p = A.list[e];
-            if (A.rec)
-                for (int u = 0; u < A.rec_u4; ++u) A.rec[(int64_t)p * A.rec_u4 + u] = A.rec_new[e * A.rec_u4 + u];
-            L = A.level[p];
-            if (L < 0 || L >= kBins) {  // only possible for levels handed to the initial sort
-                atomicOr(A.bad, 1);
-                L = L < 0 ? 0 : kBins - 1;
-            }
-            if (A.want) {
-                int32_t g = A.want[e];
-                g = g < A.lmin ? A.lmin : (g > A.lmax ? A.lmax : g);
-                if (g < L - 1) g = L - 1;
-                if (g == L - 1 && L <= A.lstar) g = L;
-                L = g;
-                if (A.granted) A.granted[e] = g;
-            }
-        }
-        const int key = in ? L : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        // per-warp count of this round per level, then offsets across the warps
-        for (int b = lane; b < kBins; b += 32) s_warp[w][b] = 0;
-        __syncwarp();
-        if (in && (peers & lt) == 0) s_warp[w][L] = __popc(peers);
-        __syncthreads();
-        // exclusive scan over warps, per level (one thread per level)
-        if (tid < kBins) {
-            int acc = s_cnt[tid];
-            for (int ww = 0; ww < kSortWarps; ++ww) {
-                const int c = s_warp[ww][tid];
-                s_warp[ww][tid] = acc;
-                acc += c;
-            }
-            s_cnt[tid] = acc;
-        }
-        __syncthreads();
-        part[r] = p;
-        lev[r] = L;
-        rank[r] = in ? s_warp[w][L] + __popc(peers & lt) : 0;
-        __syncthreads();  // s_warp is rewritten in the next round
-    }
-}
 
 // Prefix within one chunk: rank, scan the 64 counts, scatter in place, update the levels.
 __global__ void __launch_bounds__(kSortThreads) k_sort_single(SortArgs A)
@@ -133,34 +38,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_single(SortArgs A)
     __shared__ int32_t s_cnt[kBins];
     __shared__ int32_t s_base[kBins];
     __shared__ int32_t s_warp[kSortWarps][kBins];
-    pdl_trigger();
-    pdl_wait();
-    if (A.dyn) {  // a device-driven step: its prefix and coarsest level
-        if (A.dyn->halt) return;
-        A.n_act = A.dyn->n_act;
-        A.lstar = A.dyn->lstar;
-    }
-    int32_t part[kSortItems], lev[kSortItems], rank[kSortItems];
-    rank_chunk(A, 0, part, lev, rank, s_cnt, s_warp);
-    if (threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int b = kBins - 1; b >= 0; --b) {  // list order: level descending
-            s_base[b] = (int32_t)acc;
-            acc += s_cnt[b];
-        }
-    }
-    if (A.totals && threadIdx.x < kBins) A.totals[threadIdx.x] = s_cnt[threadIdx.x];
-    if (A.dyn) {  // the scheduler's device state moves on to the step's block time
-        if (threadIdx.x < kBins && threadIdx.x >= A.lstar) A.dev_count[threadIdx.x] = s_cnt[threadIdx.x];
-        if (threadIdx.x == 0) *A.dev_T = A.dyn->t_ticks;
-    }
-    __syncthreads();  // every entry is in registers: the in-place scatter is safe
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        if (part[r] < 0) continue;
-        A.list[s_base[lev[r]] + rank[r]] = part[r];
-        A.level[part[r]] = lev[r];
-    }
+    sort_prefix_cta<kSortThreads, kSortItems>(A, s_cnt, s_base, s_warp);
 }
 
 // Multi-CTA pass 1: rank each chunk, keep (particle, level, rank), write the CTA's counts.
@@ -170,7 +48,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_rank(SortArgs A)
     __shared__ int32_t s_warp[kSortWarps][kBins];
     int32_t part[kSortItems], lev[kSortItems], rank[kSortItems];
     const int64_t c0 = (int64_t)blockIdx.x * kChunk;
-    rank_chunk(A, c0, part, lev, rank, s_cnt, s_warp);
+    rank_chunk<kSortThreads, kSortItems>(A, c0, part, lev, rank, s_cnt, s_warp);
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t e = c0 + (int64_t)r * kSortThreads + threadIdx.x;
@@ -292,6 +170,7 @@ static nb_status sched_sort(nb_sched *s, int64_t n_act, const int32_t *d_want, i
     A.rec_new = nullptr;
     A.rec = nullptr;
     A.rec_u4 = 0;
+    A.next = StepBegin{};
     if (n_act <= kChunk) {
         k_sort_single<<<1, kSortThreads, 0, s->stream>>>(A);
     } else {
@@ -345,8 +224,8 @@ bool sched_pull(nb_sched *s)
            cudaStreamSynchronize(s->stream) == cudaSuccess;
 }
 
-bool sched_device_sort(nb_sched *s, const int32_t *want, const StepParams *P, const void *rec_new, void *rec,
-                       int rec_bytes, bool pdl)
+SortArgs sched_device_sort_args(nb_sched *s, const int32_t *want, const StepParams *P, const void *rec_new,
+                                void *rec, int rec_bytes, const StepBegin *next)
 {
     SortArgs A;
     A.list = s->list;
@@ -369,7 +248,8 @@ bool sched_device_sort(nb_sched *s, const int32_t *want, const StepParams *P, co
     A.rec_new = static_cast<const uint4 *>(rec_new);
     A.rec = static_cast<uint4 *>(rec);
     A.rec_u4 = rec_bytes / 16;
-    return launch_pdl(pdl, k_sort_single, dim3(1), dim3(kSortThreads), s->stream, A) == cudaSuccess;
+    A.next = next ? *next : StepBegin{};
+    return A;
 }
 
 }  // namespace nbgpu

@@ -796,7 +796,9 @@ def bench_ac(dev, n=65536, t_end=1.0 / 64, precisions=("mixed", "fp64"), referen
         e = (sum(oracle.energy(cl.m, g["x"], g["v"])) - E0) / abs(E0)
         res[prec] = {"wall_s": wall, "block_steps": st["blocks"], "irregular_steps": st["irregular_steps"],
                      "regular_steps": st["regular_steps"], "particle_steps_per_s": st["irregular_steps"] / wall,
-                     "ms_per_block_step": wall * 1e3 / max(st["blocks"], 1), "energy_rel_error": e,
+                     "ms_per_block_step": wall * 1e3 / max(st["blocks"], 1),
+                     "us_per_block_step": wall * 1e6 / max(st["blocks"], 1),
+                     "device_driven_block_steps": st["device_blocks"], "energy_rel_error": e,
                      "all_synchronised": bool(np.all(g["t"] == t_end)), "median_neighbours": float(np.median(g["nb_count"]))}
         ac.close()
         ctx.close()

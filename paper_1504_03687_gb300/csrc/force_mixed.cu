@@ -663,7 +663,9 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
                         int32_t *cp = srow + AR_CNT * NR * BLOCK + slot;
                         const int cnt = *cp;
                         if (cnt < A.L) {
-                            int32_t *seg = A.seg_slots + ((int64_t)s * A.n_i + srow[AR_K * NR * BLOCK + slot]) * A.L;
+                            // the row's segment at its position in the spatial order
+                            const int64_t r = (int64_t)blockIdx.x * (NR * BLOCK) + slot;
+                            int32_t *seg = A.seg_slots + ((int64_t)s * A.n_i + r) * A.L;
                             if (HITS > 0) {
                                 int32_t *sbuf = srow + AR_WORDS * NR * BLOCK + slot;
                                 sbuf[(cnt & (HITS - 1)) * NR * BLOCK] = j32;
@@ -836,18 +838,27 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
         const int slot = q * BLOCK + tid;
         const int64_t k = srow[AR_K * NI * BLOCK + slot];
         if (k >= 0) {
+            // the sums at the row's position in the spatial order (consecutive threads,
+            // consecutive positions: whole sectors); the reduction puts them back in row order
+            const int64_t r = kbase + slot;
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
                 const double v = dacc[(c * NI + q) * BLOCK + tid];
-                __stcs(A.part + ((int64_t)s * 7 + c) * A.n_i + k, (c == 6) ? -v : v);
+                __stcs(A.part + ((int64_t)s * 7 + c) * A.n_i + r, (c == 6) ? -v : v);
             }
-            if (A.want_nb) {
+            if (A.want_nb) {  // the count and the last group, at the position too
                 const int cnt = srow[AR_CNT * NI * BLOCK + slot];
-                A.seg_cnt[(int64_t)s * A.n_i + k] = cnt;
+                A.seg_cnt[(int64_t)s * A.n_i + r] = cnt;
                 const int c = cnt < A.L ? cnt : A.L;  // staged hits not yet written (a last, partial group)
-                if (HITS > 0 && c < A.L && (c & (HITS - 1)) != 0)
-                    flush_staged<HITS>(A.seg_slots + ((int64_t)s * A.n_i + k) * A.L,
-                                       srow + AR_WORDS * NI * BLOCK + slot, NI * BLOCK, c & ~(HITS - 1), c - 1, false);
+                if (HITS > 0 && c < A.L && (c & (HITS - 1)) != 0) {
+                    // with L a multiple of HITS the whole group is written (the slots past the
+                    // count hold stale values that nothing reads), so every list store is a
+                    // whole aligned chunk
+                    const bool whole = (A.L & (HITS - 1)) == 0;
+                    flush_staged<HITS>(A.seg_slots + ((int64_t)s * A.n_i + r) * A.L,
+                                       srow + AR_WORDS * NI * BLOCK + slot, NI * BLOCK, c & ~(HITS - 1),
+                                       whole ? (c | (HITS - 1)) : c - 1, whole);
+                }
             }
         }
     }
@@ -865,6 +876,15 @@ template <int NI, int BLOCK, int TJ, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_staged_x2(ForceArgs A)
 {
     anchored_body<NI, BLOCK, TJ, MINB, NI >= 4 ? 8 : 16>(A);
+}
+
+// The same with 16 hits (64 bytes) a group whatever the rows per thread.  HBM is written in
+// 64-byte units: a group of 8 hits is half a unit, which the memory system completes with a
+// read of the other half.
+template <int NI, int BLOCK, int TJ, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_staged16_x2(ForceArgs A)
+{
+    anchored_body<NI, BLOCK, TJ, MINB, 16>(A);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1072,12 +1092,13 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
 // ------------------------------------------------------------------------------------------
 // Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM, kind).  The plan's
 // `variant` indexes this list; ids 0-3 are the scalar kernel, 4-9 the packed-FP32x2 one
-// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-16 the
+// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-17 the
 // anchored packed kernel (rows in spatial order, anchor-relative separations; 13 and 14 with
-// row tiles of 128 and 64; 15 and 16 staging the neighbour hits).
+// row tiles of 128 and 64; 15-17 staging the neighbour hits).
 // Last column: 0 = scalar (static shared memory), 1 = packed (x2_smem_bytes), 2 = anchored
 // (anchored_smem_bytes; needs the row order A.perm), 3 = anchored with the neighbour hits staged
-// in shared memory and written as whole sectors (15, 16).
+// in shared memory and written as whole sectors (15, 16: 8 hits a group with four rows a
+// thread, 16 with two), 4 = the same with 16 hits a group (17).
 #define NB_MIXED_TILED_VARIANTS(X)                       \
     X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)         \
     X(1, k_force_mixed_tiled, 2, 128, 256, 4, 0)         \
@@ -1095,7 +1116,8 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
     X(13, k_force_mixed_anchored_x2, 2, 64, 64, 8, 2)    \
     X(14, k_force_mixed_anchored_x2, 2, 32, 64, 12, 2)   \
     X(15, k_force_mixed_staged_x2, 4, 128, 64, 3, 3)     \
-    X(16, k_force_mixed_staged_x2, 2, 128, 64, 4, 3)
+    X(16, k_force_mixed_staged_x2, 2, 128, 64, 4, 3)     \
+    X(17, k_force_mixed_staged16_x2, 4, 128, 64, 2, 4)
 
 struct TiledVariant {
     int ni, block, tj, smem, kind;
@@ -1103,7 +1125,7 @@ struct TiledVariant {
 #define NB_TV_ROW(id, K, NI, B, TJ, MB, KIND)                                                         \
     {NI, B, TJ,                                                                                      \
      KIND == 1 ? x2_smem_bytes<NI, B, TJ>()                                                          \
-               : (KIND >= 2 ? anchored_smem_bytes<NI, B, TJ, KIND == 3 ? (NI >= 4 ? 8 : 16) : 0>() : 0), \
+               : (KIND >= 2 ? anchored_smem_bytes<NI, B, TJ, KIND == 4 ? 16 : (KIND == 3 ? (NI >= 4 ? 8 : 16) : 0)>() : 0), \
      KIND},
 static const TiledVariant kTiled[] = {NB_MIXED_TILED_VARIANTS(NB_TV_ROW)};
 #undef NB_TV_ROW

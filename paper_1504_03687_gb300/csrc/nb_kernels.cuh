@@ -121,7 +121,8 @@ bool sched_pull(::nb_sched *s);                      // device -> host (synchron
 // Neighbour capture.  The j-range is cut into G ordered segments; for every (segment g,
 // active row k) exactly one thread (tiled kernels) or one warp (j-streamed kernels) walks
 // the segment in ascending j and appends hits to seg_slots[(g*n_i + k)*L ...] (at most L
-// kept, all counted in seg_cnt[g*n_i + k]).  The CSR row k is then the concatenation of
+// kept, all counted in seg_cnt[g*n_i + k]; the anchored kernels index both by the row's
+// position r in their spatial order instead).  The CSR row k is then the concatenation of
 // its segments in order, cut at nb_cap: ascending j, deterministic, no atomics, no sort.
 // L = min(nb_cap, longest segment) suffices because a segment that holds more than L
 // hits can only be reached when L = nb_cap.
@@ -139,7 +140,7 @@ struct ForceArgs {
     int32_t want_nb;        // 0: skip neighbour capture
     int32_t S;              // j-splits (blockIdx.y)
     int32_t L;              // neighbour slots per (segment, row); 0 = count only
-    double *part;           // partial sums [S][7][n_i]
+    double *part;           // partial sums [S][7][n_i] at row k (the anchored kernels: at row-order position r)
     int32_t *seg_cnt;       // [G][n_i]
     int32_t *seg_slots;     // [G][n_i][L]
     unsigned *status;
@@ -198,17 +199,21 @@ void roworder_configure();
 int launch_row_order(cudaStream_t st, const void *rec, const int32_t *idx, int64_t n, int64_t n_i, void *scratch,
                      const int32_t **perm_out);
 
+// The fixed-order sum of S partial-sum sets; position r of part holds row perm[r] (perm null:
+// row r), as the anchored force kernel writes them.
 void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc,
-                   double *jerk, double *pot);
+                   double *jerk, double *pot, const int32_t *perm = nullptr);
 
 // Neighbour CSR from the segment lists: counts -> offsets -> ordered gather.
 // Returns the number of kernels launched.
-// row_total: (n_i) int32 scratch used when there are many segments per row (may be NULL
-// when G is small).
+// row_total: (n_i) int32 scratch used when there are many segments per row or a perm (may be
+// NULL when G is small and perm is NULL).  perm: the segments of position r belong to row
+// perm[r] (the anchored force kernel's spatial order); NULL = row r.
 int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap,
                          const int32_t *seg_cnt, const int32_t *seg_slots, int64_t *off,
                          int32_t *nb_idx, int64_t nb_capacity, int32_t *count_true,
-                         int64_t *scan_tmp, int32_t *row_total, unsigned *status);
+                         int64_t *scan_tmp, int32_t *row_total, unsigned *status,
+                         const int32_t *perm = nullptr);
 
 size_t neighbour_scan_tmp_elems(int64_t n_i);
 

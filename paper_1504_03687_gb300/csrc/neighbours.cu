@@ -12,18 +12,22 @@
 namespace nbgpu {
 
 // ------------------------------------------------------------------------------ K4
-__global__ void k_reduce(const double *__restrict__ part, int S, int64_t n_i, double *__restrict__ acc,
-                         double *__restrict__ jerk, double *__restrict__ pot)
+// The partial sums of position r are those of row perm[r] (perm == null: row r).  The anchored
+// force kernel writes them at the position of its spatial row order, so that its stores are
+// whole sectors; the reduction reads them in that order and writes each row's sums in place.
+__global__ void k_reduce(const double *__restrict__ part, int S, int64_t n_i, const int32_t *__restrict__ perm,
+                         double *__restrict__ acc, double *__restrict__ jerk, double *__restrict__ pot)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_i;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_i;
+         r += (int64_t)gridDim.x * blockDim.x) {
         double v[7];
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
             double sum = 0.0;
-            for (int s = 0; s < S; ++s) sum += part[((int64_t)s * 7 + c) * n_i + k];
+            for (int s = 0; s < S; ++s) sum += part[((int64_t)s * 7 + c) * n_i + r];
             v[c] = sum;
         }
+        const int64_t k = perm ? perm[r] : r;
         acc[3 * k] = v[0];
         acc[3 * k + 1] = v[1];
         acc[3 * k + 2] = v[2];
@@ -34,20 +38,21 @@ __global__ void k_reduce(const double *__restrict__ part, int S, int64_t n_i, do
     }
 }
 
-// Many splits (small active blocks): one CTA per row, warp c sums component c; lane l adds
-// the splits s = l, l+32, ... in increasing order, then the warp adds the 32 lane sums with a
-// fixed butterfly, so the result is deterministic for a given split count.
+// Many splits: one CTA per position, warp c sums component c; lane l adds the splits s = l,
+// l+32, ... in increasing order, then the warp adds the 32 lane sums with a fixed butterfly,
+// so the result is deterministic for a given split count.
 __global__ void __launch_bounds__(256) k_reduce_wide(const double *__restrict__ part, int S, int64_t n_i,
-                                                     double *__restrict__ acc, double *__restrict__ jerk,
-                                                     double *__restrict__ pot)
+                                                     const int32_t *__restrict__ perm, double *__restrict__ acc,
+                                                     double *__restrict__ jerk, double *__restrict__ pot)
 {
-    const int64_t k = blockIdx.x;
+    const int64_t r = blockIdx.x;
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (c >= 7) return;  // warp-uniform
     double sum = 0.0;
-    for (int s = lane; s < S; s += 32) sum += part[((int64_t)s * 7 + c) * n_i + k];
+    for (int s = lane; s < S; s += 32) sum += part[((int64_t)s * 7 + c) * n_i + r];
     sum = warp_sum(sum);
     if (lane == 0) {
+        const int64_t k = perm ? perm[r] : r;
         if (c < 3)
             acc[3 * k + c] = sum;
         else if (c < 6)
@@ -58,16 +63,16 @@ __global__ void __launch_bounds__(256) k_reduce_wide(const double *__restrict__ 
 }
 
 void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc, double *jerk,
-                   double *pot)
+                   double *pot, const int32_t *perm)
 {
-    if (S > 16 && n_i <= 1024) {
-        k_reduce_wide<<<(unsigned)n_i, 256, 0, st>>>(part, S, n_i, acc, jerk, pot);
+    if (S > 16) {  // a warp per component and position: the split loop in parallel
+        k_reduce_wide<<<(unsigned)n_i, 256, 0, st>>>(part, S, n_i, perm, acc, jerk, pot);
         return;
     }
     int64_t g = (n_i + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
     if (g < 1) g = 1;
-    k_reduce<<<(unsigned)g, 256, 0, st>>>(part, S, n_i, acc, jerk, pot);
+    k_reduce<<<(unsigned)g, 256, 0, st>>>(part, S, n_i, perm, acc, jerk, pot);
 }
 
 // ------------------------------------------------------------------------------ scan
@@ -164,13 +169,14 @@ size_t neighbour_scan_tmp_elems(int64_t n_i) { return (size_t)((n_i + SCAN_BLOCK
 // each segment's place in the row, then the warp copies segment after segment (coalesced).
 __global__ void k_seg_gather(const int32_t *__restrict__ seg_cnt, const int32_t *__restrict__ seg_slots, int64_t G,
                              int64_t n_i, int L, const int64_t *__restrict__ off, int32_t *__restrict__ nb_idx,
-                             int64_t capacity)
+                             int64_t capacity, const int32_t *__restrict__ perm)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);  // segment position
     if (k >= n_i) return;  // warp-uniform
-    const int64_t o0 = off[k];
-    const int64_t kept = off[k + 1] - o0;
+    const int64_t row = perm ? perm[k] : k;
+    const int64_t o0 = off[row];
+    const int64_t kept = off[row + 1] - o0;
     int64_t done = 0;
     for (int64_t g0 = 0; g0 < G && done < kept; g0 += 32) {
         const int64_t g = g0 + lane;
@@ -203,10 +209,11 @@ constexpr int ROW_BLOCK = 256;
 
 // True neighbour count of every row: block-wide sum over the row's segments.
 __global__ void __launch_bounds__(ROW_BLOCK) k_seg_count_rows(const int32_t *__restrict__ seg_cnt, int64_t G,
-                                                              int64_t n_i, int32_t *__restrict__ total)
+                                                              int64_t n_i, int32_t *__restrict__ total,
+                                                              const int32_t *__restrict__ perm)
 {
     __shared__ int64_t ws[ROW_BLOCK / 32];
-    const int64_t k = blockIdx.x;
+    const int64_t k = blockIdx.x;  // segment position (row perm[k])
     int64_t c = 0;
     for (int64_t g = threadIdx.x; g < G; g += ROW_BLOCK) c += seg_cnt[g * n_i + k];
     c = warp_sum(c);
@@ -215,7 +222,18 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_seg_count_rows(const int32_t *__r
     if (threadIdx.x == 0) {
         int64_t s = 0;
         for (int w = 0; w < ROW_BLOCK / 32; ++w) s += ws[w];
-        total[k] = (int32_t)(s < INT32_MAX ? s : INT32_MAX);
+        total[perm ? perm[k] : k] = (int32_t)(s < INT32_MAX ? s : INT32_MAX);
+    }
+}
+
+// The same with few segments: a thread per position.
+__global__ void k_seg_count_pos(const int32_t *__restrict__ seg_cnt, int64_t G, int64_t n_i,
+                                int32_t *__restrict__ total, const int32_t *__restrict__ perm)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_i; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int64_t g = 0; g < G; ++g) c += seg_cnt[g * n_i + k];
+        total[perm[k]] = (int32_t)(c < INT32_MAX ? c : INT32_MAX);
     }
 }
 
@@ -224,10 +242,11 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_seg_count_rows(const int32_t *__r
 __global__ void __launch_bounds__(ROW_BLOCK) k_seg_gather_rows(const int32_t *__restrict__ seg_cnt,
                                                                const int32_t *__restrict__ seg_slots, int64_t G,
                                                                int64_t n_i, int L, const int64_t *__restrict__ off,
-                                                               int32_t *__restrict__ nb_idx, int64_t capacity)
+                                                               int32_t *__restrict__ nb_idx, int64_t capacity,
+                                                               const int32_t *__restrict__ perm)
 {
     __shared__ int64_t wsum[32];
-    const int64_t k = blockIdx.x;
+    const int64_t k = blockIdx.x;  // segment position (row perm[k])
     const int64_t g0 = (G * threadIdx.x) / ROW_BLOCK, g1 = (G * (threadIdx.x + 1)) / ROW_BLOCK;
     int64_t mine = 0;
     for (int64_t g = g0; g < g1; ++g) {
@@ -236,7 +255,8 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_seg_gather_rows(const int32_t *__
     }
     int64_t total;
     int64_t pos = block_exclusive_scan(mine, wsum, total);
-    const int64_t o0 = off[k], kept = off[k + 1] - o0;
+    const int64_t row = perm ? perm[k] : k;
+    const int64_t o0 = off[row], kept = off[row + 1] - o0;
     for (int64_t g = g0; g < g1 && pos < kept; ++g) {
         int c = seg_cnt[g * n_i + k];
         c = c < L ? c : L;
@@ -250,13 +270,20 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_seg_gather_rows(const int32_t *__
 
 int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap, const int32_t *seg_cnt,
                          const int32_t *seg_slots, int64_t *off, int32_t *nb_idx, int64_t nb_capacity,
-                         int32_t *count_true, int64_t *scan_tmp, int32_t *row_total, unsigned *status)
+                         int32_t *count_true, int64_t *scan_tmp, int32_t *row_total, unsigned *status,
+                         const int32_t *perm)
 {
     const int64_t nb = (n_i + SCAN_BLOCK - 1) / SCAN_BLOCK;
     int kernels = 0;
-    const bool many = G > 64 && row_total != nullptr;
-    if (many) {  // sum the segments of every row in parallel first
-        k_seg_count_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, G, n_i, row_total);
+    // segments at spatial-order positions: the per-row totals are put in row order first
+    const bool many = (G > 64 || perm) && row_total != nullptr;
+    if (many && (G > 64 || !perm)) {  // sum the segments of every row in parallel first
+        k_seg_count_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, G, n_i, row_total, perm);
+        ++kernels;
+    } else if (many) {
+        int64_t g = (n_i + 255) / 256;
+        if (g > 152 * 16) g = 152 * 16;
+        k_seg_count_pos<<<(unsigned)(g < 1 ? 1 : g), 256, 0, st>>>(seg_cnt, G, n_i, row_total, perm);
         ++kernels;
     }
     k_seg_scan_local<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(many ? row_total : seg_cnt, many ? 1 : G, n_i, cap, off,
@@ -268,11 +295,12 @@ int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap
         kernels += 2;
     }
     if (!nb_idx || L <= 0) return kernels;
-    if (many) {
-        k_seg_gather_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity);
+    if (G > 64 && row_total != nullptr) {
+        k_seg_gather_rows<<<(unsigned)n_i, ROW_BLOCK, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity,
+                                                               perm);
     } else {
         const int64_t blocks = (n_i + 7) / 8;
-        k_seg_gather<<<(unsigned)blocks, 256, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity);
+        k_seg_gather<<<(unsigned)blocks, 256, 0, st>>>(seg_cnt, seg_slots, G, n_i, L, off, nb_idx, nb_capacity, perm);
     }
     return kernels + 1;
 }

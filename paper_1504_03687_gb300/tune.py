@@ -23,7 +23,7 @@ import numpy as np
 TABLE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_plans.json")
 
 # candidate plans: (kernel, variant, splits); splits 0 = the planner's split count
-MIXED_CANDIDATES = [(1, v, 0) for v in range(17)] + [(2, v, 0) for v in range(3)]
+MIXED_CANDIDATES = [(1, v, 0) for v in range(18)] + [(2, v, 0) for v in range(3)]
 FP64_CANDIDATES = [(0, 0, 0), (3, 0, 0), (3, 1, 0)]
 
 

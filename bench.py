@@ -37,10 +37,11 @@ NB_CAP = 512
 
 # DRAM bytes (read + write) of the four force launches of one step (blocks 2^10 .. 2^20), from
 # one ncu capture of `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu --no-ensemble
-# --no-adjoint` (metrics dram__bytes_read.sum, dram__bytes_write.sum), valid only for the
+# --no-adjoint --no-irregular --no-scheduler --no-integrator` (metrics dram__bytes_read.sum,
+# dram__bytes_write.sum; -s 12 -c 4: the timed step's launches), valid only for the
 # force-kernel sources whose SHA-256 is recorded with them.
-FORCE_TRAFFIC = {"sources_sha256": "bbd7f6e973dcee1abf08528ebdacb8ec3facaf31f82f4846bd9b33ad60453125",
-                 "bytes_per_launch": [64852224, 141047296, 1287248640, 3185677312]}
+FORCE_TRAFFIC = {"sources_sha256": "65a344188e8a1caf447875a567c4493612a58052c985232352c5b0b28d8ce19a",
+                 "bytes_per_launch": [59673344, 131630848, 1008468480, 2086584832]}
 FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh", "roworder.cu")
 
 

@@ -62,11 +62,47 @@ __global__ void __launch_bounds__(256) k_reduce_wide(const double *__restrict__ 
     }
 }
 
+// Many splits and a few thousand positions: one warp per position, the seven components in turn, each
+// summed as in k_reduce_wide (lanes over the splits, the same butterfly), so the two kernels
+// give the same bits.
+__global__ void __launch_bounds__(256) k_reduce_warp(const double *__restrict__ part, int S, int64_t n_i,
+                                                     const int32_t *__restrict__ perm, double *__restrict__ acc,
+                                                     double *__restrict__ jerk, double *__restrict__ pot)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n_i) return;  // warp-uniform
+    double v[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        double sum = 0.0;
+        for (int s = lane; s < S; s += 32) sum += part[((int64_t)s * 7 + c) * n_i + r];
+        v[c] = warp_sum(sum);
+    }
+    if (lane < 7) {
+        const int64_t k = perm ? perm[r] : r;
+        double x = v[0];
+#pragma unroll
+        for (int c = 1; c < 7; ++c)
+            if (lane == c) x = v[c];
+        if (lane < 3)
+            acc[3 * k + lane] = x;
+        else if (lane < 6)
+            jerk[3 * k + lane - 3] = x;
+        else
+            pot[k] = x;
+    }
+}
+
 void launch_reduce(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc, double *jerk,
                    double *pot, const int32_t *perm)
 {
-    if (S > 16) {  // a warp per component and position: the split loop in parallel
+    if (S > 16 && n_i <= 1024) {  // a warp per component and position: the split loop in parallel
         k_reduce_wide<<<(unsigned)n_i, 256, 0, st>>>(part, S, n_i, perm, acc, jerk, pot);
+        return;
+    }
+    if (S > 16 && n_i <= 4096) {  // a warp per position (above, the coalesced thread-per-position form)
+        k_reduce_warp<<<(unsigned)((n_i + 7) / 8), 256, 0, st>>>(part, S, n_i, perm, acc, jerk, pot);
         return;
     }
     int64_t g = (n_i + 255) / 256;

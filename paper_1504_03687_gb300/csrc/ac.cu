@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kStepThreads) k_ac_irregular_step(AcDev D, int
                 hermite_taylor(P.x, V.x, Ac.x, J.x, dt, x0j, v0j);
                 hermite_taylor(P.y, V.y, Ac.y, J.y, dt, x1j, v1j);
                 hermite_taylor(P.z, V.z, Ac.z, J.z, dt, x2j, v2j);
-                pair_f64(make_dvec4(x0j, x1j, x2j, V.w), make_dvec4(v0j, v1j, v2j, 0.0), xi, vi, false, sum);
+                pair_f64_fma(make_dvec4(x0j, x1j, x2j, V.w), make_dvec4(v0j, v1j, v2j, 0.0), xi, vi, sum);
             }
 #pragma unroll
             for (int u = 0; u < 7; ++u) sum[u] = warp_sum(sum[u]);

@@ -13,7 +13,7 @@
 //
 // Two precisions, as the context's:
 //  * FP64: the predictor is hermite_taylor, so a neighbour predicted here is bit-identical to
-//    the same particle after nb_predict; the pair is pair_f64.
+//    the same particle after nb_predict; the pair is pair_f64_fma (pair_f64's sums, fused).
 //  * mixed: r = (x_j - x_i) + (D_j - D_i) with the base difference in double-single (as in
 //    the mixed regular force) and the Taylor increments D = dt (v + dt (a/2 + dt jerk/6)) in
 //    FP32; likewise w = (v_j - v_i) + (E_j - E_i), E = dt (a + dt jerk/2).  dt = t - t_last
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_fp64(IrrArgs A)
             hermite_taylor(P.x, V.x, Ac.x, J.x, dt, x0, v0);
             hermite_taylor(P.y, V.y, Ac.y, J.y, dt, x1, v1);
             hermite_taylor(P.z, V.z, Ac.z, J.z, dt, x2, v2);
-            pair_f64(make_dvec4(x0, x1, x2, V.w), make_dvec4(v0, v1, v2, 0.0), xi, vi, false, s);
+            pair_f64_fma(make_dvec4(x0, x1, x2, V.w), make_dvec4(v0, v1, v2, 0.0), xi, vi, s);
         }
 #pragma unroll
         for (int c = 0; c < 7; ++c) s[c] = warp_sum(s[c]);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_rec_fp64(IrrArgs A)
                 continue;
             }
             if (j == i) continue;
-            pair_f64(R[2 * j], R[2 * j + 1], xi, vi, false, s);
+            pair_f64_fma(R[2 * j], R[2 * j + 1], xi, vi, s);
         }
 #pragma unroll
         for (int c = 0; c < 7; ++c) s[c] = warp_sum(s[c]);

@@ -140,6 +140,30 @@ __device__ __forceinline__ void irr_store_df(const IrrArgs &A, int64_t k, int la
     }
 }
 
+// One FP64 pair of the irregular force (pair_f64's sums) with every multiply-add written as an
+// explicit fused operation: the same bits under any contraction setting, and FMA-dense on the
+// narrow FP64 pipe (the irregular units are compiled without automatic contraction).
+__device__ __forceinline__ void pair_f64_fma(const dvec4 &p0, const dvec4 &p1, const double (&xi)[3],
+                                             const double (&vi)[3], double *acc)
+{
+    const double rx = __dsub_rn(p0.x, xi[0]), ry = __dsub_rn(p0.y, xi[1]), rz = __dsub_rn(p0.z, xi[2]);
+    const double r2 = __fma_rn(rz, rz, __fma_rn(ry, ry, __dmul_rn(rx, rx)));
+    const double rinv = rsqrt(r2);
+    const double wx = __dsub_rn(p1.x, vi[0]), wy = __dsub_rn(p1.y, vi[1]), wz = __dsub_rn(p1.z, vi[2]);
+    const double rw = __fma_rn(rz, wz, __fma_rn(ry, wy, __dmul_rn(rx, wx)));
+    const double rinv2 = __dmul_rn(rinv, rinv);
+    const double mr = __dmul_rn(p0.w, rinv);
+    const double mr3 = __dmul_rn(mr, rinv2);
+    const double beta = __dmul_rn(-3.0, __dmul_rn(rw, rinv2));
+    acc[0] = __fma_rn(mr3, rx, acc[0]);
+    acc[1] = __fma_rn(mr3, ry, acc[1]);
+    acc[2] = __fma_rn(mr3, rz, acc[2]);
+    acc[3] = __fma_rn(mr3, __fma_rn(beta, rx, wx), acc[3]);
+    acc[4] = __fma_rn(mr3, __fma_rn(beta, ry, wy), acc[4]);
+    acc[5] = __fma_rn(mr3, __fma_rn(beta, rz, wz), acc[5]);
+    acc[6] = __dsub_rn(acc[6], mr);
+}
+
 // Taylor increments of the mixed path: D = dt (v + dt (a/2 + dt jerk/6)), E = dt (a + dt jerk/2).
 __device__ __forceinline__ void incr_f32(float v, float a, float j, float dt, float &D, float &E)
 {

@@ -446,6 +446,43 @@ def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec,variant", [("mixed", 4), ("mixed", 10), ("mixed", 15), ("fp64", 0)])
+@pytest.mark.parametrize("n_i,splits", [(2000, 40), (600, 40), (6000, 24)])
+def test_many_splits(gpu_lib, p128k, prec, variant, n_i, splits):
+    """Many j-splits (the partial-sum reductions of more than 16 splits: a warp per component
+    for up to 1024 rows, a warp per row up to 4096, a thread per row above), over kernels that
+    write their partial sums and segments at the row index and at the spatial-order position:
+    the bars against the oracle, and lists identical to the one-split call's."""
+    cl, rs2, steps = p128k
+    idx = W.active_block(steps, n_i)
+    sel = np.sort(np.random.default_rng(n_i).choice(n_i, 96, replace=False))
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx[sel], rs2, cap=512)
+    ctx = make_ctx(cl.n, prec)
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    kernel = 1 if prec == "mixed" else 0
+    ctx.set_plan_override(kernel, variant, splits)
+    assert ctx.plan(cl.n, n_i)["splits"] == splits
+    res = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    ctx.set_plan_override(kernel, variant, 1)
+    one = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    assert torch.equal(one.nb_off, res.nb_off) and torch.equal(one.nb_count, res.nb_count)
+    tot = int(one.nb_off[-1])
+    assert torch.equal(one.nb_idx[:tot], res.nb_idx[:tot])
+
+    class _Rows:
+        pass
+    sub = _Rows()
+    sub.acc, sub.jerk, sub.pot = res.acc[sel], res.jerk[sel], res.pot[sel]
+    if prec == "mixed":
+        check_mixed(sub, ref)
+    else:
+        sub.acc, sub.jerk, sub.pot = sub.acc.cpu().numpy(), sub.jerk.cpu().numpy(), sub.pot.cpu().numpy()
+        check_fp64(sub, ref, cl.x, cl.v, cl.m, idx[sel])
+    ctx.close()
+
+
 def test_mixed_far_from_the_origin(gpu_lib):
     """The cluster translated by (1e4, -2e4, 3e3) length units (a star cluster far from the
     coordinate origin): forces do not change, but single-precision coordinates would lose about

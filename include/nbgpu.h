@@ -281,7 +281,7 @@ nb_status nb_hermite_correct_backward(nb_ctx *ctx, int64_t n, double t, const do
                                       double *g_a0, double *g_j0, double *g_a1, double *g_j1);
 
 /* Spatial order of an active block's rows: the permutation that the anchored mixed force
- * kernel (plan variants 10-17) takes before it runs, and that a caller may use to lay out its
+ * kernel (plan variants 10-19) takes before it runs, and that a caller may use to lay out its
  * own blocks (no counterpart in the paper; a locality device of this GPU design).  The rows
  * idx (n_i, device int32) are ordered along the Morton (Z) curve of their predicted positions,
  * quantised to 8 bits per coordinate over the block's bounding box (the hi parts of the mixed
@@ -313,7 +313,7 @@ nb_status nb_set_plan_table(nb_ctx *ctx, int32_t n_entries, const int64_t *ni_ma
                             const int32_t *kernel, const int32_t *variant, const int32_t *splits);
 
 /* The automatic plan for a given device shape, without a context or a GPU (host-only):
- * num_sms SMs, ctas_per_sm[0..18] resident CTAs of the eighteen mixed tiled variants and the
+ * num_sms SMs, ctas_per_sm[0..20] resident CTAs of the twenty mixed tiled variants and the
  * FP64 tiled kernel (NULL = 1 each), and the context's nb_cap. */
 nb_status nb_plan_for(int32_t precision, int32_t num_sms, const int32_t *ctas_per_sm, int64_t n,
                       int64_t n_i, int32_t nb_cap, int64_t *out);

@@ -140,7 +140,7 @@ def plan_for(precision: str, num_sms: int, ctas_per_sm, n: int, n_i: int, nb_cap
     """Host-only launch plan (no GPU needed)."""
     lib = load_library()
     out = (ctypes.c_int64 * 6)()
-    occ = (ctypes.c_int32 * 19)(*ctas_per_sm) if ctas_per_sm is not None else None
+    occ = (ctypes.c_int32 * 21)(*ctas_per_sm) if ctas_per_sm is not None else None
     s = lib.nb_plan_for(PRECISIONS[precision], num_sms, ctypes.cast(occ, ctypes.c_void_p) if occ else None,
                         n, n_i, nb_cap, ctypes.cast(out, ctypes.c_void_p))
     if s != NB_OK:

@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 // (the loop reads the first four; the replay also reads the absolute hi/lo position).
 // Per-row data the replay needs live in shared memory: index, output row, neighbour count,
 // r_s^2 (float) and the row's hi/lo position.
-enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_XH = 4, AR_XL = 7, AR_WORDS = 10 };
+enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_WORDS = 4 };
 
 // HITS > 0: every row's neighbour hits are gathered in shared memory, HITS at a time (8: one
 // 32-byte sector, 16: two), and written out as whole aligned groups instead of one 4-byte store
@@ -653,11 +653,14 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
                     const int32_t gi = srow[AR_GI * NR * BLOCK + slot];
                     if (j32 == gi) continue;
                     const float *xr = reinterpret_cast<const float *>(srow);
+                    // the row's double-single position from its j-record (a candidate pair is
+                    // rare, and shared memory is what bounds the staged variants' occupancy)
+                    const float4 *recp = static_cast<const float4 *>(A.rec);
+                    const float4 ph = __ldg(recp + 3 * (int64_t)gi), pl = __ldg(recp + 3 * (int64_t)gi + 1);
+                    const float xh3[3] = {ph.x, ph.y, ph.z}, xl3[3] = {pl.x, pl.y, pl.z};
                     float r[3];
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc)
-                        r[cc] = ds_diff(jh[cc], jl[cc], xr[(AR_XH + cc) * NR * BLOCK + slot],
-                                        xr[(AR_XL + cc) * NR * BLOCK + slot]);
+                    for (int cc = 0; cc < 3; ++cc) r[cc] = ds_diff(jh[cc], jl[cc], xh3[cc], xl3[cc]);
                     const float r2p = r2_f32(r[0], r[1], r[2]);
                     if (r2p < xr[AR_RS2 * NR * BLOCK + slot] && j < A.j_hi) {
                         int32_t *cp = srow + AR_CNT * NR * BLOCK + slot;
@@ -774,11 +777,7 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
             srow[AR_K * NI * BLOCK + slot] = (int32_t)k;
             srow[AR_CNT * NI * BLOCK + slot] = 0;
             srowf[AR_RS2 * NI * BLOCK + slot] = rs2f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                srowf[(AR_XH + c) * NI * BLOCK + slot] = h3[c];
-                srowf[(AR_XL + c) * NI * BLOCK + slot] = l3[c];
-            }
+
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -1092,13 +1091,13 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
 // ------------------------------------------------------------------------------------------
 // Variants of the tiled kernel: (id, kernel, NI, BLOCK, TJ, min CTAs per SM, kind).  The plan's
 // `variant` indexes this list; ids 0-3 are the scalar kernel, 4-9 the packed-FP32x2 one
-// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-17 the
+// (8 and 9: row tiles of 128 and 64 for blocks of tens to hundreds of rows), 10-19 the
 // anchored packed kernel (rows in spatial order, anchor-relative separations; 13 and 14 with
-// row tiles of 128 and 64; 15-17 staging the neighbour hits).
+// row tiles of 128 and 64; 15-19 staging the neighbour hits).
 // Last column: 0 = scalar (static shared memory), 1 = packed (x2_smem_bytes), 2 = anchored
 // (anchored_smem_bytes; needs the row order A.perm), 3 = anchored with the neighbour hits staged
-// in shared memory and written as whole sectors (15, 16: 8 hits a group with four rows a
-// thread, 16 with two), 4 = the same with 16 hits a group (17).
+// in shared memory and written as whole sectors (15, 16, 18, 19: 8 hits a group with four rows
+// a thread, 16 with two), 4 = the same with 16 hits a group (17).
 #define NB_MIXED_TILED_VARIANTS(X)                       \
     X(0, k_force_mixed_tiled, 4, 128, 256, 3, 0)         \
     X(1, k_force_mixed_tiled, 2, 128, 256, 4, 0)         \
@@ -1117,7 +1116,9 @@ void launch_force_mixed_batched(cudaStream_t st, int variant, int ctas, const Ba
     X(14, k_force_mixed_anchored_x2, 2, 32, 64, 12, 2)   \
     X(15, k_force_mixed_staged_x2, 4, 128, 64, 3, 3)     \
     X(16, k_force_mixed_staged_x2, 2, 128, 64, 4, 3)     \
-    X(17, k_force_mixed_staged16_x2, 4, 128, 64, 2, 4)
+    X(17, k_force_mixed_staged16_x2, 4, 128, 64, 2, 4)   \
+    X(18, k_force_mixed_staged_x2, 4, 128, 128, 3, 3)    \
+    X(19, k_force_mixed_staged_x2, 4, 128, 256, 2, 3)
 
 struct TiledVariant {
     int ni, block, tj, smem, kind;

@@ -53,9 +53,9 @@ int launch_adjoint(cudaStream_t st, int precision, const void *rec, int64_t n, c
 }  // namespace nbgpu
 
 static constexpr int kTilePad = 256;   // j-record arrays are padded to a multiple of this
-static constexpr int kMixedTiledVariants = 18;  // entries of the mixed tiled variant table
-static constexpr int kOccFp64 = 18;             // occupancy slot of the FP64 tiled kernel
-static constexpr int kOccSlots = 19;
+static constexpr int kMixedTiledVariants = 20;  // entries of the mixed tiled variant table
+static constexpr int kOccFp64 = 20;             // occupancy slot of the FP64 tiled kernel
+static constexpr int kOccSlots = 21;
 static_assert(kOccSlots == kMixedTiledVariants + 1, "one occupancy slot per mixed tiled variant, then the FP64 kernel");
 static constexpr int kMaxCap = 8192;   // largest nb_cap (sort buffers live in shared memory)
 // Irregular force: predict all particles once when N_i * factor >= N.  Measured on this GPU
@@ -312,9 +312,9 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
         // GB300 at N = 2^20, N_i = 2^17 (King W0 = 6); the two small-tile packed variants
         // (NI=2 x 64 and x 32 threads) estimated from their occupancy; the anchored variants
         // measured the same way (10-12) or estimated (13, 14: the small-tile packed ones x 1.1;
-        // 15-17: the staged-hit forms of 10 and 11)
+        // 15-19: the staged-hit forms of 10-12, measured)
         static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91, 0.85,
-                                                           0.75, 1.12, 1.08, 1.04, 0.94, 0.82, 1.10, 1.06, 1.05};
+                                                           0.75, 1.12, 1.08, 1.125, 0.94, 0.82, 1.11, 1.06, 1.02, 1.115, 1.12};
         double best = -1.0;
         for (int v = 0; v < kMixedTiledVariants; ++v) {
             if (only_variant >= 0 && v != only_variant) continue;

@@ -50,7 +50,7 @@ def test_null_arguments_are_rejected_without_gpu():
     assert lib.nb_last_error(None) == b"null context"
 
 
-OCC = [3, 4, 4, 1, 3, 4, 3, 2, 8, 12, 3, 4, 2, 8, 12, 3, 4, 2, 3]  # resident CTAs/SM: 18 mixed tiled variants, FP64 tiled
+OCC = [3, 4, 4, 1, 3, 4, 3, 2, 8, 12, 3, 4, 2, 8, 12, 3, 4, 2, 3, 2, 3]  # resident CTAs/SM: 20 mixed tiled variants, FP64 tiled
 
 
 @pytest.mark.parametrize("n_i", [1, 2, 16, 32, 33, 100, 1024, 16384, 131072, 1 << 20])

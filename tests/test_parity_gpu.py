@@ -402,7 +402,7 @@ def test_million_body_sampled_rows(gpu_lib, king1m):
 
 
 # ------------------------------------------------------------------ every tiled kernel variant
-@pytest.mark.parametrize("variant", list(range(18)))
+@pytest.mark.parametrize("variant", list(range(20)))
 def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
     """Every variant of the mixed tiled kernel (scalar and packed FP32x2, forced through the plan
     override) meets the mixed bar against the oracle and gives the same neighbour lists."""
@@ -426,7 +426,7 @@ def test_each_mixed_tiled_variant(gpu_lib, p128k, variant):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", list(range(18)))
+@pytest.mark.parametrize("variant", list(range(20)))
 def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
     """Dense neighbourhoods (r_s^2 x 9, hundreds of neighbours a row) with nb_cap 16: many hits
     in every 32-j chunk of the packed kernels' interaction loop and lists cut at the cap inside a

@@ -82,7 +82,7 @@ def test_row_order_puts_bad_rows_last(gpu_lib, p128k):
     assert list(perm[-3:]) == [3, 1000, 4999]
 
 
-@pytest.mark.parametrize("variant", [10, 11, 12, 13, 14, 15, 16, 17])
+@pytest.mark.parametrize("variant", [10, 11, 12, 13, 14, 15, 16, 17, 18, 19])
 def test_anchored_kernel_on_a_large_block(gpu_lib, p128k, variant):
     """20000 rows (the many-CTA ordering), forced anchored variant against the oracle on
     sampled rows; all lists bit-identical to the double-single packed kernel's."""
@@ -134,7 +134,7 @@ def test_anchored_kernel_with_close_pairs(gpu_lib):
     ref = oracle.regular_force(x, v, m, idx, rs2, cap=512)
     ctx = Context(n, precision="mixed", nb_cap=512)
     ctx.set_predicted(T(x), T(v), T(m))
-    for variant in (10, 11, 12, 13, 14, 15, 16, 17):
+    for variant in (10, 11, 12, 13, 14, 15, 16, 17, 18, 19):
         ctx.set_plan_override(1, variant, 0)
         res = ctx.regular_force(T(idx), rs2)
         ctx.sync()

@@ -40,6 +40,14 @@ def device_key(precision: str, n: int) -> str:
     return f"{p.name}|sms={p.multi_processor_count}|{precision}|n=2^{int(round(math.log2(max(n, 1))))}"
 
 
+def choose_plan(timed):
+    """The table entry from [(plan, ms), ...]: the fastest plan, or the fastest staged-hit
+    variant if it is within TIE of it."""
+    best = min(timed, key=lambda e: e[1])
+    staged = [e for e in timed if e[0][0] == 1 and e[0][1] in STAGED_VARIANTS and e[1] <= best[1] * (1 + TIE)]
+    return min(staged, key=lambda e: e[1]) if staged else best
+
+
 def _time_plan(ctx, idx, rs2, plan, reps):
     ctx.set_plan_override(*plan)
     ctx.regular_force(idx, rs2, neighbours=True)  # warm-up (and scratch growth)
@@ -80,10 +88,7 @@ def tune_force(ctx, order, rs2, buckets=None, reps=2, candidates=None, log=print
                 log(f"  n_i={ni} plan={plan}: skipped ({exc})")
                 continue
             timed.append((plan, ms))
-        best = min(timed, key=lambda e: e[1])
-        staged = [e for e in timed if e[0][0] == 1 and e[0][1] in STAGED_VARIANTS and e[1] <= best[1] * (1 + TIE)]
-        if staged:
-            best = min(staged, key=lambda e: e[1])
+        best = choose_plan(timed)
         log(f"n_i={ni}: best {best[0]} {best[1]:.4f} ms ({ni * n / best[1] / 1e6:.1f} Ginteractions/s)")
         table.append((ni, best[0][0], best[0][1], best[0][2], best[1]))
     return table

@@ -1,0 +1,23 @@
+"""The autotuner's choice among timed plans (host logic): the fastest plan, except that a
+staged-hit variant within 1 % of it is preferred (lower DRAM traffic at a tie)."""
+from paper_1504_03687_gb300 import tune
+
+
+def test_staged_variant_taken_only_at_a_tie():
+    timed = [((1, 10, 0), 100.0), ((1, 12, 0), 98.0), ((1, 15, 0), 98.9), ((2, 0, 0), 150.0)]
+    assert tune.choose_plan(timed) == ((1, 15, 0), 98.9)  # 98.9 <= 98 * 1.01
+    timed = [((1, 10, 0), 100.0), ((1, 12, 0), 98.0), ((1, 15, 0), 99.1)]
+    assert tune.choose_plan(timed) == ((1, 12, 0), 98.0)  # 99.1 > 98.98
+
+
+def test_fastest_staged_variant_among_ties():
+    timed = [((1, 12, 0), 50.0), ((1, 18, 0), 50.4), ((1, 19, 0), 50.2), ((1, 15, 0), 50.6)]
+    assert tune.choose_plan(timed) == ((1, 19, 0), 50.2)
+
+
+def test_only_mixed_tiled_staged_variants_count():
+    # variant 15 of another kernel (the j-streamed one has variants 0-2 only) is no staged form
+    timed = [((1, 12, 0), 10.0), ((2, 15, 0), 10.05)]
+    assert tune.choose_plan(timed) == ((1, 12, 0), 10.0)
+    assert set(tune.STAGED_VARIANTS) == {15, 16, 17, 18, 19}
+    assert all((1, v, 0) in tune.MIXED_CANDIDATES for v in tune.STAGED_VARIANTS)

@@ -501,15 +501,23 @@ __global__ void __launch_bounds__(kStepThreads) k_ac_irregular_step(AcDev D, int
             if (ok)
 #pragma unroll
                 for (int u = 0; u < 5; ++u) Pi[u] = S[5 * i + u];
-            // the lane's first list entry and its record are requested before the FP64 work,
-            // and each round's successor while the round is summed (the per-lane order of the
-            // terms is the irregular force kernel's)
-            int64_t e = e0 + lane;
-            int32_t jn = irr_neighbour(A, e, e1);
-            float4 Rn[5];
-            if (jn >= 0)
+            // the lane's list entries four rounds (128 entries a row) at a time: a batch's indices
+            // and then its records are requested together, so a batch costs two round trips
+            // whatever its length, and the first batch is in flight during the FP64 work (the
+            // per-lane order of the terms is the irregular force kernel's)
+            constexpr int kBatch = 4;
+            int32_t jb[kBatch];
+            float4 Rb[kBatch][5];
+            auto fetch = [&](int64_t eb) {
 #pragma unroll
-                for (int u = 0; u < 5; ++u) Rn[u] = S[5 * (int64_t)jn + u];
+                for (int r = 0; r < kBatch; ++r) jb[r] = irr_neighbour(A, eb + 32 * r, e1);
+#pragma unroll
+                for (int r = 0; r < kBatch; ++r)
+                    if (jb[r] >= 0)
+#pragma unroll
+                        for (int u = 0; u < 5; ++u) Rb[r][u] = S[5 * (int64_t)jb[r] + u];
+            };
+            fetch(e0 + lane);
             prework();
             if (ok) {
                 const float4 P = Pi[0], L = Pi[1], V = Pi[2], Ac = Pi[3], J = Pi[4];
@@ -522,17 +530,11 @@ __global__ void __launch_bounds__(kStepThreads) k_ac_irregular_step(AcDev D, int
                 incr_f32(V.z, Ac.z, J.z, dt, iD[2], iE[2]);
             }
             float f[7] = {0, 0, 0, 0, 0, 0, 0};
-            while (e < e1) {
-                const int32_t j = jn;
-                float4 R[5];
+            for (int64_t eb = e0 + lane; eb < e1; eb += 32 * kBatch) {
 #pragma unroll
-                for (int u = 0; u < 5; ++u) R[u] = Rn[u];
-                e += 32;
-                jn = irr_neighbour(A, e, e1);
-                if (jn >= 0)
-#pragma unroll
-                    for (int u = 0; u < 5; ++u) Rn[u] = S[5 * (int64_t)jn + u];
-                if (j >= 0 && j != i) state_pair_mixed(R, A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
+                for (int r = 0; r < kBatch; ++r)
+                    if (jb[r] >= 0 && jb[r] != i) state_pair_mixed(Rb[r], A.t_hi, A.t_lo, ih, il, iv, iD, iE, f);
+                if (eb + 32 * kBatch < e1) fetch(eb + 32 * kBatch);
             }
             float h, l;
             warp_sum7_df(f, lane, h, l);

@@ -2,8 +2,9 @@
 // is stated with the declarations in nbgpu.h).  One block step is a fixed sequence of
 // launches on the context stream:
 //   nb_sched_next (host)          -> block time t, active particles = list prefix
-//   k_ac_classify                 -> which active particles also take a regular step (only
-//                                    when the regular-level histogram predicts some)
+//   k_ac_classify_count, _place   -> which active particles also take a regular step, in
+//                                    list order (only when the regular-level histogram
+//                                    predicts some)
 //   with a regular subset:
 //     nb_predict(t)               -> all particles predicted, j-records built
 //     nb_regular_force (regular)  -> all-j sums and the new lists of the regular subset
@@ -16,9 +17,15 @@
 //                                    state records of the corrected particles
 //   k_ac_lists                    -> the new lists replace the old ones
 //   nb_sched_update               -> the requested levels re-sort the active prefix
+// nb_ac_run drives runs of block steps without a regular subset from the device instead: per
+// step one launch of k_ac_irregular_step (irregular force, corrector, step rule; its last CTA
+// re-sorts the prefix and selects the next step into StepParams), enqueued in batches sized
+// from the level histograms, each launch a programmatic dependent of the one before, one host
+// synchronisation per batch.  Both paths give the same bits.
 // The corrector's FP64 arithmetic is written operation by operation in the order of the
-// plain definition and this file is compiled without FMA contraction, so an FP64 context
-// follows the reference integration to rounding.
+// plain definition (its divisions by powers of two as exact scalings) and this file is
+// compiled without FMA contraction, so an FP64 context follows the reference integration to
+// rounding.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

@@ -347,14 +347,39 @@ def main():
                                      nb_count=pin(np.empty(b, np.int32))))
         h2d = sum(q.nbytes for q in h_state) + sum(q.nbytes for q in h_idx) + 8 * len(BLOCKS)
 
+        # one GPU: the step's inputs go up, the blocks run on the device largest first, and each
+        # block's results come down on a copy stream while the next block computes (the copies
+        # of the largest block's 1 GB of lists hide behind the three smaller blocks)
+        order_q = sorted(range(len(BLOCKS)), key=lambda q: -BLOCKS[q])
+        d_idx_e = [torch.empty(b, dtype=torch.int32, device=dev) for b in BLOCKS]
+        outs_e = [None] * len(BLOCKS)
+        copy_stream = torch.cuda.Stream(device=dev)
+        done_ev = [torch.cuda.Event() for _ in BLOCKS]
+
         def e2e_step():
             d2h = 0
             ctx.set_particles(*h_state)
             if world == 1:
-                for q, b in enumerate(BLOCKS):
+                for q in order_q:
+                    d_idx_e[q].copy_(torch.from_numpy(h_idx[q]), non_blocking=True)
                     ctx.predict(0.125)
-                    r = host_force(ctx, h_idx[q], rs2, h_out[q])
-                    d2h += r
+                    outs_e[q] = ctx.regular_force(d_idx_e[q], rs2_dev, nb_capacity=BLOCKS[q] * NB_PER_ROW,
+                                                  out=outs_e[q])
+                    done_ev[q].record()
+                with torch.cuda.stream(copy_stream):
+                    for q in order_q:
+                        copy_stream.wait_event(done_ev[q])
+                        r, h = outs_e[q], h_out[q]
+                        used = int(r.nb_off[-1:].to("cpu").item())  # waits for this block only
+                        used = min(used, h.nb_idx.shape[0])
+                        for hd, dv in ((h.acc, r.acc), (h.jerk, r.jerk), (h.pot, r.pot), (h.nb_off, r.nb_off),
+                                       (h.nb_count, r.nb_count)):
+                            torch.from_numpy(hd).copy_(dv, non_blocking=True)
+                            d2h += hd.nbytes
+                        torch.from_numpy(h.nb_idx[:used]).copy_(r.nb_idx[:used], non_blocking=True)
+                        d2h += used * 4
+                copy_stream.synchronize()
+                ctx.sync()
                 return d2h
             # several ranks: each computes its share of the rows from the host arrays, the shares
             # are exchanged on the device (NCCL) and every rank reads the whole block back

@@ -812,7 +812,7 @@ def bench_ac(dev, n=65536, t_end=1.0 / 64, precisions=("mixed", "fp64"), referen
                        f"t = 0 .. {t_end} (= dt_max: every particle ends at t_end)"}
     for prec in precisions:
         ctx = Context(n, precision=prec, nb_cap=256, device=dev.index or 0)
-        ctx.apply_tuned()  # the autotuner's launch plans for this particle count, if any
+        ctx.apply_tuned(n)  # the autotuner's launch plans for this particle count, if any
         ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -903,7 +903,7 @@ def bench_ac_king_1m(dev, t_end=1.0 / 64, dt_max=None):
     rs2 = W.neighbour_radius2(cl.x, 50, seed=2)
     E0 = gpu_energy(dev, cl.m, cl.x, cl.v)
     ctx = Context(cl.n, precision="mixed", nb_cap=256, device=dev.index or 0)
-    ctx.apply_tuned()
+    ctx.apply_tuned(cl.n)
     ac = ACIntegrator(ctx, cl.m, cl.x, cl.v, rs2, eta_irr=0.02, eta_reg=0.03, eta_s=0.01,
                       dt_max=t_end if dt_max is None else dt_max, nb_opt=50)
     torch.cuda.synchronize()

@@ -314,7 +314,7 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
         // measured the same way (10-12) or estimated (13, 14: the small-tile packed ones x 1.1;
         // 15-19: the staged-hit forms of 10-12, measured)
         static const double speed[kMixedTiledVariants] = {0.81, 0.87, 0.71, 0.76, 0.99, 0.92, 1.0, 0.91, 0.85,
-                                                           0.75, 1.12, 1.08, 1.125, 0.94, 0.82, 1.11, 1.06, 1.02, 1.115, 1.12};
+                                                           0.75, 1.12, 1.08, 1.125, 0.94, 0.82, 1.107, 1.06, 1.027, 1.111, 1.036};
         double best = -1.0;
         for (int v = 0; v < kMixedTiledVariants; ++v) {
             if (only_variant >= 0 && v != only_variant) continue;

@@ -130,6 +130,25 @@ __device__ __forceinline__ int ac_level_rule_est(int L, float A, float J, float 
     return L;
 }
 
+// ac_level_rule(L, ac_crit(eta, a, j, a2, a3), ...) for one thread's three components: decided
+// on the FP32 estimate where that provably gives the same level, on the FP64 criterion
+// otherwise (the sums of squares are formed as in the fused step kernel, ((x0^2 + x1^2) + x2^2)).
+__device__ __forceinline__ int ac_level_rule_vec(double eta, const double *a, const double *j, const double *a2,
+                                                 const double *a3, int L, int64_t t_ticks, int lmin, int lmax)
+{
+    float sq[4] = {0.f, 0.f, 0.f, 0.f};
+    const double *v[4] = {a, j, a2, a3};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float x = __double2float_rn(v[u][c]);
+            sq[u] = c == 0 ? __fmul_rn(x, x) : __fadd_rn(sq[u], __fmul_rn(x, x));
+        }
+    const int Le = ac_level_rule_est(L, sq[0], sq[1], sq[2], sq[3], (float)eta, t_ticks, lmin, lmax);
+    return Le >= 0 ? Le : ac_level_rule(L, ac_crit(eta, a, j, a2, a3), t_ticks, lmin, lmax);
+}
+
 // Largest power of two (level) not above crit and not above dt_max.
 __device__ int ac_quantise(double crit, int lmin, int lmax)
 {
@@ -338,8 +357,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
                 a2r[c] = a2 + H * a3;
                 a3r[c] = a3;
             }
-            const double critR = ac_crit(D.eta_reg, Fold, Jold, a2r, a3r);
-            LR = ac_level_rule(LR0, critR, t_ticks, D.lmin, D.lmax);
+            LR = ac_level_rule_vec(D.eta_reg, Fold, Jold, a2r, a3r, LR0, t_ticks, D.lmin, D.lmax);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int64_t q = 3 * i + c;
@@ -375,8 +393,7 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
             D.jk[q] = j1[c];
         }
         D.tl[i] = t;
-        const double crit = ac_crit(D.eta_irr, a1, j1, a2e, a3);
-        int L = ac_level_rule(LI0, crit, t_ticks, D.lmin, D.lmax);
+        int L = ac_level_rule_vec(D.eta_irr, a1, j1, a2e, a3, LI0, t_ticks, D.lmin, D.lmax);
         if (p >= 0) {
             if (LR > L) LR = L;  // regular step at least the new irregular step
             D.LR[i] = LR;

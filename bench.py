@@ -40,8 +40,8 @@ NB_CAP = 512
 # --no-adjoint --no-irregular --no-scheduler --no-integrator` (metrics dram__bytes_read.sum,
 # dram__bytes_write.sum; -s 12 -c 4: the timed step's launches), valid only for the
 # force-kernel sources whose SHA-256 is recorded with them.
-FORCE_TRAFFIC = {"sources_sha256": "aa67df7d18f27b4719e0d598b00f3daa69cc2cc7e905db7f83a704cc19f2fe68",
-                 "bytes_per_launch": [55062016, 130493952, 1015407872, 2144403456]}
+FORCE_TRAFFIC = {"sources_sha256": "9ee2fa97f574a23cdd73f20ce1fdefb0049eb63d55beb620c3e32783c821f091",
+                 "bytes_per_launch": [55172096, 118991616, 431562240, 1166722816]}
 FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh", "roworder.cu")
 
 

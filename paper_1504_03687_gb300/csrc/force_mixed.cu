@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_tiled_x2(ForceArgs 
 // (the loop reads the first four; the replay also reads the absolute hi/lo position).
 // Per-row data the replay needs live in shared memory: index, output row, neighbour count,
 // r_s^2 (float) and the row's hi/lo position.
-enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_WORDS = 4 };
+enum { AR_GI = 0, AR_K = 1, AR_CNT = 2, AR_RS2 = 3, AR_LIM = 4, AR_WORDS = 5 };
 
 // HITS > 0: every row's neighbour hits are gathered in shared memory, HITS at a time (8: one
 // 32-byte sector, 16: two), and written out as whole aligned groups instead of one 4-byte store
@@ -665,14 +665,15 @@ __device__ __forceinline__ void tile_mixed_anchored(const float4 *__restrict__ s
                     if (r2p < xr[AR_RS2 * NR * BLOCK + slot] && j < A.j_hi) {
                         int32_t *cp = srow + AR_CNT * NR * BLOCK + slot;
                         const int cnt = *cp;
-                        if (cnt < A.L) {
+                        const int lim = srow[AR_LIM * NR * BLOCK + slot];
+                        if (cnt < lim) {
                             // the row's segment at its position in the spatial order
                             const int64_t r = (int64_t)blockIdx.x * (NR * BLOCK) + slot;
                             int32_t *seg = A.seg_slots + ((int64_t)s * A.n_i + r) * A.L;
                             if (HITS > 0) {
                                 int32_t *sbuf = srow + AR_WORDS * NR * BLOCK + slot;
                                 sbuf[(cnt & (HITS - 1)) * NR * BLOCK] = j32;
-                                if ((cnt & (HITS - 1)) == HITS - 1 || cnt == A.L - 1)
+                                if ((cnt & (HITS - 1)) == HITS - 1 || cnt == lim - 1)
                                     flush_staged<HITS>(seg, sbuf, NR * BLOCK, cnt & ~(HITS - 1), cnt,
                                                        (A.L & (HITS - 1)) == 0);
                             } else {
@@ -776,6 +777,20 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
             srow[AR_GI * NI * BLOCK + slot] = (int32_t)g;
             srow[AR_K * NI * BLOCK + slot] = (int32_t)k;
             srow[AR_CNT * NI * BLOCK + slot] = 0;
+            int32_t lim = A.L;
+            if (A.cap > 0 && s > 0 && k >= 0) {
+                // the hits the row's earlier segments hold, from the counts their CTAs have
+                // written by now (-1: not yet written, taken as none): only nb_cap minus those
+                // can reach the row's list, so no more are stored (the count stays complete)
+                int64_t prior = 0;
+                for (int q2 = 0; q2 < s; ++q2) {
+                    const int32_t c2 = __ldcg(A.seg_cnt + (int64_t)q2 * A.n_i + r);
+                    if (c2 > 0) prior += c2;
+                }
+                const int64_t room = (int64_t)A.cap - prior;
+                lim = room <= 0 ? 0 : (room < A.L ? (int32_t)room : A.L);
+            }
+            srow[AR_LIM * NI * BLOCK + slot] = lim;
             srowf[AR_RS2 * NI * BLOCK + slot] = rs2f;
 
         }
@@ -848,8 +863,9 @@ __device__ __forceinline__ void anchored_body(const ForceArgs &A)
             if (A.want_nb) {  // the count and the last group, at the position too
                 const int cnt = srow[AR_CNT * NI * BLOCK + slot];
                 A.seg_cnt[(int64_t)s * A.n_i + r] = cnt;
-                const int c = cnt < A.L ? cnt : A.L;  // staged hits not yet written (a last, partial group)
-                if (HITS > 0 && c < A.L && (c & (HITS - 1)) != 0) {
+                const int lim = srow[AR_LIM * NI * BLOCK + slot];
+                const int c = cnt;  // staged hits not yet written (a last, partial group)
+                if (HITS > 0 && cnt < lim && (c & (HITS - 1)) != 0) {
                     // with L a multiple of HITS the whole group is written (the slots past the
                     // count hold stale values that nothing reads), so every list store is a
                     // whole aligned chunk

@@ -935,6 +935,12 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
     fa.rs2_scalar = rs2_scalar ? 1 : 0;
     fa.want_nb = want_nb ? 1 : 0;
     fa.L = L;
+    // the anchored kernels skip storing hits that earlier segments of the row already make
+    // surplus; they read those segments' counts, which start as -1 (not yet known)
+    if (want_nb && p.S > 1 && p.S <= kPriorSegMax && p.kernel == 1 && mixed_tiled_anchored(p.variant)) {
+        fa.cap = c->cap;
+        CK(cudaMemsetAsync(c->seg_cnt, 0xff, (size_t)p.S * n_i * 4, c->stream), "clear counts");
+    }
     fa.part = c->part;
     fa.seg_cnt = c->seg_cnt;
     fa.seg_slots = c->seg_slots;

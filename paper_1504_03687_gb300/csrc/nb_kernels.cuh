@@ -27,6 +27,11 @@ namespace nbgpu {
 // L = min(nb_cap, longest segment) suffices because a segment that holds more than L
 // hits can only be reached when L = nb_cap.
 
+// With at most this many j-splits the anchored kernels read, at the start of a CTA, the
+// neighbour counts that the CTAs of the earlier segments of its rows have written, and store
+// only the hits a row can still keep (nb_cap minus the hits before it).
+constexpr int kPriorSegMax = 64;
+
 struct ForceArgs {
     const void *rec;        // dvec4* (FP64) or float4* (mixed)
     int64_t n;              // particles
@@ -40,6 +45,7 @@ struct ForceArgs {
     int32_t want_nb;        // 0: skip neighbour capture
     int32_t S;              // j-splits (blockIdx.y)
     int32_t L;              // neighbour slots per (segment, row); 0 = count only
+    int32_t cap;            // nb_cap; 0 = store every hit up to L (see prior_count below)
     double *part;           // partial sums [S][7][n_i] at row k (the anchored kernels: at row-order position r)
     int32_t *seg_cnt;       // [G][n_i]
     int32_t *seg_slots;     // [G][n_i][L]

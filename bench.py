@@ -39,10 +39,11 @@ NB_CAP = 512
 # one ncu capture of `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu --no-ensemble
 # --no-adjoint --no-irregular --no-scheduler --no-integrator` (metrics dram__bytes_read.sum,
 # dram__bytes_write.sum; -s 12 -c 4: the timed step's launches), valid only for the
-# force-kernel sources whose SHA-256 is recorded with them.
-FORCE_TRAFFIC = {"sources_sha256": "9ee2fa97f574a23cdd73f20ce1fdefb0049eb63d55beb620c3e32783c821f091",
+# force-kernel sources whose SHA-256 is recorded with them (FORCE_SOURCES: the kernels, their
+# device helpers and their argument header).
+FORCE_TRAFFIC = {"sources_sha256": "abd040a14350a4da3ea6128d4fe0191fef428487ff447b1a5f4cce4eb9b9385b",
                  "bytes_per_launch": [55172096, 118991616, 431562240, 1166722816]}
-FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_kernels.cuh", "roworder.cu")
+FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_force.cuh", "roworder.cu")
 
 
 def force_sources_sha256() -> str:

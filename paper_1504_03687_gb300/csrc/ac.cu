@@ -283,14 +283,8 @@ __global__ void __launch_bounds__(kClassifyBlock)
 __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double t, int64_t t_ticks,
                              const int32_t *reg_pos, const double *Fo, const double *Jo, const double *Fa,
                              const double *Ja, const double *Fn, const double *Jn, const int32_t *cnt_true,
-                             int32_t *want, unsigned long long *pairs, unsigned *status, const StepParams *dyn)
+                             int32_t *want, unsigned long long *pairs, unsigned *status)
 {
-    if (dyn) {  // a device-driven step: its prefix and block time (nothing to do when halted)
-        if (dyn->halt) return;
-        n_act = dyn->n_act;
-        t = dyn->t;
-        t_ticks = dyn->t_ticks;
-    }
     // CTAs past the rows have nothing to do and take no part in the last-CTA epilogue
     const int64_t per = (int64_t)gridDim.x * blockDim.x;
     const int64_t used = n_act <= 0 ? 1 : (n_act < per ? (n_act + blockDim.x - 1) / blockDim.x : gridDim.x);
@@ -411,10 +405,9 @@ __global__ void k_ac_correct(AcDev D, int64_t n_act, const int32_t *list, double
     // one atomic per warp for the neighbour-pair count (a row's count is at most nb_cap)
     const unsigned wp = __reduce_add_sync(0xffffffffu, (unsigned)my_pairs);
     if ((threadIdx.x & 31) == 0 && wp) atomicAdd(pairs, (unsigned long long)wp);
-    if (dyn) return;  // a batch of device-driven steps publishes once, after its last step
     // the last CTA to finish publishes the final histogram and the step's status flags to the
-    // host words (read after the scheduler's synchronisation; the flags are OR-ed in, so a batch
-    // of device-driven steps reports every step's) and clears the device flags
+    // host words (read after the scheduler's synchronisation; the flags are OR-ed in) and
+    // clears the device flags
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -736,12 +729,13 @@ __global__ void k_ac_get_steps(const AcDev D, int64_t n, double *dt, double *DT,
     }
 }
 
-// The first kernel of a device-driven block step (one thread): the next block time and the
-// active prefix from the scheduler's device counts, as nb_sched_next finds them on the host.
-// The step halts, and with it every step queued after it, when that time passes t_end, when
-// the regular-level histogram says some particle takes a regular step there (the host path
-// runs those), when the prefix is longer than one device re-sort takes, or when the batch's
-// budget dstep[0] is spent; otherwise it counts the step (dstep[1]) and its rows (dstep[2]).
+// The begin of the first step of a batch of device-driven block steps (one warp, step_begin):
+// the next block time and the active prefix from the scheduler's device counts, as
+// nb_sched_next finds them on the host.  The step halts, and with it every step queued after
+// it, when that time passes t_end, when the regular-level histogram says some particle takes a
+// regular step there (the host path runs those), when the prefix is longer than the step
+// kernel's re-sort takes, or when the batch's budget dstep[0] is spent; otherwise it counts the
+// step (dstep[1]) and its rows (dstep[2]).  Later steps begin in the last CTA of the step before.
 __global__ void __launch_bounds__(32) k_ac_begin(StepBegin B, SchedDevice S)
 {
     // one warp: lane l holds the levels l and l + 32
@@ -1038,7 +1032,7 @@ nb_status nb_ac_step(nb_ac *s, double *t_block, int64_t *n_active, int64_t *n_re
     k_ac_correct<<<grid_of(na, 128, 152 * 32), 128, 0, st>>>(s->D, na, list, t, t_ticks,
                                                               nr > 0 ? s->reg_pos : nullptr, s->Fo, s->Jo,
                                                               s->Fa, s->Ja, s->Fn, s->Jn, s->cnt_true, s->want,
-                                                              s->pairs, cs.status + SS_FLAGS, nullptr);
+                                                              s->pairs, cs.status + SS_FLAGS);
     if (nr > 0) k_ac_lists<<<grid_of(nr * 32, 256, 152 * 16), 256, 0, st>>>(s->D, nr, s->reg_idx, s->off, s->csr);
     ACK(cudaGetLastError(), "corrector launch");
     ctx_state_changed(s->ctx);  // the corrector rewrote the context's state arrays

@@ -39,7 +39,6 @@ __global__ void k_pack_state(int64_t n, const double *__restrict__ x, const doub
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_irregular_fp64(IrrArgs A)
 {
-    if (!irr_dyn(A)) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * BLOCK) >> 5;
@@ -88,7 +87,6 @@ __global__ void __launch_bounds__(BLOCK) k_irregular_fp64(IrrArgs A)
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_irregular_mixed(IrrArgs A)
 {
-    if (!irr_dyn(A)) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * BLOCK) >> 5;
@@ -220,10 +218,9 @@ size_t state_record_bytes(int precision, int64_t n) { return (size_t)n * (precis
 void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *srec, int predicted, int64_t n,
                       double t, int64_t n_i, const int32_t *idx, const int64_t *off, const int32_t *nb, double *acc,
                       double *jerk, double *pot, double *acc_reg, double *jerk_reg, double *pot_reg, unsigned *status,
-                      const int32_t *ell_cnt, int64_t ell_stride, const StepParams *dyn)
+                      const int32_t *ell_cnt, int64_t ell_stride)
 {
     IrrArgs A;
-    A.dyn = dyn;
     A.srec = srec;
     A.n = n;
     A.n_i = n_i;
@@ -246,7 +243,6 @@ void launch_irregular(cudaStream_t st, int precision, int num_sms, const void *s
     int64_t g = (n_i + rows_per_cta - 1) / rows_per_cta;
     const int64_t gmax = (int64_t)num_sms * 8;  // 8 CTAs of 8 warps: 64 warps per SM
     if (g > gmax) g = gmax;
-    if (dyn) g = num_sms;  // the row count is on the device: a fixed grid (8 rows a CTA), rows strided
     if (predicted) {
         if (precision == 0)
             k_irregular_rec_fp64<kIrrBlock><<<(int)g, kIrrBlock, 0, st>>>(A);

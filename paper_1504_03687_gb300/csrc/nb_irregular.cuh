@@ -23,20 +23,7 @@ struct IrrArgs {
     unsigned *status;
     const int32_t *ell_cnt;  // per-particle lists: i's list is nb[i * ell_stride .. + ell_cnt[i])
     int64_t ell_stride;      // 0: CSR lists (off)
-    const StepParams *dyn;   // device-driven step: n_i and t from here (nothing to do when halted)
 };
-
-// A device-driven step's row count and block time replace the launch's (false: halted).
-__device__ __forceinline__ bool irr_dyn(IrrArgs &A)
-{
-    if (!A.dyn) return true;
-    if (A.dyn->halt) return false;
-    A.n_i = A.dyn->n_act;
-    A.t = A.dyn->t;
-    A.t_hi = A.dyn->t_hi;
-    A.t_lo = A.dyn->t_lo;
-    return true;
-}
 
 // Row k's checked index and list range (an empty range and a status bit when malformed).
 __device__ __forceinline__ bool irr_row(const IrrArgs &A, int64_t k, int lane, int64_t &i, int64_t &e0, int64_t &e1)

@@ -102,6 +102,17 @@ nb_status nb_set_predicted(nb_ctx *ctx, int64_t n, const double *xp, const doubl
 /* Copy the predicted positions and velocities (n,3) out of the context. */
 nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp, int32_t on_device);
 
+/* Copy the j-records of the n predicted particles, the data the force kernels stream (built
+ * by nb_predict or nb_set_predicted; Sec. 3.2.1: the j-particles' predicted positions,
+ * velocities and masses), into out:
+ *   mixed: 12 floats per particle, {x_hi, y_hi, z_hi, m} {x_lo, y_lo, z_lo, 0} {vx, vy, vz, 0},
+ *          where hi is the FP64 position with its 29 low mantissa bits cleared (exactly a
+ *          float), lo = x - hi rounded to FP32, and v and m are rounded to FP32 (to nearest);
+ *   fp64:  8 doubles per particle, {x, y, z, m} {vx, vy, vz, 0}.
+ * out holds n * 48 bytes (mixed) or n * 64 bytes (fp64), host or device memory as on_device
+ * says; the caller owns it.  NB_ERR_STATE before any predicted state exists. */
+nb_status nb_get_records(nb_ctx *ctx, void *out, int32_t on_device);
+
 /* Regular force step for the active block idx[0..n_i) (Sec. 2, Sec. 3.2.1):
  *   acc_k  = sum_{j != i} m_j r / |r|^3
  *   jerk_k = sum_{j != i} m_j [ w / |r|^3 - 3 (r.w) r / |r|^5 ]
@@ -117,6 +128,8 @@ nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp, int32_t on_devic
  *                nb_idx[nb_off[k] .. nb_off[k+1]); each list holds at most nb_cap entries
  *                (the smallest j's).  If the lists need more than nb_idx_capacity entries
  *                in total, the CSR is cut there and NB_ERR_NB_OVERFLOW is reported.
+ *                With nb_idx NULL only the counts (and nb_off, if given) are produced, and
+ *                nothing is reported about a capacity.
  * nb_count_true: (n_i) int32, the untruncated neighbour count of each row (may be NULL).
  * n_i = 0 is allowed (only nb_off[0] = 0 is written).
  * Status: NB_ERR_NB_OVERFLOW (a warning, results valid) is returned by this call when

@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED}
 
 # every symbol include/nbgpu.h declares
 EXPORTS = ("nb_version", "nb_init", "nb_free", "nb_set_stream", "nb_set_particles", "nb_predict",
-           "nb_set_predicted", "nb_get_predicted", "nb_regular_force", "nb_regular_force_backward",
+           "nb_set_predicted", "nb_get_predicted", "nb_get_records", "nb_regular_force", "nb_regular_force_backward",
            "nb_sync", "nb_last_error", "nb_plan", "nb_plan_for", "nb_set_plan_override", "nb_set_timing",
            "nb_get_timings", "nb_regular_force_noalloc", "nb_batch_plan", "nb_regular_force_batched",
            "nb_set_plan_table", "nb_set_source_range", "nb_irregular_force", "nb_sched_init", "nb_sched_free",
@@ -88,6 +88,7 @@ def load_library(build_if_needed: bool = True):
         "nb_predict": (st, [P, dbl]),
         "nb_set_predicted": (st, [P, i64, P, P, P, i32]),
         "nb_get_predicted": (st, [P, P, P, i32]),
+        "nb_get_records": (st, [P, P, i32]),
         "nb_regular_force": (st, [P, i64, P, P, i32, P, P, P, P, P, i64, P, i32]),
         "nb_regular_force_backward": (st, [P, i64, P, P, P, P, P, P, P, i32]),
         "nb_sync": (st, [P]),
@@ -260,6 +261,16 @@ class Context:
         self._bind_stream()
         self._check(self.lib.nb_get_predicted(self.h, xp.data_ptr(), vp.data_ptr(), 1), "nb_get_predicted")
         return xp, vp
+
+    def get_records(self):
+        """The j-records of the predicted particles: (n, 12) float32 (mixed) or (n, 8) float64."""
+        torch = self._torch
+        mixed = self.precision == "mixed"
+        rec = torch.empty((self.n, 12 if mixed else 8), dtype=torch.float32 if mixed else torch.float64,
+                          device=f"cuda:{self.device}")
+        self._bind_stream()
+        self._check(self.lib.nb_get_records(self.h, rec.data_ptr(), 1), "nb_get_records")
+        return rec
 
     def regular_force(self, idx, rs2, neighbours: bool = True, nb_capacity: int | None = None,
                       out: ForceResult | None = None) -> ForceResult:

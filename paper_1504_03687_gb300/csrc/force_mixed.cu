@@ -18,7 +18,8 @@
 //  * j-streamed     : for tiny active blocks.  CTA = IB active particles x one j-chunk;
 //                     every warp streams its own contiguous sub-chunk (coalesced) and the
 //                     block reduces the IB x 7 partial sums with warp shuffles.  HBM /
-//                     latency bound.
+//                     latency bound.  One row a CTA in scalar form; four or eight rows as
+//                     row pairs in FP32x2 operations (k_force_mixed_jstream_x2).
 //  * batched        : many independent clusters in one persistent launch (a work queue of
 //                     cost-sorted items), the packed inner loop.
 // The per-call kernels write FP64 partial sums [split][7][n_i] that k_reduce adds in a fixed
@@ -392,6 +393,183 @@ __device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int
             hm |= (unsigned)hit << u;
         }
         if (hm) x2_record_hits<NP>(sc, jb + jc, hm, jend, L, nh, nl, rs2f, gi, slot0, sstride, cnt);
+    }
+}
+
+// Packed j-streamed kernel for small active blocks (IB = 4 or 8 rows a CTA).  The
+// decomposition is that of k_force_mixed_jstream: warp w walks the contiguous sub-chunk w of
+// the CTA's j-chunk, 32 consecutive j a round, one j a lane, and its neighbour segment
+// (g = s*W + w) is built in ascending j by ballot.  Every lane holds the IB rows as IB/2 row
+// pairs, so that each FP32x2 operation of the pair interaction updates two rows against the
+// lane's j (the operations and their order are those of tile_mixed_x2; r^2 is bit-identical
+// to pair_mixed's, so the neighbour decisions are the scalar kernel's).  The self-pair mask
+// is applied only in the one round of a warp that holds a row's own index, and the per-row
+// ballots run only in rounds where some lane has a hit, when that lane's r^2 is recomputed
+// with the same operations.
+// One round of the packed j-streamed kernel: the lane's j in the duplicated layout of the
+// tiled kernel ({xh,xh,yh,yh} {zh,zh,m,m} {xl,xl,yl,yl} {zl,zl,vx,vx}, and vy, vz) against
+// its NP row pairs; returns whether any of the rows has j inside its r_s.
+template <int NP, bool MASK>
+__device__ __forceinline__ bool js_round_x2(const float4 &a, const float4 &b, const float4 &c, const float4 &d,
+                                            float2 VY, float2 VZ, int32_t j32, const float2 (&nh)[NP][3],
+                                            const float2 (&nl)[NP][3], const float2 (&nv)[NP][3],
+                                            const float2 (&rs2f)[NP], const int32_t (&gi)[NP][2],
+                                            float2 (&acc)[NP][7])
+{
+    const float2 M = make_float2(b.z, b.w), VX = make_float2(d.z, d.w);
+    const float2 m3 = make_float2(-3.f, -3.f);
+    bool hit = false;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        float2 dx, dy, dz;
+        const float2 r2 = x2_r2(a, b, c, d, nh[q], nl[q], dx, dy, dz);
+        float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        if (MASK) {
+            rinv.x = (j32 == gi[q][0]) ? 0.f : rinv.x;
+            rinv.y = (j32 == gi[q][1]) ? 0.f : rinv.y;
+        }
+        const float2 wx = f2add(VX, nv[q][0]), wy = f2add(VY, nv[q][1]), wz = f2add(VZ, nv[q][2]);
+        const float2 rw = f2fma(dz, wz, f2fma(dy, wy, f2mul(dx, wx)));
+        const float2 rinv2 = f2mul(rinv, rinv);
+        const float2 mr = f2mul(M, rinv);
+        const float2 mr3 = f2mul(mr, rinv2);
+        const float2 beta = f2mul(rw, f2mul(rinv2, m3));
+        acc[q][0] = f2fma(mr3, dx, acc[q][0]);
+        acc[q][1] = f2fma(mr3, dy, acc[q][1]);
+        acc[q][2] = f2fma(mr3, dz, acc[q][2]);
+        acc[q][3] = f2fma(mr3, f2fma(beta, dx, wx), acc[q][3]);
+        acc[q][4] = f2fma(mr3, f2fma(beta, dy, wy), acc[q][4]);
+        acc[q][5] = f2fma(mr3, f2fma(beta, dz, wz), acc[q][5]);
+        acc[q][6] = f2add(acc[q][6], mr);
+        hit |= (r2.x < rs2f[q].x) | (r2.y < rs2f[q].y);
+    }
+    return hit;
+}
+
+template <int IB, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_force_mixed_jstream_x2(ForceArgs A)
+{
+    static_assert(IB % 2 == 0, "rows come in pairs");
+    constexpr int W = BLOCK / 32, NP = IB / 2;
+    __shared__ double red[W][IB][7];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int s = blockIdx.y;
+    const int64_t k0 = (int64_t)blockIdx.x * IB;
+    const int64_t j0 = A.j_lo + ((A.j_hi - A.j_lo) * s) / A.S, j1 = A.j_lo + ((A.j_hi - A.j_lo) * (s + 1)) / A.S;
+    const int64_t w0 = j0 + ((j1 - j0) * w) / W, w1 = j0 + ((j1 - j0) * (w + 1)) / W;
+    const int64_t g = (int64_t)s * W + w;
+    const float4 *rec = static_cast<const float4 *>(A.rec);
+
+    // the rows, negated (x - y is computed as x + (-y), which IEEE rounds identically)
+    float2 nh[NP][3], nl[NP][3], nv[NP][3], rs2f[NP];
+    int32_t gi[NP][2];
+    int cnt[IB];
+#pragma unroll
+    for (int q = 0; q < IB; ++q) {
+        const int64_t k = k0 + q;
+        int64_t gg = -1;
+        if (k < A.n_i) {
+            gg = A.idx[k];
+            if (gg < 0 || gg >= A.n) {
+                if (s == 0 && tid == 0) atomicOr(A.status, ST_BAD_INDEX);
+                gg = -1;
+            }
+        }
+        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, r = -1.f;
+        if (gg >= 0) {
+            const float4 p0 = rec[3 * gg], p1 = rec[3 * gg + 1], p2 = rec[3 * gg + 2];
+            h[0] = -p0.x; h[1] = -p0.y; h[2] = -p0.z;
+            l[0] = -p1.x; l[1] = -p1.y; l[2] = -p1.z;
+            v[0] = -p2.x; v[1] = -p2.y; v[2] = -p2.z;
+            if (A.want_nb) r = __double2float_rn(A.rs2[A.rs2_scalar ? 0 : k]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (q & 1) {
+                nh[q / 2][c].y = h[c]; nl[q / 2][c].y = l[c]; nv[q / 2][c].y = v[c];
+            } else {
+                nh[q / 2][c].x = h[c]; nl[q / 2][c].x = l[c]; nv[q / 2][c].x = v[c];
+            }
+        }
+        if (q & 1) rs2f[q / 2].y = r; else rs2f[q / 2].x = r;
+        gi[q / 2][q & 1] = (int32_t)gg;  // -1 matches no j
+        cnt[q] = 0;
+    }
+    float2 acc[NP][7];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[q][c] = make_float2(0.f, 0.f);
+
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t base = w0; base < w1; base += 32) {  // warp-uniform trip count
+        const int64_t j = base + lane;
+        const bool valid = j < w1;
+        const int32_t j32 = (int32_t)j;
+        float4 a, b, c, d;
+        float2 VY, VZ;
+        {
+            float4 p0 = make_float4(kPadPos, kPadPos, kPadPos, 0.f), p1 = make_float4(0.f, 0.f, 0.f, 0.f), p2 = p1;
+            if (valid) {
+                p0 = __ldg(rec + 3 * j);
+                p1 = __ldg(rec + 3 * j + 1);
+                p2 = __ldg(rec + 3 * j + 2);
+            }
+            a = make_float4(p0.x, p0.x, p0.y, p0.y);
+            b = make_float4(p0.z, p0.z, p0.w, p0.w);
+            c = make_float4(p1.x, p1.x, p1.y, p1.y);
+            d = make_float4(p1.z, p1.z, p2.x, p2.x);
+            VY = make_float2(p2.y, p2.y);
+            VZ = make_float2(p2.z, p2.z);
+        }
+        bool self = false;  // warp-uniform: does a row's own index fall in this round?
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            self |= (gi[q][0] >= base && gi[q][0] < base + 32) | (gi[q][1] >= base && gi[q][1] < base + 32);
+        const bool hit = self ? js_round_x2<NP, true>(a, b, c, d, VY, VZ, j32, nh, nl, nv, rs2f, gi, acc)
+                              : js_round_x2<NP, false>(a, b, c, d, VY, VZ, j32, nh, nl, nv, rs2f, gi, acc);
+        if (__any_sync(0xffffffffu, hit)) {  // rare: record this round's hits row by row
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float2 dx, dy, dz;
+                const float2 r2 = x2_r2(a, b, c, d, nh[q], nl[q], dx, dy, dz);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int row = 2 * q + h;
+                    const bool hq = valid && (h ? r2.y < rs2f[q].y : r2.x < rs2f[q].x) && j32 != gi[q][h];
+                    const unsigned mask = __ballot_sync(0xffffffffu, hq);
+                    if (mask) {
+                        const int pos = cnt[row] + __popc(mask & below);
+                        if (hq && pos < A.L) A.seg_slots[(g * A.n_i + k0 + row) * A.L + pos] = j32;
+                        cnt[row] += __popc(mask);
+                    }
+                }
+            }
+        }
+    }
+    if (A.want_nb && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < IB; ++q)
+            if (k0 + q < A.n_i) A.seg_cnt[g * A.n_i + k0 + q] = cnt[q];
+    }
+    // block reduction: warp shuffles, then one FP64 slot per warp, summed in warp order
+#pragma unroll
+    for (int q = 0; q < IB; ++q)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const float v = warp_sum((q & 1) ? acc[q / 2][c].y : acc[q / 2][c].x);
+            if (lane == 0) red[w][q][c] = (double)v;
+        }
+    __syncthreads();
+    for (int e = tid; e < IB * 7; e += BLOCK) {
+        const int q = e / 7, c = e % 7;
+        const int64_t k = k0 + q;
+        if (k < A.n_i) {
+            double sum = 0.0;
+#pragma unroll
+            for (int ww = 0; ww < W; ++ww) sum += red[ww][q][c];
+            A.part[((int64_t)s * 7 + c) * A.n_i + k] = (c == 6) ? -sum : sum;
+        }
     }
 }
 
@@ -1196,8 +1374,8 @@ void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x
     } else {
         switch (variant) {
         case 0: k_force_mixed_jstream<1, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
-        case 1: k_force_mixed_jstream<4, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
-        default: k_force_mixed_jstream<8, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        case 1: k_force_mixed_jstream_x2<4, kJstreamBlock, 2><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        default: k_force_mixed_jstream_x2<8, kJstreamBlock, 1><<<grid, kJstreamBlock, 0, st>>>(a); break;
         }
     }
 }

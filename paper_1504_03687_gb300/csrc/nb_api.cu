@@ -657,6 +657,19 @@ nb_status nb_get_predicted(nb_ctx *c, double *xp, double *vp, int32_t on_device)
     return NB_OK;
 }
 
+nb_status nb_get_records(nb_ctx *c, void *out, int32_t on_device)
+{
+    nb_status s = check_usable(c);
+    if (s != NB_OK) return s;
+    if (!c->have_pred) return fail(c, NB_ERR_STATE, "no predicted state");
+    if (!out) return fail(c, NB_ERR_ARG, "null array");
+    const size_t b = (size_t)c->n * (c->precision == NB_FP64 ? 2 * sizeof(dvec4) : 3 * sizeof(float4));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(out, c->rec, b, kind, c->stream), "cudaMemcpyAsync");
+    if (!on_device) CK(ctx_sync(c), "cudaStreamSynchronize");
+    return NB_OK;
+}
+
 // The plan of a call: the override if one is set, else the first tuned table entry whose
 // bucket holds n_i, else the automatic plan.
 static Plan ctx_plan(const nb_ctx *c, int64_t n, int64_t n_i)
@@ -949,16 +962,26 @@ nb_status nb_regular_force(nb_ctx *c, int64_t n_i, const int32_t *idx, const dou
     launch_force(c->stream, p, fa);
     CK_LAUNCH("force kernel launch");
     span_end(c, PH_FORCE, t0, 1);
-    t0 = span_begin(c);
-    launch_reduce(c->stream, c->part, p.S, n_i, d_acc, d_jerk, d_pot, fa.perm);  // anchored: row-order positions
-    CK_LAUNCH("k_reduce launch");
-    span_end(c, PH_REDUCE, t0, 1);
-    if (want_nb) {
-        // counts only: the scan still needs an offsets buffer, taken from the scan scratch
-        int64_t *off_buf = d_off ? d_off : c->scan + neighbour_scan_tmp_elems(n_i);
+    // counts only: the scan still needs an offsets buffer, taken from the scan scratch
+    int64_t *off_buf = want_nb ? (d_off ? d_off : c->scan + neighbour_scan_tmp_elems(n_i)) : nullptr;
+    const bool tiny = !fa.perm && n_i <= kTinyRows && (!want_nb || tiny_epilogue_fits(G, n_i));
+    if (tiny) {  // a tiny block: the sums and the lists in one launch (timed as the reduction)
+        t0 = span_begin(c);
+        launch_tiny_epilogue(c->stream, c->part, p.S, n_i, d_acc, d_jerk, d_pot, G, L, c->cap,
+                             want_nb ? c->seg_cnt : nullptr, c->seg_slots, off_buf, d_nbidx,
+                             d_nbidx ? nb_idx_capacity : INT64_MAX, d_cnt_true, c->status);
+        CK_LAUNCH("tiny-block epilogue launch");
+        span_end(c, PH_REDUCE, t0, 1);
+    } else {
+        t0 = span_begin(c);
+        launch_reduce(c->stream, c->part, p.S, n_i, d_acc, d_jerk, d_pot, fa.perm);  // anchored: row-order positions
+        CK_LAUNCH("k_reduce launch");
+        span_end(c, PH_REDUCE, t0, 1);
+    }
+    if (want_nb && !tiny) {
         t0 = span_begin(c);
         const int kernels = launch_neighbour_csr(c->stream, G, n_i, L, c->cap, c->seg_cnt, c->seg_slots, off_buf,
-                                                 d_nbidx, d_nbidx ? nb_idx_capacity : 0, d_cnt_true, c->scan,
+                                                 d_nbidx, d_nbidx ? nb_idx_capacity : INT64_MAX, d_cnt_true, c->scan,
                                                  c->row_total, c->status, fa.perm);
         CK_LAUNCH("neighbour CSR launch");
         span_end(c, PH_NEIGHBOURS, t0, kernels);

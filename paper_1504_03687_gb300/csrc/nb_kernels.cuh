@@ -82,6 +82,18 @@ int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap
 
 size_t neighbour_scan_tmp_elems(int64_t n_i);
 
+// Reduction and neighbour CSR of a tiny active block (n_i <= kTinyRows, rows in caller order)
+// in one launch, in place of launch_reduce + launch_neighbour_csr, with the same results:
+// the same bits of the sums, the same offsets, counts, lists and status flags.  seg_cnt null:
+// sums only; nb_idx null or L = 0: counts and offsets only.  It stages the G x n_i segment
+// counts in shared memory, so it applies while tiny_epilogue_fits(G, n_i).
+constexpr int kTinyRows = 8;  // one CTA does it all: past a few rows the work outgrows the launches saved
+constexpr int kTinySmemMax = 100 * 1024;
+bool tiny_epilogue_fits(int64_t G, int64_t n_i);
+void launch_tiny_epilogue(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc, double *jerk,
+                          double *pot, int64_t G, int L, int cap, const int32_t *seg_cnt, const int32_t *seg_slots,
+                          int64_t *off, int32_t *nb_idx, int64_t nb_capacity, int32_t *count_true, unsigned *status);
+
 // Device state of a context, for the integrator inside the library (nb_api.cu).
 struct CtxState {
     double *x, *v, *a, *jk, *tl, *m, *xp, *vp;

@@ -6,6 +6,8 @@
 // that j-segment in ascending order and their true count.  K5 sums the counts per row
 // (the untruncated neighbour number), scans min(count, nb_cap) into CSR offsets, and
 // gathers each row's segments in segment order until nb_cap entries are written.
+#include <atomic>
+
 #include "nb_common.cuh"
 #include "nb_kernels.cuh"
 
@@ -302,6 +304,197 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_seg_gather_rows(const int32_t *__
             if (o0 + pos + e < capacity) nb_idx[o0 + pos + e] = src[e];
         pos += c;
     }
+}
+
+// ------------------------------------------------------------------------------ tiny blocks
+// Reduction and neighbour CSR of a tiny active block (at most kTinyRows rows, in caller order)
+// in one CTA, in place of the reduce kernel and the three CSR kernels: for such a block the
+// dependent launches, not the work, are the cost.  The partial sums are added in the order
+// launch_reduce takes for S splits (a warp per row and component: lanes over the splits and
+// the warp butterfly for S > 16, one lane in split order otherwise), so they carry the same
+// bits.  The lists are those of the CSR kernels: the G x n_i segment counts are staged in
+// shared memory (row r's segments contiguous, row stride Gp odd so the transposing stores
+// do not collide in a bank); one block scan over the (row, segment) items, each thread
+// owning a contiguous run of them, gives every row's true count, kept = min(count, cap), the
+// offsets (a scan over the rows) and every segment's place in its row; a segment's kept
+// entries (at most L) are copied there while the row has room.
+constexpr int kTinyBlock = 1024;
+constexpr int kTinyPer = (kTinySmemMax / 4 + kTinyBlock - 1) / kTinyBlock;  // counts a thread loads
+
+__global__ void __launch_bounds__(kTinyBlock) k_tiny_epilogue(
+    const double *__restrict__ part, int S, int n_i, double *__restrict__ acc, double *__restrict__ jerk,
+    double *__restrict__ pot, int G, int L, int cap, const int32_t *__restrict__ seg_cnt,
+    const int32_t *__restrict__ seg_slots, int64_t *__restrict__ off, int32_t *__restrict__ nb_idx, int64_t capacity,
+    int32_t *__restrict__ count_true, unsigned *status)
+{
+    extern __shared__ int32_t cnt_s[];  // [n_i][Gp]
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t base_l[kTinyRows + 1], base_t[kTinyRows + 1], row_off[kTinyRows], row_kept[kTinyRows];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int Gp = G | 1;
+    const int F = G * n_i;  // at most kTinySmemMax / 4 items
+    // segment counts into shared memory: every load of a thread issued before the first
+    // store (a single CTA cannot hide the latency of one load at a time), in global order
+    if (seg_cnt) {
+        int v[kTinyPer];
+#pragma unroll
+        for (int i = 0; i < kTinyPer; ++i) {
+            const int f = tid + i * kTinyBlock;
+            v[i] = f < F ? seg_cnt[f] : 0;
+        }
+        // f = tid + i * kTinyBlock is segment f / n_i of row f % n_i: stepped, not divided
+        int r = tid % n_i, g = tid / n_i;
+        const int dr = kTinyBlock % n_i, dg = kTinyBlock / n_i;
+#pragma unroll
+        for (int i = 0; i < kTinyPer; ++i) {
+            if (tid + i * kTinyBlock < F) cnt_s[r * Gp + g] = v[i];
+            r += dr;
+            g += dg;
+            if (r >= n_i) r -= n_i, ++g;
+        }
+    }
+    // the sums: item e = (row e / 7, component e % 7), a warp each
+    for (int e = w; e < n_i * 7; e += kTinyBlock / 32) {
+        const int r = e / 7, c = e % 7;
+        const double *pc = part + (int64_t)c * n_i + r;  // split s at pc[s * 7 * n_i]
+        const int64_t ps = (int64_t)7 * n_i;
+        double sum = 0.0;
+        if (S > 16) {
+#pragma unroll 8
+            for (int s = lane; s < S; s += 32) sum += pc[s * ps];
+            sum = warp_sum(sum);
+        } else if (lane == 0) {
+#pragma unroll 8
+            for (int s = 0; s < S; ++s) sum += pc[s * ps];
+        }
+        if (lane == 0) {
+            if (c < 3)
+                acc[3 * r + c] = sum;
+            else if (c < 6)
+                jerk[3 * r + c - 3] = sum;
+            else
+                pot[r] = sum;
+        }
+    }
+    if (!seg_cnt) return;  // no neighbour output wanted
+    __syncthreads();
+    // thread-contiguous runs [f0, f1) of the flattened items f = r * G + g
+    const int per = (F + kTinyBlock - 1) / kTinyBlock;
+    const int f0 = tid * per < F ? tid * per : F, f1 = f0 + per < F ? f0 + per : F;
+    const int r0 = f0 / G, g0 = f0 % G;
+    int64_t sl = 0, st = 0;  // stored (at most L a segment) and true counts of the run
+    for (int f = f0, r = r0, g = g0; f < f1; ++f) {
+        const int c = cnt_s[r * Gp + g];
+        sl += c < L ? c : L;
+        st += c;
+        if (++g == G) g = 0, ++r;
+    }
+    int64_t tot_l, tot_t;
+    const int64_t ex_l = block_exclusive_scan(sl, wsum, tot_l);
+    const int64_t ex_t = block_exclusive_scan(st, wsum, tot_t);
+    {  // the prefixes at the first segment of every row
+        int64_t pl = ex_l, pt = ex_t;
+        for (int f = f0, r = r0, g = g0; f < f1; ++f) {
+            const int c = cnt_s[r * Gp + g];
+            if (g == 0) {
+                base_l[r] = pl;
+                base_t[r] = pt;
+            }
+            pl += c < L ? c : L;
+            pt += c;
+            if (++g == G) g = 0, ++r;
+        }
+        if (tid == 0) {
+            base_l[n_i] = tot_l;
+            base_t[n_i] = tot_t;
+        }
+    }
+    __syncthreads();
+    if (w == 0) {  // rows: true and kept counts, offsets (a warp scan over at most 32 rows)
+        int64_t c = 0, kept = 0;
+        if (lane < n_i) {
+            c = base_t[lane + 1] - base_t[lane];
+            kept = c < cap ? c : cap;
+            if (c > cap) atomicOr(status, ST_NB_TRUNCATED);
+            if (count_true) count_true[lane] = (int32_t)(c < INT32_MAX ? c : INT32_MAX);
+        }
+        int64_t x = kept;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < n_i) {
+            off[lane] = x - kept;
+            row_off[lane] = x - kept;
+            row_kept[lane] = kept;
+        }
+        if (lane == 31) {
+            off[n_i] = x;
+            if (x > capacity) atomicOr(status, ST_CSR_FULL);
+        }
+    }
+    if (!nb_idx || L <= 0) return;
+    // every count becomes its segment's place in the row: the entries the row's earlier
+    // segments store (each run is read and overwritten by its own thread only)
+    {
+        int64_t pl = ex_l;
+        for (int f = f0, r = r0, g = g0; f < f1; ++f) {
+            int32_t *q = &cnt_s[r * Gp + g];
+            const int c = *q;
+            *q = (int32_t)(pl - base_l[r]);
+            pl += c < L ? c : L;
+            if (++g == G) g = 0, ++r;
+        }
+    }
+    __syncthreads();
+    // the copies, spread over the output positions: position o of the CSR lies in row r
+    // (row_off[r] <= o < row_off[r] + kept_r) at place q of it, taken from the last segment
+    // whose place is <= q (a binary search over the row's places); a dense row's entries come
+    // from few segments, so a thread per segment would copy them one after another
+    const int64_t total = row_off[n_i - 1] + row_kept[n_i - 1];
+    const int64_t last = total < capacity ? total : capacity;
+    for (int64_t o = tid; o < last; o += kTinyBlock) {
+        int r = 0, rh = n_i;  // the last row whose offset is <= o
+        while (rh - r > 1) {
+            const int mid = (r + rh) >> 1;
+            if (row_off[mid] <= o) r = mid; else rh = mid;
+        }
+        const int q = (int)(o - row_off[r]);
+        const int32_t *P = cnt_s + r * Gp;
+        int lo = 0, hi = G;  // the first segment whose place exceeds q is hi
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (P[mid] <= q) lo = mid + 1; else hi = mid;
+        }
+        const int g = lo - 1;
+        nb_idx[o] = seg_slots[((int64_t)g * n_i + r) * L + (q - P[g])];
+    }
+}
+
+bool tiny_epilogue_fits(int64_t G, int64_t n_i)
+{
+    return n_i >= 1 && n_i <= kTinyRows && (G | 1) * n_i * 4 <= kTinySmemMax;
+}
+
+void launch_tiny_epilogue(cudaStream_t st, const double *part, int S, int64_t n_i, double *acc, double *jerk,
+                          double *pot, int64_t G, int L, int cap, const int32_t *seg_cnt, const int32_t *seg_slots,
+                          int64_t *off, int32_t *nb_idx, int64_t nb_capacity, int32_t *count_true, unsigned *status)
+{
+    const size_t smem = seg_cnt ? (size_t)(G | 1) * n_i * 4 : 0;
+    if (smem > 48 * 1024) {  // the opt-in above 48 KB of dynamic shared memory, once per device
+        static std::atomic<unsigned long long> done{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const unsigned long long bit = 1ull << (dev & 63);
+        if (!(done.load() & bit)) {
+            if (cudaFuncSetAttribute(k_tiny_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, kTinySmemMax) ==
+                cudaSuccess)
+                done.fetch_or(bit);
+        }
+    }
+    k_tiny_epilogue<<<1, kTinyBlock, smem, st>>>(part, S, (int)n_i, acc, jerk, pot, (int)G, L, cap, seg_cnt, seg_slots,
+                                                 off, nb_idx, nb_capacity, count_true, status);
 }
 
 int launch_neighbour_csr(cudaStream_t st, int64_t G, int64_t n_i, int L, int cap, const int32_t *seg_cnt,

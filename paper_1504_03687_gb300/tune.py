@@ -11,7 +11,7 @@ the same kind of device installs it without re-tuning (Context.apply_tuned()).
 
 The batched ensemble form is tuned the same way over its tile variants (tune_batched).
 
-Usage (on a GPU): python -m paper_1504_03687_gb300.tune --n 1048576 [--prec mixed]
+Usage (on a GPU): python -m paper_1504_03687_gb300.tune --n 1048576 [--prec mixed] [--max-ni 32]
 """
 from __future__ import annotations
 
@@ -133,6 +133,15 @@ def save_table(key: str, table, path: str = TABLE_FILE):
         json.dump(data, f, indent=1, sort_keys=True)
 
 
+def merge_table(old, new):
+    """The stored table with the buckets of `new` replaced (or added), in bucket order: a
+    re-tune of some buckets keeps the entries of the others."""
+    keep = {float(e[0]): list(e) for e in (old or [])}
+    for e in new:
+        keep[float(e[0])] = [float(e[0])] + list(e[1:4]) + [float(e[4])]
+    return [keep[k] for k in sorted(keep)]
+
+
 def apply_table(ctx, table):
     """Install a tuned table: bucket b covers (previous bucket, b]; the last bucket covers
     every larger block as well."""
@@ -153,6 +162,8 @@ def main():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--out", default=TABLE_FILE)
+    ap.add_argument("--max-ni", type=int, default=0,
+                    help="re-tune only the buckets up to this block size and keep the stored others")
     args = ap.parse_args()
     cl = W.king(args.n, 2, W0=6.0, masses="kroupa", binary_fraction=0.05)
     rs2 = W.neighbour_radius2(cl.x, 80, seed=2)
@@ -164,8 +175,12 @@ def main():
     buckets = [1 << k for k in range(0, int(math.log2(cl.n)) + 1, 1)]
     if args.prec == "fp64":
         buckets = [b for b in buckets if b <= 1 << 14]
+    if args.max_ni > 0:
+        buckets = [b for b in buckets if b <= args.max_ni]
     table = tune_force(ctx, order, rs2, buckets=buckets, reps=args.reps)
     key = device_key(args.prec, cl.n)
+    if args.max_ni > 0:
+        table = merge_table(load_table(key, args.out), table)
     save_table(key, table, args.out)
     print(json.dumps({"key": key, "table": table}))
 

@@ -129,6 +129,74 @@ def test_predictor_within_rounding(gpu_lib, prec):
     assert (xp.cpu().numpy() != rx).mean() < 0.5  # mostly bit-identical anyway
 
 
+def expected_records(xp, vp, m, prec):
+    """The j-records as the header defines them, from the FP64 predicted state, with numpy's
+    FP64 -> FP32 conversion (round to nearest, ties to even)."""
+    if prec == "fp64":
+        out = np.zeros((len(m), 8))
+        out[:, 0:3], out[:, 3], out[:, 4:7] = xp, m, vp
+        return out.view(np.uint64)
+    hi = (xp.view(np.uint64) & ~np.uint64(0x1FFFFFFF)).view(np.float64)
+    with np.errstate(over="ignore"):
+        out = np.zeros((len(m), 12), np.float32)
+        out[:, 0:3], out[:, 3] = hi.astype(np.float32), m.astype(np.float32)
+        out[:, 4:7] = (xp - hi).astype(np.float32)
+        out[:, 8:11] = vp.astype(np.float32)
+    return out.view(np.uint32)
+
+
+def edge_values(rng, k):
+    """FP64 values that take every branch of the record's rounding: zeros, values exact in
+    FP32, ties and near-ties at the rounding bit of x (v, m) and of x - hi, remainders of
+    every length, carries into the exponent, magnitudes outside the normal FP32 range."""
+    e = rng.integers(1023 - 40, 1023 + 40, k).astype(np.uint64)
+    mant = rng.integers(0, 1 << 52, k, dtype=np.uint64)
+    sign = rng.integers(0, 2, k).astype(np.uint64) << np.uint64(63)
+    kind = np.arange(k) % 6
+    low = mant & np.uint64(0x1FFFFFFF)
+    sh = rng.integers(1, 6, k).astype(np.uint64)
+    tie_lo = ((rng.integers(0, 1 << 24, k, dtype=np.uint64) | np.uint64(1 << 23)) << sh) | (np.uint64(1) << (sh - np.uint64(1)))
+    low = np.where(kind == 0, np.uint64(0x10000000), low)                       # tie of x -> float
+    low = np.where(kind == 1, tie_lo & np.uint64(0x1FFFFFFF), low)             # tie of lo
+    low = np.where(kind == 2, low >> rng.integers(0, 29, k).astype(np.uint64), low)  # short remainders
+    low = np.where(kind == 3, np.uint64(0), low)                               # exact in FP32
+    mant = (mant & ~np.uint64(0x1FFFFFFF)) | low
+    mant = np.where(kind == 4, np.uint64(0xFFFFFF0000000) | (mant & np.uint64(0xFFFFFFF)), mant)  # carries
+    b = sign | (e << np.uint64(52)) | mant
+    v = b.view(np.float64).copy()
+    special = np.array([0.0, -0.0, 1.5, -3.25, 1e-40, -1e-40, 1e-30, 3e-39, 3.4028235677973366e38, 1e39,
+                        -1e39, 2.0 ** -126, 2.0 ** 127 * 1.9999999, 5e-324])
+    v[:len(special)] = special
+    return v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_records_are_the_rounded_predicted_state(gpu_lib, prec):
+    """The j-records the force kernels stream, bit for bit: from the predictor's output
+    (Plummer 1k with a Hermite state) and from chosen edge values loaded as a predicted state
+    (mixed: the hi/lo split and the FP32 roundings of v and m; fp64: plain copies)."""
+    cl, _ = W.plummer_1k_equal()
+    steps = W.block_steps(cl, seed=0)
+    a0, j0, tl = W.hermite_state(cl, seed=1, t_block=0.5, steps=steps)
+    ctx = make_ctx(cl.n, prec)
+    ctx.set_particles(T(cl.x), T(cl.v), T(a0), T(j0), T(cl.m), T(tl))
+    ctx.predict(0.5)
+    xp, vp = (q.cpu().numpy() for q in ctx.get_predicted())
+    got = ctx.get_records().cpu().numpy()
+    assert np.array_equal(got.view(np.uint32 if prec == "mixed" else np.uint64), expected_records(xp, vp, cl.m, prec))
+    rng = np.random.default_rng(11)
+    n = 3000
+    xq = edge_values(rng, 3 * n).reshape(n, 3)
+    vq = edge_values(rng, 3 * n).reshape(n, 3)[rng.permutation(n)]
+    mq = np.abs(edge_values(rng, n))
+    ctx2 = make_ctx(n, prec)
+    ctx2.set_predicted(T(xq), T(vq), T(mq))
+    got = ctx2.get_records().cpu().numpy()
+    assert np.array_equal(got.view(np.uint32 if prec == "mixed" else np.uint64), expected_records(xq, vq, mq, prec))
+    ctx.close()
+    ctx2.close()
+
+
 # ------------------------------------------------------------------ Plummer 1024, full block
 @pytest.fixture(scope="module")
 def p1k():
@@ -255,6 +323,91 @@ def test_csr_capacity_too_small_is_reported(gpu_lib, p1k):
     assert res.nb_off[-1] == sum(min(c, 512) for c in ref[3])
     flat = np.concatenate(ref[4])[:100]
     np.testing.assert_array_equal(res.nb_idx[:100], flat)
+
+
+# ------------------------------------------------------------------ tiny blocks (one-launch epilogue)
+@pytest.mark.parametrize("prec,plan", [("fp64", (0, 0, 20)), ("fp64", (0, 0, 8)), ("mixed", (1, 4, 24)),
+                                       ("mixed", (1, 4, 5))])
+def test_tiny_block_epilogue_is_bit_identical(gpu_lib, p128k, prec, plan):
+    """Blocks of at most 8 rows take one launch for the partial-sum reduction and the
+    neighbour CSR.  With a forced plan whose per-row partial sums do not depend on the other
+    rows of the block, the rows of a 6-row block must carry the same bits (sums, counts,
+    offsets within the row, lists) as the same rows inside a 100-row block, which takes the
+    separate reduction and CSR kernels; the split counts reach both reduction orders (more
+    than 16 splits: lanes over the splits and a butterfly; up to 16: split order)."""
+    cl, rs2, steps = p128k
+    idx = W.active_block(steps, 100)
+    ctx = make_ctx(cl.n, prec)
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    ctx.set_plan_override(*plan)
+    big = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    small = ctx.regular_force(T(idx[:6]), rs2)
+    ctx.sync()
+    for a, b in ((small.acc, big.acc[:6]), (small.jerk, big.jerk[:6]), (small.pot, big.pot[:6]),
+                 (small.nb_count, big.nb_count[:6])):
+        assert torch.equal(a, b)
+    ls, lb = lists_of(small), lists_of(big)
+    for k in range(6):
+        assert np.array_equal(ls[k], lb[k]), k
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tiny_block_cap_truncation_and_capacity(gpu_lib, p1k, prec):
+    """A 5-row block with many neighbours a row, cap 16: lists keep the smallest indices and
+    the true counts are reported; then a CSR buffer too small for the kept entries is
+    reported, its offsets still those of the full lists and its first entries the lists'."""
+    from paper_1504_03687_gb300 import api
+    cl, rs2, idx, _ = p1k
+    big = 9 * rs2
+    sel = idx[[3, 100, 511, 700, 1023]]
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, sel, big, cap=16)
+    assert (ref[3] > 16).all()
+    ctx = make_ctx(cl.n, prec, cap=16)
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    res = ctx.regular_force(T(sel), big)
+    with pytest.warns(Warning):
+        ctx.sync()
+    if prec == "fp64":
+        check_lists_exact(res, ref[3], ref[4], 16)
+    else:
+        check_lists_band(res, cl.x, sel, big, ref[3], ref[4], 16)
+    with pytest.warns(api.NBOverflow):
+        small = ctx.regular_force(T(sel), big, nb_capacity=40)
+        ctx.sync()
+    assert int(small.nb_off[-1]) == 5 * 16
+    assert torch.equal(small.nb_off, res.nb_off)
+    assert torch.equal(small.nb_idx[:40], res.nb_idx[:40])
+    ctx.close()
+
+
+def test_tiny_block_counts_only(gpu_lib, p1k):
+    """Through the C ABI with no list buffer: a 7-row block gets the true counts and the
+    offsets of the kept counts, as the oracle's lists give them, and no capacity report."""
+    import ctypes
+    cl, rs2, idx, _ = p1k
+    sel = idx[::113][:7].astype(np.int32)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, sel, rs2, cap=512)
+    ctx = make_ctx(cl.n, "fp64")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    d_idx, d_rs2 = T(sel), T(np.array([rs2]))
+    acc = torch.empty((7, 3), dtype=torch.float64, device=DEV)
+    jerk, pot = torch.empty_like(acc), torch.empty(7, dtype=torch.float64, device=DEV)
+    off = torch.full((8,), -7, dtype=torch.int64, device=DEV)
+    cnt = torch.full((7,), -7, dtype=torch.int32, device=DEV)
+    ctx._bind_stream()
+    s = ctx.lib.nb_regular_force(ctx.h, 7, d_idx.data_ptr(), d_rs2.data_ptr(), 1, acc.data_ptr(), jerk.data_ptr(),
+                                 pot.data_ptr(), off.data_ptr(), None, 0, cnt.data_ptr(), 1)
+    assert s == 0
+    assert ctx.sync(allow_overflow=False) == 0
+    np.testing.assert_array_equal(cnt.cpu().numpy(), ref[3])
+    assert ref[3].max() <= 512
+    kept = ref[3]
+    np.testing.assert_array_equal(off.cpu().numpy(), np.concatenate([[0], np.cumsum(kept)]))
+    check_fp64(type("R", (), {"acc": acc.cpu().numpy(), "jerk": jerk.cpu().numpy(), "pot": pot.cpu().numpy()}),
+               ref, cl.x, cl.v, cl.m, sel)
+    ctx.close()
 
 
 def test_per_particle_rs2(gpu_lib, p1k):
@@ -443,6 +596,33 @@ def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
         ctx.sync()
     check_mixed(res, ref)
     check_lists_band(res, cl.x, idx, big, ref[3], ref[4], 16)
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("n_i,splits", [(1, 37), (3, 37), (6, 152), (16, 37), (21, 5)])
+def test_jstream_variants(gpu_lib, p128k, variant, n_i, splits):
+    """The j-streamed kernels of tiny blocks (1, 4 and 8 rows a CTA, the last batch ragged;
+    the 4- and 8-row forms packed FP32x2), forced at several j-split counts: the mixed bars
+    against the oracle on every row, lists within the 1e-6 band of the oracle's, and lists
+    identical to those of the packed tiled kernel with one split."""
+    cl, rs2, steps = p128k
+    idx = W.active_block(steps, n_i)
+    ref = oracle.regular_force(cl.x, cl.v, cl.m, idx, rs2, cap=512)
+    ctx = make_ctx(cl.n, "mixed")
+    ctx.set_predicted(T(cl.x), T(cl.v), T(cl.m))
+    ctx.set_plan_override(2, variant, splits)
+    assert ctx.plan(cl.n, n_i)["kernel"] == 2
+    res = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    check_mixed(res, ref)
+    check_lists_band(res, cl.x, idx, rs2, ref[3], ref[4], 512)
+    ctx.set_plan_override(1, 4, 1)
+    one = ctx.regular_force(T(idx), rs2)
+    ctx.sync()
+    assert torch.equal(one.nb_off, res.nb_off) and torch.equal(one.nb_count, res.nb_count)
+    tot = int(one.nb_off[-1])
+    assert torch.equal(one.nb_idx[:tot], res.nb_idx[:tot])
     ctx.close()
 
 

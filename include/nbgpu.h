@@ -315,7 +315,8 @@ nb_status nb_plan(const nb_ctx *ctx, int64_t n, int64_t n_i, int64_t *out);
  * benchmark individual kernel variants): kernel and variant as reported by nb_plan (mixed
  * tiled kernel variants: 0-3 scalar double-single, 4-9 packed FP32x2 double-single, 10-14
  * packed with anchor-relative separations over the spatial row order, 15-19 the same with the
- * neighbour hits staged in shared memory and written as whole 32- or 64-byte groups),
+ * neighbour hits staged in shared memory and written as whole 32- or 64-byte groups; mixed
+ * j-streamed variants: 0 one row a CTA, 1-3 four, eight and two rows a CTA as FP32x2 pairs),
  * `splits` j-splits (clipped to the tile count; 0 with the mixed tiled kernel = the
  * planner's split count for that variant).  kernel < 0 restores automatic planning.
  * NB_ERR_ARG if the kernel does not match the context's precision. */

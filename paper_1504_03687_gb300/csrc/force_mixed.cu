@@ -18,8 +18,8 @@
 //  * j-streamed     : for tiny active blocks.  CTA = IB active particles x one j-chunk;
 //                     every warp streams its own contiguous sub-chunk (coalesced) and the
 //                     block reduces the IB x 7 partial sums with warp shuffles.  HBM /
-//                     latency bound.  One row a CTA in scalar form; four or eight rows as
-//                     row pairs in FP32x2 operations (k_force_mixed_jstream_x2).
+//                     latency bound.  One row a CTA in scalar form; two, four or eight rows
+//                     as row pairs in FP32x2 operations (k_force_mixed_jstream_x2).
 //  * batched        : many independent clusters in one persistent launch (a work queue of
 //                     cost-sorted items), the packed inner loop.
 // The per-call kernels write FP64 partial sums [split][7][n_i] that k_reduce adds in a fixed
@@ -396,7 +396,7 @@ __device__ __forceinline__ void tile_mixed_x2(const float4 *__restrict__ sd, int
     }
 }
 
-// Packed j-streamed kernel for small active blocks (IB = 4 or 8 rows a CTA).  The
+// Packed j-streamed kernel for small active blocks (IB = 2, 4 or 8 rows a CTA).  The
 // decomposition is that of k_force_mixed_jstream: warp w walks the contiguous sub-chunk w of
 // the CTA's j-chunk, 32 consecutive j a round, one j a lane, and its neighbour segment
 // (g = s*W + w) is built in ascending j by ballot.  Every lane holds the IB rows as IB/2 row
@@ -1356,7 +1356,7 @@ void *mixed_tiled_fn(int v)
 int mixed_tiled_i_per_cta(int v) { return kTiled[v].ni * kTiled[v].block; }
 int mixed_tiled_block(int v) { return kTiled[v].block; }
 int mixed_tiled_tj(int v) { return kTiled[v].tj; }
-int mixed_jstream_ib(int v) { return v == 0 ? 1 : (v == 1 ? 4 : 8); }
+int mixed_jstream_ib(int v) { return v == 0 ? 1 : (v == 1 ? 4 : (v == 2 ? 8 : 2)); }
 constexpr int kJstreamBlock = 256;
 int jstream_warps() { return kJstreamBlock / 32; }
 
@@ -1375,7 +1375,9 @@ void launch_force_mixed(cudaStream_t st, int kernel, int variant, int64_t ctas_x
         switch (variant) {
         case 0: k_force_mixed_jstream<1, kJstreamBlock><<<grid, kJstreamBlock, 0, st>>>(a); break;
         case 1: k_force_mixed_jstream_x2<4, kJstreamBlock, 2><<<grid, kJstreamBlock, 0, st>>>(a); break;
-        default: k_force_mixed_jstream_x2<8, kJstreamBlock, 1><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        case 2: k_force_mixed_jstream_x2<8, kJstreamBlock, 1><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        case 3: k_force_mixed_jstream_x2<2, kJstreamBlock, 3><<<grid, kJstreamBlock, 0, st>>>(a); break;
+        default: break;
         }
     }
 }

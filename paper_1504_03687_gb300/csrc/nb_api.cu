@@ -293,11 +293,14 @@ static Plan plan_force_variant(int precision, int num_sms, const int *occ, int64
     const int64_t n_pad = ((n + kTilePad - 1) / kTilePad) * kTilePad;
     if (precision == NB_MIXED) {
         if (n_i <= 32 && only_variant < 0) {
+            // one row a CTA up to two rows, then the packed forms: two rows a CTA (three CTAs an
+            // SM) up to 16 rows, four rows a CTA above (measured on a GB300, King W0 = 6, 2^20)
             p.kernel = 2;
-            p.variant = n_i <= 2 ? 0 : (n_i <= 16 ? 1 : 2);
+            p.variant = n_i <= 2 ? 0 : (n_i <= 16 ? 3 : 1);
             p.i_per_cta = mixed_jstream_ib(p.variant);
             const int64_t batches = (n_i + p.i_per_cta - 1) / p.i_per_cta;
-            int64_t S = (4 * (int64_t)num_sms + batches - 1) / batches;
+            const int64_t per_sm = p.variant == 3 ? 3 : 4;
+            int64_t S = (per_sm * (int64_t)num_sms + batches - 1) / batches;
             const int64_t smax = n / 2048 > 1 ? n / 2048 : 1;  // >= 2048 j per CTA
             if (S > smax) S = smax;
             if (S < 1) S = 1;
@@ -433,9 +436,11 @@ static Plan forced_plan(int precision, int num_sms, const int *occ, int64_t n, i
         p.tj = 0;
     }
     int64_t S = splits > 0 ? splits : 1;
-    if (splits <= 0 && p.tj == 0) {  // j-streamed kernel, automatic splits: ~4 CTAs per SM
+    if (splits <= 0 && p.tj == 0) {  // j-streamed kernel, automatic splits: ~4 CTAs per SM (3 for the
+                                     // two-row packed form, which fits three)
         const int64_t batches = (n_i + p.i_per_cta - 1) / p.i_per_cta;
-        S = (4 * (int64_t)(num_sms > 0 ? num_sms : 152) + batches - 1) / (batches > 0 ? batches : 1);
+        const int64_t per_sm = (kernel == 2 && variant == 3) ? 3 : 4;
+        S = (per_sm * (int64_t)(num_sms > 0 ? num_sms : 152) + batches - 1) / (batches > 0 ? batches : 1);
         const int64_t per = kernel == 2 ? 2048 : 1024;
         const int64_t smax = n / per > 1 ? n / per : 1;
         if (S > smax) S = smax;
@@ -686,7 +691,7 @@ static Plan ctx_plan(const nb_ctx *c, int64_t n, int64_t n_i)
 static bool plan_valid(int precision, int kernel, int variant, int splits)
 {
     const bool ok = (kernel == 1 && precision == NB_MIXED && variant >= 0 && variant < kMixedTiledVariants) ||
-                    (kernel == 2 && precision == NB_MIXED && variant >= 0 && variant <= 2) ||
+                    (kernel == 2 && precision == NB_MIXED && variant >= 0 && variant <= 3) ||
                     (kernel == 0 && precision == NB_FP64 && variant == 0) ||
                     (kernel == 3 && precision == NB_FP64 && variant >= 0 && variant <= 1);
     return ok && splits >= 0 && !(splits == 0 && kernel == 0);
@@ -826,7 +831,7 @@ nb_status nb_set_plan_override(nb_ctx *c, int32_t kernel, int32_t variant, int32
         return NB_OK;
     }
     const bool ok = (kernel == 1 && c->precision == NB_MIXED && variant >= 0 && variant < kMixedTiledVariants) ||
-                    (kernel == 2 && c->precision == NB_MIXED && variant >= 0 && variant <= 2) ||
+                    (kernel == 2 && c->precision == NB_MIXED && variant >= 0 && variant <= 3) ||
                     (kernel == 0 && c->precision == NB_FP64 && variant == 0) ||
                     (kernel == 3 && c->precision == NB_FP64 && variant >= 0 && variant <= 1);
     if (!ok || splits < 0 || (splits == 0 && kernel == 0))

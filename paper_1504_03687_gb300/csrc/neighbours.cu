@@ -309,15 +309,17 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_seg_gather_rows(const int32_t *__
 // ------------------------------------------------------------------------------ tiny blocks
 // Reduction and neighbour CSR of a tiny active block (at most kTinyRows rows, in caller order)
 // in one CTA, in place of the reduce kernel and the three CSR kernels: for such a block the
-// dependent launches, not the work, are the cost.  The partial sums are added in the order
-// launch_reduce takes for S splits (a warp per row and component: lanes over the splits and
-// the warp butterfly for S > 16, one lane in split order otherwise), so they carry the same
-// bits.  The lists are those of the CSR kernels: the G x n_i segment counts are staged in
-// shared memory (row r's segments contiguous, row stride Gp odd so the transposing stores
-// do not collide in a bank); one block scan over the (row, segment) items, each thread
-// owning a contiguous run of them, gives every row's true count, kept = min(count, cap), the
-// offsets (a scan over the rows) and every segment's place in its row; a segment's kept
-// entries (at most L) are copied there while the row has room.
+// dependent launches, not the work, are the cost (with more rows the one CTA's own work, FP64
+// adds on one SM and the copies of dense rows, outgrows the launches saved).  The partial sums
+// are added in the order launch_reduce takes for S splits (a warp per row and component:
+// lanes over the splits and the warp butterfly for S > 16, one lane in split order
+// otherwise), so they carry the same bits.  The lists are those of the CSR kernels: the
+// G x n_i segment counts are staged in shared memory (row r's segments contiguous, row stride
+// Gp odd so the transposing stores do not collide in a bank); one block scan over the
+// (row, segment) items, each thread owning a contiguous run of them, gives every row's true
+// count, kept = min(count, cap), the offsets (a scan over the rows) and every segment's place
+// in its row, which replaces its count in shared memory; then every output position finds its
+// row and, by binary search over the places, the segment entry it takes.
 constexpr int kTinyBlock = 1024;
 constexpr int kTinyPer = (kTinySmemMax / 4 + kTinyBlock - 1) / kTinyBlock;  // counts a thread loads
 

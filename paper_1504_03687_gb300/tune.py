@@ -25,7 +25,7 @@ import numpy as np
 TABLE_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_plans.json")
 
 # candidate plans: (kernel, variant, splits); splits 0 = the planner's split count
-MIXED_CANDIDATES = [(1, v, 0) for v in range(20)] + [(2, v, 0) for v in range(3)]
+MIXED_CANDIDATES = [(1, v, 0) for v in range(20)] + [(2, v, 0) for v in range(4)]
 # the mixed variants that stage their neighbour hits and write them as whole groups (less
 # DRAM traffic for the same lists); a plan within TIE of the fastest counts as a tie (the
 # run-to-run spread of a call is about 1 %), and a tie goes to the fastest of these

@@ -599,11 +599,11 @@ def test_each_mixed_tiled_variant_dense_lists(gpu_lib, p1k, variant):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("n_i,splits", [(1, 37), (3, 37), (6, 152), (16, 37), (21, 5)])
 def test_jstream_variants(gpu_lib, p128k, variant, n_i, splits):
-    """The j-streamed kernels of tiny blocks (1, 4 and 8 rows a CTA, the last batch ragged;
-    the 4- and 8-row forms packed FP32x2), forced at several j-split counts: the mixed bars
+    """The j-streamed kernels of tiny blocks (1, 4, 8 and 2 rows a CTA, the last batch ragged;
+    the 2-, 4- and 8-row forms packed FP32x2), forced at several j-split counts: the mixed bars
     against the oracle on every row, lists within the 1e-6 band of the oracle's, and lists
     identical to those of the packed tiled kernel with one split."""
     cl, rs2, steps = p128k

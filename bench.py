@@ -41,8 +41,8 @@ NB_CAP = 512
 # dram__bytes_write.sum; -s 12 -c 4: the timed step's launches), valid only for the
 # force-kernel sources whose SHA-256 is recorded with them (FORCE_SOURCES: the kernels, their
 # device helpers and their argument header).
-FORCE_TRAFFIC = {"sources_sha256": "a97e8ef19a8697714bc54875ec96781ba72361fc54159dd16efb80cebf6586df",
-                 "bytes_per_launch": [55232256, 119086592, 431151104, 1169663232]}
+FORCE_TRAFFIC = {"sources_sha256": "3af94ab8688af704dc2a434cae013cb3e265cf9e64425017717da68e9a09c748",
+                 "bytes_per_launch": [55140864, 119358976, 431456768, 1169148672]}
 FORCE_SOURCES = ("force_mixed.cu", "nb_common.cuh", "nb_force.cuh", "roworder.cu")
 
 

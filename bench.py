@@ -658,7 +658,7 @@ def bench_small_blocks(ctx, n, order, rs2_dev, dev, sizes=(1, 16, 128, 1024), re
            "blocks": {}}
     for b in sizes:
         idx = torch.as_tensor(order[:b], device=dev)
-        force, step = [], []
+        force, step, phases = [], [], []
         for it in range(reps + 3):
             flush.fill_(it & 0xff)
             torch.cuda.synchronize()
@@ -671,9 +671,15 @@ def bench_small_blocks(ctx, n, order, rs2_dev, dev, sizes=(1, 16, 128, 1024), re
             if it >= 3:
                 force.append(ph["force"][0])
                 step.append(sum(v[0] for v in ph.values()))
+                phases.append(ph)
         f = float(np.median(force))
         gbs = rec_bytes / (f * 1e-3) / 1e9
+        # where the step goes: predictor, row order, force, and the reduction + CSR (one launch
+        # for blocks of at most 8 rows, timed as the reduction)
+        med = {k: float(np.median([p[k][0] for p in phases])) for k in ("predict", "order", "force")}
+        med["reduce_and_csr"] = float(np.median([p["reduce"][0] + p["neighbours"][0] for p in phases]))
         res["blocks"][str(b)] = {"force_ms_median": f, "step_ms_median": float(np.median(step)),
+                                 "phase_ms_median": med,
                                  "achieved_GBs": gbs, "frac_of_hbm_peak": gbs / peak if peak else None,
                                  "plan": ctx.plan(n, b)}
     ctx.sync()

@@ -485,11 +485,11 @@ void launch_tiny_epilogue(cudaStream_t st, const double *part, int S, int64_t n_
 {
     const size_t smem = seg_cnt ? (size_t)(G | 1) * n_i * 4 : 0;
     if (smem > 48 * 1024) {  // the opt-in above 48 KB of dynamic shared memory, once per device
-        static std::atomic<unsigned long long> done{0};
+        static std::atomic<unsigned long long> done{0};  // a bit per device 0..63; others set it every call
         int dev = 0;
         cudaGetDevice(&dev);
-        const unsigned long long bit = 1ull << (dev & 63);
-        if (!(done.load() & bit)) {
+        const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+        if (!bit || !(done.load() & bit)) {
             if (cudaFuncSetAttribute(k_tiny_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, kTinySmemMax) ==
                 cudaSuccess)
                 done.fetch_or(bit);

@@ -53,13 +53,15 @@ def test_null_arguments_are_rejected_without_gpu():
 OCC = [3, 4, 4, 1, 3, 4, 3, 2, 8, 12, 3, 4, 2, 8, 12, 3, 4, 2, 3, 2, 3]  # resident CTAs/SM: 20 mixed tiled variants, FP64 tiled
 
 
-@pytest.mark.parametrize("n_i", [1, 2, 16, 32, 33, 100, 1024, 16384, 131072, 1 << 20])
+@pytest.mark.parametrize("n_i", [1, 2, 3, 8, 16, 17, 32, 33, 100, 1024, 16384, 131072, 1 << 20])
 def test_planner_mixed(n_i):
     n = 1 << 20
     p = api.plan_for("mixed", 152, OCC, n, n_i)
     if n_i <= 32:
         assert p["kernel"] == 2 and p["tile"] == 0
         assert p["ctas"] >= 152  # small blocks still spread over every SM
+        # one row a CTA up to 2 rows, two-row packed pairs up to 16, four-row above
+        assert (p["variant"], p["i_per_cta"]) == ((0, 1) if n_i <= 2 else (3, 2) if n_i <= 16 else (1, 4))
     else:
         assert p["kernel"] == 1 and p["tile"] in (128, 256)
         tiles = ((n + 255) // 256 * 256) // p["tile"]

@@ -460,6 +460,45 @@ def test_degenerate_sizes(gpu_lib):
         ctx.close()
 
 
+def test_two_particles_1e_12_apart(gpu_lib):
+    """Two distinct particles 1e-12 length units apart inside a 64-body Plummer sphere (the
+    self-exclusion reading: distinct particles are never skipped, only j = i is).  FP64: every
+    row, the close pair's included, within the FP64 bar of the oracle.  Mixed: the positions
+    carry 2^-48 |x| in double-single, so the pair's separation (|x| about 0.6) is known to a few
+    parts in 1e3 and its two rows are bounded by 1e-2; every other row keeps the mixed bars.
+    Both find each other as neighbours; with the whole block (tiled kernels) and with just the
+    pair (the j-streamed kernel)."""
+    cl = W.plummer(64, 79)
+    d = np.array([0.6, -0.48, 0.64]) * 1e-12
+    x = np.concatenate([cl.x, cl.x[:1] + d])
+    v = np.concatenate([cl.v, cl.v[:1] + np.array([[0.01, 0.02, -0.01]])])
+    m = np.concatenate([cl.m, cl.m[:1]])
+    n, close = x.shape[0], np.array([0, 64])
+    assert 0 < np.linalg.norm(x[64] - x[0]) < 2e-12
+    rs2 = float(W.neighbour_radius2(x, 8, seed=79))
+    for rows in (np.arange(n, dtype=np.int32), close.astype(np.int32)):
+        ref = oracle.regular_force(x, v, m, rows, rs2, cap=64)
+        for prec in ("fp64", "mixed"):
+            ctx = make_ctx(n, prec, cap=64)
+            ctx.set_predicted(T(x), T(v), T(m))
+            res = ctx.regular_force(T(rows), rs2)
+            ctx.sync()
+            if prec == "fp64":
+                check_fp64(res, ref, x, v, m, rows)
+            else:
+                for g, r in ((res.acc, ref[0]), (res.jerk, ref[1]), (res.pot, ref[2])):
+                    e = rel_err(g.cpu().numpy(), r)
+                    pair = np.isin(rows, close)
+                    assert e[pair].max() <= 1e-2, float(e[pair].max())
+                    if (~pair).any():
+                        assert np.median(e[~pair]) <= 2e-6 and e[~pair].max() <= 1e-4
+            got = res.neighbour_lists()
+            for k, i in enumerate(rows):
+                if i in close:
+                    assert (64 if i == 0 else 0) in set(got[k].tolist())
+            ctx.close()
+
+
 def test_call_order_and_argument_errors(gpu_lib):
     from paper_1504_03687_gb300 import api
     ctx = make_ctx(8, "mixed")
